@@ -1,0 +1,880 @@
+/*
+ * FP64 CPU oracle for the polar AC-OPF callbacks with branch-flow variables.
+ *
+ * TEST INFRASTRUCTURE ONLY: it judges the CUDA path. Only the tests, the smoke
+ * check and the benchmark's CPU baseline may load it; the library never does,
+ * and the two share no code.
+ *
+ * What it computes, and where the paper states it:
+ *   - NLP form  min f(x)  s.t.  xl <= x <= xu,  gl <= g(x) <= gu      (Sec. II-A)
+ *   - callbacks obj, grad, cons, jac, hess(x, lambda; obj_weight)       (Listing 1)
+ *   - the static polar model with branch-flow variables                 (Listing 3)
+ *       variables va, vm, pg, qg, p, q and their bounds
+ *       objective sum of generator costs (quadratic c2 pg^2 + c1 pg + c0)
+ *       ref angle, four branch-flow rows, angle difference, P/Q balance with
+ *       the arc and generator augmentations of constraint!, two thermal rows
+ *     The flow functions follow the pi-model of the formulation the paper
+ *     points to (Sec. III-C-1, "as described in" PowerModels / MATPOWER):
+ *       ys = 1/(r + j x), tap tau (0 means 1), shift theta, charging b split
+ *       Yff = (ys + j b/2)/tau^2, Yft = -ys/conj(tau e^{j theta}),
+ *       Ytf = -ys/(tau e^{j theta}), Ytt = ys + j b/2,
+ *       S_fr = V_f conj(Yff V_f + Yft V_t),  S_to = V_t conj(Ytf V_f + Ytt V_t).
+ *   - multi-period: per-period demand, ramp rows |pg_t - pg_{t-1}| <= ratio pmax
+ *     (Sec. III-C-2, Listing 6, corrective_action_ratio), 2-D layout of Listing 10
+ *   - constraint violation Cvio (Sec. IV-A)
+ *
+ * Readings where the paper is silent (flow row = variable minus function,
+ * thermal p^2+q^2-rate^2, demand Pd + gs vm^2 / Qd - bs vm^2, arc numbering,
+ * Hessian as deduplicated lower triangle in (row, col) order) are listed in
+ * the design notes of the repository.
+ *
+ * Every value is computed in complex arithmetic on the pi-model; derivatives
+ * are derived by hand in complex form (d/dva V = j V, d/dvm V = V/vm). The
+ * sparsity pattern is built from the term structure alone, then every term's
+ * contribution is added into its entry found by binary search. No blocking,
+ * no fusion, one thread.
+ */
+#include "oracle.h"
+
+#include <complex.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef double complex cplx;
+
+static __thread char g_err[512];
+
+static void set_err(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+}
+
+const char *ora_error(void) { return g_err; }
+
+enum { G_REF, G_FPF, G_FQF, G_FPT, G_FQT, G_ANG, G_PB, G_QB, G_THF, G_THT, G_RAMP };
+
+typedef struct {
+    ora_net net;     /* pointers into the owned copies below */
+    void *own[32];
+    int nown;
+    int64_t xoff, coff;  /* first variable / first row of this instance */
+    int64_t n, m;
+    int ramp;
+    double *Pd, *Qd;     /* per bus and period: [nperiod][nbus] */
+} inst_t;
+
+struct ora_ctx {
+    int ninst;
+    inst_t *in;
+    double link_ratio;
+    int link;
+    int64_t n, m, link_row;
+    int64_t nnzj, nnzh;
+    int64_t *jrow, *jcol, *jkey;
+    int64_t *hrow, *hcol, *hkey;
+};
+
+/* ---------------------------------------------------------------- layout -- */
+
+static int64_t v_va(const inst_t *s, int64_t i, int64_t t)
+{
+    return s->xoff + i + (int64_t)s->net.nbus * t;
+}
+static int64_t v_vm(const inst_t *s, int64_t i, int64_t t)
+{
+    int64_t nbT = (int64_t)s->net.nbus * s->net.nperiod;
+    return s->xoff + nbT + i + (int64_t)s->net.nbus * t;
+}
+static int64_t v_pg(const inst_t *s, int64_t g, int64_t t)
+{
+    int64_t nbT = (int64_t)s->net.nbus * s->net.nperiod;
+    return s->xoff + 2 * nbT + g + (int64_t)s->net.ngen * t;
+}
+static int64_t v_qg(const inst_t *s, int64_t g, int64_t t)
+{
+    int64_t T = s->net.nperiod, nbT = (int64_t)s->net.nbus * T, ngT = (int64_t)s->net.ngen * T;
+    return s->xoff + 2 * nbT + ngT + g + (int64_t)s->net.ngen * t;
+}
+static int64_t v_p(const inst_t *s, int64_t a, int64_t t)
+{
+    int64_t T = s->net.nperiod, nbT = (int64_t)s->net.nbus * T, ngT = (int64_t)s->net.ngen * T;
+    return s->xoff + 2 * nbT + 2 * ngT + a + 2 * (int64_t)s->net.nbranch * t;
+}
+static int64_t v_q(const inst_t *s, int64_t a, int64_t t)
+{
+    int64_t T = s->net.nperiod, nbT = (int64_t)s->net.nbus * T, ngT = (int64_t)s->net.ngen * T;
+    int64_t naT = 2 * (int64_t)s->net.nbranch * T;
+    return s->xoff + 2 * nbT + 2 * ngT + naT + a + 2 * (int64_t)s->net.nbranch * t;
+}
+
+/* row of element e of group grp in period t (ramp: t = 1..T-1) */
+static int64_t row_of(const inst_t *s, int grp, int64_t e, int64_t t)
+{
+    int64_t T = s->net.nperiod, nl = s->net.nbranch, nb = s->net.nbus;
+    int64_t size[10] = {1, nl, nl, nl, nl, nl, nb, nb, nl, nl};
+    int64_t base = 0;
+    for (int k = 0; k < grp && k < 10; k++)
+        base += size[k] * T;
+    if (grp == G_RAMP)
+        return s->coff + base + e + (int64_t)s->net.ngen * (t - 1);
+    return s->coff + base + e + size[grp] * t;
+}
+
+/* arc a: a < nbranch is the from-end of branch a, else the to-end of a - nbranch */
+static int arc_bus(const inst_t *s, int64_t a)
+{
+    int64_t nl = s->net.nbranch;
+    return a < nl ? s->net.f[a] : s->net.t[a - nl];
+}
+
+/* ------------------------------------------------------------ pi-model -- */
+
+/* One end of a branch: S_i = V_i conj(Y_ii V_i + Y_ij V_j), V = vm e^{j va}.
+ * Local variable order u = (vm_i, vm_j, va_i, va_j).  First and second
+ * derivatives follow from dV/dvm = e^{j va} and dV/dva = j V. The b* fields
+ * bound the modulus of each quantity by a sum of moduli of its terms. */
+typedef struct {
+    cplx S, dS[4], d2S[4][4];
+    double bS, bdS[4], bd2S[4][4];
+} bend_t;
+
+static void branch_end(double vmi, double vmj, double vai, double vaj, cplx Yii, cplx Yij,
+                       bend_t *e)
+{
+    cplx Ei = cexp(I * vai), Ej = cexp(I * vaj);
+    cplx Vi = vmi * Ei, Vj = vmj * Ej;
+    cplx Ii = Yii * Vi + Yij * Vj;
+    cplx W = Vi * conj(Yij * Vj); /* the cross (transfer) part of S_i */
+    double ai = cabs(Yii), aj = cabs(Yij);
+
+    e->S = Vi * conj(Ii);
+    e->bS = ai * vmi * vmi + aj * vmi * vmj;
+
+    e->dS[0] = Ei * conj(Ii) + vmi * conj(Yii); /* d/dvm_i */
+    e->dS[1] = Vi * conj(Yij * Ej);             /* d/dvm_j */
+    e->dS[2] = I * W;                           /* d/dva_i */
+    e->dS[3] = -I * W;                          /* d/dva_j */
+    e->bdS[0] = ai * vmi + aj * vmj + ai * vmi;
+    e->bdS[1] = aj * vmi;
+    e->bdS[2] = aj * vmi * vmj;
+    e->bdS[3] = aj * vmi * vmj;
+
+    cplx d2[4][4];
+    double b2[4][4];
+    d2[0][0] = 2.0 * conj(Yii);             b2[0][0] = 2.0 * ai;
+    d2[0][1] = Ei * conj(Yij * Ej);         b2[0][1] = aj;
+    d2[1][1] = 0.0;                         b2[1][1] = 0.0;
+    d2[0][2] = I * Ei * conj(Yij * Vj);     b2[0][2] = aj * vmj;
+    d2[0][3] = -I * Ei * conj(Yij * Vj);    b2[0][3] = aj * vmj;
+    d2[1][2] = I * Vi * conj(Yij * Ej);     b2[1][2] = aj * vmi;
+    d2[1][3] = -I * Vi * conj(Yij * Ej);    b2[1][3] = aj * vmi;
+    d2[2][2] = -W;                          b2[2][2] = aj * vmi * vmj;
+    d2[2][3] = W;                           b2[2][3] = aj * vmi * vmj;
+    d2[3][3] = -W;                          b2[3][3] = aj * vmi * vmj;
+    for (int a = 0; a < 4; a++)
+        for (int b = a; b < 4; b++) {
+            e->d2S[a][b] = e->d2S[b][a] = d2[a][b];
+            e->bd2S[a][b] = e->bd2S[b][a] = b2[a][b];
+        }
+}
+
+/* the four admittances of branch k */
+static void branch_Y(const ora_net *n, int k, cplx *Yff, cplx *Yft, cplx *Ytf, cplx *Ytt)
+{
+    cplx ys = 1.0 / (n->r[k] + I * n->x[k]);
+    double tau = n->tap[k] == 0.0 ? 1.0 : n->tap[k];
+    cplx T = tau * cexp(I * n->shift[k]);
+    cplx ych = I * (n->b[k] / 2.0);
+    *Yff = (ys + ych) / (tau * tau);
+    *Yft = -ys / conj(T);
+    *Ytf = -ys / T;
+    *Ytt = ys + ych;
+}
+
+typedef struct {
+    int64_t u[4];      /* global (vm_i, vm_j, va_i, va_j) */
+    bend_t e;
+    int64_t pvar, qvar; /* the arc's own flow variables */
+} end_t;
+
+static void ends_of(const inst_t *s, const double *x, int k, int t, end_t *fr, end_t *to)
+{
+    const ora_net *n = &s->net;
+    int f = n->f[k], b = n->t[k];
+    cplx Yff, Yft, Ytf, Ytt;
+    branch_Y(n, k, &Yff, &Yft, &Ytf, &Ytt);
+    double vmf = x[v_vm(s, f, t)], vmt = x[v_vm(s, b, t)];
+    double vaf = x[v_va(s, f, t)], vat = x[v_va(s, b, t)];
+    branch_end(vmf, vmt, vaf, vat, Yff, Yft, &fr->e);
+    branch_end(vmt, vmf, vat, vaf, Ytt, Ytf, &to->e);
+    fr->u[0] = v_vm(s, f, t); fr->u[1] = v_vm(s, b, t);
+    fr->u[2] = v_va(s, f, t); fr->u[3] = v_va(s, b, t);
+    to->u[0] = v_vm(s, b, t); to->u[1] = v_vm(s, f, t);
+    to->u[2] = v_va(s, b, t); to->u[3] = v_va(s, f, t);
+    fr->pvar = v_p(s, k, t); fr->qvar = v_q(s, k, t);
+    to->pvar = v_p(s, n->nbranch + k, t); to->qvar = v_q(s, n->nbranch + k, t);
+}
+
+/* ---------------------------------------------------------------- create -- */
+
+static void *own_copy(inst_t *s, const void *src, size_t bytes)
+{
+    void *p = malloc(bytes ? bytes : 1);
+    if (bytes)
+        memcpy(p, src, bytes);
+    s->own[s->nown++] = p;
+    return p;
+}
+
+static double *own_fill(inst_t *s, const double *src, int64_t count, double dflt)
+{
+    double *p = malloc(sizeof(double) * (count ? count : 1));
+    for (int64_t i = 0; i < count; i++)
+        p[i] = src ? src[i] : dflt;
+    s->own[s->nown++] = p;
+    return p;
+}
+
+static int cmp_i64(const void *a, const void *b)
+{
+    int64_t x = *(const int64_t *)a, y = *(const int64_t *)b;
+    return (x > y) - (x < y);
+}
+
+static int64_t sort_unique(int64_t *k, int64_t cnt)
+{
+    qsort(k, (size_t)cnt, sizeof(int64_t), cmp_i64);
+    int64_t w = 0;
+    for (int64_t i = 0; i < cnt; i++)
+        if (w == 0 || k[i] != k[w - 1])
+            k[w++] = k[i];
+    return w;
+}
+
+static int64_t find(const int64_t *keys, int64_t nnz, int64_t key)
+{
+    int64_t lo = 0, hi = nnz - 1;
+    while (lo <= hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (keys[mid] == key)
+            return mid;
+        if (keys[mid] < key)
+            lo = mid + 1;
+        else
+            hi = mid - 1;
+    }
+    return -1;
+}
+
+void ora_destroy(ora_ctx *C)
+{
+    if (!C)
+        return;
+    for (int s = 0; s < C->ninst; s++)
+        for (int k = 0; k < C->in[s].nown; k++)
+            free(C->in[s].own[k]);
+    free(C->in);
+    free(C->jrow); free(C->jcol); free(C->jkey);
+    free(C->hrow); free(C->hcol); free(C->hkey);
+    free(C);
+}
+
+static int validate(const ora_net *n)
+{
+    if (n->nbus < 1 || n->nbranch < 0 || n->ngen < 0 || n->nload < 0 || n->nperiod < 1) {
+        set_err("bad sizes");
+        return -1;
+    }
+    if (n->ref_bus < 0 || n->ref_bus >= n->nbus) {
+        set_err("ref_bus out of range");
+        return -1;
+    }
+    for (int k = 0; k < n->nbranch; k++) {
+        if (n->f[k] < 0 || n->f[k] >= n->nbus || n->t[k] < 0 || n->t[k] >= n->nbus ||
+            n->f[k] == n->t[k]) {
+            set_err("branch %d endpoints invalid", k);
+            return -1;
+        }
+        if (n->r[k] == 0.0 && n->x[k] == 0.0) {
+            set_err("branch %d has zero impedance", k);
+            return -1;
+        }
+        if (n->tap && n->tap[k] < 0.0) {
+            set_err("branch %d has negative tap", k);
+            return -1;
+        }
+    }
+    for (int g = 0; g < n->ngen; g++)
+        if (n->gen_bus[g] < 0 || n->gen_bus[g] >= n->nbus) {
+            set_err("gen %d bus out of range", g);
+            return -1;
+        }
+    for (int l = 0; l < n->nload; l++)
+        if (n->load_bus[l] < 0 || n->load_bus[l] >= n->nbus) {
+            set_err("load %d bus out of range", l);
+            return -1;
+        }
+    return 0;
+}
+
+static void push(int64_t *keys, int64_t *cnt, int64_t n, int64_t r, int64_t c)
+{
+    keys[(*cnt)++] = r * n + c;
+}
+
+ora_ctx *ora_create(const ora_net *nets, int32_t ninst, double link_ratio)
+{
+    if (ninst < 1) {
+        set_err("ninst < 1");
+        return NULL;
+    }
+    for (int s = 0; s < ninst; s++)
+        if (validate(&nets[s]))
+            return NULL;
+    ora_ctx *C = calloc(1, sizeof *C);
+    C->ninst = ninst;
+    C->in = calloc((size_t)ninst, sizeof(inst_t));
+    C->link_ratio = link_ratio;
+    C->link = link_ratio > 0.0 && ninst > 1;
+    if (C->link)
+        for (int s = 0; s < ninst; s++)
+            if (nets[s].ngen != nets[0].ngen || nets[s].nperiod != 1) {
+                set_err("linking rows need equal ngen and one period");
+                ora_destroy(C);
+                return NULL;
+            }
+    int64_t xo = 0, co = 0;
+    for (int s = 0; s < ninst; s++) {
+        inst_t *S = &C->in[s];
+        const ora_net *n = &nets[s];
+        ora_net *d = &S->net;
+        *d = *n;
+        int64_t nb = n->nbus, nl = n->nbranch, ng = n->ngen, nlo = n->nload, T = n->nperiod;
+        d->vmin = own_copy(S, n->vmin, sizeof(double) * nb);
+        d->vmax = own_copy(S, n->vmax, sizeof(double) * nb);
+        d->gs = own_fill(S, n->gs, nb, 0.0);
+        d->bs = own_fill(S, n->bs, nb, 0.0);
+        d->f = own_copy(S, n->f, sizeof(int32_t) * nl);
+        d->t = own_copy(S, n->t, sizeof(int32_t) * nl);
+        d->r = own_copy(S, n->r, sizeof(double) * nl);
+        d->x = own_copy(S, n->x, sizeof(double) * nl);
+        d->b = own_copy(S, n->b, sizeof(double) * nl);
+        d->tap = own_fill(S, n->tap, nl, 1.0);
+        d->shift = own_fill(S, n->shift, nl, 0.0);
+        d->rate_a = own_copy(S, n->rate_a, sizeof(double) * nl);
+        d->angmin = own_copy(S, n->angmin, sizeof(double) * nl);
+        d->angmax = own_copy(S, n->angmax, sizeof(double) * nl);
+        d->gen_bus = own_copy(S, n->gen_bus, sizeof(int32_t) * ng);
+        d->pmin = own_copy(S, n->pmin, sizeof(double) * ng);
+        d->pmax = own_copy(S, n->pmax, sizeof(double) * ng);
+        d->qmin = own_copy(S, n->qmin, sizeof(double) * ng);
+        d->qmax = own_copy(S, n->qmax, sizeof(double) * ng);
+        d->c2 = own_copy(S, n->c2, sizeof(double) * ng);
+        d->c1 = own_copy(S, n->c1, sizeof(double) * ng);
+        d->c0 = own_fill(S, n->c0, ng, 0.0);
+        d->load_bus = own_copy(S, n->load_bus, sizeof(int32_t) * nlo);
+        d->pd = own_copy(S, n->pd, sizeof(double) * nlo * T);
+        d->qd = own_copy(S, n->qd, sizeof(double) * nlo * T);
+        /* demand per bus and period: sum of the loads at the bus */
+        S->Pd = own_fill(S, NULL, nb * T, 0.0);
+        S->Qd = own_fill(S, NULL, nb * T, 0.0);
+        for (int64_t t = 0; t < T; t++)
+            for (int64_t l = 0; l < nlo; l++) {
+                S->Pd[t * nb + d->load_bus[l]] += d->pd[t * nlo + l];
+                S->Qd[t * nb + d->load_bus[l]] += d->qd[t * nlo + l];
+            }
+        S->ramp = T > 1 && n->ramp_ratio > 0.0;
+        S->n = T * (2 * nb + 2 * ng + 4 * nl);
+        S->m = T * (1 + 7 * nl + 2 * nb) + (S->ramp ? ng * (T - 1) : 0);
+        S->xoff = xo;
+        S->coff = co;
+        xo += S->n;
+        co += S->m;
+    }
+    C->n = xo;
+    C->link_row = co;
+    C->m = co + (C->link ? (int64_t)nets[0].ngen * (ninst - 1) : 0);
+
+    /* ---- Jacobian pattern: one (row, col) per variable a term depends on */
+    int64_t cap = 0;
+    for (int s = 0; s < ninst; s++) {
+        const ora_net *n = &C->in[s].net;
+        int64_t T = n->nperiod;
+        cap += T * (1 + 30 * (int64_t)n->nbranch + 2 * (int64_t)n->nbus + 2 * (int64_t)n->ngen) +
+               2 * (int64_t)n->ngen * T;
+    }
+    cap += C->link ? 2 * (int64_t)nets[0].ngen * ninst : 0;
+    int64_t *keys = malloc(sizeof(int64_t) * (cap + 1));
+    int64_t cnt = 0, N = C->n;
+    for (int s = 0; s < ninst; s++) {
+        const inst_t *S = &C->in[s];
+        const ora_net *n = &S->net;
+        int64_t nl = n->nbranch;
+        for (int t = 0; t < n->nperiod; t++) {
+            push(keys, &cnt, N, row_of(S, G_REF, 0, t), v_va(S, n->ref_bus, t));
+            for (int k = 0; k < nl; k++) {
+                int f = n->f[k], b = n->t[k];
+                int64_t dep[4] = {v_vm(S, f, t), v_vm(S, b, t), v_va(S, f, t), v_va(S, b, t)};
+                int64_t own[4] = {v_p(S, k, t), v_q(S, k, t), v_p(S, nl + k, t), v_q(S, nl + k, t)};
+                int grp[4] = {G_FPF, G_FQF, G_FPT, G_FQT};
+                for (int r = 0; r < 4; r++) {
+                    int64_t row = row_of(S, grp[r], k, t);
+                    push(keys, &cnt, N, row, own[r]);
+                    for (int d = 0; d < 4; d++)
+                        push(keys, &cnt, N, row, dep[d]);
+                }
+                push(keys, &cnt, N, row_of(S, G_ANG, k, t), v_va(S, f, t));
+                push(keys, &cnt, N, row_of(S, G_ANG, k, t), v_va(S, b, t));
+                push(keys, &cnt, N, row_of(S, G_THF, k, t), v_p(S, k, t));
+                push(keys, &cnt, N, row_of(S, G_THF, k, t), v_q(S, k, t));
+                push(keys, &cnt, N, row_of(S, G_THT, k, t), v_p(S, nl + k, t));
+                push(keys, &cnt, N, row_of(S, G_THT, k, t), v_q(S, nl + k, t));
+            }
+            for (int i = 0; i < n->nbus; i++) {
+                push(keys, &cnt, N, row_of(S, G_PB, i, t), v_vm(S, i, t));
+                push(keys, &cnt, N, row_of(S, G_QB, i, t), v_vm(S, i, t));
+            }
+            for (int64_t a = 0; a < 2 * nl; a++) {
+                int i = arc_bus(S, a);
+                push(keys, &cnt, N, row_of(S, G_PB, i, t), v_p(S, a, t));
+                push(keys, &cnt, N, row_of(S, G_QB, i, t), v_q(S, a, t));
+            }
+            for (int g = 0; g < n->ngen; g++) {
+                int i = n->gen_bus[g];
+                push(keys, &cnt, N, row_of(S, G_PB, i, t), v_pg(S, g, t));
+                push(keys, &cnt, N, row_of(S, G_QB, i, t), v_qg(S, g, t));
+            }
+            if (S->ramp && t >= 1)
+                for (int g = 0; g < n->ngen; g++) {
+                    push(keys, &cnt, N, row_of(S, G_RAMP, g, t), v_pg(S, g, t));
+                    push(keys, &cnt, N, row_of(S, G_RAMP, g, t), v_pg(S, g, t - 1));
+                }
+        }
+    }
+    if (C->link)
+        for (int s = 1; s < ninst; s++)
+            for (int g = 0; g < nets[0].ngen; g++) {
+                int64_t row = C->link_row + g + (int64_t)nets[0].ngen * (s - 1);
+                push(keys, &cnt, N, row, v_pg(&C->in[s], g, 0));
+                push(keys, &cnt, N, row, v_pg(&C->in[0], g, 0));
+            }
+    C->nnzj = sort_unique(keys, cnt);
+    C->jkey = keys;
+    C->jrow = malloc(sizeof(int64_t) * (C->nnzj + 1));
+    C->jcol = malloc(sizeof(int64_t) * (C->nnzj + 1));
+    for (int64_t e = 0; e < C->nnzj; e++) {
+        C->jrow[e] = keys[e] / N;
+        C->jcol[e] = keys[e] % N;
+    }
+
+    /* ---- Hessian pattern: lower triangle of every term's second-order
+     * structure (row >= col), deduplicated */
+    cap = 0;
+    for (int s = 0; s < ninst; s++) {
+        const ora_net *n = &C->in[s].net;
+        cap += (int64_t)n->nperiod * (10 * (int64_t)n->nbranch + n->nbus + n->ngen + 4 * (int64_t)n->nbranch);
+    }
+    keys = malloc(sizeof(int64_t) * (cap + 1));
+    cnt = 0;
+    for (int s = 0; s < ninst; s++) {
+        const inst_t *S = &C->in[s];
+        const ora_net *n = &S->net;
+        int64_t nl = n->nbranch;
+        for (int t = 0; t < n->nperiod; t++) {
+            for (int k = 0; k < nl; k++) {
+                int64_t u[4] = {v_vm(S, n->f[k], t), v_vm(S, n->t[k], t), v_va(S, n->f[k], t),
+                                v_va(S, n->t[k], t)};
+                for (int a = 0; a < 4; a++)
+                    for (int b = a; b < 4; b++) {
+                        int64_t r = u[a] > u[b] ? u[a] : u[b], c = u[a] > u[b] ? u[b] : u[a];
+                        push(keys, &cnt, N, r, c);
+                    }
+            }
+            for (int i = 0; i < n->nbus; i++) /* demand term: quadratic in vm_i */
+                push(keys, &cnt, N, v_vm(S, i, t), v_vm(S, i, t));
+            for (int g = 0; g < n->ngen; g++) /* cost term */
+                push(keys, &cnt, N, v_pg(S, g, t), v_pg(S, g, t));
+            for (int64_t a = 0; a < 2 * nl; a++) { /* thermal terms */
+                push(keys, &cnt, N, v_p(S, a, t), v_p(S, a, t));
+                push(keys, &cnt, N, v_q(S, a, t), v_q(S, a, t));
+            }
+        }
+    }
+    C->nnzh = sort_unique(keys, cnt);
+    C->hkey = keys;
+    C->hrow = malloc(sizeof(int64_t) * (C->nnzh + 1));
+    C->hcol = malloc(sizeof(int64_t) * (C->nnzh + 1));
+    for (int64_t e = 0; e < C->nnzh; e++) {
+        C->hrow[e] = keys[e] / N;
+        C->hcol[e] = keys[e] % N;
+    }
+    return C;
+}
+
+void ora_dims(const ora_ctx *C, int64_t *n, int64_t *m, int64_t *nnzj, int64_t *nnzh)
+{
+    *n = C->n;
+    *m = C->m;
+    *nnzj = C->nnzj;
+    *nnzh = C->nnzh;
+}
+
+void ora_jac_pattern(const ora_ctx *C, int64_t *rows, int64_t *cols)
+{
+    memcpy(rows, C->jrow, sizeof(int64_t) * C->nnzj);
+    memcpy(cols, C->jcol, sizeof(int64_t) * C->nnzj);
+}
+
+void ora_hess_pattern(const ora_ctx *C, int64_t *rows, int64_t *cols)
+{
+    memcpy(rows, C->hrow, sizeof(int64_t) * C->nnzh);
+    memcpy(cols, C->hcol, sizeof(int64_t) * C->nnzh);
+}
+
+void ora_bounds(const ora_ctx *C, double *xl, double *xu, double *gl, double *gu)
+{
+    for (int s = 0; s < C->ninst; s++) {
+        const inst_t *S = &C->in[s];
+        const ora_net *n = &S->net;
+        int64_t nl = n->nbranch;
+        for (int t = 0; t < n->nperiod; t++) {
+            for (int i = 0; i < n->nbus; i++) {
+                xl[v_va(S, i, t)] = -INFINITY;
+                xu[v_va(S, i, t)] = INFINITY;
+                xl[v_vm(S, i, t)] = n->vmin[i];
+                xu[v_vm(S, i, t)] = n->vmax[i];
+            }
+            for (int g = 0; g < n->ngen; g++) {
+                xl[v_pg(S, g, t)] = n->pmin[g];
+                xu[v_pg(S, g, t)] = n->pmax[g];
+                xl[v_qg(S, g, t)] = n->qmin[g];
+                xu[v_qg(S, g, t)] = n->qmax[g];
+            }
+            for (int64_t a = 0; a < 2 * nl; a++) {
+                double rate = n->rate_a[a % nl];
+                xl[v_p(S, a, t)] = -rate;
+                xu[v_p(S, a, t)] = rate;
+                xl[v_q(S, a, t)] = -rate;
+                xu[v_q(S, a, t)] = rate;
+            }
+            gl[row_of(S, G_REF, 0, t)] = gu[row_of(S, G_REF, 0, t)] = 0.0;
+            for (int k = 0; k < nl; k++) {
+                int grp[4] = {G_FPF, G_FQF, G_FPT, G_FQT};
+                for (int r = 0; r < 4; r++)
+                    gl[row_of(S, grp[r], k, t)] = gu[row_of(S, grp[r], k, t)] = 0.0;
+                gl[row_of(S, G_ANG, k, t)] = n->angmin[k];
+                gu[row_of(S, G_ANG, k, t)] = n->angmax[k];
+                gl[row_of(S, G_THF, k, t)] = -INFINITY;
+                gu[row_of(S, G_THF, k, t)] = 0.0;
+                gl[row_of(S, G_THT, k, t)] = -INFINITY;
+                gu[row_of(S, G_THT, k, t)] = 0.0;
+            }
+            for (int i = 0; i < n->nbus; i++) {
+                gl[row_of(S, G_PB, i, t)] = gu[row_of(S, G_PB, i, t)] = 0.0;
+                gl[row_of(S, G_QB, i, t)] = gu[row_of(S, G_QB, i, t)] = 0.0;
+            }
+            if (S->ramp && t >= 1)
+                for (int g = 0; g < n->ngen; g++) {
+                    double d = n->ramp_ratio * n->pmax[g];
+                    gl[row_of(S, G_RAMP, g, t)] = -d;
+                    gu[row_of(S, G_RAMP, g, t)] = d;
+                }
+        }
+    }
+    if (C->link) {
+        const ora_net *n0 = &C->in[0].net;
+        for (int s = 1; s < C->ninst; s++)
+            for (int g = 0; g < n0->ngen; g++) {
+                int64_t row = C->link_row + g + (int64_t)n0->ngen * (s - 1);
+                gl[row] = -C->link_ratio * n0->pmax[g];
+                gu[row] = C->link_ratio * n0->pmax[g];
+            }
+    }
+}
+
+/* ------------------------------------------------------------- objective -- */
+
+double ora_obj(const ora_ctx *C, const double *x)
+{
+    double f = 0.0;
+    for (int s = 0; s < C->ninst; s++) {
+        const inst_t *S = &C->in[s];
+        const ora_net *n = &S->net;
+        for (int t = 0; t < n->nperiod; t++)
+            for (int g = 0; g < n->ngen; g++) {
+                double pg = x[v_pg(S, g, t)];
+                f += n->c2[g] * pg * pg + n->c1[g] * pg + n->c0[g];
+            }
+    }
+    return f;
+}
+
+void ora_grad(const ora_ctx *C, const double *x, double *grad)
+{
+    memset(grad, 0, sizeof(double) * C->n);
+    for (int s = 0; s < C->ninst; s++) {
+        const inst_t *S = &C->in[s];
+        const ora_net *n = &S->net;
+        for (int t = 0; t < n->nperiod; t++)
+            for (int g = 0; g < n->ngen; g++)
+                grad[v_pg(S, g, t)] = 2.0 * n->c2[g] * x[v_pg(S, g, t)] + n->c1[g];
+    }
+}
+
+/* ----------------------------------------------------------- constraints -- */
+
+void ora_cons(const ora_ctx *C, const double *x, double *c, double *scale)
+{
+    memset(c, 0, sizeof(double) * C->m);
+    if (scale)
+        memset(scale, 0, sizeof(double) * C->m);
+#define ADD(row, v, bnd)                \
+    do {                                \
+        c[row] += (v);                  \
+        if (scale)                      \
+            scale[row] += (bnd);        \
+    } while (0)
+    for (int s = 0; s < C->ninst; s++) {
+        const inst_t *S = &C->in[s];
+        const ora_net *n = &S->net;
+        int64_t nl = n->nbranch, nb = n->nbus;
+        for (int t = 0; t < n->nperiod; t++) {
+            double va_ref = x[v_va(S, n->ref_bus, t)];
+            ADD(row_of(S, G_REF, 0, t), va_ref, fabs(va_ref));
+            for (int k = 0; k < nl; k++) {
+                end_t fr, to;
+                ends_of(S, x, k, t, &fr, &to);
+                double pf = x[fr.pvar], qf = x[fr.qvar], pt = x[to.pvar], qt = x[to.qvar];
+                ADD(row_of(S, G_FPF, k, t), pf - creal(fr.e.S), fabs(pf) + fr.e.bS);
+                ADD(row_of(S, G_FQF, k, t), qf - cimag(fr.e.S), fabs(qf) + fr.e.bS);
+                ADD(row_of(S, G_FPT, k, t), pt - creal(to.e.S), fabs(pt) + to.e.bS);
+                ADD(row_of(S, G_FQT, k, t), qt - cimag(to.e.S), fabs(qt) + to.e.bS);
+                double vaf = x[v_va(S, n->f[k], t)], vat = x[v_va(S, n->t[k], t)];
+                ADD(row_of(S, G_ANG, k, t), vaf - vat, fabs(vaf) + fabs(vat));
+                double r2 = n->rate_a[k] * n->rate_a[k];
+                ADD(row_of(S, G_THF, k, t), pf * pf + qf * qf - r2, pf * pf + qf * qf + r2);
+                ADD(row_of(S, G_THT, k, t), pt * pt + qt * qt - r2, pt * pt + qt * qt + r2);
+            }
+            for (int i = 0; i < nb; i++) {
+                double vm = x[v_vm(S, i, t)];
+                double Pd = S->Pd[t * nb + i], Qd = S->Qd[t * nb + i];
+                ADD(row_of(S, G_PB, i, t), Pd + n->gs[i] * vm * vm, fabs(Pd) + fabs(n->gs[i]) * vm * vm);
+                ADD(row_of(S, G_QB, i, t), Qd - n->bs[i] * vm * vm, fabs(Qd) + fabs(n->bs[i]) * vm * vm);
+            }
+            for (int64_t a = 0; a < 2 * nl; a++) { /* constraint! augmentation: +p[a] at a.bus */
+                int i = arc_bus(S, a);
+                double p = x[v_p(S, a, t)], q = x[v_q(S, a, t)];
+                ADD(row_of(S, G_PB, i, t), p, fabs(p));
+                ADD(row_of(S, G_QB, i, t), q, fabs(q));
+            }
+            for (int g = 0; g < n->ngen; g++) { /* -pg[g] at g.bus */
+                int i = n->gen_bus[g];
+                double pg = x[v_pg(S, g, t)], qg = x[v_qg(S, g, t)];
+                ADD(row_of(S, G_PB, i, t), -pg, fabs(pg));
+                ADD(row_of(S, G_QB, i, t), -qg, fabs(qg));
+            }
+            if (S->ramp && t >= 1)
+                for (int g = 0; g < n->ngen; g++) {
+                    double a = x[v_pg(S, g, t)], b = x[v_pg(S, g, t - 1)];
+                    ADD(row_of(S, G_RAMP, g, t), a - b, fabs(a) + fabs(b));
+                }
+        }
+    }
+    if (C->link) {
+        int ng = C->in[0].net.ngen;
+        for (int s = 1; s < C->ninst; s++)
+            for (int g = 0; g < ng; g++) {
+                double a = x[v_pg(&C->in[s], g, 0)], b = x[v_pg(&C->in[0], g, 0)];
+                ADD(C->link_row + g + (int64_t)ng * (s - 1), a - b, fabs(a) + fabs(b));
+            }
+    }
+#undef ADD
+}
+
+/* ---------------------------------------------------------------- Jacobian -- */
+
+typedef struct {
+    const int64_t *keys;
+    int64_t nnz, n;
+    double *vals, *scale;
+    int bad;
+} acc_t;
+
+static void acc(acc_t *A, int64_t r, int64_t c, double v, double bound)
+{
+    int64_t e = find(A->keys, A->nnz, r * A->n + c);
+    if (e < 0) {
+        if (!A->bad)
+            set_err("entry (%lld, %lld) not in the pattern", (long long)r, (long long)c);
+        A->bad = 1;
+        return;
+    }
+    A->vals[e] += v;
+    if (A->scale)
+        A->scale[e] += bound;
+}
+
+/* Hessian accumulation into the lower triangle */
+static void acc_sym(acc_t *A, int64_t r, int64_t c, double v, double bound)
+{
+    if (r >= c)
+        acc(A, r, c, v, bound);
+    else
+        acc(A, c, r, v, bound);
+}
+
+int ora_jac(const ora_ctx *C, const double *x, double *vals, double *scale)
+{
+    acc_t A = {C->jkey, C->nnzj, C->n, vals, scale, 0};
+    memset(vals, 0, sizeof(double) * C->nnzj);
+    if (scale)
+        memset(scale, 0, sizeof(double) * C->nnzj);
+    for (int s = 0; s < C->ninst; s++) {
+        const inst_t *S = &C->in[s];
+        const ora_net *n = &S->net;
+        int64_t nl = n->nbranch;
+        for (int t = 0; t < n->nperiod; t++) {
+            acc(&A, row_of(S, G_REF, 0, t), v_va(S, n->ref_bus, t), 1.0, 1.0);
+            for (int k = 0; k < nl; k++) {
+                end_t fr, to;
+                ends_of(S, x, k, t, &fr, &to);
+                /* flow row = own variable - Re/Im S(u) */
+                const end_t *ends[2] = {&fr, &to};
+                int gP[2] = {G_FPF, G_FPT}, gQ[2] = {G_FQF, G_FQT};
+                for (int side = 0; side < 2; side++) {
+                    const end_t *E = ends[side];
+                    int64_t rP = row_of(S, gP[side], k, t), rQ = row_of(S, gQ[side], k, t);
+                    acc(&A, rP, E->pvar, 1.0, 1.0);
+                    acc(&A, rQ, E->qvar, 1.0, 1.0);
+                    for (int d = 0; d < 4; d++) {
+                        acc(&A, rP, E->u[d], -creal(E->e.dS[d]), E->e.bdS[d]);
+                        acc(&A, rQ, E->u[d], -cimag(E->e.dS[d]), E->e.bdS[d]);
+                    }
+                }
+                acc(&A, row_of(S, G_ANG, k, t), v_va(S, n->f[k], t), 1.0, 1.0);
+                acc(&A, row_of(S, G_ANG, k, t), v_va(S, n->t[k], t), -1.0, 1.0);
+                double pf = x[fr.pvar], qf = x[fr.qvar], pt = x[to.pvar], qt = x[to.qvar];
+                acc(&A, row_of(S, G_THF, k, t), fr.pvar, 2.0 * pf, 2.0 * fabs(pf));
+                acc(&A, row_of(S, G_THF, k, t), fr.qvar, 2.0 * qf, 2.0 * fabs(qf));
+                acc(&A, row_of(S, G_THT, k, t), to.pvar, 2.0 * pt, 2.0 * fabs(pt));
+                acc(&A, row_of(S, G_THT, k, t), to.qvar, 2.0 * qt, 2.0 * fabs(qt));
+            }
+            for (int i = 0; i < n->nbus; i++) {
+                double vm = x[v_vm(S, i, t)];
+                acc(&A, row_of(S, G_PB, i, t), v_vm(S, i, t), 2.0 * n->gs[i] * vm, 2.0 * fabs(n->gs[i]) * vm);
+                acc(&A, row_of(S, G_QB, i, t), v_vm(S, i, t), -2.0 * n->bs[i] * vm, 2.0 * fabs(n->bs[i]) * vm);
+            }
+            for (int64_t a = 0; a < 2 * nl; a++) {
+                int i = arc_bus(S, a);
+                acc(&A, row_of(S, G_PB, i, t), v_p(S, a, t), 1.0, 1.0);
+                acc(&A, row_of(S, G_QB, i, t), v_q(S, a, t), 1.0, 1.0);
+            }
+            for (int g = 0; g < n->ngen; g++) {
+                int i = n->gen_bus[g];
+                acc(&A, row_of(S, G_PB, i, t), v_pg(S, g, t), -1.0, 1.0);
+                acc(&A, row_of(S, G_QB, i, t), v_qg(S, g, t), -1.0, 1.0);
+            }
+            if (S->ramp && t >= 1)
+                for (int g = 0; g < n->ngen; g++) {
+                    acc(&A, row_of(S, G_RAMP, g, t), v_pg(S, g, t), 1.0, 1.0);
+                    acc(&A, row_of(S, G_RAMP, g, t), v_pg(S, g, t - 1), -1.0, 1.0);
+                }
+        }
+    }
+    if (C->link) {
+        int ng = C->in[0].net.ngen;
+        for (int s = 1; s < C->ninst; s++)
+            for (int g = 0; g < ng; g++) {
+                int64_t row = C->link_row + g + (int64_t)ng * (s - 1);
+                acc(&A, row, v_pg(&C->in[s], g, 0), 1.0, 1.0);
+                acc(&A, row, v_pg(&C->in[0], g, 0), -1.0, 1.0);
+            }
+    }
+    return A.bad ? -1 : 0;
+}
+
+/* ----------------------------------------------------------------- Hessian -- */
+
+int ora_hess(const ora_ctx *C, const double *x, const double *lambda, double sigma, double *vals,
+             double *scale)
+{
+    acc_t A = {C->hkey, C->nnzh, C->n, vals, scale, 0};
+    memset(vals, 0, sizeof(double) * C->nnzh);
+    if (scale)
+        memset(scale, 0, sizeof(double) * C->nnzh);
+    for (int s = 0; s < C->ninst; s++) {
+        const inst_t *S = &C->in[s];
+        const ora_net *n = &S->net;
+        int64_t nl = n->nbranch;
+        for (int t = 0; t < n->nperiod; t++) {
+            /* sigma * cost: d2/dpg2 (c2 pg^2 + c1 pg + c0) = 2 c2 */
+            for (int g = 0; g < n->ngen; g++)
+                acc_sym(&A, v_pg(S, g, t), v_pg(S, g, t), sigma * 2.0 * n->c2[g],
+                        fabs(sigma * 2.0 * n->c2[g]));
+            /* flow rows: lambda_r * (own - Re/Im S) contributes -lambda_r Re/Im d2S */
+            for (int k = 0; k < nl; k++) {
+                end_t fr, to;
+                ends_of(S, x, k, t, &fr, &to);
+                const end_t *ends[2] = {&fr, &to};
+                int gP[2] = {G_FPF, G_FPT}, gQ[2] = {G_FQF, G_FQT};
+                for (int side = 0; side < 2; side++) {
+                    const end_t *E = ends[side];
+                    double lP = lambda[row_of(S, gP[side], k, t)];
+                    double lQ = lambda[row_of(S, gQ[side], k, t)];
+                    for (int a = 0; a < 4; a++)
+                        for (int b = a; b < 4; b++) {
+                            double v = -lP * creal(E->e.d2S[a][b]) - lQ * cimag(E->e.d2S[a][b]);
+                            double bnd = (fabs(lP) + fabs(lQ)) * E->e.bd2S[a][b];
+                            acc_sym(&A, E->u[a], E->u[b], v, bnd);
+                        }
+                }
+                /* thermal rows: lambda * 2 on (p, p) and (q, q) of each arc */
+                double lf = lambda[row_of(S, G_THF, k, t)], lt = lambda[row_of(S, G_THT, k, t)];
+                acc_sym(&A, fr.pvar, fr.pvar, 2.0 * lf, 2.0 * fabs(lf));
+                acc_sym(&A, fr.qvar, fr.qvar, 2.0 * lf, 2.0 * fabs(lf));
+                acc_sym(&A, to.pvar, to.pvar, 2.0 * lt, 2.0 * fabs(lt));
+                acc_sym(&A, to.qvar, to.qvar, 2.0 * lt, 2.0 * fabs(lt));
+            }
+            /* balance demand terms: gs vm^2 (P) and -bs vm^2 (Q) */
+            for (int i = 0; i < n->nbus; i++) {
+                double lP = lambda[row_of(S, G_PB, i, t)], lQ = lambda[row_of(S, G_QB, i, t)];
+                acc_sym(&A, v_vm(S, i, t), v_vm(S, i, t), 2.0 * n->gs[i] * lP - 2.0 * n->bs[i] * lQ,
+                        2.0 * fabs(n->gs[i] * lP) + 2.0 * fabs(n->bs[i] * lQ));
+            }
+        }
+    }
+    return A.bad ? -1 : 0;
+}
+
+/* ------------------------------------------------------------------ Cvio -- */
+
+void ora_cvio(const ora_ctx *C, const double *x, double *cons_viol, double *var_viol)
+{
+    double *c = malloc(sizeof(double) * (C->m + 1));
+    double *xl = malloc(sizeof(double) * (C->n + 1)), *xu = malloc(sizeof(double) * (C->n + 1));
+    double *gl = malloc(sizeof(double) * (C->m + 1)), *gu = malloc(sizeof(double) * (C->m + 1));
+    ora_cons(C, x, c, NULL);
+    ora_bounds(C, xl, xu, gl, gu);
+    double cv = 0.0, vv = 0.0;
+    for (int64_t i = 0; i < C->m; i++) {
+        if (gl[i] - c[i] > cv)
+            cv = gl[i] - c[i];
+        if (c[i] - gu[i] > cv)
+            cv = c[i] - gu[i];
+    }
+    for (int64_t j = 0; j < C->n; j++) {
+        if (xl[j] - x[j] > vv)
+            vv = xl[j] - x[j];
+        if (x[j] - xu[j] > vv)
+            vv = x[j] - xu[j];
+    }
+    *cons_viol = cv;
+    *var_viol = vv;
+    free(c); free(xl); free(xu); free(gl); free(gu);
+}

@@ -1,0 +1,72 @@
+/*
+ * FP64 CPU oracle for the polar AC-OPF callbacks with branch-flow variables.
+ *
+ * TEST INFRASTRUCTURE ONLY. This header belongs to the oracle, which exists to
+ * judge the CUDA path: only the tests, the smoke check and the benchmark's CPU
+ * baseline may load it. It shares no code, header, constant or helper with the
+ * library under paper_2510_12897_b300/, and the library never calls it.
+ *
+ * The problem is the one of the paper's Listing 3 (Sec. III-B), in the NLP
+ * form of Sec. II-A, with the multi-period extension of Sec. III-C-2 (demand
+ * per period, ramp limits between consecutive periods) and a batch of
+ * independent instances (the batch-solve direction of Sec. V), optionally tied
+ * to instance 0 by linking rows on generator output.
+ *
+ * Variable order per instance:  va, vm, pg, qg, p, q, each group indexed
+ * elem + count * period (the 2-D index rule of Listing 10).
+ * Constraint groups per instance, in Listing 3 order:
+ *   ref, flow P (from arc), flow Q (from arc), flow P (to arc), flow Q (to arc),
+ *   angle difference, P balance, Q balance, thermal (from), thermal (to),
+ *   then ramp rows g + ngen * (t - 1), t = 1..T-1.
+ * Instances are concatenated; linking rows come last.
+ */
+#ifndef OPF_ORACLE_H
+#define OPF_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    int32_t nbus, nbranch, ngen, nload, nperiod, ref_bus;
+    const double *vmin, *vmax, *gs, *bs;                 /* [nbus] */
+    const int32_t *f, *t;                                /* [nbranch] */
+    const double *r, *x, *b, *tap, *shift, *rate_a, *angmin, *angmax;
+    const int32_t *gen_bus;                              /* [ngen] */
+    const double *pmin, *pmax, *qmin, *qmax, *c2, *c1, *c0;
+    const int32_t *load_bus;                             /* [nload] */
+    const double *pd, *qd;                               /* [nperiod][nload] */
+    double ramp_ratio;                                   /* ramp rows if > 0 and nperiod > 1 */
+} ora_net;
+
+typedef struct ora_ctx ora_ctx;
+
+/* Builds layout and sparsity patterns. Copies every array. NULL on bad input. */
+ora_ctx *ora_create(const ora_net *nets, int32_t ninst, double link_ratio);
+void ora_destroy(ora_ctx *);
+const char *ora_error(void);
+
+void ora_dims(const ora_ctx *, int64_t *n, int64_t *m, int64_t *nnzj, int64_t *nnzh);
+void ora_jac_pattern(const ora_ctx *, int64_t *rows, int64_t *cols);
+void ora_hess_pattern(const ora_ctx *, int64_t *rows, int64_t *cols);
+void ora_bounds(const ora_ctx *, double *xl, double *xu, double *gl, double *gu);
+
+/* Each evaluator optionally fills a magnitude scale per output entry: the sum,
+ * over all contributions to the entry, of a bound on each contribution's
+ * absolute value. Tolerances are stated relative to it. Pass NULL to skip. */
+double ora_obj(const ora_ctx *, const double *x);
+void ora_grad(const ora_ctx *, const double *x, double *g);
+void ora_cons(const ora_ctx *, const double *x, double *c, double *scale);
+int ora_jac(const ora_ctx *, const double *x, double *vals, double *scale);
+int ora_hess(const ora_ctx *, const double *x, const double *lambda, double sigma,
+             double *vals, double *scale);
+
+/* Maximum constraint violation of Sec. IV-A (componentwise positive parts)
+ * and the maximum variable-bound violation, at x. */
+void ora_cvio(const ora_ctx *, const double *x, double *cons_viol, double *var_viol);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

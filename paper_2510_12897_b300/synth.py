@@ -1,0 +1,369 @@
+"""Seeded synthetic power grids and evaluation points.
+
+This module is the one place where inputs are drawn. It serves both the CUDA
+path and the FP64 oracle and holds none of the method's arithmetic: it draws
+network parameters, loads and points from fixed distributions and nothing
+else (no power-flow formula, no derivative, no layout of the NLP).
+
+The networks stand in for the pglib-opf cases the paper benchmarks (Sec. IV-A,
+IV-B, IV-C), which are not available here. Recipe:
+
+* buses at uniform positions in the unit square; a random spanning tree in
+  which each bus, in random order, attaches to its nearest already placed bus;
+  then ``nbranch - (nbus - 1)`` extra edges, each from a random bus to a random
+  one of its 8 nearest non-adjacent buses, never parallel to an existing edge;
+* r ~ U(0.01, 0.1), x ~ U(0.05, 0.3), b ~ U(0, 0.05) p.u., tap 1, shift 0,
+  rate_a ~ U(0.5, 2), angle-difference limits +-30 degrees;
+* generators at distinct random buses, c2 ~ U(0.01, 0.1), c1 ~ U(10, 40),
+  c0 = 0, Pg in [0, 2], Qg in [-1, 1]; the reference bus is generator 0's bus;
+* loads at round(0.7 nbus) distinct random buses, Pd ~ U(0, 0.5), Qd = 0.3 Pd;
+* V in [0.9, 1.1], no shunts.
+
+``general=True`` additionally draws shunts, off-nominal taps and phase shifts
+and a few parallel branches, so that parity tests reach every term of the
+formulation (the paper's cases contain all of them).
+
+Multi-period loads follow the paper's demand-curve interface (Sec. III-C-2,
+``mpopf_model`` with a curve): every load is scaled per period by one daily
+curve, here a seeded sinusoid, times lognormal(0, 0.05) noise per load.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field, replace
+
+import numpy as np
+from scipy.spatial import cKDTree
+
+DEG = math.pi / 180.0
+
+
+@dataclass
+class Grid:
+    """A network as structure-of-arrays (0-based indices, per-unit values)."""
+
+    nbus: int
+    bus_vmin: np.ndarray
+    bus_vmax: np.ndarray
+    bus_gs: np.ndarray
+    bus_bs: np.ndarray
+    br_f: np.ndarray
+    br_t: np.ndarray
+    br_r: np.ndarray
+    br_x: np.ndarray
+    br_b: np.ndarray
+    br_tap: np.ndarray
+    br_shift: np.ndarray
+    br_rate_a: np.ndarray
+    br_angmin: np.ndarray
+    br_angmax: np.ndarray
+    gen_bus: np.ndarray
+    gen_pmin: np.ndarray
+    gen_pmax: np.ndarray
+    gen_qmin: np.ndarray
+    gen_qmax: np.ndarray
+    gen_c2: np.ndarray
+    gen_c1: np.ndarray
+    gen_c0: np.ndarray
+    load_bus: np.ndarray
+    load_pd: np.ndarray  # [nperiod, nload]
+    load_qd: np.ndarray  # [nperiod, nload]
+    ref_bus: int
+    ramp_ratio: float = 0.0
+    xy: np.ndarray | None = field(default=None, repr=False)
+
+    @property
+    def nbranch(self) -> int:
+        return int(self.br_f.shape[0])
+
+    @property
+    def ngen(self) -> int:
+        return int(self.gen_bus.shape[0])
+
+    @property
+    def nload(self) -> int:
+        return int(self.load_bus.shape[0])
+
+    @property
+    def nperiod(self) -> int:
+        return int(self.load_pd.shape[0])
+
+    def copy(self, **changes) -> "Grid":
+        return replace(self, **changes)
+
+
+def _spanning_tree(xy: np.ndarray, rng: np.random.Generator) -> list[tuple[int, int]]:
+    nb = xy.shape[0]
+    order = rng.permutation(nb)
+    edges = []
+    # distance from every bus to the nearest placed bus, and which one it is
+    best_d = np.full(nb, np.inf)
+    best_j = np.full(nb, -1, dtype=np.int64)
+    placed = np.zeros(nb, dtype=bool)
+    for step, i in enumerate(order):
+        if step > 0:
+            edges.append((int(i), int(best_j[i])))
+        placed[i] = True
+        d = np.sum((xy - xy[i]) ** 2, axis=1)
+        upd = (d < best_d) & ~placed
+        best_d[upd] = d[upd]
+        best_j[upd] = i
+    return edges
+
+
+def _extra_edges(xy, edges, n_extra, rng, allow_parallel=0):
+    nb = xy.shape[0]
+    adj = [set() for _ in range(nb)]
+    for f, t in edges:
+        adj[f].add(t)
+        adj[t].add(f)
+    tree = cKDTree(xy)
+    out = []
+    guard = 0
+    while len(out) < n_extra:
+        guard += 1
+        if guard > 100 * (n_extra + 10):
+            raise RuntimeError("could not place extra edges")
+        i = int(rng.integers(nb))
+        k = min(nb, 9 + len(adj[i]))
+        _, idx = tree.query(xy[i], k=k)
+        cand = [int(j) for j in np.atleast_1d(idx) if j != i and j not in adj[i]][:8]
+        if not cand:
+            continue
+        j = cand[int(rng.integers(len(cand)))]
+        adj[i].add(j)
+        adj[j].add(i)
+        out.append((i, j))
+    # a few parallel branches (general grids only): duplicate existing edges
+    all_edges = edges + out
+    for _ in range(allow_parallel):
+        e = all_edges[int(rng.integers(len(all_edges)))]
+        out.append(e)
+    return out
+
+
+def make_grid(nbus: int, nbranch: int, ngen: int, seed: int, nload: int | None = None,
+              general: bool = False) -> Grid:
+    """One seeded synthetic network (single period)."""
+    if nbranch < nbus - 1:
+        raise ValueError("need at least a spanning tree")
+    rng = np.random.default_rng(seed)
+    xy = rng.random((nbus, 2))
+    tree = _spanning_tree(xy, rng)
+    npar = 0
+    if general:
+        npar = max(1, (nbranch - (nbus - 1)) // 8)
+    n_extra = nbranch - (nbus - 1) - npar
+    if n_extra < 0:
+        npar, n_extra = nbranch - (nbus - 1), 0
+    extra = _extra_edges(xy, tree, n_extra, rng, allow_parallel=npar)
+    edges = tree + extra
+    perm = rng.permutation(len(edges))
+    edges = [edges[p] for p in perm]
+    # random orientation of each branch
+    fl, tl = [], []
+    for (a, b) in edges:
+        if rng.random() < 0.5:
+            a, b = b, a
+        fl.append(a)
+        tl.append(b)
+    nl = len(edges)
+    br_f = np.asarray(fl, dtype=np.int32)
+    br_t = np.asarray(tl, dtype=np.int32)
+    br_r = rng.uniform(0.01, 0.1, nl)
+    br_x = rng.uniform(0.05, 0.3, nl)
+    br_b = rng.uniform(0.0, 0.05, nl)
+    br_tap = np.ones(nl)
+    br_shift = np.zeros(nl)
+    if general:
+        sel = rng.random(nl) < 0.3
+        br_tap[sel] = rng.uniform(0.9, 1.1, int(sel.sum()))
+        sel = rng.random(nl) < 0.2
+        br_shift[sel] = rng.uniform(-10 * DEG, 10 * DEG, int(sel.sum()))
+    br_rate_a = rng.uniform(0.5, 2.0, nl)
+    br_angmin = np.full(nl, -30 * DEG)
+    br_angmax = np.full(nl, 30 * DEG)
+
+    gen_bus = rng.choice(nbus, size=ngen, replace=False).astype(np.int32)
+    gen_c2 = rng.uniform(0.01, 0.1, ngen)
+    gen_c1 = rng.uniform(10.0, 40.0, ngen)
+    gen_c0 = np.zeros(ngen)
+    if general:
+        gen_c0 = rng.uniform(0.0, 5.0, ngen)
+    gen_pmin = np.zeros(ngen)
+    gen_pmax = np.full(ngen, 2.0)
+    gen_qmin = np.full(ngen, -1.0)
+    gen_qmax = np.full(ngen, 1.0)
+
+    if nload is None:
+        nload = int(round(0.7 * nbus))
+    load_bus = rng.choice(nbus, size=nload, replace=False).astype(np.int32)
+    pd = rng.uniform(0.0, 0.5, nload)
+    qd = 0.3 * pd
+
+    bus_gs = np.zeros(nbus)
+    bus_bs = np.zeros(nbus)
+    if general:
+        sel = rng.random(nbus) < 0.3
+        bus_gs[sel] = rng.uniform(0.0, 0.05, int(sel.sum()))
+        sel = rng.random(nbus) < 0.3
+        bus_bs[sel] = rng.uniform(-0.05, 0.05, int(sel.sum()))
+
+    return Grid(
+        nbus=nbus,
+        bus_vmin=np.full(nbus, 0.9), bus_vmax=np.full(nbus, 1.1),
+        bus_gs=bus_gs, bus_bs=bus_bs,
+        br_f=br_f, br_t=br_t, br_r=br_r, br_x=br_x, br_b=br_b,
+        br_tap=br_tap, br_shift=br_shift, br_rate_a=br_rate_a,
+        br_angmin=br_angmin, br_angmax=br_angmax,
+        gen_bus=gen_bus, gen_pmin=gen_pmin, gen_pmax=gen_pmax,
+        gen_qmin=gen_qmin, gen_qmax=gen_qmax,
+        gen_c2=gen_c2, gen_c1=gen_c1, gen_c0=gen_c0,
+        load_bus=load_bus, load_pd=pd[None, :].copy(), load_qd=qd[None, :].copy(),
+        ref_bus=int(gen_bus[0]), xy=xy,
+    )
+
+
+def daily_curve(nperiod: int, seed: int, amplitude: float = 0.2) -> np.ndarray:
+    """One seeded daily demand curve: 1 + a sin(2 pi t / T + phi)."""
+    rng = np.random.default_rng(seed)
+    phi = rng.uniform(0.0, 2.0 * math.pi)
+    t = np.arange(nperiod)
+    return 1.0 + amplitude * np.sin(2.0 * math.pi * t / nperiod + phi)
+
+
+def multi_period(g: Grid, nperiod: int, seed: int, ramp_ratio: float = 0.2,
+                 noise_sigma: float = 0.05) -> Grid:
+    """Multi-period copy of ``g``: loads scaled per period by a daily curve
+    times per-load lognormal(0, noise_sigma) noise; ramp ratio recorded."""
+    rng = np.random.default_rng(seed + 7919)
+    curve = daily_curve(nperiod, seed)
+    noise = np.exp(rng.normal(0.0, noise_sigma, (nperiod, g.nload)))
+    scale = curve[:, None] * noise
+    pd = g.load_pd[0][None, :] * scale
+    qd = g.load_qd[0][None, :] * scale
+    return g.copy(load_pd=pd, load_qd=qd, ramp_ratio=float(ramp_ratio))
+
+
+def bridges(nbus: int, f: np.ndarray, t: np.ndarray) -> np.ndarray:
+    """Boolean mask of bridge branches (iterative Tarjan low-link)."""
+    nl = len(f)
+    adj = [[] for _ in range(nbus)]
+    for k in range(nl):
+        adj[int(f[k])].append((int(t[k]), k))
+        adj[int(t[k])].append((int(f[k]), k))
+    disc = [-1] * nbus
+    low = [0] * nbus
+    is_bridge = np.zeros(nl, dtype=bool)
+    timer = 0
+    for root in range(nbus):
+        if disc[root] >= 0:
+            continue
+        disc[root] = low[root] = timer
+        timer += 1
+        stack = [(root, -1, iter(adj[root]))]
+        while stack:
+            v, pe, it = stack[-1]
+            advanced = False
+            for (w, k) in it:
+                if k == pe:
+                    continue
+                if disc[w] < 0:
+                    disc[w] = low[w] = timer
+                    timer += 1
+                    stack.append((w, k, iter(adj[w])))
+                    advanced = True
+                    break
+                low[v] = min(low[v], disc[w])
+            if not advanced:
+                stack.pop()
+                if stack:
+                    u = stack[-1][0]
+                    low[u] = min(low[u], low[v])
+                    if low[v] > disc[u]:
+                        is_bridge[pe] = True
+    return is_bridge
+
+
+def drop_branch(g: Grid, k: int) -> Grid:
+    """The N-1 contingency network without branch ``k``."""
+    keep = np.ones(g.nbranch, dtype=bool)
+    keep[k] = False
+    kw = {name: getattr(g, name)[keep] for name in (
+        "br_f", "br_t", "br_r", "br_x", "br_b", "br_tap", "br_shift",
+        "br_rate_a", "br_angmin", "br_angmax")}
+    return g.copy(**kw)
+
+
+def contingencies(g: Grid, count: int, seed: int) -> list[Grid]:
+    """Base case followed by ``count`` N-1 networks, each without one seeded
+    non-bridge branch (so every instance stays connected)."""
+    rng = np.random.default_rng(seed + 104729)
+    cand = np.flatnonzero(~bridges(g.nbus, g.br_f, g.br_t))
+    if len(cand) < count:
+        raise ValueError("not enough non-bridge branches")
+    drop = rng.choice(cand, size=count, replace=False)
+    return [g] + [drop_branch(g, int(k)) for k in drop]
+
+
+# ----------------------------------------------------------------------------
+# evaluation points
+# ----------------------------------------------------------------------------
+
+def n_vars(g: Grid) -> int:
+    T = g.nperiod
+    return T * (2 * g.nbus + 2 * g.ngen + 4 * g.nbranch)
+
+
+def random_point(g: Grid, rng: np.random.Generator) -> np.ndarray:
+    """x = [va, vm, pg, qg, p, q], each group ``elem + count * period``:
+    va ~ U(-pi/6, pi/6), vm ~ U(vmin, vmax), pg and qg uniform in their
+    bounds, p, q ~ U(-rate_a, rate_a) of the arc's branch."""
+    T, nb, ng, nl = g.nperiod, g.nbus, g.ngen, g.nbranch
+    na = 2 * nl
+    va = rng.uniform(-math.pi / 6, math.pi / 6, (T, nb))
+    vm = rng.uniform(g.bus_vmin, g.bus_vmax, (T, nb))
+    pg = rng.uniform(g.gen_pmin, g.gen_pmax, (T, ng))
+    qg = rng.uniform(g.gen_qmin, g.gen_qmax, (T, ng))
+    rate = np.concatenate([g.br_rate_a, g.br_rate_a])
+    p = rng.uniform(-rate, rate, (T, na))
+    q = rng.uniform(-rate, rate, (T, na))
+    return np.concatenate([a.ravel() for a in (va, vm, pg, qg, p, q)])
+
+
+def random_multipliers(m: int, rng: np.random.Generator) -> np.ndarray:
+    return rng.standard_normal(m)
+
+
+# ----------------------------------------------------------------------------
+# named workloads
+# ----------------------------------------------------------------------------
+
+def case30(seed: int = 30, general: bool = False) -> Grid:
+    """30 buses, 41 branches, 6 generators, 21 loads."""
+    return make_grid(30, 41, 6, seed, general=general)
+
+
+def case10k(seed: int = 10000) -> Grid:
+    """10,000 buses, 13,000 branches, 2,500 generators, 7,000 loads."""
+    return make_grid(10000, 13000, 2500, seed)
+
+
+def case2k(seed: int = 2000) -> Grid:
+    """2,000 buses, 2,600 branches, 500 generators, 1,400 loads."""
+    return make_grid(2000, 2600, 500, seed)
+
+
+def case1k(seed: int = 1000) -> Grid:
+    """1,000 buses, 1,300 branches, 250 generators, 700 loads."""
+    return make_grid(1000, 1300, 250, seed)
+
+
+def mp2k(nperiod: int = 96, seed: int = 2000) -> Grid:
+    """The 2,000-bus grid over ``nperiod`` periods, ramp 0.2 Pmax."""
+    return multi_period(case2k(seed), nperiod, seed, ramp_ratio=0.2)
+
+
+def sc1k(ncont: int = 500, seed: int = 1000) -> list[Grid]:
+    """The 1,000-bus grid plus ``ncont`` N-1 contingencies."""
+    return contingencies(case1k(seed), ncont, seed)
