@@ -1,0 +1,203 @@
+/*
+ * opf.h — C ABI of libopf: GPU evaluation of the AC optimal power flow NLP
+ * callbacks (polar voltages, branch-flow variables) at a fixed sparsity
+ * pattern, for one instance, many periods, or a batch of instances.
+ *
+ * The problem is the static polar model of the paper's Listing 3 (Sec. III-B),
+ * written in the NLP form of Sec. II-A, with the multi-period extension of
+ * Sec. III-C-2 (per-period demand, generator ramp limits between consecutive
+ * periods, corrective_action_ratio) and batches of independent instances
+ * (the batch-solve direction of Sec. V), optionally tied to instance 0 by
+ * linking rows on generator output. The callbacks are those of Listing 1
+ * (Sec. II-B): obj, grad!, cons!, jac!, hess!(x, lambda; obj_weight).
+ *
+ * Layout (per instance; instances are concatenated, linking rows last):
+ *   x = [va, vm, pg, qg, p, q]; within a group the index is
+ *       elem + count * period (the 2-D index rule of Listing 10).
+ *       Arc a < nbranch is the from-end of branch a, arc nbranch + k the
+ *       to-end of branch k.
+ *   g = [ref (1 per period), flow P from-arc, flow Q from-arc, flow P to-arc,
+ *        flow Q to-arc, angle difference, P balance, Q balance,
+ *        thermal from-arc, thermal to-arc, ramp (ngen x (nperiod-1))],
+ *       each group elem + count * period (ramp: g + ngen * (t - 1)).
+ *   Flow rows are p_arc - P(v) and q_arc - Q(v) (bounds [0, 0]); thermal rows
+ *   p^2 + q^2 - rate_a^2 (bounds [-inf, 0]); balance rows
+ *   Pd + gs vm^2 + sum(arc p) - sum(pg) and Qd - bs vm^2 + sum(arc q) - sum(qg).
+ *   Jacobian: values in row-major order of the deduplicated pattern, columns
+ *   ascending within a row. Hessian of the Lagrangian
+ *   obj_weight * grad^2 f + sum_i lambda_i grad^2 g_i: lower triangle
+ *   (row >= col), deduplicated, row-major, columns ascending.
+ *   opf_sparsity returns both patterns.
+ *
+ * Ownership: every opf_network array is a HOST pointer read during the
+ * create call only and owned by the caller. The model owns its device copies
+ * of the network, layout tables and scratch. Every d_* argument of an eval
+ * call is a caller-owned DEVICE buffer of the stated length (doubles); the
+ * call is asynchronous on the given stream (NULL = legacy default stream),
+ * performs no host<->device transfer and no allocation, and may be captured
+ * in a CUDA graph. Evaluations on one model share its scratch: calls on the
+ * same model must be ordered on one stream (or otherwise serialised).
+ *
+ * Errors: every call returns OPF_OK (0) or a positive code and never aborts,
+ * exits or traps; opf_last_error() gives a thread-local message. Invalid
+ * networks are rejected on the host at create time, before any launch.
+ */
+#ifndef OPF_H
+#define OPF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    OPF_OK = 0,
+    OPF_EINVAL = 1,   /* bad size, index out of range, self-loop, r = x = 0, tap < 0,
+                         nperiod < 1, NULL where a value is required, bad kind */
+    OPF_ENOMEM = 2,   /* device or host allocation failed */
+    OPF_ECUDA = 3,    /* a CUDA runtime call or launch failed */
+    OPF_ESTATE = 4    /* the model cannot serve this request (e.g. linking rows
+                         with unequal generator counts) */
+};
+
+enum { OPF_JAC = 0, OPF_HESS = 1 };
+
+/* One network (Listing 3 data; per-unit values, radians, 0-based indices). */
+typedef struct {
+    int32_t nbus, nbranch, ngen, nload, nperiod; /* nperiod >= 1 */
+    int32_t ref_bus;                             /* 0-based reference bus */
+    const double *bus_vmin, *bus_vmax;           /* [nbus] */
+    const double *bus_gs, *bus_bs;               /* [nbus]; NULL means 0 */
+    const int32_t *br_f, *br_t;                  /* [nbranch] endpoints, f != t */
+    const double *br_r, *br_x, *br_b;            /* series r, x; total charging b */
+    const double *br_tap;                        /* [nbranch]; NULL or 0 means 1 */
+    const double *br_shift;                      /* [nbranch]; NULL means 0 */
+    const double *br_rate_a, *br_angmin, *br_angmax;
+    const int32_t *gen_bus;                      /* [ngen] */
+    const double *gen_pmin, *gen_pmax, *gen_qmin, *gen_qmax;
+    const double *gen_c2, *gen_c1, *gen_c0;      /* cost c2 pg^2 + c1 pg + c0; c0 NULL = 0 */
+    const int32_t *load_bus;                     /* [nload] */
+    const double *load_pd, *load_qd;             /* [nperiod][nload], period-major */
+    double ramp_ratio;                           /* ramp rows |pg_t - pg_{t-1}| <= ratio pmax
+                                                    when > 0 and nperiod > 1 (Listing 6) */
+} opf_network;
+
+typedef struct {
+    double link_ratio; /* > 0: rows pg_s - pg_0 in [-ratio pmax, ratio pmax] for every
+                          instance s >= 1 (all instances need equal ngen, nperiod 1) */
+} opf_batch_opts;
+
+typedef struct opf_model opf_model;
+
+/* Launch shape of the two evaluation kernels (branch phase, bus phase). */
+typedef struct {
+    int32_t branch_block; /* threads per block, branch kernel (32..1024, multiple of 32) */
+    int32_t bus_block;    /* threads per block, bus/generator kernel */
+    int32_t branch_ctas_per_sm; /* persistent grid = ctas_per_sm * SMs; 0 = one thread per item */
+    int32_t bus_ctas_per_sm;
+} opf_launch;
+
+/* Create a model for one network (Listing 3; multi-period if nperiod > 1).
+ * Validates every index and parameter on the host, precomputes the branch
+ * admittances of the pi-model (Yff, Yft, Ytf, Ytt), builds both sparsity
+ * patterns and the per-bus layout tables, and copies them to the current
+ * CUDA device. *out receives the model, or NULL on error. */
+int opf_model_create(const opf_network *net, opf_model **out);
+
+/* Create one model over ninst independent instances of uneven size
+ * (scenarios, N-1 contingencies), evaluated by the same kernels in one
+ * launch per phase. opts may be NULL (no linking rows). */
+int opf_batch_create(const opf_network *nets, int32_t ninst, const opf_batch_opts *opts,
+                     opf_model **out);
+
+/* Host-only model over ninst networks (ninst = 1: a single network): the
+ * same validation and layout as opf_batch_create, no device memory and no
+ * CUDA call. Serves opf_dims, opf_sparsity and opf_bounds (for example a
+ * solver's symbolic analysis before a GPU is attached); every eval call on
+ * it returns OPF_ESTATE. */
+int opf_structure_create(const opf_network *nets, int32_t ninst, const opf_batch_opts *opts,
+                         opf_model **out);
+
+int opf_model_destroy(opf_model *model);
+
+/* n variables, m constraints, Jacobian and Hessian (lower) nonzeros. */
+int opf_dims(const opf_model *model, int64_t *n, int64_t *m, int64_t *nnz_jac,
+             int64_t *nnz_hess);
+
+/* Pattern of kind OPF_JAC or OPF_HESS into HOST arrays of nnz entries each. */
+int opf_sparsity(const opf_model *model, int32_t kind, int64_t *rows, int64_t *cols);
+
+/* Variable and constraint bounds into HOST arrays (n and m entries);
+ * infinite bounds are +-INFINITY. */
+int opf_bounds(const opf_model *model, double *xl, double *xu, double *gl, double *gu);
+
+/* Objective (one double, d_obj) and gradient (n) at d_x (n). Either output
+ * may be NULL. The objective is a fixed-order (deterministic) reduction. */
+int opf_eval_obj_grad(opf_model *model, const double *d_x, double *d_obj, double *d_grad,
+                      void *stream);
+
+/* Constraint values g(x) into d_c (m). */
+int opf_eval_cons(opf_model *model, const double *d_x, double *d_c, void *stream);
+
+/* Jacobian values (nnz_jac) in pattern order. */
+int opf_eval_jac(opf_model *model, const double *d_x, double *d_jvals, void *stream);
+
+/* Lagrangian Hessian values (nnz_hess) at d_x (n), d_lambda (m), obj_weight. */
+int opf_eval_hess(opf_model *model, const double *d_x, const double *d_lambda,
+                  double obj_weight, double *d_hvals, void *stream);
+
+/* Fused Jacobian and Hessian: one pass over the network. */
+int opf_eval_jac_hess(opf_model *model, const double *d_x, const double *d_lambda,
+                      double obj_weight, double *d_jvals, double *d_hvals, void *stream);
+
+/* Every callback in one pass; any output may be NULL (skipped). d_lambda may
+ * be NULL only if d_hvals is NULL. */
+int opf_eval_all(opf_model *model, const double *d_x, const double *d_lambda, double obj_weight,
+                 double *d_obj, double *d_grad, double *d_c, double *d_jvals, double *d_hvals,
+                 void *stream);
+
+/* The two kernels of one opf_eval_all, selectable: phases = OPF_PHASE_BRANCH
+ * (per-branch rows, Jacobian and Hessian parts, and the per-arc scratch),
+ * OPF_PHASE_BUS (balance rows, bus Hessian rows assembled from that scratch,
+ * generator terms, objective), or both (= opf_eval_all). A bus phase alone
+ * reads the scratch of the last branch phase run on this model, which must
+ * have had the same outputs selected and the same d_x / d_lambda. For timing
+ * and for overlapping the phases of independent models. */
+enum { OPF_PHASE_BRANCH = 1, OPF_PHASE_BUS = 2 };
+int opf_eval_phases(opf_model *model, int32_t phases, const double *d_x, const double *d_lambda,
+                    double obj_weight, double *d_obj, double *d_grad, double *d_c,
+                    double *d_jvals, double *d_hvals, void *stream);
+
+/* opf_eval_all on HOST buffers: copies h_x (and h_lambda) to device staging
+ * buffers owned by the model, evaluates, copies the requested outputs back
+ * and synchronises the stream before returning. The staging buffers are
+ * allocated on the first call (so this call allocates once per model).
+ * Pinned host memory gives asynchronous copies. */
+int opf_eval_all_host(opf_model *model, const double *h_x, const double *h_lambda,
+                      double obj_weight, double *h_obj, double *h_grad, double *h_c,
+                      double *h_jvals, double *h_hvals, void *stream);
+
+/* Flat start (reading of the usual OPF initial point): va = 0, vm = 1
+ * clipped into [vmin, vmax], pg and qg at the midpoint of their bounds,
+ * p and q equal to the branch flows at those voltages. Into d_x (n). */
+int opf_flat_start(opf_model *model, double *d_x, void *stream);
+
+/* Launch shape used by the eval calls; the default suits large instances. */
+int opf_get_launch(const opf_model *model, opf_launch *cfg);
+int opf_set_launch(opf_model *model, const opf_launch *cfg);
+
+/* Autotuner: times each candidate launch shape of the fused opf_eval_all on
+ * this model (CUDA events, `reps` repetitions each, on `stream`), keeps the
+ * fastest and returns it in *best with its time per eval in *best_us.
+ * Allocates temporary output buffers for the duration of the call. */
+int opf_autotune(opf_model *model, const double *d_x, const double *d_lambda, int32_t reps,
+                 void *stream, opf_launch *best, double *best_us);
+
+/* Thread-local description of the last error on this thread. */
+const char *opf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,438 @@
+// extern "C" entry points of libopf (declared in include/opf.h).
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "model.h"
+
+namespace opf {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+}
+
+int build_model(const opf_network *nets, int32_t ninst, double link_ratio, bool device, Model **out);
+void free_model(Model *M);
+void jac_pattern(const Model &M, int64_t *rows, int64_t *cols);
+void hess_pattern(const Model &M, int64_t *rows, int64_t *cols);
+void bounds(const Model &M, double *xl, double *xu, double *gl, double *gu);
+
+}  // namespace opf
+
+using namespace opf;
+
+struct opf_model {
+    Model *M;
+};
+
+namespace {
+
+int check(const opf_model *m)
+{
+    if (!m || !m->M) {
+        set_error("NULL model");
+        return OPF_EINVAL;
+    }
+    return OPF_OK;
+}
+
+// eval-type calls need the device arrays
+int check_dev(const opf_model *m)
+{
+    int rc = check(m);
+    if (rc)
+        return rc;
+    if (!m->M->on_device) {
+        set_error("structure-only model: create it with opf_model_create / opf_batch_create to evaluate");
+        return OPF_ESTATE;
+    }
+    return OPF_OK;
+}
+
+int eval(opf_model *m, unsigned what, const EvalArgs &a, void *stream, int phases = 3)
+{
+    int rc = check_dev(m);
+    if (rc)
+        return rc;
+    if (!a.x) {
+        set_error("d_x is NULL");
+        return OPF_EINVAL;
+    }
+    if ((what & W_HESS) && !a.lam) {
+        set_error("d_lambda is NULL but the Hessian was requested");
+        return OPF_EINVAL;
+    }
+    if (!what)
+        return OPF_OK;
+    return launch_eval(*m->M, a, what, static_cast<cudaStream_t>(stream), phases);
+}
+
+unsigned mask_of(const EvalArgs &a)
+{
+    return (a.obj ? W_OBJ : 0u) | (a.grad ? W_GRAD : 0u) | (a.c ? W_CONS : 0u) |
+           (a.jac ? W_JAC : 0u) | (a.hess ? W_HESS : 0u);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *opf_last_error(void) { return g_err; }
+
+int opf_model_create(const opf_network *net, opf_model **out)
+{
+    if (!out) {
+        set_error("out is NULL");
+        return OPF_EINVAL;
+    }
+    *out = nullptr;
+    if (!net) {
+        set_error("net is NULL");
+        return OPF_EINVAL;
+    }
+    Model *M = nullptr;
+    int rc = build_model(net, 1, 0.0, true, &M);
+    if (rc)
+        return rc;
+    *out = new opf_model{M};
+    return OPF_OK;
+}
+
+int opf_batch_create(const opf_network *nets, int32_t ninst, const opf_batch_opts *opts,
+                     opf_model **out)
+{
+    if (!out) {
+        set_error("out is NULL");
+        return OPF_EINVAL;
+    }
+    *out = nullptr;
+    Model *M = nullptr;
+    int rc = build_model(nets, ninst, opts ? opts->link_ratio : 0.0, true, &M);
+    if (rc)
+        return rc;
+    *out = new opf_model{M};
+    return OPF_OK;
+}
+
+int opf_structure_create(const opf_network *nets, int32_t ninst, const opf_batch_opts *opts,
+                         opf_model **out)
+{
+    if (!out) {
+        set_error("out is NULL");
+        return OPF_EINVAL;
+    }
+    *out = nullptr;
+    Model *M = nullptr;
+    int rc = build_model(nets, ninst, opts ? opts->link_ratio : 0.0, false, &M);
+    if (rc)
+        return rc;
+    *out = new opf_model{M};
+    return OPF_OK;
+}
+
+int opf_model_destroy(opf_model *m)
+{
+    if (!m)
+        return OPF_OK;
+    free_model(m->M);
+    delete m;
+    return OPF_OK;
+}
+
+int opf_dims(const opf_model *m, int64_t *n, int64_t *mm, int64_t *nnzj, int64_t *nnzh)
+{
+    int rc = check(m);
+    if (rc)
+        return rc;
+    if (n)
+        *n = m->M->n;
+    if (mm)
+        *mm = m->M->m;
+    if (nnzj)
+        *nnzj = m->M->nnzj;
+    if (nnzh)
+        *nnzh = m->M->nnzh;
+    return OPF_OK;
+}
+
+int opf_sparsity(const opf_model *m, int32_t kind, int64_t *rows, int64_t *cols)
+{
+    int rc = check(m);
+    if (rc)
+        return rc;
+    if (!rows || !cols) {
+        set_error("rows/cols NULL");
+        return OPF_EINVAL;
+    }
+    if (kind == OPF_JAC)
+        jac_pattern(*m->M, rows, cols);
+    else if (kind == OPF_HESS)
+        hess_pattern(*m->M, rows, cols);
+    else {
+        set_error("unknown pattern kind %d", kind);
+        return OPF_EINVAL;
+    }
+    return OPF_OK;
+}
+
+int opf_bounds(const opf_model *m, double *xl, double *xu, double *gl, double *gu)
+{
+    int rc = check(m);
+    if (rc)
+        return rc;
+    if ((xl == nullptr) != (xu == nullptr) || (gl == nullptr) != (gu == nullptr)) {
+        set_error("bounds come in pairs (xl with xu, gl with gu)");
+        return OPF_EINVAL;
+    }
+    bounds(*m->M, xl, xu, gl, gu);
+    return OPF_OK;
+}
+
+int opf_eval_obj_grad(opf_model *m, const double *d_x, double *d_obj, double *d_grad, void *stream)
+{
+    EvalArgs a{d_x, nullptr, 1.0, d_obj, d_grad, nullptr, nullptr, nullptr};
+    return eval(m, mask_of(a), a, stream);
+}
+
+int opf_eval_cons(opf_model *m, const double *d_x, double *d_c, void *stream)
+{
+    if (!d_c) {
+        set_error("d_c is NULL");
+        return OPF_EINVAL;
+    }
+    EvalArgs a{d_x, nullptr, 1.0, nullptr, nullptr, d_c, nullptr, nullptr};
+    return eval(m, W_CONS, a, stream);
+}
+
+int opf_eval_jac(opf_model *m, const double *d_x, double *d_jvals, void *stream)
+{
+    if (!d_jvals) {
+        set_error("d_jvals is NULL");
+        return OPF_EINVAL;
+    }
+    EvalArgs a{d_x, nullptr, 1.0, nullptr, nullptr, nullptr, d_jvals, nullptr};
+    return eval(m, W_JAC, a, stream);
+}
+
+int opf_eval_hess(opf_model *m, const double *d_x, const double *d_lambda, double obj_weight,
+                  double *d_hvals, void *stream)
+{
+    if (!d_hvals) {
+        set_error("d_hvals is NULL");
+        return OPF_EINVAL;
+    }
+    EvalArgs a{d_x, d_lambda, obj_weight, nullptr, nullptr, nullptr, nullptr, d_hvals};
+    return eval(m, W_HESS, a, stream);
+}
+
+int opf_eval_jac_hess(opf_model *m, const double *d_x, const double *d_lambda, double obj_weight,
+                      double *d_jvals, double *d_hvals, void *stream)
+{
+    if (!d_jvals || !d_hvals) {
+        set_error("d_jvals or d_hvals is NULL");
+        return OPF_EINVAL;
+    }
+    EvalArgs a{d_x, d_lambda, obj_weight, nullptr, nullptr, nullptr, d_jvals, d_hvals};
+    return eval(m, W_JAC | W_HESS, a, stream);
+}
+
+int opf_eval_all(opf_model *m, const double *d_x, const double *d_lambda, double obj_weight,
+                 double *d_obj, double *d_grad, double *d_c, double *d_jvals, double *d_hvals,
+                 void *stream)
+{
+    EvalArgs a{d_x, d_lambda, obj_weight, d_obj, d_grad, d_c, d_jvals, d_hvals};
+    return eval(m, mask_of(a), a, stream);
+}
+
+int opf_eval_phases(opf_model *m, int32_t phases, const double *d_x, const double *d_lambda,
+                    double obj_weight, double *d_obj, double *d_grad, double *d_c, double *d_jvals,
+                    double *d_hvals, void *stream)
+{
+    if (phases < 1 || phases > 3) {
+        set_error("phases must be OPF_PHASE_BRANCH, OPF_PHASE_BUS or both");
+        return OPF_EINVAL;
+    }
+    EvalArgs a{d_x, d_lambda, obj_weight, d_obj, d_grad, d_c, d_jvals, d_hvals};
+    return eval(m, mask_of(a), a, stream, phases);
+}
+
+int opf_eval_all_host(opf_model *m, const double *h_x, const double *h_lambda, double obj_weight,
+                      double *h_obj, double *h_grad, double *h_c, double *h_jvals, double *h_hvals,
+                      void *stream)
+{
+    int rc = check_dev(m);
+    if (rc)
+        return rc;
+    Model &M = *m->M;
+    if (!h_x || (h_hvals && !h_lambda)) {
+        set_error("h_x is NULL, or h_lambda is NULL with h_hvals requested");
+        return OPF_EINVAL;
+    }
+    // staging: x, lambda, obj, grad, c, J, H
+    const size_t need = sizeof(double) * (size_t)(M.n + M.m + 1 + M.n + M.m + M.nnzj + M.nnzh);
+    if (M.stage_bytes < need) {
+        if (M.stage)
+            cudaFree(M.stage);
+        M.stage = nullptr;
+        M.stage_bytes = 0;
+        if (cudaMalloc(&M.stage, need) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("cudaMalloc of %zu staging bytes failed", need);
+            return OPF_ENOMEM;
+        }
+        M.stage_bytes = need;
+    }
+    double *dx = M.stage, *dl = dx + M.n, *dobj = dl + M.m, *dg = dobj + 1, *dc = dg + M.n;
+    double *dj = dc + M.m, *dh = dj + M.nnzj;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(dx, h_x, sizeof(double) * M.n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && h_hvals)
+        e = cudaMemcpyAsync(dl, h_lambda, sizeof(double) * M.m, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) {
+        set_error("host to device copy failed: %s", cudaGetErrorString(e));
+        return OPF_ECUDA;
+    }
+    EvalArgs a{dx, h_hvals ? dl : nullptr, obj_weight, h_obj ? dobj : nullptr, h_grad ? dg : nullptr,
+               h_c ? dc : nullptr, h_jvals ? dj : nullptr, h_hvals ? dh : nullptr};
+    rc = eval(m, mask_of(a), a, stream);
+    if (rc)
+        return rc;
+    struct {
+        double *h;
+        const double *d;
+        int64_t n;
+    } outs[5] = {{h_obj, dobj, 1}, {h_grad, dg, M.n}, {h_c, dc, M.m}, {h_jvals, dj, M.nnzj},
+                 {h_hvals, dh, M.nnzh}};
+    for (auto &o : outs)
+        if (o.h && e == cudaSuccess)
+            e = cudaMemcpyAsync(o.h, o.d, sizeof(double) * o.n, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        set_error("device to host copy failed: %s", cudaGetErrorString(e));
+        return OPF_ECUDA;
+    }
+    return OPF_OK;
+}
+
+int opf_flat_start(opf_model *m, double *d_x, void *stream)
+{
+    int rc = check_dev(m);
+    if (rc)
+        return rc;
+    if (!d_x) {
+        set_error("d_x is NULL");
+        return OPF_EINVAL;
+    }
+    return launch_flat_start(*m->M, d_x, static_cast<cudaStream_t>(stream));
+}
+
+int opf_get_launch(const opf_model *m, opf_launch *cfg)
+{
+    int rc = check(m);
+    if (rc)
+        return rc;
+    if (!cfg) {
+        set_error("cfg is NULL");
+        return OPF_EINVAL;
+    }
+    *cfg = m->M->launch;
+    return OPF_OK;
+}
+
+int opf_set_launch(opf_model *m, const opf_launch *cfg)
+{
+    int rc = check(m);
+    if (rc)
+        return rc;
+    if (!cfg) {
+        set_error("cfg is NULL");
+        return OPF_EINVAL;
+    }
+    for (int b : {cfg->branch_block, cfg->bus_block})
+        if (b < 32 || b > 1024 || b % 32) {
+            set_error("block size %d not a multiple of 32 in [32, 1024]", b);
+            return OPF_EINVAL;
+        }
+    if (cfg->branch_ctas_per_sm < 0 || cfg->bus_ctas_per_sm < 0 || cfg->branch_ctas_per_sm > 64 ||
+        cfg->bus_ctas_per_sm > 64) {
+        set_error("ctas_per_sm must be in [0, 64]");
+        return OPF_EINVAL;
+    }
+    m->M->launch = *cfg;
+    return OPF_OK;
+}
+
+int opf_autotune(opf_model *m, const double *d_x, const double *d_lambda, int32_t reps, void *stream,
+                 opf_launch *best, double *best_us)
+{
+    int rc = check_dev(m);
+    if (rc)
+        return rc;
+    if (!d_x || !d_lambda || reps < 1) {
+        set_error("autotune needs d_x, d_lambda and reps >= 1");
+        return OPF_EINVAL;
+    }
+    Model &M = *m->M;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    double *buf = nullptr;
+    const size_t need = sizeof(double) * (size_t)(1 + M.n + M.m + M.nnzj + M.nnzh);
+    if (cudaMalloc(&buf, need) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("autotune: cudaMalloc of %zu bytes failed", need);
+        return OPF_ENOMEM;
+    }
+    EvalArgs a{d_x, d_lambda, 1.0, buf, buf + 1, buf + 1 + M.n, buf + 1 + M.n + M.m,
+               buf + 1 + M.n + M.m + M.nnzj};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const opf_launch saved = M.launch;
+    opf_launch bestc = saved;
+    float best_ms = 1e30f;
+    const int blocks[] = {64, 128, 256, 512};
+    const int ctas[] = {0, 2, 4, 8, 16};
+    for (int bb : blocks)
+        for (int bu : blocks)
+            for (int cb : ctas)
+                for (int cu : ctas) {
+                    if (cu != 0 && cu != cb)  // keep the search small: equal persistence
+                        continue;
+                    M.launch = opf_launch{bb, bu, cb, cu};
+                    rc = launch_eval(M, a, W_OBJ | W_GRAD | W_CONS | W_JAC | W_HESS, s);  // warm-up
+                    cudaEventRecord(e0, s);
+                    for (int r = 0; r < reps && !rc; r++)
+                        rc = launch_eval(M, a, W_OBJ | W_GRAD | W_CONS | W_JAC | W_HESS, s);
+                    cudaEventRecord(e1, s);
+                    if (cudaEventSynchronize(e1) != cudaSuccess)
+                        rc = OPF_ECUDA;
+                    if (rc)
+                        break;
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (ms < best_ms) {
+                        best_ms = ms;
+                        bestc = M.launch;
+                    }
+                }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(buf);
+    M.launch = rc ? saved : bestc;
+    if (rc)
+        return rc;
+    if (best)
+        *best = bestc;
+    if (best_us)
+        *best_us = 1000.0 * best_ms / reps;
+    return OPF_OK;
+}
+
+}  // extern "C"

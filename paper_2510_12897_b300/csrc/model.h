@@ -1,0 +1,131 @@
+// Internal structures of libopf (host and device). Not part of the C ABI.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/opf.h"
+
+namespace opf {
+
+// Callback selection of one fused evaluation.
+enum : unsigned { W_OBJ = 1u, W_GRAD = 2u, W_CONS = 4u, W_JAC = 8u, W_HESS = 16u };
+
+// Per-arc scratch written by the branch phase at the arc's position in its
+// bus's arc list and read back, in that order, by the bus phase.
+//   p, q    the arc's flow variables (balance sums)
+//   d_aa    d2L/dva_i^2     from this arc's flow rows (i = the arc's bus)
+//   d_ma    d2L/dvm_i dva_i
+//   d_mm    d2L/dvm_i^2
+//   x_ma    d2L/dvm_i dva_j (j = the far bus)
+//   x_aa    d2L/dva_i dva_j
+//   x_mm    d2L/dvm_i dvm_j
+struct __align__(16) ArcScratch {
+    double p, q, d_aa, d_ma, d_mm, x_ma, x_aa, x_mm;
+};
+
+// One instance of a batch, as seen by the kernels. Offsets are absolute
+// positions in the caller's x / g / Jacobian / Hessian arrays and in the
+// model's concatenated network arrays.
+struct InstDev {
+    int32_t nb, nl, ng, T;
+    int32_t ref;        // local reference bus
+    int32_t ramp;       // ramp rows present
+    int32_t br0;        // first branch in the concatenated branch arrays
+    int32_t bus0;       // first bus in the concatenated bus arrays
+    int32_t bptr0;      // first entry of this instance's bus CSR pointers (nb + 1 of them)
+    int32_t gen0;       // first generator
+    int32_t gl0;        // first entry of this instance's bus->generator list
+    int32_t pad0;
+    int64_t x0, c0, j0, h0;
+    int64_t scr0;       // first arc-scratch slot (2 nl T slots per instance)
+    int64_t pd0;        // first entry of per-bus demand [T][nb]
+    int64_t jP;         // Jacobian entries of one period of the P-balance group (nb + ng + 2 nl)
+    int64_t hva, hvm;   // Hessian entries of one period of the va rows / vm rows
+    int64_t link_c, link_j;  // this instance's linking rows and their Jacobian offset; -1 if none
+    int64_t link_x0;    // first pg of instance 0 (linking partner)
+};
+
+struct DevArrays {
+    // branches (concatenated over instances)
+    int2 *br_ft = nullptr;        // local (f, t)
+    double2 *y_ff = nullptr, *y_ft = nullptr, *y_tf = nullptr, *y_tt = nullptr;  // (G, B)
+    double *rate2 = nullptr;      // rate_a^2
+    int2 *br_pos = nullptr;       // positions of (from arc, to arc) in their buses' arc lists
+    // buses
+    double2 *gsbs = nullptr;      // (gs, bs)
+    int32_t *arc_ptr = nullptr;   // CSR over bus-sorted arc slots, nb + 1 per instance
+    int32_t *arc_nbr = nullptr;   // far bus of each slot (local)
+    int32_t *gen_ptr = nullptr;   // CSR bus -> generators, nb + 1 per instance
+    int32_t *gen_list = nullptr;  // local generator ids, ascending per bus
+    int32_t *jpos = nullptr;      // offset of bus i's balance row inside one period's group
+    int32_t *hva_pos = nullptr;   // offset of row va_i inside one period's va rows
+    int32_t *hvm_pos = nullptr;   // offset of row vm_i inside one period's vm rows
+    double *Pd = nullptr, *Qd = nullptr;  // demand per bus and period
+    // generators
+    double *c2 = nullptr, *c1 = nullptr, *c0 = nullptr;
+    double2 *pbnd = nullptr, *qbnd = nullptr;  // (min, max), flat start only
+    double2 *vbnd = nullptr;                   // (vmin, vmax) per bus, flat start only
+    // instances and work lists
+    InstDev *inst = nullptr;
+    int64_t *br_items = nullptr;   // prefix of branch items (nl T) over instances, ninst + 1
+    int64_t *bus_items = nullptr;  // prefix of bus items (nb T)
+    int64_t *gen_items = nullptr;  // prefix of generator items (ng T)
+    // scratch
+    ArcScratch *arcs = nullptr;    // total arc slots (sum over instances of 2 nl T)
+    double *obj_part = nullptr;    // per-CTA partial objective sums
+    unsigned int *ticket = nullptr;
+};
+
+// Host copy of one instance's structure, kept to answer opf_sparsity and
+// opf_bounds without storing the (possibly very large) patterns.
+struct HostInst {
+    int32_t nb = 0, nl = 0, ng = 0, T = 1, ref = 0;
+    bool ramp = false;
+    double ramp_ratio = 0.0;
+    std::vector<int32_t> f, t;
+    std::vector<int32_t> arc_ptr;   // nb + 1
+    std::vector<int32_t> slot_arc;  // arc id of each bus-sorted slot
+    std::vector<int32_t> slot_nbr;  // far bus of each slot
+    std::vector<int32_t> gen_ptr;   // nb + 1
+    std::vector<int32_t> gen_list;  // ascending per bus
+    std::vector<double> vmin, vmax, rate, angmin, angmax, pmin, pmax, qmin, qmax;
+};
+
+struct Model {
+    int32_t ninst = 0;
+    bool on_device = false;  // false: structure only (no device arrays)
+    bool link = false;
+    double link_ratio = 0.0;
+    int64_t n = 0, m = 0, nnzj = 0, nnzh = 0;
+    int64_t link_c0 = 0, link_j0 = 0;  // first linking row / its first Jacobian value
+    int64_t nbr_items = 0, nbus_items = 0, ngen_items = 0, narc_slots = 0;
+    int32_t max_part = 0;         // capacity of obj_part
+    int device = 0, num_sms = 148;
+    opf_launch launch{};
+    std::vector<InstDev> inst;
+    std::vector<HostInst> host;
+    DevArrays d;
+    std::vector<void *> allocations;
+    // staging buffers of opf_eval_all_host (allocated on first use)
+    double *stage = nullptr;
+    size_t stage_bytes = 0;
+};
+
+struct EvalArgs {
+    const double *x;
+    const double *lam;
+    double sigma;
+    double *obj, *grad, *c, *jac, *hess;
+};
+
+// kernels.cu
+int launch_eval(Model &M, const EvalArgs &a, unsigned what, cudaStream_t s, int phases = 3);
+int launch_flat_start(Model &M, double *x, cudaStream_t s);
+
+// abi.cu
+void set_error(const char *fmt, ...);
+
+}  // namespace opf

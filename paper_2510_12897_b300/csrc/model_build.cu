@@ -1,0 +1,642 @@
+// Host side of libopf: validation of the networks, the branch admittances of
+// the pi-model, the layout of x / g / Jacobian / Hessian (Listing 3 order,
+// 2-D index rule of Listing 10), the per-bus tables the bus kernel walks, and
+// the patterns and bounds generated on demand from that layout.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "model.h"
+
+namespace opf {
+
+namespace {
+
+bool finite_all(const double *p, int64_t n)
+{
+    for (int64_t i = 0; i < n; i++)
+        if (!std::isfinite(p[i]))
+            return false;
+    return true;
+}
+
+int validate(const opf_network &n, int s)
+{
+    if (n.nbus < 1 || n.nbranch < 0 || n.ngen < 0 || n.nload < 0 || n.nperiod < 1) {
+        set_error("instance %d: bad sizes (nbus %d, nbranch %d, ngen %d, nload %d, nperiod %d)", s,
+                  n.nbus, n.nbranch, n.ngen, n.nload, n.nperiod);
+        return OPF_EINVAL;
+    }
+    if (n.ref_bus < 0 || n.ref_bus >= n.nbus) {
+        set_error("instance %d: ref_bus %d out of range", s, n.ref_bus);
+        return OPF_EINVAL;
+    }
+    if (!n.bus_vmin || !n.bus_vmax || (n.nbranch && (!n.br_f || !n.br_t || !n.br_r || !n.br_x ||
+        !n.br_b || !n.br_rate_a || !n.br_angmin || !n.br_angmax)) ||
+        (n.ngen && (!n.gen_bus || !n.gen_pmin || !n.gen_pmax || !n.gen_qmin || !n.gen_qmax ||
+        !n.gen_c2 || !n.gen_c1)) || (n.nload && (!n.load_bus || !n.load_pd || !n.load_qd))) {
+        set_error("instance %d: a required array is NULL", s);
+        return OPF_EINVAL;
+    }
+    int64_t nb = n.nbus, nl = n.nbranch, ng = n.ngen;
+    if ((int64_t)n.nperiod * (4 * nl + 2 * nb + 2 * ng) > INT32_MAX / 2) {
+        set_error("instance %d: too large for 32-bit in-instance indices", s);
+        return OPF_EINVAL;
+    }
+    for (int k = 0; k < n.nbranch; k++) {
+        if (n.br_f[k] < 0 || n.br_f[k] >= n.nbus || n.br_t[k] < 0 || n.br_t[k] >= n.nbus) {
+            set_error("instance %d: branch %d endpoint out of range", s, k);
+            return OPF_EINVAL;
+        }
+        if (n.br_f[k] == n.br_t[k]) {
+            set_error("instance %d: branch %d is a self-loop", s, k);
+            return OPF_EINVAL;
+        }
+        if (n.br_r[k] == 0.0 && n.br_x[k] == 0.0) {
+            set_error("instance %d: branch %d has r = x = 0", s, k);
+            return OPF_EINVAL;
+        }
+        if (n.br_tap && n.br_tap[k] < 0.0) {
+            set_error("instance %d: branch %d has a negative tap", s, k);
+            return OPF_EINVAL;
+        }
+    }
+    for (int g = 0; g < n.ngen; g++)
+        if (n.gen_bus[g] < 0 || n.gen_bus[g] >= n.nbus) {
+            set_error("instance %d: generator %d bus out of range", s, g);
+            return OPF_EINVAL;
+        }
+    for (int l = 0; l < n.nload; l++)
+        if (n.load_bus[l] < 0 || n.load_bus[l] >= n.nbus) {
+            set_error("instance %d: load %d bus out of range", s, l);
+            return OPF_EINVAL;
+        }
+    bool ok = finite_all(n.bus_vmin, nb) && finite_all(n.bus_vmax, nb) &&
+              (!n.bus_gs || finite_all(n.bus_gs, nb)) && (!n.bus_bs || finite_all(n.bus_bs, nb));
+    if (nl)
+        ok = ok && finite_all(n.br_r, nl) && finite_all(n.br_x, nl) && finite_all(n.br_b, nl) &&
+             (!n.br_tap || finite_all(n.br_tap, nl)) && (!n.br_shift || finite_all(n.br_shift, nl)) &&
+             finite_all(n.br_rate_a, nl);
+    if (ng)
+        ok = ok && finite_all(n.gen_c2, ng) && finite_all(n.gen_c1, ng) &&
+             (!n.gen_c0 || finite_all(n.gen_c0, ng));
+    if (n.nload)
+        ok = ok && finite_all(n.load_pd, (int64_t)n.nload * n.nperiod) &&
+             finite_all(n.load_qd, (int64_t)n.nload * n.nperiod);
+    if (!ok) {
+        set_error("instance %d: a network parameter is not finite", s);
+        return OPF_EINVAL;
+    }
+    return OPF_OK;
+}
+
+template <class T>
+int upload(Model &M, T **dst, const std::vector<T> &src)
+{
+    size_t bytes = sizeof(T) * (src.empty() ? 1 : src.size());
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaMalloc of %zu bytes failed", bytes);
+        return OPF_ENOMEM;
+    }
+    M.allocations.push_back(p);
+    if (!src.empty() && cudaMemcpy(p, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice) !=
+                            cudaSuccess) {
+        set_error("cudaMemcpy failed: %s", cudaGetErrorString(cudaGetLastError()));
+        return OPF_ECUDA;
+    }
+    *dst = static_cast<T *>(p);
+    return OPF_OK;
+}
+
+template <class T>
+int alloc(Model &M, T **dst, size_t count)
+{
+    size_t bytes = sizeof(T) * (count ? count : 1);
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaMalloc of %zu bytes failed", bytes);
+        return OPF_ENOMEM;
+    }
+    M.allocations.push_back(p);
+    *dst = static_cast<T *>(p);
+    return OPF_OK;
+}
+
+}  // namespace
+
+void free_model(Model *M)
+{
+    if (!M)
+        return;
+    for (void *p : M->allocations)
+        cudaFree(p);
+    if (M->stage)
+        cudaFree(M->stage);
+    delete M;
+}
+
+// Builds one model over `ninst` networks. On error returns a code and frees
+// everything it allocated.
+int build_model(const opf_network *nets, int32_t ninst, double link_ratio, bool device, Model **out)
+{
+    *out = nullptr;
+    if (!nets || ninst < 1) {
+        set_error("need at least one network");
+        return OPF_EINVAL;
+    }
+    for (int s = 0; s < ninst; s++) {
+        int rc = validate(nets[s], s);
+        if (rc)
+            return rc;
+    }
+    bool link = link_ratio > 0.0 && ninst > 1;
+    if (link)
+        for (int s = 0; s < ninst; s++)
+            if (nets[s].ngen != nets[0].ngen || nets[s].nperiod != 1) {
+                set_error("linking rows need equal ngen and nperiod 1 in every instance");
+                return OPF_ESTATE;
+            }
+
+    Model *M = new Model();
+    M->ninst = ninst;
+    M->link = link;
+    M->link_ratio = link_ratio;
+    M->on_device = device;
+    if (device) {
+        if (cudaGetDevice(&M->device) != cudaSuccess ||
+            cudaDeviceGetAttribute(&M->num_sms, cudaDevAttrMultiProcessorCount, M->device) !=
+                cudaSuccess) {
+            cudaGetLastError();
+            set_error("no usable CUDA device");
+            delete M;
+            return OPF_ECUDA;
+        }
+        if (M->num_sms <= 0)
+            M->num_sms = 148;
+    }
+
+    // concatenated host arrays
+    std::vector<int2> br_ft, br_pos;
+    std::vector<double2> y_ff, y_ft, y_tf, y_tt, gsbs, pbnd, qbnd, vbnd;
+    std::vector<double> rate2, Pd, Qd, c2, c1, c0;
+    std::vector<int32_t> arc_ptr, arc_nbr, gen_ptr, gen_list, jpos, hva_pos, hvm_pos;
+    std::vector<int64_t> br_items(1, 0), bus_items(1, 0), gen_items(1, 0);
+
+    int64_t xo = 0, co = 0, jo = 0, ho = 0, so = 0, po = 0;
+    M->inst.resize(ninst);
+    M->host.resize(ninst);
+    for (int s = 0; s < ninst; s++) {
+        const opf_network &n = nets[s];
+        HostInst &H = M->host[s];
+        InstDev &I = M->inst[s];
+        const int nb = n.nbus, nl = n.nbranch, ng = n.ngen, T = n.nperiod, na = 2 * nl;
+        H.nb = nb; H.nl = nl; H.ng = ng; H.T = T; H.ref = n.ref_bus;
+        H.ramp = T > 1 && n.ramp_ratio > 0.0;
+        H.ramp_ratio = n.ramp_ratio;
+        H.f.assign(n.br_f, n.br_f + nl);
+        H.t.assign(n.br_t, n.br_t + nl);
+        H.vmin.assign(n.bus_vmin, n.bus_vmin + nb);
+        H.vmax.assign(n.bus_vmax, n.bus_vmax + nb);
+        H.rate.assign(n.br_rate_a, n.br_rate_a + nl);
+        H.angmin.assign(n.br_angmin, n.br_angmin + nl);
+        H.angmax.assign(n.br_angmax, n.br_angmax + nl);
+        H.pmin.assign(n.gen_pmin, n.gen_pmin + ng);
+        H.pmax.assign(n.gen_pmax, n.gen_pmax + ng);
+        H.qmin.assign(n.gen_qmin, n.gen_qmin + ng);
+        H.qmax.assign(n.gen_qmax, n.gen_qmax + ng);
+
+        I.nb = nb; I.nl = nl; I.ng = ng; I.T = T; I.ref = n.ref_bus; I.ramp = H.ramp;
+        I.br0 = (int32_t)br_ft.size();
+        I.bus0 = (int32_t)gsbs.size();
+        I.bptr0 = (int32_t)arc_ptr.size();
+        I.gen0 = (int32_t)c2.size();
+        I.gl0 = (int32_t)gen_list.size();
+
+        // ---- branches: pi-model admittances (G, B) of Yff, Yft, Ytf, Ytt
+        for (int k = 0; k < nl; k++) {
+            double r = n.br_r[k], x = n.br_x[k], b = n.br_b[k];
+            double tau = (n.br_tap && n.br_tap[k] != 0.0) ? n.br_tap[k] : 1.0;
+            double th = n.br_shift ? n.br_shift[k] : 0.0;
+            double den = r * r + x * x;
+            double gs_ = r / den, bs_ = -x / den;  // ys = 1 / (r + j x)
+            double ct = std::cos(th), st = std::sin(th);
+            double2 tt = make_double2(gs_, bs_ + 0.5 * b);
+            double2 ff = make_double2(tt.x / (tau * tau), tt.y / (tau * tau));
+            // Yft = -ys e^{j th} / tau,  Ytf = -ys e^{-j th} / tau
+            double2 ft = make_double2(-(gs_ * ct - bs_ * st) / tau, -(gs_ * st + bs_ * ct) / tau);
+            double2 tf = make_double2(-(gs_ * ct + bs_ * st) / tau, (gs_ * st - bs_ * ct) / tau);
+            y_ff.push_back(ff);
+            y_ft.push_back(ft);
+            y_tf.push_back(tf);
+            y_tt.push_back(tt);
+            rate2.push_back(n.br_rate_a[k] * n.br_rate_a[k]);
+            br_ft.push_back(make_int2(n.br_f[k], n.br_t[k]));
+        }
+
+        // ---- arcs sorted per bus by (far bus, arc id)
+        std::vector<int32_t> deg(nb + 1, 0);
+        for (int a = 0; a < na; a++)
+            deg[a < nl ? n.br_f[a] : n.br_t[a - nl]]++;
+        H.arc_ptr.assign(nb + 1, 0);
+        for (int i = 0; i < nb; i++)
+            H.arc_ptr[i + 1] = H.arc_ptr[i] + deg[i];
+        std::vector<std::pair<int64_t, int32_t>> keyed(na);
+        for (int a = 0; a < na; a++) {
+            int bus = a < nl ? n.br_f[a] : n.br_t[a - nl];
+            int far = a < nl ? n.br_t[a] : n.br_f[a - nl];
+            keyed[a] = {((int64_t)bus * nb + far) * na + a, a};
+        }
+        std::sort(keyed.begin(), keyed.end());
+        H.slot_arc.resize(na);
+        H.slot_nbr.resize(na);
+        std::vector<int32_t> pos_of(na);
+        for (int p = 0; p < na; p++) {
+            int a = keyed[p].second;
+            H.slot_arc[p] = a;
+            H.slot_nbr[p] = a < nl ? n.br_t[a] : n.br_f[a - nl];
+            pos_of[a] = p;
+        }
+        for (int k = 0; k < nl; k++)
+            br_pos.push_back(make_int2(pos_of[k], pos_of[nl + k]));
+        for (int i = 0; i <= nb; i++)
+            arc_ptr.push_back(H.arc_ptr[i]);
+        for (int p = 0; p < na; p++)
+            arc_nbr.push_back(H.slot_nbr[p]);
+
+        // ---- generators per bus (ascending id)
+        std::vector<int32_t> gcnt(nb + 1, 0);
+        for (int g = 0; g < ng; g++)
+            gcnt[n.gen_bus[g]]++;
+        H.gen_ptr.assign(nb + 1, 0);
+        for (int i = 0; i < nb; i++)
+            H.gen_ptr[i + 1] = H.gen_ptr[i] + gcnt[i];
+        H.gen_list.assign(ng, 0);
+        {
+            std::vector<int32_t> fill(H.gen_ptr.begin(), H.gen_ptr.end() - 1);
+            for (int g = 0; g < ng; g++)
+                H.gen_list[fill[n.gen_bus[g]]++] = g;
+        }
+        for (int i = 0; i <= nb; i++)
+            gen_ptr.push_back(H.gen_ptr[i]);
+        for (int g = 0; g < ng; g++)
+            gen_list.push_back(H.gen_list[g]);
+
+        // ---- per-bus row offsets inside one period
+        int64_t jsum = 0, hva = 0, hvm = 0;
+        for (int i = 0; i < nb; i++) {
+            int p0 = H.arc_ptr[i], p1 = H.arc_ptr[i + 1];
+            int nd = 0, nlt = 0;
+            for (int p = p0; p < p1; p++)
+                if (p == p0 || H.slot_nbr[p] != H.slot_nbr[p - 1]) {
+                    nd++;
+                    if (H.slot_nbr[p] < i)
+                        nlt++;
+                }
+            jpos.push_back((int32_t)jsum);
+            hva_pos.push_back((int32_t)hva);
+            hvm_pos.push_back((int32_t)hvm);
+            jsum += 1 + (H.gen_ptr[i + 1] - H.gen_ptr[i]) + (p1 - p0);
+            if (p1 > p0) {
+                hva += nlt + 1;
+                hvm += (nd + 1) + nlt + 1;
+            } else {
+                hvm += 1;
+            }
+            double gsv = n.bus_gs ? n.bus_gs[i] : 0.0, bsv = n.bus_bs ? n.bus_bs[i] : 0.0;
+            gsbs.push_back(make_double2(gsv, bsv));
+            vbnd.push_back(make_double2(n.bus_vmin[i], n.bus_vmax[i]));
+        }
+
+        // ---- demand per bus and period
+        size_t pd_base = Pd.size();
+        Pd.resize(pd_base + (size_t)nb * T, 0.0);
+        Qd.resize(pd_base + (size_t)nb * T, 0.0);
+        for (int t = 0; t < T; t++)
+            for (int l = 0; l < n.nload; l++) {
+                Pd[pd_base + (size_t)t * nb + n.load_bus[l]] += n.load_pd[(size_t)t * n.nload + l];
+                Qd[pd_base + (size_t)t * nb + n.load_bus[l]] += n.load_qd[(size_t)t * n.nload + l];
+            }
+
+        for (int g = 0; g < ng; g++) {
+            c2.push_back(n.gen_c2[g]);
+            c1.push_back(n.gen_c1[g]);
+            c0.push_back(n.gen_c0 ? n.gen_c0[g] : 0.0);
+            pbnd.push_back(make_double2(n.gen_pmin[g], n.gen_pmax[g]));
+            qbnd.push_back(make_double2(n.gen_qmin[g], n.gen_qmax[g]));
+        }
+
+        // ---- offsets
+        I.jP = (int64_t)nb + ng + na;
+        I.hva = hva;
+        I.hvm = hvm;
+        I.x0 = xo;
+        I.c0 = co;
+        I.j0 = jo;
+        I.h0 = ho;
+        I.scr0 = so;
+        I.pd0 = po;
+        I.link_c = I.link_j = -1;
+        I.link_x0 = 0;
+        xo += (int64_t)T * (2 * nb + 2 * ng + 2 * na);
+        co += (int64_t)T * (1 + 7 * (int64_t)nl + 2 * nb) + (H.ramp ? (int64_t)ng * (T - 1) : 0);
+        jo += (int64_t)T * (1 + 30 * (int64_t)nl + 2 * nb + 2 * ng) + (H.ramp ? 2 * (int64_t)ng * (T - 1) : 0);
+        ho += (int64_t)T * (hva + hvm + ng + 2 * (int64_t)na);
+        so += (int64_t)na * T;
+        po += (int64_t)nb * T;
+        br_items.push_back(br_items.back() + (int64_t)nl * T);
+        bus_items.push_back(bus_items.back() + (int64_t)nb * T);
+        gen_items.push_back(gen_items.back() + (int64_t)ng * T);
+    }
+    M->link_c0 = co;
+    M->link_j0 = jo;
+    if (link) {
+        int64_t ng = nets[0].ngen;
+        for (int s = 1; s < ninst; s++) {
+            M->inst[s].link_c = co + ng * (s - 1);
+            M->inst[s].link_j = jo + 2 * ng * (s - 1);
+            M->inst[s].link_x0 = M->inst[0].x0 + 2 * (int64_t)nets[0].nbus;  // pg of instance 0
+        }
+        co += ng * (ninst - 1);
+        jo += 2 * ng * (ninst - 1);
+    }
+    M->n = xo;
+    M->m = co;
+    M->nnzj = jo;
+    M->nnzh = ho;
+    M->nbr_items = br_items.back();
+    M->nbus_items = bus_items.back();
+    M->ngen_items = gen_items.back();
+    M->narc_slots = so;
+    M->max_part = 16 * M->num_sms;
+    M->launch = opf_launch{128, 128, 0, 0};
+
+    if (!device) {
+        *out = M;
+        return OPF_OK;
+    }
+    int rc = OPF_OK;
+    DevArrays &d = M->d;
+#define UP(field, vec)                           \
+    if (!rc)                                     \
+        rc = upload(*M, &d.field, vec);
+    UP(br_ft, br_ft) UP(y_ff, y_ff) UP(y_ft, y_ft) UP(y_tf, y_tf) UP(y_tt, y_tt)
+    UP(rate2, rate2) UP(br_pos, br_pos) UP(gsbs, gsbs) UP(arc_ptr, arc_ptr) UP(arc_nbr, arc_nbr)
+    UP(gen_ptr, gen_ptr) UP(gen_list, gen_list) UP(jpos, jpos) UP(hva_pos, hva_pos)
+    UP(hvm_pos, hvm_pos) UP(Pd, Pd) UP(Qd, Qd) UP(c2, c2) UP(c1, c1) UP(c0, c0) UP(pbnd, pbnd)
+    UP(qbnd, qbnd) UP(vbnd, vbnd) UP(inst, M->inst) UP(br_items, br_items)
+    UP(bus_items, bus_items) UP(gen_items, gen_items)
+#undef UP
+    if (!rc)
+        rc = alloc(*M, &d.arcs, (size_t)M->narc_slots);
+    if (!rc)
+        rc = alloc(*M, &d.obj_part, (size_t)M->max_part);
+    if (!rc)
+        rc = alloc(*M, &d.ticket, 1);
+    if (!rc && cudaMemset(d.ticket, 0, sizeof(unsigned int)) != cudaSuccess) {
+        set_error("cudaMemset failed");
+        rc = OPF_ECUDA;
+    }
+    if (rc) {
+        free_model(M);
+        return rc;
+    }
+    *out = M;
+    return OPF_OK;
+}
+
+// ------------------------------------------------------------ patterns --
+
+namespace {
+
+struct Offs {  // group bases of one instance
+    int64_t va, vm, pg, qg, p, q;
+};
+
+Offs xoffs(const HostInst &H, const InstDev &I)
+{
+    int64_t T = H.T, nbT = (int64_t)H.nb * T, ngT = (int64_t)H.ng * T, naT = 2 * (int64_t)H.nl * T;
+    return Offs{I.x0, I.x0 + nbT, I.x0 + 2 * nbT, I.x0 + 2 * nbT + ngT, I.x0 + 2 * nbT + 2 * ngT,
+                I.x0 + 2 * nbT + 2 * ngT + naT};
+}
+
+// distinct far buses of bus i, ascending
+void neighbours(const HostInst &H, int i, std::vector<int32_t> &out)
+{
+    out.clear();
+    for (int p = H.arc_ptr[i]; p < H.arc_ptr[i + 1]; p++)
+        if (out.empty() || out.back() != H.slot_nbr[p])
+            out.push_back(H.slot_nbr[p]);
+}
+
+}  // namespace
+
+void jac_pattern(const Model &M, int64_t *rows, int64_t *cols)
+{
+    int64_t e = 0;
+    auto put = [&](int64_t r, int64_t c) {
+        rows[e] = r;
+        cols[e] = c;
+        e++;
+    };
+    std::vector<int32_t> arcs;
+    for (int s = 0; s < M.ninst; s++) {
+        const HostInst &H = M.host[s];
+        const InstDev &I = M.inst[s];
+        const Offs X = xoffs(H, I);
+        const int64_t nb = H.nb, nl = H.nl, ng = H.ng, T = H.T, na = 2 * nl;
+        int64_t r = I.c0;
+        for (int64_t t = 0; t < T; t++)
+            put(r++, X.va + H.ref + nb * t);
+        for (int grp = 0; grp < 4; grp++)
+            for (int64_t t = 0; t < T; t++)
+                for (int64_t k = 0; k < nl; k++) {
+                    int64_t f = H.f[k], b = H.t[k], lo = std::min(f, b), hi = std::max(f, b);
+                    int64_t own = (grp == 0 ? X.p + k : grp == 1 ? X.q + k : grp == 2 ? X.p + nl + k
+                                                                                     : X.q + nl + k) + na * t;
+                    put(r, X.va + lo + nb * t);
+                    put(r, X.va + hi + nb * t);
+                    put(r, X.vm + lo + nb * t);
+                    put(r, X.vm + hi + nb * t);
+                    put(r, own);
+                    r++;
+                }
+        for (int64_t t = 0; t < T; t++)
+            for (int64_t k = 0; k < nl; k++) {
+                int64_t f = H.f[k], b = H.t[k];
+                put(r, X.va + std::min(f, b) + nb * t);
+                put(r, X.va + std::max(f, b) + nb * t);
+                r++;
+            }
+        for (int pq = 0; pq < 2; pq++)
+            for (int64_t t = 0; t < T; t++)
+                for (int i = 0; i < H.nb; i++) {
+                    put(r, X.vm + i + nb * t);
+                    for (int p = H.gen_ptr[i]; p < H.gen_ptr[i + 1]; p++)
+                        put(r, (pq ? X.qg : X.pg) + H.gen_list[p] + ng * t);
+                    arcs.assign(H.slot_arc.begin() + H.arc_ptr[i], H.slot_arc.begin() + H.arc_ptr[i + 1]);
+                    std::sort(arcs.begin(), arcs.end());
+                    for (int a : arcs)
+                        put(r, (pq ? X.q : X.p) + a + na * t);
+                    r++;
+                }
+        for (int side = 0; side < 2; side++)
+            for (int64_t t = 0; t < T; t++)
+                for (int64_t k = 0; k < nl; k++) {
+                    int64_t a = side ? nl + k : k;
+                    put(r, X.p + a + na * t);
+                    put(r, X.q + a + na * t);
+                    r++;
+                }
+        if (H.ramp)
+            for (int64_t t = 1; t < T; t++)
+                for (int64_t g = 0; g < ng; g++) {
+                    put(r, X.pg + g + ng * (t - 1));
+                    put(r, X.pg + g + ng * t);
+                    r++;
+                }
+    }
+    if (M.link) {
+        int64_t r = M.link_c0, ng = M.host[0].ng;
+        Offs X0 = xoffs(M.host[0], M.inst[0]);
+        for (int s = 1; s < M.ninst; s++) {
+            Offs Xs = xoffs(M.host[s], M.inst[s]);
+            for (int64_t g = 0; g < ng; g++) {
+                put(r, X0.pg + g);
+                put(r, Xs.pg + g);
+                r++;
+            }
+        }
+    }
+}
+
+void hess_pattern(const Model &M, int64_t *rows, int64_t *cols)
+{
+    int64_t e = 0;
+    auto put = [&](int64_t r, int64_t c) {
+        rows[e] = r;
+        cols[e] = c;
+        e++;
+    };
+    std::vector<int32_t> nbr;
+    for (int s = 0; s < M.ninst; s++) {
+        const HostInst &H = M.host[s];
+        const InstDev &I = M.inst[s];
+        const Offs X = xoffs(H, I);
+        const int64_t nb = H.nb, ng = H.ng, T = H.T, na = 2 * (int64_t)H.nl;
+        for (int64_t t = 0; t < T; t++)  // rows va_i
+            for (int i = 0; i < H.nb; i++) {
+                neighbours(H, i, nbr);
+                if (nbr.empty())
+                    continue;
+                for (int j : nbr)
+                    if (j < i)
+                        put(X.va + i + nb * t, X.va + j + nb * t);
+                put(X.va + i + nb * t, X.va + i + nb * t);
+            }
+        for (int64_t t = 0; t < T; t++)  // rows vm_i
+            for (int i = 0; i < H.nb; i++) {
+                neighbours(H, i, nbr);
+                int64_t r = X.vm + i + nb * t;
+                if (!nbr.empty()) {
+                    bool self = false;
+                    for (int j : nbr) {
+                        if (!self && j > i) {
+                            put(r, X.va + i + nb * t);
+                            self = true;
+                        }
+                        put(r, X.va + j + nb * t);
+                    }
+                    if (!self)
+                        put(r, X.va + i + nb * t);
+                    for (int j : nbr)
+                        if (j < i)
+                            put(r, X.vm + j + nb * t);
+                }
+                put(r, r);
+            }
+        for (int64_t t = 0; t < T; t++)
+            for (int64_t g = 0; g < ng; g++)
+                put(X.pg + g + ng * t, X.pg + g + ng * t);
+        for (int64_t t = 0; t < T; t++)
+            for (int64_t a = 0; a < na; a++)
+                put(X.p + a + na * t, X.p + a + na * t);
+        for (int64_t t = 0; t < T; t++)
+            for (int64_t a = 0; a < na; a++)
+                put(X.q + a + na * t, X.q + a + na * t);
+    }
+}
+
+void bounds(const Model &M, double *xl, double *xu, double *gl, double *gu)
+{
+    const double inf = INFINITY;
+    for (int s = 0; s < M.ninst; s++) {
+        const HostInst &H = M.host[s];
+        const InstDev &I = M.inst[s];
+        const Offs X = xoffs(H, I);
+        const int64_t nb = H.nb, nl = H.nl, ng = H.ng, T = H.T, na = 2 * nl;
+        for (int64_t t = 0; t < T; t++) {
+            for (int64_t i = 0; i < nb; i++) {
+                if (xl) {
+                    xl[X.va + i + nb * t] = -inf;
+                    xu[X.va + i + nb * t] = inf;
+                    xl[X.vm + i + nb * t] = H.vmin[i];
+                    xu[X.vm + i + nb * t] = H.vmax[i];
+                }
+            }
+            for (int64_t g = 0; g < ng; g++)
+                if (xl) {
+                    xl[X.pg + g + ng * t] = H.pmin[g];
+                    xu[X.pg + g + ng * t] = H.pmax[g];
+                    xl[X.qg + g + ng * t] = H.qmin[g];
+                    xu[X.qg + g + ng * t] = H.qmax[g];
+                }
+            for (int64_t a = 0; a < na; a++)
+                if (xl) {
+                    double rate = H.rate[a % nl];
+                    xl[X.p + a + na * t] = -rate;
+                    xu[X.p + a + na * t] = rate;
+                    xl[X.q + a + na * t] = -rate;
+                    xu[X.q + a + na * t] = rate;
+                }
+        }
+        if (!gl)
+            continue;
+        // groups: ref, 4 flows, angle, P, Q balance: all [0, 0] except angle
+        int64_t c = I.c0;
+        for (int64_t t = 0; t < T; t++, c++)
+            gl[c] = gu[c] = 0.0;
+        for (int64_t r = 0; r < 4 * nl * T; r++, c++)
+            gl[c] = gu[c] = 0.0;
+        for (int64_t t = 0; t < T; t++)
+            for (int64_t k = 0; k < nl; k++, c++) {
+                gl[c] = H.angmin[k];
+                gu[c] = H.angmax[k];
+            }
+        for (int64_t r = 0; r < 2 * nb * T; r++, c++)
+            gl[c] = gu[c] = 0.0;
+        for (int64_t r = 0; r < 2 * nl * T; r++, c++) {
+            gl[c] = -inf;
+            gu[c] = 0.0;
+        }
+        if (H.ramp)
+            for (int64_t t = 1; t < T; t++)
+                for (int64_t g = 0; g < ng; g++, c++) {
+                    gl[c] = -H.ramp_ratio * H.pmax[g];
+                    gu[c] = H.ramp_ratio * H.pmax[g];
+                }
+    }
+    if (M.link && gl) {
+        int64_t c = M.link_c0, ng = M.host[0].ng;
+        for (int s = 1; s < M.ninst; s++)
+            for (int64_t g = 0; g < ng; g++, c++) {
+                gl[c] = -M.link_ratio * M.host[0].pmax[g];
+                gu[c] = M.link_ratio * M.host[0].pmax[g];
+            }
+    }
+}
+
+}  // namespace opf

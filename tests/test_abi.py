@@ -1,0 +1,139 @@
+"""Host-side checks of libopf (no GPU needed): the library loads and exports
+every entry point include/opf.h declares; the layout-generated sparsity
+patterns and bounds equal the oracle's bit for bit; invalid input is
+rejected with the documented codes before any device work."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2510_12897_b300 import opf, synth
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2510_12897_b300 import build
+    build.build()
+    return opf.lib()
+
+
+def test_exports_every_declared_symbol(L):
+    names = opf.declared_symbols()
+    assert "opf_eval_jac_hess" in names and "opf_model_create" in names
+    for name in names:
+        assert hasattr(L, name), name
+
+
+def _grids():
+    g30 = synth.case30()
+    g30g = synth.case30(general=True)
+    return {
+        "case30": g30,
+        "case30_general": g30g,
+        "mp30x5": synth.multi_period(g30g, 5, seed=3, ramp_ratio=0.2),
+        "batch30": synth.contingencies(g30, 6, seed=4),
+    }
+
+
+@pytest.mark.parametrize("name", ["case30", "case30_general", "mp30x5", "batch30"])
+def test_patterns_and_bounds_equal_oracle(L, oracle_mod, name):
+    g = _grids()[name]
+    link = 0.2 if isinstance(g, list) else 0.0
+    M = opf.Model(g, link_ratio=link, structure_only=True)
+    O = oracle_mod.Oracle(g, link_ratio=link)
+    assert (M.n, M.m, M.nnzj, M.nnzh) == (O.n, O.m, O.nnzj, O.nnzh)
+    for a, b in zip(M.jac_pattern(), O.jac_pattern()):
+        np.testing.assert_array_equal(a, b)
+    for a, b in zip(M.hess_pattern(), O.hess_pattern()):
+        np.testing.assert_array_equal(a, b)
+    for a, b in zip(M.bounds(), O.bounds()):
+        np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.slow
+def test_patterns_10k_equal_oracle(L, oracle_mod):
+    g = synth.case10k()
+    M = opf.Model(g, structure_only=True)
+    O = oracle_mod.Oracle(g)
+    assert (M.n, M.m, M.nnzj, M.nnzh) == (77000, 111001, 415001, 136500)
+    for a, b in zip(M.jac_pattern() + M.hess_pattern(), O.jac_pattern() + O.hess_pattern()):
+        np.testing.assert_array_equal(a, b)
+
+
+def test_isolated_bus_and_empty_parts(L, oracle_mod):
+    """A bus with no branch keeps only (vm, vm) in the Hessian; zero loads
+    and a generator-free bus are fine."""
+    g = synth.case30(general=True)
+    nb = g.nbus + 1  # one extra isolated bus
+    g2 = g.copy(nbus=nb, bus_vmin=np.append(g.bus_vmin, 0.95), bus_vmax=np.append(g.bus_vmax, 1.05),
+                bus_gs=np.append(g.bus_gs, 0.01), bus_bs=np.append(g.bus_bs, 0.02))
+    M = opf.Model(g2, structure_only=True)
+    O = oracle_mod.Oracle(g2)
+    for a, b in zip(M.jac_pattern() + M.hess_pattern(), O.jac_pattern() + O.hess_pattern()):
+        np.testing.assert_array_equal(a, b)
+    single = g.copy(nbus=1, bus_vmin=g.bus_vmin[:1], bus_vmax=g.bus_vmax[:1], bus_gs=g.bus_gs[:1],
+                    bus_bs=g.bus_bs[:1], br_f=g.br_f[:0], br_t=g.br_t[:0], br_r=g.br_r[:0],
+                    br_x=g.br_x[:0], br_b=g.br_b[:0], br_tap=g.br_tap[:0], br_shift=g.br_shift[:0],
+                    br_rate_a=g.br_rate_a[:0], br_angmin=g.br_angmin[:0], br_angmax=g.br_angmax[:0],
+                    gen_bus=np.zeros(1, np.int32), gen_pmin=g.gen_pmin[:1], gen_pmax=g.gen_pmax[:1],
+                    gen_qmin=g.gen_qmin[:1], gen_qmax=g.gen_qmax[:1], gen_c2=g.gen_c2[:1],
+                    gen_c1=g.gen_c1[:1], gen_c0=g.gen_c0[:1], load_bus=np.zeros(0, np.int32),
+                    load_pd=np.zeros((1, 0)), load_qd=np.zeros((1, 0)), ref_bus=0)
+    M = opf.Model(single, structure_only=True)
+    O = oracle_mod.Oracle(single)
+    assert (M.n, M.m, M.nnzj, M.nnzh) == (O.n, O.m, O.nnzj, O.nnzh) == (4, 3, 5, 2)
+    for a, b in zip(M.jac_pattern() + M.hess_pattern(), O.jac_pattern() + O.hess_pattern()):
+        np.testing.assert_array_equal(a, b)
+
+
+def _expect(code, fn, *a, **k):
+    with pytest.raises(opf.OpfError) as e:
+        fn(*a, **k)
+    assert e.value.code == code, str(e.value)
+
+
+def test_invalid_networks_rejected(L):
+    g = synth.case30()
+    f = g.br_f.copy()
+    f[3] = g.br_t[3]
+    _expect(opf.OPF_EINVAL, opf.Model, g.copy(br_f=f), structure_only=True)  # self-loop
+    f = g.br_f.copy()
+    f[0] = g.nbus
+    _expect(opf.OPF_EINVAL, opf.Model, g.copy(br_f=f), structure_only=True)  # out of range
+    r, x = g.br_r.copy(), g.br_x.copy()
+    r[2] = x[2] = 0.0
+    _expect(opf.OPF_EINVAL, opf.Model, g.copy(br_r=r, br_x=x), structure_only=True)
+    tap = g.br_tap.copy()
+    tap[1] = -1.0
+    _expect(opf.OPF_EINVAL, opf.Model, g.copy(br_tap=tap), structure_only=True)
+    gb = g.gen_bus.copy()
+    gb[0] = -1
+    _expect(opf.OPF_EINVAL, opf.Model, g.copy(gen_bus=gb), structure_only=True)
+    lb = g.load_bus.copy()
+    lb[0] = 999
+    _expect(opf.OPF_EINVAL, opf.Model, g.copy(load_bus=lb), structure_only=True)
+    c2 = g.gen_c2.copy()
+    c2[0] = np.nan
+    _expect(opf.OPF_EINVAL, opf.Model, g.copy(gen_c2=c2), structure_only=True)
+    _expect(opf.OPF_EINVAL, opf.Model, g.copy(ref_bus=g.nbus), structure_only=True)
+    _expect(opf.OPF_EINVAL, opf.Model, g.copy(load_pd=np.zeros((0, g.nload)),
+                                              load_qd=np.zeros((0, g.nload))), structure_only=True)
+    # linking rows need equal generator counts
+    g2 = g.copy(gen_bus=g.gen_bus[:-1], gen_pmin=g.gen_pmin[:-1], gen_pmax=g.gen_pmax[:-1],
+                gen_qmin=g.gen_qmin[:-1], gen_qmax=g.gen_qmax[:-1], gen_c2=g.gen_c2[:-1],
+                gen_c1=g.gen_c1[:-1], gen_c0=g.gen_c0[:-1])
+    _expect(opf.OPF_ESTATE, opf.Model, [g, g2], link_ratio=0.2, structure_only=True)
+
+
+def test_null_and_state_errors(L):
+    _expect(opf.OPF_EINVAL, opf._check, L.opf_dims(None, None, None, None, None))
+    _expect(opf.OPF_EINVAL, opf._check, L.opf_model_create(None, ctypes.byref(ctypes.c_void_p())))
+    M = opf.Model(synth.case30(), structure_only=True)
+    # a structure-only model refuses evaluation without touching a device
+    _expect(opf.OPF_ESTATE, opf._check, L.opf_eval_cons(M.h, ctypes.c_void_p(16), ctypes.c_void_p(16), None))
+    _expect(opf.OPF_ESTATE, opf._check, L.opf_flat_start(M.h, ctypes.c_void_p(16), None))
+    _expect(opf.OPF_EINVAL, opf._check, L.opf_sparsity(M.h, 7, ctypes.cast(None, opf._i64p),
+                                                       ctypes.cast(None, opf._i64p)))
+    cfg = opf.OpfLaunch(100, 128, 0, 0)
+    _expect(opf.OPF_EINVAL, opf._check, L.opf_set_launch(M.h, ctypes.byref(cfg)))
+    assert b"multiple of 32" in L.opf_last_error()

@@ -1,0 +1,278 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Bar: sparsity patterns equal bit for bit; every floating-point output entry
+satisfies |gpu - oracle| <= 1e-12 * max(|oracle|, s), where s is the
+oracle's magnitude scale of the entry (the sum over its contributions of a
+bound on each contribution's absolute value), so cancellation inside an
+entry does not turn rounding noise into a failure.
+"""
+import numpy as np
+import pytest
+
+from paper_2510_12897_b300 import opf, synth
+
+pytestmark = pytest.mark.gpu
+RTOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    if not t.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    from paper_2510_12897_b300 import build
+    build.build()
+    return t
+
+
+def close(name, gpu, ora, scale, rtol=RTOL):
+    gpu = np.asarray(gpu)
+    bound = rtol * np.maximum(np.abs(ora), scale)
+    err = np.abs(gpu - ora)
+    bad = err > bound
+    if bad.any():
+        i = int(np.argmax(err - bound))
+        raise AssertionError(f"{name}: {int(bad.sum())} of {bad.size} entries off; worst #{i}: "
+                             f"gpu {gpu[i]!r} oracle {ora[i]!r} scale {scale[i]!r}")
+
+
+def dev(torch, a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def run_all(torch, M, x, lam, sigma, launch=None):
+    if launch:
+        M.set_launch(**launch)
+    dx, dl = dev(torch, x), dev(torch, lam)
+    out = dict(obj=torch.empty(1, dtype=torch.float64, device="cuda"),
+               grad=torch.empty(M.n, dtype=torch.float64, device="cuda"),
+               c=torch.empty(M.m, dtype=torch.float64, device="cuda"),
+               jv=torch.empty(M.nnzj, dtype=torch.float64, device="cuda"),
+               hv=torch.empty(M.nnzh, dtype=torch.float64, device="cuda"))
+    for v in out.values():
+        v.fill_(np.nan)  # every entry must be written
+    M.eval_all(dx, dl, sigma, **out)
+    torch.cuda.synchronize()
+    return {k: host(v) for k, v in out.items()}
+
+
+def check_against_oracle(O, got, x, lam, sigma, tag=""):
+    c, cs = O.cons(x, with_scale=True)
+    close(tag + "cons", got["c"], c, cs)
+    jv, js = O.jac(x, with_scale=True)
+    close(tag + "jac", got["jv"], jv, js)
+    hv, hs = O.hess(x, lam, sigma, with_scale=True)
+    close(tag + "hess", got["hv"], hv, hs)
+    g = O.grad(x)
+    close(tag + "grad", got["grad"], g, np.abs(g))
+    f = O.obj(x)
+    # objective: sum of per-generator costs; scale = sum of |cost terms|
+    assert abs(got["obj"][0] - f) <= 1e-12 * max(abs(f), 1.0) * 10, (got["obj"][0], f)
+
+
+def both(torch, oracle_mod, g, link=0.0):
+    M = opf.Model(g, link_ratio=link)
+    O = oracle_mod.Oracle(g, link_ratio=link)
+    assert (M.n, M.m, M.nnzj, M.nnzh) == (O.n, O.m, O.nnzj, O.nnzh)
+    for a, b in zip(M.jac_pattern() + M.hess_pattern(), O.jac_pattern() + O.hess_pattern()):
+        np.testing.assert_array_equal(a, b)
+    return M, O
+
+
+def points(g, m, count, seed):
+    rng = np.random.default_rng(seed)
+    gl = g if isinstance(g, list) else [g]
+    for _ in range(count):
+        x = np.concatenate([synth.random_point(h, rng) for h in gl])
+        yield x, rng.standard_normal(m)
+
+
+# ------------------------------------------------------------ config 1 --
+
+def test_case30_64_points(torch, oracle_mod):
+    """30-bus meshed grid, 64 random points and multipliers N(0, 1)."""
+    g = synth.case30()
+    M, O = both(torch, oracle_mod, g)
+    for k, (x, lam) in enumerate(points(g, M.m, 64, seed=1)):
+        sigma = 0.0 if k == 7 else 1.0
+        check_against_oracle(O, run_all(torch, M, x, lam, sigma), x, lam, sigma, f"pt{k} ")
+
+
+def test_general_terms(torch, oracle_mod):
+    """Shunts, off-nominal taps, phase shifters and parallel branches."""
+    for seed in (30, 31, 32):
+        g = synth.case30(seed=seed, general=True)
+        M, O = both(torch, oracle_mod, g)
+        for x, lam in points(g, M.m, 6, seed=seed):
+            check_against_oracle(O, run_all(torch, M, x, lam, 0.7), x, lam, 0.7)
+
+
+def test_separate_calls_match_fused(torch, oracle_mod):
+    g = synth.case30(general=True)
+    M, O = both(torch, oracle_mod, g)
+    x, lam = next(points(g, M.m, 1, seed=5))
+    fused = run_all(torch, M, x, lam, 1.0)
+    dx, dl = dev(torch, x), dev(torch, lam)
+    c = torch.empty(M.m, dtype=torch.float64, device="cuda")
+    jv = torch.empty(M.nnzj, dtype=torch.float64, device="cuda")
+    hv = torch.empty(M.nnzh, dtype=torch.float64, device="cuda")
+    hv2 = torch.empty_like(hv)
+    jv2 = torch.empty_like(jv)
+    ob = torch.empty(1, dtype=torch.float64, device="cuda")
+    gr = torch.empty(M.n, dtype=torch.float64, device="cuda")
+    M.eval_cons(dx, c)
+    M.eval_jac(dx, jv)
+    M.eval_hess(dx, dl, 1.0, hv)
+    M.eval_jac_hess(dx, dl, 1.0, jv2, hv2)
+    M.eval_obj_grad(dx, ob, gr)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(host(c), fused["c"])
+    np.testing.assert_array_equal(host(jv), fused["jv"])
+    np.testing.assert_array_equal(host(jv2), fused["jv"])
+    np.testing.assert_array_equal(host(hv), fused["hv"])
+    np.testing.assert_array_equal(host(hv2), fused["hv"])
+    np.testing.assert_array_equal(host(gr), fused["grad"])
+    np.testing.assert_array_equal(host(ob), fused["obj"])
+
+
+def test_deterministic_and_graph_replay(torch, oracle_mod):
+    g = synth.case30(general=True)
+    M, O = both(torch, oracle_mod, g)
+    x, lam = next(points(g, M.m, 1, seed=8))
+    a = run_all(torch, M, x, lam, 1.0)
+    b = run_all(torch, M, x, lam, 1.0)
+    for k in a:
+        np.testing.assert_array_equal(a[k], b[k])
+    dx, dl = dev(torch, x), dev(torch, lam)
+    outs = [torch.full((n,), np.nan, dtype=torch.float64, device="cuda")
+            for n in (1, M.n, M.m, M.nnzj, M.nnzh)]
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        M.eval_all(dx, dl, 1.0, *outs, stream=s)  # warm-up outside capture
+    torch.cuda.synchronize()
+    for o in outs:
+        o.fill_(np.nan)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        for _ in range(3):
+            M.eval_all(dx, dl, 1.0, *outs, stream=s)
+    graph.replay()
+    torch.cuda.synchronize()
+    for k, o in zip(("obj", "grad", "c", "jv", "hv"), outs):
+        np.testing.assert_array_equal(host(o), a[k])
+
+
+def test_host_buffers_variant(torch, oracle_mod):
+    g = synth.case30(general=True)
+    M, O = both(torch, oracle_mod, g)
+    x, lam = next(points(g, M.m, 1, seed=9))
+    a = run_all(torch, M, x, lam, 0.5)
+    outs = dict(obj=np.empty(1), grad=np.empty(M.n), c=np.empty(M.m), jv=np.empty(M.nnzj),
+                hv=np.empty(M.nnzh))
+    M.eval_all_host(x, lam, 0.5, **outs)
+    for k in a:
+        np.testing.assert_array_equal(outs[k], a[k])
+
+
+@pytest.mark.parametrize("launch", [
+    dict(branch_block=32, bus_block=32, branch_ctas_per_sm=1, bus_ctas_per_sm=1),
+    dict(branch_block=64, bus_block=256, branch_ctas_per_sm=0, bus_ctas_per_sm=0),
+    dict(branch_block=512, bus_block=64, branch_ctas_per_sm=2, bus_ctas_per_sm=0),
+])
+def test_launch_shapes(torch, oracle_mod, launch):
+    """Every launch shape the autotuner may pick gives parity (grid-stride
+    loops cover all items whatever the grid)."""
+    g = synth.multi_period(synth.case30(general=True), 7, seed=2, ramp_ratio=0.2)
+    M, O = both(torch, oracle_mod, g)
+    x, lam = next(points(g, M.m, 1, seed=3))
+    check_against_oracle(O, run_all(torch, M, x, lam, 1.0, launch), x, lam, 1.0)
+
+
+# ------------------------------------------------ edge cases --
+
+def test_isolated_bus_single_bus_no_generators(torch, oracle_mod):
+    g = synth.case30(general=True)
+    g2 = g.copy(nbus=g.nbus + 1, bus_vmin=np.append(g.bus_vmin, 0.95),
+                bus_vmax=np.append(g.bus_vmax, 1.05), bus_gs=np.append(g.bus_gs, 0.01),
+                bus_bs=np.append(g.bus_bs, 0.02))
+    M, O = both(torch, oracle_mod, g2)
+    x, lam = next(points(g2, M.m, 1, seed=4))
+    check_against_oracle(O, run_all(torch, M, x, lam, 1.0), x, lam, 1.0)
+    nogen = g.copy(gen_bus=g.gen_bus[:0], gen_pmin=g.gen_pmin[:0], gen_pmax=g.gen_pmax[:0],
+                   gen_qmin=g.gen_qmin[:0], gen_qmax=g.gen_qmax[:0], gen_c2=g.gen_c2[:0],
+                   gen_c1=g.gen_c1[:0], gen_c0=g.gen_c0[:0])
+    M, O = both(torch, oracle_mod, nogen)
+    x, lam = next(points(nogen, M.m, 1, seed=5))
+    got = run_all(torch, M, x, lam, 1.0)
+    check_against_oracle(O, got, x, lam, 1.0)
+    assert got["obj"][0] == 0.0
+
+
+# ------------------------------------------------ multi-period, batch --
+
+def test_multiperiod_small(torch, oracle_mod):
+    g = synth.multi_period(synth.case30(general=True), 5, seed=6, ramp_ratio=0.2)
+    M, O = both(torch, oracle_mod, g)
+    for x, lam in points(g, M.m, 4, seed=6):
+        check_against_oracle(O, run_all(torch, M, x, lam, 1.0), x, lam, 1.0)
+
+
+def test_batch_small_with_links(torch, oracle_mod):
+    insts = synth.contingencies(synth.case30(general=True), 9, seed=7)
+    M, O = both(torch, oracle_mod, insts, link=0.2)
+    for x, lam in points(insts, M.m, 3, seed=7):
+        check_against_oracle(O, run_all(torch, M, x, lam, 1.0), x, lam, 1.0)
+
+
+def test_flat_start(torch, oracle_mod):
+    """va = 0, vm = 1 (inside [vmin, vmax]), pg and qg at mid-bounds and
+    flow rows of the oracle at zero (p, q are the flows)."""
+    g = synth.case30(general=True)
+    M, O = both(torch, oracle_mod, g)
+    x = torch.full((M.n,), np.nan, dtype=torch.float64, device="cuda")
+    M.flat_start(x)
+    x = host(x)
+    nb, ng = g.nbus, g.ngen
+    assert np.all(x[:nb] == 0) and np.all(x[nb:2 * nb] == 1.0)
+    np.testing.assert_array_equal(x[2 * nb:2 * nb + ng], 0.5 * (g.gen_pmin + g.gen_pmax))
+    np.testing.assert_array_equal(x[2 * nb + ng:2 * nb + 2 * ng], 0.5 * (g.gen_qmin + g.gen_qmax))
+    c, s = O.cons(x, with_scale=True)
+    nl = g.nbranch
+    flows = slice(1, 1 + 4 * nl)
+    close("flat flows", c[flows], np.zeros(4 * nl), s[flows])
+
+
+# ------------------------------------------------ full-size workloads --
+
+def test_case10k_full(torch, oracle_mod):
+    """The 10,000-bus grid, every entry, in the default launch shape and the
+    autotuned one (the shape the benchmark times)."""
+    g = synth.case10k()
+    M, O = both(torch, oracle_mod, g)
+    x, lam = next(points(g, M.m, 1, seed=10))
+    check_against_oracle(O, run_all(torch, M, x, lam, 1.0), x, lam, 1.0, "default ")
+    best, _ = M.autotune(dev(torch, x), dev(torch, lam), reps=3)
+    check_against_oracle(O, run_all(torch, M, x, lam, 1.0, best), x, lam, 1.0, "tuned ")
+
+
+@pytest.mark.slow
+def test_mp2k_96_full(torch, oracle_mod):
+    """2,000-bus grid over 96 periods with ramp rows, every entry."""
+    g = synth.mp2k()
+    M, O = both(torch, oracle_mod, g)
+    x, lam = next(points(g, M.m, 1, seed=11))
+    check_against_oracle(O, run_all(torch, M, x, lam, 1.0), x, lam, 1.0)
+
+
+@pytest.mark.slow
+def test_sc1k_501_full(torch, oracle_mod):
+    """1,000-bus base case plus 500 N-1 contingencies (uneven sizes) with
+    linking rows, every entry."""
+    insts = synth.sc1k()
+    M, O = both(torch, oracle_mod, insts, link=0.2)
+    x, lam = next(points(insts, M.m, 1, seed=12))
+    check_against_oracle(O, run_all(torch, M, x, lam, 1.0), x, lam, 1.0)
