@@ -1,0 +1,499 @@
+#!/usr/bin/env python
+"""Throughput of the AC-OPF callback evaluation on a B300.
+
+Workload (default): the seeded synthetic 10,000-bus grid (13,000 branches,
+2,500 generators, 7,000 loads; polar form with branch-flow variables, the
+model of the paper's Listing 3). One step = one fused evaluation of every
+callback of Listing 1 at one point: objective, gradient, constraints,
+Jacobian values and Lagrangian-Hessian values (so each step contains one
+Jacobian and one Hessian evaluation). Inputs are resident in HBM; steps
+rotate over R independent buffer sets (point, multipliers, outputs and a
+copy of the network) whose total exceeds twice the L2, so every step reads
+from HBM. The timed region is a CUDA-graph replay bracketed by CUDA events.
+
+Also reported: the dominant kernel's own duration and HBM roofline, the
+end-to-end rate through the host-buffer C-ABI call (copies included), the
+FP64 oracle timed on this host's cores, and batched vs per-instance loops on
+the multi-period (2,000 buses x 96 periods) and N-1 (1,000 buses x 501
+instances) workloads.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl own|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica on its own GPU
+(the single-instance evaluation does not shard); value = all ranks' steps /
+the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Hessian+Jacobian evals/s at 10k buses"
+UNIT = "evals/s"
+WORKLOAD = ("synthetic 10,000-bus grid (13,000 branches, 2,500 generators, 7,000 loads), "
+            "single instance; one step = fused obj+grad+cons+Jacobian+Hessian evaluation")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=2048)
+    p.add_argument("--warmup", type=int, default=64)
+    p.add_argument("--impl", choices=["own", "reference"], default="own")
+    p.add_argument("--sets", type=int, default=32, help="rotating buffer sets (>= 2x L2 in total)")
+    p.add_argument("--no-batched", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--seed", type=int, default=10000)
+    p.add_argument("--no-autotune", action="store_true", help="default launch shape (profiling runs)")
+    p.add_argument("--e2e-steps", type=int, default=256)
+    return p.parse_args()
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def profile_traffic():
+    """DRAM bytes per launch of the branch kernel from the committed ncu
+    summary (a line 'dram_bytes_per_launch: N'), or None."""
+    path = os.path.join(ROOT, "profiles", "branch_kernel_case10k.md")
+    try:
+        m = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", open(path).read())
+        return float(m.group(1)) if m else None
+    except OSError:
+        return None
+
+
+# ----------------------------------------------------------- byte counts --
+
+def eval_bytes(g, nnzh):
+    """Algorithmic bytes of one fused evaluation (all callbacks)."""
+    nb, nl, ng, nload = g.nbus, g.nbranch, g.ngen, g.nload
+    na = 2 * nl
+    n = 2 * nb + 2 * ng + 2 * na
+    m = 1 + 7 * nl + 2 * nb
+    nnzj = 1 + 30 * nl + 2 * nb + 2 * ng
+    reads = 8 * n + 8 * m + 48 * nl + 16 * nb + 16 * nload + 28 * ng
+    writes = 8 * (1 + n + m + nnzj + nnzh)
+    return reads + writes
+
+
+def jac_hess_bytes(g, nnzh):
+    """Algorithmic bytes of one Jacobian + Hessian evaluation: x, lambda,
+    branch parameters, gs/bs, generator bus + c2; the two value arrays."""
+    nb, nl, ng = g.nbus, g.nbranch, g.ngen
+    n = 2 * nb + 2 * ng + 4 * nl
+    m = 1 + 7 * nl + 2 * nb
+    nnzj = 1 + 30 * nl + 2 * nb + 2 * ng
+    return 8 * n + 8 * m + 48 * nl + 16 * nb + 12 * ng + 8 * (nnzj + nnzh)
+
+
+def branch_kernel_bytes(g):
+    """Algorithmic bytes of one branch-phase launch of the fused evaluation."""
+    nb, nl = g.nbus, g.nbranch
+    na = 2 * nl
+    reads = 8 * (2 * nb + 2 * na + 6 * nl) + 48 * nl
+    writes = 8 * (7 * nl + 26 * nl + 4 * nl + 2 * na)
+    return reads + writes
+
+
+# ---------------------------------------------------------------- clocks --
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9 and f[1].replace(".", "").isdigit():
+                    rows.append(f)
+        except OSError:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]),
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
+
+
+# ------------------------------------------------------------- reference --
+
+def cpu_oracle_rate(g, seconds, max_steps=None, warmup=1):
+    """Full oracle evaluations (obj, grad, cons, jac, hess) per second."""
+    import oracle
+    O = oracle.Oracle(g)
+    rng = np.random.default_rng(1)
+    x = __import__("paper_2510_12897_b300.synth", fromlist=["x"]).random_point(g, rng)
+    lam = rng.standard_normal(O.m)
+
+    def one():
+        O.obj(x)
+        O.grad(x)
+        O.cons(x)
+        O.jac(x)
+        O.hess(x, lam, 1.0)
+
+    for _ in range(warmup):
+        one()
+    t0 = time.perf_counter()
+    k = 0
+    while True:
+        one()
+        k += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or (max_steps and k >= max_steps):
+            break
+    return k / el, k, el
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2510_12897_b300 import synth
+    g = synth.case10k(args.seed)
+    # each step is one full oracle evaluation; the run is bounded to about
+    # a minute whatever K is
+    t_one = time.perf_counter()
+    rate, k, el = cpu_oracle_rate(g, seconds=60.0, max_steps=args.steps, warmup=min(args.warmup, 2))
+    cores = 1
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": k, "warmup": min(args.warmup, 2), "ms_per_step": 1000.0 * el / k,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD},
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{k} of the requested {args.steps} steps (bounded to ~60 s), "
+                                   "single-threaded C oracle, full 10k-bus evaluation per step"},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    del t_one
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------- own arm --
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    import torch
+    from paper_2510_12897_b300 import build, opf, synth
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        build.build()
+    if dist:
+        dist.barrier()
+    dev = torch.device("cuda", local)
+    f64 = torch.float64
+
+    g = synth.case10k(args.seed)
+    R = max(1, args.sets)
+    models = [opf.Model(g) for _ in range(R)]
+    M0 = models[0]
+    n, m, nnzj, nnzh = M0.n, M0.m, M0.nnzj, M0.nnzh
+    rng = np.random.default_rng(1234 + rank)
+    xs = [torch.tensor(synth.random_point(g, rng), device=dev) for _ in range(R)]
+    ls = [torch.tensor(rng.standard_normal(m), device=dev) for _ in range(R)]
+    outs = [[torch.empty(k, dtype=f64, device=dev) for k in (1, n, m, nnzj, nnzh)] for _ in range(R)]
+    set_bytes = sum(t.numel() * 8 for t in xs[0:1] + ls[0:1] + outs[0])
+    stream = torch.cuda.Stream(device=dev)
+
+    # launch shape: the autotuner's pick on this workload, shared by all sets
+    if args.no_autotune:
+        best, tuned_us = M0.get_launch(), None
+    else:
+        best, tuned_us = M0.autotune(xs[0], ls[0], reps=20, stream=stream)
+    for Mk in models:
+        Mk.set_launch(**best)
+    torch.cuda.synchronize()
+
+    def step(k, s):
+        Mk = models[k % R]
+        o = outs[k % R]
+        Mk.eval_all(xs[k % R], ls[k % R], 1.0, *o, stream=s)
+
+    def capture(fn, count):
+        gr = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(stream):
+            with torch.cuda.graph(gr, stream=stream):
+                for k in range(count):
+                    fn(k, stream)
+        return gr
+
+    def timed(graph_full, reps, tail=None):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for _ in range(reps):
+                graph_full.replay()
+            if tail is not None:
+                tail.replay()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        if dist:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    # warm-up (untimed)
+    with torch.cuda.stream(stream):
+        for k in range(args.warmup):
+            step(k, stream)
+    torch.cuda.synchronize()
+
+    K = args.steps
+    g_full = capture(step, R)
+    g_tail = capture(step, K % R) if K % R else None
+    g_full.replay()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        ms = timed(g_full, K // R, g_tail)
+    clocks = clk.summary()
+    ms_per_step = ms / K
+    value = world * K / (ms / 1000.0)
+
+    # dominant kernel alone: branch phase, same rotation
+    def branch_only(k, s):
+        o = outs[k % R]
+        models[k % R].eval_phases(opf.OPF_PHASE_BRANCH, xs[k % R], ls[k % R], 1.0, *o, stream=s)
+
+    def bus_only(k, s):
+        o = outs[k % R]
+        models[k % R].eval_phases(opf.OPF_PHASE_BUS, xs[k % R], ls[k % R], 1.0, *o, stream=s)
+
+    def jac_hess(k, s):
+        o = outs[k % R]
+        models[k % R].eval_jac_hess(xs[k % R], ls[k % R], 1.0, o[3], o[4], stream=s)
+
+    reps = max(1, K // R)
+    gb = capture(branch_only, R)
+    gb.replay()
+    br_us = 1000.0 * timed(gb, reps) / (reps * R)
+    gu = capture(bus_only, R)
+    gu.replay()
+    bus_us = 1000.0 * timed(gu, reps) / (reps * R)
+    gj = capture(jac_hess, R)
+    gj.replay()
+    jh_us = 1000.0 * timed(gj, reps) / (reps * R)
+
+    hbm, peak_kind = load_peaks()
+    ev_bytes = eval_bytes(g, nnzh)
+    br_bytes = branch_kernel_bytes(g)
+    dominant = "branch" if br_us >= bus_us else "bus"
+    dom_us = max(br_us, bus_us)
+    dom_bytes = br_bytes if dominant == "branch" else ev_bytes - br_bytes
+    achieved = dom_bytes / (dom_us * 1e-6) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": profile_traffic() if dominant == "branch" else None,
+                "kernel": f"{dominant} phase", "kernel_us": dom_us,
+                "algorithmic_bytes_per_launch": dom_bytes, "peak_kind": peak_kind}
+
+    # end to end through the host-buffer C-ABI call
+    hx = [x.cpu().pin_memory() for x in xs[:2]]
+    hl = [l.cpu().pin_memory() for l in ls[:2]]
+    ho = [torch.empty(k, dtype=f64).pin_memory() for k in (1, n, m, nnzj, nnzh)]
+    e2e_steps = max(1, min(K, args.e2e_steps))
+    with torch.cuda.stream(stream):
+        M0.eval_all_host(hx[0], hl[0], 1.0, *ho, stream=stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for k in range(e2e_steps):
+            M0.eval_all_host(hx[k % 2], hl[k % 2], 1.0, *ho, stream=stream)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * e2e_steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": 8 * (n + m), "d2h_bytes_per_step": 8 * (1 + n + m + nnzj + nnzh),
+           "steps": e2e_steps, "pinned": True}
+
+    batched = None
+    if not args.no_batched and rank == 0:
+        batched = batched_vs_plain(torch, opf, synth, stream, dev)
+
+    cpu = None
+    if not args.no_cpu and rank == 0:
+        rate, k, el = cpu_oracle_rate(g, seconds=10.0)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{k} full 10k-bus evaluations (obj, grad, cons, jac, hess) in {el:.1f} s, "
+                         "single-threaded C oracle"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "l2": f"rotating {R} buffer sets incl. network copies "
+                       f"(~{R * (set_bytes + 3_000_000) / 1e6:.0f} MB > 2x L2)",
+                       "launch": best, "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": roofline,
+            "eval_roofline": {"algorithmic_bytes": ev_bytes, "us": ms_per_step * 1000.0,
+                              "achieved_gbs": ev_bytes / (ms_per_step * 1e-3) / 1e9,
+                              "frac": ev_bytes / (ms_per_step * 1e-3) / 1e9 / hbm},
+            "jac_hess": {"us": jh_us, "evals_per_s": 1e6 / jh_us, "algorithmic_bytes": jac_hess_bytes(g, nnzh),
+                         "frac": jac_hess_bytes(g, nnzh) / (jh_us * 1e-6) / 1e9 / hbm},
+            "phase_us": {"branch": br_us, "bus": bus_us, "autotune_eval": tuned_us},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * K, "clocks": clocks,
+            "batched": batched,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def batched_vs_plain(torch, opf, synth, stream, dev):
+    """One batched graph launch vs a graph of per-period / per-instance
+    single-model calls producing the same outputs."""
+    out = {}
+    f64 = torch.float64
+
+    def graph_us(fn, reps=20):
+        gr = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(stream):
+            fn()
+            torch.cuda.synchronize()
+            with torch.cuda.graph(gr, stream=stream):
+                fn()
+        gr.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for _ in range(reps):
+                gr.replay()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        return 1000.0 * e0.elapsed_time(e1) / reps
+
+    def bufs(M):
+        return [torch.empty(k, dtype=f64, device=dev) for k in (1, M.n, M.m, M.nnzj, M.nnzh)]
+
+    rng = np.random.default_rng(7)
+    # multi-period: 2,000 buses x 96 periods
+    mp = synth.mp2k()
+    B = opf.Model(mp)
+    xb = torch.tensor(synth.random_point(mp, rng), device=dev)
+    lb = torch.tensor(rng.standard_normal(B.m), device=dev)
+    ob = bufs(B)
+    tb = graph_us(lambda: B.eval_all(xb, lb, 1.0, *ob, stream=stream))
+    grids = [mp.copy(load_pd=mp.load_pd[t:t + 1], load_qd=mp.load_qd[t:t + 1], ramp_ratio=0.0)
+             for t in range(mp.nperiod)]
+    singles = [opf.Model(gt) for gt in grids]
+    xs_ = [torch.tensor(synth.random_point(gt, rng), device=dev) for gt in grids]
+    ls_ = [torch.tensor(rng.standard_normal(s.m), device=dev) for s in singles]
+    os_ = [bufs(s) for s in singles]
+
+    def plain_mp():
+        for s, x, l, o in zip(singles, xs_, ls_, os_):
+            s.eval_all(x, l, 1.0, *o, stream=stream)
+
+    tp = graph_us(plain_mp)
+    out["mp2k_96"] = {"batched_us": tb, "plain_loop_us": tp, "speedup": tp / tb,
+                      "batched_evals_per_s": 1e6 / tb, "period_evals_per_s": 96e6 / tb}
+    del B, singles, os_
+    # N-1: 1,000 buses, base + 500 contingencies
+    insts = synth.sc1k()
+    B = opf.Model(insts, link_ratio=0.2)
+    xb = torch.tensor(np.concatenate([synth.random_point(s, rng) for s in insts]), device=dev)
+    lb = torch.tensor(rng.standard_normal(B.m), device=dev)
+    ob = bufs(B)
+    tb = graph_us(lambda: B.eval_all(xb, lb, 1.0, *ob, stream=stream))
+    singles = [opf.Model(s) for s in insts]
+    xs_ = [torch.tensor(synth.random_point(s, rng), device=dev) for s in insts]
+    ls_ = [torch.tensor(rng.standard_normal(s.m), device=dev) for s in singles]
+    os_ = [bufs(s) for s in singles]
+
+    def plain_sc():
+        for s, x, l, o in zip(singles, xs_, ls_, os_):
+            s.eval_all(x, l, 1.0, *o, stream=stream)
+
+    tp = graph_us(plain_sc, reps=5)
+    out["sc1k_501"] = {"batched_us": tb, "plain_loop_us": tp, "speedup": tp / tb,
+                       "instance_evals_per_s": 501e6 / tb}
+    return out
+
+
+if __name__ == "__main__":
+    main()

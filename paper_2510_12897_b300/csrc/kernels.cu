@@ -17,6 +17,16 @@
 //                linking rows. The objective is reduced in a fixed order by the
 //                last block to finish.
 //
+// Both kernels are launched with programmatic dependent launch: each block
+// first loads the static network data of its first item (which no kernel
+// writes), then waits for the previous kernel in the stream to complete
+// (cudaGridDependencySynchronize), then reads x, lambda and the scratch. The
+// static prologue and the launch therefore overlap the previous kernel.
+//
+// FP64 is the scarce resource on this GPU (about 2 FMA per clock per SM), so
+// sign flips and selects are done on the integer pipe and every product
+// shared between rows is computed once.
+//
 // Flow arithmetic (pi-model, real expansion): with d = va_f - va_t, the
 // from-end power is S_fr = |V_f|^2 conj(Yff) + vm_f vm_t e^{jd} conj(Yft), so
 //   P_fr =  Gff vm_f^2 + vm_f vm_t A_ft,   A_ft = Gft cos d + Bft sin d
@@ -25,9 +35,14 @@
 //   P_to =  Gtt vm_t^2 + vm_f vm_t A_tf,   A_tf = Gtf cos d - Btf sin d
 //   Q_to = -Btt vm_t^2 + vm_f vm_t B_tf,   B_tf = -Gtf sin d - Btf cos d.
 // dA_ft/dd = -B_ft, dB_ft/dd = A_ft, dA_tf/dd = B_tf, dB_tf/dd = -A_tf, and
-// every second derivative is a combination of these four and the constants.
-#include <cstdio>
-
+// every second derivative is a combination of these four and the constants:
+// with multipliers m1..m4 of the rows p_fr - P_fr, q_fr - Q_fr, p_to - P_to,
+// q_to - Q_to, U = m1 A_ft + m2 B_ft + m3 A_tf + m4 B_tf and V = dU/dd, the
+// Lagrangian L = sum m_r (own_r - F_r) has
+//   d2L/dva_f2 = d2L/dva_t2 = vm_f vm_t U = -d2L/dva_f dva_t,
+//   d2L/dvm_f dvm_t = -U,  d2L/dvm_f dva_f = -vm_t V = -d2L/dvm_f dva_t,
+//   d2L/dvm_t dva_t = vm_f V = -d2L/dvm_t dva_f,
+//   d2L/dvm_f2 = -2 (m1 Gff - m2 Bff),  d2L/dvm_t2 = -2 (m3 Gtt - m4 Btt).
 #include "model.h"
 
 namespace opf {
@@ -69,6 +84,18 @@ __device__ __forceinline__ void split(int loc, int count, int T, int &t, int &e)
     }
 }
 
+// -v on the integer pipe
+__device__ __forceinline__ double neg(double v)
+{
+    return __longlong_as_double(__double_as_longlong(v) ^ (long long)0x8000000000000000ULL);
+}
+
+// v or -v on the integer pipe
+__device__ __forceinline__ double flip(double v, bool f)
+{
+    return __longlong_as_double(__double_as_longlong(v) ^ (f ? (long long)0x8000000000000000ULL : 0LL));
+}
+
 // five Jacobian entries of a flow row, columns ascending:
 // (va_lo, va_hi, vm_lo, vm_hi, own) where lo/hi order the two end buses
 __device__ __forceinline__ void put5(double *J, bool f_lo, double vaf, double vat, double vmf,
@@ -81,285 +108,349 @@ __device__ __forceinline__ void put5(double *J, bool f_lo, double vaf, double va
     J[4] = 1.0;
 }
 
+// static (never written) data of one branch item
+struct BrStatic {
+    int4 br;  // f, t, slot of the from-arc, slot of the to-arc
+    double2 yff, yft, ytf, ytt;
+    double r2;
+};
+
+__device__ __forceinline__ BrStatic load_br(const DevArrays &d, int kb, bool need_r2)
+{
+    BrStatic s;
+    s.br = __ldg(d.br + kb);
+    s.yff = __ldg(d.y_ff + kb);
+    s.yft = __ldg(d.y_ft + kb);
+    s.ytf = __ldg(d.y_tf + kb);
+    s.ytt = __ldg(d.y_tt + kb);
+    s.r2 = need_r2 ? __ldg(d.rate2 + kb) : 0.0;
+    return s;
+}
+
 template <bool CONS, bool JAC, bool HESS, bool GRAD>
 __global__ void branch_kernel(const KParams P)
 {
+    cudaTriggerProgrammaticLaunchCompletion();
     const DevArrays &d = P.d;
     const double *__restrict__ x = P.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < P.nbr_items; it += stride) {
-        const int s = P.ninst == 1 ? 0 : find_inst(d.br_items, P.ninst, it);
+    int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+
+    auto locate = [&](int64_t item, int &s, int &t, int &k) {
+        s = P.ninst == 1 ? 0 : find_inst(d.br_items, P.ninst, item);
         const InstDev *I = d.inst + s;
+        split((int)(item - __ldg(d.br_items + s)), __ldg(&I->nl), __ldg(&I->T), t, k);
+    };
+
+    int s = 0, t = 0, k = 0;
+    BrStatic st{};
+    if (it < P.nbr_items) {
+        locate(it, s, t, k);
+        st = load_br(d, __ldg(&d.inst[s].br0) + k, CONS);
+    }
+    cudaGridDependencySynchronize();
+
+    for (; it < P.nbr_items; it += stride) {
+        const BrStatic cur = st;
+        const int cs = s, ct = t, ck = k;
+        if (it + stride < P.nbr_items) {  // prefetch the next item's static data
+            locate(it + stride, s, t, k);
+            st = load_br(d, __ldg(&d.inst[s].br0) + k, CONS);
+        }
+        const InstDev *I = d.inst + cs;
         const int nl = __ldg(&I->nl), nb = __ldg(&I->nb), ng = __ldg(&I->ng), T = __ldg(&I->T);
-        int t, k;
-        split((int)(it - __ldg(d.br_items + s)), nl, T, t, k);
         const int64_t nbT = (int64_t)nb * T, ngT = (int64_t)ng * T, nlT = (int64_t)nl * T;
         const int64_t na = 2 * (int64_t)nl;
         const int64_t x0 = __ldg(&I->x0), c0 = __ldg(&I->c0);
-        const int64_t rk = k + (int64_t)nl * t;  // element index inside each branch group
-        const int kb = __ldg(&I->br0) + k;
+        const int64_t rk = ck + (int64_t)nl * ct;  // element index inside each branch group
+        const int f = cur.br.x, b = cur.br.y;
 
-        const int2 ft = __ldg(d.br_ft + kb);
-        const int64_t xva = x0 + (int64_t)nb * t, xvm = xva + nbT;
-        const int64_t xp = x0 + 2 * nbT + 2 * ngT + na * t, xq = xp + na * T;
-        const double vaf = __ldg(x + xva + ft.x), vat = __ldg(x + xva + ft.y);
-        const double vmf = __ldg(x + xvm + ft.x), vmt = __ldg(x + xvm + ft.y);
-        const double2 Yff = __ldg(d.y_ff + kb), Yft = __ldg(d.y_ft + kb);
-        const double2 Ytf = __ldg(d.y_tf + kb), Ytt = __ldg(d.y_tt + kb);
-
-        double sn, cs;
-        sincos(vaf - vat, &sn, &cs);
-        const double vft = vmf * vmt;
-        const double Aft = fma(Yft.x, cs, Yft.y * sn);
-        const double Bft = fma(Yft.x, sn, -Yft.y * cs);
-        const double Atf = fma(Ytf.x, cs, -Ytf.y * sn);
-        const double Btf = -fma(Ytf.x, sn, Ytf.y * cs);
-
+        const int64_t xva = x0 + (int64_t)nb * ct, xvm = xva + nbT;
+        const int64_t xp = x0 + 2 * nbT + 2 * ngT + na * ct, xq = xp + na * T;
+        const double vaf = __ldg(x + xva + f), vat = __ldg(x + xva + b);
+        const double vmf = __ldg(x + xvm + f), vmt = __ldg(x + xvm + b);
         double pf = 0, qf = 0, pt = 0, qt = 0;
         if (CONS || JAC || HESS) {
-            pf = __ldg(x + xp + k);
-            pt = __ldg(x + xp + nl + k);
-            qf = __ldg(x + xq + k);
-            qt = __ldg(x + xq + nl + k);
+            pf = __ldg(x + xp + ck);
+            pt = __ldg(x + xp + nl + ck);
+            qf = __ldg(x + xq + ck);
+            qt = __ldg(x + xq + nl + ck);
         }
+        double m1 = 0, m2 = 0, m3 = 0, m4 = 0, lf = 0, lt = 0;
+        if (HESS) {
+            const double *L = P.lam + c0 + T + rk;
+            m1 = __ldg(L);
+            m2 = __ldg(L + nlT);
+            m3 = __ldg(L + 2 * nlT);
+            m4 = __ldg(L + 3 * nlT);
+            lf = __ldg(L + 5 * nlT + 2 * nbT);
+            lt = __ldg(L + 6 * nlT + 2 * nbT);
+        }
+        const double2 Yff = cur.yff, Yft = cur.yft, Ytf = cur.ytf, Ytt = cur.ytt;
+
+        const double dlt = vaf - vat;
+        double sn, cs_;
+        sincos(dlt, &sn, &cs_);
+        const double vft = vmf * vmt;
+        const double Aft = fma(Yft.x, cs_, Yft.y * sn);
+        const double Bft = fma(Yft.x, sn, neg(Yft.y * cs_));
+        const double Atf = fma(Ytf.x, cs_, neg(Ytf.y * sn));
+        const double Btf = neg(fma(Ytf.x, sn, Ytf.y * cs_));
+
         if (CONS) {
             const double vf2 = vmf * vmf, vt2 = vmt * vmt;
             double *c = P.c + c0 + T + rk;
             c[0] = pf - fma(Yff.x, vf2, vft * Aft);
-            c[nlT] = qf - fma(-Yff.y, vf2, vft * Bft);
+            c[nlT] = qf - fma(neg(Yff.y), vf2, vft * Bft);
             c[2 * nlT] = pt - fma(Ytt.x, vt2, vft * Atf);
-            c[3 * nlT] = qt - fma(-Ytt.y, vt2, vft * Btf);
-            c[4 * nlT] = vaf - vat;
-            const double r2 = __ldg(d.rate2 + kb);
-            c[5 * nlT + 2 * nbT] = fma(pf, pf, qf * qf) - r2;
-            c[6 * nlT + 2 * nbT] = fma(pt, pt, qt * qt) - r2;
+            c[3 * nlT] = qt - fma(neg(Ytt.y), vt2, vft * Btf);
+            c[4 * nlT] = dlt;
+            c[5 * nlT + 2 * nbT] = fma(pf, pf, qf * qf) - cur.r2;
+            c[6 * nlT + 2 * nbT] = fma(pt, pt, qt * qt) - cur.r2;
         }
         if (JAC) {
             const int64_t j0 = __ldg(&I->j0), jP = __ldg(&I->jP);
-            const bool f_lo = ft.x < ft.y;
+            const bool f_lo = f < b;
+            const double v2f = vmf + vmf, v2t = vmt + vmt;
+            const double uB = vft * Bft, uA = vft * Aft, wB = vft * Btf, wA = vft * Atf;
             double *J = P.jac + j0 + T + 5 * rk;
             // row p_fr - P_fr
-            put5(J, f_lo, vft * Bft, -vft * Bft, -fma(2.0 * Yff.x, vmf, vmt * Aft), -vmf * Aft);
+            put5(J, f_lo, uB, neg(uB), neg(fma(Yff.x, v2f, vmt * Aft)), neg(vmf * Aft));
             // row q_fr - Q_fr
-            put5(J + 5 * nlT, f_lo, -vft * Aft, vft * Aft, fma(2.0 * Yff.y, vmf, -vmt * Bft), -vmf * Bft);
+            put5(J + 5 * nlT, f_lo, neg(uA), uA, fma(Yff.y, v2f, neg(vmt * Bft)), neg(vmf * Bft));
             // row p_to - P_to
-            put5(J + 10 * nlT, f_lo, -vft * Btf, vft * Btf, -vmt * Atf, -fma(2.0 * Ytt.x, vmt, vmf * Atf));
+            put5(J + 10 * nlT, f_lo, neg(wB), wB, neg(vmt * Atf), neg(fma(Ytt.x, v2t, vmf * Atf)));
             // row q_to - Q_to
-            put5(J + 15 * nlT, f_lo, vft * Atf, -vft * Atf, -vmt * Btf, fma(2.0 * Ytt.y, vmt, -vmf * Btf));
+            put5(J + 15 * nlT, f_lo, wA, neg(wA), neg(vmt * Btf), fma(Ytt.y, v2t, neg(vmf * Btf)));
             double *Ja = P.jac + j0 + T + 20 * nlT + 2 * rk;  // angle row va_f - va_t
-            Ja[0] = f_lo ? 1.0 : -1.0;
-            Ja[1] = f_lo ? -1.0 : 1.0;
+            Ja[0] = flip(1.0, !f_lo);
+            Ja[1] = flip(1.0, f_lo);
             double *Jt = P.jac + j0 + T + 22 * nlT + 2 * jP * T + 2 * rk;  // thermal rows
-            Jt[0] = 2.0 * pf;
-            Jt[1] = 2.0 * qf;
-            Jt[2 * nlT] = 2.0 * pt;
-            Jt[2 * nlT + 1] = 2.0 * qt;
+            Jt[0] = pf + pf;
+            Jt[1] = qf + qf;
+            Jt[2 * nlT] = pt + pt;
+            Jt[2 * nlT + 1] = qt + qt;
         }
         if (HESS || CONS) {
-            const int2 pos = __ldg(d.br_pos + kb);
-            ArcScratch *S = d.arcs + __ldg(&I->scr0) + na * t;
+            ArcScratch *S = d.arcs + __ldg(&I->scr0) + na * ct;
+            double2 *sf = reinterpret_cast<double2 *>(S + cur.br.z);
+            double2 *sto = reinterpret_cast<double2 *>(S + cur.br.w);
+            sf[0] = make_double2(pf, qf);
+            sto[0] = make_double2(pt, qt);
             if (HESS) {
-                const double *L = P.lam + c0 + T + rk;
-                const double m1 = __ldg(L), m2 = __ldg(L + nlT), m3 = __ldg(L + 2 * nlT),
-                             m4 = __ldg(L + 3 * nlT);
-                const double lf = __ldg(L + 5 * nlT + 2 * nbT), lt = __ldg(L + 6 * nlT + 2 * nbT);
-                // U = sum_r mu_r val_r(d), V = dU/dd, W = weighted vm^2 coefficients
                 const double U = fma(m1, Aft, fma(m2, Bft, fma(m3, Atf, m4 * Btf)));
-                const double V = fma(-m1, Bft, fma(m2, Aft, fma(m3, Btf, -m4 * Atf)));
-                const double Wf = fma(m1, Yff.x, -m2 * Yff.y);
-                const double Wt = fma(m3, Ytt.x, -m4 * Ytt.y);
+                const double V = fma(m2, Aft, fma(m3, Btf, fma(neg(m1), Bft, neg(m4 * Atf))));
+                const double Wf = fma(m1, Yff.x, neg(m2 * Yff.y));
+                const double Wt = fma(m3, Ytt.x, neg(m4 * Ytt.y));
                 const double vU = vft * U;
-                double2 *sf = reinterpret_cast<double2 *>(S + pos.x);
-                double2 *st = reinterpret_cast<double2 *>(S + pos.y);
-                sf[0] = make_double2(pf, qf);
-                sf[1] = make_double2(vU, -vmt * V);
-                sf[2] = make_double2(-2.0 * Wf, vmt * V);
-                sf[3] = make_double2(-vU, -U);
-                st[0] = make_double2(pt, qt);
-                st[1] = make_double2(vU, vmf * V);
-                st[2] = make_double2(-2.0 * Wt, -vmf * V);
-                st[3] = make_double2(-vU, -U);
+                sf[1] = make_double2(vU, neg(vmt * V));
+                sf[2] = make_double2(neg(Wf + Wf), neg(U));
+                sto[1] = make_double2(vU, vmf * V);
+                sto[2] = make_double2(neg(Wt + Wt), neg(U));
                 const int64_t hpq = __ldg(&I->h0) + (__ldg(&I->hva) + __ldg(&I->hvm)) * T + ngT;
-                double *Hp = P.hess + hpq + k + na * t;
-                Hp[0] = 2.0 * lf;         // (p_fr, p_fr)
-                Hp[nl] = 2.0 * lt;        // (p_to, p_to)
-                Hp[na * T] = 2.0 * lf;    // (q_fr, q_fr)
-                Hp[na * T + nl] = 2.0 * lt;
-            } else {
-                reinterpret_cast<double2 *>(S + pos.x)[0] = make_double2(pf, qf);
-                reinterpret_cast<double2 *>(S + pos.y)[0] = make_double2(pt, qt);
+                double *Hp = P.hess + hpq + ck + na * ct;
+                const double l2f = lf + lf, l2t = lt + lt;
+                Hp[0] = l2f;            // (p_fr, p_fr)
+                Hp[nl] = l2t;           // (p_to, p_to)
+                Hp[na * T] = l2f;       // (q_fr, q_fr)
+                Hp[na * T + nl] = l2t;  // (q_to, q_to)
             }
         }
         if (GRAD) {
-            P.grad[xp + k] = 0.0;
-            P.grad[xp + nl + k] = 0.0;
-            P.grad[xq + k] = 0.0;
-            P.grad[xq + nl + k] = 0.0;
+            P.grad[xp + ck] = 0.0;
+            P.grad[xp + nl + ck] = 0.0;
+            P.grad[xq + ck] = 0.0;
+            P.grad[xq + nl + ck] = 0.0;
         }
     }
 }
 
+struct BusStatic {
+    int4 a;  // first slot, end slot, first gen entry, end gen entry
+    int4 b;  // balance-row offset, va-row offset, vm-row offset, nd | nlt << 16
+    double2 gsbs;
+};
+
 template <bool CONS, bool JAC, bool HESS, bool GRAD, bool OBJ>
 __global__ void bus_kernel(const KParams P)
 {
+    cudaTriggerProgrammaticLaunchCompletion();
     const DevArrays &d = P.d;
     const double *__restrict__ x = P.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t total = P.nbus_items + P.ngen_items;
-    double obj_acc = 0.0;
-    for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < total; it += stride) {
-        if (it < P.nbus_items) {
-            const int s = P.ninst == 1 ? 0 : find_inst(d.bus_items, P.ninst, it);
+    int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+
+    auto locate = [&](int64_t item, int &s, int &t, int &e) {
+        if (item < P.nbus_items) {
+            s = P.ninst == 1 ? 0 : find_inst(d.bus_items, P.ninst, item);
             const InstDev *I = d.inst + s;
-            const int nl = __ldg(&I->nl), nb = __ldg(&I->nb), ng = __ldg(&I->ng), T = __ldg(&I->T);
-            int t, i;
-            split((int)(it - __ldg(d.bus_items + s)), nb, T, t, i);
-            const int64_t nbT = (int64_t)nb * T, ngT = (int64_t)ng * T, nlT = (int64_t)nl * T;
+            split((int)(item - __ldg(d.bus_items + s)), __ldg(&I->nb), __ldg(&I->T), t, e);
+        } else {
+            const int64_t gi = item - P.nbus_items;
+            s = P.ninst == 1 ? 0 : find_inst(d.gen_items, P.ninst, gi);
+            const InstDev *I = d.inst + s;
+            split((int)(gi - __ldg(d.gen_items + s)), __ldg(&I->ng), __ldg(&I->T), t, e);
+        }
+    };
+    auto load = [&](int64_t item, int s, int e) {
+        BusStatic b{};
+        if (item < P.nbus_items) {
+            const int ib = __ldg(&d.inst[s].bus0) + e;
+            b.a = __ldg(d.bus_a + ib);
+            b.b = __ldg(d.bus_b + ib);
+            b.gsbs = __ldg(d.gsbs + ib);
+        }
+        return b;
+    };
+
+    int s = 0, t = 0, e = 0;
+    BusStatic st{};
+    if (it < total) {
+        locate(it, s, t, e);
+        st = load(it, s, e);
+    }
+    cudaGridDependencySynchronize();
+
+    double obj_acc = 0.0;
+    for (; it < total; it += stride) {
+        const BusStatic cur = st;
+        const int cs = s, ct = t, ce = e;
+        if (it + stride < total) {
+            locate(it + stride, s, t, e);
+            st = load(it + stride, s, e);
+        }
+        const InstDev *I = d.inst + cs;
+        const int nl = __ldg(&I->nl), nb = __ldg(&I->nb), ng = __ldg(&I->ng), T = __ldg(&I->T);
+        const int64_t nbT = (int64_t)nb * T, ngT = (int64_t)ng * T, nlT = (int64_t)nl * T;
+        const int64_t x0 = __ldg(&I->x0), c0 = __ldg(&I->c0);
+        if (it < P.nbus_items) {
+            const int i = ce;
             const int64_t na = 2 * (int64_t)nl;
-            const int64_t x0 = __ldg(&I->x0), c0 = __ldg(&I->c0);
-            const int64_t xva = x0 + (int64_t)nb * t, xvm = xva + nbT;
-            const int ib = __ldg(&I->bus0) + i, bp = __ldg(&I->bptr0) + i;
+            const int64_t xva = x0 + (int64_t)nb * ct, xvm = xva + nbT;
             const double vm = __ldg(x + xvm + i);
-            const double2 gb = __ldg(d.gsbs + ib);
-            const int a0 = __ldg(d.arc_ptr + bp), a1 = __ldg(d.arc_ptr + bp + 1);
-            const ArcScratch *S = d.arcs + __ldg(&I->scr0) + na * t;
+            const double2 gb = cur.gsbs;
+            const int a0 = cur.a.x, a1 = cur.a.y, g0 = cur.a.z, g1 = cur.a.w;
+            const ArcScratch *S = d.arcs + __ldg(&I->scr0) + na * ct;
             if (GRAD) {
                 P.grad[xva + i] = 0.0;
                 P.grad[xvm + i] = 0.0;
             }
             if (i == __ldg(&I->ref)) {
                 if (CONS)
-                    P.c[c0 + t] = __ldg(x + xva + i);
+                    P.c[c0 + ct] = __ldg(x + xva + i);
                 if (JAC)
-                    P.jac[__ldg(&I->j0) + t] = 1.0;
+                    P.jac[__ldg(&I->j0) + ct] = 1.0;
             }
-            const int g0 = __ldg(d.gen_ptr + bp), g1 = __ldg(d.gen_ptr + bp + 1);
             if (CONS) {
-                const int64_t pd = __ldg(&I->pd0) + (int64_t)nb * t + i;
-                double Pb = fma(gb.x, vm * vm, __ldg(d.Pd + pd));
-                double Qb = fma(-gb.y, vm * vm, __ldg(d.Qd + pd));
-                for (int a = a0; a < a1; a++) {
-                    const double2 pq = __ldg(reinterpret_cast<const double2 *>(S + a));
-                    Pb += pq.x;
-                    Qb += pq.y;
-                }
+                const int64_t pd = __ldg(&I->pd0) + (int64_t)nb * ct + i;
+                const double vm2 = vm * vm;
+                double Pb = fma(gb.x, vm2, __ldg(d.Pd + pd));
+                double Qb = fma(neg(gb.y), vm2, __ldg(d.Qd + pd));
                 const int gl0 = __ldg(&I->gl0);
-                const int64_t xpg = x0 + 2 * nbT + (int64_t)ng * t, xqg = xpg + ngT;
+                const int64_t xpg = x0 + 2 * nbT + (int64_t)ng * ct, xqg = xpg + ngT;
                 for (int gp = g0; gp < g1; gp++) {
                     const int g = __ldg(d.gen_list + gl0 + gp);
                     Pb -= __ldg(x + xpg + g);
                     Qb -= __ldg(x + xqg + g);
                 }
-                P.c[c0 + T + 5 * nlT + (int64_t)nb * t + i] = Pb;
-                P.c[c0 + T + 5 * nlT + nbT + (int64_t)nb * t + i] = Qb;
+#pragma unroll 4
+                for (int a = a0; a < a1; a++) {
+                    const double2 pq = __ldg(reinterpret_cast<const double2 *>(S + a));
+                    Pb += pq.x;
+                    Qb += pq.y;
+                }
+                P.c[c0 + T + 5 * nlT + (int64_t)nb * ct + i] = Pb;
+                P.c[c0 + T + 5 * nlT + nbT + (int64_t)nb * ct + i] = Qb;
             }
             if (JAC) {
                 const int64_t jP = __ldg(&I->jP);
-                double *JP = P.jac + __ldg(&I->j0) + T + 22 * nlT + jP * t + __ldg(d.jpos + ib);
+                double *JP = P.jac + __ldg(&I->j0) + T + 22 * nlT + jP * ct + cur.b.x;
                 double *JQ = JP + jP * T;
-                JP[0] = 2.0 * gb.x * vm;
-                JQ[0] = -2.0 * gb.y * vm;
-                int e = 1;
-                for (int gp = g0; gp < g1; gp++, e++) {
-                    JP[e] = -1.0;
-                    JQ[e] = -1.0;
+                const double v2 = vm + vm;
+                JP[0] = gb.x * v2;
+                JQ[0] = neg(gb.y * v2);
+                int q = 1;
+                for (int gp = g0; gp < g1; gp++, q++) {
+                    JP[q] = -1.0;
+                    JQ[q] = -1.0;
                 }
-                for (int a = a0; a < a1; a++, e++) {
-                    JP[e] = 1.0;
-                    JQ[e] = 1.0;
+                for (int a = a0; a < a1; a++, q++) {
+                    JP[q] = 1.0;
+                    JQ[q] = 1.0;
                 }
             }
             if (HESS) {
-                const double lP = __ldg(P.lam + c0 + T + 5 * nlT + (int64_t)nb * t + i);
-                const double lQ = __ldg(P.lam + c0 + T + 5 * nlT + nbT + (int64_t)nb * t + i);
-                double daa = 0.0, dma = 0.0, dmm = fma(2.0 * gb.x, lP, -2.0 * gb.y * lQ);
-                for (int a = a0; a < a1; a++) {
-                    const double2 v1 = __ldg(reinterpret_cast<const double2 *>(S + a) + 1);
-                    const double2 v2 = __ldg(reinterpret_cast<const double2 *>(S + a) + 2);
-                    daa += v1.x;
-                    dma += v1.y;
-                    dmm += v2.x;
-                }
+                const int64_t lb = c0 + T + 5 * nlT + (int64_t)nb * ct + i;
+                const double lP = __ldg(P.lam + lb), lQ = __ldg(P.lam + lb + nbT);
                 const int64_t h0 = __ldg(&I->h0), hva = __ldg(&I->hva), hvm = __ldg(&I->hvm);
-                double *Hvm = P.hess + h0 + hva * T + hvm * t + __ldg(d.hvm_pos + ib);
+                double *Hvm = P.hess + h0 + hva * T + hvm * ct + cur.b.z;
+                double dmm = fma(gb.x, lP, neg(gb.y * lQ));
+                dmm = dmm + dmm;  // 2 gs lambda_P - 2 bs lambda_Q
                 if (a1 > a0) {
-                    // far bus of each of this instance's slots (2 nl per instance)
-                    const int32_t *far = d.arc_nbr + 2 * (int64_t)__ldg(&I->br0);
-                    double *Hva = P.hess + h0 + hva * t + __ldg(d.hva_pos + ib);
-                    // row va_i: (va_i, va_j) for far buses j < i, then (va_i, va_i)
-                    int e = 0, a = a0;
-                    while (a < a1) {
-                        const int j = __ldg(far + a);
-                        if (j > i)
-                            break;
-                        double acc = 0.0;
-                        for (; a < a1 && __ldg(far + a) == j; a++)
-                            acc += __ldg(&S[a].x_aa);
-                        Hva[e++] = acc;
-                    }
-                    Hva[e] = daa;
-                    // row vm_i: (vm_i, va_j) for j in far buses and i, ascending
-                    e = 0;
-                    a = a0;
-                    bool self = false;
-                    while (a < a1) {
-                        const int j = __ldg(far + a);
-                        if (!self && j > i) {
-                            Hvm[e++] = dma;
-                            self = true;
+                    double *Hva = P.hess + h0 + hva * ct + cur.b.y;
+                    const int nd = cur.b.w & 0xffff, nlt = cur.b.w >> 16;
+                    const uint8_t *code = d.slot_code + __ldg(&I->slot0);
+                    // one pass over the slots, sorted by far bus: groups of
+                    // parallel arcs are summed, then written in column order
+                    double daa = 0.0, dma = 0.0, acc_ma = 0.0, acc_aa = 0.0, acc_mm = 0.0;
+                    bool first = true;
+                    int grp = 0;
+                    for (int a = a0; a < a1; a++) {
+                        const unsigned cd = __ldg(code + a);
+                        const double2 v1 = __ldg(reinterpret_cast<const double2 *>(S + a) + 1);
+                        const double2 v2 = __ldg(reinterpret_cast<const double2 *>(S + a) + 2);
+                        daa += v1.x;
+                        dma += v1.y;
+                        dmm += v2.x;
+                        if (first) {
+                            acc_ma = neg(v1.y);
+                            acc_aa = neg(v1.x);
+                            acc_mm = v2.y;
+                        } else {
+                            acc_ma -= v1.y;
+                            acc_aa -= v1.x;
+                            acc_mm += v2.y;
                         }
-                        double acc = 0.0;
-                        for (; a < a1 && __ldg(far + a) == j; a++)
-                            acc += __ldg(&S[a].x_ma);
-                        Hvm[e++] = acc;
+                        first = (cd & SLOT_LAST) != 0;
+                        if (first) {
+                            Hvm[grp < nlt ? grp : grp + 1] = acc_ma;  // (vm_i, va_j)
+                            if (cd & SLOT_LOWER) {
+                                Hva[grp] = acc_aa;               // (va_i, va_j), j < i
+                                Hvm[nd + 1 + grp] = acc_mm;      // (vm_i, vm_j), j < i
+                            }
+                            grp++;
+                        }
                     }
-                    if (!self)
-                        Hvm[e++] = dma;
-                    // then (vm_i, vm_j) for j < i, then (vm_i, vm_i)
-                    a = a0;
-                    while (a < a1) {
-                        const int j = __ldg(far + a);
-                        if (j > i)
-                            break;
-                        double acc = 0.0;
-                        for (; a < a1 && __ldg(far + a) == j; a++)
-                            acc += __ldg(&S[a].x_mm);
-                        Hvm[e++] = acc;
-                    }
-                    Hvm[e] = dmm;
+                    Hva[nlt] = daa;
+                    Hvm[nlt] = dma;
+                    Hvm[nd + 1 + nlt] = dmm;
                 } else {
                     Hvm[0] = dmm;
                 }
             }
         } else {
-            const int64_t gi = it - P.nbus_items;
-            const int s = P.ninst == 1 ? 0 : find_inst(d.gen_items, P.ninst, gi);
-            const InstDev *I = d.inst + s;
-            const int nl = __ldg(&I->nl), nb = __ldg(&I->nb), ng = __ldg(&I->ng), T = __ldg(&I->T);
-            int t, g;
-            split((int)(gi - __ldg(d.gen_items + s)), ng, T, t, g);
-            const int64_t nbT = (int64_t)nb * T, ngT = (int64_t)ng * T, nlT = (int64_t)nl * T;
-            const int64_t x0 = __ldg(&I->x0);
-            const int64_t xpg = x0 + 2 * nbT + (int64_t)ng * t + g;
+            const int g = ce;
+            const int64_t xpg = x0 + 2 * nbT + (int64_t)ng * ct + g;
             const int gg = __ldg(&I->gen0) + g;
             const double pg = __ldg(x + xpg);
             const double c2 = __ldg(d.c2 + gg), c1 = __ldg(d.c1 + gg);
             if (OBJ)
                 obj_acc += fma(fma(c2, pg, c1), pg, __ldg(d.c0 + gg));
             if (GRAD) {
-                P.grad[xpg] = fma(2.0 * c2, pg, c1);
+                P.grad[xpg] = fma(c2 + c2, pg, c1);
                 P.grad[xpg + ngT] = 0.0;
             }
             if (HESS) {
                 const int64_t hpg = __ldg(&I->h0) + (__ldg(&I->hva) + __ldg(&I->hvm)) * T;
-                P.hess[hpg + (int64_t)ng * t + g] = P.sigma * 2.0 * c2;
+                P.hess[hpg + (int64_t)ng * ct + g] = P.sigma * (c2 + c2);
             }
-            if ((CONS || JAC) && t >= 1 && __ldg(&I->ramp)) {
-                const int64_t e = g + (int64_t)ng * (t - 1);
+            if ((CONS || JAC) && ct >= 1 && __ldg(&I->ramp)) {
+                const int64_t q = g + (int64_t)ng * (ct - 1);
                 if (CONS)
-                    P.c[__ldg(&I->c0) + T + 7 * nlT + 2 * nbT + e] = pg - __ldg(x + xpg - ng);
+                    P.c[c0 + T + 7 * nlT + 2 * nbT + q] = pg - __ldg(x + xpg - ng);
                 if (JAC) {
-                    double *J = P.jac + __ldg(&I->j0) + T + 26 * nlT + 2 * __ldg(&I->jP) * T + 2 * e;
+                    double *J = P.jac + __ldg(&I->j0) + T + 26 * nlT + 2 * __ldg(&I->jP) * T + 2 * q;
                     J[0] = -1.0;
                     J[1] = 1.0;
                 }
@@ -422,8 +513,8 @@ __global__ void flat_kernel(const DevArrays d, int32_t ninst, int64_t nbr_items,
             int t, k;
             split((int)(it - d.br_items[s]), nl, T, t, k);
             const int kb = I->br0 + k;
-            const int2 ft = d.br_ft[kb];
-            const double2 bf = d.vbnd[I->bus0 + ft.x], bt = d.vbnd[I->bus0 + ft.y];
+            const int4 br = d.br[kb];
+            const double2 bf = d.vbnd[I->bus0 + br.x], bt = d.vbnd[I->bus0 + br.y];
             const double vmf = fmin(fmax(1.0, bf.x), bf.y), vmt = fmin(fmax(1.0, bt.x), bt.y);
             const double2 Yff = d.y_ff[kb], Yft = d.y_ft[kb], Ytf = d.y_tf[kb], Ytt = d.y_tt[kb];
             const double vft = vmf * vmt;
@@ -469,41 +560,38 @@ int grid_for(int64_t items, int block, int ctas_per_sm, int num_sms, int cap)
     return (int)g;
 }
 
-template <bool C, bool J, bool H, bool G>
-void launch_branch(const KParams &P, int grid, int block, cudaStream_t s)
+// launch with programmatic stream serialization (see the file comment)
+template <class K>
+cudaError_t launch_pdl(K kernel, int grid, int block, cudaStream_t s, const KParams &P)
 {
-    branch_kernel<C, J, H, G><<<grid, block, 0, s>>>(P);
-}
-
-template <bool C, bool J, bool H, bool G, bool O>
-void launch_bus(const KParams &P, int grid, int block, cudaStream_t s)
-{
-    bus_kernel<C, J, H, G, O><<<grid, block, 0, s>>>(P);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, P);
 }
 
 template <bool C, bool J, bool H>
-void dispatch(const KParams &P, bool grad, bool obj, bool run_branch, bool run_bus, int gb, int bb,
-              int gu, int bu, cudaStream_t s)
+cudaError_t dispatch(const KParams &P, bool grad, bool obj, bool run_branch, bool run_bus, int gb,
+                     int bb, int gu, int bu, cudaStream_t s)
 {
-    if (run_branch) {
-        if (grad)
-            launch_branch<C, J, H, true>(P, gb, bb, s);
-        else
-            launch_branch<C, J, H, false>(P, gb, bb, s);
-    }
-    if (!run_bus)
-        return;
-    if (grad) {
-        if (obj)
-            launch_bus<C, J, H, true, true>(P, gu, bu, s);
-        else
-            launch_bus<C, J, H, true, false>(P, gu, bu, s);
-    } else {
-        if (obj)
-            launch_bus<C, J, H, false, true>(P, gu, bu, s);
-        else
-            launch_bus<C, J, H, false, false>(P, gu, bu, s);
-    }
+    cudaError_t e = cudaSuccess;
+    if (run_branch)
+        e = grad ? launch_pdl(branch_kernel<C, J, H, true>, gb, bb, s, P)
+                 : launch_pdl(branch_kernel<C, J, H, false>, gb, bb, s, P);
+    if (e != cudaSuccess || !run_bus)
+        return e;
+    if (grad)
+        return obj ? launch_pdl(bus_kernel<C, J, H, true, true>, gu, bu, s, P)
+                   : launch_pdl(bus_kernel<C, J, H, true, false>, gu, bu, s, P);
+    return obj ? launch_pdl(bus_kernel<C, J, H, false, true>, gu, bu, s, P)
+               : launch_pdl(bus_kernel<C, J, H, false, false>, gu, bu, s, P);
 }
 
 }  // namespace
@@ -535,17 +623,19 @@ int launch_eval(Model &M, const EvalArgs &a, unsigned what, cudaStream_t s, int 
     const bool run_branch = (phases & 1) && (C || J || H || G) && M.nbr_items > 0;
     const bool run_bus = phases & 2;
     const int bb = L.branch_block, bu = L.bus_block;
+    cudaError_t e;
     switch ((C ? 1 : 0) | (J ? 2 : 0) | (H ? 4 : 0)) {
-    case 0: dispatch<false, false, false>(P, G, O, run_branch, run_bus, gb, bb, gu, bu, s); break;
-    case 1: dispatch<true, false, false>(P, G, O, run_branch, run_bus, gb, bb, gu, bu, s); break;
-    case 2: dispatch<false, true, false>(P, G, O, run_branch, run_bus, gb, bb, gu, bu, s); break;
-    case 3: dispatch<true, true, false>(P, G, O, run_branch, run_bus, gb, bb, gu, bu, s); break;
-    case 4: dispatch<false, false, true>(P, G, O, run_branch, run_bus, gb, bb, gu, bu, s); break;
-    case 5: dispatch<true, false, true>(P, G, O, run_branch, run_bus, gb, bb, gu, bu, s); break;
-    case 6: dispatch<false, true, true>(P, G, O, run_branch, run_bus, gb, bb, gu, bu, s); break;
-    default: dispatch<true, true, true>(P, G, O, run_branch, run_bus, gb, bb, gu, bu, s); break;
+    case 0: e = dispatch<false, false, false>(P, G, O, run_branch, run_bus, gb, bb, gu, bu, s); break;
+    case 1: e = dispatch<true, false, false>(P, G, O, run_branch, run_bus, gb, bb, gu, bu, s); break;
+    case 2: e = dispatch<false, true, false>(P, G, O, run_branch, run_bus, gb, bb, gu, bu, s); break;
+    case 3: e = dispatch<true, true, false>(P, G, O, run_branch, run_bus, gb, bb, gu, bu, s); break;
+    case 4: e = dispatch<false, false, true>(P, G, O, run_branch, run_bus, gb, bb, gu, bu, s); break;
+    case 5: e = dispatch<true, false, true>(P, G, O, run_branch, run_bus, gb, bb, gu, bu, s); break;
+    case 6: e = dispatch<false, true, true>(P, G, O, run_branch, run_bus, gb, bb, gu, bu, s); break;
+    default: e = dispatch<true, true, true>(P, G, O, run_branch, run_bus, gb, bb, gu, bu, s); break;
     }
-    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaGetLastError();
     if (e != cudaSuccess) {
         set_error("kernel launch failed: %s", cudaGetErrorString(e));
         return OPF_ECUDA;

@@ -13,18 +13,20 @@ namespace opf {
 // Callback selection of one fused evaluation.
 enum : unsigned { W_OBJ = 1u, W_GRAD = 2u, W_CONS = 4u, W_JAC = 8u, W_HESS = 16u };
 
-// Per-arc scratch written by the branch phase at the arc's position in its
-// bus's arc list and read back, in that order, by the bus phase.
+// Per-arc scratch written by the branch phase at the arc's slot in its bus's
+// arc list and read back, in that order, by the bus phase. i = the arc's bus,
+// j = its far bus; L = the Lagrangian restricted to the branch's flow rows.
 //   p, q    the arc's flow variables (balance sums)
-//   d_aa    d2L/dva_i^2     from this arc's flow rows (i = the arc's bus)
-//   d_ma    d2L/dvm_i dva_i
+//   d_aa    d2L/dva_i^2        (d2L/dva_i dva_j = -d_aa)
+//   d_ma    d2L/dvm_i dva_i    (d2L/dvm_i dva_j = -d_ma)
 //   d_mm    d2L/dvm_i^2
-//   x_ma    d2L/dvm_i dva_j (j = the far bus)
-//   x_aa    d2L/dva_i dva_j
 //   x_mm    d2L/dvm_i dvm_j
 struct __align__(16) ArcScratch {
-    double p, q, d_aa, d_ma, d_mm, x_ma, x_aa, x_mm;
+    double p, q, d_aa, d_ma, d_mm, x_mm;
 };
+
+// slot codes: the slot closes its far bus's group / the far bus is lower
+enum : uint8_t { SLOT_LAST = 1u, SLOT_LOWER = 2u };
 
 // One instance of a batch, as seen by the kernels. Offsets are absolute
 // positions in the caller's x / g / Jacobian / Hessian arrays and in the
@@ -35,10 +37,9 @@ struct InstDev {
     int32_t ramp;       // ramp rows present
     int32_t br0;        // first branch in the concatenated branch arrays
     int32_t bus0;       // first bus in the concatenated bus arrays
-    int32_t bptr0;      // first entry of this instance's bus CSR pointers (nb + 1 of them)
     int32_t gen0;       // first generator
     int32_t gl0;        // first entry of this instance's bus->generator list
-    int32_t pad0;
+    int32_t slot0;      // first slot code of this instance (2 nl per instance)
     int64_t x0, c0, j0, h0;
     int64_t scr0;       // first arc-scratch slot (2 nl T slots per instance)
     int64_t pd0;        // first entry of per-bus demand [T][nb]
@@ -50,19 +51,16 @@ struct InstDev {
 
 struct DevArrays {
     // branches (concatenated over instances)
-    int2 *br_ft = nullptr;        // local (f, t)
+    int4 *br = nullptr;           // local (f, t, slot of the from-arc, slot of the to-arc)
     double2 *y_ff = nullptr, *y_ft = nullptr, *y_tf = nullptr, *y_tt = nullptr;  // (G, B)
     double *rate2 = nullptr;      // rate_a^2
-    int2 *br_pos = nullptr;       // positions of (from arc, to arc) in their buses' arc lists
     // buses
+    int4 *bus_a = nullptr;        // (first slot, end slot, first gen entry, end gen entry)
+    int4 *bus_b = nullptr;        // (balance-row offset, va-row offset, vm-row offset,
+                                  //  distinct far buses | lower ones << 16) inside one period
     double2 *gsbs = nullptr;      // (gs, bs)
-    int32_t *arc_ptr = nullptr;   // CSR over bus-sorted arc slots, nb + 1 per instance
-    int32_t *arc_nbr = nullptr;   // far bus of each slot (local)
-    int32_t *gen_ptr = nullptr;   // CSR bus -> generators, nb + 1 per instance
+    uint8_t *slot_code = nullptr; // per slot: SLOT_LAST / SLOT_LOWER
     int32_t *gen_list = nullptr;  // local generator ids, ascending per bus
-    int32_t *jpos = nullptr;      // offset of bus i's balance row inside one period's group
-    int32_t *hva_pos = nullptr;   // offset of row va_i inside one period's va rows
-    int32_t *hvm_pos = nullptr;   // offset of row vm_i inside one period's vm rows
     double *Pd = nullptr, *Qd = nullptr;  // demand per bus and period
     // generators
     double *c2 = nullptr, *c1 = nullptr, *c0 = nullptr;

@@ -180,10 +180,11 @@ int build_model(const opf_network *nets, int32_t ninst, double link_ratio, bool 
     }
 
     // concatenated host arrays
-    std::vector<int2> br_ft, br_pos;
+    std::vector<int4> br, bus_a, bus_b;
     std::vector<double2> y_ff, y_ft, y_tf, y_tt, gsbs, pbnd, qbnd, vbnd;
     std::vector<double> rate2, Pd, Qd, c2, c1, c0;
-    std::vector<int32_t> arc_ptr, arc_nbr, gen_ptr, gen_list, jpos, hva_pos, hvm_pos;
+    std::vector<int32_t> gen_list;
+    std::vector<uint8_t> slot_code;
     std::vector<int64_t> br_items(1, 0), bus_items(1, 0), gen_items(1, 0);
 
     int64_t xo = 0, co = 0, jo = 0, ho = 0, so = 0, po = 0;
@@ -210,11 +211,11 @@ int build_model(const opf_network *nets, int32_t ninst, double link_ratio, bool 
         H.qmax.assign(n.gen_qmax, n.gen_qmax + ng);
 
         I.nb = nb; I.nl = nl; I.ng = ng; I.T = T; I.ref = n.ref_bus; I.ramp = H.ramp;
-        I.br0 = (int32_t)br_ft.size();
+        I.br0 = (int32_t)y_ff.size();
         I.bus0 = (int32_t)gsbs.size();
-        I.bptr0 = (int32_t)arc_ptr.size();
         I.gen0 = (int32_t)c2.size();
         I.gl0 = (int32_t)gen_list.size();
+        I.slot0 = (int32_t)slot_code.size();
 
         // ---- branches: pi-model admittances (G, B) of Yff, Yft, Ytf, Ytt
         for (int k = 0; k < nl; k++) {
@@ -234,7 +235,6 @@ int build_model(const opf_network *nets, int32_t ninst, double link_ratio, bool 
             y_tf.push_back(tf);
             y_tt.push_back(tt);
             rate2.push_back(n.br_rate_a[k] * n.br_rate_a[k]);
-            br_ft.push_back(make_int2(n.br_f[k], n.br_t[k]));
         }
 
         // ---- arcs sorted per bus by (far bus, arc id)
@@ -261,11 +261,7 @@ int build_model(const opf_network *nets, int32_t ninst, double link_ratio, bool 
             pos_of[a] = p;
         }
         for (int k = 0; k < nl; k++)
-            br_pos.push_back(make_int2(pos_of[k], pos_of[nl + k]));
-        for (int i = 0; i <= nb; i++)
-            arc_ptr.push_back(H.arc_ptr[i]);
-        for (int p = 0; p < na; p++)
-            arc_nbr.push_back(H.slot_nbr[p]);
+            br.push_back(make_int4(n.br_f[k], n.br_t[k], pos_of[k], pos_of[nl + k]));
 
         // ---- generators per bus (ascending id)
         std::vector<int32_t> gcnt(nb + 1, 0);
@@ -280,25 +276,31 @@ int build_model(const opf_network *nets, int32_t ninst, double link_ratio, bool 
             for (int g = 0; g < ng; g++)
                 H.gen_list[fill[n.gen_bus[g]]++] = g;
         }
-        for (int i = 0; i <= nb; i++)
-            gen_ptr.push_back(H.gen_ptr[i]);
         for (int g = 0; g < ng; g++)
             gen_list.push_back(H.gen_list[g]);
 
-        // ---- per-bus row offsets inside one period
+        // ---- per-bus row offsets inside one period, slot codes
         int64_t jsum = 0, hva = 0, hvm = 0;
         for (int i = 0; i < nb; i++) {
             int p0 = H.arc_ptr[i], p1 = H.arc_ptr[i + 1];
             int nd = 0, nlt = 0;
-            for (int p = p0; p < p1; p++)
-                if (p == p0 || H.slot_nbr[p] != H.slot_nbr[p - 1]) {
+            for (int p = p0; p < p1; p++) {
+                bool first = p == p0 || H.slot_nbr[p] != H.slot_nbr[p - 1];
+                bool last = p + 1 == p1 || H.slot_nbr[p + 1] != H.slot_nbr[p];
+                if (first) {
                     nd++;
                     if (H.slot_nbr[p] < i)
                         nlt++;
                 }
-            jpos.push_back((int32_t)jsum);
-            hva_pos.push_back((int32_t)hva);
-            hvm_pos.push_back((int32_t)hvm);
+                slot_code.push_back((uint8_t)((last ? SLOT_LAST : 0) | (H.slot_nbr[p] < i ? SLOT_LOWER : 0)));
+            }
+            if (nd > 0x7fff) {
+                set_error("instance %d: bus %d has more than 32767 distinct neighbours", s, i);
+                delete M;
+                return OPF_EINVAL;
+            }
+            bus_a.push_back(make_int4(p0, p1, H.gen_ptr[i], H.gen_ptr[i + 1]));
+            bus_b.push_back(make_int4((int32_t)jsum, (int32_t)hva, (int32_t)hvm, nd | (nlt << 16)));
             jsum += 1 + (H.gen_ptr[i + 1] - H.gen_ptr[i]) + (p1 - p0);
             if (p1 > p0) {
                 hva += nlt + 1;
@@ -383,12 +385,11 @@ int build_model(const opf_network *nets, int32_t ninst, double link_ratio, bool 
 #define UP(field, vec)                           \
     if (!rc)                                     \
         rc = upload(*M, &d.field, vec);
-    UP(br_ft, br_ft) UP(y_ff, y_ff) UP(y_ft, y_ft) UP(y_tf, y_tf) UP(y_tt, y_tt)
-    UP(rate2, rate2) UP(br_pos, br_pos) UP(gsbs, gsbs) UP(arc_ptr, arc_ptr) UP(arc_nbr, arc_nbr)
-    UP(gen_ptr, gen_ptr) UP(gen_list, gen_list) UP(jpos, jpos) UP(hva_pos, hva_pos)
-    UP(hvm_pos, hvm_pos) UP(Pd, Pd) UP(Qd, Qd) UP(c2, c2) UP(c1, c1) UP(c0, c0) UP(pbnd, pbnd)
-    UP(qbnd, qbnd) UP(vbnd, vbnd) UP(inst, M->inst) UP(br_items, br_items)
-    UP(bus_items, bus_items) UP(gen_items, gen_items)
+    UP(br, br) UP(y_ff, y_ff) UP(y_ft, y_ft) UP(y_tf, y_tf) UP(y_tt, y_tt) UP(rate2, rate2)
+    UP(bus_a, bus_a) UP(bus_b, bus_b) UP(gsbs, gsbs) UP(slot_code, slot_code) UP(gen_list, gen_list)
+    UP(Pd, Pd) UP(Qd, Qd) UP(c2, c2) UP(c1, c1) UP(c0, c0) UP(pbnd, pbnd) UP(qbnd, qbnd)
+    UP(vbnd, vbnd) UP(inst, M->inst) UP(br_items, br_items) UP(bus_items, bus_items)
+    UP(gen_items, gen_items)
 #undef UP
     if (!rc)
         rc = alloc(*M, &d.arcs, (size_t)M->narc_slots);
