@@ -178,6 +178,30 @@ int opf_eval_all_host(opf_model *model, const double *h_x, const double *h_lambd
                       double obj_weight, double *h_obj, double *h_grad, double *h_c,
                       double *h_jvals, double *h_hvals, void *stream);
 
+/* opf_eval_all for callers that cannot allocate device memory while they
+ * run (the paper has no counterpart: this is a deployment variant). Typical
+ * callers: a solver embedded in a process whose device memory is owned by
+ * another runtime (a fixed arena or a pool that must not grow), or a loop
+ * that must keep cudaMalloc / cudaFree, which can synchronise the device,
+ * out of its iterations. It evaluates exactly what opf_eval_all evaluates,
+ * with the same kernels and outputs, but its scratch (per-arc slots,
+ * per-block objective partials, a block counter) lives in one static device
+ * array of OPF_NOALLOC_SCRATCH_BYTES bytes that every device loading this
+ * library holds until the process exits; the call itself calls no
+ * allocator. Limits: models needing more than 174,074 arc slots (2 x
+ * branches x periods, summed over instances) are rejected with OPF_EINVAL
+ * and a message naming the sizes. The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress, with that device current)
+ * and caches it: make that first call before any stream capture. Every
+ * call, on every model, shares the one array and leaves its last contents
+ * there; the block counter is cleared at the start of each call. Calls whose
+ * executions overlap on the GPU (other streams, or concurrent host threads)
+ * race on the array: serialise them. */
+#define OPF_NOALLOC_SCRATCH_BYTES (8u << 20)
+int opf_eval_all_noalloc(opf_model *model, const double *d_x, const double *d_lambda,
+                         double obj_weight, double *d_obj, double *d_grad, double *d_c,
+                         double *d_jvals, double *d_hvals, void *stream);
+
 /* Flat start (reading of the usual OPF initial point): va = 0, vm = 1
  * clipped into [vmin, vmax], pg and qg at the midpoint of their bounds,
  * p and q equal to the branch flows at those voltages. Into d_x (n). */

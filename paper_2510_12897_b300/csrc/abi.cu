@@ -28,10 +28,6 @@ void bounds(const Model &M, double *xl, double *xu, double *gl, double *gu);
 
 using namespace opf;
 
-struct opf_model {
-    Model *M;
-};
-
 namespace {
 
 int check(const opf_model *m)

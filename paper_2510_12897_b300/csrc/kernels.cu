@@ -643,6 +643,57 @@ int launch_eval(Model &M, const EvalArgs &a, unsigned what, cudaStream_t s, int 
     return OPF_OK;
 }
 
+// The fused evaluation with caller-chosen scratch (arc slots, objective
+// partials, block counter) in place of the model's own; used by
+// opf_eval_all_noalloc. Same kernels and launch shape as launch_eval.
+int launch_eval_scratch(Model &M, const EvalArgs &a, unsigned what, cudaStream_t s,
+                        ArcScratch *arcs, double *obj_part, int max_part, unsigned int *ticket)
+{
+    KParams P;
+    P.d = M.d;
+    P.d.arcs = arcs;
+    P.d.obj_part = obj_part;
+    P.d.ticket = ticket;
+    P.ninst = M.ninst;
+    P.nbr_items = M.nbr_items;
+    P.nbus_items = M.nbus_items;
+    P.ngen_items = M.ngen_items;
+    P.x = a.x;
+    P.lam = a.lam;
+    P.sigma = a.sigma;
+    P.obj = a.obj;
+    P.grad = a.grad;
+    P.c = a.c;
+    P.jac = a.jac;
+    P.hess = a.hess;
+    const bool C = what & W_CONS, J = what & W_JAC, H = what & W_HESS;
+    const bool G = what & W_GRAD, O = what & W_OBJ;
+    const opf_launch &L = M.launch;
+    const int gb = grid_for(M.nbr_items, L.branch_block, L.branch_ctas_per_sm, M.num_sms, 0);
+    const int cap = max_part < M.max_part ? max_part : M.max_part;
+    const int gu = grid_for(M.nbus_items + M.ngen_items, L.bus_block, L.bus_ctas_per_sm, M.num_sms, cap);
+    const bool run_branch = (C || J || H || G) && M.nbr_items > 0;
+    const int bb = L.branch_block, bu = L.bus_block;
+    cudaError_t e;
+    switch ((C ? 1 : 0) | (J ? 2 : 0) | (H ? 4 : 0)) {
+    case 0: e = dispatch<false, false, false>(P, G, O, run_branch, true, gb, bb, gu, bu, s); break;
+    case 1: e = dispatch<true, false, false>(P, G, O, run_branch, true, gb, bb, gu, bu, s); break;
+    case 2: e = dispatch<false, true, false>(P, G, O, run_branch, true, gb, bb, gu, bu, s); break;
+    case 3: e = dispatch<true, true, false>(P, G, O, run_branch, true, gb, bb, gu, bu, s); break;
+    case 4: e = dispatch<false, false, true>(P, G, O, run_branch, true, gb, bb, gu, bu, s); break;
+    case 5: e = dispatch<true, false, true>(P, G, O, run_branch, true, gb, bb, gu, bu, s); break;
+    case 6: e = dispatch<false, true, true>(P, G, O, run_branch, true, gb, bb, gu, bu, s); break;
+    default: e = dispatch<true, true, true>(P, G, O, run_branch, true, gb, bb, gu, bu, s); break;
+    }
+    if (e == cudaSuccess)
+        e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error("kernel launch failed: %s", cudaGetErrorString(e));
+        return OPF_ECUDA;
+    }
+    return OPF_OK;
+}
+
 int launch_flat_start(Model &M, double *x, cudaStream_t s)
 {
     const int64_t total = M.nbr_items + M.nbus_items + M.ngen_items;

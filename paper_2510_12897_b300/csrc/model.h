@@ -127,3 +127,8 @@ int launch_flat_start(Model &M, double *x, cudaStream_t s);
 void set_error(const char *fmt, ...);
 
 }  // namespace opf
+
+// the opaque handle of the C ABI
+struct opf_model {
+    opf::Model *M;
+};

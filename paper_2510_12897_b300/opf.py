@@ -87,6 +87,7 @@ def lib():
         "opf_eval_all": [_vp, _vp, _vp, ctypes.c_double, _vp, _vp, _vp, _vp, _vp, _vp],
         "opf_eval_phases": [_vp, ctypes.c_int32, _vp, _vp, ctypes.c_double, _vp, _vp, _vp, _vp, _vp,
                             _vp],
+        "opf_eval_all_noalloc": [_vp, _vp, _vp, ctypes.c_double, _vp, _vp, _vp, _vp, _vp, _vp],
         "opf_eval_all_host": [_vp, _vp, _vp, ctypes.c_double, _vp, _vp, _vp, _vp, _vp, _vp],
         "opf_flat_start": [_vp, _vp, _vp],
         "opf_get_launch": [_vp, ctypes.POINTER(OpfLaunch)],
@@ -249,6 +250,15 @@ class Model:
                                   float(sigma), _ptr(obj, 1, "obj"), _ptr(grad, self.n, "grad"),
                                   _ptr(c, self.m, "c"), _ptr(jv, self.nnzj, "jvals"),
                                   _ptr(hv, self.nnzh, "hvals"), _stream(stream)))
+
+    def eval_all_noalloc(self, x, lam=None, sigma=1.0, obj=None, grad=None, c=None, jv=None,
+                         hv=None, stream=None):
+        """eval_all with the library's static scratch: no allocation in the
+        call (see opf_eval_all_noalloc in include/opf.h for the limits)."""
+        _check(lib().opf_eval_all_noalloc(self.h, _ptr(x, self.n, "x"), _ptr(lam, self.m, "lambda"),
+                                          float(sigma), _ptr(obj, 1, "obj"), _ptr(grad, self.n, "grad"),
+                                          _ptr(c, self.m, "c"), _ptr(jv, self.nnzj, "jvals"),
+                                          _ptr(hv, self.nnzh, "hvals"), _stream(stream)))
 
     def eval_phases(self, phases, x, lam=None, sigma=1.0, obj=None, grad=None, c=None, jv=None,
                     hv=None, stream=None):
