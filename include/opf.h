@@ -207,6 +207,14 @@ int opf_eval_all_noalloc(opf_model *model, const double *d_x, const double *d_la
  * p and q equal to the branch flows at those voltages. Into d_x (n). */
 int opf_flat_start(opf_model *model, double *d_x, void *stream);
 
+/* The sine and cosine the branch kernel evaluates (table-driven: a table of
+ * sin and cos at multiples of 1/128 plus short Taylor series and the
+ * angle-addition formulas; CUDA's sincos beyond |d| > 3.14), applied to n
+ * angles d_angle into d_sin, d_cos (device buffers). For checking its
+ * accuracy against other implementations. */
+int opf_sincos(opf_model *model, const double *d_angle, int64_t n, double *d_sin, double *d_cos,
+               void *stream);
+
 /* Launch shape used by the eval calls; the default suits large instances. */
 int opf_get_launch(const opf_model *model, opf_launch *cfg);
 int opf_set_launch(opf_model *model, const opf_launch *cfg);

@@ -330,6 +330,21 @@ int opf_flat_start(opf_model *m, double *d_x, void *stream)
     return launch_flat_start(*m->M, d_x, static_cast<cudaStream_t>(stream));
 }
 
+int opf_sincos(opf_model *m, const double *d_angle, int64_t n, double *d_sin, double *d_cos,
+               void *stream)
+{
+    int rc = check_dev(m);
+    if (rc)
+        return rc;
+    if (n < 0 || (n > 0 && (!d_angle || !d_sin || !d_cos))) {
+        set_error("opf_sincos: bad arguments");
+        return OPF_EINVAL;
+    }
+    if (n == 0)
+        return OPF_OK;
+    return launch_sincos(*m->M, d_angle, n, d_sin, d_cos, static_cast<cudaStream_t>(stream));
+}
+
 int opf_get_launch(const opf_model *m, opf_launch *cfg)
 {
     int rc = check(m);
@@ -393,10 +408,11 @@ int opf_autotune(opf_model *m, const double *d_x, const double *d_lambda, int32_
     const opf_launch saved = M.launch;
     opf_launch bestc = saved;
     float best_ms = 1e30f;
-    const int blocks[] = {64, 128, 256, 512};
+    const int bblocks[] = {32, 64, 128, 256, 512};
+    const int ublocks[] = {32, 64, 128, 256};  // the bus kernel stages at most 8 warps
     const int ctas[] = {0, 2, 4, 8, 16};
-    for (int bb : blocks)
-        for (int bu : blocks)
+    for (int bb : bblocks)
+        for (int bu : ublocks)
             for (int cb : ctas)
                 for (int cu : ctas) {
                     if (cu != 0 && cu != cb)  // keep the search small: equal persistence

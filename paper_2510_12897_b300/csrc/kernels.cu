@@ -51,7 +51,9 @@ namespace {
 
 struct KParams {
     DevArrays d;
+    InstDev inst0;  // instance 0: the only one when ninst == 1
     int32_t ninst;
+    int32_t want_grad, want_obj;
     int64_t nbr_items, nbus_items, ngen_items;
     const double *__restrict__ x;
     const double *__restrict__ lam;
@@ -84,16 +86,82 @@ __device__ __forceinline__ void split(int loc, int count, int T, int &t, int &e)
     }
 }
 
-// -v on the integer pipe
+// the descriptor of instance s (kernel parameter for a single instance)
+template <bool ONE>
+__device__ __forceinline__ InstDev inst_of(const KParams &P, int s)
+{
+    if (ONE)
+        return P.inst0;
+    InstDev I;
+    const int4 *src = reinterpret_cast<const int4 *>(P.d.inst + s);
+    int4 *dst = reinterpret_cast<int4 *>(&I);
+#pragma unroll
+    for (int w = 0; w < (int)(sizeof(InstDev) / 16); w++)
+        dst[w] = __ldg(src + w);
+    return I;
+}
+
+// -v on the integer pipe (an opaque XOR of the sign bit: a plain negation
+// could be rematerialised as an FP64 instruction, the scarce unit here)
 __device__ __forceinline__ double neg(double v)
 {
-    return __longlong_as_double(__double_as_longlong(v) ^ (long long)0x8000000000000000ULL);
+    long long r;
+    asm("xor.b64 %0, %1, 0x8000000000000000;" : "=l"(r) : "l"(__double_as_longlong(v)));
+    return __longlong_as_double(r);
 }
 
 // v or -v on the integer pipe
 __device__ __forceinline__ double flip(double v, bool f)
 {
-    return __longlong_as_double(__double_as_longlong(v) ^ (f ? (long long)0x8000000000000000ULL : 0LL));
+    long long r;
+    asm("xor.b64 %0, %1, %2;"
+        : "=l"(r)
+        : "l"(__double_as_longlong(v)), "l"(f ? (long long)0x8000000000000000ULL : 0LL));
+    return __longlong_as_double(r);
+}
+
+// 2 v exactly, on the integer pipe: a normal v gets one more in its exponent
+// field; zero and subnormals shift their magnitude left by one (carrying into
+// the exponent field where the result becomes normal); the largest binade
+// overflows to infinity; infinities and NaNs are returned unchanged.
+__device__ __forceinline__ double twice(double v)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const unsigned long long sign = b & 0x8000000000000000ULL;
+    const unsigned long long mag = b & 0x7fffffffffffffffULL;
+    const unsigned ex = (unsigned)(mag >> 52);
+    unsigned long long r = b + (1ULL << 52);
+    r = ex == 0u ? (sign | (mag << 1)) : r;
+    r = ex == 0x7feu ? (sign | 0x7ff0000000000000ULL) : r;
+    r = ex == 0x7ffu ? b : r;
+    return __longlong_as_double((long long)r);
+}
+
+// Table-driven sine and cosine (the table-lookup method of Gal and Bachelis,
+// 1991, and of Tang, 1989): d = k h + e with h = 1/kTrigScale, k = rint(d/h)
+// (by adding 1.5 * 2^52), e = d - k h (exact, Sterbenz); sin(k h), cos(k h)
+// from the table; sin e = e - e^3/6 + e^5/120 and cos e = 1 - e^2/2 + e^4/24,
+// whose truncation errors are below 1e-20 for |e| <= 1/256; then
+// sin d = sin(kh) cos e + cos(kh) sin e, cos d = cos(kh) cos e - sin(kh) sin e.
+// Thirteen FP64 operations. |d| beyond the table falls back to sincos().
+__device__ __forceinline__ void sincos_tab(double d, const double2 *__restrict__ tab, double *sn,
+                                           double *cs)
+{
+    const double shift = 6755399441055744.0;  // 1.5 * 2^52
+    const double t = fma(d, (double)kTrigScale, shift);
+    const int k = __double2loint(t);
+    if (k < -kTrigK || k > kTrigK) {
+        sincos(d, sn, cs);
+        return;
+    }
+    const double kd = t - shift;
+    const double e = fma(kd, -1.0 / kTrigScale, d);
+    const double e2 = e * e;
+    const double se = fma(e * e2, fma(e2, 1.0 / 120.0, -1.0 / 6.0), e);
+    const double ce = fma(e2, fma(e2, 1.0 / 24.0, -0.5), 1.0);
+    const double2 tk = __ldg(tab + (k + kTrigK));
+    *sn = fma(tk.x, ce, tk.y * se);
+    *cs = fma(tk.y, ce, neg(tk.x * se));
 }
 
 // five Jacobian entries of a flow row, columns ascending:
@@ -111,14 +179,16 @@ __device__ __forceinline__ void put5(double *J, bool f_lo, double vaf, double va
 // static (never written) data of one branch item
 struct BrStatic {
     int4 br;  // f, t, slot of the from-arc, slot of the to-arc
+    int2 jb;  // the arcs' entries in their buses' balance rows (one period)
     double2 yff, yft, ytf, ytt;
     double r2;
 };
 
-__device__ __forceinline__ BrStatic load_br(const DevArrays &d, int kb, bool need_r2)
+__device__ __forceinline__ BrStatic load_br(const DevArrays &d, int kb, bool need_r2, bool need_jb)
 {
     BrStatic s;
     s.br = __ldg(d.br + kb);
+    s.jb = need_jb ? __ldg(d.br_jb + kb) : make_int2(0, 0);
     s.yff = __ldg(d.y_ff + kb);
     s.yft = __ldg(d.y_ft + kb);
     s.ytf = __ldg(d.y_tf + kb);
@@ -127,26 +197,32 @@ __device__ __forceinline__ BrStatic load_br(const DevArrays &d, int kb, bool nee
     return s;
 }
 
-template <bool CONS, bool JAC, bool HESS, bool GRAD>
-__global__ void branch_kernel(const KParams P)
+template <bool CONS, bool JAC, bool HESS, bool ONE>
+__global__ void __launch_bounds__(512) branch_kernel(const KParams P)
 {
     cudaTriggerProgrammaticLaunchCompletion();
     const DevArrays &d = P.d;
-    const double *__restrict__ x = P.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
 
-    auto locate = [&](int64_t item, int &s, int &t, int &k) {
-        s = P.ninst == 1 ? 0 : find_inst(d.br_items, P.ninst, item);
-        const InstDev *I = d.inst + s;
-        split((int)(item - __ldg(d.br_items + s)), __ldg(&I->nl), __ldg(&I->T), t, k);
+    auto locate = [&](int64_t item, int &s, int &t, int &k, int &kb) {
+        if (ONE) {
+            s = 0;
+            split((int)item, P.inst0.nl, P.inst0.T, t, k);
+            kb = k;
+        } else {
+            s = find_inst(d.br_items, P.ninst, item);
+            const InstDev *I = d.inst + s;
+            split((int)(item - __ldg(d.br_items + s)), __ldg(&I->nl), __ldg(&I->T), t, k);
+            kb = __ldg(&I->br0) + k;
+        }
     };
 
-    int s = 0, t = 0, k = 0;
+    int s = 0, t = 0, k = 0, kb = 0;
     BrStatic st{};
-    if (it < P.nbr_items) {
-        locate(it, s, t, k);
-        st = load_br(d, __ldg(&d.inst[s].br0) + k, CONS);
+    if (it < P.nbr_items) {  // static prologue, overlaps the previous kernel
+        locate(it, s, t, k, kb);
+        st = load_br(d, kb, CONS, JAC);
     }
     cudaGridDependencySynchronize();
 
@@ -154,43 +230,42 @@ __global__ void branch_kernel(const KParams P)
         const BrStatic cur = st;
         const int cs = s, ct = t, ck = k;
         if (it + stride < P.nbr_items) {  // prefetch the next item's static data
-            locate(it + stride, s, t, k);
-            st = load_br(d, __ldg(&d.inst[s].br0) + k, CONS);
+            locate(it + stride, s, t, k, kb);
+            st = load_br(d, kb, CONS, JAC);
         }
-        const InstDev *I = d.inst + cs;
-        const int nl = __ldg(&I->nl), nb = __ldg(&I->nb), ng = __ldg(&I->ng), T = __ldg(&I->T);
-        const int64_t nbT = (int64_t)nb * T, ngT = (int64_t)ng * T, nlT = (int64_t)nl * T;
-        const int64_t na = 2 * (int64_t)nl;
-        const int64_t x0 = __ldg(&I->x0), c0 = __ldg(&I->c0);
-        const int64_t rk = ck + (int64_t)nl * ct;  // element index inside each branch group
+        const InstDev I = inst_of<ONE>(P, cs);
+        const int nl = I.nl, nb = I.nb, ng = I.ng, T = I.T;
+        const int nbT = nb * T, ngT = ng * T, nlT = nl * T, na = 2 * nl;
+        const int rk = ck + nl * ct;  // element index inside each branch group
         const int f = cur.br.x, b = cur.br.y;
 
-        const int64_t xva = x0 + (int64_t)nb * ct, xvm = xva + nbT;
-        const int64_t xp = x0 + 2 * nbT + 2 * ngT + na * ct, xq = xp + na * T;
-        const double vaf = __ldg(x + xva + f), vat = __ldg(x + xva + b);
-        const double vmf = __ldg(x + xvm + f), vmt = __ldg(x + xvm + b);
+        const double *__restrict__ xs = P.x + I.x0;
+        const int iva = nb * ct, ivm = nbT + nb * ct;
+        const int ip = 2 * nbT + 2 * ngT + na * ct, iq = ip + na * T;
+        const double vaf = __ldg(xs + iva + f), vat = __ldg(xs + iva + b);
+        const double vmf = __ldg(xs + ivm + f), vmt = __ldg(xs + ivm + b);
         double pf = 0, qf = 0, pt = 0, qt = 0;
         if (CONS || JAC || HESS) {
-            pf = __ldg(x + xp + ck);
-            pt = __ldg(x + xp + nl + ck);
-            qf = __ldg(x + xq + ck);
-            qt = __ldg(x + xq + nl + ck);
+            pf = __ldg(xs + ip + ck);
+            pt = __ldg(xs + ip + nl + ck);
+            qf = __ldg(xs + iq + ck);
+            qt = __ldg(xs + iq + nl + ck);
         }
         double m1 = 0, m2 = 0, m3 = 0, m4 = 0, lf = 0, lt = 0;
         if (HESS) {
-            const double *L = P.lam + c0 + T + rk;
+            const double *L = P.lam + I.c0 + (T + rk);
             m1 = __ldg(L);
             m2 = __ldg(L + nlT);
             m3 = __ldg(L + 2 * nlT);
             m4 = __ldg(L + 3 * nlT);
-            lf = __ldg(L + 5 * nlT + 2 * nbT);
-            lt = __ldg(L + 6 * nlT + 2 * nbT);
+            lf = __ldg(L + (5 * nlT + 2 * nbT));
+            lt = __ldg(L + (6 * nlT + 2 * nbT));
         }
         const double2 Yff = cur.yff, Yft = cur.yft, Ytf = cur.ytf, Ytt = cur.ytt;
 
         const double dlt = vaf - vat;
         double sn, cs_;
-        sincos(dlt, &sn, &cs_);
+        sincos_tab(dlt, d.trig, &sn, &cs_);
         const double vft = vmf * vmt;
         const double Aft = fma(Yft.x, cs_, Yft.y * sn);
         const double Bft = fma(Yft.x, sn, neg(Yft.y * cs_));
@@ -199,7 +274,7 @@ __global__ void branch_kernel(const KParams P)
 
         if (CONS) {
             const double vf2 = vmf * vmf, vt2 = vmt * vmt;
-            double *c = P.c + c0 + T + rk;
+            double *c = P.c + I.c0 + (T + rk);
             c[0] = pf - fma(Yff.x, vf2, vft * Aft);
             c[nlT] = qf - fma(neg(Yff.y), vf2, vft * Bft);
             c[2 * nlT] = pt - fma(Ytt.x, vt2, vft * Atf);
@@ -209,30 +284,36 @@ __global__ void branch_kernel(const KParams P)
             c[6 * nlT + 2 * nbT] = fma(pt, pt, qt * qt) - cur.r2;
         }
         if (JAC) {
-            const int64_t j0 = __ldg(&I->j0), jP = __ldg(&I->jP);
+            const int jP = (int)I.jP;
             const bool f_lo = f < b;
-            const double v2f = vmf + vmf, v2t = vmt + vmt;
+            const double v2f = twice(vmf), v2t = twice(vmt);
             const double uB = vft * Bft, uA = vft * Aft, wB = vft * Btf, wA = vft * Atf;
-            double *J = P.jac + j0 + T + 5 * rk;
+            double *J = P.jac + I.j0;
+            double *Jf = J + (T + 5 * rk);
             // row p_fr - P_fr
-            put5(J, f_lo, uB, neg(uB), neg(fma(Yff.x, v2f, vmt * Aft)), neg(vmf * Aft));
+            put5(Jf, f_lo, uB, neg(uB), neg(fma(Yff.x, v2f, vmt * Aft)), neg(vmf * Aft));
             // row q_fr - Q_fr
-            put5(J + 5 * nlT, f_lo, neg(uA), uA, fma(Yff.y, v2f, neg(vmt * Bft)), neg(vmf * Bft));
+            put5(Jf + 5 * nlT, f_lo, neg(uA), uA, fma(Yff.y, v2f, neg(vmt * Bft)), neg(vmf * Bft));
             // row p_to - P_to
-            put5(J + 10 * nlT, f_lo, neg(wB), wB, neg(vmt * Atf), neg(fma(Ytt.x, v2t, vmf * Atf)));
+            put5(Jf + 10 * nlT, f_lo, neg(wB), wB, neg(vmt * Atf), neg(fma(Ytt.x, v2t, vmf * Atf)));
             // row q_to - Q_to
-            put5(J + 15 * nlT, f_lo, wA, neg(wA), neg(vmt * Btf), fma(Ytt.y, v2t, neg(vmf * Btf)));
-            double *Ja = P.jac + j0 + T + 20 * nlT + 2 * rk;  // angle row va_f - va_t
+            put5(Jf + 15 * nlT, f_lo, wA, neg(wA), neg(vmt * Btf), fma(Ytt.y, v2t, neg(vmf * Btf)));
+            double *Ja = J + (T + 20 * nlT + 2 * rk);  // angle row va_f - va_t
             Ja[0] = flip(1.0, !f_lo);
             Ja[1] = flip(1.0, f_lo);
-            double *Jt = P.jac + j0 + T + 22 * nlT + 2 * jP * T + 2 * rk;  // thermal rows
-            Jt[0] = pf + pf;
-            Jt[1] = qf + qf;
-            Jt[2 * nlT] = pt + pt;
-            Jt[2 * nlT + 1] = qt + qt;
+            double *Jb = J + (T + 22 * nlT + jP * ct);  // +1 of each arc in its bus's P and Q rows
+            Jb[cur.jb.x] = 1.0;
+            Jb[cur.jb.y] = 1.0;
+            Jb[jP * T + cur.jb.x] = 1.0;
+            Jb[jP * T + cur.jb.y] = 1.0;
+            double *Jt = J + (T + 22 * nlT + 2 * jP * T + 2 * rk);  // thermal rows
+            Jt[0] = twice(pf);
+            Jt[1] = twice(qf);
+            Jt[2 * nlT] = twice(pt);
+            Jt[2 * nlT + 1] = twice(qt);
         }
         if (HESS || CONS) {
-            ArcScratch *S = d.arcs + __ldg(&I->scr0) + na * ct;
+            ArcScratch *S = d.arcs + I.scr0 + na * ct;
             double2 *sf = reinterpret_cast<double2 *>(S + cur.br.z);
             double2 *sto = reinterpret_cast<double2 *>(S + cur.br.w);
             sf[0] = make_double2(pf, qf);
@@ -244,236 +325,281 @@ __global__ void branch_kernel(const KParams P)
                 const double Wt = fma(m3, Ytt.x, neg(m4 * Ytt.y));
                 const double vU = vft * U;
                 sf[1] = make_double2(vU, neg(vmt * V));
-                sf[2] = make_double2(neg(Wf + Wf), neg(U));
+                sf[2] = make_double2(neg(twice(Wf)), neg(U));
                 sto[1] = make_double2(vU, vmf * V);
-                sto[2] = make_double2(neg(Wt + Wt), neg(U));
-                const int64_t hpq = __ldg(&I->h0) + (__ldg(&I->hva) + __ldg(&I->hvm)) * T + ngT;
-                double *Hp = P.hess + hpq + ck + na * ct;
-                const double l2f = lf + lf, l2t = lt + lt;
+                sto[2] = make_double2(neg(twice(Wt)), neg(U));
+                double *Hp = P.hess + I.h0 + ((int)(I.hva + I.hvm) * T + ngT + ck + na * ct);
+                const double l2f = twice(lf), l2t = twice(lt);
                 Hp[0] = l2f;            // (p_fr, p_fr)
                 Hp[nl] = l2t;           // (p_to, p_to)
                 Hp[na * T] = l2f;       // (q_fr, q_fr)
                 Hp[na * T + nl] = l2t;  // (q_to, q_to)
             }
         }
-        if (GRAD) {
-            P.grad[xp + ck] = 0.0;
-            P.grad[xp + nl + ck] = 0.0;
-            P.grad[xq + ck] = 0.0;
-            P.grad[xq + nl + ck] = 0.0;
+        if (P.want_grad) {
+            double *g = P.grad + I.x0;
+            g[ip + ck] = 0.0;
+            g[ip + nl + ck] = 0.0;
+            g[iq + ck] = 0.0;
+            g[iq + nl + ck] = 0.0;
         }
     }
 }
 
-struct BusStatic {
-    int4 a;  // first slot, end slot, first gen entry, end gen entry
-    int4 b;  // balance-row offset, va-row offset, vm-row offset, nd | nlt << 16
-    double2 gsbs;
-};
+constexpr int kBusBlockMax = 256;
 
-template <bool CONS, bool JAC, bool HESS, bool GRAD, bool OBJ>
-__global__ void bus_kernel(const KParams P)
+template <bool CONS, bool JAC, bool HESS, bool ONE>
+__global__ void __launch_bounds__(kBusBlockMax) bus_kernel(const KParams P)
 {
     cudaTriggerProgrammaticLaunchCompletion();
+    __shared__ double wsum[32];
+    __shared__ bool last;
     const DevArrays &d = P.d;
-    const double *__restrict__ x = P.x;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t total = P.nbus_items + P.ngen_items;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
 
-    auto locate = [&](int64_t item, int &s, int &t, int &e) {
-        if (item < P.nbus_items) {
-            s = P.ninst == 1 ? 0 : find_inst(d.bus_items, P.ninst, item);
-            const InstDev *I = d.inst + s;
-            split((int)(item - __ldg(d.bus_items + s)), __ldg(&I->nb), __ldg(&I->T), t, e);
-        } else {
-            const int64_t gi = item - P.nbus_items;
-            s = P.ninst == 1 ? 0 : find_inst(d.gen_items, P.ninst, gi);
-            const InstDev *I = d.inst + s;
-            split((int)(gi - __ldg(d.gen_items + s)), __ldg(&I->ng), __ldg(&I->T), t, e);
-        }
+    struct Item {
+        int s, t, e;    // instance, period, bus or generator
+        int4 a, b;      // bus: slots, generator entries, row offsets
+        int2 m;         // bus: group-closing mask of its slots, number of lower slots
+        double2 gsbs;
+        int gfirst;     // first generator id at the bus, or -1
     };
-    auto load = [&](int64_t item, int s, int e) {
-        BusStatic b{};
-        if (item < P.nbus_items) {
-            const int ib = __ldg(&d.inst[s].bus0) + e;
-            b.a = __ldg(d.bus_a + ib);
-            b.b = __ldg(d.bus_b + ib);
-            b.gsbs = __ldg(d.gsbs + ib);
+    // items: generators first (the few blocks holding them do the objective
+    // reduction and finish early), then buses
+    auto load = [&](int64_t item) {
+        Item q{};
+        q.gfirst = -1;
+        if (item >= P.ngen_items && item < total) {
+            item -= P.ngen_items;
+            int r, bus0;
+            if (ONE) {
+                q.s = 0;
+                split((int)item, P.inst0.nb, P.inst0.T, q.t, r);
+                bus0 = 0;
+            } else {
+                q.s = find_inst(d.bus_items, P.ninst, item);
+                const InstDev *I = d.inst + q.s;
+                split((int)(item - __ldg(d.bus_items + q.s)), __ldg(&I->nb), __ldg(&I->T), q.t, r);
+                bus0 = __ldg(&I->bus0);
+            }
+            q.e = __ldg(d.bus_order + bus0 + r);  // buses of equal slot count share warps
+            const int ib = bus0 + q.e;
+            q.a = __ldg(d.bus_a + ib);
+            q.b = __ldg(d.bus_b + ib);
+            q.m = __ldg(d.bus_c + ib);
+            q.gsbs = __ldg(d.gsbs + ib);
+            if (CONS && q.a.z < q.a.w)
+                q.gfirst = __ldg(d.gen_list + (ONE ? P.inst0.gl0 : __ldg(&d.inst[q.s].gl0)) + q.a.z);
+        } else if (item < P.ngen_items) {
+            const int64_t gi = item;
+            if (ONE) {
+                q.s = 0;
+                split((int)gi, P.inst0.ng, P.inst0.T, q.t, q.e);
+            } else {
+                q.s = find_inst(d.gen_items, P.ninst, gi);
+                const InstDev *I = d.inst + q.s;
+                split((int)(gi - __ldg(d.gen_items + q.s)), __ldg(&I->ng), __ldg(&I->T), q.t, q.e);
+            }
         }
-        return b;
+        return q;
     };
 
-    int s = 0, t = 0, e = 0;
-    BusStatic st{};
-    if (it < total) {
-        locate(it, s, t, e);
-        st = load(it, s, e);
-    }
+    Item cur{};
+    if (it < total)  // static prologue, overlaps the previous kernel
+        cur = load(it);
     cudaGridDependencySynchronize();
 
     double obj_acc = 0.0;
     for (; it < total; it += stride) {
-        const BusStatic cur = st;
-        const int cs = s, ct = t, ce = e;
-        if (it + stride < total) {
-            locate(it + stride, s, t, e);
-            st = load(it + stride, s, e);
-        }
-        const InstDev *I = d.inst + cs;
-        const int nl = __ldg(&I->nl), nb = __ldg(&I->nb), ng = __ldg(&I->ng), T = __ldg(&I->T);
-        const int64_t nbT = (int64_t)nb * T, ngT = (int64_t)ng * T, nlT = (int64_t)nl * T;
-        const int64_t x0 = __ldg(&I->x0), c0 = __ldg(&I->c0);
-        if (it < P.nbus_items) {
-            const int i = ce;
-            const int64_t na = 2 * (int64_t)nl;
-            const int64_t xva = x0 + (int64_t)nb * ct, xvm = xva + nbT;
-            const double vm = __ldg(x + xvm + i);
-            const double2 gb = cur.gsbs;
-            const int a0 = cur.a.x, a1 = cur.a.y, g0 = cur.a.z, g1 = cur.a.w;
-            const ArcScratch *S = d.arcs + __ldg(&I->scr0) + na * ct;
-            if (GRAD) {
-                P.grad[xva + i] = 0.0;
-                P.grad[xvm + i] = 0.0;
-            }
-            if (i == __ldg(&I->ref)) {
-                if (CONS)
-                    P.c[c0 + ct] = __ldg(x + xva + i);
-                if (JAC)
-                    P.jac[__ldg(&I->j0) + ct] = 1.0;
+        const Item q = cur;
+        if (it + stride < total)
+            cur = load(it + stride);
+        const InstDev I = inst_of<ONE>(P, q.s);
+        const int nl = I.nl, nb = I.nb, ng = I.ng, T = I.T;
+        const int nbT = nb * T, ngT = ng * T, nlT = nl * T, na = 2 * nl;
+        const double *__restrict__ xs = P.x + I.x0;
+        if (it >= P.ngen_items) {
+            const int i = q.e;
+            const int iva = nb * q.t, ivm = nbT + nb * q.t;
+            // every dynamic scalar of the bus, issued together
+            const double vm = __ldg(xs + ivm + i);
+            double lP = 0.0, lQ = 0.0, Pd = 0.0, Qd = 0.0, pg1 = 0.0, qg1 = 0.0;
+            if (HESS) {
+                const double *L = P.lam + I.c0 + (T + 5 * nlT + nb * q.t + i);
+                lP = __ldg(L);
+                lQ = __ldg(L + nbT);
             }
             if (CONS) {
-                const int64_t pd = __ldg(&I->pd0) + (int64_t)nb * ct + i;
-                const double vm2 = vm * vm;
-                double Pb = fma(gb.x, vm2, __ldg(d.Pd + pd));
-                double Qb = fma(neg(gb.y), vm2, __ldg(d.Qd + pd));
-                const int gl0 = __ldg(&I->gl0);
-                const int64_t xpg = x0 + 2 * nbT + (int64_t)ng * ct, xqg = xpg + ngT;
-                for (int gp = g0; gp < g1; gp++) {
-                    const int g = __ldg(d.gen_list + gl0 + gp);
-                    Pb -= __ldg(x + xpg + g);
-                    Qb -= __ldg(x + xqg + g);
+                Pd = __ldg(d.Pd + I.pd0 + (nb * q.t + i));
+                Qd = __ldg(d.Qd + I.pd0 + (nb * q.t + i));
+                if (q.gfirst >= 0) {
+                    pg1 = __ldg(xs + 2 * nbT + ng * q.t + q.gfirst);
+                    qg1 = __ldg(xs + 2 * nbT + ngT + ng * q.t + q.gfirst);
                 }
-#pragma unroll 4
-                for (int a = a0; a < a1; a++) {
-                    const double2 pq = __ldg(reinterpret_cast<const double2 *>(S + a));
-                    Pb += pq.x;
-                    Qb += pq.y;
-                }
-                P.c[c0 + T + 5 * nlT + (int64_t)nb * ct + i] = Pb;
-                P.c[c0 + T + 5 * nlT + nbT + (int64_t)nb * ct + i] = Qb;
             }
-            if (JAC) {
-                const int64_t jP = __ldg(&I->jP);
-                double *JP = P.jac + __ldg(&I->j0) + T + 22 * nlT + jP * ct + cur.b.x;
+            const double2 gb = q.gsbs;
+            const int nsl = q.a.y - q.a.x;
+            const int ng_here = q.a.w - q.a.z;
+            const double2 *__restrict__ Sg =
+                reinterpret_cast<const double2 *>(d.arcs + I.scr0 + (int64_t)na * q.t + q.a.x);
+            if (P.want_grad) {
+                P.grad[I.x0 + iva + i] = 0.0;
+                P.grad[I.x0 + ivm + i] = 0.0;
+            }
+            if (i == I.ref) {
+                if (CONS)
+                    P.c[I.c0 + q.t] = __ldg(xs + iva + i);
+                if (JAC)
+                    P.jac[I.j0 + q.t] = 1.0;
+            }
+            if (JAC) {  // the arcs' +1 entries are written by the branch phase
+                const int jP = (int)I.jP;
+                double *JP = P.jac + I.j0 + (T + 22 * nlT + jP * q.t + q.b.x);
                 double *JQ = JP + jP * T;
-                const double v2 = vm + vm;
+                const double v2 = twice(vm);
                 JP[0] = gb.x * v2;
                 JQ[0] = neg(gb.y * v2);
-                int q = 1;
-                for (int gp = g0; gp < g1; gp++, q++) {
-                    JP[q] = -1.0;
-                    JQ[q] = -1.0;
-                }
-                for (int a = a0; a < a1; a++, q++) {
-                    JP[q] = 1.0;
-                    JQ[q] = 1.0;
+                for (int e = 1; e <= ng_here; e++) {
+                    JP[e] = -1.0;
+                    JQ[e] = -1.0;
                 }
             }
-            if (HESS) {
-                const int64_t lb = c0 + T + 5 * nlT + (int64_t)nb * ct + i;
-                const double lP = __ldg(P.lam + lb), lQ = __ldg(P.lam + lb + nbT);
-                const int64_t h0 = __ldg(&I->h0), hva = __ldg(&I->hva), hvm = __ldg(&I->hvm);
-                double *Hvm = P.hess + h0 + hva * T + hvm * ct + cur.b.z;
-                double dmm = fma(gb.x, lP, neg(gb.y * lQ));
-                dmm = dmm + dmm;  // 2 gs lambda_P - 2 bs lambda_Q
-                if (a1 > a0) {
-                    double *Hva = P.hess + h0 + hva * ct + cur.b.y;
-                    const int nd = cur.b.w & 0xffff, nlt = cur.b.w >> 16;
-                    const uint8_t *code = d.slot_code + __ldg(&I->slot0);
-                    // one pass over the slots, sorted by far bus: groups of
-                    // parallel arcs are summed, then written in column order
-                    double daa = 0.0, dma = 0.0, acc_ma = 0.0, acc_aa = 0.0, acc_mm = 0.0;
-                    bool first = true;
-                    int grp = 0;
-                    for (int a = a0; a < a1; a++) {
-                        const unsigned cd = __ldg(code + a);
-                        const double2 v1 = __ldg(reinterpret_cast<const double2 *>(S + a) + 1);
-                        const double2 v2 = __ldg(reinterpret_cast<const double2 *>(S + a) + 2);
-                        daa += v1.x;
-                        dma += v1.y;
-                        dmm += v2.x;
-                        if (first) {
-                            acc_ma = neg(v1.y);
-                            acc_aa = neg(v1.x);
-                            acc_mm = v2.y;
-                        } else {
-                            acc_ma -= v1.y;
-                            acc_aa -= v1.x;
-                            acc_mm += v2.y;
-                        }
-                        first = (cd & SLOT_LAST) != 0;
-                        if (first) {
-                            Hvm[grp < nlt ? grp : grp + 1] = acc_ma;  // (vm_i, va_j)
-                            if (cd & SLOT_LOWER) {
-                                Hva[grp] = acc_aa;               // (va_i, va_j), j < i
-                                Hvm[nd + 1 + grp] = acc_mm;      // (vm_i, vm_j), j < i
+            if (CONS || HESS) {
+                const double vm2 = vm * vm;
+                double Pb = fma(gb.x, vm2, Pd), Qb = fma(neg(gb.y), vm2, Qd);
+                if (CONS && q.gfirst >= 0) {
+                    Pb -= pg1;
+                    Qb -= qg1;
+                    for (int gp = q.a.z + 1; gp < q.a.w; gp++) {
+                        const int g = __ldg(d.gen_list + I.gl0 + gp);
+                        Pb -= __ldg(xs + 2 * nbT + ng * q.t + g);
+                        Qb -= __ldg(xs + 2 * nbT + ngT + ng * q.t + g);
+                    }
+                }
+                const int hva = (int)I.hva, hvm = (int)I.hvm;
+                double *Hvm = P.hess + I.h0 + (hva * T + hvm * q.t + q.b.z);
+                double *Hva = P.hess + I.h0 + (hva * q.t + q.b.y);
+                const int nd = q.b.w & 0xffff, nlt = q.b.w >> 16;
+                const uint8_t *code = d.slot_code + I.slot0 + q.a.x;
+                double daa = 0.0, dma = 0.0, acc_ma = 0.0, acc_aa = 0.0, acc_mm = 0.0;
+                double dmm = HESS ? twice(fma(gb.x, lP, neg(gb.y * lQ))) : 0.0;  // 2 gs lP - 2 bs lQ
+                bool first = true;
+                int grp = 0;
+                // the bus's slots (sorted by far bus), four at a time: the loads
+                // of a chunk are all in flight before its arithmetic
+                for (int a0 = 0; a0 < nsl; a0 += 4) {
+                    double2 v0[4], v1[4], v2[4];
+#pragma unroll
+                    for (int u = 0; u < 4; u++)
+                        if (a0 + u < nsl) {
+                            if (CONS)
+                                v0[u] = __ldcg(Sg + 3 * (a0 + u));
+                            if (HESS) {
+                                v1[u] = __ldcg(Sg + 3 * (a0 + u) + 1);
+                                v2[u] = __ldcg(Sg + 3 * (a0 + u) + 2);
                             }
-                            grp++;
+                        }
+#pragma unroll
+                    for (int u = 0; u < 4; u++) {
+                        const int a = a0 + u;
+                        if (a >= nsl)
+                            break;
+                        if (CONS) {
+                            Pb += v0[u].x;
+                            Qb += v0[u].y;
+                        }
+                        if (HESS) {
+                            const unsigned cd = nsl <= 32
+                                ? (((unsigned)q.m.x >> a) & 1u) | (a < q.m.y ? 2u : 0u)
+                                : (unsigned)__ldg(code + a);
+                            daa += v1[u].x;
+                            dma += v1[u].y;
+                            dmm += v2[u].x;
+                            if (first) {
+                                acc_ma = neg(v1[u].y);
+                                acc_aa = neg(v1[u].x);
+                                acc_mm = v2[u].y;
+                            } else {
+                                acc_ma -= v1[u].y;
+                                acc_aa -= v1[u].x;
+                                acc_mm += v2[u].y;
+                            }
+                            first = (cd & SLOT_LAST) != 0;
+                            if (first) {  // a group of parallel arcs ends: write its entries
+                                Hvm[grp < nlt ? grp : grp + 1] = acc_ma;  // (vm_i, va_j)
+                                if (cd & SLOT_LOWER) {
+                                    Hva[grp] = acc_aa;               // (va_i, va_j), j < i
+                                    Hvm[nd + 1 + grp] = acc_mm;      // (vm_i, vm_j), j < i
+                                }
+                                grp++;
+                            }
                         }
                     }
-                    Hva[nlt] = daa;
-                    Hvm[nlt] = dma;
-                    Hvm[nd + 1 + nlt] = dmm;
-                } else {
-                    Hvm[0] = dmm;
+                }
+                if (CONS) {
+                    double *c = P.c + I.c0 + (T + 5 * nlT + nb * q.t + i);
+                    c[0] = Pb;
+                    c[nbT] = Qb;
+                }
+                if (HESS) {
+                    if (nsl > 0) {
+                        Hva[nlt] = daa;
+                        Hvm[nlt] = dma;
+                        Hvm[nd + 1 + nlt] = dmm;
+                    } else {
+                        Hvm[0] = dmm;
+                    }
                 }
             }
         } else {
-            const int g = ce;
-            const int64_t xpg = x0 + 2 * nbT + (int64_t)ng * ct + g;
-            const int gg = __ldg(&I->gen0) + g;
-            const double pg = __ldg(x + xpg);
+            const int g = q.e;
+            const int ipg = 2 * nbT + ng * q.t + g;
+            const int gg = I.gen0 + g;
+            const double pg = __ldg(xs + ipg);
             const double c2 = __ldg(d.c2 + gg), c1 = __ldg(d.c1 + gg);
-            if (OBJ)
+            if (P.want_obj)
                 obj_acc += fma(fma(c2, pg, c1), pg, __ldg(d.c0 + gg));
-            if (GRAD) {
-                P.grad[xpg] = fma(c2 + c2, pg, c1);
-                P.grad[xpg + ngT] = 0.0;
+            if (P.want_grad) {
+                P.grad[I.x0 + ipg] = fma(twice(c2), pg, c1);
+                P.grad[I.x0 + ipg + ngT] = 0.0;
             }
-            if (HESS) {
-                const int64_t hpg = __ldg(&I->h0) + (__ldg(&I->hva) + __ldg(&I->hvm)) * T;
-                P.hess[hpg + (int64_t)ng * ct + g] = P.sigma * (c2 + c2);
-            }
-            if ((CONS || JAC) && ct >= 1 && __ldg(&I->ramp)) {
-                const int64_t q = g + (int64_t)ng * (ct - 1);
+            if (HESS)
+                P.hess[I.h0 + ((int)(I.hva + I.hvm) * T + ng * q.t + g)] = P.sigma * twice(c2);
+            if ((CONS || JAC) && q.t >= 1 && I.ramp) {
+                const int r = g + ng * (q.t - 1);
                 if (CONS)
-                    P.c[c0 + T + 7 * nlT + 2 * nbT + q] = pg - __ldg(x + xpg - ng);
+                    P.c[I.c0 + (T + 7 * nlT + 2 * nbT + r)] = pg - __ldg(xs + ipg - ng);
                 if (JAC) {
-                    double *J = P.jac + __ldg(&I->j0) + T + 26 * nlT + 2 * __ldg(&I->jP) * T + 2 * q;
+                    double *J = P.jac + I.j0 + (T + 26 * nlT + 2 * (int)I.jP * T + 2 * r);
                     J[0] = -1.0;
                     J[1] = 1.0;
                 }
             }
-            const int64_t lc = __ldg(&I->link_c);
-            if ((CONS || JAC) && lc >= 0) {
+            if ((CONS || JAC) && I.link_c >= 0) {
                 if (CONS)
-                    P.c[lc + g] = pg - __ldg(x + __ldg(&I->link_x0) + g);
+                    P.c[I.link_c + g] = pg - __ldg(P.x + I.link_x0 + g);
                 if (JAC) {
-                    double *J = P.jac + __ldg(&I->link_j) + 2 * g;
+                    double *J = P.jac + I.link_j + 2 * g;
                     J[0] = -1.0;
                     J[1] = 1.0;
                 }
             }
         }
     }
-    if (OBJ) {
-        // fixed-order reduction: warp, block, then the last block over blocks
-        __shared__ double wsum[32];
-        __shared__ bool last;
+    // Objective: fixed-order reduction (warp, block, then the last of the
+    // blocks that can hold generator items sums their partials). Only those
+    // blocks take part; they come first in the grid.
+    const int64_t per_pass = (int64_t)gridDim.x * blockDim.x;
+    unsigned gblocks = P.ngen_items >= per_pass
+        ? gridDim.x : (unsigned)((P.ngen_items + blockDim.x - 1) / blockDim.x);
+    if (gblocks == 0)
+        gblocks = 1;  // no generators: block 0 still writes the (zero) objective
+    if (P.want_obj && blockIdx.x < gblocks) {
         for (int off = 16; off; off >>= 1)
             obj_acc += __shfl_down_sync(0xffffffffu, obj_acc, off);
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
         if (lane == 0)
             wsum[warp] = obj_acc;
         __syncthreads();
@@ -484,16 +610,27 @@ __global__ void bus_kernel(const KParams P)
             d.obj_part[blockIdx.x] = b;
             __threadfence();
             const unsigned prev = atomicAdd(d.ticket, 1u);
-            last = prev == gridDim.x - 1;
+            last = prev == gblocks - 1;
         }
         __syncthreads();
-        if (last && threadIdx.x == 0) {
+        if (last) {  // the whole last block sums the partials, in a fixed order
             __threadfence();
             double tot = 0.0;
-            for (unsigned b = 0; b < gridDim.x; b++)
+            for (unsigned b = threadIdx.x; b < gblocks; b += blockDim.x)
                 tot += __ldcg(d.obj_part + b);
-            *P.obj = tot;
-            *d.ticket = 0u;  // ready for the next launch
+            for (int off = 16; off; off >>= 1)
+                tot += __shfl_down_sync(0xffffffffu, tot, off);
+            __syncthreads();
+            if (lane == 0)
+                wsum[warp] = tot;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double all = 0.0;
+                for (int w = 0; w < (int)(blockDim.x >> 5); w++)
+                    all += wsum[w];
+                *P.obj = all;
+                *d.ticket = 0u;  // ready for the next launch
+            }
         }
     }
 }
@@ -548,6 +685,14 @@ __global__ void flat_kernel(const DevArrays d, int32_t ninst, int64_t nbr_items,
     }
 }
 
+__global__ void sincos_tab_kernel(const double2 *__restrict__ tab, const double *__restrict__ d,
+                                  int64_t n, double *sn, double *cs)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        sincos_tab(d[i], tab, sn + i, cs + i);
+}
+
 int grid_for(int64_t items, int block, int ctas_per_sm, int num_sms, int cap)
 {
     int64_t g = (items + block - 1) / block;
@@ -578,28 +723,29 @@ cudaError_t launch_pdl(K kernel, int grid, int block, cudaStream_t s, const KPar
 }
 
 template <bool C, bool J, bool H>
-cudaError_t dispatch(const KParams &P, bool grad, bool obj, bool run_branch, bool run_bus, int gb,
-                     int bb, int gu, int bu, cudaStream_t s)
+cudaError_t dispatch(const KParams &P, bool one, bool run_branch, bool run_bus, int gb, int bb,
+                     int gu, int bu, cudaStream_t s)
 {
     cudaError_t e = cudaSuccess;
     if (run_branch)
-        e = grad ? launch_pdl(branch_kernel<C, J, H, true>, gb, bb, s, P)
-                 : launch_pdl(branch_kernel<C, J, H, false>, gb, bb, s, P);
+        e = one ? launch_pdl(branch_kernel<C, J, H, true>, gb, bb, s, P)
+                : launch_pdl(branch_kernel<C, J, H, false>, gb, bb, s, P);
     if (e != cudaSuccess || !run_bus)
         return e;
-    if (grad)
-        return obj ? launch_pdl(bus_kernel<C, J, H, true, true>, gu, bu, s, P)
-                   : launch_pdl(bus_kernel<C, J, H, true, false>, gu, bu, s, P);
-    return obj ? launch_pdl(bus_kernel<C, J, H, false, true>, gu, bu, s, P)
-               : launch_pdl(bus_kernel<C, J, H, false, false>, gu, bu, s, P);
+    return one ? launch_pdl(bus_kernel<C, J, H, true>, gu, bu, s, P)
+               : launch_pdl(bus_kernel<C, J, H, false>, gu, bu, s, P);
 }
 
-}  // namespace
-
-int launch_eval(Model &M, const EvalArgs &a, unsigned what, cudaStream_t s, int phases)
+// Launches one fused evaluation with the given scratch.
+int launch_all(Model &M, const EvalArgs &a, unsigned what, cudaStream_t s, int phases,
+               ArcScratch *arcs, double *obj_part, int max_part, unsigned int *ticket)
 {
     KParams P;
     P.d = M.d;
+    P.d.arcs = arcs;
+    P.d.obj_part = obj_part;
+    P.d.ticket = ticket;
+    P.inst0 = M.inst[0];
     P.ninst = M.ninst;
     P.nbr_items = M.nbr_items;
     P.nbus_items = M.nbus_items;
@@ -613,26 +759,29 @@ int launch_eval(Model &M, const EvalArgs &a, unsigned what, cudaStream_t s, int 
     P.jac = a.jac;
     P.hess = a.hess;
     const bool C = what & W_CONS, J = what & W_JAC, H = what & W_HESS;
-    const bool G = what & W_GRAD, O = what & W_OBJ;
+    P.want_grad = (what & W_GRAD) ? 1 : 0;
+    P.want_obj = (what & W_OBJ) ? 1 : 0;
     const opf_launch &L = M.launch;
+    const int bu = L.bus_block > kBusBlockMax ? kBusBlockMax : L.bus_block;
     const int gb = grid_for(M.nbr_items, L.branch_block, L.branch_ctas_per_sm, M.num_sms, 0);
-    const int gu = grid_for(M.nbus_items + M.ngen_items, L.bus_block, L.bus_ctas_per_sm, M.num_sms,
-                            M.max_part);
+    const int cap = max_part < M.max_part ? max_part : M.max_part;
+    const int gu = grid_for(M.nbus_items + M.ngen_items, bu, L.bus_ctas_per_sm, M.num_sms, cap);
     // the branch phase is needed for its rows and for the scratch the bus
     // phase reads (balance sums, Hessian), and to zero the p, q gradient
-    const bool run_branch = (phases & 1) && (C || J || H || G) && M.nbr_items > 0;
+    const bool run_branch = (phases & 1) && (C || J || H || P.want_grad) && M.nbr_items > 0;
     const bool run_bus = phases & 2;
-    const int bb = L.branch_block, bu = L.bus_block;
+    const bool one = M.ninst == 1;
+    const int bb = L.branch_block;
     cudaError_t e;
     switch ((C ? 1 : 0) | (J ? 2 : 0) | (H ? 4 : 0)) {
-    case 0: e = dispatch<false, false, false>(P, G, O, run_branch, run_bus, gb, bb, gu, bu, s); break;
-    case 1: e = dispatch<true, false, false>(P, G, O, run_branch, run_bus, gb, bb, gu, bu, s); break;
-    case 2: e = dispatch<false, true, false>(P, G, O, run_branch, run_bus, gb, bb, gu, bu, s); break;
-    case 3: e = dispatch<true, true, false>(P, G, O, run_branch, run_bus, gb, bb, gu, bu, s); break;
-    case 4: e = dispatch<false, false, true>(P, G, O, run_branch, run_bus, gb, bb, gu, bu, s); break;
-    case 5: e = dispatch<true, false, true>(P, G, O, run_branch, run_bus, gb, bb, gu, bu, s); break;
-    case 6: e = dispatch<false, true, true>(P, G, O, run_branch, run_bus, gb, bb, gu, bu, s); break;
-    default: e = dispatch<true, true, true>(P, G, O, run_branch, run_bus, gb, bb, gu, bu, s); break;
+    case 0: e = dispatch<false, false, false>(P, one, run_branch, run_bus, gb, bb, gu, bu, s); break;
+    case 1: e = dispatch<true, false, false>(P, one, run_branch, run_bus, gb, bb, gu, bu, s); break;
+    case 2: e = dispatch<false, true, false>(P, one, run_branch, run_bus, gb, bb, gu, bu, s); break;
+    case 3: e = dispatch<true, true, false>(P, one, run_branch, run_bus, gb, bb, gu, bu, s); break;
+    case 4: e = dispatch<false, false, true>(P, one, run_branch, run_bus, gb, bb, gu, bu, s); break;
+    case 5: e = dispatch<true, false, true>(P, one, run_branch, run_bus, gb, bb, gu, bu, s); break;
+    case 6: e = dispatch<false, true, true>(P, one, run_branch, run_bus, gb, bb, gu, bu, s); break;
+    default: e = dispatch<true, true, true>(P, one, run_branch, run_bus, gb, bb, gu, bu, s); break;
     }
     if (e == cudaSuccess)
         e = cudaGetLastError();
@@ -643,50 +792,27 @@ int launch_eval(Model &M, const EvalArgs &a, unsigned what, cudaStream_t s, int 
     return OPF_OK;
 }
 
+}  // namespace
+
+int launch_eval(Model &M, const EvalArgs &a, unsigned what, cudaStream_t s, int phases)
+{
+    return launch_all(M, a, what, s, phases, M.d.arcs, M.d.obj_part, M.max_part, M.d.ticket);
+}
+
 // The fused evaluation with caller-chosen scratch (arc slots, objective
 // partials, block counter) in place of the model's own; used by
 // opf_eval_all_noalloc. Same kernels and launch shape as launch_eval.
 int launch_eval_scratch(Model &M, const EvalArgs &a, unsigned what, cudaStream_t s,
                         ArcScratch *arcs, double *obj_part, int max_part, unsigned int *ticket)
 {
-    KParams P;
-    P.d = M.d;
-    P.d.arcs = arcs;
-    P.d.obj_part = obj_part;
-    P.d.ticket = ticket;
-    P.ninst = M.ninst;
-    P.nbr_items = M.nbr_items;
-    P.nbus_items = M.nbus_items;
-    P.ngen_items = M.ngen_items;
-    P.x = a.x;
-    P.lam = a.lam;
-    P.sigma = a.sigma;
-    P.obj = a.obj;
-    P.grad = a.grad;
-    P.c = a.c;
-    P.jac = a.jac;
-    P.hess = a.hess;
-    const bool C = what & W_CONS, J = what & W_JAC, H = what & W_HESS;
-    const bool G = what & W_GRAD, O = what & W_OBJ;
-    const opf_launch &L = M.launch;
-    const int gb = grid_for(M.nbr_items, L.branch_block, L.branch_ctas_per_sm, M.num_sms, 0);
-    const int cap = max_part < M.max_part ? max_part : M.max_part;
-    const int gu = grid_for(M.nbus_items + M.ngen_items, L.bus_block, L.bus_ctas_per_sm, M.num_sms, cap);
-    const bool run_branch = (C || J || H || G) && M.nbr_items > 0;
-    const int bb = L.branch_block, bu = L.bus_block;
-    cudaError_t e;
-    switch ((C ? 1 : 0) | (J ? 2 : 0) | (H ? 4 : 0)) {
-    case 0: e = dispatch<false, false, false>(P, G, O, run_branch, true, gb, bb, gu, bu, s); break;
-    case 1: e = dispatch<true, false, false>(P, G, O, run_branch, true, gb, bb, gu, bu, s); break;
-    case 2: e = dispatch<false, true, false>(P, G, O, run_branch, true, gb, bb, gu, bu, s); break;
-    case 3: e = dispatch<true, true, false>(P, G, O, run_branch, true, gb, bb, gu, bu, s); break;
-    case 4: e = dispatch<false, false, true>(P, G, O, run_branch, true, gb, bb, gu, bu, s); break;
-    case 5: e = dispatch<true, false, true>(P, G, O, run_branch, true, gb, bb, gu, bu, s); break;
-    case 6: e = dispatch<false, true, true>(P, G, O, run_branch, true, gb, bb, gu, bu, s); break;
-    default: e = dispatch<true, true, true>(P, G, O, run_branch, true, gb, bb, gu, bu, s); break;
-    }
-    if (e == cudaSuccess)
-        e = cudaGetLastError();
+    return launch_all(M, a, what, s, 3, arcs, obj_part, max_part, ticket);
+}
+
+int launch_sincos(Model &M, const double *d, int64_t n, double *sn, double *cs, cudaStream_t s)
+{
+    const int grid = grid_for(n, 256, 8, M.num_sms, 0);
+    sincos_tab_kernel<<<grid, 256, 0, s>>>(M.d.trig, d, n, sn, cs);
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         set_error("kernel launch failed: %s", cudaGetErrorString(e));
         return OPF_ECUDA;

@@ -25,13 +25,18 @@ struct __align__(16) ArcScratch {
     double p, q, d_aa, d_ma, d_mm, x_mm;
 };
 
+// Table of the table-driven sine/cosine of the branch kernel: (sin, cos) at
+// k / kTrigScale for |k| <= kTrigK, which covers |d| <= pi.
+constexpr int kTrigScale = 128;
+constexpr int kTrigK = 402;
+
 // slot codes: the slot closes its far bus's group / the far bus is lower
 enum : uint8_t { SLOT_LAST = 1u, SLOT_LOWER = 2u };
 
 // One instance of a batch, as seen by the kernels. Offsets are absolute
 // positions in the caller's x / g / Jacobian / Hessian arrays and in the
 // model's concatenated network arrays.
-struct InstDev {
+struct __align__(16) InstDev {
     int32_t nb, nl, ng, T;
     int32_t ref;        // local reference bus
     int32_t ramp;       // ramp rows present
@@ -40,6 +45,7 @@ struct InstDev {
     int32_t gen0;       // first generator
     int32_t gl0;        // first entry of this instance's bus->generator list
     int32_t slot0;      // first slot code of this instance (2 nl per instance)
+    int32_t pad0;
     int64_t x0, c0, j0, h0;
     int64_t scr0;       // first arc-scratch slot (2 nl T slots per instance)
     int64_t pd0;        // first entry of per-bus demand [T][nb]
@@ -48,18 +54,25 @@ struct InstDev {
     int64_t link_c, link_j;  // this instance's linking rows and their Jacobian offset; -1 if none
     int64_t link_x0;    // first pg of instance 0 (linking partner)
 };
+static_assert(sizeof(InstDev) % 16 == 0, "InstDev is loaded as int4 words");
 
 struct DevArrays {
     // branches (concatenated over instances)
     int4 *br = nullptr;           // local (f, t, slot of the from-arc, slot of the to-arc)
+    int2 *br_jb = nullptr;        // entries of the from-arc and to-arc in their buses' balance
+                                  // rows, inside one period's balance-row group
     double2 *y_ff = nullptr, *y_ft = nullptr, *y_tf = nullptr, *y_tt = nullptr;  // (G, B)
     double *rate2 = nullptr;      // rate_a^2
     // buses
+    int32_t *bus_order = nullptr; // bus-phase processing order: buses grouped by slot count
     int4 *bus_a = nullptr;        // (first slot, end slot, first gen entry, end gen entry)
     int4 *bus_b = nullptr;        // (balance-row offset, va-row offset, vm-row offset,
                                   //  distinct far buses | lower ones << 16) inside one period
+    int2 *bus_c = nullptr;        // (bit j: slot j closes its group of parallel arcs, for
+                                  //  buses with <= 32 slots; slots whose far bus is lower)
     double2 *gsbs = nullptr;      // (gs, bs)
-    uint8_t *slot_code = nullptr; // per slot: SLOT_LAST / SLOT_LOWER
+    uint8_t *slot_code = nullptr; // per slot: SLOT_LAST / SLOT_LOWER (buses with > 32 slots)
+    double2 *trig = nullptr;      // (sin, cos) of k / kTrigScale, k = -kTrigK..kTrigK
     int32_t *gen_list = nullptr;  // local generator ids, ascending per bus
     double *Pd = nullptr, *Qd = nullptr;  // demand per bus and period
     // generators
@@ -122,6 +135,7 @@ struct EvalArgs {
 // kernels.cu
 int launch_eval(Model &M, const EvalArgs &a, unsigned what, cudaStream_t s, int phases = 3);
 int launch_flat_start(Model &M, double *x, cudaStream_t s);
+int launch_sincos(Model &M, const double *d, int64_t n, double *sn, double *cs, cudaStream_t s);
 
 // abi.cu
 void set_error(const char *fmt, ...);

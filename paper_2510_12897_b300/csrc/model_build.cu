@@ -40,8 +40,11 @@ int validate(const opf_network &n, int s)
         return OPF_EINVAL;
     }
     int64_t nb = n.nbus, nl = n.nbranch, ng = n.ngen;
-    if ((int64_t)n.nperiod * (4 * nl + 2 * nb + 2 * ng) > INT32_MAX / 2) {
-        set_error("instance %d: too large for 32-bit in-instance indices", s);
+    // every in-instance offset (variables, rows, Jacobian and Hessian values,
+    // scratch slots) must fit in 32 bits; the Jacobian is the largest
+    if ((int64_t)n.nperiod * (1 + 30 * nl + 2 * nb + 4 * ng) > INT32_MAX / 2 ||
+        (int64_t)n.nperiod * (2 * nb + 2 * ng + 4 * nl + 10 * nl + 2 * nb) > INT32_MAX / 2) {
+        set_error("instance %d: too large for 32-bit in-instance offsets", s);
         return OPF_EINVAL;
     }
     for (int k = 0; k < n.nbranch; k++) {
@@ -181,6 +184,8 @@ int build_model(const opf_network *nets, int32_t ninst, double link_ratio, bool 
 
     // concatenated host arrays
     std::vector<int4> br, bus_a, bus_b;
+    std::vector<int2> bus_c, br_jb;
+    std::vector<int32_t> bus_order;
     std::vector<double2> y_ff, y_ft, y_tf, y_tt, gsbs, pbnd, qbnd, vbnd;
     std::vector<double> rate2, Pd, Qd, c2, c1, c0;
     std::vector<int32_t> gen_list;
@@ -281,9 +286,12 @@ int build_model(const opf_network *nets, int32_t ninst, double link_ratio, bool 
 
         // ---- per-bus row offsets inside one period, slot codes
         int64_t jsum = 0, hva = 0, hvm = 0;
+        std::vector<int32_t> jp_local(nb);
         for (int i = 0; i < nb; i++) {
+            jp_local[i] = (int32_t)jsum;
             int p0 = H.arc_ptr[i], p1 = H.arc_ptr[i + 1];
-            int nd = 0, nlt = 0;
+            int nd = 0, nlt = 0, nlow = 0;
+            uint32_t lastmask = 0;
             for (int p = p0; p < p1; p++) {
                 bool first = p == p0 || H.slot_nbr[p] != H.slot_nbr[p - 1];
                 bool last = p + 1 == p1 || H.slot_nbr[p + 1] != H.slot_nbr[p];
@@ -293,6 +301,10 @@ int build_model(const opf_network *nets, int32_t ninst, double link_ratio, bool 
                         nlt++;
                 }
                 slot_code.push_back((uint8_t)((last ? SLOT_LAST : 0) | (H.slot_nbr[p] < i ? SLOT_LOWER : 0)));
+                if (last && p - p0 < 32)
+                    lastmask |= 1u << (p - p0);
+                if (H.slot_nbr[p] < i)
+                    nlow++;
             }
             if (nd > 0x7fff) {
                 set_error("instance %d: bus %d has more than 32767 distinct neighbours", s, i);
@@ -301,6 +313,7 @@ int build_model(const opf_network *nets, int32_t ninst, double link_ratio, bool 
             }
             bus_a.push_back(make_int4(p0, p1, H.gen_ptr[i], H.gen_ptr[i + 1]));
             bus_b.push_back(make_int4((int32_t)jsum, (int32_t)hva, (int32_t)hvm, nd | (nlt << 16)));
+            bus_c.push_back(make_int2((int32_t)lastmask, nlow));
             jsum += 1 + (H.gen_ptr[i + 1] - H.gen_ptr[i]) + (p1 - p0);
             if (p1 > p0) {
                 hva += nlt + 1;
@@ -311,6 +324,34 @@ int build_model(const opf_network *nets, int32_t ninst, double link_ratio, bool 
             double gsv = n.bus_gs ? n.bus_gs[i] : 0.0, bsv = n.bus_bs ? n.bus_bs[i] : 0.0;
             gsbs.push_back(make_double2(gsv, bsv));
             vbnd.push_back(make_double2(n.bus_vmin[i], n.bus_vmax[i]));
+        }
+
+        // ---- each arc's +1 entry in its bus's balance row: after the vm entry
+        // and the bus's generators, arcs in ascending id
+        {
+            std::vector<int32_t> jb(na);
+            std::vector<int32_t> ids;
+            for (int i = 0; i < nb; i++) {
+                ids.assign(H.slot_arc.begin() + H.arc_ptr[i], H.slot_arc.begin() + H.arc_ptr[i + 1]);
+                std::sort(ids.begin(), ids.end());
+                const int base = jp_local[i] + 1 + (H.gen_ptr[i + 1] - H.gen_ptr[i]);
+                for (size_t r = 0; r < ids.size(); r++)
+                    jb[ids[r]] = base + (int32_t)r;
+            }
+            for (int k = 0; k < nl; k++)
+                br_jb.push_back(make_int2(jb[k], jb[nl + k]));
+        }
+        // ---- bus-phase order: buses grouped by slot count (up to 9), so the
+        // threads of a warp walk the same number of slots
+        {
+            std::vector<int32_t> ord(nb);
+            std::iota(ord.begin(), ord.end(), 0);
+            std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
+                int da = std::min(H.arc_ptr[a + 1] - H.arc_ptr[a], 9);
+                int db = std::min(H.arc_ptr[b + 1] - H.arc_ptr[b], 9);
+                return da < db;
+            });
+            bus_order.insert(bus_order.end(), ord.begin(), ord.end());
         }
 
         // ---- demand per bus and period
@@ -386,7 +427,12 @@ int build_model(const opf_network *nets, int32_t ninst, double link_ratio, bool 
     if (!rc)                                     \
         rc = upload(*M, &d.field, vec);
     UP(br, br) UP(y_ff, y_ff) UP(y_ft, y_ft) UP(y_tf, y_tf) UP(y_tt, y_tt) UP(rate2, rate2)
-    UP(bus_a, bus_a) UP(bus_b, bus_b) UP(gsbs, gsbs) UP(slot_code, slot_code) UP(gen_list, gen_list)
+    std::vector<double2> trig;
+    for (int k = -kTrigK; k <= kTrigK; k++)
+        trig.push_back(make_double2(std::sin((double)k / kTrigScale), std::cos((double)k / kTrigScale)));
+    UP(trig, trig)
+    UP(br_jb, br_jb) UP(bus_order, bus_order)
+    UP(bus_a, bus_a) UP(bus_b, bus_b) UP(bus_c, bus_c) UP(gsbs, gsbs) UP(slot_code, slot_code) UP(gen_list, gen_list)
     UP(Pd, Pd) UP(Qd, Qd) UP(c2, c2) UP(c1, c1) UP(c0, c0) UP(pbnd, pbnd) UP(qbnd, qbnd)
     UP(vbnd, vbnd) UP(inst, M->inst) UP(br_items, br_items) UP(bus_items, bus_items)
     UP(gen_items, gen_items)

@@ -90,6 +90,7 @@ def lib():
         "opf_eval_all_noalloc": [_vp, _vp, _vp, ctypes.c_double, _vp, _vp, _vp, _vp, _vp, _vp],
         "opf_eval_all_host": [_vp, _vp, _vp, ctypes.c_double, _vp, _vp, _vp, _vp, _vp, _vp],
         "opf_flat_start": [_vp, _vp, _vp],
+        "opf_sincos": [_vp, _vp, ctypes.c_int64, _vp, _vp, _vp],
         "opf_get_launch": [_vp, ctypes.POINTER(OpfLaunch)],
         "opf_set_launch": [_vp, ctypes.POINTER(OpfLaunch)],
         "opf_autotune": [_vp, _vp, _vp, ctypes.c_int32, _vp, ctypes.POINTER(OpfLaunch), _f64p],
@@ -289,6 +290,11 @@ class Model:
 
     def flat_start(self, x, stream=None):
         _check(lib().opf_flat_start(self.h, _ptr(x, self.n, "x"), _stream(stream)))
+
+    def sincos(self, d, sn, cs, stream=None):
+        n = d.numel()
+        _check(lib().opf_sincos(self.h, _ptr(d, n, "angles"), n, _ptr(sn, n, "sin"), _ptr(cs, n, "cos"),
+                                _stream(stream)))
 
     def get_launch(self) -> dict:
         cfg = OpfLaunch()

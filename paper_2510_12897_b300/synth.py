@@ -245,6 +245,15 @@ def multi_period(g: Grid, nperiod: int, seed: int, ramp_ratio: float = 0.2,
     return g.copy(load_pd=pd, load_qd=qd, ramp_ratio=float(ramp_ratio))
 
 
+def scenarios(g: Grid, count: int, seed: int, low: float = 0.8, high: float = 1.2) -> Grid:
+    """``count`` load scenarios of ``g`` as the periods of one model without
+    ramp rows: scenario s scales every load by its own U(low, high) factor."""
+    rng = np.random.default_rng(seed + 31337)
+    scale = rng.uniform(low, high, count)[:, None]
+    return g.copy(load_pd=g.load_pd[0][None, :] * scale, load_qd=g.load_qd[0][None, :] * scale,
+                  ramp_ratio=0.0)
+
+
 def bridges(nbus: int, f: np.ndarray, t: np.ndarray) -> np.ndarray:
     """Boolean mask of bridge branches (iterative Tarjan low-link)."""
     nl = len(f)

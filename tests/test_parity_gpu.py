@@ -276,3 +276,39 @@ def test_sc1k_501_full(torch, oracle_mod):
     M, O = both(torch, oracle_mod, insts, link=0.2)
     x, lam = next(points(insts, M.m, 1, seed=12))
     check_against_oracle(O, run_all(torch, M, x, lam, 1.0), x, lam, 1.0)
+
+
+# ------------------------------------------------ trig and large angles --
+
+def test_table_sincos_against_cuda(torch):
+    """The branch kernel's table-driven sine and cosine against CUDA's
+    double-precision sin and cos (through torch) and the host libm, on
+    angles across and beyond the table: absolute error below 4e-16."""
+    M = opf.Model(synth.case30())
+    rng = np.random.default_rng(3)
+    ang = np.concatenate([rng.uniform(-3.2, 3.2, 200_000), rng.uniform(-50, 50, 20_000),
+                          np.arange(-402, 403) / 128.0, (np.arange(-402, 402) + 0.5) / 128.0,
+                          [0.0, -0.0, 1e-300, -1e-300, np.pi, -np.pi]])
+    d = dev(torch, ang)
+    sn = torch.empty_like(d)
+    cs = torch.empty_like(d)
+    M.sincos(d, sn, cs)
+    torch.cuda.synchronize()
+    s_ref = torch.sin(d).cpu().numpy()
+    c_ref = torch.cos(d).cpu().numpy()
+    assert np.max(np.abs(host(sn) - s_ref)) < 4e-16
+    assert np.max(np.abs(host(cs) - c_ref)) < 4e-16
+    assert np.max(np.abs(host(sn) - np.sin(ang))) < 4e-16
+    assert np.max(np.abs(host(cs) - np.cos(ang))) < 4e-16
+
+
+def test_large_angle_differences(torch, oracle_mod):
+    """Angle differences beyond +-pi take the fallback path of the branch
+    kernel's sine/cosine; parity must hold there too."""
+    g = synth.case30(general=True)
+    M, O = both(torch, oracle_mod, g)
+    rng = np.random.default_rng(41)
+    x = synth.random_point(g, rng)
+    x[:g.nbus] = rng.uniform(-6.0, 6.0, g.nbus)
+    lam = rng.standard_normal(M.m)
+    check_against_oracle(O, run_all(torch, M, x, lam, 1.0), x, lam, 1.0)
