@@ -202,6 +202,24 @@ int opf_eval_all_noalloc(opf_model *model, const double *d_x, const double *d_la
                          double obj_weight, double *d_obj, double *d_grad, double *d_c,
                          double *d_jvals, double *d_hvals, void *stream);
 
+/* Jacobian-transpose product d_out (n) = J(x)^T d_v (d_v has m entries),
+ * evaluated term by term like the Hessian (no Jacobian values needed):
+ * NLPModels' jtprod!, the companion of Listing 1's jac!. Deterministic. */
+int opf_eval_jtprod(opf_model *model, const double *d_x, const double *d_v, double *d_out,
+                    void *stream);
+
+/* Sets the p and q entries of d_x (n) to the branch flows at d_x's voltage
+ * magnitudes and angles (the pi-model of Listing 3), so every flow row is
+ * zero; the other entries are left as they are. */
+int opf_eval_flows(opf_model *model, double *d_x, void *stream);
+
+/* Replaces the model's loads on the device: d_load_pd, d_load_qd hold each
+ * instance's [nperiod][nload] values (instances concatenated, in creation
+ * order). The demand of each bus and period becomes the sum of its loads in
+ * ascending load order, exactly as at creation. Asynchronous on stream;
+ * later evaluations on that stream see the new loads. */
+int opf_set_loads(opf_model *model, const double *d_load_pd, const double *d_load_qd, void *stream);
+
 /* Flat start (reading of the usual OPF initial point): va = 0, vm = 1
  * clipped into [vmin, vmax], pg and qg at the midpoint of their bounds,
  * p and q equal to the branch flows at those voltages. Into d_x (n). */

@@ -345,6 +345,42 @@ int opf_sincos(opf_model *m, const double *d_angle, int64_t n, double *d_sin, do
     return launch_sincos(*m->M, d_angle, n, d_sin, d_cos, static_cast<cudaStream_t>(stream));
 }
 
+int opf_eval_jtprod(opf_model *m, const double *d_x, const double *d_v, double *d_out, void *stream)
+{
+    int rc = check_dev(m);
+    if (rc)
+        return rc;
+    if (!d_x || !d_v || !d_out) {
+        set_error("opf_eval_jtprod: d_x, d_v and d_out are required");
+        return OPF_EINVAL;
+    }
+    return launch_jtprod(*m->M, d_x, d_v, d_out, static_cast<cudaStream_t>(stream));
+}
+
+int opf_eval_flows(opf_model *m, double *d_x, void *stream)
+{
+    int rc = check_dev(m);
+    if (rc)
+        return rc;
+    if (!d_x) {
+        set_error("opf_eval_flows: d_x is NULL");
+        return OPF_EINVAL;
+    }
+    return launch_flows(*m->M, d_x, static_cast<cudaStream_t>(stream));
+}
+
+int opf_set_loads(opf_model *m, const double *d_load_pd, const double *d_load_qd, void *stream)
+{
+    int rc = check_dev(m);
+    if (rc)
+        return rc;
+    if (m->M->nload_total > 0 && (!d_load_pd || !d_load_qd)) {
+        set_error("opf_set_loads: d_load_pd and d_load_qd are required");
+        return OPF_EINVAL;
+    }
+    return launch_set_loads(*m->M, d_load_pd, d_load_qd, static_cast<cudaStream_t>(stream));
+}
+
 int opf_get_launch(const opf_model *m, opf_launch *cfg)
 {
     int rc = check(m);

@@ -53,6 +53,8 @@ struct KParams {
     DevArrays d;
     InstDev inst0;  // instance 0: the only one when ninst == 1
     int32_t ninst;
+    int32_t link;       // linking rows present (J^T v of instance 0's generators)
+    int64_t link_c0;    // first linking row
     int32_t want_grad, want_obj;
     int64_t nbr_items, nbus_items, ngen_items;
     const double *__restrict__ x;
@@ -635,6 +637,244 @@ __global__ void __launch_bounds__(kBusBlockMax) bus_kernel(const KParams P)
     }
 }
 
+// ---------------------------------------------------------------- J^T v --
+//
+// out = J^T v, term by term (no Jacobian stored). Branch phase: the flow,
+// angle and thermal rows of a branch give the p, q entries of its two arcs
+// completely (with the +v of the arcs' balance rows) and their va, vm parts
+// for the end buses, stored in the first 16 bytes of the arc's scratch
+// record. Bus phase: va_i, vm_i sum their slots in a fixed order and add the
+// reference and balance-row terms; generator items take their balance,
+// ramp and linking rows.
+
+template <bool ONE>
+__global__ void __launch_bounds__(512) jt_branch_kernel(const KParams P)
+{
+    cudaTriggerProgrammaticLaunchCompletion();
+    const DevArrays &d = P.d;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int s = 0, t = 0, k = 0, kb = 0;
+    BrStatic st{};
+    auto locate = [&](int64_t item) {
+        if (ONE) {
+            s = 0;
+            split((int)item, P.inst0.nl, P.inst0.T, t, k);
+            kb = k;
+        } else {
+            s = find_inst(d.br_items, P.ninst, item);
+            const InstDev *I = d.inst + s;
+            split((int)(item - __ldg(d.br_items + s)), __ldg(&I->nl), __ldg(&I->T), t, k);
+            kb = __ldg(&I->br0) + k;
+        }
+    };
+    if (it < P.nbr_items) {
+        locate(it);
+        st = load_br(d, kb, false, false);
+    }
+    cudaGridDependencySynchronize();
+    for (; it < P.nbr_items; it += stride) {
+        const BrStatic cur = st;
+        const int cs = s, ct = t, ck = k;
+        if (it + stride < P.nbr_items) {
+            locate(it + stride);
+            st = load_br(d, kb, false, false);
+        }
+        const InstDev I = inst_of<ONE>(P, cs);
+        const int nl = I.nl, nb = I.nb, ng = I.ng, T = I.T;
+        const int nbT = nb * T, ngT = ng * T, nlT = nl * T, na = 2 * nl;
+        const int rk = ck + nl * ct;
+        const int f = cur.br.x, b = cur.br.y;
+        const double *__restrict__ xs = P.x + I.x0;
+        const int iva = nb * ct, ivm = nbT + nb * ct;
+        const int ip = 2 * nbT + 2 * ngT + na * ct, iq = ip + na * T;
+        const double vaf = __ldg(xs + iva + f), vat = __ldg(xs + iva + b);
+        const double vmf = __ldg(xs + ivm + f), vmt = __ldg(xs + ivm + b);
+        const double pf = __ldg(xs + ip + ck), pt = __ldg(xs + ip + nl + ck);
+        const double qf = __ldg(xs + iq + ck), qt = __ldg(xs + iq + nl + ck);
+        const double *V = P.lam + I.c0 + (T + rk);  // the vector v, indexed like the rows
+        const double m1 = __ldg(V), m2 = __ldg(V + nlT), m3 = __ldg(V + 2 * nlT), m4 = __ldg(V + 3 * nlT);
+        const double va_ = __ldg(V + 4 * nlT);
+        const double tf = __ldg(V + (5 * nlT + 2 * nbT)), tt = __ldg(V + (6 * nlT + 2 * nbT));
+        const double *VB = P.lam + I.c0 + (T + 5 * nlT + nb * ct);  // balance rows, period ct
+        const double bPf = __ldg(VB + f), bPt = __ldg(VB + b);
+        const double bQf = __ldg(VB + nbT + f), bQt = __ldg(VB + nbT + b);
+        const double2 Yff = cur.yff, Yft = cur.yft, Ytf = cur.ytf, Ytt = cur.ytt;
+        double sn, cs_;
+        sincos_tab(vaf - vat, d.trig, &sn, &cs_);
+        const double vft = vmf * vmt;
+        const double Aft = fma(Yft.x, cs_, Yft.y * sn);
+        const double Bft = fma(Yft.x, sn, neg(Yft.y * cs_));
+        const double Atf = fma(Ytf.x, cs_, neg(Ytf.y * sn));
+        const double Btf = neg(fma(Ytf.x, sn, Ytf.y * cs_));
+        // own variables: flow row, thermal row, balance row of the arc's bus
+        double *o = P.grad + I.x0;  // P.grad carries `out`
+        o[ip + ck] = fma(twice(pf), tf, m1 + bPf);
+        o[iq + ck] = fma(twice(qf), tf, m2 + bQf);
+        o[ip + nl + ck] = fma(twice(pt), tt, m3 + bPt);
+        o[iq + nl + ck] = fma(twice(qt), tt, m4 + bQt);
+        // va: the flow rows' angle derivatives are +-vft (B_ft, A_ft, B_tf,
+        // A_tf); the to-end gets exactly the negation of the from-end
+        const double dva = fma(m1, Bft, fma(neg(m2), Aft, fma(neg(m3), Btf, m4 * Atf)));
+        const double dva_f = fma(vft, dva, va_);
+        // vm
+        const double v2f = twice(vmf), v2t = twice(vmt);
+        const double dvm_f = fma(neg(m1), fma(Yff.x, v2f, vmt * Aft),
+                             fma(m2, fma(Yff.y, v2f, neg(vmt * Bft)),
+                                 neg(vmt * fma(m3, Atf, m4 * Btf))));
+        const double dvm_t = fma(neg(m3), fma(Ytt.x, v2t, vmf * Atf),
+                             fma(m4, fma(Ytt.y, v2t, neg(vmf * Btf)),
+                                 neg(vmf * fma(m1, Aft, m2 * Bft))));
+        ArcScratch *S = d.arcs + I.scr0 + na * ct;
+        reinterpret_cast<double2 *>(S + cur.br.z)[0] = make_double2(dva_f, dvm_f);
+        reinterpret_cast<double2 *>(S + cur.br.w)[0] = make_double2(neg(dva_f), dvm_t);
+    }
+}
+
+template <bool ONE>
+__global__ void __launch_bounds__(256) jt_bus_kernel(const KParams P)
+{
+    cudaTriggerProgrammaticLaunchCompletion();
+    cudaGridDependencySynchronize();
+    const DevArrays &d = P.d;
+    const int64_t total = P.nbus_items + P.ngen_items;
+    for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < total;
+         it += (int64_t)gridDim.x * blockDim.x) {
+        int s, t, e;
+        if (it < P.nbus_items) {
+            if (ONE) {
+                s = 0;
+                split((int)it, P.inst0.nb, P.inst0.T, t, e);
+            } else {
+                s = find_inst(d.bus_items, P.ninst, it);
+                split((int)(it - __ldg(d.bus_items + s)), __ldg(&d.inst[s].nb), __ldg(&d.inst[s].T), t, e);
+            }
+        } else {
+            const int64_t gi = it - P.nbus_items;
+            if (ONE) {
+                s = 0;
+                split((int)gi, P.inst0.ng, P.inst0.T, t, e);
+            } else {
+                s = find_inst(d.gen_items, P.ninst, gi);
+                split((int)(gi - __ldg(d.gen_items + s)), __ldg(&d.inst[s].ng), __ldg(&d.inst[s].T), t, e);
+            }
+        }
+        const InstDev I = inst_of<ONE>(P, s);
+        const int nl = I.nl, nb = I.nb, ng = I.ng, T = I.T;
+        const int nbT = nb * T, ngT = ng * T, nlT = nl * T, na = 2 * nl;
+        const double *__restrict__ xs = P.x + I.x0;
+        const double *V = P.lam + I.c0;
+        double *o = P.grad + I.x0;
+        if (it < P.nbus_items) {
+            const int i = e, ib = I.bus0 + i;
+            const int4 a = __ldg(d.bus_a + ib);
+            const double2 gb = __ldg(d.gsbs + ib);
+            const double vm = __ldg(xs + nbT + nb * t + i);
+            const double vP = __ldg(V + (T + 5 * nlT + nb * t + i)), vQ = __ldg(V + (T + 5 * nlT + nbT + nb * t + i));
+            const double2 *Sg = reinterpret_cast<const double2 *>(d.arcs + I.scr0 + (int64_t)na * t + a.x);
+            double dva = i == I.ref ? __ldg(V + t) : 0.0;
+            double dvm = twice(vm * fma(gb.x, vP, neg(gb.y * vQ)));  // 2 vm (gs vP - bs vQ)
+            for (int q = 0; q < a.y - a.x; q++) {
+                const double2 w = __ldcg(Sg + 3 * q);
+                dva += w.x;
+                dvm += w.y;
+            }
+            o[nb * t + i] = dva;
+            o[nbT + nb * t + i] = dvm;
+        } else {
+            const int g = e;
+            const int bus = __ldg(d.gen_busid + I.gen0 + g);
+            double vpg = neg(__ldg(V + (T + 5 * nlT + nb * t + bus)));
+            const double vqg = neg(__ldg(V + (T + 5 * nlT + nbT + nb * t + bus)));
+            if (I.ramp) {  // rows pg_t - pg_{t-1}, t = 1..T-1
+                const int rb = T + 7 * nlT + 2 * nbT;
+                if (t >= 1)
+                    vpg += __ldg(V + (rb + g + ng * (t - 1)));
+                if (t + 1 <= T - 1)
+                    vpg -= __ldg(V + (rb + g + ng * t));
+            }
+            if (I.link_c >= 0)  // rows pg_s - pg_0 of instance s >= 1
+                vpg += __ldg(P.lam + I.link_c + g);
+            if (P.link && s == 0)  // instance 0 appears in every linking row
+                for (int q = 1; q < P.ninst; q++)
+                    vpg -= __ldg(P.lam + P.link_c0 + g + (int64_t)ng * (q - 1));
+            o[2 * nbT + ng * t + g] = vpg;
+            o[2 * nbT + ngT + ng * t + g] = vqg;
+        }
+    }
+}
+
+// p, q of every arc := the flows at the point's voltages (flow rows exactly
+// zero), one thread per branch item.
+template <bool ONE>
+__global__ void flows_kernel(const KParams P, double *x)
+{
+    const DevArrays &d = P.d;
+    for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < P.nbr_items;
+         it += (int64_t)gridDim.x * blockDim.x) {
+        int s, t, k, kb;
+        if (ONE) {
+            s = 0;
+            split((int)it, P.inst0.nl, P.inst0.T, t, k);
+            kb = k;
+        } else {
+            s = find_inst(d.br_items, P.ninst, it);
+            split((int)(it - __ldg(d.br_items + s)), __ldg(&d.inst[s].nl), __ldg(&d.inst[s].T), t, k);
+            kb = __ldg(&d.inst[s].br0) + k;
+        }
+        const InstDev I = inst_of<ONE>(P, s);
+        const int nl = I.nl, nb = I.nb, ng = I.ng, T = I.T;
+        const int nbT = nb * T, ngT = ng * T, na = 2 * nl;
+        const BrStatic br = load_br(d, kb, false, false);
+        double *xs = x + I.x0;
+        const int iva = nb * t, ivm = nbT + nb * t;
+        const int ip = 2 * nbT + 2 * ngT + na * t, iq = ip + na * T;
+        const double vaf = xs[iva + br.br.x], vat = xs[iva + br.br.y];
+        const double vmf = xs[ivm + br.br.x], vmt = xs[ivm + br.br.y];
+        double sn, cs_;
+        sincos_tab(vaf - vat, d.trig, &sn, &cs_);
+        const double vft = vmf * vmt;
+        const double Aft = fma(br.yft.x, cs_, br.yft.y * sn);
+        const double Bft = fma(br.yft.x, sn, neg(br.yft.y * cs_));
+        const double Atf = fma(br.ytf.x, cs_, neg(br.ytf.y * sn));
+        const double Btf = neg(fma(br.ytf.x, sn, br.ytf.y * cs_));
+        xs[ip + k] = fma(br.yff.x, vmf * vmf, vft * Aft);
+        xs[iq + k] = fma(neg(br.yff.y), vmf * vmf, vft * Bft);
+        xs[ip + nl + k] = fma(br.ytt.x, vmt * vmt, vft * Atf);
+        xs[iq + nl + k] = fma(neg(br.ytt.y), vmt * vmt, vft * Btf);
+    }
+}
+
+// Demand per bus and period from per-load values [T][nload] (instance-major):
+// the sum over the bus's loads in ascending id, as at model creation.
+template <bool ONE>
+__global__ void set_loads_kernel(const KParams P, const double *pd, const double *qd)
+{
+    const DevArrays &d = P.d;
+    for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < P.nbus_items;
+         it += (int64_t)gridDim.x * blockDim.x) {
+        int s, t, i;
+        if (ONE) {
+            s = 0;
+            split((int)it, P.inst0.nb, P.inst0.T, t, i);
+        } else {
+            s = find_inst(d.bus_items, P.ninst, it);
+            split((int)(it - __ldg(d.bus_items + s)), __ldg(&d.inst[s].nb), __ldg(&d.inst[s].T), t, i);
+        }
+        const InstDev I = inst_of<ONE>(P, s);
+        const int l0 = __ldg(d.load_ptr + I.lp0 + i), l1 = __ldg(d.load_ptr + I.lp0 + i + 1);
+        const double *ps = pd + I.ld0 + (int64_t)I.nload * t, *qs = qd + I.ld0 + (int64_t)I.nload * t;
+        double P_ = 0.0, Q_ = 0.0;
+        for (int q = l0; q < l1; q++) {
+            const int l = __ldg(d.load_list + I.ll0 + q);
+            P_ += ps[l];
+            Q_ += qs[l];
+        }
+        d.Pd[I.pd0 + (int64_t)I.nb * t + i] = P_;
+        d.Qd[I.pd0 + (int64_t)I.nb * t + i] = Q_;
+    }
+}
+
 // Flat start: va = 0, vm = clamp(1), pg, qg at mid-bounds, p, q = flows at
 // those voltages (d = 0: cos d = 1, sin d = 0).
 __global__ void flat_kernel(const DevArrays d, int32_t ninst, int64_t nbr_items, int64_t nbus_items,
@@ -747,6 +987,8 @@ int launch_all(Model &M, const EvalArgs &a, unsigned what, cudaStream_t s, int p
     P.d.ticket = ticket;
     P.inst0 = M.inst[0];
     P.ninst = M.ninst;
+    P.link = M.link ? 1 : 0;
+    P.link_c0 = M.link_c0;
     P.nbr_items = M.nbr_items;
     P.nbus_items = M.nbus_items;
     P.ngen_items = M.ngen_items;
@@ -818,6 +1060,77 @@ int launch_sincos(Model &M, const double *d, int64_t n, double *sn, double *cs, 
         return OPF_ECUDA;
     }
     return OPF_OK;
+}
+
+namespace {
+KParams base_params(Model &M)
+{
+    KParams P{};
+    P.d = M.d;
+    P.inst0 = M.inst[0];
+    P.ninst = M.ninst;
+    P.link = M.link ? 1 : 0;
+    P.link_c0 = M.link_c0;
+    P.nbr_items = M.nbr_items;
+    P.nbus_items = M.nbus_items;
+    P.ngen_items = M.ngen_items;
+    return P;
+}
+
+int launch_status()
+{
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error("kernel launch failed: %s", cudaGetErrorString(e));
+        return OPF_ECUDA;
+    }
+    return OPF_OK;
+}
+}  // namespace
+
+int launch_jtprod(Model &M, const double *x, const double *v, double *out, cudaStream_t s)
+{
+    KParams P = base_params(M);
+    P.x = x;
+    P.lam = v;
+    P.grad = out;
+    const int gb = grid_for(M.nbr_items, 128, 0, M.num_sms, 0);
+    const int gu = grid_for(M.nbus_items + M.ngen_items, 128, 0, M.num_sms, 0);
+    const bool one = M.ninst == 1;
+    cudaError_t e = cudaSuccess;
+    if (M.nbr_items > 0)
+        e = one ? launch_pdl(jt_branch_kernel<true>, gb, 128, s, P) : launch_pdl(jt_branch_kernel<false>, gb, 128, s, P);
+    if (e == cudaSuccess)
+        e = one ? launch_pdl(jt_bus_kernel<true>, gu, 128, s, P) : launch_pdl(jt_bus_kernel<false>, gu, 128, s, P);
+    if (e != cudaSuccess) {
+        set_error("kernel launch failed: %s", cudaGetErrorString(e));
+        return OPF_ECUDA;
+    }
+    return launch_status();
+}
+
+int launch_flows(Model &M, double *x, cudaStream_t s)
+{
+    if (M.nbr_items == 0)
+        return OPF_OK;
+    KParams P = base_params(M);
+    const int grid = grid_for(M.nbr_items, 128, 0, M.num_sms, 0);
+    if (M.ninst == 1)
+        flows_kernel<true><<<grid, 128, 0, s>>>(P, x);
+    else
+        flows_kernel<false><<<grid, 128, 0, s>>>(P, x);
+    return launch_status();
+}
+
+int launch_set_loads(Model &M, const double *pd, const double *qd, cudaStream_t s)
+{
+    KParams P = base_params(M);
+    const int grid = grid_for(M.nbus_items, 128, 0, M.num_sms, 0);
+    if (M.ninst == 1)
+        set_loads_kernel<true><<<grid, 128, 0, s>>>(P, pd, qd);
+    else
+        set_loads_kernel<false><<<grid, 128, 0, s>>>(P, pd, qd);
+    return launch_status();
 }
 
 int launch_flat_start(Model &M, double *x, cudaStream_t s)

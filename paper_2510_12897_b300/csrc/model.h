@@ -45,8 +45,12 @@ struct __align__(16) InstDev {
     int32_t gen0;       // first generator
     int32_t gl0;        // first entry of this instance's bus->generator list
     int32_t slot0;      // first slot code of this instance (2 nl per instance)
-    int32_t pad0;
+    int32_t nload;      // loads of this instance
+    int32_t lp0;        // first entry of this instance's bus->load pointers (nb + 1)
+    int32_t ll0;        // first entry of this instance's bus->load list
+    int32_t pad1, pad2;
     int64_t x0, c0, j0, h0;
+    int64_t ld0;        // first entry of this instance's loads in opf_set_loads arrays [T][nload]
     int64_t scr0;       // first arc-scratch slot (2 nl T slots per instance)
     int64_t pd0;        // first entry of per-bus demand [T][nb]
     int64_t jP;         // Jacobian entries of one period of the P-balance group (nb + ng + 2 nl)
@@ -75,7 +79,10 @@ struct DevArrays {
     double2 *trig = nullptr;      // (sin, cos) of k / kTrigScale, k = -kTrigK..kTrigK
     int32_t *gen_list = nullptr;  // local generator ids, ascending per bus
     double *Pd = nullptr, *Qd = nullptr;  // demand per bus and period
+    int32_t *load_ptr = nullptr;  // CSR bus -> loads, nb + 1 per instance
+    int32_t *load_list = nullptr; // local load ids, ascending per bus
     // generators
+    int32_t *gen_busid = nullptr; // local bus of each generator
     double *c2 = nullptr, *c1 = nullptr, *c0 = nullptr;
     double2 *pbnd = nullptr, *qbnd = nullptr;  // (min, max), flat start only
     double2 *vbnd = nullptr;                   // (vmin, vmax) per bus, flat start only
@@ -113,6 +120,7 @@ struct Model {
     int64_t n = 0, m = 0, nnzj = 0, nnzh = 0;
     int64_t link_c0 = 0, link_j0 = 0;  // first linking row / its first Jacobian value
     int64_t nbr_items = 0, nbus_items = 0, ngen_items = 0, narc_slots = 0;
+    int64_t nload_total = 0;      // sum over instances of nload * nperiod
     int32_t max_part = 0;         // capacity of obj_part
     int device = 0, num_sms = 148;
     opf_launch launch{};
@@ -136,6 +144,9 @@ struct EvalArgs {
 int launch_eval(Model &M, const EvalArgs &a, unsigned what, cudaStream_t s, int phases = 3);
 int launch_flat_start(Model &M, double *x, cudaStream_t s);
 int launch_sincos(Model &M, const double *d, int64_t n, double *sn, double *cs, cudaStream_t s);
+int launch_jtprod(Model &M, const double *x, const double *v, double *out, cudaStream_t s);
+int launch_flows(Model &M, double *x, cudaStream_t s);
+int launch_set_loads(Model &M, const double *pd, const double *qd, cudaStream_t s);
 
 // abi.cu
 void set_error(const char *fmt, ...);

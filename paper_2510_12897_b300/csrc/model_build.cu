@@ -188,7 +188,7 @@ int build_model(const opf_network *nets, int32_t ninst, double link_ratio, bool 
     std::vector<int32_t> bus_order;
     std::vector<double2> y_ff, y_ft, y_tf, y_tt, gsbs, pbnd, qbnd, vbnd;
     std::vector<double> rate2, Pd, Qd, c2, c1, c0;
-    std::vector<int32_t> gen_list;
+    std::vector<int32_t> gen_list, load_ptr, load_list, gen_busid;
     std::vector<uint8_t> slot_code;
     std::vector<int64_t> br_items(1, 0), bus_items(1, 0), gen_items(1, 0);
 
@@ -221,6 +221,11 @@ int build_model(const opf_network *nets, int32_t ninst, double link_ratio, bool 
         I.gen0 = (int32_t)c2.size();
         I.gl0 = (int32_t)gen_list.size();
         I.slot0 = (int32_t)slot_code.size();
+        I.nload = n.nload;
+        I.lp0 = (int32_t)load_ptr.size();
+        I.ll0 = (int32_t)load_list.size();
+        I.ld0 = M->nload_total;
+        M->nload_total += (int64_t)n.nload * T;
 
         // ---- branches: pi-model admittances (G, B) of Yff, Yft, Ytf, Ytt
         for (int k = 0; k < nl; k++) {
@@ -354,6 +359,19 @@ int build_model(const opf_network *nets, int32_t ninst, double link_ratio, bool 
             bus_order.insert(bus_order.end(), ord.begin(), ord.end());
         }
 
+        // ---- loads per bus (ascending id), the order the demand sums use
+        {
+            std::vector<int32_t> cnt(nb + 1, 0);
+            for (int l = 0; l < n.nload; l++)
+                cnt[n.load_bus[l] + 1]++;
+            for (int i = 0; i < nb; i++)
+                cnt[i + 1] += cnt[i];
+            std::vector<int32_t> fill(cnt.begin(), cnt.end() - 1), lst(n.nload);
+            for (int l = 0; l < n.nload; l++)
+                lst[fill[n.load_bus[l]]++] = l;
+            load_ptr.insert(load_ptr.end(), cnt.begin(), cnt.end());
+            load_list.insert(load_list.end(), lst.begin(), lst.end());
+        }
         // ---- demand per bus and period
         size_t pd_base = Pd.size();
         Pd.resize(pd_base + (size_t)nb * T, 0.0);
@@ -365,6 +383,7 @@ int build_model(const opf_network *nets, int32_t ninst, double link_ratio, bool 
             }
 
         for (int g = 0; g < ng; g++) {
+            gen_busid.push_back(n.gen_bus[g]);
             c2.push_back(n.gen_c2[g]);
             c1.push_back(n.gen_c1[g]);
             c0.push_back(n.gen_c0 ? n.gen_c0[g] : 0.0);
@@ -431,7 +450,8 @@ int build_model(const opf_network *nets, int32_t ninst, double link_ratio, bool 
     for (int k = -kTrigK; k <= kTrigK; k++)
         trig.push_back(make_double2(std::sin((double)k / kTrigScale), std::cos((double)k / kTrigScale)));
     UP(trig, trig)
-    UP(br_jb, br_jb) UP(bus_order, bus_order)
+    UP(br_jb, br_jb) UP(bus_order, bus_order) UP(load_ptr, load_ptr) UP(load_list, load_list)
+    UP(gen_busid, gen_busid)
     UP(bus_a, bus_a) UP(bus_b, bus_b) UP(bus_c, bus_c) UP(gsbs, gsbs) UP(slot_code, slot_code) UP(gen_list, gen_list)
     UP(Pd, Pd) UP(Qd, Qd) UP(c2, c2) UP(c1, c1) UP(c0, c0) UP(pbnd, pbnd) UP(qbnd, qbnd)
     UP(vbnd, vbnd) UP(inst, M->inst) UP(br_items, br_items) UP(bus_items, bus_items)

@@ -91,6 +91,9 @@ def lib():
         "opf_eval_all_host": [_vp, _vp, _vp, ctypes.c_double, _vp, _vp, _vp, _vp, _vp, _vp],
         "opf_flat_start": [_vp, _vp, _vp],
         "opf_sincos": [_vp, _vp, ctypes.c_int64, _vp, _vp, _vp],
+        "opf_eval_jtprod": [_vp, _vp, _vp, _vp, _vp],
+        "opf_eval_flows": [_vp, _vp, _vp],
+        "opf_set_loads": [_vp, _vp, _vp, _vp],
         "opf_get_launch": [_vp, ctypes.POINTER(OpfLaunch)],
         "opf_set_launch": [_vp, ctypes.POINTER(OpfLaunch)],
         "opf_autotune": [_vp, _vp, _vp, ctypes.c_int32, _vp, ctypes.POINTER(OpfLaunch), _f64p],
@@ -290,6 +293,18 @@ class Model:
 
     def flat_start(self, x, stream=None):
         _check(lib().opf_flat_start(self.h, _ptr(x, self.n, "x"), _stream(stream)))
+
+    def eval_jtprod(self, x, v, out, stream=None):
+        _check(lib().opf_eval_jtprod(self.h, _ptr(x, self.n, "x"), _ptr(v, self.m, "v"),
+                                     _ptr(out, self.n, "out"), _stream(stream)))
+
+    def eval_flows(self, x, stream=None):
+        _check(lib().opf_eval_flows(self.h, _ptr(x, self.n, "x"), _stream(stream)))
+
+    def set_loads(self, pd, qd, stream=None):
+        """pd, qd: float64 CUDA tensors holding every instance's [nperiod][nload]
+        loads, instances concatenated."""
+        _check(lib().opf_set_loads(self.h, _ptr(pd, None, "pd"), _ptr(qd, None, "qd"), _stream(stream)))
 
     def sincos(self, d, sn, cs, stream=None):
         n = d.numel()

@@ -312,3 +312,58 @@ def test_large_angle_differences(torch, oracle_mod):
     x[:g.nbus] = rng.uniform(-6.0, 6.0, g.nbus)
     lam = rng.standard_normal(M.m)
     check_against_oracle(O, run_all(torch, M, x, lam, 1.0), x, lam, 1.0)
+
+
+# ------------------------------------------------ J^T v, flows, loads --
+
+@pytest.mark.parametrize("which", ["case30g", "mp30", "batch30", "case10k"])
+def test_jtprod_against_oracle_jacobian(torch, oracle_mod, which):
+    """J^T v from the term-wise kernels equals the oracle's sparse Jacobian
+    transposed times v; tolerance from the Jacobian's entry scales."""
+    import scipy.sparse as sp
+    g = {"case30g": lambda: synth.case30(general=True),
+         "mp30": lambda: synth.multi_period(synth.case30(general=True), 4, seed=9, ramp_ratio=0.2),
+         "batch30": lambda: synth.contingencies(synth.case30(general=True), 5, seed=2),
+         "case10k": lambda: synth.case10k()}[which]()
+    link = 0.2 if which == "batch30" else 0.0
+    M, O = both(torch, oracle_mod, g, link=link)
+    x, v = next(points(g, M.m, 1, seed=13))
+    out = torch.full((M.n,), np.nan, dtype=torch.float64, device="cuda")
+    M.eval_jtprod(dev(torch, x), dev(torch, v), out)
+    torch.cuda.synchronize()
+    r, c = O.jac_pattern()
+    jv, js = O.jac(x, with_scale=True)
+    ref = sp.coo_matrix((jv, (r, c)), shape=(O.m, O.n)).T @ v
+    scale = sp.coo_matrix((js, (r, c)), shape=(O.m, O.n)).T @ np.abs(v)
+    close("jtprod", host(out), ref, scale)
+
+
+def test_flows_make_flow_rows_vanish(torch, oracle_mod):
+    g = synth.multi_period(synth.case30(general=True), 3, seed=4, ramp_ratio=0.2)
+    M, O = both(torch, oracle_mod, g)
+    x, _ = next(points(g, M.m, 1, seed=14))
+    dx = dev(torch, x)
+    M.eval_flows(dx)
+    torch.cuda.synchronize()
+    y = host(dx)
+    nb, ng, T = g.nbus, g.ngen, g.nperiod
+    np.testing.assert_array_equal(y[:2 * (nb + ng) * T], x[:2 * (nb + ng) * T])
+    c, s = O.cons(y, with_scale=True)
+    nl = g.nbranch
+    flows = slice(T, T + 4 * nl * T)
+    close("flow rows", c[flows], np.zeros(4 * nl * T), s[flows])
+
+
+def test_set_loads_matches_fresh_model(torch, oracle_mod):
+    g = synth.multi_period(synth.case30(general=True), 4, seed=6, ramp_ratio=0.2)
+    rng = np.random.default_rng(3)
+    g2 = g.copy(load_pd=g.load_pd * rng.uniform(0.7, 1.3, g.load_pd.shape),
+                load_qd=g.load_qd * rng.uniform(0.7, 1.3, g.load_qd.shape))
+    M = opf.Model(g)
+    M2 = opf.Model(g2)
+    M.set_loads(dev(torch, g2.load_pd), dev(torch, g2.load_qd))
+    x, lam = next(points(g, M.m, 1, seed=15))
+    a = run_all(torch, M, x, lam, 1.0)
+    b = run_all(torch, M2, x, lam, 1.0)
+    for k in a:
+        np.testing.assert_array_equal(a[k], b[k])
