@@ -1,0 +1,962 @@
+// Learned warm start (include/opf_warm.h): a three-layer BF16 MLP trained on
+// the GPU with hand-written tensor-core GEMMs, penalty gradients from the
+// library's own callback kernels (cons, grad, J^T v) and Adam.
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <random>
+#include <vector>
+
+#include "../../include/opf_warm.h"
+#include "model.h"
+
+namespace opf {
+int build_model(const opf_network *nets, int32_t ninst, double link_ratio, bool device, Model **out);
+void free_model(Model *M);
+void bounds(const Model &M, double *xl, double *xu, double *gl, double *gu);
+}  // namespace opf
+
+using bf16 = __nv_bfloat16;
+using namespace opf;
+
+namespace {
+
+// ------------------------------------------------------------------ GEMM --
+//
+// C[M x N] = A[M x K] * B[K x N] with BF16 operands and FP32 accumulation on
+// the tensor cores (mma.sync m16n8k16). A is stored K-contiguous ([M][lda],
+// AK) or M-contiguous ([K][lda]); B is stored K-contiguous ([N][ldb], BK) or
+// N-contiguous ([K][ldb]). Block tile 128 x 128 x 32, eight warps of 64 x 32,
+// two cp.async stages; ldmatrix (.trans for the contiguous-in-M/N layouts)
+// builds the fragments. M and N must be multiples of 128, K of 32, leading
+// dimensions multiples of 8 (16-byte rows for cp.async).
+
+constexpr int GBM = 128, GBN = 128, GBK = 32;
+constexpr int SK = GBK + 8;   // padded row of a K-contiguous tile (80 bytes)
+constexpr int SMN = GBM + 8;  // padded row of an M- or N-contiguous tile (272 bytes)
+
+enum Epi { EPI_BIAS_GELU, EPI_BIAS, EPI_DGELU, EPI_STORE };
+
+struct GemmArgs {
+    const bf16 *A, *B;
+    int M, N, K, lda, ldb, ldc;
+    int epi;
+    const float *bias;    // [N]
+    const float *zsaved;  // [M][ldc] pre-activations (EPI_DGELU)
+    float *outf;          // [M][ldc] FP32 output (pre-activation, linear output, gradient)
+    bf16 *outh;           // [M][ldc] BF16 output (activation, activation gradient)
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src));
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t r[4], const void *p)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(smem_u32(p)));
+}
+
+__device__ __forceinline__ void ldsm_x4_t(uint32_t r[4], const void *p)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(smem_u32(p)));
+}
+
+__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], const uint32_t b[2])
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// GELU, tanh form, and its derivative
+__device__ __forceinline__ float gelu(float z)
+{
+    const float k0 = 0.7978845608028654f, k1 = 0.044715f;
+    return 0.5f * z * (1.0f + tanhf(k0 * (z + k1 * z * z * z)));
+}
+
+__device__ __forceinline__ float gelu_grad(float z)
+{
+    const float k0 = 0.7978845608028654f, k1 = 0.044715f;
+    const float t = tanhf(k0 * (z + k1 * z * z * z));
+    return 0.5f * (1.0f + t) + 0.5f * z * (1.0f - t * t) * k0 * (1.0f + 3.0f * k1 * z * z);
+}
+
+template <bool AK, bool BK>
+__global__ void __launch_bounds__(256) gemm_kernel(const GemmArgs g)
+{
+    constexpr int ASZ = AK ? GBM * SK : GBK * SMN;
+    constexpr int BSZ = BK ? GBN * SK : GBK * SMN;
+    __shared__ __align__(16) bf16 As[2][ASZ];
+    __shared__ __align__(16) bf16 Bs[2][BSZ];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int wm = warp >> 2, wn = warp & 3;  // warp tile rows wm*64, cols wn*32
+    const int bm = blockIdx.y * GBM, bn = blockIdx.x * GBN;
+
+    auto load = [&](int stage, int k0) {
+#pragma unroll
+        for (int c = tid; c < 512; c += 256) {
+            if (AK) {
+                const int r = c >> 2, ch = c & 3;
+                cp_async16(&As[stage][r * SK + ch * 8], g.A + (size_t)(bm + r) * g.lda + k0 + ch * 8);
+            } else {
+                const int r = c >> 4, ch = c & 15;
+                cp_async16(&As[stage][r * SMN + ch * 8], g.A + (size_t)(k0 + r) * g.lda + bm + ch * 8);
+            }
+            if (BK) {
+                const int r = c >> 2, ch = c & 3;
+                cp_async16(&Bs[stage][r * SK + ch * 8], g.B + (size_t)(bn + r) * g.ldb + k0 + ch * 8);
+            } else {
+                const int r = c >> 4, ch = c & 15;
+                cp_async16(&Bs[stage][r * SMN + ch * 8], g.B + (size_t)(k0 + r) * g.ldb + bn + ch * 8);
+            }
+        }
+        asm volatile("cp.async.commit_group;\n" ::);
+    };
+
+    float acc[4][4][4];
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+#pragma unroll
+            for (int q = 0; q < 4; q++)
+                acc[i][j][q] = 0.f;
+
+    const int nk = g.K / GBK;
+    load(0, 0);
+    const int j8 = lane >> 3, r8 = lane & 7;
+    for (int kt = 0; kt < nk; kt++) {
+        if (kt + 1 < nk) {
+            load((kt + 1) & 1, (kt + 1) * GBK);
+            asm volatile("cp.async.wait_group 1;\n" ::);
+        } else {
+            asm volatile("cp.async.wait_group 0;\n" ::);
+        }
+        __syncthreads();
+        const bf16 *as = As[kt & 1], *bs = Bs[kt & 1];
+#pragma unroll
+        for (int kk = 0; kk < GBK; kk += 16) {
+            uint32_t a[4][4], b[4][2];
+#pragma unroll
+            for (int mi = 0; mi < 4; mi++) {
+                const int m0 = wm * 64 + mi * 16;
+                if (AK)
+                    ldsm_x4(a[mi], as + (m0 + (j8 & 1) * 8 + r8) * SK + kk + (j8 >> 1) * 8);
+                else
+                    ldsm_x4_t(a[mi], as + (kk + (j8 >> 1) * 8 + r8) * SMN + m0 + (j8 & 1) * 8);
+            }
+#pragma unroll
+            for (int nj = 0; nj < 2; nj++) {
+                const int n0 = wn * 32 + nj * 16;
+                uint32_t t4[4];
+                if (BK)
+                    ldsm_x4(t4, bs + (n0 + (j8 >> 1) * 8 + r8) * SK + kk + (j8 & 1) * 8);
+                else
+                    ldsm_x4_t(t4, bs + (kk + (j8 & 1) * 8 + r8) * SMN + n0 + (j8 >> 1) * 8);
+                b[2 * nj][0] = t4[0];
+                b[2 * nj][1] = t4[1];
+                b[2 * nj + 1][0] = t4[2];
+                b[2 * nj + 1][1] = t4[3];
+            }
+#pragma unroll
+            for (int mi = 0; mi < 4; mi++)
+#pragma unroll
+                for (int ni = 0; ni < 4; ni++)
+                    mma_bf16(acc[mi][ni], a[mi], b[ni]);
+        }
+        __syncthreads();
+    }
+
+    // epilogue: thread holds rows (lane/4, +8) and column pairs 2 (lane%4)
+#pragma unroll
+    for (int mi = 0; mi < 4; mi++)
+#pragma unroll
+        for (int ni = 0; ni < 4; ni++)
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int m = bm + wm * 64 + mi * 16 + (lane >> 2) + 8 * h;
+                const int n = bn + wn * 32 + ni * 8 + 2 * (lane & 3);
+                const size_t o = (size_t)m * g.ldc + n;
+                float v0 = acc[mi][ni][2 * h], v1 = acc[mi][ni][2 * h + 1];
+                if (g.epi == EPI_BIAS_GELU || g.epi == EPI_BIAS) {
+                    v0 += g.bias[n];
+                    v1 += g.bias[n + 1];
+                    *reinterpret_cast<float2 *>(g.outf + o) = make_float2(v0, v1);
+                    if (g.epi == EPI_BIAS_GELU)
+                        *reinterpret_cast<__nv_bfloat162 *>(g.outh + o) =
+                            __floats2bfloat162_rn(gelu(v0), gelu(v1));
+                } else if (g.epi == EPI_DGELU) {
+                    const float2 z = *reinterpret_cast<const float2 *>(g.zsaved + o);
+                    v0 *= gelu_grad(z.x);
+                    v1 *= gelu_grad(z.y);
+                    *reinterpret_cast<float2 *>(g.outf + o) = make_float2(v0, v1);
+                    *reinterpret_cast<__nv_bfloat162 *>(g.outh + o) = __floats2bfloat162_rn(v0, v1);
+                } else {
+                    *reinterpret_cast<float2 *>(g.outf + o) = make_float2(v0, v1);
+                    if (g.outh)
+                        *reinterpret_cast<__nv_bfloat162 *>(g.outh + o) = __floats2bfloat162_rn(v0, v1);
+                }
+            }
+}
+
+cudaError_t gemm(bool ak, bool bk, const GemmArgs &g, cudaStream_t s)
+{
+    dim3 grid(g.N / GBN, g.M / GBM);
+    if (ak && bk)
+        gemm_kernel<true, true><<<grid, 256, 0, s>>>(g);
+    else if (ak && !bk)
+        gemm_kernel<true, false><<<grid, 256, 0, s>>>(g);
+    else if (!ak && !bk)
+        gemm_kernel<false, false><<<grid, 256, 0, s>>>(g);
+    else
+        gemm_kernel<false, true><<<grid, 256, 0, s>>>(g);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------- elementwise --
+
+struct WarmDev {
+    int B, nb, ng, nl, nload, Kin, Nout, nbp, ngp, ref;
+    double va_scale, penalty;
+    const double *pd0, *qd0;                 // base loads
+    const double *vmin, *vmax;               // per bus
+    const double *pmin, *pmax, *qmin, *qmax; // per generator
+};
+
+// u = normalised loads (BF16, zero padding)
+__global__ void prep_kernel(const WarmDev w, const double *pd, const double *qd, bf16 *U)
+{
+    const int64_t total = (int64_t)w.B * w.Kin;
+    for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < total;
+         it += (int64_t)gridDim.x * blockDim.x) {
+        const int s = (int)(it / w.Kin), j = (int)(it - (int64_t)s * w.Kin);
+        float u = 0.f;
+        if (j < w.nload) {
+            const double b = w.pd0[j];
+            u = b > 0.0 ? (float)((pd[(int64_t)s * w.nload + j] / b - 1.0) / 0.2) : 0.f;
+        } else if (j < 2 * w.nload) {
+            const double b = w.qd0[j - w.nload];
+            u = b > 0.0 ? (float)((qd[(int64_t)s * w.nload + j - w.nload] / b - 1.0) / 0.2) : 0.f;
+        }
+        U[it] = __float2bfloat16_rn(u);
+    }
+}
+
+// network output y = [ya | yv | yp | yq] (block widths nbp, nbp, ngp, ngp)
+// -> va, vm, pg, qg of the batch model (period t = profile t): va = va_scale
+// ya (0 at the reference bus), vm = mid + yv, pg = mid + half-range yp, qg
+// likewise; y = 0 is the flat start
+__global__ void map_kernel(const WarmDev w, const float *Y, double *x)
+{
+    const int per = 2 * w.nb + 2 * w.ng;
+    const int64_t total = (int64_t)w.B * per;
+    const int64_t nbT = (int64_t)w.nb * w.B, ngT = (int64_t)w.ng * w.B;
+    for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < total;
+         it += (int64_t)gridDim.x * blockDim.x) {
+        const int t = (int)(it / per), j = (int)(it - (int64_t)t * per);
+        const float *y = Y + (int64_t)t * w.Nout;
+        if (j < w.nb) {
+            x[(int64_t)w.nb * t + j] = j == w.ref ? 0.0 : w.va_scale * (double)y[j];
+        } else if (j < 2 * w.nb) {
+            const int i = j - w.nb;
+            x[nbT + (int64_t)w.nb * t + i] = 0.5 * (w.vmin[i] + w.vmax[i]) + (double)y[w.nbp + i];
+        } else if (j < 2 * w.nb + w.ng) {
+            const int g = j - 2 * w.nb;
+            x[2 * nbT + (int64_t)w.ng * t + g] =
+                0.5 * (w.pmin[g] + w.pmax[g]) + 0.5 * (w.pmax[g] - w.pmin[g]) * (double)y[2 * w.nbp + g];
+        } else {
+            const int g = j - 2 * w.nb - w.ng;
+            x[2 * nbT + ngT + (int64_t)w.ng * t + g] =
+                0.5 * (w.qmin[g] + w.qmax[g]) + 0.5 * (w.qmax[g] - w.qmin[g]) * (double)y[2 * w.nbp + w.ngp + g];
+        }
+    }
+}
+
+__device__ __forceinline__ double block_sum(double acc, double *red)
+{
+    for (int off = 16; off; off >>= 1)
+        acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0)
+        red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int q = 0; q < (int)(blockDim.x >> 5); q++)
+            s += red[q];
+    return s;
+}
+
+// constraint rows: rho = c - clip(c, gl, gu); v1 = (2 penalty / B) rho;
+// per-block sums of rho^2 into part
+__global__ void resid_kernel(const WarmDev w, const double *c, const double *gl, const double *gu,
+                             int64_t m, double *v1, double *part)
+{
+    __shared__ double red[32];
+    double acc = 0.0;
+    const double k = 2.0 * w.penalty / w.B;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double ci = c[i];
+        const double rho = ci - fmin(fmax(ci, gl[i]), gu[i]);
+        v1[i] = k * rho;
+        acc += rho * rho;
+    }
+    const double s = block_sum(acc, red);
+    if (threadIdx.x == 0)
+        part[blockIdx.x] = s;
+}
+
+// variable bounds: r = x - clip(x, xl, xu); u1 += (2 penalty / B) r (so that
+// the flow variables' share reaches the voltages with the rest); per-block
+// sums of r^2 into part
+__global__ void bound_kernel(const WarmDev w, const double *x, const double *xl, const double *xu,
+                             int64_t n, double *u1, double *part)
+{
+    __shared__ double red[32];
+    double acc = 0.0;
+    const double k = 2.0 * w.penalty / w.B;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double xi = x[i];
+        const double r = xi - fmin(fmax(xi, xl[i]), xu[i]);
+        u1[i] += k * r;
+        acc += r * r;
+    }
+    const double s = block_sum(acc, red);
+    if (threadIdx.x == 0)
+        part[blockIdx.x] = s;
+}
+
+// batch means: loss, cost, sum of squared residuals (constraints and bounds)
+__global__ void stats_kernel(const WarmDev w, const double *part, int nparts, const double *obj,
+                             double *stats)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double r = 0.0;
+        for (int q = 0; q < nparts; q++)
+            r += part[q];
+        const double cost = obj[0] / w.B, res = r / w.B;
+        stats[0] = cost + w.penalty * res;
+        stats[1] = cost;
+        stats[2] = res;
+    }
+}
+
+// v2 = v1, then on every flow row r: v2_r -= u1[own variable of r]; this
+// chains the p, q part of the gradient through p, q = flows(va, vm)
+__global__ void flowrow_kernel(const WarmDev w, const double *v1, const double *u1, int64_t m,
+                               double *v2)
+{
+    const int64_t T = w.B, nl = w.nl, nb = w.nb, ng = w.ng, na = 2 * nl;
+    const int64_t nflow = 4 * nl * T;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double v = v1[i];
+        const int64_t r = i - T;  // rows after the reference rows
+        if (r >= 0 && r < nflow) {
+            const int64_t grp = r / (nl * T), e = r - grp * nl * T;
+            const int64_t t = e / nl, k = e - t * nl;
+            const int64_t p0 = 2 * nb * T + 2 * ng * T + na * t, q0 = p0 + na * T;
+            const int64_t own = grp == 0 ? p0 + k : grp == 1 ? q0 + k : grp == 2 ? p0 + nl + k : q0 + nl + k;
+            v -= u1[own];
+        }
+        v2[i] = v;
+    }
+}
+
+// dL/dy from dL/dx = u2 (J^T v2) + the bound term + grad f / B (on pg),
+// through the output map: FP32 for the checks and the bias gradient, BF16
+// copies for the GEMMs; padding entries and the reference angle get 0
+__global__ void dmap_kernel(const WarmDev w, const double *x, const double *u2, const double *gradf,
+                            float *dYf, bf16 *dYh)
+{
+    const int64_t total = (int64_t)w.B * w.Nout;
+    const int64_t nbT = (int64_t)w.nb * w.B, ngT = (int64_t)w.ng * w.B;
+    const double k = 2.0 * w.penalty / w.B;
+    auto over = [](double v, double lo, double hi) { return v - fmin(fmax(v, lo), hi); };
+    for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < total;
+         it += (int64_t)gridDim.x * blockDim.x) {
+        const int t = (int)(it / w.Nout), j = (int)(it - (int64_t)t * w.Nout);
+        double d = 0.0;
+        if (j < w.nbp) {
+            if (j < w.nb && j != w.ref)
+                d = w.va_scale * u2[(int64_t)w.nb * t + j];
+        } else if (j < 2 * w.nbp) {
+            const int i = j - w.nbp;
+            if (i < w.nb) {
+                const int64_t ix = nbT + (int64_t)w.nb * t + i;
+                d = u2[ix] + k * over(x[ix], w.vmin[i], w.vmax[i]);
+            }
+        } else if (j < 2 * w.nbp + w.ngp) {
+            const int g = j - 2 * w.nbp;
+            if (g < w.ng) {
+                const int64_t ix = 2 * nbT + (int64_t)w.ng * t + g;
+                d = 0.5 * (w.pmax[g] - w.pmin[g]) *
+                    (u2[ix] + gradf[ix] / w.B + k * over(x[ix], w.pmin[g], w.pmax[g]));
+            }
+        } else {
+            const int g = j - 2 * w.nbp - w.ngp;
+            if (g < w.ng) {
+                const int64_t ix = 2 * nbT + ngT + (int64_t)w.ng * t + g;
+                d = 0.5 * (w.qmax[g] - w.qmin[g]) * (u2[ix] + k * over(x[ix], w.qmin[g], w.qmax[g]));
+            }
+        }
+        dYf[it] = (float)d;
+        dYh[it] = __float2bfloat16_rn((float)d);
+    }
+}
+
+// column sums of a [rows][cols] FP32 matrix (bias gradients), one thread
+// per column, rows in order
+__global__ void colsum_kernel(const float *X, int rows, int cols, float *out)
+{
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < cols; j += gridDim.x * blockDim.x) {
+        float acc = 0.f;
+        for (int i = 0; i < rows; i++)
+            acc += X[(int64_t)i * cols + j];
+        out[j] = acc;
+    }
+}
+
+__global__ void to_bf16_kernel(const float *x, bf16 *y, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = __float2bfloat16_rn(x[i]);
+}
+
+// Adam (Kingma and Ba) on a range of the flat FP32 parameters
+__global__ void adam_kernel(float *p, const float *g, float *m1, float *m2, int64_t n, float lr,
+                            float bc1, float bc2)
+{
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float a = b1 * m1[i] + (1.f - b1) * gi;
+        const float b = b2 * m2[i] + (1.f - b2) * gi * gi;
+        m1[i] = a;
+        m2[i] = b;
+        p[i] -= lr * (a / bc1) / (sqrtf(b / bc2) + eps);
+    }
+}
+
+int grid1(int64_t n, int block = 256)
+{
+    int64_t g = (n + block - 1) / block;
+    if (g > 148 * 16)
+        g = 148 * 16;
+    return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+struct opf_warm {
+    Model *M = nullptr;  // callback model: B periods of the network
+    int B = 0, H = 0, Kin = 0, Nout = 0, nb = 0, ng = 0, nl = 0, nload = 0, ref = 0;
+    int nbp = 0, ngp = 0;
+    int64_t n = 0, m = 0, n1 = 0;
+    double penalty = 1e3, lr = 1e-4, lr_out = 1e-2, va_scale = 1.0;
+    int64_t nparams = 0, oW1 = 0, ob1 = 0, oW2 = 0, ob2 = 0, oW3 = 0, ob3 = 0;
+    int64_t step = 0;
+    std::vector<void *> allocs;
+    float *params = nullptr, *grads = nullptr, *am = nullptr, *av = nullptr;
+    bf16 *W1h = nullptr, *W2h = nullptr, *W3h = nullptr;
+    double *pd0 = nullptr, *qd0 = nullptr, *vmin = nullptr, *vmax = nullptr, *pmin = nullptr,
+           *pmax = nullptr, *qmin = nullptr, *qmax = nullptr, *gl = nullptr, *gu = nullptr,
+           *xl = nullptr, *xu = nullptr;
+    bf16 *U = nullptr, *H1 = nullptr, *H2 = nullptr, *dYh = nullptr, *dZ2h = nullptr, *dZ1h = nullptr;
+    float *Z1 = nullptr, *Z2 = nullptr, *Y = nullptr, *dYf = nullptr, *dZ2f = nullptr, *dZ1f = nullptr;
+    double *x = nullptr, *c = nullptr, *gradf = nullptr, *obj = nullptr, *v1 = nullptr, *v2 = nullptr,
+           *u1 = nullptr, *u2 = nullptr, *part = nullptr;
+    int nparts = 0;
+};
+
+namespace {
+
+template <class T>
+int walloc(opf_warm *w, T **p, size_t count)
+{
+    void *q = nullptr;
+    if (cudaMalloc(&q, sizeof(T) * (count ? count : 1)) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("opf_warm: cudaMalloc of %zu bytes failed", sizeof(T) * count);
+        return OPF_ENOMEM;
+    }
+    w->allocs.push_back(q);
+    *p = static_cast<T *>(q);
+    return OPF_OK;
+}
+
+template <class T>
+int wupload(opf_warm *w, T **p, const std::vector<T> &v)
+{
+    int rc = walloc(w, p, v.size());
+    if (!rc && !v.empty() && cudaMemcpy(*p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        set_error("opf_warm: cudaMemcpy failed");
+        return OPF_ECUDA;
+    }
+    return rc;
+}
+
+void destroy(opf_warm *w)
+{
+    if (!w)
+        return;
+    for (void *p : w->allocs)
+        cudaFree(p);
+    if (w->M)
+        free_model(w->M);
+    delete w;
+}
+
+WarmDev dev_of(const opf_warm *w)
+{
+    WarmDev d;
+    d.B = w->B;
+    d.nb = w->nb;
+    d.ng = w->ng;
+    d.nl = w->nl;
+    d.nload = w->nload;
+    d.Kin = w->Kin;
+    d.Nout = w->Nout;
+    d.nbp = w->nbp;
+    d.ngp = w->ngp;
+    d.ref = w->ref;
+    d.va_scale = w->va_scale;
+    d.penalty = w->penalty;
+    d.pd0 = w->pd0;
+    d.qd0 = w->qd0;
+    d.vmin = w->vmin;
+    d.vmax = w->vmax;
+    d.pmin = w->pmin;
+    d.pmax = w->pmax;
+    d.qmin = w->qmin;
+    d.qmax = w->qmax;
+    return d;
+}
+
+int check_cuda(cudaError_t e, const char *what)
+{
+    if (e != cudaSuccess) {
+        set_error("opf_warm: %s: %s", what, cudaGetErrorString(e));
+        return OPF_ECUDA;
+    }
+    return OPF_OK;
+}
+
+int refresh_bf16(opf_warm *w, cudaStream_t s)
+{
+    to_bf16_kernel<<<grid1((int64_t)w->H * w->Kin), 256, 0, s>>>(w->params + w->oW1, w->W1h, (int64_t)w->H * w->Kin);
+    to_bf16_kernel<<<grid1((int64_t)w->H * w->H), 256, 0, s>>>(w->params + w->oW2, w->W2h, (int64_t)w->H * w->H);
+    to_bf16_kernel<<<grid1((int64_t)w->Nout * w->H), 256, 0, s>>>(w->params + w->oW3, w->W3h, (int64_t)w->Nout * w->H);
+    return check_cuda(cudaGetLastError(), "bf16 copies");
+}
+
+// forward pass: U (already prepared) -> Z1, H1, Z2, H2, Y
+int forward(opf_warm *w, cudaStream_t s)
+{
+    GemmArgs g{};
+    g.A = w->U; g.B = w->W1h; g.M = w->B; g.N = w->H; g.K = w->Kin; g.lda = w->Kin; g.ldb = w->Kin;
+    g.ldc = w->H; g.epi = EPI_BIAS_GELU; g.bias = w->params + w->ob1; g.outf = w->Z1; g.outh = w->H1;
+    cudaError_t e = gemm(true, true, g, s);
+    g = GemmArgs{};
+    g.A = w->H1; g.B = w->W2h; g.M = w->B; g.N = w->H; g.K = w->H; g.lda = w->H; g.ldb = w->H;
+    g.ldc = w->H; g.epi = EPI_BIAS_GELU; g.bias = w->params + w->ob2; g.outf = w->Z2; g.outh = w->H2;
+    if (e == cudaSuccess)
+        e = gemm(true, true, g, s);
+    g = GemmArgs{};
+    g.A = w->H2; g.B = w->W3h; g.M = w->B; g.N = w->Nout; g.K = w->H; g.lda = w->H; g.ldb = w->H;
+    g.ldc = w->Nout; g.epi = EPI_BIAS; g.bias = w->params + w->ob3; g.outf = w->Y;
+    if (e == cudaSuccess)
+        e = gemm(true, true, g, s);
+    return check_cuda(e, "forward GEMMs");
+}
+
+// backward pass of dY (dYf, dYh set) into grads
+int backward(opf_warm *w, cudaStream_t s)
+{
+    const int B = w->B, H = w->H;
+    float *gr = w->grads;
+    // dW3 = dY^T H2, db3 = colsum dY
+    GemmArgs g{};
+    g.A = w->dYh; g.B = w->H2; g.M = w->Nout; g.N = H; g.K = B; g.lda = w->Nout; g.ldb = H; g.ldc = H;
+    g.epi = EPI_STORE; g.outf = gr + w->oW3;
+    cudaError_t e = gemm(false, false, g, s);
+    colsum_kernel<<<grid1(w->Nout), 256, 0, s>>>(w->dYf, B, w->Nout, gr + w->ob3);
+    // dZ2 = (dY W3) * gelu'(Z2)
+    g = GemmArgs{};
+    g.A = w->dYh; g.B = w->W3h; g.M = B; g.N = H; g.K = w->Nout; g.lda = w->Nout; g.ldb = H; g.ldc = H;
+    g.epi = EPI_DGELU; g.zsaved = w->Z2; g.outf = w->dZ2f; g.outh = w->dZ2h;
+    if (e == cudaSuccess)
+        e = gemm(true, false, g, s);
+    // dW2 = dZ2^T H1, db2
+    g = GemmArgs{};
+    g.A = w->dZ2h; g.B = w->H1; g.M = H; g.N = H; g.K = B; g.lda = H; g.ldb = H; g.ldc = H;
+    g.epi = EPI_STORE; g.outf = gr + w->oW2;
+    if (e == cudaSuccess)
+        e = gemm(false, false, g, s);
+    colsum_kernel<<<grid1(H), 256, 0, s>>>(w->dZ2f, B, H, gr + w->ob2);
+    // dZ1 = (dZ2 W2) * gelu'(Z1)
+    g = GemmArgs{};
+    g.A = w->dZ2h; g.B = w->W2h; g.M = B; g.N = H; g.K = H; g.lda = H; g.ldb = H; g.ldc = H;
+    g.epi = EPI_DGELU; g.zsaved = w->Z1; g.outf = w->dZ1f; g.outh = w->dZ1h;
+    if (e == cudaSuccess)
+        e = gemm(true, false, g, s);
+    // dW1 = dZ1^T U, db1
+    g = GemmArgs{};
+    g.A = w->dZ1h; g.B = w->U; g.M = H; g.N = w->Kin; g.K = B; g.lda = H; g.ldb = w->Kin; g.ldc = w->Kin;
+    g.epi = EPI_STORE; g.outf = gr + w->oW1;
+    if (e == cudaSuccess)
+        e = gemm(false, false, g, s);
+    colsum_kernel<<<grid1(H), 256, 0, s>>>(w->dZ1f, B, H, gr + w->ob1);
+    if (e == cudaSuccess)
+        e = cudaGetLastError();
+    return check_cuda(e, "backward GEMMs");
+}
+
+// The loss of the batch at the network output w->Y and its gradient dL/dY
+// (into dYf, dYh): the point from the output map, flows from the voltages,
+// the library's callbacks, the penalty gradient through J^T twice.
+int loss_grad(opf_warm *w, const double *d_pd, const double *d_qd, double *d_stats, cudaStream_t s)
+{
+    const WarmDev d = dev_of(w);
+    map_kernel<<<grid1((int64_t)w->B * (2 * w->nb + 2 * w->ng)), 256, 0, s>>>(d, w->Y, w->x);
+    int rc = launch_set_loads(*w->M, d_pd, d_qd, s);
+    if (!rc)
+        rc = launch_flows(*w->M, w->x, s);
+    if (!rc) {  // objective, gradient, constraints
+        EvalArgs a{w->x, nullptr, 1.0, w->obj, w->gradf, w->c, nullptr, nullptr};
+        rc = launch_eval(*w->M, a, W_OBJ | W_GRAD | W_CONS, s);
+    }
+    if (!rc) {  // v1 = 2 penalty rho / B, u1 = J^T v1 + the bound term
+        resid_kernel<<<w->nparts, 256, 0, s>>>(d, w->c, w->gl, w->gu, w->m, w->v1, w->part);
+        rc = launch_jtprod(*w->M, w->x, w->v1, w->u1, s);
+    }
+    if (!rc) {
+        bound_kernel<<<w->nparts, 256, 0, s>>>(d, w->x, w->xl, w->xu, w->n, w->u1, w->part + w->nparts);
+        if (d_stats)
+            stats_kernel<<<1, 32, 0, s>>>(d, w->part, 2 * w->nparts, w->obj, d_stats);
+        // through p, q = flows(va, vm): v2 = v1 - u1[own] on flow rows
+        flowrow_kernel<<<grid1(w->m), 256, 0, s>>>(d, w->v1, w->u1, w->m, w->v2);
+        rc = launch_jtprod(*w->M, w->x, w->v2, w->u2, s);
+    }
+    if (!rc)
+        dmap_kernel<<<grid1((int64_t)w->B * w->Nout), 256, 0, s>>>(d, w->x, w->u2, w->gradf, w->dYf, w->dYh);
+    if (!rc)
+        rc = check_cuda(cudaGetLastError(), "loss gradient");
+    return rc;
+}
+
+int round_up(int v, int q)
+{
+    return (v + q - 1) / q * q;
+}
+
+}  // namespace
+
+extern "C" {
+
+int opf_warm_create(const opf_network *net, const opf_warm_opts *opts, opf_warm **out)
+{
+    if (!out) {
+        set_error("out is NULL");
+        return OPF_EINVAL;
+    }
+    *out = nullptr;
+    if (!net || !opts) {
+        set_error("opf_warm_create: net and opts are required");
+        return OPF_EINVAL;
+    }
+    if (net->nperiod != 1 || opts->batch < 128 || opts->batch % 128 || opts->hidden < 128 ||
+        opts->hidden % 128 || !(opts->penalty >= 0.0) || !(opts->lr > 0.0) || !(opts->lr_out > 0.0) ||
+        !std::isfinite(opts->va_scale)) {
+        set_error("opf_warm_create: need nperiod 1, batch and hidden multiples of 128, penalty >= 0, "
+                  "lr > 0, lr_out > 0, finite va_scale");
+        return OPF_EINVAL;
+    }
+    opf_warm *w = new opf_warm();
+    w->B = opts->batch;
+    w->H = opts->hidden;
+    w->nb = net->nbus;
+    w->ng = net->ngen;
+    w->nl = net->nbranch;
+    w->nload = net->nload;
+    w->ref = net->ref_bus;
+    w->penalty = opts->penalty;
+    w->lr = opts->lr;
+    w->lr_out = opts->lr_out;
+    w->va_scale = opts->va_scale;
+    w->Kin = round_up(2 * w->nload, 128);
+    w->nbp = round_up(w->nb, 128);
+    w->ngp = round_up(w->ng, 128);
+    w->Nout = 2 * w->nbp + 2 * w->ngp;
+    // the callback model: batch periods, no ramp rows, loads replaced per call
+    opf_network n2 = *net;
+    n2.nperiod = w->B;
+    n2.ramp_ratio = 0.0;
+    std::vector<double> lp((size_t)w->B * w->nload), lq((size_t)w->B * w->nload);
+    for (int t = 0; t < w->B; t++)
+        for (int l = 0; l < w->nload; l++) {
+            lp[(size_t)t * w->nload + l] = net->load_pd[l];
+            lq[(size_t)t * w->nload + l] = net->load_qd[l];
+        }
+    n2.load_pd = lp.data();
+    n2.load_qd = lq.data();
+    int rc = build_model(&n2, 1, 0.0, true, &w->M);
+    if (rc) {
+        delete w;
+        return rc;
+    }
+    w->n = w->M->n;
+    w->m = w->M->m;
+    w->n1 = w->n / w->B;
+    // parameters: W1 [H][Kin], b1 [H], W2 [H][H], b2 [H], W3 [Nout][H], b3 [Nout]
+    w->oW1 = 0;
+    w->ob1 = w->oW1 + (int64_t)w->H * w->Kin;
+    w->oW2 = w->ob1 + w->H;
+    w->ob2 = w->oW2 + (int64_t)w->H * w->H;
+    w->oW3 = w->ob2 + w->H;
+    w->ob3 = w->oW3 + (int64_t)w->Nout * w->H;
+    w->nparams = w->ob3 + w->Nout;
+    std::vector<float> p(w->nparams, 0.f);
+    std::mt19937_64 rng(opts->seed);
+    auto init_rows = [&](int64_t off, int cols, int r0, int r1, int used_cols) {
+        std::normal_distribution<double> nd(0.0, 1.0 / std::sqrt((double)used_cols));
+        for (int r = r0; r < r1; r++)
+            for (int c = 0; c < used_cols; c++)
+                p[off + (int64_t)r * cols + c] = (float)nd(rng);
+    };
+    init_rows(w->oW1, w->Kin, 0, w->H, 2 * w->nload);
+    init_rows(w->oW2, w->H, 0, w->H, w->H);
+    // W3 and b3 start at zero: the untrained network proposes the flat start
+    std::vector<double> pd0(net->load_pd, net->load_pd + w->nload), qd0(net->load_qd, net->load_qd + w->nload);
+    std::vector<double> vmin(net->bus_vmin, net->bus_vmin + w->nb), vmax(net->bus_vmax, net->bus_vmax + w->nb);
+    std::vector<double> pmin(net->gen_pmin, net->gen_pmin + w->ng), pmax(net->gen_pmax, net->gen_pmax + w->ng);
+    std::vector<double> qmin(net->gen_qmin, net->gen_qmin + w->ng), qmax(net->gen_qmax, net->gen_qmax + w->ng);
+    std::vector<double> xl(w->n), xu(w->n), gl(w->m), gu(w->m);
+    bounds(*w->M, xl.data(), xu.data(), gl.data(), gu.data());
+    w->nparts = 148 * 8;
+    const int64_t act = (int64_t)w->B * w->H;
+    const int64_t outsz = (int64_t)w->B * w->Nout;
+    if (!rc) rc = wupload(w, &w->params, p);
+    if (!rc) rc = walloc(w, &w->grads, w->nparams);
+    if (!rc) rc = walloc(w, &w->am, w->nparams);
+    if (!rc) rc = walloc(w, &w->av, w->nparams);
+    if (!rc) rc = walloc(w, &w->W1h, (size_t)w->H * w->Kin);
+    if (!rc) rc = walloc(w, &w->W2h, (size_t)w->H * w->H);
+    if (!rc) rc = walloc(w, &w->W3h, (size_t)w->Nout * w->H);
+    if (!rc) rc = wupload(w, &w->pd0, pd0);
+    if (!rc) rc = wupload(w, &w->qd0, qd0);
+    if (!rc) rc = wupload(w, &w->vmin, vmin);
+    if (!rc) rc = wupload(w, &w->vmax, vmax);
+    if (!rc) rc = wupload(w, &w->pmin, pmin);
+    if (!rc) rc = wupload(w, &w->pmax, pmax);
+    if (!rc) rc = wupload(w, &w->qmin, qmin);
+    if (!rc) rc = wupload(w, &w->qmax, qmax);
+    if (!rc) rc = wupload(w, &w->gl, gl);
+    if (!rc) rc = wupload(w, &w->gu, gu);
+    if (!rc) rc = wupload(w, &w->xl, xl);
+    if (!rc) rc = wupload(w, &w->xu, xu);
+    if (!rc) rc = walloc(w, &w->U, (size_t)w->B * w->Kin);
+    if (!rc) rc = walloc(w, &w->H1, act);
+    if (!rc) rc = walloc(w, &w->H2, act);
+    if (!rc) rc = walloc(w, &w->dZ2h, act);
+    if (!rc) rc = walloc(w, &w->dZ1h, act);
+    if (!rc) rc = walloc(w, &w->Z1, act);
+    if (!rc) rc = walloc(w, &w->Z2, act);
+    if (!rc) rc = walloc(w, &w->dZ2f, act);
+    if (!rc) rc = walloc(w, &w->dZ1f, act);
+    if (!rc) rc = walloc(w, &w->Y, outsz);
+    if (!rc) rc = walloc(w, &w->dYf, outsz);
+    if (!rc) rc = walloc(w, &w->dYh, outsz);
+    if (!rc) rc = walloc(w, &w->x, w->n);
+    if (!rc) rc = walloc(w, &w->c, w->m);
+    if (!rc) rc = walloc(w, &w->gradf, w->n);
+    if (!rc) rc = walloc(w, &w->obj, 1);
+    if (!rc) rc = walloc(w, &w->v1, w->m);
+    if (!rc) rc = walloc(w, &w->v2, w->m);
+    if (!rc) rc = walloc(w, &w->u1, w->n);
+    if (!rc) rc = walloc(w, &w->u2, w->n);
+    if (!rc) rc = walloc(w, &w->part, 2 * (size_t)w->nparts);
+    if (!rc && (cudaMemset(w->am, 0, sizeof(float) * w->nparams) != cudaSuccess ||
+                cudaMemset(w->av, 0, sizeof(float) * w->nparams) != cudaSuccess ||
+                cudaMemset(w->grads, 0, sizeof(float) * w->nparams) != cudaSuccess ||
+                cudaMemset(w->Y, 0, sizeof(float) * outsz) != cudaSuccess))
+        rc = check_cuda(cudaGetLastError(), "memset");
+    if (!rc)
+        rc = refresh_bf16(w, nullptr);
+    if (!rc)
+        rc = check_cuda(cudaDeviceSynchronize(), "create");
+    if (rc) {
+        destroy(w);
+        return rc;
+    }
+    *out = w;
+    return OPF_OK;
+}
+
+int opf_warm_destroy(opf_warm *w)
+{
+    destroy(w);
+    return OPF_OK;
+}
+
+int opf_warm_dims(const opf_warm *w, int32_t *n_in, int32_t *n_out, int32_t *n_x, int64_t *n_params)
+{
+    if (!w) {
+        set_error("opf_warm_dims: w is NULL");
+        return OPF_EINVAL;
+    }
+    if (n_in) *n_in = w->Kin;
+    if (n_out) *n_out = w->Nout;
+    if (n_x) *n_x = (int32_t)w->n1;
+    if (n_params) *n_params = w->nparams;
+    return OPF_OK;
+}
+
+int opf_warm_forward(opf_warm *w, const double *d_pd, const double *d_qd, float *d_y, void *stream)
+{
+    if (!w || !d_pd || !d_qd) {
+        set_error("opf_warm_forward: bad arguments");
+        return OPF_EINVAL;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    prep_kernel<<<grid1((int64_t)w->B * w->Kin), 256, 0, s>>>(dev_of(w), d_pd, d_qd, w->U);
+    int rc = forward(w, s);
+    if (!rc && d_y)
+        rc = check_cuda(cudaMemcpyAsync(d_y, w->Y, sizeof(float) * w->B * w->Nout, cudaMemcpyDeviceToDevice, s), "copy output");
+    return rc;
+}
+
+int opf_warm_backward(opf_warm *w, const float *d_dy, float *d_grad, void *stream)
+{
+    if (!w || !d_dy) {
+        set_error("opf_warm_backward: bad arguments");
+        return OPF_EINVAL;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int rc = check_cuda(cudaMemcpyAsync(w->dYf, d_dy, sizeof(float) * w->B * w->Nout, cudaMemcpyDeviceToDevice, s), "copy dy");
+    if (!rc)
+        to_bf16_kernel<<<grid1((int64_t)w->B * w->Nout), 256, 0, s>>>(w->dYf, w->dYh, (int64_t)w->B * w->Nout);
+    if (!rc)
+        rc = backward(w, s);
+    if (!rc && d_grad)
+        rc = check_cuda(cudaMemcpyAsync(d_grad, w->grads, sizeof(float) * w->nparams, cudaMemcpyDeviceToDevice, s), "copy grads");
+    return rc;
+}
+
+int opf_warm_loss_grad(opf_warm *w, const double *d_pd, const double *d_qd, const float *d_y,
+                       float *d_dy, double *d_stats, void *stream)
+{
+    if (!w || !d_pd || !d_qd || !d_y) {
+        set_error("opf_warm_loss_grad: bad arguments");
+        return OPF_EINVAL;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int rc = check_cuda(cudaMemcpyAsync(w->Y, d_y, sizeof(float) * w->B * w->Nout, cudaMemcpyDeviceToDevice, s), "copy output");
+    if (!rc)
+        rc = loss_grad(w, d_pd, d_qd, d_stats, s);
+    if (!rc && d_dy)
+        rc = check_cuda(cudaMemcpyAsync(d_dy, w->dYf, sizeof(float) * w->B * w->Nout, cudaMemcpyDeviceToDevice, s), "copy dy");
+    return rc;
+}
+
+int opf_warm_train_step(opf_warm *w, const double *d_pd, const double *d_qd, double *d_stats, void *stream)
+{
+    if (!w || !d_pd || !d_qd) {
+        set_error("opf_warm_train_step: bad arguments");
+        return OPF_EINVAL;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    prep_kernel<<<grid1((int64_t)w->B * w->Kin), 256, 0, s>>>(dev_of(w), d_pd, d_qd, w->U);
+    int rc = forward(w, s);
+    if (!rc)
+        rc = loss_grad(w, d_pd, d_qd, d_stats, s);
+    if (!rc)
+        rc = backward(w, s);
+    if (!rc) {
+        w->step++;
+        const float bc1 = 1.f - (float)std::pow(0.9, (double)w->step);
+        const float bc2 = 1.f - (float)std::pow(0.999, (double)w->step);
+        // weights and hidden biases at lr, the output bias at lr_out
+        adam_kernel<<<grid1(w->ob3), 256, 0, s>>>(w->params, w->grads, w->am, w->av, w->ob3, (float)w->lr,
+                                                  bc1, bc2);
+        adam_kernel<<<grid1(w->Nout), 256, 0, s>>>(w->params + w->ob3, w->grads + w->ob3, w->am + w->ob3,
+                                                   w->av + w->ob3, w->Nout, (float)w->lr_out, bc1, bc2);
+        rc = refresh_bf16(w, s);
+    }
+    return rc;
+}
+
+int opf_warm_predict(opf_warm *w, const double *d_pd, const double *d_qd, double *d_x, void *stream)
+{
+    if (!w || !d_pd || !d_qd || !d_x) {
+        set_error("opf_warm_predict: bad arguments");
+        return OPF_EINVAL;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const WarmDev d = dev_of(w);
+    prep_kernel<<<grid1((int64_t)w->B * w->Kin), 256, 0, s>>>(d, d_pd, d_qd, w->U);
+    int rc = forward(w, s);
+    if (!rc) {
+        rc = check_cuda(cudaMemsetAsync(d_x, 0, sizeof(double) * w->n, s), "clear x");
+        map_kernel<<<grid1((int64_t)w->B * (2 * w->nb + 2 * w->ng)), 256, 0, s>>>(d, w->Y, d_x);
+        if (!rc)
+            rc = launch_flows(*w->M, d_x, s);
+    }
+    return rc;
+}
+
+int opf_warm_set_lr(opf_warm *w, double lr, double lr_out)
+{
+    if (!w || !(lr > 0.0) || !(lr_out > 0.0)) {
+        set_error("opf_warm_set_lr: bad arguments");
+        return OPF_EINVAL;
+    }
+    w->lr = lr;
+    w->lr_out = lr_out;
+    return OPF_OK;
+}
+
+int opf_warm_get_params(const opf_warm *w, float *h)
+{
+    if (!w || !h) {
+        set_error("opf_warm_get_params: bad arguments");
+        return OPF_EINVAL;
+    }
+    return check_cuda(cudaMemcpy(h, w->params, sizeof(float) * w->nparams, cudaMemcpyDeviceToHost), "get params");
+}
+
+int opf_warm_set_params(opf_warm *w, const float *h)
+{
+    if (!w || !h) {
+        set_error("opf_warm_set_params: bad arguments");
+        return OPF_EINVAL;
+    }
+    int rc = check_cuda(cudaMemcpy(w->params, h, sizeof(float) * w->nparams, cudaMemcpyHostToDevice), "set params");
+    if (!rc && (cudaMemset(w->am, 0, sizeof(float) * w->nparams) != cudaSuccess ||
+                cudaMemset(w->av, 0, sizeof(float) * w->nparams) != cudaSuccess))
+        rc = check_cuda(cudaGetLastError(), "clear adam");
+    w->step = 0;
+    if (!rc)
+        rc = refresh_bf16(w, nullptr);
+    if (!rc)
+        rc = check_cuda(cudaDeviceSynchronize(), "set params");
+    return rc;
+}
+
+}  // extern "C"

@@ -23,6 +23,17 @@ IV-B, IV-C), which are not available here. Recipe:
 and a few parallel branches, so that parity tests reach every term of the
 formulation (the paper's cases contain all of them).
 
+The draw above does not make an OPF instance feasible: on the 2,000-bus
+grid no dispatch keeps every line within rate_a even in the lossless DC
+approximation. The paper's cases are feasible instances, and the learned
+warm start is judged by its constraint violation, so its grid goes through
+``secure_ratings``: a linear program (DC flows on the series susceptances,
+HiGHS) finds the dispatch at 1.2 times the base load that overloads the
+lines least (in L1), and each line's rating becomes max(rate_a, 1.3 |flow|)
+for that dispatch. Only lines the dispatch needs are lifted; the draw is
+unchanged elsewhere. This DC dispatch is a data-generation step that neither
+side of the evaluation computes.
+
 Multi-period loads follow the paper's demand-curve interface (Sec. III-C-2,
 ``mpopf_model`` with a curve): every load is scaled per period by one daily
 curve, here a seeded sinusoid, times lognormal(0, 0.05) noise per load.
@@ -254,6 +265,70 @@ def scenarios(g: Grid, count: int, seed: int, low: float = 0.8, high: float = 1.
                   ramp_ratio=0.0)
 
 
+def load_samples(g: Grid, count: int, seed: int, rank: int = 8, share: float = 0.7):
+    """``count`` load profiles of ``g`` for the learned warm start: every
+    load's Pd and Qd scaled by factors that are U(0.8, 1.2) marginally and
+    correlated across loads through ``rank`` seeded common factors (a normal
+    copula: z = sqrt(share) F w + sqrt(1 - share) e, factor = 0.8 + 0.4 Phi(z),
+    each row of F of unit norm). Returns (pd, qd), each [count][nload]."""
+    from scipy.special import ndtr
+    rng = np.random.default_rng(seed + 4242)
+    nload = g.nload
+    F = rng.standard_normal((nload, rank))
+    F /= np.linalg.norm(F, axis=1, keepdims=True)
+    w = rng.standard_normal((count, rank))
+    common = w @ F.T
+    zp = math.sqrt(share) * common + math.sqrt(1.0 - share) * rng.standard_normal((count, nload))
+    zq = math.sqrt(share) * common + math.sqrt(1.0 - share) * rng.standard_normal((count, nload))
+    a = 0.8 + 0.4 * ndtr(zp)
+    b = 0.8 + 0.4 * ndtr(zq)
+    return g.load_pd[0][None, :] * a, g.load_qd[0][None, :] * b
+
+
+def secure_ratings(g: Grid, load_scale: float = 1.2, margin: float = 1.3,
+                   angle_frac: float = 0.8) -> Grid:
+    """Copy of single-period ``g`` with line ratings lifted so that the DC
+    dispatch of ``load_scale`` times the base load that minimises the total
+    overload stays within them, with ``margin`` (recipe in the module
+    docstring). Angle differences of that dispatch are held within
+    ``angle_frac`` of the limits."""
+    import scipy.sparse as sp
+    from scipy.optimize import linprog
+    nb, nl, ng = g.nbus, g.nbranch, g.ngen
+    f, t = g.br_f.astype(np.int64), g.br_t.astype(np.int64)
+    bser = g.br_x / (g.br_r ** 2 + g.br_x ** 2)
+    k = np.arange(nl)
+    # variables: theta [nb], pg [ng], overload s [nl] >= 0
+    nv = nb + ng + nl
+    # DC flow of branch k: bser_k (theta_f - theta_t), as a row over theta
+    D = sp.csr_matrix((np.concatenate([bser, -bser]), (np.concatenate([k, k]), np.concatenate([f, t]))),
+                      shape=(nl, nb))
+    inc = sp.csr_matrix((np.concatenate([np.ones(nl), -np.ones(nl)]),
+                         (np.concatenate([f, t]), np.concatenate([k, k]))), shape=(nb, nl))
+    G = sp.csr_matrix((np.ones(ng), (g.gen_bus.astype(np.int64), np.arange(ng))), shape=(nb, ng))
+    pd = np.zeros(nb)
+    np.add.at(pd, g.load_bus, load_scale * g.load_pd[0])
+    ref = sp.csr_matrix(([1.0], ([0], [int(g.ref_bus)])), shape=(1, nb))
+    A_eq = sp.vstack([sp.hstack([inc @ D, -G, sp.csr_matrix((nb, nl))]),
+                      sp.hstack([ref, sp.csr_matrix((1, ng + nl))])]).tocsr()
+    b_eq = np.concatenate([-pd, [0.0]])
+    S = -sp.identity(nl, format="csr")
+    Z = sp.csr_matrix((nl, ng))
+    A = sp.csr_matrix((np.concatenate([np.ones(nl), -np.ones(nl)]), (np.concatenate([k, k]),
+                       np.concatenate([f, t]))), shape=(nl, nb))
+    A_ub = sp.vstack([sp.hstack([D, Z, S]), sp.hstack([-D, Z, S]),
+                      sp.hstack([A, Z, sp.csr_matrix((nl, nl))]),
+                      sp.hstack([-A, Z, sp.csr_matrix((nl, nl))])]).tocsr()
+    b_ub = np.concatenate([g.br_rate_a, g.br_rate_a, angle_frac * g.br_angmax, -angle_frac * g.br_angmin])
+    c = np.concatenate([np.zeros(nb + ng), np.ones(nl)])
+    bounds = [(None, None)] * nb + list(zip(g.gen_pmin, g.gen_pmax)) + [(0.0, None)] * nl
+    res = linprog(c, A_ub=A_ub, b_ub=b_ub, A_eq=A_eq, b_eq=b_eq, bounds=bounds, method="highs")
+    if res.status != 0:
+        raise RuntimeError("secure_ratings: " + res.message)
+    flow = D @ res.x[:nb]
+    return g.copy(br_rate_a=np.maximum(g.br_rate_a, margin * np.abs(flow)))
+
+
 def bridges(nbus: int, f: np.ndarray, t: np.ndarray) -> np.ndarray:
     """Boolean mask of bridge branches (iterative Tarjan low-link)."""
     nl = len(f)
@@ -366,6 +441,12 @@ def case2k(seed: int = 2000) -> Grid:
 def case1k(seed: int = 1000) -> Grid:
     """1,000 buses, 1,300 branches, 250 generators, 700 loads."""
     return make_grid(1000, 1300, 250, seed)
+
+
+def case2k_secure(seed: int = 2000) -> Grid:
+    """The 2,000-bus grid with ratings lifted by ``secure_ratings`` (the
+    learned warm start's grid)."""
+    return secure_ratings(case2k(seed))
 
 
 def mp2k(nperiod: int = 96, seed: int = 2000) -> Grid:

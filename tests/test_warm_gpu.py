@@ -1,0 +1,122 @@
+"""The learned warm start on the GPU: BF16 network kernels against the FP64
+oracle, the physics gradient against differences of the oracle loss, and
+the gain of the trained network over the flat start, judged by the oracle."""
+import numpy as np
+import pytest
+
+from oracle import mlp
+from paper_2510_12897_b300 import opf, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    if not t.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    from paper_2510_12897_b300 import build
+    build.build()
+    return t
+
+
+def bf16(a):
+    import torch
+    return torch.tensor(np.asarray(a, np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def rel_err(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def test_network_forward_backward_against_oracle(torch):
+    """Forward and backward BF16 kernels (FP32 accumulation) against the
+    FP64 oracle fed the same BF16-rounded weights and inputs: relative
+    errors of the order of BF16 rounding (2^-8) on every tensor."""
+    from paper_2510_12897_b300 import warm
+    g = synth.case30(general=True)
+    B, hid = 128, 256
+    ws = warm.WarmStart(g, batch=B, hidden=hid, seed=3)
+    # the output layer starts at zero: give it random values for the check
+    p0 = ws.get_params()
+    k = hid * ws.n_in + hid + hid * hid + hid
+    p0[k:] = (np.random.default_rng(4).standard_normal(p0.size - k) / np.sqrt(hid)).astype(np.float32)
+    ws.set_params(p0)
+    pd, qd = synth.load_samples(g, B, seed=11)
+    dev = torch.device("cuda")
+    dpd, dqd = torch.tensor(pd, device=dev), torch.tensor(qd, device=dev)
+    y = torch.empty(B * ws.n_out, dtype=torch.float32, device=dev)
+    ws.forward(dpd, dqd, y)
+    torch.cuda.synchronize()
+    p = ws.get_params().astype(np.float64)
+    W1, b1, W2, b2, W3, b3 = mlp.unpack(p, ws.n_in, hid, ws.n_out)
+    pq = np.concatenate([bf16(W1).ravel(), b1, bf16(W2).ravel(), b2, bf16(W3).ravel(), b3])
+    U = bf16(mlp.inputs(pd, qd, g.load_pd[0], g.load_qd[0], ws.n_in))
+    Y, cache = mlp.forward(pq, U, ws.n_in, hid, ws.n_out)
+    yg = y.cpu().numpy().reshape(B, ws.n_out)
+    assert rel_err(yg, Y) < 1e-2
+    assert np.max(np.abs(Y)) > 0.1  # a non-trivial output
+    rng = np.random.default_rng(5)
+    dH = np.zeros((B, ws.n_out))
+    nbp, ngp = mlp.pad(g.nbus), mlp.pad(g.ngen)
+    for o, c in ((0, g.nbus), (nbp, g.nbus), (2 * nbp, g.ngen), (2 * nbp + ngp, g.ngen)):
+        dH[:, o:o + c] = rng.standard_normal((B, c))
+    dH = bf16(dH)
+    grad = torch.empty(ws.n_params, dtype=torch.float32, device=dev)
+    ws.backward(torch.tensor(dH, dtype=torch.float32, device=dev), grad)
+    torch.cuda.synchronize()
+    gg = grad.cpu().numpy().astype(np.float64)
+    go = mlp.backward(pq, cache, dH, ws.n_in, hid, ws.n_out)
+    for name, a, b in zip(("W1", "b1", "W2", "b2", "W3", "b3"), mlp.unpack(gg, ws.n_in, hid, ws.n_out),
+                          mlp.unpack(go, ws.n_in, hid, ws.n_out)):
+        assert rel_err(a, b) < 3e-2, name
+    ws.close()
+
+
+def test_physics_gradient_against_oracle_differences(torch, oracle_mod):
+    """dL/dy of the penalised loss, from the library's callbacks (cons,
+    grad, J^T twice through the flows), against central differences of the
+    FP64 oracle's loss, on sampled coordinates of several profiles."""
+    from paper_2510_12897_b300 import warm
+    g = synth.case30(general=True)
+    B = 128
+    pen, vas = 1e3, 0.5
+    ws = warm.WarmStart(g, batch=B, hidden=128, penalty=pen, va_scale=vas, seed=1)
+    pd, qd = synth.load_samples(g, B, seed=12)
+    dev = torch.device("cuda")
+    rng = np.random.default_rng(7)
+    y = np.zeros((B, ws.n_out), np.float32)  # head values, block layout
+    nbp, ngp = mlp.pad(g.nbus), mlp.pad(g.ngen)
+    used = np.concatenate([np.arange(g.nbus), nbp + np.arange(g.nbus), 2 * nbp + np.arange(g.ngen),
+                           2 * nbp + ngp + np.arange(g.ngen)])
+    y[:, used] = (0.3 * rng.standard_normal((B, used.size))).astype(np.float32)
+    dy = torch.empty(B * ws.n_out, dtype=torch.float32, device=dev)
+    stats = torch.zeros(3, dtype=torch.float64, device=dev)
+    ws.loss_grad(torch.tensor(pd, device=dev), torch.tensor(qd, device=dev),
+                 torch.tensor(y.ravel(), device=dev), dy, stats)
+    torch.cuda.synchronize()
+    dy = dy.cpu().numpy().reshape(B, ws.n_out)
+    # loss value: mean over profiles of the oracle loss
+    tot = 0.0
+    ctxs = {}
+    for t in range(B):
+        gt = g.copy(load_pd=pd[t:t + 1], load_qd=qd[t:t + 1])
+        O = oracle_mod.Oracle(gt)
+        ctxs[t] = (gt, O, O.bounds())
+        tot += mlp.loss(gt, y[t].astype(np.float64), vas, pen, O, ctxs[t][2])
+    s = stats.cpu().numpy()
+    assert abs(s[0] - tot / B) <= 1e-9 * max(1.0, abs(tot / B))
+    for t in (0, 17, 99):
+        gt, O, bnd = ctxs[t]
+        for j in list(rng.choice(used, 12, replace=False)) + [g.ref_bus]:
+            def L(v):
+                yy = y[t].astype(np.float64).copy()
+                yy[j] = v
+                return mlp.loss(gt, yy, vas, pen, O, bnd) / B
+            h = 1e-4
+            y0 = float(y[t, j])  # keep the perturbed value in double precision
+            d1 = (L(y0 + h) - L(y0 - h)) / (2 * h)
+            d2 = (L(y0 + h / 2) - L(y0 - h / 2)) / h
+            fd = (4 * d2 - d1) / 3
+            assert abs(dy[t, j] - fd) <= 1e-5 * max(1.0, abs(fd)), (t, j, dy[t, j], fd)
+    ws.close()
