@@ -59,6 +59,8 @@ def parse():
     p.add_argument("--seed", type=int, default=10000)
     p.add_argument("--no-autotune", action="store_true", help="default launch shape (profiling runs)")
     p.add_argument("--e2e-steps", type=int, default=256)
+    p.add_argument("--no-warm", action="store_true", help="skip the learned warm-start section")
+    p.add_argument("--warm-epochs", type=int, default=100)
     return p.parse_args()
 
 
@@ -392,6 +394,10 @@ def main():
     if not args.no_batched and rank == 0:
         batched = batched_vs_plain(torch, opf, synth, stream, dev)
 
+    warm_start = None
+    if not args.no_warm and rank == 0:
+        warm_start = warm_start_summary(torch, opf, synth, dev, args.warm_epochs)
+
     cpu = None
     if not args.no_cpu and rank == 0:
         rate, k, el = cpu_oracle_rate(g, seconds=10.0)
@@ -415,7 +421,7 @@ def main():
                          "frac": jac_hess_bytes(g, nnzh) / (jh_us * 1e-6) / 1e9 / hbm},
             "phase_us": {"branch": br_us, "bus": bus_us, "autotune_eval": tuned_us},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * K, "clocks": clocks,
-            "batched": batched,
+            "batched": batched, "warm_start": warm_start,
         }
         print(json.dumps(line), flush=True)
     if dist:
@@ -520,6 +526,84 @@ def batched_vs_plain(torch, opf, synth, stream, dev):
     out["sc1k_501"] = {"batched_us": tb, "plain_loop_us": tp, "speedup": tp / tb,
                        "instance_evals_per_s": 501e6 / tb}
     return out
+
+
+def per_period_max(v, counts, T):
+    """Max over each period's entries of a batch-model vector whose groups
+    are laid out [group][period][entry]."""
+    out = None
+    off = 0
+    for c in counts:
+        blk = v[off:off + c * T].view(T, c).amax(1)
+        out = blk if out is None else out.maximum(blk)
+        off += c * T
+    return out
+
+
+def warm_start_summary(torch, opf, synth, dev, epochs):
+    """The learned warm start on the 2,000-bus grid: training time on 100k
+    load profiles, prediction throughput for batches of 4,096, and the max
+    constraint violation (constraints and bounds, FP64, from the library's
+    constraint kernel) of its points against the flat start's on 4,096
+    held-out profiles."""
+    from paper_2510_12897_b300 import warm
+    g = synth.case2k_secure()
+    N, B = 100_000, 4096
+    t0 = time.perf_counter()
+    pd, qd = synth.load_samples(g, N + B, seed=2024)
+    sample_s = time.perf_counter() - t0
+    pd_t, qd_t = torch.tensor(pd[:N], device=dev), torch.tensor(qd[:N], device=dev)
+    pd_h, qd_h = torch.tensor(pd[N:], device=dev), torch.tensor(qd[N:], device=dev)
+    ws = warm.WarmStart(g, batch=B, hidden=1024, penalty=1e3, lr=1e-4, lr_out=1e-2, seed=0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hist = warm.train(ws, pd_t, qd_t, epochs=epochs, lr=1e-4, lr_out=1e-2, decay=1000.0)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    x = torch.empty(ws.n_x * B, dtype=torch.float64, device=dev)
+    ws.predict(pd_h, qd_h, x)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(10):
+        ws.predict(pd_h, qd_h, x)
+    e1.record()
+    torch.cuda.synchronize()
+    pred_ms = e0.elapsed_time(e1) / 10
+    # judge: max violation per profile, batch model of the held-out profiles
+    M = opf.Model(g.copy(load_pd=pd[N:], load_qd=qd[N:], ramp_ratio=0.0))
+    xl, xu, gl, gu = (torch.tensor(a, device=dev) for a in M.bounds())
+    c = torch.empty(M.m, dtype=torch.float64, device=dev)
+    nb, ng, nl = g.nbus, g.ngen, g.nbranch
+    rows = [1, nl, nl, nl, nl, nl, nb, nb, nl, nl]
+    cols = [nb, nb, ng, ng, 2 * nl, 2 * nl]
+
+    def cvio(xx):
+        M.eval_cons(xx, c)
+        torch.cuda.synchronize()
+        vc = torch.clamp(gl - c, min=0) + torch.clamp(c - gu, min=0)
+        vx = torch.clamp(xl - xx, min=0) + torch.clamp(xx - xu, min=0)
+        return torch.maximum(per_period_max(vc, rows, B), per_period_max(vx, cols, B))
+
+    xf = torch.empty(M.n, dtype=torch.float64, device=dev)
+    M.flat_start(xf)
+    cf, cw = cvio(xf), cvio(x)
+    gain = (cf / cw).cpu().numpy()
+    cw_np, cf_np = cw.cpu().numpy(), cf.cpu().numpy()
+    ws.close()
+    return {
+        "grid": "2,000 buses, 2,600 branches, 500 generators, 1,400 loads (ratings secured by a DC dispatch)",
+        "network": "3 layers, width 1024, GELU, BF16 with FP32 accumulation",
+        "samples": N, "samples_s": sample_s, "epochs": epochs, "batch": B, "train_s": train_s,
+        "final_loss": float(hist[-1][0]), "final_cost": float(hist[-1][1]), "final_res2": float(hist[-1][2]),
+        "predict_ms_per_batch": pred_ms, "predict_profiles_per_s": B / (pred_ms * 1e-3),
+        "held_out": B, "cvio_flat_median": float(np.median(cf_np)),
+        "cvio_warm_median": float(np.median(cw_np)), "cvio_warm_p99": float(np.percentile(cw_np, 99)),
+        "cvio_warm_max": float(cw_np.max()),
+        "gain_median": float(np.median(gain)), "gain_min": float(gain.min()),
+        "frac_profiles_gain_ge_10": float(np.mean(gain >= 10.0)),
+        "judge": "max violation of constraints and bounds from the library's FP64 constraint kernel",
+    }
 
 
 if __name__ == "__main__":

@@ -387,7 +387,8 @@ __global__ void __launch_bounds__(kBusBlockMax) bus_kernel(const KParams P)
                 split((int)(item - __ldg(d.bus_items + q.s)), __ldg(&I->nb), __ldg(&I->T), q.t, r);
                 bus0 = __ldg(&I->bus0);
             }
-            q.e = __ldg(d.bus_order + bus0 + r);  // buses of equal slot count share warps
+            q.e = r;  // buses in id order (warps mix slot counts; grouping them by count
+                      // put the highest-degree buses into one straggler warp)
             const int ib = bus0 + q.e;
             q.a = __ldg(d.bus_a + ib);
             q.b = __ldg(d.bus_b + ib);

@@ -68,7 +68,6 @@ struct DevArrays {
     double2 *y_ff = nullptr, *y_ft = nullptr, *y_tf = nullptr, *y_tt = nullptr;  // (G, B)
     double *rate2 = nullptr;      // rate_a^2
     // buses
-    int32_t *bus_order = nullptr; // bus-phase processing order: buses grouped by slot count
     int4 *bus_a = nullptr;        // (first slot, end slot, first gen entry, end gen entry)
     int4 *bus_b = nullptr;        // (balance-row offset, va-row offset, vm-row offset,
                                   //  distinct far buses | lower ones << 16) inside one period

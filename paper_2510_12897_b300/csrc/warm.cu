@@ -231,12 +231,13 @@ cudaError_t gemm(bool ak, bool bk, const GemmArgs &g, cudaStream_t s)
 struct WarmDev {
     int B, nb, ng, nl, nload, Kin, Nout, nbp, ngp, ref;
     double va_scale, penalty;
-    const double *pd0, *qd0;                 // base loads
+    const double *pk, *qk;                   // 5 / base load (0 where the base is 0)
     const double *vmin, *vmax;               // per bus
     const double *pmin, *pmax, *qmin, *qmax; // per generator
 };
 
-// u = normalised loads (BF16, zero padding)
+// u = normalised loads (BF16, zero padding): (load / base - 1) / 0.2 as one
+// FMA with the precomputed 5 / base (0 where the base load is 0)
 __global__ void prep_kernel(const WarmDev w, const double *pd, const double *qd, bf16 *U)
 {
     const int64_t total = (int64_t)w.B * w.Kin;
@@ -245,11 +246,11 @@ __global__ void prep_kernel(const WarmDev w, const double *pd, const double *qd,
         const int s = (int)(it / w.Kin), j = (int)(it - (int64_t)s * w.Kin);
         float u = 0.f;
         if (j < w.nload) {
-            const double b = w.pd0[j];
-            u = b > 0.0 ? (float)((pd[(int64_t)s * w.nload + j] / b - 1.0) / 0.2) : 0.f;
+            const double k = w.pk[j];
+            u = k != 0.0 ? (float)fma(pd[(int64_t)s * w.nload + j], k, -5.0) : 0.f;
         } else if (j < 2 * w.nload) {
-            const double b = w.qd0[j - w.nload];
-            u = b > 0.0 ? (float)((qd[(int64_t)s * w.nload + j - w.nload] / b - 1.0) / 0.2) : 0.f;
+            const double k = w.qk[j - w.nload];
+            u = k != 0.0 ? (float)fma(qd[(int64_t)s * w.nload + j - w.nload], k, -5.0) : 0.f;
         }
         U[it] = __float2bfloat16_rn(u);
     }
@@ -340,14 +341,17 @@ __global__ void bound_kernel(const WarmDev w, const double *x, const double *xl,
         part[blockIdx.x] = s;
 }
 
-// batch means: loss, cost, sum of squared residuals (constraints and bounds)
+// batch means: loss, cost, sum of squared residuals (constraints and bounds);
+// one warp, lane-strided partial sums then a fixed shuffle tree
 __global__ void stats_kernel(const WarmDev w, const double *part, int nparts, const double *obj,
                              double *stats)
 {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double r = 0.0;
-        for (int q = 0; q < nparts; q++)
-            r += part[q];
+    double r = 0.0;
+    for (int q = threadIdx.x; q < nparts; q += 32)
+        r += part[q];
+    for (int off = 16; off; off >>= 1)
+        r += __shfl_down_sync(0xffffffffu, r, off);
+    if (threadIdx.x == 0) {
         const double cost = obj[0] / w.B, res = r / w.B;
         stats[0] = cost + w.penalty * res;
         stats[1] = cost;
@@ -419,15 +423,24 @@ __global__ void dmap_kernel(const WarmDev w, const double *x, const double *u2, 
     }
 }
 
-// column sums of a [rows][cols] FP32 matrix (bias gradients), one thread
-// per column, rows in order
+// column sums of a [rows][cols] FP32 matrix (bias gradients): a block of
+// 32 x 32 threads per 32 columns; thread (c, r) sums rows r, r + 32, ... of
+// column c, then row 0 of the block adds the 32 partials in order
 __global__ void colsum_kernel(const float *X, int rows, int cols, float *out)
 {
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < cols; j += gridDim.x * blockDim.x) {
-        float acc = 0.f;
-        for (int i = 0; i < rows; i++)
-            acc += X[(int64_t)i * cols + j];
-        out[j] = acc;
+    __shared__ float part[32][33];
+    const int c = blockIdx.x * 32 + threadIdx.x;
+    float acc = 0.f;
+    if (c < cols)
+        for (int i = threadIdx.y; i < rows; i += 32)
+            acc += X[(int64_t)i * cols + c];
+    part[threadIdx.y][threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.y == 0 && c < cols) {
+        float s = 0.f;
+        for (int r = 0; r < 32; r++)
+            s += part[r][threadIdx.x];
+        out[c] = s;
     }
 }
 
@@ -475,7 +488,7 @@ struct opf_warm {
     std::vector<void *> allocs;
     float *params = nullptr, *grads = nullptr, *am = nullptr, *av = nullptr;
     bf16 *W1h = nullptr, *W2h = nullptr, *W3h = nullptr;
-    double *pd0 = nullptr, *qd0 = nullptr, *vmin = nullptr, *vmax = nullptr, *pmin = nullptr,
+    double *pk = nullptr, *qk = nullptr, *vmin = nullptr, *vmax = nullptr, *pmin = nullptr,
            *pmax = nullptr, *qmin = nullptr, *qmax = nullptr, *gl = nullptr, *gu = nullptr,
            *xl = nullptr, *xu = nullptr;
     bf16 *U = nullptr, *H1 = nullptr, *H2 = nullptr, *dYh = nullptr, *dZ2h = nullptr, *dZ1h = nullptr;
@@ -538,8 +551,8 @@ WarmDev dev_of(const opf_warm *w)
     d.ref = w->ref;
     d.va_scale = w->va_scale;
     d.penalty = w->penalty;
-    d.pd0 = w->pd0;
-    d.qd0 = w->qd0;
+    d.pk = w->pk;
+    d.qk = w->qk;
     d.vmin = w->vmin;
     d.vmax = w->vmax;
     d.pmin = w->pmin;
@@ -596,7 +609,7 @@ int backward(opf_warm *w, cudaStream_t s)
     g.A = w->dYh; g.B = w->H2; g.M = w->Nout; g.N = H; g.K = B; g.lda = w->Nout; g.ldb = H; g.ldc = H;
     g.epi = EPI_STORE; g.outf = gr + w->oW3;
     cudaError_t e = gemm(false, false, g, s);
-    colsum_kernel<<<grid1(w->Nout), 256, 0, s>>>(w->dYf, B, w->Nout, gr + w->ob3);
+    colsum_kernel<<<(w->Nout + 31) / 32, dim3(32, 32), 0, s>>>(w->dYf, B, w->Nout, gr + w->ob3);
     // dZ2 = (dY W3) * gelu'(Z2)
     g = GemmArgs{};
     g.A = w->dYh; g.B = w->W3h; g.M = B; g.N = H; g.K = w->Nout; g.lda = w->Nout; g.ldb = H; g.ldc = H;
@@ -609,7 +622,7 @@ int backward(opf_warm *w, cudaStream_t s)
     g.epi = EPI_STORE; g.outf = gr + w->oW2;
     if (e == cudaSuccess)
         e = gemm(false, false, g, s);
-    colsum_kernel<<<grid1(H), 256, 0, s>>>(w->dZ2f, B, H, gr + w->ob2);
+    colsum_kernel<<<(H + 31) / 32, dim3(32, 32), 0, s>>>(w->dZ2f, B, H, gr + w->ob2);
     // dZ1 = (dZ2 W2) * gelu'(Z1)
     g = GemmArgs{};
     g.A = w->dZ2h; g.B = w->W2h; g.M = B; g.N = H; g.K = H; g.lda = H; g.ldb = H; g.ldc = H;
@@ -622,7 +635,7 @@ int backward(opf_warm *w, cudaStream_t s)
     g.epi = EPI_STORE; g.outf = gr + w->oW1;
     if (e == cudaSuccess)
         e = gemm(false, false, g, s);
-    colsum_kernel<<<grid1(H), 256, 0, s>>>(w->dZ1f, B, H, gr + w->ob1);
+    colsum_kernel<<<(H + 31) / 32, dim3(32, 32), 0, s>>>(w->dZ1f, B, H, gr + w->ob1);
     if (e == cudaSuccess)
         e = cudaGetLastError();
     return check_cuda(e, "backward GEMMs");
@@ -743,7 +756,11 @@ int opf_warm_create(const opf_network *net, const opf_warm_opts *opts, opf_warm 
     init_rows(w->oW1, w->Kin, 0, w->H, 2 * w->nload);
     init_rows(w->oW2, w->H, 0, w->H, w->H);
     // W3 and b3 start at zero: the untrained network proposes the flat start
-    std::vector<double> pd0(net->load_pd, net->load_pd + w->nload), qd0(net->load_qd, net->load_qd + w->nload);
+    std::vector<double> pk(w->nload), qk(w->nload);
+    for (int l = 0; l < w->nload; l++) {
+        pk[l] = net->load_pd[l] > 0.0 ? 5.0 / net->load_pd[l] : 0.0;
+        qk[l] = net->load_qd[l] > 0.0 ? 5.0 / net->load_qd[l] : 0.0;
+    }
     std::vector<double> vmin(net->bus_vmin, net->bus_vmin + w->nb), vmax(net->bus_vmax, net->bus_vmax + w->nb);
     std::vector<double> pmin(net->gen_pmin, net->gen_pmin + w->ng), pmax(net->gen_pmax, net->gen_pmax + w->ng);
     std::vector<double> qmin(net->gen_qmin, net->gen_qmin + w->ng), qmax(net->gen_qmax, net->gen_qmax + w->ng);
@@ -759,8 +776,8 @@ int opf_warm_create(const opf_network *net, const opf_warm_opts *opts, opf_warm 
     if (!rc) rc = walloc(w, &w->W1h, (size_t)w->H * w->Kin);
     if (!rc) rc = walloc(w, &w->W2h, (size_t)w->H * w->H);
     if (!rc) rc = walloc(w, &w->W3h, (size_t)w->Nout * w->H);
-    if (!rc) rc = wupload(w, &w->pd0, pd0);
-    if (!rc) rc = wupload(w, &w->qd0, qd0);
+    if (!rc) rc = wupload(w, &w->pk, pk);
+    if (!rc) rc = wupload(w, &w->qk, qk);
     if (!rc) rc = wupload(w, &w->vmin, vmin);
     if (!rc) rc = wupload(w, &w->vmax, vmax);
     if (!rc) rc = wupload(w, &w->pmin, pmin);
