@@ -61,6 +61,9 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=256)
     p.add_argument("--no-warm", action="store_true", help="skip the learned warm-start section")
     p.add_argument("--warm-epochs", type=int, default=100)
+    p.add_argument("--profile-batched", type=int, default=0, metavar="REPS",
+                   help="profiling aid: only run REPS plain evaluations of the 10k-bus grid "
+                        "with 32 load scenarios in one model, then exit")
     return p.parse_args()
 
 
@@ -257,6 +260,18 @@ def main():
         dist.barrier()
     dev = torch.device("cuda", local)
     f64 = torch.float64
+    if args.profile_batched:
+        sc = synth.scenarios(synth.case10k(), 32, seed=5)
+        Mb = opf.Model(sc)
+        rng = np.random.default_rng(7)
+        xb = torch.tensor(synth.random_point(sc, rng), device=dev)
+        lb = torch.tensor(rng.standard_normal(Mb.m), device=dev)
+        ob = [torch.empty(k, dtype=f64, device=dev) for k in (1, Mb.n, Mb.m, Mb.nnzj, Mb.nnzh)]
+        for _ in range(args.profile_batched):
+            Mb.eval_all(xb, lb, 1.0, *ob)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_batched": args.profile_batched, "n": Mb.n, "m": Mb.m}))
+        return
 
     g = synth.case10k(args.seed)
     R = max(1, args.sets)
@@ -456,6 +471,13 @@ def batched_vs_plain(torch, opf, synth, stream, dev):
     def bufs(M):
         return [torch.empty(k, dtype=f64, device=dev) for k in (1, M.n, M.m, M.nnzj, M.nnzh)]
 
+    def tune_all(models, x, lam):
+        """The autotuner's shape for the first per-instance model, used by all."""
+        cfg = models[0].autotune(x, lam, reps=20, stream=stream)[0]
+        for Mk in models:
+            Mk.set_launch(**cfg)
+        return cfg
+
     rng = np.random.default_rng(7)
     # 10k grid: S load scenarios in one launch vs S single-scenario calls
     S = 32
@@ -465,12 +487,14 @@ def batched_vs_plain(torch, opf, synth, stream, dev):
     xb = torch.tensor(synth.random_point(sc, rng), device=dev)
     lb = torch.tensor(rng.standard_normal(B.m), device=dev)
     ob = bufs(B)
+    tuned = {"batched": B.autotune(xb, lb, reps=5, stream=stream)[0]}
     tb = graph_us(lambda: B.eval_all(xb, lb, 1.0, *ob, stream=stream))
     grids = [g10.copy(load_pd=sc.load_pd[t:t + 1], load_qd=sc.load_qd[t:t + 1]) for t in range(S)]
     singles = [opf.Model(gt) for gt in grids]
     xs_ = [torch.tensor(synth.random_point(gt, rng), device=dev) for gt in grids]
     ls_ = [torch.tensor(rng.standard_normal(s.m), device=dev) for s in singles]
     os_ = [bufs(s) for s in singles]
+    tuned["plain"] = tune_all(singles, xs_[0], ls_[0])
 
     def plain_10k():
         for s, x, l, o in zip(singles, xs_, ls_, os_):
@@ -479,7 +503,7 @@ def batched_vs_plain(torch, opf, synth, stream, dev):
     tp = graph_us(plain_10k)
     ev = eval_bytes(g10, singles[0].nnzh)
     out["case10k_32_scenarios"] = {
-        "batched_us": tb, "plain_loop_us": tp, "speedup": tp / tb,
+        "batched_us": tb, "plain_loop_us": tp, "speedup": tp / tb, "launch": tuned,
         "evals_per_s": S * 1e6 / tb,
         "achieved_gbs": S * ev / (tb * 1e-6) / 1e9,
         "hbm_frac": S * ev / (tb * 1e-6) / 1e9 / load_peaks()[0]}
@@ -490,6 +514,7 @@ def batched_vs_plain(torch, opf, synth, stream, dev):
     xb = torch.tensor(synth.random_point(mp, rng), device=dev)
     lb = torch.tensor(rng.standard_normal(B.m), device=dev)
     ob = bufs(B)
+    tuned = {"batched": B.autotune(xb, lb, reps=5, stream=stream)[0]}
     tb = graph_us(lambda: B.eval_all(xb, lb, 1.0, *ob, stream=stream))
     grids = [mp.copy(load_pd=mp.load_pd[t:t + 1], load_qd=mp.load_qd[t:t + 1], ramp_ratio=0.0)
              for t in range(mp.nperiod)]
@@ -497,13 +522,14 @@ def batched_vs_plain(torch, opf, synth, stream, dev):
     xs_ = [torch.tensor(synth.random_point(gt, rng), device=dev) for gt in grids]
     ls_ = [torch.tensor(rng.standard_normal(s.m), device=dev) for s in singles]
     os_ = [bufs(s) for s in singles]
+    tuned["plain"] = tune_all(singles, xs_[0], ls_[0])
 
     def plain_mp():
         for s, x, l, o in zip(singles, xs_, ls_, os_):
             s.eval_all(x, l, 1.0, *o, stream=stream)
 
     tp = graph_us(plain_mp)
-    out["mp2k_96"] = {"batched_us": tb, "plain_loop_us": tp, "speedup": tp / tb,
+    out["mp2k_96"] = {"batched_us": tb, "plain_loop_us": tp, "speedup": tp / tb, "launch": tuned,
                       "batched_evals_per_s": 1e6 / tb, "period_evals_per_s": 96e6 / tb}
     del B, singles, os_
     # N-1: 1,000 buses, base + 500 contingencies
@@ -512,18 +538,20 @@ def batched_vs_plain(torch, opf, synth, stream, dev):
     xb = torch.tensor(np.concatenate([synth.random_point(s, rng) for s in insts]), device=dev)
     lb = torch.tensor(rng.standard_normal(B.m), device=dev)
     ob = bufs(B)
+    tuned = {"batched": B.autotune(xb, lb, reps=5, stream=stream)[0]}
     tb = graph_us(lambda: B.eval_all(xb, lb, 1.0, *ob, stream=stream))
     singles = [opf.Model(s) for s in insts]
     xs_ = [torch.tensor(synth.random_point(s, rng), device=dev) for s in insts]
     ls_ = [torch.tensor(rng.standard_normal(s.m), device=dev) for s in singles]
     os_ = [bufs(s) for s in singles]
+    tuned["plain"] = tune_all(singles, xs_[0], ls_[0])
 
     def plain_sc():
         for s, x, l, o in zip(singles, xs_, ls_, os_):
             s.eval_all(x, l, 1.0, *o, stream=stream)
 
     tp = graph_us(plain_sc, reps=5)
-    out["sc1k_501"] = {"batched_us": tb, "plain_loop_us": tp, "speedup": tp / tb,
+    out["sc1k_501"] = {"batched_us": tb, "plain_loop_us": tp, "speedup": tp / tb, "launch": tuned,
                        "instance_evals_per_s": 501e6 / tb}
     return out
 

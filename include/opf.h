@@ -92,10 +92,18 @@ typedef struct opf_model opf_model;
 
 /* Launch shape of the two evaluation kernels (branch phase, bus phase). */
 typedef struct {
-    int32_t branch_block; /* threads per block, branch kernel (32..1024, multiple of 32) */
-    int32_t bus_block;    /* threads per block, bus/generator kernel */
+    int32_t branch_block; /* threads per block, branch kernel (32..512, multiple of 32;
+                             at most 256 with branch_occupancy 1) */
+    int32_t bus_block;    /* threads per block, bus/generator kernel (32..1024, multiple of
+                             32; more than 256 runs as 256) */
     int32_t branch_ctas_per_sm; /* persistent grid = ctas_per_sm * SMs; 0 = one thread per item */
     int32_t bus_ctas_per_sm;
+    int32_t bus_order;    /* 0: buses in id order; 1: buses sorted by arc count into warps
+                             of 32, warps dealt heaviest and lightest alternately (fewer
+                             idle lanes in the slot loops: better for large batches) */
+    int32_t branch_occupancy; /* 0: branch kernel compiled for up to 128 registers per
+                                 thread (shortest chains); 1: for 80 (three blocks of 256
+                                 per SM: more warps to hide latency in large batches) */
 } opf_launch;
 
 /* Create a model for one network (Listing 3; multi-period if nperiod > 1).
@@ -237,8 +245,8 @@ int opf_sincos(opf_model *model, const double *d_angle, int64_t n, double *d_sin
 int opf_get_launch(const opf_model *model, opf_launch *cfg);
 int opf_set_launch(opf_model *model, const opf_launch *cfg);
 
-/* Autotuner: times each candidate launch shape of the fused opf_eval_all on
- * this model (CUDA events, `reps` repetitions each, on `stream`), keeps the
+/* Autotuner: times each candidate launch shape (block sizes, persistence,
+ * bus order, branch occupancy) of the fused opf_eval_all on this model (CUDA events, `reps` repetitions each, on `stream`), keeps the
  * fastest and returns it in *best with its time per eval in *best_us.
  * Allocates temporary output buffers for the duration of the call. */
 int opf_autotune(opf_model *model, const double *d_x, const double *d_lambda, int32_t reps,

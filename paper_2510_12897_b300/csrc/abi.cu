@@ -408,6 +408,15 @@ int opf_set_launch(opf_model *m, const opf_launch *cfg)
             set_error("block size %d not a multiple of 32 in [32, 1024]", b);
             return OPF_EINVAL;
         }
+    if (cfg->bus_order < 0 || cfg->bus_order > 1 || cfg->branch_occupancy < 0 || cfg->branch_occupancy > 1) {
+        set_error("bus_order and branch_occupancy must be 0 or 1");
+        return OPF_EINVAL;
+    }
+    if (cfg->branch_block > (cfg->branch_occupancy ? 256 : 512)) {
+        set_error("branch_block %d above the branch kernel's limit (%d)", cfg->branch_block,
+                  cfg->branch_occupancy ? 256 : 512);
+        return OPF_EINVAL;
+    }
     if (cfg->branch_ctas_per_sm < 0 || cfg->bus_ctas_per_sm < 0 || cfg->branch_ctas_per_sm > 64 ||
         cfg->bus_ctas_per_sm > 64) {
         set_error("ctas_per_sm must be in [0, 64]");
@@ -447,13 +456,17 @@ int opf_autotune(opf_model *m, const double *d_x, const double *d_lambda, int32_
     const int bblocks[] = {32, 64, 128, 256, 512};
     const int ublocks[] = {32, 64, 128, 256};  // the bus kernel stages at most 8 warps
     const int ctas[] = {0, 2, 4, 8, 16};
+    for (int occ = 0; occ < 2; occ++)
+    for (int order = 0; order < 2; order++)
     for (int bb : bblocks)
         for (int bu : ublocks)
             for (int cb : ctas)
                 for (int cu : ctas) {
                     if (cu != 0 && cu != cb)  // keep the search small: equal persistence
                         continue;
-                    M.launch = opf_launch{bb, bu, cb, cu};
+                    if (occ && bb > 256)
+                        continue;
+                    M.launch = opf_launch{bb, bu, cb, cu, order, occ};
                     rc = launch_eval(M, a, W_OBJ | W_GRAD | W_CONS | W_JAC | W_HESS, s);  // warm-up
                     cudaEventRecord(e0, s);
                     for (int r = 0; r < reps && !rc; r++)

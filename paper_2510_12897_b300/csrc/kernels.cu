@@ -57,6 +57,7 @@ struct KParams {
     int64_t link_c0;    // first linking row
     int32_t want_grad, want_obj;
     int64_t nbr_items, nbus_items, ngen_items;
+    const int32_t *order = nullptr;  // bus-phase order within an instance, or null for id order
     const double *__restrict__ x;
     const double *__restrict__ lam;
     double sigma;
@@ -199,8 +200,8 @@ __device__ __forceinline__ BrStatic load_br(const DevArrays &d, int kb, bool nee
     return s;
 }
 
-template <bool CONS, bool JAC, bool HESS, bool ONE>
-__global__ void __launch_bounds__(512) branch_kernel(const KParams P)
+template <bool CONS, bool JAC, bool HESS, bool ONE, bool OCC>
+__global__ void __launch_bounds__(OCC ? 256 : 512, OCC ? 3 : 1) branch_kernel(const KParams P)
 {
     cudaTriggerProgrammaticLaunchCompletion();
     const DevArrays &d = P.d;
@@ -387,8 +388,7 @@ __global__ void __launch_bounds__(kBusBlockMax) bus_kernel(const KParams P)
                 split((int)(item - __ldg(d.bus_items + q.s)), __ldg(&I->nb), __ldg(&I->T), q.t, r);
                 bus0 = __ldg(&I->bus0);
             }
-            q.e = r;  // buses in id order (warps mix slot counts; grouping them by count
-                      // put the highest-degree buses into one straggler warp)
+            q.e = P.order ? __ldg(P.order + bus0 + r) : r;
             const int ib = bus0 + q.e;
             q.a = __ldg(d.bus_a + ib);
             q.b = __ldg(d.bus_b + ib);
@@ -964,13 +964,18 @@ cudaError_t launch_pdl(K kernel, int grid, int block, cudaStream_t s, const KPar
 }
 
 template <bool C, bool J, bool H>
-cudaError_t dispatch(const KParams &P, bool one, bool run_branch, bool run_bus, int gb, int bb,
+cudaError_t dispatch(const KParams &P, bool one, bool occ, bool run_branch, bool run_bus, int gb, int bb,
                      int gu, int bu, cudaStream_t s)
 {
     cudaError_t e = cudaSuccess;
-    if (run_branch)
-        e = one ? launch_pdl(branch_kernel<C, J, H, true>, gb, bb, s, P)
-                : launch_pdl(branch_kernel<C, J, H, false>, gb, bb, s, P);
+    if (run_branch) {
+        if (occ)
+            e = one ? launch_pdl(branch_kernel<C, J, H, true, true>, gb, bb, s, P)
+                    : launch_pdl(branch_kernel<C, J, H, false, true>, gb, bb, s, P);
+        else
+            e = one ? launch_pdl(branch_kernel<C, J, H, true, false>, gb, bb, s, P)
+                    : launch_pdl(branch_kernel<C, J, H, false, false>, gb, bb, s, P);
+    }
     if (e != cudaSuccess || !run_bus)
         return e;
     return one ? launch_pdl(bus_kernel<C, J, H, true>, gu, bu, s, P)
@@ -1014,17 +1019,19 @@ int launch_all(Model &M, const EvalArgs &a, unsigned what, cudaStream_t s, int p
     const bool run_branch = (phases & 1) && (C || J || H || P.want_grad) && M.nbr_items > 0;
     const bool run_bus = phases & 2;
     const bool one = M.ninst == 1;
+    const bool occ = L.branch_occupancy != 0;
     const int bb = L.branch_block;
+    P.order = L.bus_order ? M.d.bus_order : nullptr;
     cudaError_t e;
     switch ((C ? 1 : 0) | (J ? 2 : 0) | (H ? 4 : 0)) {
-    case 0: e = dispatch<false, false, false>(P, one, run_branch, run_bus, gb, bb, gu, bu, s); break;
-    case 1: e = dispatch<true, false, false>(P, one, run_branch, run_bus, gb, bb, gu, bu, s); break;
-    case 2: e = dispatch<false, true, false>(P, one, run_branch, run_bus, gb, bb, gu, bu, s); break;
-    case 3: e = dispatch<true, true, false>(P, one, run_branch, run_bus, gb, bb, gu, bu, s); break;
-    case 4: e = dispatch<false, false, true>(P, one, run_branch, run_bus, gb, bb, gu, bu, s); break;
-    case 5: e = dispatch<true, false, true>(P, one, run_branch, run_bus, gb, bb, gu, bu, s); break;
-    case 6: e = dispatch<false, true, true>(P, one, run_branch, run_bus, gb, bb, gu, bu, s); break;
-    default: e = dispatch<true, true, true>(P, one, run_branch, run_bus, gb, bb, gu, bu, s); break;
+    case 0: e = dispatch<false, false, false>(P, one, occ, run_branch, run_bus, gb, bb, gu, bu, s); break;
+    case 1: e = dispatch<true, false, false>(P, one, occ, run_branch, run_bus, gb, bb, gu, bu, s); break;
+    case 2: e = dispatch<false, true, false>(P, one, occ, run_branch, run_bus, gb, bb, gu, bu, s); break;
+    case 3: e = dispatch<true, true, false>(P, one, occ, run_branch, run_bus, gb, bb, gu, bu, s); break;
+    case 4: e = dispatch<false, false, true>(P, one, occ, run_branch, run_bus, gb, bb, gu, bu, s); break;
+    case 5: e = dispatch<true, false, true>(P, one, occ, run_branch, run_bus, gb, bb, gu, bu, s); break;
+    case 6: e = dispatch<false, true, true>(P, one, occ, run_branch, run_bus, gb, bb, gu, bu, s); break;
+    default: e = dispatch<true, true, true>(P, one, occ, run_branch, run_bus, gb, bb, gu, bu, s); break;
     }
     if (e == cudaSuccess)
         e = cudaGetLastError();

@@ -61,6 +61,7 @@ struct __align__(16) InstDev {
 static_assert(sizeof(InstDev) % 16 == 0, "InstDev is loaded as int4 words");
 
 struct DevArrays {
+    int32_t *bus_order = nullptr; // per instance: buses by arc count, warps dealt heavy / light
     // branches (concatenated over instances)
     int4 *br = nullptr;           // local (f, t, slot of the from-arc, slot of the to-arc)
     int2 *br_jb = nullptr;        // entries of the from-arc and to-arc in their buses' balance

@@ -185,6 +185,7 @@ int build_model(const opf_network *nets, int32_t ninst, double link_ratio, bool 
     // concatenated host arrays
     std::vector<int4> br, bus_a, bus_b;
     std::vector<int2> bus_c, br_jb;
+    std::vector<int32_t> bus_order;
     std::vector<double2> y_ff, y_ft, y_tf, y_tt, gsbs, pbnd, qbnd, vbnd;
     std::vector<double> rate2, Pd, Qd, c2, c1, c0;
     std::vector<int32_t> gen_list, load_ptr, load_list, gen_busid;
@@ -345,6 +346,26 @@ int build_model(const opf_network *nets, int32_t ninst, double link_ratio, bool 
             for (int k = 0; k < nl; k++)
                 br_jb.push_back(make_int2(jb[k], jb[nl + k]));
         }
+        // ---- alternative bus-phase order: buses sorted by arc count (stable),
+        // cut into warps of 32, the warps dealt heaviest, lightest, next
+        // heaviest, ... so that lanes of a warp walk similar slot counts and
+        // the heavy warps spread over the grid
+        {
+            std::vector<int32_t> ord(nb);
+            std::iota(ord.begin(), ord.end(), 0);
+            std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
+                return H.arc_ptr[a + 1] - H.arc_ptr[a] < H.arc_ptr[b + 1] - H.arc_ptr[b];
+            });
+            const int nw = (nb + 31) / 32;
+            int lo = 0, hi = nw - 1;
+            bool heavy = true;
+            while (lo <= hi) {
+                const int w = heavy ? hi-- : lo++;
+                heavy = !heavy;
+                for (int q = w * 32; q < std::min(nb, w * 32 + 32); q++)
+                    bus_order.push_back(ord[q]);
+            }
+        }
         // ---- loads per bus (ascending id), the order the demand sums use
         {
             std::vector<int32_t> cnt(nb + 1, 0);
@@ -420,7 +441,7 @@ int build_model(const opf_network *nets, int32_t ninst, double link_ratio, bool 
     M->ngen_items = gen_items.back();
     M->narc_slots = so;
     M->max_part = 16 * M->num_sms;
-    M->launch = opf_launch{128, 128, 0, 0};
+    M->launch = opf_launch{128, 128, 0, 0, 0, 0};
 
     if (!device) {
         *out = M;
@@ -436,7 +457,7 @@ int build_model(const opf_network *nets, int32_t ninst, double link_ratio, bool 
     for (int k = -kTrigK; k <= kTrigK; k++)
         trig.push_back(make_double2(std::sin((double)k / kTrigScale), std::cos((double)k / kTrigScale)));
     UP(trig, trig)
-    UP(br_jb, br_jb) UP(load_ptr, load_ptr) UP(load_list, load_list)
+    UP(br_jb, br_jb) UP(bus_order, bus_order) UP(load_ptr, load_ptr) UP(load_list, load_list)
     UP(gen_busid, gen_busid)
     UP(bus_a, bus_a) UP(bus_b, bus_b) UP(bus_c, bus_c) UP(gsbs, gsbs) UP(slot_code, slot_code) UP(gen_list, gen_list)
     UP(Pd, Pd) UP(Qd, Qd) UP(c2, c2) UP(c1, c1) UP(c0, c0) UP(pbnd, pbnd) UP(qbnd, qbnd)

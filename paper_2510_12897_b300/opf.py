@@ -45,7 +45,8 @@ class OpfBatchOpts(ctypes.Structure):
 
 class OpfLaunch(ctypes.Structure):
     _fields_ = [("branch_block", ctypes.c_int32), ("bus_block", ctypes.c_int32),
-                ("branch_ctas_per_sm", ctypes.c_int32), ("bus_ctas_per_sm", ctypes.c_int32)]
+                ("branch_ctas_per_sm", ctypes.c_int32), ("bus_ctas_per_sm", ctypes.c_int32),
+                ("bus_order", ctypes.c_int32), ("branch_occupancy", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -316,8 +317,10 @@ class Model:
         _check(lib().opf_get_launch(self.h, ctypes.byref(cfg)))
         return cfg.as_dict()
 
-    def set_launch(self, branch_block=128, bus_block=128, branch_ctas_per_sm=0, bus_ctas_per_sm=0):
-        cfg = OpfLaunch(branch_block, bus_block, branch_ctas_per_sm, bus_ctas_per_sm)
+    def set_launch(self, branch_block=128, bus_block=128, branch_ctas_per_sm=0, bus_ctas_per_sm=0,
+                   bus_order=0, branch_occupancy=0):
+        cfg = OpfLaunch(branch_block, bus_block, branch_ctas_per_sm, bus_ctas_per_sm, bus_order,
+                        branch_occupancy)
         _check(lib().opf_set_launch(self.h, ctypes.byref(cfg)))
 
     def autotune(self, x, lam, reps: int = 20, stream=None):

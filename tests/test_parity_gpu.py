@@ -182,6 +182,12 @@ def test_host_buffers_variant(torch, oracle_mod):
     dict(branch_block=32, bus_block=32, branch_ctas_per_sm=1, bus_ctas_per_sm=1),
     dict(branch_block=64, bus_block=256, branch_ctas_per_sm=0, bus_ctas_per_sm=0),
     dict(branch_block=512, bus_block=64, branch_ctas_per_sm=2, bus_ctas_per_sm=0),
+    dict(branch_block=256, bus_block=32, branch_ctas_per_sm=0, bus_ctas_per_sm=0, bus_order=1,
+         branch_occupancy=1),
+    dict(branch_block=32, bus_block=128, branch_ctas_per_sm=4, bus_ctas_per_sm=4, bus_order=1,
+         branch_occupancy=0),
+    dict(branch_block=128, bus_block=64, branch_ctas_per_sm=2, bus_ctas_per_sm=0, bus_order=0,
+         branch_occupancy=1),
 ])
 def test_launch_shapes(torch, oracle_mod, launch):
     """Every launch shape the autotuner may pick gives parity (grid-stride
