@@ -58,6 +58,8 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--seed", type=int, default=10000)
     p.add_argument("--no-autotune", action="store_true", help="default launch shape (profiling runs)")
+    p.add_argument("--launch", default=None, metavar="BB,BU,CB,CU,ORDER,OCC",
+                   help="fixed launch shape instead of the autotuner's (profiling runs)")
     p.add_argument("--e2e-steps", type=int, default=256)
     p.add_argument("--no-warm", action="store_true", help="skip the learned warm-start section")
     p.add_argument("--warm-epochs", type=int, default=100)
@@ -77,10 +79,10 @@ def load_peaks():
         return 6400.0, "fallback"
 
 
-def profile_traffic():
-    """DRAM bytes per launch of the branch kernel from the committed ncu
-    summary (a line 'dram_bytes_per_launch: N'), or None."""
-    path = os.path.join(ROOT, "profiles", "branch_kernel_case10k.md")
+def profile_traffic(kernel):
+    """DRAM bytes per launch of the branch or bus kernel from its committed
+    ncu summary (a line 'dram_bytes_per_launch: N'), or None."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_kernel_case10k.md")
     try:
         m = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", open(path).read())
         return float(m.group(1)) if m else None
@@ -286,7 +288,11 @@ def main():
     stream = torch.cuda.Stream(device=dev)
 
     # launch shape: the autotuner's pick on this workload, shared by all sets
-    if args.no_autotune:
+    if args.launch:
+        keys = ("branch_block", "bus_block", "branch_ctas_per_sm", "bus_ctas_per_sm", "bus_order",
+                "branch_occupancy")
+        best, tuned_us = dict(zip(keys, (int(v) for v in args.launch.split(",")))), None
+    elif args.no_autotune:
         best, tuned_us = M0.get_launch(), None
     else:
         best, tuned_us = M0.autotune(xs[0], ls[0], reps=20, stream=stream)
@@ -377,7 +383,7 @@ def main():
     dom_bytes = br_bytes if dominant == "branch" else ev_bytes - br_bytes
     achieved = dom_bytes / (dom_us * 1e-6) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": profile_traffic() if dominant == "branch" else None,
+                "frac": achieved / hbm, "traffic": profile_traffic(dominant),
                 "kernel": f"{dominant} phase", "kernel_us": dom_us,
                 "algorithmic_bytes_per_launch": dom_bytes, "peak_kind": peak_kind}
 
