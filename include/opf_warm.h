@@ -10,8 +10,8 @@
  * starting point. Network: u -> GELU(W1 u + b1) -> GELU(W2 h1 + b2) ->
  * W3 h2 + b3 = y, GELU the tanh form 0.5 z (1 + tanh(sqrt(2/pi)(z + 0.044715
  * z^3))) (Hendrycks and Gimpel, 2016). Weights and activations in BF16,
- * products accumulated in FP32 (tensor-core mma), master weights, biases and
- * optimiser state in FP32.
+ * products accumulated in FP32 in tensor memory (tcgen05.mma fed by TMA),
+ * master weights, biases and optimiser state in FP32.
  *
  * Input u (2 nload, zero-padded to a multiple of 128): for every load l,
  * (Pd_l / Pd0_l - 1) / 0.2 then (Qd_l / Qd0_l - 1) / 0.2, Pd0/Qd0 the
@@ -102,7 +102,10 @@ int opf_warm_loss_grad(opf_warm *w, const double *d_load_pd, const double *d_loa
 int opf_warm_set_lr(opf_warm *w, double lr, double lr_out);
 
 /* FP32 master parameters to / from HOST memory (n_params floats, layout as
- * above); setting also refreshes the BF16 copies and clears Adam's state. */
+ * above); setting also refreshes the BF16 copies and clears Adam's state.
+ * Getting synchronises the device and also returns OPF_ECUDA if a
+ * tensor-core GEMM gave up waiting on one of its barriers since the last
+ * check (the results of that GEMM are then invalid). */
 int opf_warm_get_params(const opf_warm *w, float *h_params);
 int opf_warm_set_params(opf_warm *w, const float *h_params);
 

@@ -1,6 +1,7 @@
 // Learned warm start (include/opf_warm.h): a three-layer BF16 MLP trained on
 // the GPU with hand-written tensor-core GEMMs, penalty gradients from the
 // library's own callback kernels (cons, grad, J^T v) and Adam.
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -23,28 +24,40 @@ namespace {
 
 // ------------------------------------------------------------------ GEMM --
 //
-// C[M x N] = A[M x K] * B[K x N] with BF16 operands and FP32 accumulation on
-// the tensor cores (mma.sync m16n8k16). A is stored K-contiguous ([M][lda],
-// AK) or M-contiguous ([K][lda]); B is stored K-contiguous ([N][ldb], BK) or
-// N-contiguous ([K][ldb]). Block tile 128 x 128 x 32, eight warps of 64 x 32,
-// two cp.async stages; ldmatrix (.trans for the contiguous-in-M/N layouts)
-// builds the fragments. M and N must be multiples of 128, K of 32, leading
-// dimensions multiples of 8 (16-byte rows for cp.async).
+// C[M x N] = A[M x K] B[N x K]^T with BF16 operands and FP32 accumulation on
+// the 5th-generation tensor cores. Both operands are row-major with K
+// contiguous (the backward pass feeds transposed copies). One CTA of 128
+// threads per 128 x 128 tile of C:
+//   warp 0, one lane   TMA producer: 128 x 64 tiles of A and B (128-byte
+//                      swizzle) into a 3-stage ring, completion counted in
+//                      bytes on the stage's "full" mbarrier;
+//   warp 1, one lane   MMA issuer: per stage four tcgen05.mma (M 128, N 128,
+//                      K 16) from shared-memory descriptors into a 128-column
+//                      FP32 accumulator in tensor memory; tcgen05.commit
+//                      frees the stage ("empty") and finally signals "done";
+//   warps 0-3          epilogue: tcgen05.ld of their 32 accumulator lanes,
+//                      16 columns at a time, bias / GELU / GELU' in FP32,
+//                      stores.
+// Every wait on an mbarrier gives up after a bounded number of polls and
+// records the timeout in a device flag the host reads (no unbounded spin).
+// M and N must be multiples of 128, K of 64.
 
-constexpr int GBM = 128, GBN = 128, GBK = 32;
-constexpr int SK = GBK + 8;   // padded row of a K-contiguous tile (80 bytes)
-constexpr int SMN = GBM + 8;  // padded row of an M- or N-contiguous tile (272 bytes)
+constexpr int UBM = 128, UBN = 128, UBK = 64, USTAGES = 3;
+constexpr int UTILE = UBM * UBK * 2;                   // bytes of one A or B stage tile
+constexpr int USMEM = 2 * USTAGES * UTILE + 1024 + 256;  // tiles, alignment slack, barriers
+constexpr uint32_t kWaitPolls = 1u << 22;
+
+__device__ int g_umma_timeout;  // set when a bounded wait gave up
 
 enum Epi { EPI_BIAS_GELU, EPI_BIAS, EPI_DGELU, EPI_STORE };
 
 struct GemmArgs {
-    const bf16 *A, *B;
-    int M, N, K, lda, ldb, ldc;
+    int M, N, K, ldc;
     int epi;
     const float *bias;    // [N]
     const float *zsaved;  // [M][ldc] pre-activations (EPI_DGELU)
     float *outf;          // [M][ldc] FP32 output (pre-activation, linear output, gradient)
-    bf16 *outh;           // [M][ldc] BF16 output (activation, activation gradient)
+    bf16 *outh;           // [M][ldc] BF16 output (activation, activation gradient), or null
 };
 
 __device__ __forceinline__ unsigned smem_u32(const void *p)
@@ -52,32 +65,74 @@ __device__ __forceinline__ unsigned smem_u32(const void *p)
     return (unsigned)__cvta_generic_to_shared(p);
 }
 
-__device__ __forceinline__ void cp_async16(void *dst, const void *src)
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
 {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
 }
 
-__device__ __forceinline__ void ldsm_x4(uint32_t r[4], const void *p)
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
 {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(smem_u32(p)));
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
-__device__ __forceinline__ void ldsm_x4_t(uint32_t r[4], const void *p)
+// wait for the completion of the barrier's phase of the given parity
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
 {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(smem_u32(p)));
+    for (uint32_t i = 0; i < kWaitPolls; i++) {
+        uint32_t ok;
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok)
+            return true;
+    }
+    atomicExch(&g_umma_timeout, 1);
+    return false;
 }
 
-__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], const uint32_t b[2])
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar)
 {
     asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-        "{%8,%9}, {%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+// shared-memory matrix descriptor: K-major tile of 128-byte rows, 128-byte
+// swizzle, 8-row groups 1024 bytes apart (start address and offsets in
+// 16-byte units; version 1; swizzle mode 2 = 128 bytes)
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr)
+{
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1u << 16) | ((uint64_t)(1024u >> 4) << 32) |
+           ((uint64_t)1u << 46) | ((uint64_t)2u << 61);
+}
+
+// instruction descriptor of kind::f16: D FP32, A and B BF16, both K-major,
+// N = 128 (N >> 3 at bit 17), M = 128 (M >> 4 at bit 24)
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(UBN >> 3) << 17) |
+                            ((uint32_t)(UBM >> 4) << 24);
+
+__device__ __forceinline__ void umma(uint32_t tmem, uint64_t da, uint64_t db, uint32_t acc)
+{
+    asm volatile("{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(tmem),
+                 "l"(da), "l"(db), "r"(kIdesc), "r"(acc));
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t r[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
 // GELU, tanh form, and its derivative
@@ -94,136 +149,170 @@ __device__ __forceinline__ float gelu_grad(float z)
     return 0.5f * (1.0f + t) + 0.5f * z * (1.0f - t * t) * k0 * (1.0f + 3.0f * k1 * z * z);
 }
 
-template <bool AK, bool BK>
-__global__ void __launch_bounds__(256) gemm_kernel(const GemmArgs g)
+__global__ void __launch_bounds__(128) umma_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                        const __grid_constant__ CUtensorMap tmB, const GemmArgs g)
 {
-    constexpr int ASZ = AK ? GBM * SK : GBK * SMN;
-    constexpr int BSZ = BK ? GBN * SK : GBK * SMN;
-    __shared__ __align__(16) bf16 As[2][ASZ];
-    __shared__ __align__(16) bf16 Bs[2][BSZ];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int wm = warp >> 2, wn = warp & 3;  // warp tile rows wm*64, cols wn*32
-    const int bm = blockIdx.y * GBM, bn = blockIdx.x * GBN;
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;  // 1024-byte aligned tiles
+    const uint32_t sA = base, sB = base + USTAGES * UTILE;
+    const uint32_t bars = sB + USTAGES * UTILE;   // full[S], empty[S], done: 8 bytes each
+    const uint32_t slot = bars + 8 * (2 * USTAGES + 1);
+    uint32_t *slot_ptr = reinterpret_cast<uint32_t *>(smem_raw + (slot - raw));
+    auto full = [&](int st) { return bars + 8u * st; };
+    auto empty = [&](int st) { return bars + 8u * (USTAGES + st); };
+    const uint32_t done = bars + 8u * (2 * USTAGES);
 
-    auto load = [&](int stage, int k0) {
-#pragma unroll
-        for (int c = tid; c < 512; c += 256) {
-            if (AK) {
-                const int r = c >> 2, ch = c & 3;
-                cp_async16(&As[stage][r * SK + ch * 8], g.A + (size_t)(bm + r) * g.lda + k0 + ch * 8);
-            } else {
-                const int r = c >> 4, ch = c & 15;
-                cp_async16(&As[stage][r * SMN + ch * 8], g.A + (size_t)(k0 + r) * g.lda + bm + ch * 8);
-            }
-            if (BK) {
-                const int r = c >> 2, ch = c & 3;
-                cp_async16(&Bs[stage][r * SK + ch * 8], g.B + (size_t)(bn + r) * g.ldb + k0 + ch * 8);
-            } else {
-                const int r = c >> 4, ch = c & 15;
-                cp_async16(&Bs[stage][r * SMN + ch * 8], g.B + (size_t)(k0 + r) * g.ldb + bn + ch * 8);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int bm = blockIdx.y * UBM, bn = blockIdx.x * UBN;
+    const int nk = g.K / UBK;
+
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < USTAGES; st++) {
+            mbar_init(full(st), 1);
+            mbar_init(empty(st), 1);
+        }
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {  // 128 accumulator columns
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(UBN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *slot_ptr;
+
+    if (warp == 0) {
+        if (lane == 0) {  // producer
+            for (int kt = 0; kt < nk; kt++) {
+                const int st = kt % USTAGES, round = kt / USTAGES;
+                if (round > 0)
+                    mbar_wait(empty(st), (round - 1) & 1);
+                mbar_expect_tx(full(st), 2 * UTILE);
+                tma_load_2d(sA + st * UTILE, &tmA, kt * UBK, bm, full(st));
+                tma_load_2d(sB + st * UTILE, &tmB, kt * UBK, bn, full(st));
             }
         }
-        asm volatile("cp.async.commit_group;\n" ::);
-    };
-
-    float acc[4][4][4];
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {  // MMA issuer
+            for (int kt = 0; kt < nk; kt++) {
+                const int st = kt % USTAGES, round = kt / USTAGES;
+                mbar_wait(full(st), round & 1);
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-    for (int i = 0; i < 4; i++)
-#pragma unroll
-        for (int j = 0; j < 4; j++)
-#pragma unroll
-            for (int q = 0; q < 4; q++)
-                acc[i][j][q] = 0.f;
-
-    const int nk = g.K / GBK;
-    load(0, 0);
-    const int j8 = lane >> 3, r8 = lane & 7;
-    for (int kt = 0; kt < nk; kt++) {
-        if (kt + 1 < nk) {
-            load((kt + 1) & 1, (kt + 1) * GBK);
-            asm volatile("cp.async.wait_group 1;\n" ::);
-        } else {
-            asm volatile("cp.async.wait_group 0;\n" ::);
-        }
-        __syncthreads();
-        const bf16 *as = As[kt & 1], *bs = Bs[kt & 1];
-#pragma unroll
-        for (int kk = 0; kk < GBK; kk += 16) {
-            uint32_t a[4][4], b[4][2];
-#pragma unroll
-            for (int mi = 0; mi < 4; mi++) {
-                const int m0 = wm * 64 + mi * 16;
-                if (AK)
-                    ldsm_x4(a[mi], as + (m0 + (j8 & 1) * 8 + r8) * SK + kk + (j8 >> 1) * 8);
-                else
-                    ldsm_x4_t(a[mi], as + (kk + (j8 >> 1) * 8 + r8) * SMN + m0 + (j8 & 1) * 8);
+                for (int k = 0; k < UBK / 16; k++)  // 16 elements = 32 bytes along K per MMA
+                    umma(tmem, smem_desc(sA + st * UTILE + 32 * k), smem_desc(sB + st * UTILE + 32 * k),
+                         (kt | k) != 0);
+                umma_commit(empty(st));
             }
-#pragma unroll
-            for (int nj = 0; nj < 2; nj++) {
-                const int n0 = wn * 32 + nj * 16;
-                uint32_t t4[4];
-                if (BK)
-                    ldsm_x4(t4, bs + (n0 + (j8 >> 1) * 8 + r8) * SK + kk + (j8 & 1) * 8);
-                else
-                    ldsm_x4_t(t4, bs + (kk + (j8 & 1) * 8 + r8) * SMN + n0 + (j8 >> 1) * 8);
-                b[2 * nj][0] = t4[0];
-                b[2 * nj][1] = t4[1];
-                b[2 * nj + 1][0] = t4[2];
-                b[2 * nj + 1][1] = t4[3];
-            }
-#pragma unroll
-            for (int mi = 0; mi < 4; mi++)
-#pragma unroll
-                for (int ni = 0; ni < 4; ni++)
-                    mma_bf16(acc[mi][ni], a[mi], b[ni]);
+            umma_commit(done);
         }
-        __syncthreads();
+        __syncwarp();
     }
 
-    // epilogue: thread holds rows (lane/4, +8) and column pairs 2 (lane%4)
+    // epilogue: thread (warp, lane) holds row bm + 32 warp + lane
+    mbar_wait(done, 0);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int m = bm + 32 * warp + lane;
+    const size_t row = (size_t)m * g.ldc;
+#pragma unroll 1
+    for (int c = 0; c < UBN / 16; c++) {
+        uint32_t r[16];
+        tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + 16 * c, r);
+        const int n0 = bn + 16 * c;
+        float v[16];
 #pragma unroll
-    for (int mi = 0; mi < 4; mi++)
+        for (int j = 0; j < 16; j++)
+            v[j] = __uint_as_float(r[j]);
+        if (g.epi == EPI_BIAS_GELU || g.epi == EPI_BIAS) {
 #pragma unroll
-        for (int ni = 0; ni < 4; ni++)
+            for (int j = 0; j < 16; j++)
+                v[j] += g.bias[n0 + j];
+        } else if (g.epi == EPI_DGELU) {
+            const float4 *z4 = reinterpret_cast<const float4 *>(g.zsaved + row + n0);
 #pragma unroll
-            for (int h = 0; h < 2; h++) {
-                const int m = bm + wm * 64 + mi * 16 + (lane >> 2) + 8 * h;
-                const int n = bn + wn * 32 + ni * 8 + 2 * (lane & 3);
-                const size_t o = (size_t)m * g.ldc + n;
-                float v0 = acc[mi][ni][2 * h], v1 = acc[mi][ni][2 * h + 1];
-                if (g.epi == EPI_BIAS_GELU || g.epi == EPI_BIAS) {
-                    v0 += g.bias[n];
-                    v1 += g.bias[n + 1];
-                    *reinterpret_cast<float2 *>(g.outf + o) = make_float2(v0, v1);
-                    if (g.epi == EPI_BIAS_GELU)
-                        *reinterpret_cast<__nv_bfloat162 *>(g.outh + o) =
-                            __floats2bfloat162_rn(gelu(v0), gelu(v1));
-                } else if (g.epi == EPI_DGELU) {
-                    const float2 z = *reinterpret_cast<const float2 *>(g.zsaved + o);
-                    v0 *= gelu_grad(z.x);
-                    v1 *= gelu_grad(z.y);
-                    *reinterpret_cast<float2 *>(g.outf + o) = make_float2(v0, v1);
-                    *reinterpret_cast<__nv_bfloat162 *>(g.outh + o) = __floats2bfloat162_rn(v0, v1);
-                } else {
-                    *reinterpret_cast<float2 *>(g.outf + o) = make_float2(v0, v1);
-                    if (g.outh)
-                        *reinterpret_cast<__nv_bfloat162 *>(g.outh + o) = __floats2bfloat162_rn(v0, v1);
-                }
+            for (int q = 0; q < 4; q++) {
+                const float4 z = z4[q];
+                v[4 * q] *= gelu_grad(z.x);
+                v[4 * q + 1] *= gelu_grad(z.y);
+                v[4 * q + 2] *= gelu_grad(z.z);
+                v[4 * q + 3] *= gelu_grad(z.w);
             }
+        }
+        float4 *o4 = reinterpret_cast<float4 *>(g.outf + row + n0);
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+            o4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        if (g.outh) {
+            __nv_bfloat162 h[8];
+#pragma unroll
+            for (int q = 0; q < 8; q++)
+                h[q] = g.epi == EPI_BIAS_GELU ? __floats2bfloat162_rn(gelu(v[2 * q]), gelu(v[2 * q + 1]))
+                                              : __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+            uint4 *oh = reinterpret_cast<uint4 *>(g.outh + row + n0);
+            oh[0] = *reinterpret_cast<const uint4 *>(&h[0]);
+            oh[1] = *reinterpret_cast<const uint4 *>(&h[4]);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(UBN));
 }
 
-cudaError_t gemm(bool ak, bool bk, const GemmArgs &g, cudaStream_t s)
+// out [C][R] = in [R][C]^T (BF16; R and C multiples of 32), 32 x 32 tiles
+__global__ void transpose_bf16_kernel(const bf16 *in, int R, int C, bf16 *out)
 {
-    dim3 grid(g.N / GBN, g.M / GBM);
-    if (ak && bk)
-        gemm_kernel<true, true><<<grid, 256, 0, s>>>(g);
-    else if (ak && !bk)
-        gemm_kernel<true, false><<<grid, 256, 0, s>>>(g);
-    else if (!ak && !bk)
-        gemm_kernel<false, false><<<grid, 256, 0, s>>>(g);
-    else
-        gemm_kernel<false, true><<<grid, 256, 0, s>>>(g);
+    __shared__ unsigned short t[32][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    const unsigned short *src = reinterpret_cast<const unsigned short *>(in);
+    unsigned short *dst = reinterpret_cast<unsigned short *>(out);
+    for (int y = threadIdx.y; y < 32; y += blockDim.y)
+        t[y][threadIdx.x] = src[(size_t)(r0 + y) * C + c0 + threadIdx.x];
+    __syncthreads();
+    for (int y = threadIdx.y; y < 32; y += blockDim.y)
+        dst[(size_t)(c0 + y) * R + r0 + threadIdx.x] = t[threadIdx.x][y];
+}
+
+cudaError_t transpose(const bf16 *in, int R, int C, bf16 *out, cudaStream_t s)
+{
+    transpose_bf16_kernel<<<dim3(C / 32, R / 32), dim3(32, 8), 0, s>>>(in, R, C, out);
     return cudaGetLastError();
+}
+
+cudaError_t gemm(const CUtensorMap &A, const CUtensorMap &B, const GemmArgs &g, cudaStream_t s)
+{
+    umma_gemm_kernel<<<dim3(g.N / UBN, g.M / UBM), 128, USMEM, s>>>(A, B, g);
+    return cudaGetLastError();
+}
+
+// tensor map of a row-major [rows][k] BF16 matrix, boxes of 128 rows x 64
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+bool make_map(CUtensorMap *map, const bf16 *ptr, int rows, int k)
+{
+    static EncodeTiled encode = nullptr;
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return false;
+        encode = reinterpret_cast<EncodeTiled>(fn);
+    }
+    const cuuint64_t dims[2] = {(cuuint64_t)k, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)k * 2};
+    const cuuint32_t box[2] = {UBK, UBM};
+    const cuuint32_t estr[2] = {1, 1};
+    return encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16 *>(ptr), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // ------------------------------------------------------------- elementwise --
@@ -492,6 +581,11 @@ struct opf_warm {
            *pmax = nullptr, *qmin = nullptr, *qmax = nullptr, *gl = nullptr, *gu = nullptr,
            *xl = nullptr, *xu = nullptr;
     bf16 *U = nullptr, *H1 = nullptr, *H2 = nullptr, *dYh = nullptr, *dZ2h = nullptr, *dZ1h = nullptr;
+    // transposed BF16 copies (the backward GEMMs take K-contiguous operands)
+    bf16 *UT = nullptr, *H1T = nullptr, *H2T = nullptr, *W2T = nullptr, *W3T = nullptr, *dYT = nullptr,
+         *dZ2T = nullptr, *dZ1T = nullptr;
+    // TMA tensor maps of every GEMM operand (buffers fixed for the model's life)
+    CUtensorMap mU, mW1, mH1, mW2, mH2, mW3, mdYT, mH2T, mdY, mW3T, mdZ2T, mH1T, mdZ2, mW2T, mdZ1T, mUT;
     float *Z1 = nullptr, *Z2 = nullptr, *Y = nullptr, *dYf = nullptr, *dZ2f = nullptr, *dZ1f = nullptr;
     double *x = nullptr, *c = nullptr, *gradf = nullptr, *obj = nullptr, *v1 = nullptr, *v2 = nullptr,
            *u1 = nullptr, *u2 = nullptr, *part = nullptr;
@@ -576,26 +670,53 @@ int refresh_bf16(opf_warm *w, cudaStream_t s)
     to_bf16_kernel<<<grid1((int64_t)w->H * w->Kin), 256, 0, s>>>(w->params + w->oW1, w->W1h, (int64_t)w->H * w->Kin);
     to_bf16_kernel<<<grid1((int64_t)w->H * w->H), 256, 0, s>>>(w->params + w->oW2, w->W2h, (int64_t)w->H * w->H);
     to_bf16_kernel<<<grid1((int64_t)w->Nout * w->H), 256, 0, s>>>(w->params + w->oW3, w->W3h, (int64_t)w->Nout * w->H);
-    return check_cuda(cudaGetLastError(), "bf16 copies");
+    cudaError_t e = transpose(w->W2h, w->H, w->H, w->W2T, s);
+    if (e == cudaSuccess)
+        e = transpose(w->W3h, w->Nout, w->H, w->W3T, s);
+    return check_cuda(e == cudaSuccess ? cudaGetLastError() : e, "bf16 copies");
 }
 
-// forward pass: U (already prepared) -> Z1, H1, Z2, H2, Y
+// a GEMM wait that gave up since the last check (the flag is cleared)
+int check_timeout()
+{
+    int v = 0, zero = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(&v, g_umma_timeout, sizeof(int));
+    if (e == cudaSuccess && v)
+        e = cudaMemcpyToSymbol(g_umma_timeout, &zero, sizeof(int));
+    if (e != cudaSuccess)
+        return check_cuda(e, "GEMM status");
+    if (v) {
+        set_error("opf_warm: a tensor-core GEMM wait timed out; results are invalid");
+        return OPF_ECUDA;
+    }
+    return OPF_OK;
+}
+
+GemmArgs gargs(int M, int N, int K, int ldc, int epi, const float *bias, const float *zsaved, float *outf,
+               bf16 *outh)
+{
+    GemmArgs g;
+    g.M = M; g.N = N; g.K = K; g.ldc = ldc; g.epi = epi;
+    g.bias = bias; g.zsaved = zsaved; g.outf = outf; g.outh = outh;
+    return g;
+}
+
+// forward pass: U (already prepared) -> Z1, H1, Z2, H2, Y, plus the
+// transposed copies U^T, H1^T, H2^T the weight gradients read
 int forward(opf_warm *w, cudaStream_t s)
 {
-    GemmArgs g{};
-    g.A = w->U; g.B = w->W1h; g.M = w->B; g.N = w->H; g.K = w->Kin; g.lda = w->Kin; g.ldb = w->Kin;
-    g.ldc = w->H; g.epi = EPI_BIAS_GELU; g.bias = w->params + w->ob1; g.outf = w->Z1; g.outh = w->H1;
-    cudaError_t e = gemm(true, true, g, s);
-    g = GemmArgs{};
-    g.A = w->H1; g.B = w->W2h; g.M = w->B; g.N = w->H; g.K = w->H; g.lda = w->H; g.ldb = w->H;
-    g.ldc = w->H; g.epi = EPI_BIAS_GELU; g.bias = w->params + w->ob2; g.outf = w->Z2; g.outh = w->H2;
+    const int B = w->B, H = w->H;
+    cudaError_t e = transpose(w->U, B, w->Kin, w->UT, s);
     if (e == cudaSuccess)
-        e = gemm(true, true, g, s);
-    g = GemmArgs{};
-    g.A = w->H2; g.B = w->W3h; g.M = w->B; g.N = w->Nout; g.K = w->H; g.lda = w->H; g.ldb = w->H;
-    g.ldc = w->Nout; g.epi = EPI_BIAS; g.bias = w->params + w->ob3; g.outf = w->Y;
+        e = gemm(w->mU, w->mW1, gargs(B, H, w->Kin, H, EPI_BIAS_GELU, w->params + w->ob1, nullptr, w->Z1, w->H1), s);
     if (e == cudaSuccess)
-        e = gemm(true, true, g, s);
+        e = transpose(w->H1, B, H, w->H1T, s);
+    if (e == cudaSuccess)
+        e = gemm(w->mH1, w->mW2, gargs(B, H, H, H, EPI_BIAS_GELU, w->params + w->ob2, nullptr, w->Z2, w->H2), s);
+    if (e == cudaSuccess)
+        e = transpose(w->H2, B, H, w->H2T, s);
+    if (e == cudaSuccess)
+        e = gemm(w->mH2, w->mW3, gargs(B, w->Nout, H, w->Nout, EPI_BIAS, w->params + w->ob3, nullptr, w->Y, nullptr), s);
     return check_cuda(e, "forward GEMMs");
 }
 
@@ -604,37 +725,28 @@ int backward(opf_warm *w, cudaStream_t s)
 {
     const int B = w->B, H = w->H;
     float *gr = w->grads;
-    // dW3 = dY^T H2, db3 = colsum dY
-    GemmArgs g{};
-    g.A = w->dYh; g.B = w->H2; g.M = w->Nout; g.N = H; g.K = B; g.lda = w->Nout; g.ldb = H; g.ldc = H;
-    g.epi = EPI_STORE; g.outf = gr + w->oW3;
-    cudaError_t e = gemm(false, false, g, s);
+    // dW3 = dY^T H2 [Nout][H], db3 = colsum dY
+    cudaError_t e = transpose(w->dYh, B, w->Nout, w->dYT, s);
+    if (e == cudaSuccess)
+        e = gemm(w->mdYT, w->mH2T, gargs(w->Nout, H, B, H, EPI_STORE, nullptr, nullptr, gr + w->oW3, nullptr), s);
     colsum_kernel<<<(w->Nout + 31) / 32, dim3(32, 32), 0, s>>>(w->dYf, B, w->Nout, gr + w->ob3);
     // dZ2 = (dY W3) * gelu'(Z2)
-    g = GemmArgs{};
-    g.A = w->dYh; g.B = w->W3h; g.M = B; g.N = H; g.K = w->Nout; g.lda = w->Nout; g.ldb = H; g.ldc = H;
-    g.epi = EPI_DGELU; g.zsaved = w->Z2; g.outf = w->dZ2f; g.outh = w->dZ2h;
     if (e == cudaSuccess)
-        e = gemm(true, false, g, s);
+        e = gemm(w->mdY, w->mW3T, gargs(B, H, w->Nout, H, EPI_DGELU, nullptr, w->Z2, w->dZ2f, w->dZ2h), s);
     // dW2 = dZ2^T H1, db2
-    g = GemmArgs{};
-    g.A = w->dZ2h; g.B = w->H1; g.M = H; g.N = H; g.K = B; g.lda = H; g.ldb = H; g.ldc = H;
-    g.epi = EPI_STORE; g.outf = gr + w->oW2;
     if (e == cudaSuccess)
-        e = gemm(false, false, g, s);
+        e = transpose(w->dZ2h, B, H, w->dZ2T, s);
+    if (e == cudaSuccess)
+        e = gemm(w->mdZ2T, w->mH1T, gargs(H, H, B, H, EPI_STORE, nullptr, nullptr, gr + w->oW2, nullptr), s);
     colsum_kernel<<<(H + 31) / 32, dim3(32, 32), 0, s>>>(w->dZ2f, B, H, gr + w->ob2);
     // dZ1 = (dZ2 W2) * gelu'(Z1)
-    g = GemmArgs{};
-    g.A = w->dZ2h; g.B = w->W2h; g.M = B; g.N = H; g.K = H; g.lda = H; g.ldb = H; g.ldc = H;
-    g.epi = EPI_DGELU; g.zsaved = w->Z1; g.outf = w->dZ1f; g.outh = w->dZ1h;
     if (e == cudaSuccess)
-        e = gemm(true, false, g, s);
+        e = gemm(w->mdZ2, w->mW2T, gargs(B, H, H, H, EPI_DGELU, nullptr, w->Z1, w->dZ1f, w->dZ1h), s);
     // dW1 = dZ1^T U, db1
-    g = GemmArgs{};
-    g.A = w->dZ1h; g.B = w->U; g.M = H; g.N = w->Kin; g.K = B; g.lda = H; g.ldb = w->Kin; g.ldc = w->Kin;
-    g.epi = EPI_STORE; g.outf = gr + w->oW1;
     if (e == cudaSuccess)
-        e = gemm(false, false, g, s);
+        e = transpose(w->dZ1h, B, H, w->dZ1T, s);
+    if (e == cudaSuccess)
+        e = gemm(w->mdZ1T, w->mUT, gargs(H, w->Kin, B, w->Kin, EPI_STORE, nullptr, nullptr, gr + w->oW1, nullptr), s);
     colsum_kernel<<<(H + 31) / 32, dim3(32, 32), 0, s>>>(w->dZ1f, B, H, gr + w->ob1);
     if (e == cudaSuccess)
         e = cudaGetLastError();
@@ -797,6 +909,14 @@ int opf_warm_create(const opf_network *net, const opf_warm_opts *opts, opf_warm 
     if (!rc) rc = walloc(w, &w->Z2, act);
     if (!rc) rc = walloc(w, &w->dZ2f, act);
     if (!rc) rc = walloc(w, &w->dZ1f, act);
+    if (!rc) rc = walloc(w, &w->UT, (size_t)w->Kin * w->B);
+    if (!rc) rc = walloc(w, &w->H1T, act);
+    if (!rc) rc = walloc(w, &w->H2T, act);
+    if (!rc) rc = walloc(w, &w->W2T, (size_t)w->H * w->H);
+    if (!rc) rc = walloc(w, &w->W3T, (size_t)w->H * w->Nout);
+    if (!rc) rc = walloc(w, &w->dYT, outsz);
+    if (!rc) rc = walloc(w, &w->dZ2T, act);
+    if (!rc) rc = walloc(w, &w->dZ1T, act);
     if (!rc) rc = walloc(w, &w->Y, outsz);
     if (!rc) rc = walloc(w, &w->dYf, outsz);
     if (!rc) rc = walloc(w, &w->dYh, outsz);
@@ -809,6 +929,24 @@ int opf_warm_create(const opf_network *net, const opf_warm_opts *opts, opf_warm 
     if (!rc) rc = walloc(w, &w->u1, w->n);
     if (!rc) rc = walloc(w, &w->u2, w->n);
     if (!rc) rc = walloc(w, &w->part, 2 * (size_t)w->nparts);
+    if (!rc) {  // tensor maps: A operands [M][K], B operands [N][K]
+        const int B = w->B, H = w->H, Kin = w->Kin, No = w->Nout;
+        const bool ok = make_map(&w->mU, w->U, B, Kin) && make_map(&w->mW1, w->W1h, H, Kin) &&
+                        make_map(&w->mH1, w->H1, B, H) && make_map(&w->mW2, w->W2h, H, H) &&
+                        make_map(&w->mH2, w->H2, B, H) && make_map(&w->mW3, w->W3h, No, H) &&
+                        make_map(&w->mdYT, w->dYT, No, B) && make_map(&w->mH2T, w->H2T, H, B) &&
+                        make_map(&w->mdY, w->dYh, B, No) && make_map(&w->mW3T, w->W3T, H, No) &&
+                        make_map(&w->mdZ2T, w->dZ2T, H, B) && make_map(&w->mH1T, w->H1T, H, B) &&
+                        make_map(&w->mdZ2, w->dZ2h, B, H) && make_map(&w->mW2T, w->W2T, H, H) &&
+                        make_map(&w->mdZ1T, w->dZ1T, H, B) && make_map(&w->mUT, w->UT, Kin, B);
+        if (!ok) {
+            set_error("opf_warm_create: cuTensorMapEncodeTiled failed");
+            rc = OPF_ECUDA;
+        }
+    }
+    if (!rc)
+        rc = check_cuda(cudaFuncSetAttribute(umma_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, USMEM),
+                        "GEMM shared memory");
     if (!rc && (cudaMemset(w->am, 0, sizeof(float) * w->nparams) != cudaSuccess ||
                 cudaMemset(w->av, 0, sizeof(float) * w->nparams) != cudaSuccess ||
                 cudaMemset(w->grads, 0, sizeof(float) * w->nparams) != cudaSuccess ||
@@ -955,7 +1093,10 @@ int opf_warm_get_params(const opf_warm *w, float *h)
         set_error("opf_warm_get_params: bad arguments");
         return OPF_EINVAL;
     }
-    return check_cuda(cudaMemcpy(h, w->params, sizeof(float) * w->nparams, cudaMemcpyDeviceToHost), "get params");
+    int rc = check_cuda(cudaMemcpy(h, w->params, sizeof(float) * w->nparams, cudaMemcpyDeviceToHost), "get params");
+    if (!rc)
+        rc = check_timeout();
+    return rc;
 }
 
 int opf_warm_set_params(opf_warm *w, const float *h)
