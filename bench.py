@@ -79,6 +79,14 @@ def load_peaks():
         return 6400.0, "fallback"
 
 
+def load_bf16_peak():
+    """Measured dense BF16 TFLOP/s (burst) of the B300s, else the fallback."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
+    except (OSError, KeyError, ValueError):
+        return 1800.0
+
+
 def profile_traffic(kernel):
     """DRAM bytes per launch of the branch or bus kernel from its committed
     ncu summary (a line 'dram_bytes_per_launch: N'), or None."""
@@ -237,6 +245,23 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------- multi-rank glue --
+
+def max_over_ranks(value, dist, device):
+    """The largest of every rank's value (identity on one process)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, steps_per_rank, seconds):
+    """Whole-job throughput: all ranks' steps over the slowest rank's time."""
+    return world * steps_per_rank / seconds
+
+
 # --------------------------------------------------------------- own arm --
 
 def main():
@@ -327,12 +352,7 @@ def main():
                 tail.replay()
             e1.record(stream)
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        if dist:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return max_over_ranks(e0.elapsed_time(e1), dist, dev)
 
     # warm-up (untimed)
     with torch.cuda.stream(stream):
@@ -349,7 +369,7 @@ def main():
         ms = timed(g_full, K // R, g_tail)
     clocks = clk.summary()
     ms_per_step = ms / K
-    value = world * K / (ms / 1000.0)
+    value = job_rate(world, K, ms / 1000.0)
 
     # dominant kernel alone: branch phase, same rotation
     def branch_only(k, s):
@@ -402,12 +422,8 @@ def main():
         for k in range(e2e_steps):
             M0.eval_all_host(hx[k % 2], hl[k % 2], 1.0, *ho, stream=stream)
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * e2e_steps / e2e_s, "unit": UNIT,
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, dev)
+    e2e = {"value": job_rate(world, e2e_steps, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": 8 * (n + m), "d2h_bytes_per_step": 8 * (1 + n + m + nnzj + nnzh),
            "steps": e2e_steps, "pinned": True}
 
@@ -604,6 +620,18 @@ def warm_start_summary(torch, opf, synth, dev, epochs):
     e1.record()
     torch.cuda.synchronize()
     pred_ms = e0.elapsed_time(e1) / 10
+    # the network alone (input preparation, transposes and the three
+    # tcgen05 GEMMs): FLOPs of the GEMMs over its time
+    yb = torch.empty(B * ws.n_out, dtype=torch.float32, device=dev)
+    ws.forward(pd_h, qd_h, yb)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(20):
+        ws.forward(pd_h, qd_h, yb)
+    e1.record()
+    torch.cuda.synchronize()
+    fwd_us = 1000.0 * e0.elapsed_time(e1) / 20
+    fwd_flops = 2.0 * B * (ws.n_in * 1024 + 1024 * 1024 + 1024 * ws.n_out)
     # judge: max violation per profile, batch model of the held-out profiles
     M = opf.Model(g.copy(load_pd=pd[N:], load_qd=qd[N:], ramp_ratio=0.0))
     xl, xu, gl, gu = (torch.tensor(a, device=dev) for a in M.bounds())
@@ -631,6 +659,8 @@ def warm_start_summary(torch, opf, synth, dev, epochs):
         "samples": N, "samples_s": sample_s, "epochs": epochs, "batch": B, "train_s": train_s,
         "final_loss": float(hist[-1][0]), "final_cost": float(hist[-1][1]), "final_res2": float(hist[-1][2]),
         "predict_ms_per_batch": pred_ms, "predict_profiles_per_s": B / (pred_ms * 1e-3),
+        "forward_us": fwd_us, "forward_gemm_tflops": fwd_flops / (fwd_us * 1e-6) / 1e12,
+        "forward_gemm_frac_of_bf16_peak": fwd_flops / (fwd_us * 1e-6) / 1e12 / load_bf16_peak(),
         "held_out": B, "cvio_flat_median": float(np.median(cf_np)),
         "cvio_warm_median": float(np.median(cw_np)), "cvio_warm_p99": float(np.percentile(cw_np, 99)),
         "cvio_warm_max": float(cw_np.max()),

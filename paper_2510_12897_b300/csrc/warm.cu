@@ -320,13 +320,14 @@ bool make_map(CUtensorMap *map, const bf16 *ptr, int rows, int k)
 struct WarmDev {
     int B, nb, ng, nl, nload, Kin, Nout, nbp, ngp, ref;
     double va_scale, penalty;
-    const double *pk, *qk;                   // 5 / base load (0 where the base is 0)
+    const float *pk, *qk;                    // 5 / base load (0 where the base is 0)
     const double *vmin, *vmax;               // per bus
     const double *pmin, *pmax, *qmin, *qmax; // per generator
 };
 
 // u = normalised loads (BF16, zero padding): (load / base - 1) / 0.2 as one
-// FMA with the precomputed 5 / base (0 where the base load is 0)
+// FP32 FMA with the precomputed 5 / base (0 where the base load is 0); the
+// result is rounded to BF16 anyway
 __global__ void prep_kernel(const WarmDev w, const double *pd, const double *qd, bf16 *U)
 {
     const int64_t total = (int64_t)w.B * w.Kin;
@@ -335,11 +336,11 @@ __global__ void prep_kernel(const WarmDev w, const double *pd, const double *qd,
         const int s = (int)(it / w.Kin), j = (int)(it - (int64_t)s * w.Kin);
         float u = 0.f;
         if (j < w.nload) {
-            const double k = w.pk[j];
-            u = k != 0.0 ? (float)fma(pd[(int64_t)s * w.nload + j], k, -5.0) : 0.f;
+            const float k = w.pk[j];
+            u = k != 0.f ? fmaf((float)pd[(int64_t)s * w.nload + j], k, -5.f) : 0.f;
         } else if (j < 2 * w.nload) {
-            const double k = w.qk[j - w.nload];
-            u = k != 0.0 ? (float)fma(qd[(int64_t)s * w.nload + j - w.nload], k, -5.0) : 0.f;
+            const float k = w.qk[j - w.nload];
+            u = k != 0.f ? fmaf((float)qd[(int64_t)s * w.nload + j - w.nload], k, -5.f) : 0.f;
         }
         U[it] = __float2bfloat16_rn(u);
     }
@@ -409,25 +410,56 @@ __global__ void resid_kernel(const WarmDev w, const double *c, const double *gl,
         part[blockIdx.x] = s;
 }
 
-// variable bounds: r = x - clip(x, xl, xu); u1 += (2 penalty / B) r (so that
-// the flow variables' share reaches the voltages with the rest); per-block
-// sums of r^2 into part
-__global__ void bound_kernel(const WarmDev w, const double *x, const double *xl, const double *xu,
-                             int64_t n, double *u1, double *part)
+// variable bounds: per-block sums of r^2, r = x - clip(x, xl, xu) (their
+// gradient enters through the flow multipliers for p, q and through the
+// output map for vm, pg, qg)
+__global__ void bound_kernel(const double *x, const double *xl, const double *xu, int64_t n, double *part)
 {
     __shared__ double red[32];
     double acc = 0.0;
-    const double k = 2.0 * w.penalty / w.B;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const double xi = x[i];
         const double r = xi - fmin(fmax(xi, xl[i]), xu[i]);
-        u1[i] += k * r;
         acc += r * r;
     }
     const double s = block_sum(acc, red);
     if (threadIdx.x == 0)
         part[blockIdx.x] = s;
+}
+
+// The flow variables are functions of the voltages (p, q = F(va, vm)), so
+// the gradient of the penalised loss with respect to the voltages is
+// J_v^T v1 + J_v(F)^T g_pq, g_pq the loss's gradient in the arc variables:
+// the thermal and balance rows where each arc variable appears, plus its
+// bound term. Since a flow row is (own arc variable) - F, J_v(F) = -J_v(flow
+// row), and the whole gradient is J_v^T v2 with v2 = v1 except on the flow
+// rows, where v2 = -g_own = -(2 x_own v_thermal + v_balance + k r_own),
+// k = 2 penalty / B. This kernel overwrites the flow rows of v1 with v2 (one
+// thread per branch and period, its four arc variables).
+__global__ void flowmult_kernel(const WarmDev w, const int4 *br, const double *x, const double *xl,
+                                const double *xu, double *v)
+{
+    const int64_t T = w.B, nl = w.nl, nb = w.nb, ng = w.ng, na = 2 * nl;
+    const int64_t nlT = nl * T, nbT = nb * T, ngT = ng * T;
+    const double kpen = 2.0 * w.penalty / w.B;
+    for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < nlT;
+         it += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = it / nl, k = it - t * nl;
+        const int4 b = __ldg(br + k);
+        const int64_t ip = 2 * nbT + 2 * ngT + na * t, iq = ip + na * T;
+        const int64_t own[4] = {ip + k, iq + k, ip + nl + k, iq + nl + k};
+        const int64_t th = T + 5 * nlT + 2 * nbT + it;  // thermal row (from); + nlT: to
+        const int64_t bal = T + 5 * nlT + nb * t;       // P balance of bus 0 in period t; + nbT: Q
+        const int64_t vb[4] = {bal + b.x, bal + nbT + b.x, bal + b.y, bal + nbT + b.y};
+#pragma unroll
+        for (int g = 0; g < 4; g++) {
+            const double xo = x[own[g]];
+            const double r = xo - fmin(fmax(xo, xl[own[g]]), xu[own[g]]);
+            const double vt = v[th + (g < 2 ? 0 : nlT)];
+            v[T + it + g * nlT] = -(fma(2.0 * xo, vt, v[vb[g]]) + kpen * r);
+        }
+    }
 }
 
 // batch means: loss, cost, sum of squared residuals (constraints and bounds);
@@ -448,29 +480,7 @@ __global__ void stats_kernel(const WarmDev w, const double *part, int nparts, co
     }
 }
 
-// v2 = v1, then on every flow row r: v2_r -= u1[own variable of r]; this
-// chains the p, q part of the gradient through p, q = flows(va, vm)
-__global__ void flowrow_kernel(const WarmDev w, const double *v1, const double *u1, int64_t m,
-                               double *v2)
-{
-    const int64_t T = w.B, nl = w.nl, nb = w.nb, ng = w.ng, na = 2 * nl;
-    const int64_t nflow = 4 * nl * T;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        double v = v1[i];
-        const int64_t r = i - T;  // rows after the reference rows
-        if (r >= 0 && r < nflow) {
-            const int64_t grp = r / (nl * T), e = r - grp * nl * T;
-            const int64_t t = e / nl, k = e - t * nl;
-            const int64_t p0 = 2 * nb * T + 2 * ng * T + na * t, q0 = p0 + na * T;
-            const int64_t own = grp == 0 ? p0 + k : grp == 1 ? q0 + k : grp == 2 ? p0 + nl + k : q0 + nl + k;
-            v -= u1[own];
-        }
-        v2[i] = v;
-    }
-}
-
-// dL/dy from dL/dx = u2 (J^T v2) + the bound term + grad f / B (on pg),
+// dL/dy from dL/dx = u (J^T v2) + the bound term + grad f / B (on pg),
 // through the output map: FP32 for the checks and the bias gradient, BF16
 // copies for the GEMMs; padding entries and the reference angle get 0
 __global__ void dmap_kernel(const WarmDev w, const double *x, const double *u2, const double *gradf,
@@ -577,7 +587,8 @@ struct opf_warm {
     std::vector<void *> allocs;
     float *params = nullptr, *grads = nullptr, *am = nullptr, *av = nullptr;
     bf16 *W1h = nullptr, *W2h = nullptr, *W3h = nullptr;
-    double *pk = nullptr, *qk = nullptr, *vmin = nullptr, *vmax = nullptr, *pmin = nullptr,
+    float *pk = nullptr, *qk = nullptr;
+    double *vmin = nullptr, *vmax = nullptr, *pmin = nullptr,
            *pmax = nullptr, *qmin = nullptr, *qmax = nullptr, *gl = nullptr, *gu = nullptr,
            *xl = nullptr, *xu = nullptr;
     bf16 *U = nullptr, *H1 = nullptr, *H2 = nullptr, *dYh = nullptr, *dZ2h = nullptr, *dZ1h = nullptr;
@@ -587,8 +598,8 @@ struct opf_warm {
     // TMA tensor maps of every GEMM operand (buffers fixed for the model's life)
     CUtensorMap mU, mW1, mH1, mW2, mH2, mW3, mdYT, mH2T, mdY, mW3T, mdZ2T, mH1T, mdZ2, mW2T, mdZ1T, mUT;
     float *Z1 = nullptr, *Z2 = nullptr, *Y = nullptr, *dYf = nullptr, *dZ2f = nullptr, *dZ1f = nullptr;
-    double *x = nullptr, *c = nullptr, *gradf = nullptr, *obj = nullptr, *v1 = nullptr, *v2 = nullptr,
-           *u1 = nullptr, *u2 = nullptr, *part = nullptr;
+    double *x = nullptr, *c = nullptr, *gradf = nullptr, *obj = nullptr, *v1 = nullptr, *u2 = nullptr,
+           *part = nullptr;
     int nparts = 0;
 };
 
@@ -701,32 +712,33 @@ GemmArgs gargs(int M, int N, int K, int ldc, int epi, const float *bias, const f
     return g;
 }
 
-// forward pass: U (already prepared) -> Z1, H1, Z2, H2, Y, plus the
-// transposed copies U^T, H1^T, H2^T the weight gradients read
+// forward pass: U (already prepared) -> Z1, H1, Z2, H2, Y
 int forward(opf_warm *w, cudaStream_t s)
 {
     const int B = w->B, H = w->H;
-    cudaError_t e = transpose(w->U, B, w->Kin, w->UT, s);
-    if (e == cudaSuccess)
-        e = gemm(w->mU, w->mW1, gargs(B, H, w->Kin, H, EPI_BIAS_GELU, w->params + w->ob1, nullptr, w->Z1, w->H1), s);
-    if (e == cudaSuccess)
-        e = transpose(w->H1, B, H, w->H1T, s);
+    cudaError_t e =
+        gemm(w->mU, w->mW1, gargs(B, H, w->Kin, H, EPI_BIAS_GELU, w->params + w->ob1, nullptr, w->Z1, w->H1), s);
     if (e == cudaSuccess)
         e = gemm(w->mH1, w->mW2, gargs(B, H, H, H, EPI_BIAS_GELU, w->params + w->ob2, nullptr, w->Z2, w->H2), s);
-    if (e == cudaSuccess)
-        e = transpose(w->H2, B, H, w->H2T, s);
     if (e == cudaSuccess)
         e = gemm(w->mH2, w->mW3, gargs(B, w->Nout, H, w->Nout, EPI_BIAS, w->params + w->ob3, nullptr, w->Y, nullptr), s);
     return check_cuda(e, "forward GEMMs");
 }
 
-// backward pass of dY (dYf, dYh set) into grads
+// backward pass of dY (dYf, dYh set) into grads, after a forward pass of
+// the same batch (U, H1, H2 are read through transposed copies)
 int backward(opf_warm *w, cudaStream_t s)
 {
     const int B = w->B, H = w->H;
     float *gr = w->grads;
+    cudaError_t e = transpose(w->U, B, w->Kin, w->UT, s);
+    if (e == cudaSuccess)
+        e = transpose(w->H1, B, H, w->H1T, s);
+    if (e == cudaSuccess)
+        e = transpose(w->H2, B, H, w->H2T, s);
     // dW3 = dY^T H2 [Nout][H], db3 = colsum dY
-    cudaError_t e = transpose(w->dYh, B, w->Nout, w->dYT, s);
+    if (e == cudaSuccess)
+        e = transpose(w->dYh, B, w->Nout, w->dYT, s);
     if (e == cudaSuccess)
         e = gemm(w->mdYT, w->mH2T, gargs(w->Nout, H, B, H, EPI_STORE, nullptr, nullptr, gr + w->oW3, nullptr), s);
     colsum_kernel<<<(w->Nout + 31) / 32, dim3(32, 32), 0, s>>>(w->dYf, B, w->Nout, gr + w->ob3);
@@ -755,7 +767,8 @@ int backward(opf_warm *w, cudaStream_t s)
 
 // The loss of the batch at the network output w->Y and its gradient dL/dY
 // (into dYf, dYh): the point from the output map, flows from the voltages,
-// the library's callbacks, the penalty gradient through J^T twice.
+// the library's callbacks, the penalty gradient through one J^T product of
+// the reduced multipliers (flowmult_kernel).
 int loss_grad(opf_warm *w, const double *d_pd, const double *d_qd, double *d_stats, cudaStream_t s)
 {
     const WarmDev d = dev_of(w);
@@ -767,17 +780,13 @@ int loss_grad(opf_warm *w, const double *d_pd, const double *d_qd, double *d_sta
         EvalArgs a{w->x, nullptr, 1.0, w->obj, w->gradf, w->c, nullptr, nullptr};
         rc = launch_eval(*w->M, a, W_OBJ | W_GRAD | W_CONS, s);
     }
-    if (!rc) {  // v1 = 2 penalty rho / B, u1 = J^T v1 + the bound term
+    if (!rc) {  // v1 = 2 penalty rho / B; residual sums; flow rows of v1 := v2
         resid_kernel<<<w->nparts, 256, 0, s>>>(d, w->c, w->gl, w->gu, w->m, w->v1, w->part);
-        rc = launch_jtprod(*w->M, w->x, w->v1, w->u1, s);
-    }
-    if (!rc) {
-        bound_kernel<<<w->nparts, 256, 0, s>>>(d, w->x, w->xl, w->xu, w->n, w->u1, w->part + w->nparts);
+        bound_kernel<<<w->nparts, 256, 0, s>>>(w->x, w->xl, w->xu, w->n, w->part + w->nparts);
         if (d_stats)
             stats_kernel<<<1, 32, 0, s>>>(d, w->part, 2 * w->nparts, w->obj, d_stats);
-        // through p, q = flows(va, vm): v2 = v1 - u1[own] on flow rows
-        flowrow_kernel<<<grid1(w->m), 256, 0, s>>>(d, w->v1, w->u1, w->m, w->v2);
-        rc = launch_jtprod(*w->M, w->x, w->v2, w->u2, s);
+        flowmult_kernel<<<grid1((int64_t)w->nl * w->B), 256, 0, s>>>(d, w->M->d.br, w->x, w->xl, w->xu, w->v1);
+        rc = launch_jtprod(*w->M, w->x, w->v1, w->u2, s);
     }
     if (!rc)
         dmap_kernel<<<grid1((int64_t)w->B * w->Nout), 256, 0, s>>>(d, w->x, w->u2, w->gradf, w->dYf, w->dYh);
@@ -868,10 +877,10 @@ int opf_warm_create(const opf_network *net, const opf_warm_opts *opts, opf_warm 
     init_rows(w->oW1, w->Kin, 0, w->H, 2 * w->nload);
     init_rows(w->oW2, w->H, 0, w->H, w->H);
     // W3 and b3 start at zero: the untrained network proposes the flat start
-    std::vector<double> pk(w->nload), qk(w->nload);
+    std::vector<float> pk(w->nload), qk(w->nload);
     for (int l = 0; l < w->nload; l++) {
-        pk[l] = net->load_pd[l] > 0.0 ? 5.0 / net->load_pd[l] : 0.0;
-        qk[l] = net->load_qd[l] > 0.0 ? 5.0 / net->load_qd[l] : 0.0;
+        pk[l] = net->load_pd[l] > 0.0 ? (float)(5.0 / net->load_pd[l]) : 0.f;
+        qk[l] = net->load_qd[l] > 0.0 ? (float)(5.0 / net->load_qd[l]) : 0.f;
     }
     std::vector<double> vmin(net->bus_vmin, net->bus_vmin + w->nb), vmax(net->bus_vmax, net->bus_vmax + w->nb);
     std::vector<double> pmin(net->gen_pmin, net->gen_pmin + w->ng), pmax(net->gen_pmax, net->gen_pmax + w->ng);
@@ -925,8 +934,6 @@ int opf_warm_create(const opf_network *net, const opf_warm_opts *opts, opf_warm 
     if (!rc) rc = walloc(w, &w->gradf, w->n);
     if (!rc) rc = walloc(w, &w->obj, 1);
     if (!rc) rc = walloc(w, &w->v1, w->m);
-    if (!rc) rc = walloc(w, &w->v2, w->m);
-    if (!rc) rc = walloc(w, &w->u1, w->n);
     if (!rc) rc = walloc(w, &w->u2, w->n);
     if (!rc) rc = walloc(w, &w->part, 2 * (size_t)w->nparts);
     if (!rc) {  // tensor maps: A operands [M][K], B operands [N][K]
