@@ -3,6 +3,7 @@ every entry point include/opf.h declares; the layout-generated sparsity
 patterns and bounds equal the oracle's bit for bit; invalid input is
 rejected with the documented codes before any device work."""
 import ctypes
+import os
 
 import numpy as np
 import pytest
@@ -18,7 +19,8 @@ def L():
 
 
 def test_exports_every_declared_symbol(L):
-    names = opf.declared_symbols()
+    names = opf.declared_symbols() + opf.declared_symbols(os.path.join(os.path.dirname(opf.HEADER), "opf_warm.h"))
+    assert "opf_warm_train_step" in names and "opf_eval_all" in names
     assert "opf_eval_jac_hess" in names and "opf_model_create" in names
     for name in names:
         assert hasattr(L, name), name
@@ -143,3 +145,26 @@ def test_null_and_state_errors(L):
     ok = opf.OpfLaunch(256, 64, 0, 0, 1, 1)
     opf._check(L.opf_set_launch(M.h, ctypes.byref(ok)))
     assert M.get_launch() == ok.as_dict()
+
+
+def test_warm_create_rejects_bad_options(L):
+    """opf_warm_create validates its options on the host before any device
+    work (batch and hidden multiples of 128, one period, positive rates)."""
+    from paper_2510_12897_b300 import warm
+    g = synth.case30()
+    keep = []
+    net = opf._net_struct(g, keep)
+    wl = warm._lib()
+    bad = [warm.WarmOpts(100, 128, 1e3, 1e-4, 1e-2, 1.0, 0), warm.WarmOpts(128, 96, 1e3, 1e-4, 1e-2, 1.0, 0),
+           warm.WarmOpts(128, 128, -1.0, 1e-4, 1e-2, 1.0, 0), warm.WarmOpts(128, 128, 1e3, 0.0, 1e-2, 1.0, 0),
+           warm.WarmOpts(128, 128, 1e3, 1e-4, -1.0, 1.0, 0),
+           warm.WarmOpts(128, 128, 1e3, 1e-4, 1e-2, float("nan"), 0)]
+    for opts in bad:
+        h = ctypes.c_void_p()
+        _expect(opf.OPF_EINVAL, opf._check, wl.opf_warm_create(ctypes.byref(net), ctypes.byref(opts), ctypes.byref(h)))
+        assert not h.value
+    mp = synth.multi_period(g, 3, seed=1)
+    net2 = opf._net_struct(mp, keep)
+    h = ctypes.c_void_p()
+    _expect(opf.OPF_EINVAL, opf._check, wl.opf_warm_create(ctypes.byref(net2), ctypes.byref(warm.WarmOpts(128, 128, 1e3, 1e-4, 1e-2, 1.0, 0)), ctypes.byref(h)))
+    _expect(opf.OPF_EINVAL, opf._check, wl.opf_warm_create(None, None, ctypes.byref(h)))
