@@ -168,3 +168,41 @@ def test_trained_network_beats_flat_start(torch, oracle_mod):
         ratios.append(flat / max(O.cvio(profile(xw, t))))
     assert min(ratios) >= 10.0, ratios
     ws.close()
+
+
+@pytest.mark.slow
+def test_full_size_gain_judged_by_oracle(torch, oracle_mod):
+    """The 2,000-bus workload: 100k training profiles, 200 epochs, batches
+    of 4,096; on 32 held-out profiles the FP64 oracle's max violation
+    (constraints and bounds) of the predicted point is at least 9x below
+    the flat start's at the median and 4x below it on every profile (the
+    penalised loss's own optimum sits near 10x, see the design notes)."""
+    from paper_2510_12897_b300 import warm
+    g = synth.case2k_secure()
+    N, B = 100_000, 4096
+    pd, qd = synth.load_samples(g, N + B, seed=2024)
+    dev = torch.device("cuda")
+    ws = warm.WarmStart(g, batch=B, hidden=1024, seed=0)
+    warm.train(ws, torch.tensor(pd[:N], device=dev), torch.tensor(qd[:N], device=dev), epochs=200,
+               lr=1e-4, lr_out=1e-2, decay=1000.0)
+    x = torch.empty(ws.n_x * B, dtype=torch.float64, device=dev)
+    ws.predict(torch.tensor(pd[N:], device=dev), torch.tensor(qd[N:], device=dev), x)
+    ws.get_params()  # raises if a GEMM barrier wait timed out
+    xw = x.cpu().numpy()
+    M = opf.Model(g)
+    xf = torch.empty(M.n, dtype=torch.float64, device=dev)
+    M.flat_start(xf)
+    xf = xf.cpu().numpy()
+    counts = [g.nbus, g.nbus, g.ngen, g.ngen, 2 * g.nbranch, 2 * g.nbranch]
+    gains = []
+    for t in range(0, B, B // 32):
+        parts, off = [], 0
+        for c in counts:
+            parts.append(xw[off + c * t: off + c * (t + 1)])
+            off += c * B
+        gt = g.copy(load_pd=pd[N + t:N + t + 1], load_qd=qd[N + t:N + t + 1])
+        O = oracle_mod.Oracle(gt)
+        gains.append(max(O.cvio(xf)) / max(O.cvio(np.concatenate(parts))))
+    ws.close()
+    assert np.median(gains) >= 9.0, gains
+    assert min(gains) >= 4.0, gains
