@@ -87,15 +87,25 @@ def load_bf16_peak():
         return 1800.0
 
 
-def profile_traffic(kernel):
-    """DRAM bytes per launch of the branch or bus kernel from its committed
-    ncu summary (a line 'dram_bytes_per_launch: N'), or None."""
+def profile_value(kernel, key):
+    """A number 'key: N' from the committed ncu summary of the branch or bus
+    kernel on the 10k grid (dram_bytes_per_launch, fp64_flops_per_launch),
+    or None."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_kernel_case10k.md")
     try:
-        m = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", open(path).read())
+        m = re.search(key + r":\s*([0-9.eE+]+)", open(path).read())
         return float(m.group(1)) if m else None
     except OSError:
         return None
+
+
+def profile_traffic(kernel):
+    return profile_value(kernel, "dram_bytes_per_launch")
+
+
+# FP64 peak from the unit counts: 148 SMs x 2 FP64 FMA per clock (ncu:
+# 296 DFMA thread instructions per cycle for the GPU) x 2 flops x 2.032 GHz
+FP64_PEAK_TFLOPS = 148 * 2 * 2 * 2.032e9 / 1e12
 
 
 # ----------------------------------------------------------- byte counts --
@@ -218,6 +228,43 @@ def cpu_oracle_rate(g, seconds, max_steps=None, warmup=1):
         if el >= seconds or (max_steps and k >= max_steps):
             break
     return k / el, k, el
+
+
+def cpu_oracle_threads(grids, seconds):
+    """Full oracle evaluations per second over independent instances, one
+    thread per host core (the C oracle runs outside the interpreter lock)."""
+    import threading
+    import oracle
+    cores = len(os.sched_getaffinity(0))
+    rng = np.random.default_rng(2)
+    synth = __import__("paper_2510_12897_b300.synth", fromlist=["x"])
+    work = []
+    for g in grids:
+        O = oracle.Oracle(g)
+        work.append((O, synth.random_point(g, rng), rng.standard_normal(O.m)))
+    counts = [0] * cores
+    stop = time.perf_counter() + seconds
+
+    def run(w):
+        q = w
+        while time.perf_counter() < stop:
+            O, x, lam = work[q % len(work)]
+            O.obj(x)
+            O.grad(x)
+            O.cons(x)
+            O.jac(x)
+            O.hess(x, lam, 1.0)
+            counts[w] += 1
+            q += cores
+
+    t0 = time.perf_counter()
+    threads = [threading.Thread(target=run, args=(w,)) for w in range(cores)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    el = time.perf_counter() - t0
+    return sum(counts) / el, sum(counts), el, cores
 
 
 def reference_arm(args):
@@ -371,6 +418,12 @@ def main():
     ms_per_step = ms / K
     value = job_rate(world, K, ms / 1000.0)
 
+    # warm cache: the same step on one buffer set (the solver-loop case,
+    # data resident in L2)
+    g_warm = capture(lambda k, st: step(0, st), R)
+    g_warm.replay()
+    warm_ms = timed(g_warm, K // R) / (R * (K // R))
+
     # dominant kernel alone: branch phase, same rotation
     def branch_only(k, s):
         o = outs[k % R]
@@ -407,6 +460,17 @@ def main():
                 "kernel": f"{dominant} phase", "kernel_us": dom_us,
                 "algorithmic_bytes_per_launch": dom_bytes, "peak_kind": peak_kind}
 
+    fl_br, fl_bus = profile_value("branch", "fp64_flops_per_launch"), profile_value("bus", "fp64_flops_per_launch")
+    fp64 = None
+    if fl_br and fl_bus:
+        dom_fl = fl_br if dominant == "branch" else fl_bus
+        fp64 = {"bound": "alu", "unit": "TFLOP/s", "peak": FP64_PEAK_TFLOPS, "peak_kind": "unit counts x clock",
+                "eval_flops": fl_br + fl_bus,
+                "eval_achieved": (fl_br + fl_bus) / (ms_per_step * 1e-3) / 1e12,
+                "eval_frac": (fl_br + fl_bus) / (ms_per_step * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
+                "kernel": f"{dominant} phase", "kernel_achieved": dom_fl / (dom_us * 1e-6) / 1e12,
+                "kernel_frac": dom_fl / (dom_us * 1e-6) / 1e12 / FP64_PEAK_TFLOPS}
+
     # end to end through the host-buffer C-ABI call
     hx = [x.cpu().pin_memory() for x in xs[:2]]
     hl = [l.cpu().pin_memory() for l in ls[:2]]
@@ -429,7 +493,7 @@ def main():
 
     batched = None
     if not args.no_batched and rank == 0:
-        batched = batched_vs_plain(torch, opf, synth, stream, dev)
+        batched = batched_vs_plain(torch, opf, synth, stream, dev, cpu=not args.no_cpu)
 
     warm_start = None
     if not args.no_warm and rank == 0:
@@ -457,6 +521,9 @@ def main():
             "jac_hess": {"us": jh_us, "evals_per_s": 1e6 / jh_us, "algorithmic_bytes": jac_hess_bytes(g, nnzh),
                          "frac": jac_hess_bytes(g, nnzh) / (jh_us * 1e-6) / 1e9 / hbm},
             "phase_us": {"branch": br_us, "bus": bus_us, "autotune_eval": tuned_us},
+            "fp64_roofline": fp64,
+            "warm_cache": {"ms_per_step": warm_ms, "evals_per_s": 1000.0 / warm_ms,
+                           "note": "one buffer set, data resident in L2 (the solver-loop case)"},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * K, "clocks": clocks,
             "batched": batched, "warm_start": warm_start,
         }
@@ -466,7 +533,7 @@ def main():
         dist.destroy_process_group()
 
 
-def batched_vs_plain(torch, opf, synth, stream, dev):
+def batched_vs_plain(torch, opf, synth, stream, dev, cpu=False):
     """One batched graph launch vs a graph of per-period / per-instance
     single-model calls producing the same outputs."""
     out = {}
@@ -575,6 +642,11 @@ def batched_vs_plain(torch, opf, synth, stream, dev):
     tp = graph_us(plain_sc, reps=5)
     out["sc1k_501"] = {"batched_us": tb, "plain_loop_us": tp, "speedup": tp / tb, "launch": tuned,
                        "instance_evals_per_s": 501e6 / tb}
+    if cpu:
+        rate, k, el, cores = cpu_oracle_threads(insts[:64], 10.0)
+        out["sc1k_501"]["cpu_oracle_threads"] = {
+            "value": rate, "unit": "instance evals/s", "cores": cores, "kind": "oracle",
+            "sample": f"{k} full evaluations of 64 of the 501 instances in {el:.1f} s, one thread per core"}
     return out
 
 
