@@ -460,6 +460,22 @@ def main():
                 "kernel": f"{dominant} phase", "kernel_us": dom_us,
                 "algorithmic_bytes_per_launch": dom_bytes, "peak_kind": peak_kind}
 
+    # one augmented-Lagrangian inner iteration (f, grad f, g, J^T mu, Adam
+    # step) on the 10k grid: the callbacks inside a solver loop
+    from paper_2510_12897_b300 import al
+    A10 = al.AugLag(M0, rho=100.0, lr=1e-3)
+    xa, la = xs[0].clone(), torch.zeros(M0.m, dtype=f64, device=dev)
+    A10.iterate(xa, la, 5, stream=stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        A10.iterate(xa, la, 200, stream=stream)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    al_us = 1000.0 * e0.elapsed_time(e1) / 200
+    A10.close()
+
     fl_br, fl_bus = profile_value("branch", "fp64_flops_per_launch"), profile_value("bus", "fp64_flops_per_launch")
     fp64 = None
     if fl_br and fl_bus:
@@ -522,6 +538,7 @@ def main():
                          "frac": jac_hess_bytes(g, nnzh) / (jh_us * 1e-6) / 1e9 / hbm},
             "phase_us": {"branch": br_us, "bus": bus_us, "autotune_eval": tuned_us},
             "fp64_roofline": fp64,
+            "al_inner_iteration_us": al_us,
             "warm_cache": {"ms_per_step": warm_ms, "evals_per_s": 1000.0 / warm_ms,
                            "note": "one buffer set, data resident in L2 (the solver-loop case)"},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * K, "clocks": clocks,
@@ -725,6 +742,34 @@ def warm_start_summary(torch, opf, synth, dev, epochs):
     gain = (cf / cw).cpu().numpy()
     cw_np, cf_np = cw.cpu().numpy(), cf.cpu().numpy()
     ws.close()
+    # the warm start inside a solver loop: the augmented-Lagrangian loop of
+    # the library on held-out profile 0, from the flat start and from the
+    # network's point (largest row violation after each outer iteration)
+    from paper_2510_12897_b300 import al
+    f64 = torch.float64
+    g0 = g.copy(load_pd=pd[N:N + 1], load_qd=qd[N:N + 1])
+    M1 = opf.Model(g0)
+    xw = torch.cat([x[off * B:off * B + cnt] for off, cnt in
+                    zip(np.cumsum([0] + cols[:-1]).tolist(), cols)])
+    st = torch.zeros(3, dtype=f64, device=dev)
+    al_runs = {}
+    for start in ("flat", "warm"):
+        x1 = torch.empty(M1.n, dtype=f64, device=dev)
+        if start == "flat":
+            M1.flat_start(x1)
+        else:
+            x1.copy_(xw)
+        lam = torch.zeros(M1.m, dtype=f64, device=dev)
+        A = al.AugLag(M1, rho=100.0, lr=3e-3)
+        A.update(x1, lam, st)
+        traj = [float(st[1])]
+        lam.zero_()
+        for _ in range(10):
+            A.iterate(x1, lam, 100)
+            A.update(x1, lam, st)
+            traj.append(float(st[1]))
+        al_runs[start] = traj
+        A.close()
     return {
         "grid": "2,000 buses, 2,600 branches, 500 generators, 1,400 loads (ratings secured by a DC dispatch)",
         "network": "3 layers, width 1024, GELU, BF16 with FP32 accumulation",
@@ -739,6 +784,9 @@ def warm_start_summary(torch, opf, synth, dev, epochs):
         "gain_median": float(np.median(gain)), "gain_min": float(gain.min()),
         "frac_profiles_gain_ge_10": float(np.mean(gain >= 10.0)),
         "judge": "max violation of constraints and bounds from the library's FP64 constraint kernel",
+        "al_loop": {"problem": "held-out profile 0, single period", "rho": 100.0, "lr": 3e-3,
+                    "inner_per_outer": 100, "max_row_violation_flat": al_runs["flat"],
+                    "max_row_violation_warm": al_runs["warm"]},
     }
 
 

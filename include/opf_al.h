@@ -1,0 +1,67 @@
+/*
+ * opf_al.h — C ABI of a first-order augmented-Lagrangian loop on the GPU
+ * that consumes the callbacks of include/opf.h: a solver-side user of the
+ * objective, gradient, constraint and J^T v kernels, with every step of the
+ * iteration in the library's kernels (no host round trip per iteration).
+ *
+ * The paper's solvers (Sec. IV) are second-order interior-point methods
+ * whose KKT solves are out of scope here; this loop shows the callbacks in a
+ * solver iteration and serves as the consumer of the learned warm start.
+ *
+ * Problem: min f(x) s.t. gl <= g(x) <= gu, xl <= x <= xu (the NLP of
+ * include/opf.h). With multipliers lambda (one per row) and penalty rho > 0,
+ * the augmented Lagrangian is
+ *   L(x; lambda) = f(x) + sum_i [ rho/2 d_i(x)^2 - lambda_i^2 / (2 rho) ],
+ *   d_i(x) = s_i - clip(s_i, gl_i, gu_i),  s_i = g_i(x) + lambda_i / rho,
+ * and its gradient is grad f(x) + J(x)^T mu, mu_i = rho d_i(x).
+ * Inner iteration (Adam, Kingma and Ba; beta1 0.9, beta2 0.999, eps 1e-8,
+ * step count kept across calls until opf_al_reset):
+ *   G = grad f(x) + J(x)^T mu(x);  m = b1 m + (1 - b1) G;
+ *   v = b2 v + (1 - b2) G^2;  x = clip(x - lr (m / (1 - b1^k)) /
+ *   (sqrt(v / (1 - b2^k)) + eps), xl, xu).
+ * Outer update: lambda = mu(x).
+ *
+ * Ownership and errors as in include/opf.h: device buffers are caller-owned,
+ * calls are asynchronous on the given stream, codes OPF_*.
+ */
+#ifndef OPF_AL_H
+#define OPF_AL_H
+
+#include <stdint.h>
+
+#include "opf.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct opf_al opf_al;
+
+typedef struct {
+    double rho; /* penalty, > 0 */
+    double lr;  /* Adam step size, > 0 */
+} opf_al_opts;
+
+/* Loop state for one model (the model must outlive it): work vectors, Adam
+ * moments and device copies of the bounds. */
+int opf_al_create(opf_model *model, const opf_al_opts *opts, opf_al **out);
+int opf_al_destroy(opf_al *al);
+
+/* `iters` inner iterations on d_x (n, device, updated in place, projected
+ * onto [xl, xu] after every step) at fixed d_lambda (m, device). d_stats
+ * (device, 3 doubles, may be NULL) receives, at the point the last
+ * iteration started from: f(x), the largest row violation
+ * max_i max(gl_i - g_i, g_i - gu_i, 0), and L(x; lambda). */
+int opf_al_iterate(opf_al *al, double *d_x, const double *d_lambda, int32_t iters, double *d_stats,
+                   void *stream);
+
+/* Multiplier update at d_x: d_lambda = mu(x). d_stats as above, at d_x. */
+int opf_al_update(opf_al *al, const double *d_x, double *d_lambda, double *d_stats, void *stream);
+
+/* Clear the Adam moments and step count; set the penalty and step size. */
+int opf_al_reset(opf_al *al, double rho, double lr);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

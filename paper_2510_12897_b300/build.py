@@ -22,7 +22,7 @@ def sources():
 
 def deps():
     return (sources() + sorted(glob.glob(os.path.join(HERE, "csrc", "*.h")))
-            + [os.path.join(ROOT, "include", "opf.h")])
+            + sorted(glob.glob(os.path.join(ROOT, "include", "*.h"))))
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
