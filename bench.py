@@ -659,6 +659,17 @@ def batched_vs_plain(torch, opf, synth, stream, dev, cpu=False):
     tp = graph_us(plain_sc, reps=5)
     out["sc1k_501"] = {"batched_us": tb, "plain_loop_us": tp, "speedup": tp / tb, "launch": tuned,
                        "instance_evals_per_s": 501e6 / tb}
+    # the same batch with per-contingency corrective ratios and reserve rows
+    ratios = np.concatenate([[0.0], np.random.default_rng(3).uniform(0.1, 0.3, len(insts) - 1)])
+    Br = opf.Model(insts, link_ratios=ratios, reserve=0.1)
+    lr_ = torch.tensor(rng.standard_normal(Br.m), device=dev)
+    obr = bufs(Br)
+    Br.set_launch(**tuned["batched"])
+    tr = graph_us(lambda: Br.eval_all(xb, lr_, 1.0, *obr, stream=stream))
+    out["sc1k_501"]["with_reserve_and_corrective_ratios"] = {
+        "batched_us": tr, "rows": Br.m, "extra_rows": Br.m - B.m, "reserve": 0.1,
+        "corrective_ratios": "U(0.1, 0.3) per contingency"}
+    del Br, obr
     if cpu:
         rate, k, el, cores = cpu_oracle_threads(insts[:64], 10.0)
         out["sc1k_501"]["cpu_oracle_threads"] = {

@@ -86,6 +86,12 @@ typedef struct {
 typedef struct {
     double link_ratio; /* > 0: rows pg_s - pg_0 in [-ratio pmax, ratio pmax] for every
                           instance s >= 1 (all instances need equal ngen, nperiod 1) */
+    const double *link_ratios; /* NULL, or [ninst] per-instance corrective ratios (entry s
+                                  replaces link_ratio for instance s >= 1; entry 0 unused;
+                                  every entry finite and >= 0) */
+    double reserve;    /* > 0: one reserve row per instance and period,
+                          sum_g pg_g <= sum_g pmax_g - reserve * (total Pd of the period),
+                          i.e. the spare capacity covers that share of the demand */
 } opf_batch_opts;
 
 typedef struct opf_model opf_model;

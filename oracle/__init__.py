@@ -72,6 +72,8 @@ def lib():
         L = ctypes.CDLL(LIB_PATH)
         L.ora_create.restype = ctypes.c_void_p
         L.ora_create.argtypes = [ctypes.POINTER(OraNet), ctypes.c_int32, ctypes.c_double]
+        L.ora_create2.restype = ctypes.c_void_p
+        L.ora_create2.argtypes = [ctypes.POINTER(OraNet), ctypes.c_int32, ctypes.c_double, _f64p, ctypes.c_double]
         L.ora_destroy.argtypes = [ctypes.c_void_p]
         L.ora_error.restype = ctypes.c_char_p
         L.ora_dims.argtypes = [ctypes.c_void_p, _i64p, _i64p, _i64p, _i64p]
@@ -109,10 +111,12 @@ class Oracle:
     """The oracle for one instance (a grid) or a batch (a list of grids).
 
     ``link_ratio > 0`` adds rows pg_s - pg_0 in [-ratio pmax, ratio pmax]
-    tying every instance s >= 1 to instance 0.
+    tying every instance s >= 1 to instance 0 (``link_ratios``: one ratio
+    per instance instead); ``reserve > 0`` adds per instance and period the
+    row sum_g pg_g <= sum_g pmax_g - reserve * (total Pd).
     """
 
-    def __init__(self, grids, link_ratio: float = 0.0):
+    def __init__(self, grids, link_ratio: float = 0.0, link_ratios=None, reserve: float = 0.0):
         if not isinstance(grids, (list, tuple)):
             grids = [grids]
         self.grids = list(grids)
@@ -121,7 +125,12 @@ class Oracle:
         for k, g in enumerate(grids):
             self._fill(nets[k], g)
         self._nets = nets
-        self.ctx = lib().ora_create(nets, len(grids), float(link_ratio))
+        lr = None
+        if link_ratios is not None:
+            lr = np.ascontiguousarray(link_ratios, dtype=np.float64)
+            self._keep.append(lr)
+        self.ctx = lib().ora_create2(nets, len(grids), float(link_ratio),
+                                     None if lr is None else lr.ctypes.data_as(_f64p), float(reserve))
         if not self.ctx:
             raise ValueError("oracle: " + lib().ora_error().decode())
         n, m, nj, nh = (ctypes.c_int64() for _ in range(4))

@@ -73,8 +73,10 @@ struct ora_ctx {
     int ninst;
     inst_t *in;
     double link_ratio;
+    double *link_ratios; /* per instance (entry 0 unused) */
+    double reserve;      /* > 0: reserve rows, one per instance and period */
     int link;
-    int64_t n, m, link_row;
+    int64_t n, m, link_row, res_row;
     int64_t nnzj, nnzh;
     int64_t *jrow, *jcol, *jkey;
     int64_t *hrow, *hcol, *hkey;
@@ -280,6 +282,7 @@ void ora_destroy(ora_ctx *C)
         for (int k = 0; k < C->in[s].nown; k++)
             free(C->in[s].own[k]);
     free(C->in);
+    free(C->link_ratios);
     free(C->jrow); free(C->jcol); free(C->jkey);
     free(C->hrow); free(C->hcol); free(C->hkey);
     free(C);
@@ -330,8 +333,18 @@ static void push(int64_t *keys, int64_t *cnt, int64_t n, int64_t r, int64_t c)
 
 ora_ctx *ora_create(const ora_net *nets, int32_t ninst, double link_ratio)
 {
+    return ora_create2(nets, ninst, link_ratio, NULL, 0.0);
+}
+
+ora_ctx *ora_create2(const ora_net *nets, int32_t ninst, double link_ratio, const double *link_ratios,
+                     double reserve)
+{
     if (ninst < 1) {
         set_err("ninst < 1");
+        return NULL;
+    }
+    if (!(link_ratio >= 0.0) || !(reserve >= 0.0)) {
+        set_err("link_ratio and reserve must be >= 0");
         return NULL;
     }
     for (int s = 0; s < ninst; s++)
@@ -341,7 +354,11 @@ ora_ctx *ora_create(const ora_net *nets, int32_t ninst, double link_ratio)
     C->ninst = ninst;
     C->in = calloc((size_t)ninst, sizeof(inst_t));
     C->link_ratio = link_ratio;
-    C->link = link_ratio > 0.0 && ninst > 1;
+    C->link_ratios = malloc(sizeof(double) * (size_t)ninst);
+    for (int s = 0; s < ninst; s++)
+        C->link_ratios[s] = link_ratios ? link_ratios[s] : link_ratio;
+    C->reserve = reserve;
+    C->link = (link_ratio > 0.0 || link_ratios) && ninst > 1;
     if (C->link)
         for (int s = 0; s < ninst; s++)
             if (nets[s].ngen != nets[0].ngen || nets[s].nperiod != 1) {
@@ -399,7 +416,11 @@ ora_ctx *ora_create(const ora_net *nets, int32_t ninst, double link_ratio)
     }
     C->n = xo;
     C->link_row = co;
-    C->m = co + (C->link ? (int64_t)nets[0].ngen * (ninst - 1) : 0);
+    C->res_row = co + (C->link ? (int64_t)nets[0].ngen * (ninst - 1) : 0);
+    C->m = C->res_row;
+    if (C->reserve > 0.0)
+        for (int s = 0; s < ninst; s++)
+            C->m += nets[s].nperiod;
 
     /* ---- Jacobian pattern: one (row, col) per variable a term depends on */
     int64_t cap = 0;
@@ -410,6 +431,9 @@ ora_ctx *ora_create(const ora_net *nets, int32_t ninst, double link_ratio)
                2 * (int64_t)n->ngen * T;
     }
     cap += C->link ? 2 * (int64_t)nets[0].ngen * ninst : 0;
+    if (C->reserve > 0.0)
+        for (int s = 0; s < ninst; s++)
+            cap += (int64_t)nets[s].nperiod * nets[s].ngen;
     int64_t *keys = malloc(sizeof(int64_t) * (cap + 1));
     int64_t cnt = 0, N = C->n;
     for (int s = 0; s < ninst; s++) {
@@ -464,6 +488,13 @@ ora_ctx *ora_create(const ora_net *nets, int32_t ninst, double link_ratio)
                 push(keys, &cnt, N, row, v_pg(&C->in[s], g, 0));
                 push(keys, &cnt, N, row, v_pg(&C->in[0], g, 0));
             }
+    if (C->reserve > 0.0) {
+        int64_t row = C->res_row;
+        for (int s = 0; s < ninst; s++)
+            for (int t = 0; t < nets[s].nperiod; t++, row++)
+                for (int g = 0; g < nets[s].ngen; g++)
+                    push(keys, &cnt, N, row, v_pg(&C->in[s], g, t));
+    }
     C->nnzj = sort_unique(keys, cnt);
     C->jkey = keys;
     C->jrow = malloc(sizeof(int64_t) * (C->nnzj + 1));
@@ -592,9 +623,25 @@ void ora_bounds(const ora_ctx *C, double *xl, double *xu, double *gl, double *gu
         for (int s = 1; s < C->ninst; s++)
             for (int g = 0; g < n0->ngen; g++) {
                 int64_t row = C->link_row + g + (int64_t)n0->ngen * (s - 1);
-                gl[row] = -C->link_ratio * n0->pmax[g];
-                gu[row] = C->link_ratio * n0->pmax[g];
+                gl[row] = -C->link_ratios[s] * n0->pmax[g];
+                gu[row] = C->link_ratios[s] * n0->pmax[g];
             }
+    }
+    if (C->reserve > 0.0) {
+        int64_t row = C->res_row;
+        for (int s = 0; s < C->ninst; s++) {
+            const ora_net *n = &C->in[s].net;
+            double cap = 0.0;
+            for (int g = 0; g < n->ngen; g++)
+                cap += n->pmax[g];
+            for (int t = 0; t < n->nperiod; t++, row++) {
+                double pd = 0.0;
+                for (int l = 0; l < n->nload; l++)
+                    pd += n->pd[(int64_t)t * n->nload + l];
+                gl[row] = -INFINITY;
+                gu[row] = cap - C->reserve * pd;
+            }
+        }
     }
 }
 
@@ -693,6 +740,15 @@ void ora_cons(const ora_ctx *C, const double *x, double *c, double *scale)
                 double a = x[v_pg(&C->in[s], g, 0)], b = x[v_pg(&C->in[0], g, 0)];
                 ADD(C->link_row + g + (int64_t)ng * (s - 1), a - b, fabs(a) + fabs(b));
             }
+    }
+    if (C->reserve > 0.0) {
+        int64_t row = C->res_row;
+        for (int s = 0; s < C->ninst; s++)
+            for (int t = 0; t < C->in[s].net.nperiod; t++, row++)
+                for (int g = 0; g < C->in[s].net.ngen; g++) {
+                    double a = x[v_pg(&C->in[s], g, t)];
+                    ADD(row, a, fabs(a));
+                }
     }
 #undef ADD
 }
@@ -795,6 +851,13 @@ int ora_jac(const ora_ctx *C, const double *x, double *vals, double *scale)
                 acc(&A, row, v_pg(&C->in[s], g, 0), 1.0, 1.0);
                 acc(&A, row, v_pg(&C->in[0], g, 0), -1.0, 1.0);
             }
+    }
+    if (C->reserve > 0.0) {
+        int64_t row = C->res_row;
+        for (int s = 0; s < C->ninst; s++)
+            for (int t = 0; t < C->in[s].net.nperiod; t++, row++)
+                for (int g = 0; g < C->in[s].net.ngen; g++)
+                    acc(&A, row, v_pg(&C->in[s], g, t), 1.0, 1.0);
     }
     return A.bad ? -1 : 0;
 }

@@ -44,6 +44,11 @@ typedef struct ora_ctx ora_ctx;
 
 /* Builds layout and sparsity patterns. Copies every array. NULL on bad input. */
 ora_ctx *ora_create(const ora_net *nets, int32_t ninst, double link_ratio);
+/* As ora_create, with per-instance corrective ratios (NULL: link_ratio for
+ * every instance; entry 0 unused) and reserve rows when reserve > 0: per
+ * instance and period, sum_g pg_g <= sum_g pmax_g - reserve * (total Pd). */
+ora_ctx *ora_create2(const ora_net *nets, int32_t ninst, double link_ratio, const double *link_ratios,
+                     double reserve);
 void ora_destroy(ora_ctx *);
 const char *ora_error(void);
 

@@ -18,7 +18,7 @@ void set_error(const char *fmt, ...)
     va_end(ap);
 }
 
-int build_model(const opf_network *nets, int32_t ninst, double link_ratio, bool device, Model **out);
+int build_model(const opf_network *nets, int32_t ninst, const opf_batch_opts *opts, bool device, Model **out);
 void free_model(Model *M);
 void jac_pattern(const Model &M, int64_t *rows, int64_t *cols);
 void hess_pattern(const Model &M, int64_t *rows, int64_t *cols);
@@ -94,7 +94,7 @@ int opf_model_create(const opf_network *net, opf_model **out)
         return OPF_EINVAL;
     }
     Model *M = nullptr;
-    int rc = build_model(net, 1, 0.0, true, &M);
+    int rc = build_model(net, 1, nullptr, true, &M);
     if (rc)
         return rc;
     *out = new opf_model{M};
@@ -110,7 +110,7 @@ int opf_batch_create(const opf_network *nets, int32_t ninst, const opf_batch_opt
     }
     *out = nullptr;
     Model *M = nullptr;
-    int rc = build_model(nets, ninst, opts ? opts->link_ratio : 0.0, true, &M);
+    int rc = build_model(nets, ninst, opts, true, &M);
     if (rc)
         return rc;
     *out = new opf_model{M};
@@ -126,7 +126,7 @@ int opf_structure_create(const opf_network *nets, int32_t ninst, const opf_batch
     }
     *out = nullptr;
     Model *M = nullptr;
-    int rc = build_model(nets, ninst, opts ? opts->link_ratio : 0.0, false, &M);
+    int rc = build_model(nets, ninst, opts, false, &M);
     if (rc)
         return rc;
     *out = new opf_model{M};

@@ -796,6 +796,8 @@ __global__ void __launch_bounds__(256) jt_bus_kernel(const KParams P)
             }
             if (I.link_c >= 0)  // rows pg_s - pg_0 of instance s >= 1
                 vpg += __ldg(P.lam + I.link_c + g);
+            if (I.res_c >= 0)  // the instance's reserve row of this period
+                vpg += __ldg(P.lam + I.res_c + t);
             if (P.link && s == 0)  // instance 0 appears in every linking row
                 for (int q = 1; q < P.ninst; q++)
                     vpg -= __ldg(P.lam + P.link_c0 + g + (int64_t)ng * (q - 1));
@@ -926,6 +928,36 @@ __global__ void flat_kernel(const DevArrays d, int32_t ninst, int64_t nbr_items,
     }
 }
 
+// Reserve rows (sum over an instance's generators of pg in one period), one
+// warp per row: lane-strided partial sums, then a fixed shuffle tree; their
+// Jacobian entries (+1 for each generator) lane-strided.
+__global__ void reserve_kernel(const DevArrays d, int64_t nres, int64_t res_c0, const double *__restrict__ x,
+                               double *c, double *jac)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < nres; r += warps) {
+        const int2 st = __ldg(d.res_st + r);
+        const InstDev *I = d.inst + st.x;
+        const int ng = __ldg(&I->ng), T = __ldg(&I->T), nb = __ldg(&I->nb);
+        if (c) {
+            const double *pg = x + __ldg(&I->x0) + 2 * (int64_t)nb * T + (int64_t)ng * st.y;
+            double acc = 0.0;
+            for (int g = lane; g < ng; g += 32)
+                acc += __ldg(pg + g);
+            for (int off = 16; off; off >>= 1)
+                acc += __shfl_down_sync(0xffffffffu, acc, off);
+            if (lane == 0)
+                c[res_c0 + r] = acc;
+        }
+        if (jac) {
+            double *J = jac + __ldg(&I->res_j) + (int64_t)ng * st.y;
+            for (int g = lane; g < ng; g += 32)
+                J[g] = 1.0;
+        }
+    }
+}
+
 __global__ void sincos_tab_kernel(const double2 *__restrict__ tab, const double *__restrict__ d,
                                   int64_t n, double *sn, double *cs)
 {
@@ -1032,6 +1064,11 @@ int launch_all(Model &M, const EvalArgs &a, unsigned what, cudaStream_t s, int p
     case 5: e = dispatch<true, false, true>(P, one, occ, run_branch, run_bus, gb, bb, gu, bu, s); break;
     case 6: e = dispatch<false, true, true>(P, one, occ, run_branch, run_bus, gb, bb, gu, bu, s); break;
     default: e = dispatch<true, true, true>(P, one, occ, run_branch, run_bus, gb, bb, gu, bu, s); break;
+    }
+    if (e == cudaSuccess && M.reserve && (C || J) && (phases & 2)) {
+        const int64_t threads = 32 * M.nres;
+        reserve_kernel<<<(int)((threads + 255) / 256), 256, 0, s>>>(M.d, M.nres, M.res_c0, a.x, C ? a.c : nullptr,
+                                                                    J ? a.jac : nullptr);
     }
     if (e == cudaSuccess)
         e = cudaGetLastError();

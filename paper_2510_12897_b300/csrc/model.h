@@ -57,10 +57,12 @@ struct __align__(16) InstDev {
     int64_t hva, hvm;   // Hessian entries of one period of the va rows / vm rows
     int64_t link_c, link_j;  // this instance's linking rows and their Jacobian offset; -1 if none
     int64_t link_x0;    // first pg of instance 0 (linking partner)
+    int64_t res_c, res_j;  // this instance's reserve rows (one per period) and their Jacobian offset; -1 if none
 };
 static_assert(sizeof(InstDev) % 16 == 0, "InstDev is loaded as int4 words");
 
 struct DevArrays {
+    int2 *res_st = nullptr;       // per reserve row: (instance, period)
     int32_t *bus_order = nullptr; // per instance: buses by arc count, warps dealt heavy / light
     // branches (concatenated over instances)
     int4 *br = nullptr;           // local (f, t, slot of the from-arc, slot of the to-arc)
@@ -117,8 +119,14 @@ struct Model {
     bool on_device = false;  // false: structure only (no device arrays)
     bool link = false;
     double link_ratio = 0.0;
+    std::vector<double> link_ratios;   // per instance (entry 0 unused)
+    bool reserve = false;
+    double reserve_frac = 0.0;
+    std::vector<double> res_cap;       // per reserve row: sum pmax - reserve * total Pd
+    int64_t nres = 0;                  // reserve rows (one per instance and period)
     int64_t n = 0, m = 0, nnzj = 0, nnzh = 0;
     int64_t link_c0 = 0, link_j0 = 0;  // first linking row / its first Jacobian value
+    int64_t res_c0 = 0, res_j0 = 0;    // first reserve row / its first Jacobian value
     int64_t nbr_items = 0, nbus_items = 0, ngen_items = 0, narc_slots = 0;
     int64_t nload_total = 0;      // sum over instances of nload * nperiod
     int32_t max_part = 0;         // capacity of obj_part

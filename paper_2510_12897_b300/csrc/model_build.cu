@@ -144,7 +144,7 @@ void free_model(Model *M)
 
 // Builds one model over `ninst` networks. On error returns a code and frees
 // everything it allocated.
-int build_model(const opf_network *nets, int32_t ninst, double link_ratio, bool device, Model **out)
+int build_model(const opf_network *nets, int32_t ninst, const opf_batch_opts *opts, bool device, Model **out)
 {
     *out = nullptr;
     if (!nets || ninst < 1) {
@@ -156,7 +156,19 @@ int build_model(const opf_network *nets, int32_t ninst, double link_ratio, bool 
         if (rc)
             return rc;
     }
-    bool link = link_ratio > 0.0 && ninst > 1;
+    const double link_ratio = opts ? opts->link_ratio : 0.0;
+    const double reserve = opts ? opts->reserve : 0.0;
+    if (!(link_ratio >= 0.0) || !std::isfinite(link_ratio) || !(reserve >= 0.0) || !std::isfinite(reserve)) {
+        set_error("link_ratio and reserve must be finite and >= 0");
+        return OPF_EINVAL;
+    }
+    if (opts && opts->link_ratios)
+        for (int s = 1; s < ninst; s++)
+            if (!(opts->link_ratios[s] >= 0.0) || !std::isfinite(opts->link_ratios[s])) {
+                set_error("link_ratios[%d] must be finite and >= 0", s);
+                return OPF_EINVAL;
+            }
+    bool link = (link_ratio > 0.0 || (opts && opts->link_ratios)) && ninst > 1;
     if (link)
         for (int s = 0; s < ninst; s++)
             if (nets[s].ngen != nets[0].ngen || nets[s].nperiod != 1) {
@@ -168,6 +180,12 @@ int build_model(const opf_network *nets, int32_t ninst, double link_ratio, bool 
     M->ninst = ninst;
     M->link = link;
     M->link_ratio = link_ratio;
+    M->link_ratios.assign(ninst, link_ratio);
+    if (opts && opts->link_ratios)
+        for (int s = 1; s < ninst; s++)
+            M->link_ratios[s] = opts->link_ratios[s];
+    M->reserve = reserve > 0.0;
+    M->reserve_frac = reserve;
     M->on_device = device;
     if (device) {
         if (cudaGetDevice(&M->device) != cudaSuccess ||
@@ -410,6 +428,7 @@ int build_model(const opf_network *nets, int32_t ninst, double link_ratio, bool 
         I.pd0 = po;
         I.link_c = I.link_j = -1;
         I.link_x0 = 0;
+        I.res_c = I.res_j = -1;
         xo += (int64_t)T * (2 * nb + 2 * ng + 2 * na);
         co += (int64_t)T * (1 + 7 * (int64_t)nl + 2 * nb) + (H.ramp ? (int64_t)ng * (T - 1) : 0);
         jo += (int64_t)T * (1 + 30 * (int64_t)nl + 2 * nb + 2 * ng) + (H.ramp ? 2 * (int64_t)ng * (T - 1) : 0);
@@ -431,6 +450,30 @@ int build_model(const opf_network *nets, int32_t ninst, double link_ratio, bool 
         }
         co += ng * (ninst - 1);
         jo += 2 * ng * (ninst - 1);
+    }
+    // reserve rows: per instance, one per period, after the linking rows
+    M->res_c0 = co;
+    M->res_j0 = jo;
+    std::vector<int2> res_st;
+    if (M->reserve) {
+        for (int s = 0; s < ninst; s++) {
+            const opf_network &n = nets[s];
+            M->inst[s].res_c = co;
+            M->inst[s].res_j = jo;
+            double cap = 0.0;
+            for (int g = 0; g < n.ngen; g++)
+                cap += n.gen_pmax[g];
+            for (int t = 0; t < n.nperiod; t++) {
+                double pd = 0.0;
+                for (int l = 0; l < n.nload; l++)
+                    pd += n.load_pd[(int64_t)t * n.nload + l];
+                M->res_cap.push_back(cap - reserve * pd);
+                res_st.push_back(make_int2(s, t));
+            }
+            co += n.nperiod;
+            jo += (int64_t)n.nperiod * n.ngen;
+        }
+        M->nres = (int64_t)res_st.size();
     }
     M->n = xo;
     M->m = co;
@@ -457,7 +500,7 @@ int build_model(const opf_network *nets, int32_t ninst, double link_ratio, bool 
     for (int k = -kTrigK; k <= kTrigK; k++)
         trig.push_back(make_double2(std::sin((double)k / kTrigScale), std::cos((double)k / kTrigScale)));
     UP(trig, trig)
-    UP(br_jb, br_jb) UP(bus_order, bus_order) UP(load_ptr, load_ptr) UP(load_list, load_list)
+    UP(br_jb, br_jb) UP(bus_order, bus_order) UP(res_st, res_st) UP(load_ptr, load_ptr) UP(load_list, load_list)
     UP(gen_busid, gen_busid)
     UP(bus_a, bus_a) UP(bus_b, bus_b) UP(bus_c, bus_c) UP(gsbs, gsbs) UP(slot_code, slot_code) UP(gen_list, gen_list)
     UP(Pd, Pd) UP(Qd, Qd) UP(c2, c2) UP(c1, c1) UP(c0, c0) UP(pbnd, pbnd) UP(qbnd, qbnd)
@@ -585,6 +628,16 @@ void jac_pattern(const Model &M, int64_t *rows, int64_t *cols)
             }
         }
     }
+    if (M.reserve) {
+        int64_t r = M.res_c0;
+        for (int s = 0; s < M.ninst; s++) {
+            Offs Xs = xoffs(M.host[s], M.inst[s]);
+            const int64_t ng = M.host[s].ng, T = M.host[s].T;
+            for (int64_t t = 0; t < T; t++, r++)
+                for (int64_t g = 0; g < ng; g++)
+                    put(r, Xs.pg + g + ng * t);
+        }
+    }
 }
 
 void hess_pattern(const Model &M, int64_t *rows, int64_t *cols)
@@ -707,10 +760,15 @@ void bounds(const Model &M, double *xl, double *xu, double *gl, double *gu)
         int64_t c = M.link_c0, ng = M.host[0].ng;
         for (int s = 1; s < M.ninst; s++)
             for (int64_t g = 0; g < ng; g++, c++) {
-                gl[c] = -M.link_ratio * M.host[0].pmax[g];
-                gu[c] = M.link_ratio * M.host[0].pmax[g];
+                gl[c] = -M.link_ratios[s] * M.host[0].pmax[g];
+                gu[c] = M.link_ratios[s] * M.host[0].pmax[g];
             }
     }
+    if (M.reserve && gl)
+        for (int64_t r = 0; r < M.nres; r++) {
+            gl[M.res_c0 + r] = -INFINITY;
+            gu[M.res_c0 + r] = M.res_cap[r];
+        }
 }
 
 }  // namespace opf

@@ -12,7 +12,7 @@
 #include "model.h"
 
 namespace opf {
-int build_model(const opf_network *nets, int32_t ninst, double link_ratio, bool device, Model **out);
+int build_model(const opf_network *nets, int32_t ninst, const opf_batch_opts *opts, bool device, Model **out);
 void free_model(Model *M);
 void bounds(const Model &M, double *xl, double *xu, double *gl, double *gu);
 }  // namespace opf
@@ -850,7 +850,7 @@ int opf_warm_create(const opf_network *net, const opf_warm_opts *opts, opf_warm 
         }
     n2.load_pd = lp.data();
     n2.load_qd = lq.data();
-    int rc = build_model(&n2, 1, 0.0, true, &w->M);
+    int rc = build_model(&n2, 1, nullptr, true, &w->M);
     if (rc) {
         delete w;
         return rc;

@@ -40,7 +40,8 @@ class OpfNetwork(ctypes.Structure):
 
 
 class OpfBatchOpts(ctypes.Structure):
-    _fields_ = [("link_ratio", ctypes.c_double)]
+    _fields_ = [("link_ratio", ctypes.c_double), ("link_ratios", ctypes.POINTER(ctypes.c_double)),
+                ("reserve", ctypes.c_double)]
 
 
 class OpfLaunch(ctypes.Structure):
@@ -177,14 +178,19 @@ class Model:
     only (dims, patterns, bounds) without touching a GPU.
     """
 
-    def __init__(self, grids, link_ratio: float = 0.0, structure_only: bool = False):
-        batch = isinstance(grids, (list, tuple))
-        gl = list(grids) if batch else [grids]
+    def __init__(self, grids, link_ratio: float = 0.0, structure_only: bool = False, link_ratios=None,
+                 reserve: float = 0.0):
+        batch = isinstance(grids, (list, tuple)) or link_ratios is not None or reserve > 0.0
+        gl = list(grids) if isinstance(grids, (list, tuple)) else [grids]
         self._keep = []
         arr = (OpfNetwork * len(gl))(*[_net_struct(g, self._keep) for g in gl])
         h = _vp()
         L = lib()
-        opts = OpfBatchOpts(float(link_ratio))
+        lr = None
+        if link_ratios is not None:
+            lr = np.ascontiguousarray(link_ratios, dtype=np.float64)
+            self._keep.append(lr)
+        opts = OpfBatchOpts(float(link_ratio), None if lr is None else lr.ctypes.data_as(_f64p), float(reserve))
         if structure_only:
             _check(L.opf_structure_create(arr, len(gl), ctypes.byref(opts), ctypes.byref(h)))
         elif batch:

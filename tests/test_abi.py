@@ -52,6 +52,35 @@ def test_patterns_and_bounds_equal_oracle(L, oracle_mod, name):
         np.testing.assert_array_equal(a, b)
 
 
+@pytest.mark.parametrize("name,opts", [
+    ("batch30", dict(link_ratios=[0.0, 0.1, 0.3, 0.05, 0.2, 0.15, 0.25], reserve=0.1)),
+    ("mp30x5", dict(reserve=0.2)),
+    ("case30_general", dict(reserve=0.05)),
+])
+def test_reserve_and_corrective_patterns_equal_oracle(L, oracle_mod, name, opts):
+    """Reserve rows (one per instance and period, after the linking rows) and
+    per-instance corrective ratios: sizes, patterns and bounds equal the
+    oracle's bit for bit."""
+    g = _grids()[name]
+    M = opf.Model(g, structure_only=True, **opts)
+    O = oracle_mod.Oracle(g, **opts)
+    assert (M.n, M.m, M.nnzj, M.nnzh) == (O.n, O.m, O.nnzj, O.nnzh)
+    for a, b in zip(M.jac_pattern() + M.hess_pattern(), O.jac_pattern() + O.hess_pattern()):
+        np.testing.assert_array_equal(a, b)
+    for a, b in zip(M.bounds(), O.bounds()):
+        np.testing.assert_array_equal(a, b)
+    # one reserve row per instance and period on top of the plain model
+    nres = sum(x.nperiod for x in (g if isinstance(g, list) else [g]))
+    plain = oracle_mod.Oracle(g, link_ratio=max(opts.get("link_ratios") or [0.0]))
+    assert O.m == plain.m + nres
+
+
+def test_reserve_options_rejected(L):
+    g = synth.contingencies(synth.case30(), 2, seed=4)
+    _expect(opf.OPF_EINVAL, opf.Model, g, structure_only=True, reserve=-0.1)
+    _expect(opf.OPF_EINVAL, opf.Model, g, structure_only=True, link_ratios=[0.0, float("nan"), 0.1])
+
+
 @pytest.mark.slow
 def test_patterns_10k_equal_oracle(L, oracle_mod):
     g = synth.case10k()

@@ -262,14 +262,21 @@ def test_jacobian_differences(oracle_mod, which):
     assert np.max(np.abs(fd[~mask])) < 1e-9
 
 
-def test_jacobian_batch_with_links(oracle_mod):
+@pytest.mark.parametrize("opts", [dict(link_ratio=0.2),
+                                  dict(link_ratios=[0.0, 0.1, 0.3], reserve=0.15)])
+def test_jacobian_batch_with_links(oracle_mod, opts):
+    """Central differences of cons over sampled columns (every pg column
+    included) for a batch with linking rows, and with per-instance ratios
+    and reserve rows."""
     insts = synth.contingencies(synth.case30(), 2, seed=9)
-    O = oracle_mod.Oracle(insts, link_ratio=0.2)
+    O = oracle_mod.Oracle(insts, **opts)
     x = np.concatenate([point(s, 20 + k) for k, s in enumerate(insts)])
     r, c = O.jac_pattern()
     J = sp.coo_matrix((O.jac(x), (r, c)), shape=(O.m, O.n)).toarray()
     # differences only over a subset of columns to keep it fast
-    cols = np.random.default_rng(0).choice(O.n, 120, replace=False)
+    pgs = np.concatenate([np.arange(2 * s.nbus, 2 * s.nbus + s.ngen) + off for s, off in
+                          zip(insts, np.cumsum([0] + [synth.n_vars(s) for s in insts[:-1]]))])
+    cols = np.union1d(np.random.default_rng(0).choice(O.n, 120, replace=False), pgs)
     for j in cols:
         def fj(t):
             y = x.copy()
@@ -468,3 +475,22 @@ def test_invalid_networks_rejected(oracle_mod):
     bad = g.copy(gen_bus=np.array([0, 5], np.int32))
     with pytest.raises(ValueError):
         oracle_mod.Oracle(bad)
+
+
+def test_reserve_rows_value_and_bounds(oracle_mod):
+    """A reserve row holds the instance-period's total generation and its
+    upper bound leaves the requested share of the period's demand as spare
+    capacity (both checked on hand-set outputs: every generator at the same
+    value)."""
+    g = synth.multi_period(synth.case30(), 3, seed=2, ramp_ratio=0.0)
+    O = oracle_mod.Oracle(g, reserve=0.25)
+    plain = oracle_mod.Oracle(g)
+    x = np.zeros(O.n)
+    nb, ng, T = g.nbus, g.ngen, 3
+    x[2 * nb * T:2 * nb * T + ng * T] = 0.75  # every pg, every period
+    c = O.cons(x)
+    np.testing.assert_allclose(c[plain.m:], np.full(T, 0.75 * ng), rtol=1e-15)
+    _, _, gl, gu = O.bounds()
+    assert np.all(np.isneginf(gl[plain.m:]))
+    demand = g.load_pd.sum(axis=1)
+    np.testing.assert_allclose(gu[plain.m:], g.gen_pmax.sum() - 0.25 * demand, rtol=1e-14)

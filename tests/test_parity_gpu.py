@@ -74,9 +74,9 @@ def check_against_oracle(O, got, x, lam, sigma, tag=""):
     assert abs(got["obj"][0] - f) <= 1e-12 * max(abs(f), 1.0) * 10, (got["obj"][0], f)
 
 
-def both(torch, oracle_mod, g, link=0.0):
-    M = opf.Model(g, link_ratio=link)
-    O = oracle_mod.Oracle(g, link_ratio=link)
+def both(torch, oracle_mod, g, link=0.0, **opts):
+    M = opf.Model(g, link_ratio=link, **opts)
+    O = oracle_mod.Oracle(g, link_ratio=link, **opts)
     assert (M.n, M.m, M.nnzj, M.nnzh) == (O.n, O.m, O.nnzj, O.nnzh)
     for a, b in zip(M.jac_pattern() + M.hess_pattern(), O.jac_pattern() + O.hess_pattern()):
         np.testing.assert_array_equal(a, b)
@@ -231,6 +231,34 @@ def test_batch_small_with_links(torch, oracle_mod):
     insts = synth.contingencies(synth.case30(general=True), 9, seed=7)
     M, O = both(torch, oracle_mod, insts, link=0.2)
     for x, lam in points(insts, M.m, 3, seed=7):
+        check_against_oracle(O, run_all(torch, M, x, lam, 1.0), x, lam, 1.0)
+
+
+@pytest.mark.parametrize("opts", [dict(link_ratios=[0.0] + [0.05 * k for k in range(1, 10)], reserve=0.1),
+                                  dict(reserve=0.3)])
+def test_batch_with_reserve_and_corrective_ratios(torch, oracle_mod, opts):
+    """N-1 batch with per-contingency corrective ratios and reserve rows
+    (one per instance): every output against the oracle, and J^T v."""
+    import scipy.sparse as sp
+    insts = synth.contingencies(synth.case30(general=True), 9, seed=7)
+    M, O = both(torch, oracle_mod, insts, **opts)
+    for x, lam in points(insts, M.m, 2, seed=8):
+        check_against_oracle(O, run_all(torch, M, x, lam, 1.0), x, lam, 1.0)
+    x, v = next(points(insts, M.m, 1, seed=9))
+    out = torch.full((M.n,), np.nan, dtype=torch.float64, device="cuda")
+    M.eval_jtprod(dev(torch, x), dev(torch, v), out)
+    torch.cuda.synchronize()
+    r, c = O.jac_pattern()
+    jv, js = O.jac(x, with_scale=True)
+    ref = sp.coo_matrix((jv, (r, c)), shape=(O.m, O.n)).T @ v
+    scale = sp.coo_matrix((js, (r, c)), shape=(O.m, O.n)).T @ np.abs(v)
+    close("jtprod", host(out), ref, scale)
+
+
+def test_multi_period_reserve(torch, oracle_mod):
+    g = synth.multi_period(synth.case30(general=True), 6, seed=3, ramp_ratio=0.2)
+    M, O = both(torch, oracle_mod, g, reserve=0.2)
+    for x, lam in points(g, M.m, 2, seed=4):
         check_against_oracle(O, run_all(torch, M, x, lam, 1.0), x, lam, 1.0)
 
 
