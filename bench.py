@@ -62,7 +62,7 @@ def parse():
                    help="fixed launch shape instead of the autotuner's (profiling runs)")
     p.add_argument("--e2e-steps", type=int, default=256)
     p.add_argument("--no-warm", action="store_true", help="skip the learned warm-start section")
-    p.add_argument("--warm-epochs", type=int, default=400)
+    p.add_argument("--warm-epochs", type=int, default=600)
     p.add_argument("--profile-batched", type=int, default=0, metavar="REPS",
                    help="profiling aid: only run REPS plain evaluations of the 10k-bus grid "
                         "with 32 load scenarios in one model, then exit")
