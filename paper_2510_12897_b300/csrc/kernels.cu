@@ -58,6 +58,7 @@ struct KParams {
     int32_t want_grad, want_obj;
     int64_t nbr_items, nbus_items, ngen_items;
     const int32_t *order = nullptr;  // bus-phase order within an instance, or null for id order
+    double *xw = nullptr;            // x, writable (branch phase that sets the flows)
     const double *__restrict__ x;
     const double *__restrict__ lam;
     double sigma;
@@ -200,7 +201,7 @@ __device__ __forceinline__ BrStatic load_br(const DevArrays &d, int kb, bool nee
     return s;
 }
 
-template <bool CONS, bool JAC, bool HESS, bool ONE, bool OCC>
+template <bool CONS, bool JAC, bool HESS, bool ONE, bool OCC, bool SETF = false>
 __global__ void __launch_bounds__(OCC ? 256 : 512, OCC ? 3 : 1) branch_kernel(const KParams P)
 {
     cudaTriggerProgrammaticLaunchCompletion();
@@ -248,7 +249,7 @@ __global__ void __launch_bounds__(OCC ? 256 : 512, OCC ? 3 : 1) branch_kernel(co
         const double vaf = __ldg(xs + iva + f), vat = __ldg(xs + iva + b);
         const double vmf = __ldg(xs + ivm + f), vmt = __ldg(xs + ivm + b);
         double pf = 0, qf = 0, pt = 0, qt = 0;
-        if (CONS || JAC || HESS) {
+        if ((CONS || JAC || HESS) && !SETF) {
             pf = __ldg(xs + ip + ck);
             pt = __ldg(xs + ip + nl + ck);
             qf = __ldg(xs + iq + ck);
@@ -274,6 +275,18 @@ __global__ void __launch_bounds__(OCC ? 256 : 512, OCC ? 3 : 1) branch_kernel(co
         const double Bft = fma(Yft.x, sn, neg(Yft.y * cs_));
         const double Atf = fma(Ytf.x, cs_, neg(Ytf.y * sn));
         const double Btf = neg(fma(Ytf.x, sn, Ytf.y * cs_));
+        if (SETF) {  // p, q := the flows at the voltages (their rows become exactly zero)
+            const double vf2 = vmf * vmf, vt2 = vmt * vmt;
+            pf = fma(Yff.x, vf2, vft * Aft);
+            qf = fma(neg(Yff.y), vf2, vft * Bft);
+            pt = fma(Ytt.x, vt2, vft * Atf);
+            qt = fma(neg(Ytt.y), vt2, vft * Btf);
+            double *xw = P.xw + I.x0;
+            xw[ip + ck] = pf;
+            xw[ip + nl + ck] = pt;
+            xw[iq + ck] = qf;
+            xw[iq + nl + ck] = qt;
+        }
 
         if (CONS) {
             const double vf2 = vmf * vmf, vt2 = vmt * vmt;
@@ -1147,6 +1160,38 @@ int launch_jtprod(Model &M, const double *x, const double *v, double *out, cudaS
         e = one ? launch_pdl(jt_branch_kernel<true>, gb, 128, s, P) : launch_pdl(jt_branch_kernel<false>, gb, 128, s, P);
     if (e == cudaSuccess)
         e = one ? launch_pdl(jt_bus_kernel<true>, gu, 128, s, P) : launch_pdl(jt_bus_kernel<false>, gu, 128, s, P);
+    if (e != cudaSuccess) {
+        set_error("kernel launch failed: %s", cudaGetErrorString(e));
+        return OPF_ECUDA;
+    }
+    return launch_status();
+}
+
+int launch_cons_setflows(Model &M, double *x, double *obj, double *grad, double *c, cudaStream_t s)
+{
+    if (M.ninst != 1) {
+        set_error("launch_cons_setflows: single-instance models only");
+        return OPF_ESTATE;
+    }
+    KParams P = base_params(M);
+    P.x = x;
+    P.xw = x;
+    P.lam = nullptr;
+    P.sigma = 1.0;
+    P.obj = obj;
+    P.grad = grad;
+    P.c = c;
+    P.jac = nullptr;
+    P.hess = nullptr;
+    P.want_grad = grad ? 1 : 0;
+    P.want_obj = obj ? 1 : 0;
+    cudaError_t e = cudaSuccess;
+    if (M.nbr_items > 0)
+        e = launch_pdl(branch_kernel<true, false, false, true, false, true>,
+                       grid_for(M.nbr_items, 128, 0, M.num_sms, 0), 128, s, P);
+    if (e == cudaSuccess)
+        e = launch_pdl(bus_kernel<true, false, false, true>,
+                       grid_for(M.nbus_items + M.ngen_items, 128, 0, M.num_sms, M.max_part), 128, s, P);
     if (e != cudaSuccess) {
         set_error("kernel launch failed: %s", cudaGetErrorString(e));
         return OPF_ECUDA;

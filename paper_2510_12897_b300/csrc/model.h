@@ -154,6 +154,9 @@ int launch_flat_start(Model &M, double *x, cudaStream_t s);
 int launch_sincos(Model &M, const double *d, int64_t n, double *sn, double *cs, cudaStream_t s);
 int launch_jtprod(Model &M, const double *x, const double *v, double *out, cudaStream_t s);
 int launch_flows(Model &M, double *x, cudaStream_t s);
+// single instance: p, q := flows at x's voltages (written into x), then the
+// objective, gradient and constraints at that point (flow rows zero)
+int launch_cons_setflows(Model &M, double *x, double *obj, double *grad, double *c, cudaStream_t s);
 int launch_set_loads(Model &M, const double *pd, const double *qd, cudaStream_t s);
 
 // abi.cu

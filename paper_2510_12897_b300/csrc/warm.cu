@@ -323,6 +323,7 @@ struct WarmDev {
     const float *pk, *qk;                    // 5 / base load (0 where the base is 0)
     const double *vmin, *vmax;               // per bus
     const double *pmin, *pmax, *qmin, *qmax; // per generator
+    const double *angmin, *angmax, *rate;    // per branch
 };
 
 // u = normalised loads (BF16, zero padding): (load / base - 1) / 0.2 as one
@@ -390,10 +391,78 @@ __device__ __forceinline__ double block_sum(double acc, double *red)
     return s;
 }
 
+// Bounds of the batch model's rows and variables from their structure (no
+// bound arrays read): rows [ref | 4 flow groups | angle | P, Q balance |
+// thermal from, to], each group [period][element]; only the angle rows
+// ([angmin, angmax] of the branch) and the thermal rows ((-inf, 0]) are not
+// equalities. Variables [va | vm | pg | qg | p | q]: va free, vm in
+// [vmin, vmax], pg, qg in their limits, p, q in [-rate_a, rate_a].
+__device__ __forceinline__ void row_bounds(const WarmDev &w, int64_t r, double &lo, double &hi)
+{
+    const int64_t T = w.B, nlT = (int64_t)w.nl * T, nbT = (int64_t)w.nb * T;
+    lo = 0.0;
+    hi = 0.0;
+    if (r >= T + 4 * nlT && r < T + 5 * nlT) {
+        const unsigned k = (unsigned)(r - T - 4 * nlT) % (unsigned)w.nl;  // 32-bit: the batch model has < 2^31 rows
+        lo = w.angmin[k];
+        hi = w.angmax[k];
+    } else if (r >= T + 5 * nlT + 2 * nbT) {
+        lo = -INFINITY;
+    }
+}
+
+__device__ __forceinline__ bool var_bounds(const WarmDev &w, int64_t j, double &lo, double &hi)
+{
+    const int64_t T = w.B, nbT = (int64_t)w.nb * T, ngT = (int64_t)w.ng * T, naT = 2 * (int64_t)w.nl * T;
+    if (j < nbT)
+        return false;  // va
+    // 32-bit remainders: the batch model has fewer than 2^31 variables
+    if (j < 2 * nbT) {
+        const unsigned i = (unsigned)(j - nbT) % (unsigned)w.nb;
+        lo = w.vmin[i];
+        hi = w.vmax[i];
+    } else if (j < 2 * nbT + ngT) {
+        const unsigned g = (unsigned)(j - 2 * nbT) % (unsigned)w.ng;
+        lo = w.pmin[g];
+        hi = w.pmax[g];
+    } else if (j < 2 * nbT + 2 * ngT) {
+        const unsigned g = (unsigned)(j - 2 * nbT - ngT) % (unsigned)w.ng;
+        lo = w.qmin[g];
+        hi = w.qmax[g];
+    } else {
+        int64_t off = j - 2 * nbT - 2 * ngT;  // p block, then q block, each [period][arc]
+        if (off >= naT)
+            off -= naT;
+        const unsigned k = (unsigned)off % (unsigned)w.nl;  // arc k and nl + k share branch k's rating
+        hi = w.rate[k];
+        lo = -hi;
+    }
+    return true;
+}
+
+// one-time check at creation: the structured bounds equal the model's
+__global__ void bounds_check_kernel(const WarmDev w, const double *xl, const double *xu, int64_t n,
+                                    const double *gl, const double *gu, int64_t m, unsigned *bad)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m + n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double lo = -INFINITY, hi = INFINITY;
+        bool ok;
+        if (i < m) {
+            row_bounds(w, i, lo, hi);
+            ok = lo == gl[i] && hi == gu[i];
+        } else {
+            var_bounds(w, i - m, lo, hi);
+            ok = lo == xl[i - m] && hi == xu[i - m];
+        }
+        if (!ok)
+            atomicAdd(bad, 1u);
+    }
+}
+
 // constraint rows: rho = c - clip(c, gl, gu); v1 = (2 penalty / B) rho;
 // per-block sums of rho^2 into part
-__global__ void resid_kernel(const WarmDev w, const double *c, const double *gl, const double *gu,
-                             int64_t m, double *v1, double *part)
+__global__ void resid_kernel(const WarmDev w, const double *c, int64_t m, double *v1, double *part)
 {
     __shared__ double red[32];
     double acc = 0.0;
@@ -401,7 +470,9 @@ __global__ void resid_kernel(const WarmDev w, const double *c, const double *gl,
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
          i += (int64_t)gridDim.x * blockDim.x) {
         const double ci = c[i];
-        const double rho = ci - fmin(fmax(ci, gl[i]), gu[i]);
+        double lo, hi;
+        row_bounds(w, i, lo, hi);
+        const double rho = ci - fmin(fmax(ci, lo), hi);
         v1[i] = k * rho;
         acc += rho * rho;
     }
@@ -413,14 +484,17 @@ __global__ void resid_kernel(const WarmDev w, const double *c, const double *gl,
 // variable bounds: per-block sums of r^2, r = x - clip(x, xl, xu) (their
 // gradient enters through the flow multipliers for p, q and through the
 // output map for vm, pg, qg)
-__global__ void bound_kernel(const double *x, const double *xl, const double *xu, int64_t n, double *part)
+__global__ void bound_kernel(const WarmDev w, const double *x, int64_t n, double *part)
 {
     __shared__ double red[32];
     double acc = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const double xi = x[i];
-        const double r = xi - fmin(fmax(xi, xl[i]), xu[i]);
+    const int64_t j0 = (int64_t)w.nb * w.B;  // va has no bounds
+    for (int64_t j = j0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        double lo, hi;
+        var_bounds(w, j, lo, hi);
+        const double xj = x[j];
+        const double r = xj - fmin(fmax(xj, lo), hi);
         acc += r * r;
     }
     const double s = block_sum(acc, red);
@@ -437,8 +511,7 @@ __global__ void bound_kernel(const double *x, const double *xl, const double *xu
 // rows, where v2 = -g_own = -(2 x_own v_thermal + v_balance + k r_own),
 // k = 2 penalty / B. This kernel overwrites the flow rows of v1 with v2 (one
 // thread per branch and period, its four arc variables).
-__global__ void flowmult_kernel(const WarmDev w, const int4 *br, const double *x, const double *xl,
-                                const double *xu, double *v)
+__global__ void flowmult_kernel(const WarmDev w, const int4 *br, const double *x, double *v)
 {
     const int64_t T = w.B, nl = w.nl, nb = w.nb, ng = w.ng, na = 2 * nl;
     const int64_t nlT = nl * T, nbT = nb * T, ngT = ng * T;
@@ -454,8 +527,8 @@ __global__ void flowmult_kernel(const WarmDev w, const int4 *br, const double *x
         const int64_t vb[4] = {bal + b.x, bal + nbT + b.x, bal + b.y, bal + nbT + b.y};
 #pragma unroll
         for (int g = 0; g < 4; g++) {
-            const double xo = x[own[g]];
-            const double r = xo - fmin(fmax(xo, xl[own[g]]), xu[own[g]]);
+            const double xo = x[own[g]], rate = w.rate[k];
+            const double r = xo - fmin(fmax(xo, -rate), rate);
             const double vt = v[th + (g < 2 ? 0 : nlT)];
             v[T + it + g * nlT] = -(fma(2.0 * xo, vt, v[vb[g]]) + kpen * r);
         }
@@ -590,7 +663,7 @@ struct opf_warm {
     float *pk = nullptr, *qk = nullptr;
     double *vmin = nullptr, *vmax = nullptr, *pmin = nullptr,
            *pmax = nullptr, *qmin = nullptr, *qmax = nullptr, *gl = nullptr, *gu = nullptr,
-           *xl = nullptr, *xu = nullptr;
+           *xl = nullptr, *xu = nullptr, *angmin = nullptr, *angmax = nullptr, *rate = nullptr;
     bf16 *U = nullptr, *H1 = nullptr, *H2 = nullptr, *dYh = nullptr, *dZ2h = nullptr, *dZ1h = nullptr;
     // transposed BF16 copies (the backward GEMMs take K-contiguous operands)
     bf16 *UT = nullptr, *H1T = nullptr, *H2T = nullptr, *W2T = nullptr, *W3T = nullptr, *dYT = nullptr,
@@ -664,6 +737,9 @@ WarmDev dev_of(const opf_warm *w)
     d.pmax = w->pmax;
     d.qmin = w->qmin;
     d.qmax = w->qmax;
+    d.angmin = w->angmin;
+    d.angmax = w->angmax;
+    d.rate = w->rate;
     return d;
 }
 
@@ -774,18 +850,14 @@ int loss_grad(opf_warm *w, const double *d_pd, const double *d_qd, double *d_sta
     const WarmDev d = dev_of(w);
     map_kernel<<<grid1((int64_t)w->B * (2 * w->nb + 2 * w->ng)), 256, 0, s>>>(d, w->Y, w->x);
     int rc = launch_set_loads(*w->M, d_pd, d_qd, s);
-    if (!rc)
-        rc = launch_flows(*w->M, w->x, s);
-    if (!rc) {  // objective, gradient, constraints
-        EvalArgs a{w->x, nullptr, 1.0, w->obj, w->gradf, w->c, nullptr, nullptr};
-        rc = launch_eval(*w->M, a, W_OBJ | W_GRAD | W_CONS, s);
-    }
+    if (!rc)  // p, q := flows at the voltages; objective, gradient, constraints there
+        rc = launch_cons_setflows(*w->M, w->x, w->obj, w->gradf, w->c, s);
     if (!rc) {  // v1 = 2 penalty rho / B; residual sums; flow rows of v1 := v2
-        resid_kernel<<<w->nparts, 256, 0, s>>>(d, w->c, w->gl, w->gu, w->m, w->v1, w->part);
-        bound_kernel<<<w->nparts, 256, 0, s>>>(w->x, w->xl, w->xu, w->n, w->part + w->nparts);
+        resid_kernel<<<w->nparts, 256, 0, s>>>(d, w->c, w->m, w->v1, w->part);
+        bound_kernel<<<w->nparts, 256, 0, s>>>(d, w->x, w->n, w->part + w->nparts);
         if (d_stats)
             stats_kernel<<<1, 32, 0, s>>>(d, w->part, 2 * w->nparts, w->obj, d_stats);
-        flowmult_kernel<<<grid1((int64_t)w->nl * w->B), 256, 0, s>>>(d, w->M->d.br, w->x, w->xl, w->xu, w->v1);
+        flowmult_kernel<<<grid1((int64_t)w->nl * w->B), 256, 0, s>>>(d, w->M->d.br, w->x, w->v1);
         rc = launch_jtprod(*w->M, w->x, w->v1, w->u2, s);
     }
     if (!rc)
@@ -857,6 +929,12 @@ int opf_warm_create(const opf_network *net, const opf_warm_opts *opts, opf_warm 
     }
     w->n = w->M->n;
     w->m = w->M->m;
+    if (w->n >= (int64_t)1 << 31 || w->m >= (int64_t)1 << 31) {
+        set_error("opf_warm_create: batch x network too large (%lld variables, %lld rows; the warm start's "
+                  "kernels index them in 32 bits)", (long long)w->n, (long long)w->m);
+        destroy(w);
+        return OPF_EINVAL;
+    }
     w->n1 = w->n / w->B;
     // parameters: W1 [H][Kin], b1 [H], W2 [H][H], b2 [H], W3 [Nout][H], b3 [Nout]
     w->oW1 = 0;
@@ -905,10 +983,9 @@ int opf_warm_create(const opf_network *net, const opf_warm_opts *opts, opf_warm 
     if (!rc) rc = wupload(w, &w->pmax, pmax);
     if (!rc) rc = wupload(w, &w->qmin, qmin);
     if (!rc) rc = wupload(w, &w->qmax, qmax);
-    if (!rc) rc = wupload(w, &w->gl, gl);
-    if (!rc) rc = wupload(w, &w->gu, gu);
-    if (!rc) rc = wupload(w, &w->xl, xl);
-    if (!rc) rc = wupload(w, &w->xu, xu);
+    if (!rc) rc = wupload(w, &w->angmin, std::vector<double>(net->br_angmin, net->br_angmin + w->nl));
+    if (!rc) rc = wupload(w, &w->angmax, std::vector<double>(net->br_angmax, net->br_angmax + w->nl));
+    if (!rc) rc = wupload(w, &w->rate, std::vector<double>(net->br_rate_a, net->br_rate_a + w->nl));
     if (!rc) rc = walloc(w, &w->U, (size_t)w->B * w->Kin);
     if (!rc) rc = walloc(w, &w->H1, act);
     if (!rc) rc = walloc(w, &w->H2, act);
@@ -954,6 +1031,31 @@ int opf_warm_create(const opf_network *net, const opf_warm_opts *opts, opf_warm 
     if (!rc)
         rc = check_cuda(cudaFuncSetAttribute(umma_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, USMEM),
                         "GEMM shared memory");
+    if (!rc) {  // the structured bounds of the kernels against the model's own
+        double *b = nullptr;
+        unsigned *bad = nullptr, nbad = 0;
+        const size_t bytes = sizeof(double) * 2 * (size_t)(w->n + w->m);
+        if (cudaMalloc(&b, bytes) != cudaSuccess || cudaMalloc(&bad, sizeof(unsigned)) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("opf_warm_create: cudaMalloc of %zu bytes failed", bytes);
+            rc = OPF_ENOMEM;
+        } else {
+            double *bxl = b, *bxu = b + w->n, *bgl = b + 2 * w->n, *bgu = b + 2 * w->n + w->m;
+            cudaMemcpy(bxl, xl.data(), sizeof(double) * w->n, cudaMemcpyHostToDevice);
+            cudaMemcpy(bxu, xu.data(), sizeof(double) * w->n, cudaMemcpyHostToDevice);
+            cudaMemcpy(bgl, gl.data(), sizeof(double) * w->m, cudaMemcpyHostToDevice);
+            cudaMemcpy(bgu, gu.data(), sizeof(double) * w->m, cudaMemcpyHostToDevice);
+            cudaMemset(bad, 0, sizeof(unsigned));
+            bounds_check_kernel<<<grid1(w->n + w->m), 256>>>(dev_of(w), bxl, bxu, w->n, bgl, bgu, w->m, bad);
+            rc = check_cuda(cudaMemcpy(&nbad, bad, sizeof(unsigned), cudaMemcpyDeviceToHost), "bounds check");
+            if (!rc && nbad) {
+                set_error("opf_warm_create: %u structured bounds differ from the model's", nbad);
+                rc = OPF_ESTATE;
+            }
+        }
+        cudaFree(b);
+        cudaFree(bad);
+    }
     if (!rc && (cudaMemset(w->am, 0, sizeof(float) * w->nparams) != cudaSuccess ||
                 cudaMemset(w->av, 0, sizeof(float) * w->nparams) != cudaSuccess ||
                 cudaMemset(w->grads, 0, sizeof(float) * w->nparams) != cudaSuccess ||
