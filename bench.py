@@ -488,24 +488,37 @@ def main():
                 "kernel_frac": dom_fl / (dom_us * 1e-6) / 1e12 / FP64_PEAK_TFLOPS}
 
     # end to end through the host-buffer C-ABI call
-    hx = [x.cpu().pin_memory() for x in xs[:2]]
-    hl = [l.cpu().pin_memory() for l in ls[:2]]
-    ho = [torch.empty(k, dtype=f64).pin_memory() for k in (1, n, m, nnzj, nnzh)]
+    # host buffers page-locked by the library itself (memory pinned by another
+    # CUDA runtime in the process copies at pageable speed on these boxes)
+    hx = [x.cpu().numpy().copy() for x in xs[:2]]
+    hl = [l.cpu().numpy().copy() for l in ls[:2]]
+    ho = [[np.empty(k) for k in (1, n, m, nnzj, nnzh)] for _ in range(2)]
+    for a in hx + hl + ho[0] + ho[1]:
+        opf.host_register(a)
     e2e_steps = max(1, min(K, args.e2e_steps))
-    with torch.cuda.stream(stream):
-        M0.eval_all_host(hx[0], hl[0], 1.0, *ho, stream=stream)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    t0 = time.perf_counter()
-    with torch.cuda.stream(stream):
-        for k in range(e2e_steps):
-            M0.eval_all_host(hx[k % 2], hl[k % 2], 1.0, *ho, stream=stream)
-    torch.cuda.synchronize()
-    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, dev)
+
+    def host_loop(pipelined):
+        with torch.cuda.stream(stream):
+            M0.eval_all_host(hx[0], hl[0], 1.0, *ho[0], stream=stream, pipelined=pipelined)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            for k in range(e2e_steps):
+                M0.eval_all_host(hx[k % 2], hl[k % 2], 1.0, *ho[k % 2], stream=stream, pipelined=pipelined)
+        torch.cuda.synchronize()
+        return max_over_ranks(time.perf_counter() - t0, dist, dev)
+
+    e2e_sync_s = host_loop(False)   # one synchronous call per step
+    e2e_s = host_loop(True)         # pipelined calls: copies overlap the next evaluation
+    for a in hx + hl + ho[0] + ho[1]:
+        opf.host_unregister(a)
     e2e = {"value": job_rate(world, e2e_steps, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": 8 * (n + m), "d2h_bytes_per_step": 8 * (1 + n + m + nnzj + nnzh),
-           "steps": e2e_steps, "pinned": True}
+           "steps": e2e_steps, "pinned": "registered with opf_host_register",
+           "call": "opf_eval_all_host_async (pipelined), every step's inputs in and outputs out",
+           "synchronous_call_value": job_rate(world, e2e_steps, e2e_sync_s)}
 
     batched = None
     if not args.no_batched and rank == 0:

@@ -45,6 +45,7 @@
 #ifndef OPF_H
 #define OPF_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -257,6 +258,30 @@ int opf_set_launch(opf_model *model, const opf_launch *cfg);
  * Allocates temporary output buffers for the duration of the call. */
 int opf_autotune(opf_model *model, const double *d_x, const double *d_lambda, int32_t reps,
                  void *stream, opf_launch *best, double *best_us);
+
+/* opf_eval_all_host without the final synchronisation, pipelined across
+ * calls: inputs are copied in on an internal stream into one of two staging
+ * slots, the evaluation runs on a second internal stream and the outputs
+ * are copied out on a third, so the copies of one call overlap the
+ * evaluation and copies of the next. `stream` (the caller's) orders the
+ * call after the caller's earlier work on it and is made to wait for the
+ * call's outputs: the host buffers are complete (and the inputs may be
+ * reused) once `stream` has been synchronised. Host buffers should be
+ * page-locked (opf_host_register). Calls on one model must come from one
+ * thread; allocates its staging and streams on first use (freed with the
+ * model). */
+int opf_eval_all_host_async(opf_model *model, const double *h_x, const double *h_lambda,
+                            double obj_weight, double *h_obj, double *h_grad, double *h_c,
+                            double *h_jvals, double *h_hvals, void *stream);
+
+/* Page-lock caller host memory for this library's host<->device copies
+ * (opf_eval_all_host) so they run at full DMA bandwidth; unregister before
+ * freeing. Memory page-locked by another CUDA runtime loaded in the same
+ * process (for example a framework's pinned allocator) can be copied by
+ * this library only at pageable speed, so register it here. Errors:
+ * OPF_EINVAL for NULL or zero size, OPF_ECUDA if the runtime refuses. */
+int opf_host_register(void *ptr, size_t bytes);
+int opf_host_unregister(void *ptr);
 
 /* Thread-local description of the last error on this thread. */
 const char *opf_last_error(void);

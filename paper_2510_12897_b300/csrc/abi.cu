@@ -318,6 +318,110 @@ int opf_eval_all_host(opf_model *m, const double *h_x, const double *h_lambda, d
     return OPF_OK;
 }
 
+int opf_eval_all_host_async(opf_model *m, const double *h_x, const double *h_lambda, double obj_weight,
+                            double *h_obj, double *h_grad, double *h_c, double *h_jvals, double *h_hvals,
+                            void *stream)
+{
+    int rc = check_dev(m);
+    if (rc)
+        return rc;
+    Model &M = *m->M;
+    if (!h_x || (h_hvals && !h_lambda)) {
+        set_error("h_x is NULL, or h_lambda is NULL with h_hvals requested");
+        return OPF_EINVAL;
+    }
+    const size_t words = (size_t)(M.n + M.m + 1 + M.n + M.m + M.nnzj + M.nnzh);
+    if (!M.s_cmp) {  // first use: two staging slots, three streams, events
+        bool ok = true;
+        for (int k = 0; k < 2 && ok; k++)
+            ok = cudaMalloc(&M.astage[k], sizeof(double) * words) == cudaSuccess;
+        ok = ok && cudaStreamCreateWithFlags(&M.s_in, cudaStreamNonBlocking) == cudaSuccess &&
+             cudaStreamCreateWithFlags(&M.s_cmp, cudaStreamNonBlocking) == cudaSuccess &&
+             cudaStreamCreateWithFlags(&M.s_out, cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&M.ev_entry, cudaEventDisableTiming) == cudaSuccess;
+        for (int k = 0; k < 2 && ok; k++)
+            ok = cudaEventCreateWithFlags(&M.ev_in[k], cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&M.ev_cmp[k], cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&M.ev_out[k], cudaEventDisableTiming) == cudaSuccess;
+        if (!ok || !M.s_cmp) {
+            cudaGetLastError();
+            set_error("opf_eval_all_host_async: staging or stream creation failed");
+            return OPF_ENOMEM;
+        }
+    }
+    const int k = M.aslot;
+    M.aslot ^= 1;
+    double *dx = M.astage[k], *dl = dx + M.n, *dobj = dl + M.m, *dg = dobj + 1, *dc = dg + M.n;
+    double *dj = dc + M.m, *dh = dj + M.nnzj;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // copy-in after the caller's earlier work and after the compute that last read this slot
+    cudaError_t e = cudaEventRecord(M.ev_entry, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(M.s_in, M.ev_entry, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(M.s_in, M.ev_cmp[k], 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dx, h_x, sizeof(double) * M.n, cudaMemcpyHostToDevice, M.s_in);
+    if (e == cudaSuccess && h_hvals)
+        e = cudaMemcpyAsync(dl, h_lambda, sizeof(double) * M.m, cudaMemcpyHostToDevice, M.s_in);
+    if (e == cudaSuccess) e = cudaEventRecord(M.ev_in[k], M.s_in);
+    // compute after the copy-in and after the copy-out that last read this slot's outputs
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(M.s_cmp, M.ev_in[k], 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(M.s_cmp, M.ev_out[k], 0);
+    if (e != cudaSuccess) {
+        set_error("opf_eval_all_host_async: %s", cudaGetErrorString(e));
+        return OPF_ECUDA;
+    }
+    EvalArgs a{dx, h_hvals ? dl : nullptr, obj_weight, h_obj ? dobj : nullptr, h_grad ? dg : nullptr,
+               h_c ? dc : nullptr, h_jvals ? dj : nullptr, h_hvals ? dh : nullptr};
+    rc = eval(m, mask_of(a), a, M.s_cmp);
+    if (rc)
+        return rc;
+    e = cudaEventRecord(M.ev_cmp[k], M.s_cmp);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(M.s_out, M.ev_cmp[k], 0);
+    struct {
+        double *h;
+        const double *d;
+        int64_t n;
+    } outs[5] = {{h_obj, dobj, 1}, {h_grad, dg, M.n}, {h_c, dc, M.m}, {h_jvals, dj, M.nnzj},
+                 {h_hvals, dh, M.nnzh}};
+    for (auto &o : outs)
+        if (o.h && e == cudaSuccess)
+            e = cudaMemcpyAsync(o.h, o.d, sizeof(double) * o.n, cudaMemcpyDeviceToHost, M.s_out);
+    if (e == cudaSuccess) e = cudaEventRecord(M.ev_out[k], M.s_out);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, M.ev_out[k], 0);  // the caller's stream sees completion
+    if (e != cudaSuccess) {
+        set_error("opf_eval_all_host_async: %s", cudaGetErrorString(e));
+        return OPF_ECUDA;
+    }
+    return OPF_OK;
+}
+
+int opf_host_register(void *ptr, size_t bytes)
+{
+    if (!ptr || bytes == 0) {
+        set_error("opf_host_register: NULL pointer or zero size");
+        return OPF_EINVAL;
+    }
+    cudaError_t e = cudaHostRegister(ptr, bytes, cudaHostRegisterDefault);
+    if (e != cudaSuccess) {
+        set_error("cudaHostRegister failed: %s", cudaGetErrorString(e));
+        return OPF_ECUDA;
+    }
+    return OPF_OK;
+}
+
+int opf_host_unregister(void *ptr)
+{
+    if (!ptr) {
+        set_error("opf_host_unregister: NULL pointer");
+        return OPF_EINVAL;
+    }
+    cudaError_t e = cudaHostUnregister(ptr);
+    if (e != cudaSuccess) {
+        set_error("cudaHostUnregister failed: %s", cudaGetErrorString(e));
+        return OPF_ECUDA;
+    }
+    return OPF_OK;
+}
+
 int opf_flat_start(opf_model *m, double *d_x, void *stream)
 {
     int rc = check_dev(m);

@@ -139,6 +139,13 @@ struct Model {
     // staging buffers of opf_eval_all_host (allocated on first use)
     double *stage = nullptr;
     size_t stage_bytes = 0;
+    // pipelined host-buffer evaluation (opf_eval_all_host_async): two staging
+    // slots, copy-in / compute / copy-out streams and their events
+    double *astage[2] = {nullptr, nullptr};
+    cudaStream_t s_in = nullptr, s_cmp = nullptr, s_out = nullptr;
+    cudaEvent_t ev_entry = nullptr, ev_in[2] = {nullptr, nullptr}, ev_cmp[2] = {nullptr, nullptr},
+                ev_out[2] = {nullptr, nullptr};
+    int aslot = 0;
 };
 
 struct EvalArgs {

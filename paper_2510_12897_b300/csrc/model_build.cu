@@ -139,6 +139,21 @@ void free_model(Model *M)
         cudaFree(p);
     if (M->stage)
         cudaFree(M->stage);
+    if (M->s_cmp) {  // the pipelined host-buffer path was used
+        cudaStreamSynchronize(M->s_in);
+        cudaStreamSynchronize(M->s_cmp);
+        cudaStreamSynchronize(M->s_out);
+        for (int k = 0; k < 2; k++) {
+            cudaFree(M->astage[k]);
+            cudaEventDestroy(M->ev_in[k]);
+            cudaEventDestroy(M->ev_cmp[k]);
+            cudaEventDestroy(M->ev_out[k]);
+        }
+        cudaEventDestroy(M->ev_entry);
+        cudaStreamDestroy(M->s_in);
+        cudaStreamDestroy(M->s_cmp);
+        cudaStreamDestroy(M->s_out);
+    }
     delete M;
 }
 

@@ -91,6 +91,7 @@ def lib():
                             _vp],
         "opf_eval_all_noalloc": [_vp, _vp, _vp, ctypes.c_double, _vp, _vp, _vp, _vp, _vp, _vp],
         "opf_eval_all_host": [_vp, _vp, _vp, ctypes.c_double, _vp, _vp, _vp, _vp, _vp, _vp],
+        "opf_eval_all_host_async": [_vp, _vp, _vp, ctypes.c_double, _vp, _vp, _vp, _vp, _vp, _vp],
         "opf_flat_start": [_vp, _vp, _vp],
         "opf_sincos": [_vp, _vp, ctypes.c_int64, _vp, _vp, _vp],
         "opf_eval_jtprod": [_vp, _vp, _vp, _vp, _vp],
@@ -99,6 +100,8 @@ def lib():
         "opf_get_launch": [_vp, ctypes.POINTER(OpfLaunch)],
         "opf_set_launch": [_vp, ctypes.POINTER(OpfLaunch)],
         "opf_autotune": [_vp, _vp, _vp, ctypes.c_int32, _vp, ctypes.POINTER(OpfLaunch), _f64p],
+        "opf_host_register": [_vp, ctypes.c_size_t],
+        "opf_host_unregister": [_vp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -108,6 +111,26 @@ def lib():
     L.opf_last_error.argtypes = []
     _lib = L
     return L
+
+
+def host_register(array) -> None:
+    """Page-lock a host numpy array (or CPU tensor) for this library's copies."""
+    ptr, nbytes = _host_buf(array)
+    _check(lib().opf_host_register(ptr, nbytes))
+
+
+def host_unregister(array) -> None:
+    _check(lib().opf_host_unregister(_host_buf(array)[0]))
+
+
+def _host_buf(a):
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("host buffer must be contiguous")
+        return a.ctypes.data, a.nbytes
+    if not a.is_contiguous() or a.is_cuda:
+        raise ValueError("host buffer must be a contiguous CPU tensor")
+    return a.data_ptr(), a.numel() * a.element_size()
 
 
 def declared_symbols(header: str = HEADER) -> list[str]:
@@ -280,9 +303,12 @@ class Model:
                                      _stream(stream)))
 
     def eval_all_host(self, x, lam=None, sigma=1.0, obj=None, grad=None, c=None, jv=None, hv=None,
-                      stream=None):
-        """Host arrays (numpy or CPU tensors, float64, contiguous; pinned
-        memory gives asynchronous copies) in and out; synchronises."""
+                      stream=None, pipelined=False):
+        """Host arrays (numpy or CPU tensors, float64, contiguous; memory
+        page-locked with host_register copies at full speed) in and out.
+        Synchronises, unless `pipelined`: then the call returns at once, its
+        copies and evaluation overlap those of the next call, and the host
+        outputs are complete when `stream` has been synchronised."""
         def hp(a, n, name):
             if a is None:
                 return None
@@ -293,10 +319,10 @@ class Model:
             if a.dtype != np.float64 or not a.flags.c_contiguous or a.size < n:
                 raise TypeError(f"{name}: contiguous float64 array of {n} entries expected")
             return a.ctypes.data
-        _check(lib().opf_eval_all_host(self.h, hp(x, self.n, "x"), hp(lam, self.m, "lambda"),
-                                       float(sigma), hp(obj, 1, "obj"), hp(grad, self.n, "grad"),
-                                       hp(c, self.m, "c"), hp(jv, self.nnzj, "jvals"),
-                                       hp(hv, self.nnzh, "hvals"), _stream(stream)))
+        fn = lib().opf_eval_all_host_async if pipelined else lib().opf_eval_all_host
+        _check(fn(self.h, hp(x, self.n, "x"), hp(lam, self.m, "lambda"), float(sigma), hp(obj, 1, "obj"),
+                  hp(grad, self.n, "grad"), hp(c, self.m, "c"), hp(jv, self.nnzj, "jvals"),
+                  hp(hv, self.nnzh, "hvals"), _stream(stream)))
 
     def flat_start(self, x, stream=None):
         _check(lib().opf_flat_start(self.h, _ptr(x, self.n, "x"), _stream(stream)))

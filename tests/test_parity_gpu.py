@@ -401,3 +401,51 @@ def test_set_loads_matches_fresh_model(torch, oracle_mod):
     b = run_all(torch, M2, x, lam, 1.0)
     for k in a:
         np.testing.assert_array_equal(a[k], b[k])
+
+
+def test_host_registered_buffers(torch, oracle_mod):
+    """opf_eval_all_host with host buffers page-locked by the library gives
+    the same bits as the device path."""
+    g = synth.case30(general=True)
+    M, O = both(torch, oracle_mod, g)
+    x, lam = next(points(g, M.m, 1, seed=21))
+    outs = dict(obj=np.empty(1), grad=np.empty(M.n), c=np.empty(M.m), jv=np.empty(M.nnzj),
+                hv=np.empty(M.nnzh))
+    hx, hl = x.copy(), lam.copy()
+    for a in [hx, hl] + list(outs.values()):
+        opf.host_register(a)
+    try:
+        M.eval_all_host(hx, hl, 1.0, **outs)
+    finally:
+        for a in [hx, hl] + list(outs.values()):
+            opf.host_unregister(a)
+    ref = run_all(torch, M, x, lam, 1.0)
+    for k, v in outs.items():
+        np.testing.assert_array_equal(v, ref[k])
+
+
+def test_pipelined_host_calls(torch, oracle_mod):
+    """Three pipelined host-buffer calls in a row (copies of one overlapping
+    the evaluation of the next) give, after one synchronisation, the same
+    bits as the device path for each call."""
+    g = synth.case30(general=True)
+    M, O = both(torch, oracle_mod, g)
+    pts = list(points(g, M.m, 3, seed=22))
+    outs = [dict(obj=np.empty(1), grad=np.empty(M.n), c=np.empty(M.m), jv=np.empty(M.nnzj),
+                 hv=np.empty(M.nnzh)) for _ in pts]
+    ins = [(x.copy(), lam.copy()) for x, lam in pts]
+    bufs = [a for o in outs for a in o.values()] + [a for p in ins for a in p]
+    for a in bufs:
+        opf.host_register(a)
+    stream = torch.cuda.Stream()
+    try:
+        for (hx, hl), o in zip(ins, outs):
+            M.eval_all_host(hx, hl, 1.0, **o, stream=stream, pipelined=True)
+        stream.synchronize()
+    finally:
+        for a in bufs:
+            opf.host_unregister(a)
+    for (x, lam), o in zip(pts, outs):
+        ref = run_all(torch, M, x, lam, 1.0)
+        for k, v in o.items():
+            np.testing.assert_array_equal(v, ref[k])
