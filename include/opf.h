@@ -263,13 +263,14 @@ int opf_autotune(opf_model *model, const double *d_x, const double *d_lambda, in
  * calls: inputs are copied in on an internal stream into one of two staging
  * slots, the evaluation runs on a second internal stream and the outputs
  * are copied out on a third, so the copies of one call overlap the
- * evaluation and copies of the next. `stream` (the caller's) orders the
- * call after the caller's earlier work on it and is made to wait for the
- * call's outputs: the host buffers are complete (and the inputs may be
- * reused) once `stream` has been synchronised. Host buffers should be
- * page-locked (opf_host_register). Calls on one model must come from one
- * thread; allocates its staging and streams on first use (freed with the
- * model). */
+ * evaluation and copies of the next. The call starts at once (the host
+ * inputs must be ready; it does not wait for earlier work on `stream`);
+ * `stream` (the caller's) is made to wait for the call's outputs: the host
+ * outputs are complete, and the inputs may be reused, once `stream` has
+ * been synchronised. Host buffers should be page-locked
+ * (opf_host_register). Calls on one model must come from one thread and
+ * must not overlap evaluations of the same model on other streams;
+ * allocates its staging and streams on first use (freed with the model). */
 int opf_eval_all_host_async(opf_model *model, const double *h_x, const double *h_lambda,
                             double obj_weight, double *h_obj, double *h_grad, double *h_c,
                             double *h_jvals, double *h_hvals, void *stream);

@@ -354,10 +354,10 @@ int opf_eval_all_host_async(opf_model *m, const double *h_x, const double *h_lam
     double *dx = M.astage[k], *dl = dx + M.n, *dobj = dl + M.m, *dg = dobj + 1, *dc = dg + M.n;
     double *dj = dc + M.m, *dh = dj + M.nnzj;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    // copy-in after the caller's earlier work and after the compute that last read this slot
-    cudaError_t e = cudaEventRecord(M.ev_entry, s);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(M.s_in, M.ev_entry, 0);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(M.s_in, M.ev_cmp[k], 0);
+    // copy-in after the compute that last read this slot (not after the
+    // caller's stream: it waits for the previous call's outputs, and
+    // ordering on it would serialise the pipeline)
+    cudaError_t e = cudaStreamWaitEvent(M.s_in, M.ev_cmp[k], 0);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dx, h_x, sizeof(double) * M.n, cudaMemcpyHostToDevice, M.s_in);
     if (e == cudaSuccess && h_hvals)
         e = cudaMemcpyAsync(dl, h_lambda, sizeof(double) * M.m, cudaMemcpyHostToDevice, M.s_in);
