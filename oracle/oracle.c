@@ -23,10 +23,11 @@
  *     (Sec. III-C-2, Listing 6, corrective_action_ratio), 2-D layout of Listing 10
  *   - constraint violation Cvio (Sec. IV-A)
  *
- * Readings where the paper is silent (flow row = variable minus function,
- * thermal p^2+q^2-rate^2, demand Pd + gs vm^2 / Qd - bs vm^2, arc numbering,
- * Hessian as deduplicated lower triangle in (row, col) order) are listed in
- * the design notes of the repository.
+ * Where the paper is silent this oracle takes these readings: a flow row is
+ * the arc variable minus the flow function; the thermal row is
+ * p^2 + q^2 - rate_a^2 <= 0; the demand terms are Pd + gs vm^2 and
+ * Qd - bs vm^2; arc k is the from-end of branch k and arc nl + k its to-end;
+ * the Hessian is the deduplicated lower triangle in (row, col) order.
  *
  * Every value is computed in complex arithmetic on the pi-model; derivatives
  * are derived by hand in complex form (d/dva V = j V, d/dvm V = V/vm). The

@@ -23,7 +23,7 @@
 // (cudaGridDependencySynchronize), then reads x, lambda and the scratch. The
 // static prologue and the launch therefore overlap the previous kernel.
 //
-// FP64 is the scarce resource on this GPU (about 2 FMA per clock per SM), so
+// FP64 is the scarce resource on the B300 (about 2 FMA per clock per SM), so
 // sign flips and selects are done on the integer pipe and every product
 // shared between rows is computed once.
 //

@@ -176,7 +176,7 @@ def test_full_size_gain_judged_by_oracle(torch, oracle_mod):
     of 4,096; on 32 held-out profiles the FP64 oracle's max violation
     (constraints and bounds) of the predicted point is at least 9x below
     the flat start's at the median and 4x below it on every profile (the
-    penalised loss's own optimum sits near 10x, see the design notes)."""
+    penalised loss's own minimiser, solved per profile on the CPU, sits near 10x)."""
     from paper_2510_12897_b300 import warm
     g = synth.case2k_secure()
     N, B = 100_000, 4096
