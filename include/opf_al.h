@@ -49,9 +49,11 @@ int opf_al_destroy(opf_al *al);
 
 /* `iters` inner iterations on d_x (n, device, updated in place, projected
  * onto [xl, xu] after every step) at fixed d_lambda (m, device). d_stats
- * (device, 3 doubles, may be NULL) receives, at the point the last
- * iteration started from: f(x), the largest row violation
- * max_i max(gl_i - g_i, g_i - gu_i, 0), and L(x; lambda). */
+ * (device, 3 doubles, may be NULL) receives, at the final point: f(x), the
+ * largest row violation max_i max(gl_i - g_i, g_i - gu_i, 0), and
+ * L(x; lambda). One iteration is captured once per (d_x, d_lambda) pair as
+ * a CUDA graph and replayed (the step count's bias corrections live on the
+ * device); opf_al_reset drops the captured graphs. */
 int opf_al_iterate(opf_al *al, double *d_x, const double *d_lambda, int32_t iters, double *d_stats,
                    void *stream);
 

@@ -51,17 +51,16 @@ class AugLagOracle:
         return np.array([f, viol, f + float(np.sum(mu * mu) - np.sum(lam * lam)) / (2.0 * self.rho)])
 
     def iterate(self, x, lam, iters):
+        """`iters` Adam steps; returns the final x and its statistics."""
         x = np.array(x, dtype=np.float64, copy=True)
-        last = None
         for _ in range(iters):
-            last = self.stats(x, lam)
             G = self.gradient(x, lam)
             self.k += 1
             self.m1 = 0.9 * self.m1 + 0.1 * G
             self.m2 = 0.999 * self.m2 + 0.001 * G * G
             step = self.lr * (self.m1 / (1 - 0.9 ** self.k)) / (np.sqrt(self.m2 / (1 - 0.999 ** self.k)) + 1e-8)
             x = np.clip(x - step, self.xl, self.xu)
-        return x, last
+        return x, self.stats(x, lam)
 
     def update(self, x, lam):
         mu, _ = self.mu(x, lam)

@@ -23,6 +23,15 @@ struct opf_al {
     double *xl = nullptr, *xu = nullptr, *gl = nullptr, *gu = nullptr;
     double *grad = nullptr, *c = nullptr, *mu = nullptr, *u = nullptr, *m1 = nullptr, *m2 = nullptr;
     double *obj = nullptr, *part = nullptr;  // part: [3][nparts] block partials
+    double *bpow = nullptr;  // device: beta1^k, beta2^k, 1 - beta1^k, 1 - beta2^k
+    // one inner iteration captured as a CUDA graph per (x, lambda) pair: the
+    // loop replays it instead of launching its seven kernels one by one
+    cudaStream_t cap = nullptr;
+    struct Graph {
+        const double *x, *lam;
+        cudaGraphExec_t exec;
+    };
+    std::vector<Graph> graphs;
 };
 
 namespace {
@@ -50,10 +59,22 @@ int al_alloc(opf_al *a, T **p, size_t count)
     return OPF_OK;
 }
 
+void al_drop_graphs(opf_al *a)
+{
+    for (auto &g : a->graphs)
+        cudaGraphExecDestroy(g.exec);
+    a->graphs.clear();
+}
+
 void al_free(opf_al *a)
 {
     if (!a)
         return;
+    al_drop_graphs(a);
+    if (a->cap) {
+        cudaStreamSynchronize(a->cap);
+        cudaStreamDestroy(a->cap);
+    }
     for (void *p : a->allocs)
         cudaFree(p);
     delete a;
@@ -138,11 +159,21 @@ __global__ void al_stats_kernel(const double *obj, const double *part, int npart
     }
 }
 
+// the step count's bias corrections, kept on the device (one thread)
+__global__ void al_step_kernel(double *bp)
+{
+    bp[0] *= 0.9;
+    bp[1] *= 0.999;
+    bp[2] = 1.0 - bp[0];
+    bp[3] = 1.0 - bp[1];
+}
+
 // Adam step on G = grad + u, then projection onto [xl, xu]
 __global__ void al_adam_kernel(double *x, const double *grad, const double *u, const double *xl, const double *xu,
-                               double *m1, double *m2, int64_t n, double lr, double bc1, double bc2)
+                               double *m1, double *m2, int64_t n, double lr, const double *bp)
 {
     const double b1 = 0.9, b2 = 0.999, eps = 1e-8;
+    const double bc1 = bp[2], bc2 = bp[3];
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
          j += (int64_t)gridDim.x * blockDim.x) {
         const double G = grad[j] + u[j];
@@ -218,6 +249,13 @@ int opf_al_create(opf_model *model, const opf_al_opts *opts, opf_al **out)
     if (!rc) rc = al_alloc(a, &a->m2, a->n);
     if (!rc) rc = al_alloc(a, &a->obj, 1);
     if (!rc) rc = al_alloc(a, &a->part, 3 * (size_t)a->nparts);
+    if (!rc) rc = al_alloc(a, &a->bpow, 4);
+    if (!rc) {
+        const double init[4] = {1.0, 1.0, 0.0, 0.0};
+        rc = al_check(cudaMemcpy(a->bpow, init, sizeof(init), cudaMemcpyHostToDevice), "step state");
+    }
+    if (!rc)
+        rc = al_check(cudaStreamCreateWithFlags(&a->cap, cudaStreamNonBlocking), "capture stream");
     if (!rc)
         rc = al_check(cudaMemcpy(a->xl, xl.data(), sizeof(double) * a->n, cudaMemcpyHostToDevice), "upload bounds");
     if (!rc)
@@ -250,14 +288,67 @@ int opf_al_reset(opf_al *al, double rho, double lr)
         set_error("opf_al_reset: need a loop and finite rho > 0, lr > 0");
         return OPF_EINVAL;
     }
+    cudaDeviceSynchronize();  // no replay of the old graphs may still run
+    al_drop_graphs(al);       // they hold rho and lr
     al->rho = rho;
     al->lr = lr;
     al->step = 0;
+    const double init[4] = {1.0, 1.0, 0.0, 0.0};
     int rc = al_check(cudaMemset(al->m1, 0, sizeof(double) * al->n), "clear moments");
     if (!rc)
         rc = al_check(cudaMemset(al->m2, 0, sizeof(double) * al->n), "clear moments");
+    if (!rc)
+        rc = al_check(cudaMemcpy(al->bpow, init, sizeof(init), cudaMemcpyHostToDevice), "step state");
     return rc;
 }
+
+namespace {
+
+// one inner iteration on stream s: f, grad f, g, mu; J^T mu; step; Adam
+int al_inner(opf_al *al, double *d_x, const double *d_lambda, cudaStream_t s)
+{
+    int rc = al_point(al, d_x, d_lambda, true, nullptr, s);
+    if (!rc)
+        rc = launch_jtprod(*al->M, d_x, al->mu, al->u, s);
+    if (rc)
+        return rc;
+    al_step_kernel<<<1, 1, 0, s>>>(al->bpow);
+    al_adam_kernel<<<grid_of(al->n), 256, 0, s>>>(d_x, al->grad, al->u, al->xl, al->xu, al->m1, al->m2, al->n,
+                                                  al->lr, al->bpow);
+    return al_check(cudaGetLastError(), "Adam step");
+}
+
+// the captured iteration for (x, lambda), built on first use
+int al_graph(opf_al *al, double *d_x, const double *d_lambda, cudaGraphExec_t *out)
+{
+    for (auto &g : al->graphs)
+        if (g.x == d_x && g.lam == d_lambda) {
+            *out = g.exec;
+            return OPF_OK;
+        }
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int rc = al_check(cudaStreamBeginCapture(al->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+    if (rc)
+        return rc;
+    const int rc_inner = al_inner(al, d_x, d_lambda, al->cap);
+    cudaError_t e = cudaStreamEndCapture(al->cap, &graph);
+    if (rc_inner)
+        rc = rc_inner;
+    else if (e == cudaSuccess)
+        rc = al_check(cudaGraphInstantiate(&exec, graph, 0), "graph instantiate");
+    else
+        rc = al_check(e, "end capture");
+    if (graph)
+        cudaGraphDestroy(graph);
+    if (rc)
+        return rc;
+    al->graphs.push_back({d_x, d_lambda, exec});
+    *out = exec;
+    return OPF_OK;
+}
+
+}  // namespace
 
 int opf_al_iterate(opf_al *al, double *d_x, const double *d_lambda, int32_t iters, double *d_stats, void *stream)
 {
@@ -266,22 +357,14 @@ int opf_al_iterate(opf_al *al, double *d_x, const double *d_lambda, int32_t iter
         return OPF_EINVAL;
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    for (int it = 0; it < iters; it++) {
-        int rc = al_point(al, d_x, d_lambda, true, it == iters - 1 ? d_stats : nullptr, s);
-        if (!rc)
-            rc = launch_jtprod(*al->M, d_x, al->mu, al->u, s);
-        if (rc)
-            return rc;
-        al->step++;
-        const double bc1 = 1.0 - std::pow(0.9, (double)al->step);
-        const double bc2 = 1.0 - std::pow(0.999, (double)al->step);
-        al_adam_kernel<<<grid_of(al->n), 256, 0, s>>>(d_x, al->grad, al->u, al->xl, al->xu, al->m1, al->m2, al->n,
-                                                      al->lr, bc1, bc2);
-        rc = al_check(cudaGetLastError(), "Adam step");
-        if (rc)
-            return rc;
-    }
-    return OPF_OK;
+    cudaGraphExec_t exec = nullptr;
+    int rc = iters > 0 ? al_graph(al, d_x, d_lambda, &exec) : OPF_OK;
+    for (int it = 0; it < iters && !rc; it++)
+        rc = al_check(cudaGraphLaunch(exec, s), "graph launch");
+    al->step += iters;
+    if (!rc && d_stats)  // statistics at the final point
+        rc = al_point(al, d_x, d_lambda, false, d_stats, s);
+    return rc;
 }
 
 int opf_al_update(opf_al *al, const double *d_x, double *d_lambda, double *d_stats, void *stream)
