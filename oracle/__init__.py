@@ -1,4 +1,4 @@
-"""FP64 CPU oracle for the polar AC-OPF callbacks (ctypes wrapper of oracle.c).
+"""FP64 CPU oracle for the AC-OPF callbacks, polar and rectangular (ctypes wrapper of oracle.c).
 
 TEST INFRASTRUCTURE ONLY. The oracle judges the CUDA library; only tests/,
 ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may import
@@ -15,6 +15,11 @@ Parity status of each function (what pins it lives in tests/test_oracle_*.py):
   patterns       nnz closed forms; every structural nonzero found by
                  differences lies in the pattern
   bounds, cvio   closed forms on hand-built cases
+  form="rect"    Newton power flow in rectangular voltages; equality with the
+                 polar model at the same point; chain rule against the polar
+                 Jacobian; trigonometric closed form of the angle rows; the
+                 exact second-order expansion of the (quadratic) Lagrangian;
+                 differences of cons and of grad + J^T lambda
 """
 from __future__ import annotations
 
@@ -74,6 +79,9 @@ def lib():
         L.ora_create.argtypes = [ctypes.POINTER(OraNet), ctypes.c_int32, ctypes.c_double]
         L.ora_create2.restype = ctypes.c_void_p
         L.ora_create2.argtypes = [ctypes.POINTER(OraNet), ctypes.c_int32, ctypes.c_double, _f64p, ctypes.c_double]
+        L.ora_create3.restype = ctypes.c_void_p
+        L.ora_create3.argtypes = [ctypes.POINTER(OraNet), ctypes.c_int32, ctypes.c_double, _f64p, ctypes.c_double,
+                                  ctypes.c_int32]
         L.ora_destroy.argtypes = [ctypes.c_void_p]
         L.ora_error.restype = ctypes.c_char_p
         L.ora_dims.argtypes = [ctypes.c_void_p, _i64p, _i64p, _i64p, _i64p]
@@ -113,10 +121,16 @@ class Oracle:
     ``link_ratio > 0`` adds rows pg_s - pg_0 in [-ratio pmax, ratio pmax]
     tying every instance s >= 1 to instance 0 (``link_ratios``: one ratio
     per instance instead); ``reserve > 0`` adds per instance and period the
-    row sum_g pg_g <= sum_g pmax_g - reserve * (total Pd).
+    row sum_g pg_g <= sum_g pmax_g - reserve * (total Pd). ``form``: "polar"
+    (va, vm) or "rect" (vr, vi, with the angle and magnitude rows of the
+    rectangular model).
     """
 
-    def __init__(self, grids, link_ratio: float = 0.0, link_ratios=None, reserve: float = 0.0):
+    def __init__(self, grids, link_ratio: float = 0.0, link_ratios=None, reserve: float = 0.0,
+                 form: str = "polar"):
+        if form not in ("polar", "rect"):
+            raise ValueError("form must be 'polar' or 'rect'")
+        self.form = form
         if not isinstance(grids, (list, tuple)):
             grids = [grids]
         self.grids = list(grids)
@@ -129,8 +143,9 @@ class Oracle:
         if link_ratios is not None:
             lr = np.ascontiguousarray(link_ratios, dtype=np.float64)
             self._keep.append(lr)
-        self.ctx = lib().ora_create2(nets, len(grids), float(link_ratio),
-                                     None if lr is None else lr.ctypes.data_as(_f64p), float(reserve))
+        self.ctx = lib().ora_create3(nets, len(grids), float(link_ratio),
+                                     None if lr is None else lr.ctypes.data_as(_f64p), float(reserve),
+                                     1 if form == "rect" else 0)
         if not self.ctx:
             raise ValueError("oracle: " + lib().ora_error().decode())
         n, m, nj, nh = (ctypes.c_int64() for _ in range(4))

@@ -22,6 +22,15 @@
  *   - multi-period: per-period demand, ramp rows |pg_t - pg_{t-1}| <= ratio pmax
  *     (Sec. III-C-2, Listing 6, corrective_action_ratio), 2-D layout of Listing 10
  *   - constraint violation Cvio (Sec. IV-A)
+ *   - the rectangular form (form = :rect of Sec. III-C-1, whose equations the
+ *     paper leaves to the rectangular AC model of PowerModels): variables
+ *     vr, vi in the places of va, vm with bounds -vmax <= vr, vi <= vmax; the
+ *     same pi-model flows with V = vr + j vi; the reference row vi_ref = 0;
+ *     the angle-difference limits as two rows Im(w) - tan(angmax) Re(w) <= 0
+ *     (in the angle group's place) and Im(w) - tan(angmin) Re(w) >= 0 (after
+ *     the thermal rows), w = V_f conj(V_t), valid for limits inside
+ *     (-pi/2, pi/2); a voltage-magnitude row vmin^2 <= vr^2 + vi^2 <= vmax^2
+ *     per bus (after those); demand terms gs |V|^2 and -bs |V|^2.
  *
  * Where the paper is silent this oracle takes these readings: a flow row is
  * the arc variable minus the flow function; the thermal row is
@@ -30,7 +39,8 @@
  * the Hessian is the deduplicated lower triangle in (row, col) order.
  *
  * Every value is computed in complex arithmetic on the pi-model; derivatives
- * are derived by hand in complex form (d/dva V = j V, d/dvm V = V/vm). The
+ * are derived by hand in complex form (polar: d/dva V = j V, d/dvm V = V/vm;
+ * rectangular: d/dvr V = 1, d/dvi V = j). The
  * sparsity pattern is built from the term structure alone, then every term's
  * contribution is added into its entry found by binary search. No blocking,
  * no fusion, one thread.
@@ -58,7 +68,8 @@ static void set_err(const char *fmt, ...)
 
 const char *ora_error(void) { return g_err; }
 
-enum { G_REF, G_FPF, G_FQF, G_FPT, G_FQT, G_ANG, G_PB, G_QB, G_THF, G_THT, G_RAMP };
+/* row groups; G_ANL and G_VM exist in the rectangular form only */
+enum { G_REF, G_FPF, G_FQF, G_FPT, G_FQT, G_ANG, G_PB, G_QB, G_THF, G_THT, G_ANL, G_VM, G_RAMP };
 
 typedef struct {
     ora_net net;     /* pointers into the owned copies below */
@@ -67,11 +78,13 @@ typedef struct {
     int64_t xoff, coff;  /* first variable / first row of this instance */
     int64_t n, m;
     int ramp;
+    int rect;            /* rectangular voltages: vr, vi in the places of va, vm */
     double *Pd, *Qd;     /* per bus and period: [nperiod][nbus] */
 } inst_t;
 
 struct ora_ctx {
     int ninst;
+    int rect;
     inst_t *in;
     double link_ratio;
     double *link_ratios; /* per instance (entry 0 unused) */
@@ -120,9 +133,9 @@ static int64_t v_q(const inst_t *s, int64_t a, int64_t t)
 static int64_t row_of(const inst_t *s, int grp, int64_t e, int64_t t)
 {
     int64_t T = s->net.nperiod, nl = s->net.nbranch, nb = s->net.nbus;
-    int64_t size[10] = {1, nl, nl, nl, nl, nl, nb, nb, nl, nl};
+    int64_t size[12] = {1, nl, nl, nl, nl, nl, nb, nb, nl, nl, s->rect ? nl : 0, s->rect ? nb : 0};
     int64_t base = 0;
-    for (int k = 0; k < grp && k < 10; k++)
+    for (int k = 0; k < grp && k < 12; k++)
         base += size[k] * T;
     if (grp == G_RAMP)
         return s->coff + base + e + (int64_t)s->net.ngen * (t - 1);
@@ -187,6 +200,76 @@ static void branch_end(double vmi, double vmj, double vai, double vaj, cplx Yii,
         }
 }
 
+/* One end of a branch in rectangular voltages, V = vr + j vi:
+ * S_i = V_i conj(Y_ii V_i + Y_ij V_j), local order u = (vr_i, vr_j, vi_i, vi_j),
+ * dV/dvr = 1 and dV/dvi = j, so that, with I_i = Y_ii V_i + Y_ij V_j,
+ *   dS/dvr_i = conj(I_i) + V_i conj(Y_ii),  dS/dvi_i = j conj(I_i) - j V_i conj(Y_ii),
+ *   dS/dvr_j = V_i conj(Y_ij),              dS/dvi_j = -j V_i conj(Y_ij),
+ * and the second derivatives are constants: 2 conj(Y_ii) on (vr_i, vr_i) and
+ * (vi_i, vi_i), conj(Y_ij) on (vr_i, vr_j) and (vi_i, vi_j), -j conj(Y_ij) on
+ * (vr_i, vi_j), j conj(Y_ij) on (vi_i, vr_j), zero elsewhere. */
+static void branch_end_rect(double vri, double vrj, double vii, double vij, cplx Yii, cplx Yij,
+                            bend_t *e)
+{
+    cplx Vi = vri + I * vii, Vj = vrj + I * vij;
+    cplx Ii = Yii * Vi + Yij * Vj;
+    double ai = cabs(Yii), aj = cabs(Yij), mi = cabs(Vi), mj = cabs(Vj);
+
+    e->S = Vi * conj(Ii);
+    e->bS = ai * mi * mi + aj * mi * mj;
+
+    e->dS[0] = conj(Ii) + Vi * conj(Yii);
+    e->dS[1] = Vi * conj(Yij);
+    e->dS[2] = I * conj(Ii) - I * Vi * conj(Yii);
+    e->dS[3] = -I * Vi * conj(Yij);
+    e->bdS[0] = e->bdS[2] = 2.0 * ai * mi + aj * mj;
+    e->bdS[1] = e->bdS[3] = aj * mi;
+
+    for (int a = 0; a < 4; a++)
+        for (int b = 0; b < 4; b++) {
+            e->d2S[a][b] = 0.0;
+            e->bd2S[a][b] = 0.0;
+        }
+    e->d2S[0][0] = e->d2S[2][2] = 2.0 * conj(Yii);
+    e->bd2S[0][0] = e->bd2S[2][2] = 2.0 * ai;
+    e->d2S[0][1] = e->d2S[1][0] = conj(Yij);
+    e->d2S[2][3] = e->d2S[3][2] = conj(Yij);
+    e->d2S[0][3] = e->d2S[3][0] = -I * conj(Yij);
+    e->d2S[1][2] = e->d2S[2][1] = I * conj(Yij);
+    e->bd2S[0][1] = e->bd2S[1][0] = e->bd2S[2][3] = e->bd2S[3][2] = aj;
+    e->bd2S[0][3] = e->bd2S[3][0] = e->bd2S[1][2] = e->bd2S[2][1] = aj;
+}
+
+/* the (a, b), a <= b, of a rectangular branch end's local order whose second
+ * derivative is structurally nonzero (the others are identically zero) */
+static const int RECT_D2[6][2] = {{0, 0}, {2, 2}, {0, 1}, {0, 3}, {1, 2}, {2, 3}};
+
+/* Angle-difference row of the rectangular form, Im((1 - j tau) w) with
+ * w = V_f conj(V_t) (= Im w - tau Re w), in the from-end's local order
+ * (vr_f, vr_t, vi_f, vi_t): dw = (conj(V_t), V_f, j conj(V_t), -j V_f), and
+ * d2w is 1 on (vr_f, vr_t) and (vi_f, vi_t), -j on (vr_f, vi_t), j on
+ * (vi_f, vr_t). bnd bounds |value|; dbnd the derivatives' moduli. */
+static void angle_rect(double vrf, double vrt, double vif, double vit, double tau, double *val,
+                       double d[4], double d2[4][4], double *bnd, double dbnd[4])
+{
+    cplx Vf = vrf + I * vif, Vt = vrt + I * vit;
+    cplx w = Vf * conj(Vt), k = 1.0 - I * tau;
+    cplx dw[4] = {conj(Vt), Vf, I * conj(Vt), -I * Vf};
+    double ak = cabs(k);
+    *val = cimag(k * w);
+    *bnd = ak * cabs(w);
+    for (int a = 0; a < 4; a++) {
+        d[a] = cimag(k * dw[a]);
+        dbnd[a] = ak * cabs(dw[a]);
+        for (int b = 0; b < 4; b++)
+            d2[a][b] = 0.0;
+    }
+    d2[0][1] = d2[1][0] = cimag(k);
+    d2[2][3] = d2[3][2] = cimag(k);
+    d2[0][3] = d2[3][0] = cimag(-I * k);
+    d2[1][2] = d2[2][1] = cimag(I * k);
+}
+
 /* the four admittances of branch k */
 static void branch_Y(const ora_net *n, int k, cplx *Yff, cplx *Yft, cplx *Ytf, cplx *Ytt)
 {
@@ -212,14 +295,25 @@ static void ends_of(const inst_t *s, const double *x, int k, int t, end_t *fr, e
     int f = n->f[k], b = n->t[k];
     cplx Yff, Yft, Ytf, Ytt;
     branch_Y(n, k, &Yff, &Yft, &Ytf, &Ytt);
-    double vmf = x[v_vm(s, f, t)], vmt = x[v_vm(s, b, t)];
-    double vaf = x[v_va(s, f, t)], vat = x[v_va(s, b, t)];
-    branch_end(vmf, vmt, vaf, vat, Yff, Yft, &fr->e);
-    branch_end(vmt, vmf, vat, vaf, Ytt, Ytf, &to->e);
-    fr->u[0] = v_vm(s, f, t); fr->u[1] = v_vm(s, b, t);
-    fr->u[2] = v_va(s, f, t); fr->u[3] = v_va(s, b, t);
-    to->u[0] = v_vm(s, b, t); to->u[1] = v_vm(s, f, t);
-    to->u[2] = v_va(s, b, t); to->u[3] = v_va(s, f, t);
+    if (s->rect) { /* first block vr, second vi; u = (vr_i, vr_j, vi_i, vi_j) */
+        double vrf = x[v_va(s, f, t)], vrt = x[v_va(s, b, t)];
+        double vif = x[v_vm(s, f, t)], vit = x[v_vm(s, b, t)];
+        branch_end_rect(vrf, vrt, vif, vit, Yff, Yft, &fr->e);
+        branch_end_rect(vrt, vrf, vit, vif, Ytt, Ytf, &to->e);
+        fr->u[0] = v_va(s, f, t); fr->u[1] = v_va(s, b, t);
+        fr->u[2] = v_vm(s, f, t); fr->u[3] = v_vm(s, b, t);
+        to->u[0] = v_va(s, b, t); to->u[1] = v_va(s, f, t);
+        to->u[2] = v_vm(s, b, t); to->u[3] = v_vm(s, f, t);
+    } else {
+        double vmf = x[v_vm(s, f, t)], vmt = x[v_vm(s, b, t)];
+        double vaf = x[v_va(s, f, t)], vat = x[v_va(s, b, t)];
+        branch_end(vmf, vmt, vaf, vat, Yff, Yft, &fr->e);
+        branch_end(vmt, vmf, vat, vaf, Ytt, Ytf, &to->e);
+        fr->u[0] = v_vm(s, f, t); fr->u[1] = v_vm(s, b, t);
+        fr->u[2] = v_va(s, f, t); fr->u[3] = v_va(s, b, t);
+        to->u[0] = v_vm(s, b, t); to->u[1] = v_vm(s, f, t);
+        to->u[2] = v_va(s, b, t); to->u[3] = v_va(s, f, t);
+    }
     fr->pvar = v_p(s, k, t); fr->qvar = v_q(s, k, t);
     to->pvar = v_p(s, n->nbranch + k, t); to->qvar = v_q(s, n->nbranch + k, t);
 }
@@ -340,6 +434,16 @@ ora_ctx *ora_create(const ora_net *nets, int32_t ninst, double link_ratio)
 ora_ctx *ora_create2(const ora_net *nets, int32_t ninst, double link_ratio, const double *link_ratios,
                      double reserve)
 {
+    return ora_create3(nets, ninst, link_ratio, link_ratios, reserve, 0);
+}
+
+ora_ctx *ora_create3(const ora_net *nets, int32_t ninst, double link_ratio, const double *link_ratios,
+                     double reserve, int32_t form)
+{
+    if (form != 0 && form != 1) {
+        set_err("form must be 0 (polar) or 1 (rectangular)");
+        return NULL;
+    }
     if (ninst < 1) {
         set_err("ninst < 1");
         return NULL;
@@ -351,8 +455,16 @@ ora_ctx *ora_create2(const ora_net *nets, int32_t ninst, double link_ratio, cons
     for (int s = 0; s < ninst; s++)
         if (validate(&nets[s]))
             return NULL;
+    if (form == 1) /* the tangent form of the angle rows needs |limit| < pi/2 */
+        for (int s = 0; s < ninst; s++)
+            for (int k = 0; k < nets[s].nbranch; k++)
+                if (!(fabs(nets[s].angmin[k]) < M_PI / 2) || !(fabs(nets[s].angmax[k]) < M_PI / 2)) {
+                    set_err("rectangular form: branch %d angle limits outside (-pi/2, pi/2)", k);
+                    return NULL;
+                }
     ora_ctx *C = calloc(1, sizeof *C);
     C->ninst = ninst;
+    C->rect = form == 1;
     C->in = calloc((size_t)ninst, sizeof(inst_t));
     C->link_ratio = link_ratio;
     C->link_ratios = malloc(sizeof(double) * (size_t)ninst);
@@ -408,8 +520,11 @@ ora_ctx *ora_create2(const ora_net *nets, int32_t ninst, double link_ratio, cons
                 S->Qd[t * nb + d->load_bus[l]] += d->qd[t * nlo + l];
             }
         S->ramp = T > 1 && n->ramp_ratio > 0.0;
+        S->rect = C->rect;
         S->n = T * (2 * nb + 2 * ng + 4 * nl);
         S->m = T * (1 + 7 * nl + 2 * nb) + (S->ramp ? ng * (T - 1) : 0);
+        if (S->rect) /* the lower angle rows and the voltage-magnitude rows */
+            S->m += T * (nl + nb);
         S->xoff = xo;
         S->coff = co;
         xo += S->n;
@@ -428,7 +543,7 @@ ora_ctx *ora_create2(const ora_net *nets, int32_t ninst, double link_ratio, cons
     for (int s = 0; s < ninst; s++) {
         const ora_net *n = &C->in[s].net;
         int64_t T = n->nperiod;
-        cap += T * (1 + 30 * (int64_t)n->nbranch + 2 * (int64_t)n->nbus + 2 * (int64_t)n->ngen) +
+        cap += T * (1 + 40 * (int64_t)n->nbranch + 6 * (int64_t)n->nbus + 2 * (int64_t)n->ngen) +
                2 * (int64_t)n->ngen * T;
     }
     cap += C->link ? 2 * (int64_t)nets[0].ngen * ninst : 0;
@@ -442,7 +557,9 @@ ora_ctx *ora_create2(const ora_net *nets, int32_t ninst, double link_ratio, cons
         const ora_net *n = &S->net;
         int64_t nl = n->nbranch;
         for (int t = 0; t < n->nperiod; t++) {
-            push(keys, &cnt, N, row_of(S, G_REF, 0, t), v_va(S, n->ref_bus, t));
+            /* polar: va_ref; rectangular: vi_ref */
+            push(keys, &cnt, N, row_of(S, G_REF, 0, t),
+                 S->rect ? v_vm(S, n->ref_bus, t) : v_va(S, n->ref_bus, t));
             for (int k = 0; k < nl; k++) {
                 int f = n->f[k], b = n->t[k];
                 int64_t dep[4] = {v_vm(S, f, t), v_vm(S, b, t), v_va(S, f, t), v_va(S, b, t)};
@@ -454,8 +571,15 @@ ora_ctx *ora_create2(const ora_net *nets, int32_t ninst, double link_ratio, cons
                     for (int d = 0; d < 4; d++)
                         push(keys, &cnt, N, row, dep[d]);
                 }
-                push(keys, &cnt, N, row_of(S, G_ANG, k, t), v_va(S, f, t));
-                push(keys, &cnt, N, row_of(S, G_ANG, k, t), v_va(S, b, t));
+                if (S->rect) /* both angle rows depend on all four voltages */
+                    for (int d = 0; d < 4; d++) {
+                        push(keys, &cnt, N, row_of(S, G_ANG, k, t), dep[d]);
+                        push(keys, &cnt, N, row_of(S, G_ANL, k, t), dep[d]);
+                    }
+                else {
+                    push(keys, &cnt, N, row_of(S, G_ANG, k, t), v_va(S, f, t));
+                    push(keys, &cnt, N, row_of(S, G_ANG, k, t), v_va(S, b, t));
+                }
                 push(keys, &cnt, N, row_of(S, G_THF, k, t), v_p(S, k, t));
                 push(keys, &cnt, N, row_of(S, G_THF, k, t), v_q(S, k, t));
                 push(keys, &cnt, N, row_of(S, G_THT, k, t), v_p(S, nl + k, t));
@@ -464,6 +588,12 @@ ora_ctx *ora_create2(const ora_net *nets, int32_t ninst, double link_ratio, cons
             for (int i = 0; i < n->nbus; i++) {
                 push(keys, &cnt, N, row_of(S, G_PB, i, t), v_vm(S, i, t));
                 push(keys, &cnt, N, row_of(S, G_QB, i, t), v_vm(S, i, t));
+                if (S->rect) { /* |V|^2 depends on vr too; the magnitude row */
+                    push(keys, &cnt, N, row_of(S, G_PB, i, t), v_va(S, i, t));
+                    push(keys, &cnt, N, row_of(S, G_QB, i, t), v_va(S, i, t));
+                    push(keys, &cnt, N, row_of(S, G_VM, i, t), v_va(S, i, t));
+                    push(keys, &cnt, N, row_of(S, G_VM, i, t), v_vm(S, i, t));
+                }
             }
             for (int64_t a = 0; a < 2 * nl; a++) {
                 int i = arc_bus(S, a);
@@ -510,7 +640,10 @@ ora_ctx *ora_create2(const ora_net *nets, int32_t ninst, double link_ratio, cons
     cap = 0;
     for (int s = 0; s < ninst; s++) {
         const ora_net *n = &C->in[s].net;
-        cap += (int64_t)n->nperiod * (10 * (int64_t)n->nbranch + n->nbus + n->ngen + 4 * (int64_t)n->nbranch);
+        /* per branch: 10 (polar) or 12 (rectangular, 6 per end) voltage pairs
+         * and 4 thermal diagonals; 2 per bus; 1 per generator */
+        cap += (int64_t)n->nperiod * (12 * (int64_t)n->nbranch + 2 * (int64_t)n->nbus + n->ngen +
+                                      4 * (int64_t)n->nbranch);
     }
     keys = malloc(sizeof(int64_t) * (cap + 1));
     cnt = 0;
@@ -520,6 +653,18 @@ ora_ctx *ora_create2(const ora_net *nets, int32_t ninst, double link_ratio, cons
         int64_t nl = n->nbranch;
         for (int t = 0; t < n->nperiod; t++) {
             for (int k = 0; k < nl; k++) {
+                if (S->rect) { /* each end's structurally nonzero second derivatives;
+                                  the angle rows' are a subset of the from-end's */
+                    int f = n->f[k], b = n->t[k];
+                    int64_t ue[2][4] = {{v_va(S, f, t), v_va(S, b, t), v_vm(S, f, t), v_vm(S, b, t)},
+                                        {v_va(S, b, t), v_va(S, f, t), v_vm(S, b, t), v_vm(S, f, t)}};
+                    for (int side = 0; side < 2; side++)
+                        for (int q = 0; q < 6; q++) {
+                            int64_t ua = ue[side][RECT_D2[q][0]], ub = ue[side][RECT_D2[q][1]];
+                            push(keys, &cnt, N, ua > ub ? ua : ub, ua > ub ? ub : ua);
+                        }
+                    continue;
+                }
                 int64_t u[4] = {v_vm(S, n->f[k], t), v_vm(S, n->t[k], t), v_va(S, n->f[k], t),
                                 v_va(S, n->t[k], t)};
                 for (int a = 0; a < 4; a++)
@@ -528,8 +673,11 @@ ora_ctx *ora_create2(const ora_net *nets, int32_t ninst, double link_ratio, cons
                         push(keys, &cnt, N, r, c);
                     }
             }
-            for (int i = 0; i < n->nbus; i++) /* demand term: quadratic in vm_i */
+            for (int i = 0; i < n->nbus; i++) { /* demand terms: quadratic in vm_i (|V_i|) */
                 push(keys, &cnt, N, v_vm(S, i, t), v_vm(S, i, t));
+                if (S->rect)
+                    push(keys, &cnt, N, v_va(S, i, t), v_va(S, i, t));
+            }
             for (int g = 0; g < n->ngen; g++) /* cost term */
                 push(keys, &cnt, N, v_pg(S, g, t), v_pg(S, g, t));
             for (int64_t a = 0; a < 2 * nl; a++) { /* thermal terms */
@@ -577,6 +725,13 @@ void ora_bounds(const ora_ctx *C, double *xl, double *xu, double *gl, double *gu
         int64_t nl = n->nbranch;
         for (int t = 0; t < n->nperiod; t++) {
             for (int i = 0; i < n->nbus; i++) {
+                if (S->rect) {
+                    xl[v_va(S, i, t)] = xl[v_vm(S, i, t)] = -n->vmax[i];
+                    xu[v_va(S, i, t)] = xu[v_vm(S, i, t)] = n->vmax[i];
+                    gl[row_of(S, G_VM, i, t)] = n->vmin[i] * n->vmin[i];
+                    gu[row_of(S, G_VM, i, t)] = n->vmax[i] * n->vmax[i];
+                    continue;
+                }
                 xl[v_va(S, i, t)] = -INFINITY;
                 xu[v_va(S, i, t)] = INFINITY;
                 xl[v_vm(S, i, t)] = n->vmin[i];
@@ -600,8 +755,15 @@ void ora_bounds(const ora_ctx *C, double *xl, double *xu, double *gl, double *gu
                 int grp[4] = {G_FPF, G_FQF, G_FPT, G_FQT};
                 for (int r = 0; r < 4; r++)
                     gl[row_of(S, grp[r], k, t)] = gu[row_of(S, grp[r], k, t)] = 0.0;
-                gl[row_of(S, G_ANG, k, t)] = n->angmin[k];
-                gu[row_of(S, G_ANG, k, t)] = n->angmax[k];
+                if (S->rect) {
+                    gl[row_of(S, G_ANG, k, t)] = -INFINITY;
+                    gu[row_of(S, G_ANG, k, t)] = 0.0;
+                    gl[row_of(S, G_ANL, k, t)] = 0.0;
+                    gu[row_of(S, G_ANL, k, t)] = INFINITY;
+                } else {
+                    gl[row_of(S, G_ANG, k, t)] = n->angmin[k];
+                    gu[row_of(S, G_ANG, k, t)] = n->angmax[k];
+                }
                 gl[row_of(S, G_THF, k, t)] = -INFINITY;
                 gu[row_of(S, G_THF, k, t)] = 0.0;
                 gl[row_of(S, G_THT, k, t)] = -INFINITY;
@@ -693,8 +855,9 @@ void ora_cons(const ora_ctx *C, const double *x, double *c, double *scale)
         const ora_net *n = &S->net;
         int64_t nl = n->nbranch, nb = n->nbus;
         for (int t = 0; t < n->nperiod; t++) {
-            double va_ref = x[v_va(S, n->ref_bus, t)];
-            ADD(row_of(S, G_REF, 0, t), va_ref, fabs(va_ref));
+            /* polar: va_ref; rectangular: vi_ref */
+            double ref = x[S->rect ? v_vm(S, n->ref_bus, t) : v_va(S, n->ref_bus, t)];
+            ADD(row_of(S, G_REF, 0, t), ref, fabs(ref));
             for (int k = 0; k < nl; k++) {
                 end_t fr, to;
                 ends_of(S, x, k, t, &fr, &to);
@@ -704,16 +867,27 @@ void ora_cons(const ora_ctx *C, const double *x, double *c, double *scale)
                 ADD(row_of(S, G_FPT, k, t), pt - creal(to.e.S), fabs(pt) + to.e.bS);
                 ADD(row_of(S, G_FQT, k, t), qt - cimag(to.e.S), fabs(qt) + to.e.bS);
                 double vaf = x[v_va(S, n->f[k], t)], vat = x[v_va(S, n->t[k], t)];
-                ADD(row_of(S, G_ANG, k, t), vaf - vat, fabs(vaf) + fabs(vat));
+                if (S->rect) {
+                    double vif = x[v_vm(S, n->f[k], t)], vit = x[v_vm(S, n->t[k], t)];
+                    double v, d[4], d2[4][4], bnd, db[4];
+                    angle_rect(vaf, vat, vif, vit, tan(n->angmax[k]), &v, d, d2, &bnd, db);
+                    ADD(row_of(S, G_ANG, k, t), v, bnd);
+                    angle_rect(vaf, vat, vif, vit, tan(n->angmin[k]), &v, d, d2, &bnd, db);
+                    ADD(row_of(S, G_ANL, k, t), v, bnd);
+                } else
+                    ADD(row_of(S, G_ANG, k, t), vaf - vat, fabs(vaf) + fabs(vat));
                 double r2 = n->rate_a[k] * n->rate_a[k];
                 ADD(row_of(S, G_THF, k, t), pf * pf + qf * qf - r2, pf * pf + qf * qf + r2);
                 ADD(row_of(S, G_THT, k, t), pt * pt + qt * qt - r2, pt * pt + qt * qt + r2);
             }
             for (int i = 0; i < nb; i++) {
-                double vm = x[v_vm(S, i, t)];
+                double vm = x[v_vm(S, i, t)], vr = x[v_va(S, i, t)];
+                double V2 = S->rect ? vr * vr + vm * vm : vm * vm; /* |V_i|^2 */
                 double Pd = S->Pd[t * nb + i], Qd = S->Qd[t * nb + i];
-                ADD(row_of(S, G_PB, i, t), Pd + n->gs[i] * vm * vm, fabs(Pd) + fabs(n->gs[i]) * vm * vm);
-                ADD(row_of(S, G_QB, i, t), Qd - n->bs[i] * vm * vm, fabs(Qd) + fabs(n->bs[i]) * vm * vm);
+                ADD(row_of(S, G_PB, i, t), Pd + n->gs[i] * V2, fabs(Pd) + fabs(n->gs[i]) * V2);
+                ADD(row_of(S, G_QB, i, t), Qd - n->bs[i] * V2, fabs(Qd) + fabs(n->bs[i]) * V2);
+                if (S->rect)
+                    ADD(row_of(S, G_VM, i, t), V2, V2);
             }
             for (int64_t a = 0; a < 2 * nl; a++) { /* constraint! augmentation: +p[a] at a.bus */
                 int i = arc_bus(S, a);
@@ -797,7 +971,8 @@ int ora_jac(const ora_ctx *C, const double *x, double *vals, double *scale)
         const ora_net *n = &S->net;
         int64_t nl = n->nbranch;
         for (int t = 0; t < n->nperiod; t++) {
-            acc(&A, row_of(S, G_REF, 0, t), v_va(S, n->ref_bus, t), 1.0, 1.0);
+            acc(&A, row_of(S, G_REF, 0, t), S->rect ? v_vm(S, n->ref_bus, t) : v_va(S, n->ref_bus, t),
+                1.0, 1.0);
             for (int k = 0; k < nl; k++) {
                 end_t fr, to;
                 ends_of(S, x, k, t, &fr, &to);
@@ -814,8 +989,19 @@ int ora_jac(const ora_ctx *C, const double *x, double *vals, double *scale)
                         acc(&A, rQ, E->u[d], -cimag(E->e.dS[d]), E->e.bdS[d]);
                     }
                 }
-                acc(&A, row_of(S, G_ANG, k, t), v_va(S, n->f[k], t), 1.0, 1.0);
-                acc(&A, row_of(S, G_ANG, k, t), v_va(S, n->t[k], t), -1.0, 1.0);
+                if (S->rect) { /* local order of the from-end: (vr_f, vr_t, vi_f, vi_t) */
+                    double v, d[4], d2[4][4], bnd, db[4];
+                    double xv[4] = {x[fr.u[0]], x[fr.u[1]], x[fr.u[2]], x[fr.u[3]]};
+                    angle_rect(xv[0], xv[1], xv[2], xv[3], tan(n->angmax[k]), &v, d, d2, &bnd, db);
+                    for (int q = 0; q < 4; q++)
+                        acc(&A, row_of(S, G_ANG, k, t), fr.u[q], d[q], db[q]);
+                    angle_rect(xv[0], xv[1], xv[2], xv[3], tan(n->angmin[k]), &v, d, d2, &bnd, db);
+                    for (int q = 0; q < 4; q++)
+                        acc(&A, row_of(S, G_ANL, k, t), fr.u[q], d[q], db[q]);
+                } else {
+                    acc(&A, row_of(S, G_ANG, k, t), v_va(S, n->f[k], t), 1.0, 1.0);
+                    acc(&A, row_of(S, G_ANG, k, t), v_va(S, n->t[k], t), -1.0, 1.0);
+                }
                 double pf = x[fr.pvar], qf = x[fr.qvar], pt = x[to.pvar], qt = x[to.qvar];
                 acc(&A, row_of(S, G_THF, k, t), fr.pvar, 2.0 * pf, 2.0 * fabs(pf));
                 acc(&A, row_of(S, G_THF, k, t), fr.qvar, 2.0 * qf, 2.0 * fabs(qf));
@@ -823,9 +1009,16 @@ int ora_jac(const ora_ctx *C, const double *x, double *vals, double *scale)
                 acc(&A, row_of(S, G_THT, k, t), to.qvar, 2.0 * qt, 2.0 * fabs(qt));
             }
             for (int i = 0; i < n->nbus; i++) {
-                double vm = x[v_vm(S, i, t)];
-                acc(&A, row_of(S, G_PB, i, t), v_vm(S, i, t), 2.0 * n->gs[i] * vm, 2.0 * fabs(n->gs[i]) * vm);
-                acc(&A, row_of(S, G_QB, i, t), v_vm(S, i, t), -2.0 * n->bs[i] * vm, 2.0 * fabs(n->bs[i]) * vm);
+                /* d|V|^2: polar 2 vm on vm; rectangular 2 vr on vr and 2 vi on vi */
+                int nv = S->rect ? 2 : 1;
+                int64_t col[2] = {v_vm(S, i, t), v_va(S, i, t)};
+                for (int q = 0; q < nv; q++) {
+                    double v = x[col[q]];
+                    acc(&A, row_of(S, G_PB, i, t), col[q], 2.0 * n->gs[i] * v, 2.0 * fabs(n->gs[i] * v));
+                    acc(&A, row_of(S, G_QB, i, t), col[q], -2.0 * n->bs[i] * v, 2.0 * fabs(n->bs[i] * v));
+                    if (S->rect)
+                        acc(&A, row_of(S, G_VM, i, t), col[q], 2.0 * v, 2.0 * fabs(v));
+                }
             }
             for (int64_t a = 0; a < 2 * nl; a++) {
                 int i = arc_bus(S, a);
@@ -891,12 +1084,34 @@ int ora_hess(const ora_ctx *C, const double *x, const double *lambda, double sig
                     const end_t *E = ends[side];
                     double lP = lambda[row_of(S, gP[side], k, t)];
                     double lQ = lambda[row_of(S, gQ[side], k, t)];
+                    if (S->rect) { /* the structurally nonzero pairs only */
+                        for (int q = 0; q < 6; q++) {
+                            int a = RECT_D2[q][0], b = RECT_D2[q][1];
+                            double v = -lP * creal(E->e.d2S[a][b]) - lQ * cimag(E->e.d2S[a][b]);
+                            double bnd = (fabs(lP) + fabs(lQ)) * E->e.bd2S[a][b];
+                            acc_sym(&A, E->u[a], E->u[b], v, bnd);
+                        }
+                        continue;
+                    }
                     for (int a = 0; a < 4; a++)
                         for (int b = a; b < 4; b++) {
                             double v = -lP * creal(E->e.d2S[a][b]) - lQ * cimag(E->e.d2S[a][b]);
                             double bnd = (fabs(lP) + fabs(lQ)) * E->e.bd2S[a][b];
                             acc_sym(&A, E->u[a], E->u[b], v, bnd);
                         }
+                }
+                if (S->rect) { /* the two angle rows: constant second derivatives */
+                    double v, d[4], dh[4][4], dl[4][4], bnd, db[4];
+                    double lh = lambda[row_of(S, G_ANG, k, t)], ll = lambda[row_of(S, G_ANL, k, t)];
+                    double xv[4] = {x[fr.u[0]], x[fr.u[1]], x[fr.u[2]], x[fr.u[3]]};
+                    angle_rect(xv[0], xv[1], xv[2], xv[3], tan(n->angmax[k]), &v, d, dh, &bnd, db);
+                    angle_rect(xv[0], xv[1], xv[2], xv[3], tan(n->angmin[k]), &v, d, dl, &bnd, db);
+                    int pr[4][2] = {{0, 1}, {2, 3}, {0, 3}, {1, 2}};
+                    for (int q = 0; q < 4; q++) {
+                        int a = pr[q][0], b = pr[q][1];
+                        acc_sym(&A, fr.u[a], fr.u[b], lh * dh[a][b] + ll * dl[a][b],
+                                fabs(lh * dh[a][b]) + fabs(ll * dl[a][b]));
+                    }
                 }
                 /* thermal rows: lambda * 2 on (p, p) and (q, q) of each arc */
                 double lf = lambda[row_of(S, G_THF, k, t)], lt = lambda[row_of(S, G_THT, k, t)];
@@ -905,11 +1120,17 @@ int ora_hess(const ora_ctx *C, const double *x, const double *lambda, double sig
                 acc_sym(&A, to.pvar, to.pvar, 2.0 * lt, 2.0 * fabs(lt));
                 acc_sym(&A, to.qvar, to.qvar, 2.0 * lt, 2.0 * fabs(lt));
             }
-            /* balance demand terms: gs vm^2 (P) and -bs vm^2 (Q) */
+            /* balance demand terms gs |V|^2 (P) and -bs |V|^2 (Q), and the
+             * rectangular form's magnitude row |V|^2: d2|V|^2 = 2 on vm (polar),
+             * on vr and on vi (rectangular) */
             for (int i = 0; i < n->nbus; i++) {
                 double lP = lambda[row_of(S, G_PB, i, t)], lQ = lambda[row_of(S, G_QB, i, t)];
-                acc_sym(&A, v_vm(S, i, t), v_vm(S, i, t), 2.0 * n->gs[i] * lP - 2.0 * n->bs[i] * lQ,
-                        2.0 * fabs(n->gs[i] * lP) + 2.0 * fabs(n->bs[i] * lQ));
+                double lV = S->rect ? lambda[row_of(S, G_VM, i, t)] : 0.0;
+                double v = 2.0 * n->gs[i] * lP - 2.0 * n->bs[i] * lQ + 2.0 * lV;
+                double bnd = 2.0 * fabs(n->gs[i] * lP) + 2.0 * fabs(n->bs[i] * lQ) + 2.0 * fabs(lV);
+                acc_sym(&A, v_vm(S, i, t), v_vm(S, i, t), v, bnd);
+                if (S->rect)
+                    acc_sym(&A, v_va(S, i, t), v_va(S, i, t), v, bnd);
             }
         }
     }

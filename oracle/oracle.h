@@ -19,6 +19,11 @@
  *   angle difference, P balance, Q balance, thermal (from), thermal (to),
  *   then ramp rows g + ngen * (t - 1), t = 1..T-1.
  * Instances are concatenated; linking rows come last.
+ *
+ * Rectangular form (form 1): vr, vi take the places of va, vm; the reference
+ * row is vi_ref; the angle group holds Im(w) - tan(angmax) Re(w) <= 0 and two
+ * groups follow the thermal rows: Im(w) - tan(angmin) Re(w) >= 0 per branch
+ * and vmin^2 <= vr^2 + vi^2 <= vmax^2 per bus (w = V_f conj(V_t)).
  */
 #ifndef OPF_ORACLE_H
 #define OPF_ORACLE_H
@@ -49,6 +54,9 @@ ora_ctx *ora_create(const ora_net *nets, int32_t ninst, double link_ratio);
  * instance and period, sum_g pg_g <= sum_g pmax_g - reserve * (total Pd). */
 ora_ctx *ora_create2(const ora_net *nets, int32_t ninst, double link_ratio, const double *link_ratios,
                      double reserve);
+/* As ora_create2 in the polar (form 0) or rectangular (form 1) voltages. */
+ora_ctx *ora_create3(const ora_net *nets, int32_t ninst, double link_ratio, const double *link_ratios,
+                     double reserve, int32_t form);
 void ora_destroy(ora_ctx *);
 const char *ora_error(void);
 
