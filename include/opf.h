@@ -1,7 +1,8 @@
 /*
  * opf.h — C ABI of libopf: GPU evaluation of the AC optimal power flow NLP
- * callbacks (polar voltages, branch-flow variables) at a fixed sparsity
- * pattern, for one instance, many periods, or a batch of instances.
+ * callbacks (polar or rectangular voltages, branch-flow variables) at a
+ * fixed sparsity pattern, for one instance, many periods, or a batch of
+ * instances.
  *
  * The problem is the static polar model of the paper's Listing 3 (Sec. III-B),
  * written in the NLP form of Sec. II-A, with the multi-period extension of
@@ -23,6 +24,16 @@
  *   Flow rows are p_arc - P(v) and q_arc - Q(v) (bounds [0, 0]); thermal rows
  *   p^2 + q^2 - rate_a^2 (bounds [-inf, 0]); balance rows
  *   Pd + gs vm^2 + sum(arc p) - sum(pg) and Qd - bs vm^2 + sum(arc q) - sum(qg).
+ *   Rectangular form (opf_batch_opts.form = OPF_FORM_RECT; the paper's
+ *   form = :rect of Sec. III-C-1, whose equations it leaves to the
+ *   rectangular AC model of PowerModels): x = [vr, vi, pg, qg, p, q] with
+ *   -vmax <= vr, vi <= vmax; the same flow functions with V = vr + j vi;
+ *   the reference row is vi_ref (bounds [0, 0]); the angle-difference group
+ *   holds Im(w) - tan(angmax) Re(w) (bounds [-inf, 0]), w = V_f conj(V_t),
+ *   and two groups follow the thermal rows: Im(w) - tan(angmin) Re(w)
+ *   (bounds [0, inf]) per branch and vr^2 + vi^2 (bounds [vmin^2, vmax^2])
+ *   per bus; balance rows use gs |V|^2 and -bs |V|^2; angle limits must lie
+ *   in (-pi/2, pi/2).
  *   Jacobian: values in row-major order of the deduplicated pattern, columns
  *   ascending within a row. Hessian of the Lagrangian
  *   obj_weight * grad^2 f + sum_i lambda_i grad^2 g_i: lower triangle
@@ -84,6 +95,8 @@ typedef struct {
                                                     when > 0 and nperiod > 1 (Listing 6) */
 } opf_network;
 
+enum { OPF_FORM_POLAR = 0, OPF_FORM_RECT = 1 };
+
 typedef struct {
     double link_ratio; /* > 0: rows pg_s - pg_0 in [-ratio pmax, ratio pmax] for every
                           instance s >= 1 (all instances need equal ngen, nperiod 1) */
@@ -93,6 +106,8 @@ typedef struct {
     double reserve;    /* > 0: one reserve row per instance and period,
                           sum_g pg_g <= sum_g pmax_g - reserve * (total Pd of the period),
                           i.e. the spare capacity covers that share of the demand */
+    int32_t form;      /* OPF_FORM_POLAR (va, vm) or OPF_FORM_RECT (vr, vi), for every
+                          instance; models from opf_model_create are polar */
 } opf_batch_opts;
 
 typedef struct opf_model opf_model;
@@ -223,8 +238,8 @@ int opf_eval_all_noalloc(opf_model *model, const double *d_x, const double *d_la
 int opf_eval_jtprod(opf_model *model, const double *d_x, const double *d_v, double *d_out,
                     void *stream);
 
-/* Sets the p and q entries of d_x (n) to the branch flows at d_x's voltage
- * magnitudes and angles (the pi-model of Listing 3), so every flow row is
+/* Sets the p and q entries of d_x (n) to the branch flows at d_x's voltages
+ * (the pi-model of Listing 3, in the model's form), so every flow row is
  * zero; the other entries are left as they are. */
 int opf_eval_flows(opf_model *model, double *d_x, void *stream);
 
@@ -236,8 +251,9 @@ int opf_eval_flows(opf_model *model, double *d_x, void *stream);
 int opf_set_loads(opf_model *model, const double *d_load_pd, const double *d_load_qd, void *stream);
 
 /* Flat start (reading of the usual OPF initial point): va = 0, vm = 1
- * clipped into [vmin, vmax], pg and qg at the midpoint of their bounds,
- * p and q equal to the branch flows at those voltages. Into d_x (n). */
+ * clipped into [vmin, vmax] (rectangular form: vr = that magnitude, vi = 0),
+ * pg and qg at the midpoint of their bounds, p and q equal to the branch
+ * flows at those voltages. Into d_x (n). */
 int opf_flat_start(opf_model *model, double *d_x, void *stream);
 
 /* The sine and cosine the branch kernel evaluates (table-driven: a table of

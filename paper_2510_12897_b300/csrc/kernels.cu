@@ -43,6 +43,19 @@
 //   d2L/dvm_f dvm_t = -U,  d2L/dvm_f dva_f = -vm_t V = -d2L/dvm_f dva_t,
 //   d2L/dvm_t dva_t = vm_f V = -d2L/dvm_t dva_f,
 //   d2L/dvm_f2 = -2 (m1 Gff - m2 Bff),  d2L/dvm_t2 = -2 (m3 Gtt - m4 Btt).
+//
+// Rectangular form (form = :rect): with V = vr + j vi and w = V_f conj(V_t),
+//   wR = vr_f vr_t + vi_f vi_t,  wI = vi_f vr_t - vr_f vi_t,
+//   P_fr =  Gff |V_f|^2 + Gft wR + Bft wI,   Q_fr = -Bff |V_f|^2 + Gft wI - Bft wR,
+//   P_to =  Gtt |V_t|^2 + Gtf wR - Btf wI,   Q_to = -Btt |V_t|^2 - Gtf wI - Btf wR,
+// and the angle rows are wI - tan(angmax) wR and wI - tan(angmin) wR. Every
+// row is a |V_e|^2 + c wR + d wI, whose gradient in (vr_f, vr_t, vi_f, vi_t)
+// is (c vr_t - d vi_t, c vr_f + d vi_f, c vi_t + d vr_t, c vi_f - d vr_f)
+// plus 2 a V_e on the end's own pair; the Lagrangian of a branch's rows is
+// (Df/2) |V_f|^2 + (Dt/2) |V_t|^2 + aR wR + aI wI + linear terms, so its
+// Hessian is constant: Df on (vr_f, vr_f) and (vi_f, vi_f), Dt likewise at
+// the to-end, aR on (vr_f, vr_t) and (vi_f, vi_t), aI on (vi_f, vr_t) and
+// -aI on (vr_f, vi_t).
 #include "model.h"
 
 namespace opf {
@@ -362,9 +375,205 @@ __global__ void __launch_bounds__(OCC ? 256 : 512, OCC ? 3 : 1) branch_kernel(co
     }
 }
 
+// gradient of c wR + d wI in the order (vr_f, vr_t, vi_f, vi_t)
+struct Grad4 {
+    double rf, rt, jf, jt;
+};
+__device__ __forceinline__ Grad4 wgrad(double c, double d, double vrf, double vrt, double vif, double vit)
+{
+    Grad4 g;
+    g.rf = fma(c, vrt, neg(d * vit));
+    g.rt = fma(c, vrf, d * vif);
+    g.jf = fma(c, vit, d * vrt);
+    g.jt = fma(c, vif, neg(d * vrf));
+    return g;
+}
+
+// the Jacobian entries of a rectangular row, columns ascending:
+// (vr_lo, vr_hi, vi_lo, vi_hi), then the own flow variable if `own`
+__device__ __forceinline__ void put_rect(double *J, bool f_lo, const Grad4 &g, bool own)
+{
+    J[0] = f_lo ? g.rf : g.rt;
+    J[1] = f_lo ? g.rt : g.rf;
+    J[2] = f_lo ? g.jf : g.jt;
+    J[3] = f_lo ? g.jt : g.jf;
+    if (own)
+        J[4] = 1.0;
+}
+
+// Branch phase of the rectangular form: the same items, rows and scratch
+// slots as the polar branch kernel, without trigonometry. Row groups per
+// instance: ref, four flow groups, upper angle rows, P and Q balance, two
+// thermal groups, lower angle rows, magnitude rows, ramp rows.
+template <bool CONS, bool JAC, bool HESS, bool ONE>
+__global__ void __launch_bounds__(512, 1) rect_branch_kernel(const KParams P)
+{
+    cudaTriggerProgrammaticLaunchCompletion();
+    const DevArrays &d = P.d;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+
+    auto locate = [&](int64_t item, int &s, int &t, int &k, int &kb) {
+        if (ONE) {
+            s = 0;
+            split((int)item, P.inst0.nl, P.inst0.T, t, k);
+            kb = k;
+        } else {
+            s = find_inst(d.br_items, P.ninst, item);
+            const InstDev *I = d.inst + s;
+            split((int)(item - __ldg(d.br_items + s)), __ldg(&I->nl), __ldg(&I->T), t, k);
+            kb = __ldg(&I->br0) + k;
+        }
+    };
+
+    int s = 0, t = 0, k = 0, kb = 0;
+    BrStatic st{};
+    double2 tb = make_double2(0.0, 0.0);
+    if (it < P.nbr_items) {  // static prologue, overlaps the previous kernel
+        locate(it, s, t, k, kb);
+        st = load_br(d, kb, CONS, JAC);
+        tb = __ldg(d.tanb + kb);
+    }
+    cudaGridDependencySynchronize();
+
+    for (; it < P.nbr_items; it += stride) {
+        const BrStatic cur = st;
+        const double2 tan_ = tb;
+        const int cs = s, ct = t, ck = k;
+        if (it + stride < P.nbr_items) {  // prefetch the next item's static data
+            locate(it + stride, s, t, k, kb);
+            st = load_br(d, kb, CONS, JAC);
+            tb = __ldg(d.tanb + kb);
+        }
+        const InstDev I = inst_of<ONE>(P, cs);
+        const int nl = I.nl, nb = I.nb, ng = I.ng, T = I.T;
+        const int nbT = nb * T, ngT = ng * T, nlT = nl * T, na = 2 * nl;
+        const int rk = ck + nl * ct;
+        const int f = cur.br.x, b = cur.br.y;
+
+        const double *__restrict__ xs = P.x + I.x0;
+        const int ivr = nb * ct, ivi = nbT + nb * ct;
+        const int ip = 2 * nbT + 2 * ngT + na * ct, iq = ip + na * T;
+        const double vrf = __ldg(xs + ivr + f), vrt = __ldg(xs + ivr + b);
+        const double vif = __ldg(xs + ivi + f), vit = __ldg(xs + ivi + b);
+        double pf = 0, qf = 0, pt = 0, qt = 0;
+        if (CONS || JAC || HESS) {
+            pf = __ldg(xs + ip + ck);
+            pt = __ldg(xs + ip + nl + ck);
+            qf = __ldg(xs + iq + ck);
+            qt = __ldg(xs + iq + nl + ck);
+        }
+        double m1 = 0, m2 = 0, m3 = 0, m4 = 0, a1 = 0, a2 = 0, lf = 0, lt = 0;
+        if (HESS) {
+            const double *L = P.lam + I.c0 + (T + rk);
+            m1 = __ldg(L);
+            m2 = __ldg(L + nlT);
+            m3 = __ldg(L + 2 * nlT);
+            m4 = __ldg(L + 3 * nlT);
+            a1 = __ldg(L + 4 * nlT);
+            lf = __ldg(L + (5 * nlT + 2 * nbT));
+            lt = __ldg(L + (6 * nlT + 2 * nbT));
+            a2 = __ldg(L + (7 * nlT + 2 * nbT));
+        }
+        const double2 Yff = cur.yff, Yft = cur.yft, Ytf = cur.ytf, Ytt = cur.ytt;
+        const double wR = fma(vrf, vrt, vif * vit);
+        const double wI = fma(vif, vrt, neg(vrf * vit));
+
+        if (CONS) {
+            const double vf2 = fma(vrf, vrf, vif * vif), vt2 = fma(vrt, vrt, vit * vit);
+            double *c = P.c + I.c0 + (T + rk);
+            c[0] = pf - fma(Yff.x, vf2, fma(Yft.x, wR, Yft.y * wI));
+            c[nlT] = qf - fma(neg(Yff.y), vf2, fma(Yft.x, wI, neg(Yft.y * wR)));
+            c[2 * nlT] = pt - fma(Ytt.x, vt2, fma(Ytf.x, wR, neg(Ytf.y * wI)));
+            c[3 * nlT] = qt - fma(neg(Ytt.y), vt2, neg(fma(Ytf.x, wI, Ytf.y * wR)));
+            c[4 * nlT] = fma(neg(tan_.x), wR, wI);
+            c[5 * nlT + 2 * nbT] = fma(pf, pf, qf * qf) - cur.r2;
+            c[6 * nlT + 2 * nbT] = fma(pt, pt, qt * qt) - cur.r2;
+            c[7 * nlT + 2 * nbT] = fma(neg(tan_.y), wR, wI);
+        }
+        if (JAC) {
+            const int jP = (int)I.jP;
+            const bool f_lo = f < b;
+            double *J = P.jac + I.j0;
+            double *Jf = J + (T + 5 * rk);
+            // row p_fr - P_fr: a = -Gff (from end), c = -Gft, d = -Bft
+            Grad4 g = wgrad(neg(Yft.x), neg(Yft.y), vrf, vrt, vif, vit);
+            const double pa = neg(twice(Yff.x));
+            g.rf = fma(pa, vrf, g.rf);
+            g.jf = fma(pa, vif, g.jf);
+            put_rect(Jf, f_lo, g, true);
+            // row q_fr - Q_fr: a = Bff, c = Bft, d = -Gft
+            g = wgrad(Yft.y, neg(Yft.x), vrf, vrt, vif, vit);
+            const double qa = twice(Yff.y);
+            g.rf = fma(qa, vrf, g.rf);
+            g.jf = fma(qa, vif, g.jf);
+            put_rect(Jf + 5 * nlT, f_lo, g, true);
+            // row p_to - P_to: a = -Gtt (to end), c = -Gtf, d = Btf
+            g = wgrad(neg(Ytf.x), Ytf.y, vrf, vrt, vif, vit);
+            const double pb = neg(twice(Ytt.x));
+            g.rt = fma(pb, vrt, g.rt);
+            g.jt = fma(pb, vit, g.jt);
+            put_rect(Jf + 10 * nlT, f_lo, g, true);
+            // row q_to - Q_to: a = Btt, c = Btf, d = Gtf
+            g = wgrad(Ytf.y, Ytf.x, vrf, vrt, vif, vit);
+            const double qb = twice(Ytt.y);
+            g.rt = fma(qb, vrt, g.rt);
+            g.jt = fma(qb, vit, g.jt);
+            put_rect(Jf + 15 * nlT, f_lo, g, true);
+            // angle rows: c = -tan(limit), d = 1
+            put_rect(J + (T + 20 * nlT + 4 * rk), f_lo, wgrad(neg(tan_.x), 1.0, vrf, vrt, vif, vit), false);
+            put_rect(J + (T + 28 * nlT + 2 * jP * T + 4 * rk), f_lo, wgrad(neg(tan_.y), 1.0, vrf, vrt, vif, vit),
+                     false);
+            double *Jb = J + (T + 24 * nlT + jP * ct);  // +1 of each arc in its bus's P and Q rows
+            Jb[cur.jb.x] = 1.0;
+            Jb[cur.jb.y] = 1.0;
+            Jb[jP * T + cur.jb.x] = 1.0;
+            Jb[jP * T + cur.jb.y] = 1.0;
+            double *Jt = J + (T + 24 * nlT + 2 * jP * T + 2 * rk);  // thermal rows
+            Jt[0] = twice(pf);
+            Jt[1] = twice(qf);
+            Jt[2 * nlT] = twice(pt);
+            Jt[2 * nlT + 1] = twice(qt);
+        }
+        if (HESS || CONS) {
+            ArcScratch *S = d.arcs + I.scr0 + na * ct;
+            double2 *sf = reinterpret_cast<double2 *>(S + cur.br.z);
+            double2 *sto = reinterpret_cast<double2 *>(S + cur.br.w);
+            sf[0] = make_double2(pf, qf);
+            sto[0] = make_double2(pt, qt);
+            if (HESS) {
+                // aR = -m1 Gft + m2 Bft - m3 Gtf + m4 Btf - a1 tan(angmax) - a2 tan(angmin)
+                // aI = -m1 Bft - m2 Gft + m3 Btf + m4 Gtf + a1 + a2
+                const double aR = neg(fma(m1, Yft.x, fma(neg(m2), Yft.y, fma(m3, Ytf.x,
+                                  fma(neg(m4), Ytf.y, fma(a1, tan_.x, a2 * tan_.y))))));
+                const double aI = fma(neg(m1), Yft.y, fma(neg(m2), Yft.x, fma(m3, Ytf.y, fma(m4, Ytf.x, a1 + a2))));
+                const double Df = neg(twice(fma(m1, Yff.x, neg(m2 * Yff.y))));
+                const double Dt = neg(twice(fma(m3, Ytt.x, neg(m4 * Ytt.y))));
+                sf[1] = make_double2(Df, aR);
+                sto[1] = make_double2(Dt, aR);
+                reinterpret_cast<double *>(sf + 2)[0] = aI;
+                reinterpret_cast<double *>(sto + 2)[0] = neg(aI);
+                double *Hp = P.hess + I.h0 + ((int)(I.hva + I.hvm) * T + ngT + ck + na * ct);
+                const double l2f = twice(lf), l2t = twice(lt);
+                Hp[0] = l2f;            // (p_fr, p_fr)
+                Hp[nl] = l2t;           // (p_to, p_to)
+                Hp[na * T] = l2f;       // (q_fr, q_fr)
+                Hp[na * T + nl] = l2t;  // (q_to, q_to)
+            }
+        }
+        if (P.want_grad) {
+            double *g = P.grad + I.x0;
+            g[ip + ck] = 0.0;
+            g[ip + nl + ck] = 0.0;
+            g[iq + ck] = 0.0;
+            g[iq + nl + ck] = 0.0;
+        }
+    }
+}
+
 constexpr int kBusBlockMax = 256;
 
-template <bool CONS, bool JAC, bool HESS, bool ONE>
+template <bool CONS, bool JAC, bool HESS, bool ONE, bool RECT = false>
 __global__ void __launch_bounds__(kBusBlockMax) bus_kernel(const KParams P)
 {
     cudaTriggerProgrammaticLaunchCompletion();
@@ -440,13 +649,17 @@ __global__ void __launch_bounds__(kBusBlockMax) bus_kernel(const KParams P)
         if (it >= P.ngen_items) {
             const int i = q.e;
             const int iva = nb * q.t, ivm = nbT + nb * q.t;
-            // every dynamic scalar of the bus, issued together
+            // every dynamic scalar of the bus, issued together (rectangular:
+            // vr, vi in the places of va, vm)
             const double vm = __ldg(xs + ivm + i);
-            double lP = 0.0, lQ = 0.0, Pd = 0.0, Qd = 0.0, pg1 = 0.0, qg1 = 0.0;
+            const double vr = RECT ? __ldg(xs + iva + i) : 0.0;
+            double lP = 0.0, lQ = 0.0, lV = 0.0, Pd = 0.0, Qd = 0.0, pg1 = 0.0, qg1 = 0.0;
             if (HESS) {
                 const double *L = P.lam + I.c0 + (T + 5 * nlT + nb * q.t + i);
                 lP = __ldg(L);
                 lQ = __ldg(L + nbT);
+                if (RECT)  // the magnitude row
+                    lV = __ldg(L + (3 * nlT + 2 * nbT));
             }
             if (CONS) {
                 Pd = __ldg(d.Pd + I.pd0 + (nb * q.t + i));
@@ -465,26 +678,37 @@ __global__ void __launch_bounds__(kBusBlockMax) bus_kernel(const KParams P)
                 P.grad[I.x0 + iva + i] = 0.0;
                 P.grad[I.x0 + ivm + i] = 0.0;
             }
-            if (i == I.ref) {
+            if (i == I.ref) {  // va_ref, or vi_ref (rectangular)
                 if (CONS)
-                    P.c[I.c0 + q.t] = __ldg(xs + iva + i);
+                    P.c[I.c0 + q.t] = RECT ? vm : __ldg(xs + iva + i);
                 if (JAC)
                     P.jac[I.j0 + q.t] = 1.0;
             }
             if (JAC) {  // the arcs' +1 entries are written by the branch phase
                 const int jP = (int)I.jP;
-                double *JP = P.jac + I.j0 + (T + 22 * nlT + jP * q.t + q.b.x);
+                double *JP = P.jac + I.j0 + (T + (RECT ? 24 : 22) * nlT + jP * q.t + q.b.x);
                 double *JQ = JP + jP * T;
                 const double v2 = twice(vm);
-                JP[0] = gb.x * v2;
-                JQ[0] = neg(gb.y * v2);
-                for (int e = 1; e <= ng_here; e++) {
+                if constexpr (RECT) {  // d|V|^2 = (2 vr, 2 vi); the magnitude row
+                    const double r2 = twice(vr);
+                    JP[0] = gb.x * r2;
+                    JP[1] = gb.x * v2;
+                    JQ[0] = neg(gb.y * r2);
+                    JQ[1] = neg(gb.y * v2);
+                    double *JV = P.jac + I.j0 + (T + 32 * nlT + 2 * jP * T + 2 * (nb * q.t + i));
+                    JV[0] = r2;
+                    JV[1] = v2;
+                } else {
+                    JP[0] = gb.x * v2;
+                    JQ[0] = neg(gb.y * v2);
+                }
+                for (int e = RECT ? 2 : 1; e <= ng_here + (RECT ? 1 : 0); e++) {
                     JP[e] = -1.0;
                     JQ[e] = -1.0;
                 }
             }
             if (CONS || HESS) {
-                const double vm2 = vm * vm;
+                const double vm2 = RECT ? fma(vr, vr, vm * vm) : vm * vm;  // |V|^2
                 double Pb = fma(gb.x, vm2, Pd), Qb = fma(neg(gb.y), vm2, Qd);
                 if (CONS && q.gfirst >= 0) {
                     Pb -= pg1;
@@ -501,7 +725,8 @@ __global__ void __launch_bounds__(kBusBlockMax) bus_kernel(const KParams P)
                 const int nd = q.b.w & 0xffff, nlt = q.b.w >> 16;
                 const uint8_t *code = d.slot_code + I.slot0 + q.a.x;
                 double daa = 0.0, dma = 0.0, acc_ma = 0.0, acc_aa = 0.0, acc_mm = 0.0;
-                double dmm = HESS ? twice(fma(gb.x, lP, neg(gb.y * lQ))) : 0.0;  // 2 gs lP - 2 bs lQ
+                // 2 gs lP - 2 bs lQ (+ 2 lV, the magnitude row, rectangular)
+                double dmm = HESS ? twice(fma(gb.x, lP, fma(neg(gb.y), lQ, lV))) : 0.0;
                 bool first = true;
                 int grp = 0;
                 // the bus's slots (sorted by far bus), four at a time: the loads
@@ -527,7 +752,29 @@ __global__ void __launch_bounds__(kBusBlockMax) bus_kernel(const KParams P)
                             Pb += v0[u].x;
                             Qb += v0[u].y;
                         }
-                        if (HESS) {
+                        if (HESS && RECT) {
+                            // v1 = (diagonal part, aR), v2.x = signed aI
+                            const unsigned cd = nsl <= 32
+                                ? (((unsigned)q.m.x >> a) & 1u) | (a < q.m.y ? 2u : 0u)
+                                : (unsigned)__ldg(code + a);
+                            dmm += v1[u].x;
+                            if (first) {
+                                acc_aa = v1[u].y;
+                                acc_ma = v2[u].x;
+                            } else {
+                                acc_aa += v1[u].y;
+                                acc_ma += v2[u].x;
+                            }
+                            first = (cd & SLOT_LAST) != 0;
+                            if (first) {  // a group of parallel arcs ends
+                                Hvm[grp] = acc_ma;  // (vi_i, vr_j)
+                                if (cd & SLOT_LOWER) {
+                                    Hva[grp] = acc_aa;           // (vr_i, vr_j), j < i
+                                    Hvm[nd + grp] = acc_aa;      // (vi_i, vi_j), j < i
+                                }
+                                grp++;
+                            }
+                        } else if (HESS) {
                             const unsigned cd = nsl <= 32
                                 ? (((unsigned)q.m.x >> a) & 1u) | (a < q.m.y ? 2u : 0u)
                                 : (unsigned)__ldg(code + a);
@@ -559,8 +806,13 @@ __global__ void __launch_bounds__(kBusBlockMax) bus_kernel(const KParams P)
                     double *c = P.c + I.c0 + (T + 5 * nlT + nb * q.t + i);
                     c[0] = Pb;
                     c[nbT] = Qb;
+                    if (RECT)
+                        c[3 * nlT + 2 * nbT] = vm2;  // the magnitude row
                 }
-                if (HESS) {
+                if (HESS && RECT) {  // diagonals (vr_i, vr_i) and (vi_i, vi_i)
+                    Hva[nlt] = dmm;
+                    Hvm[nd + nlt] = dmm;
+                } else if (HESS) {
                     if (nsl > 0) {
                         Hva[nlt] = daa;
                         Hvm[nlt] = dma;
@@ -587,9 +839,9 @@ __global__ void __launch_bounds__(kBusBlockMax) bus_kernel(const KParams P)
             if ((CONS || JAC) && q.t >= 1 && I.ramp) {
                 const int r = g + ng * (q.t - 1);
                 if (CONS)
-                    P.c[I.c0 + (T + 7 * nlT + 2 * nbT + r)] = pg - __ldg(xs + ipg - ng);
+                    P.c[I.c0 + (T + (RECT ? 8 * nlT + 3 * nbT : 7 * nlT + 2 * nbT) + r)] = pg - __ldg(xs + ipg - ng);
                 if (JAC) {
-                    double *J = P.jac + I.j0 + (T + 26 * nlT + 2 * (int)I.jP * T + 2 * r);
+                    double *J = P.jac + I.j0 + (T + (RECT ? 32 * nlT + 2 * nbT : 26 * nlT) + 2 * (int)I.jP * T + 2 * r);
                     J[0] = -1.0;
                     J[1] = 1.0;
                 }
@@ -661,7 +913,7 @@ __global__ void __launch_bounds__(kBusBlockMax) bus_kernel(const KParams P)
 // reference and balance-row terms; generator items take their balance,
 // ramp and linking rows.
 
-template <bool ONE>
+template <bool ONE, bool RECT = false>
 __global__ void __launch_bounds__(512) jt_branch_kernel(const KParams P)
 {
     cudaTriggerProgrammaticLaunchCompletion();
@@ -714,6 +966,33 @@ __global__ void __launch_bounds__(512) jt_branch_kernel(const KParams P)
         const double bPf = __ldg(VB + f), bPt = __ldg(VB + b);
         const double bQf = __ldg(VB + nbT + f), bQt = __ldg(VB + nbT + b);
         const double2 Yff = cur.yff, Yft = cur.yft, Ytf = cur.ytf, Ytt = cur.ytt;
+        double *o = P.grad + I.x0;  // P.grad carries `out`
+        if constexpr (RECT) {
+            // vr = the first block (vaf, vat), vi = the second (vmf, vmt);
+            // v^T g over the branch's rows has the voltage part
+            // (Df/2)|V_f|^2 + (Dt/2)|V_t|^2 + aR wR + aI wI (angle rows: v at
+            // the upper row's and the lower row's places)
+            const double a1 = va_;
+            const double a2 = __ldg(V + (7 * nlT + 2 * nbT));
+            const double2 tn = __ldg(d.tanb + (I.br0 + ck));
+            const double aR = neg(fma(m1, Yft.x, fma(neg(m2), Yft.y, fma(m3, Ytf.x,
+                              fma(neg(m4), Ytf.y, fma(a1, tn.x, a2 * tn.y))))));
+            const double aI = fma(neg(m1), Yft.y, fma(neg(m2), Yft.x, fma(m3, Ytf.y, fma(m4, Ytf.x, a1 + a2))));
+            const double Df = neg(twice(fma(m1, Yff.x, neg(m2 * Yff.y))));
+            const double Dt = neg(twice(fma(m3, Ytt.x, neg(m4 * Ytt.y))));
+            o[ip + ck] = fma(twice(pf), tf, m1 + bPf);
+            o[iq + ck] = fma(twice(qf), tf, m2 + bQf);
+            o[ip + nl + ck] = fma(twice(pt), tt, m3 + bPt);
+            o[iq + nl + ck] = fma(twice(qt), tt, m4 + bQt);
+            const double drf = fma(Df, vaf, fma(aR, vat, neg(aI * vmt)));
+            const double dif = fma(Df, vmf, fma(aR, vmt, aI * vat));
+            const double drt = fma(Dt, vat, fma(aR, vaf, aI * vmf));
+            const double dit = fma(Dt, vmt, fma(aR, vmf, neg(aI * vaf)));
+            ArcScratch *S = d.arcs + I.scr0 + na * ct;
+            reinterpret_cast<double2 *>(S + cur.br.z)[0] = make_double2(drf, dif);
+            reinterpret_cast<double2 *>(S + cur.br.w)[0] = make_double2(drt, dit);
+            continue;
+        }
         double sn, cs_;
         sincos_tab(vaf - vat, d.trig, &sn, &cs_);
         const double vft = vmf * vmt;
@@ -722,7 +1001,6 @@ __global__ void __launch_bounds__(512) jt_branch_kernel(const KParams P)
         const double Atf = fma(Ytf.x, cs_, neg(Ytf.y * sn));
         const double Btf = neg(fma(Ytf.x, sn, Ytf.y * cs_));
         // own variables: flow row, thermal row, balance row of the arc's bus
-        double *o = P.grad + I.x0;  // P.grad carries `out`
         o[ip + ck] = fma(twice(pf), tf, m1 + bPf);
         o[iq + ck] = fma(twice(qf), tf, m2 + bQf);
         o[ip + nl + ck] = fma(twice(pt), tt, m3 + bPt);
@@ -745,7 +1023,7 @@ __global__ void __launch_bounds__(512) jt_branch_kernel(const KParams P)
     }
 }
 
-template <bool ONE>
+template <bool ONE, bool RECT = false>
 __global__ void __launch_bounds__(256) jt_bus_kernel(const KParams P)
 {
     cudaTriggerProgrammaticLaunchCompletion();
@@ -786,8 +1064,17 @@ __global__ void __launch_bounds__(256) jt_bus_kernel(const KParams P)
             const double vm = __ldg(xs + nbT + nb * t + i);
             const double vP = __ldg(V + (T + 5 * nlT + nb * t + i)), vQ = __ldg(V + (T + 5 * nlT + nbT + nb * t + i));
             const double2 *Sg = reinterpret_cast<const double2 *>(d.arcs + I.scr0 + (int64_t)na * t + a.x);
-            double dva = i == I.ref ? __ldg(V + t) : 0.0;
-            double dvm = twice(vm * fma(gb.x, vP, neg(gb.y * vQ)));  // 2 vm (gs vP - bs vQ)
+            double dva, dvm;
+            if constexpr (RECT) {  // vr, vi: 2 V (gs vP - bs vQ + vV); the reference row is vi_ref
+                const double vr = __ldg(xs + nb * t + i);
+                const double vV = __ldg(V + (T + 8 * nlT + 2 * nbT + nb * t + i));
+                const double k = twice(fma(gb.x, vP, fma(neg(gb.y), vQ, vV)));
+                dva = vr * k;
+                dvm = fma(vm, k, i == I.ref ? __ldg(V + t) : 0.0);
+            } else {
+                dva = i == I.ref ? __ldg(V + t) : 0.0;
+                dvm = twice(vm * fma(gb.x, vP, neg(gb.y * vQ)));  // 2 vm (gs vP - bs vQ)
+            }
             for (int q = 0; q < a.y - a.x; q++) {
                 const double2 w = __ldcg(Sg + 3 * q);
                 dva += w.x;
@@ -801,7 +1088,7 @@ __global__ void __launch_bounds__(256) jt_bus_kernel(const KParams P)
             double vpg = neg(__ldg(V + (T + 5 * nlT + nb * t + bus)));
             const double vqg = neg(__ldg(V + (T + 5 * nlT + nbT + nb * t + bus)));
             if (I.ramp) {  // rows pg_t - pg_{t-1}, t = 1..T-1
-                const int rb = T + 7 * nlT + 2 * nbT;
+                const int rb = T + (RECT ? 8 * nlT + 3 * nbT : 7 * nlT + 2 * nbT);
                 if (t >= 1)
                     vpg += __ldg(V + (rb + g + ng * (t - 1)));
                 if (t + 1 <= T - 1)
@@ -822,7 +1109,7 @@ __global__ void __launch_bounds__(256) jt_bus_kernel(const KParams P)
 
 // p, q of every arc := the flows at the point's voltages (flow rows exactly
 // zero), one thread per branch item.
-template <bool ONE>
+template <bool ONE, bool RECT = false>
 __global__ void flows_kernel(const KParams P, double *x)
 {
     const DevArrays &d = P.d;
@@ -847,6 +1134,15 @@ __global__ void flows_kernel(const KParams P, double *x)
         const int ip = 2 * nbT + 2 * ngT + na * t, iq = ip + na * T;
         const double vaf = xs[iva + br.br.x], vat = xs[iva + br.br.y];
         const double vmf = xs[ivm + br.br.x], vmt = xs[ivm + br.br.y];
+        if constexpr (RECT) {  // (vr, vi) in the places of (va, vm)
+            const double wR = fma(vaf, vat, vmf * vmt), wI = fma(vmf, vat, neg(vaf * vmt));
+            const double vf2 = fma(vaf, vaf, vmf * vmf), vt2 = fma(vat, vat, vmt * vmt);
+            xs[ip + k] = fma(br.yff.x, vf2, fma(br.yft.x, wR, br.yft.y * wI));
+            xs[iq + k] = fma(neg(br.yff.y), vf2, fma(br.yft.x, wI, neg(br.yft.y * wR)));
+            xs[ip + nl + k] = fma(br.ytt.x, vt2, fma(br.ytf.x, wR, neg(br.ytf.y * wI)));
+            xs[iq + nl + k] = fma(neg(br.ytt.y), vt2, neg(fma(br.ytf.x, wI, br.ytf.y * wR)));
+            continue;
+        }
         double sn, cs_;
         sincos_tab(vaf - vat, d.trig, &sn, &cs_);
         const double vft = vmf * vmt;
@@ -892,9 +1188,10 @@ __global__ void set_loads_kernel(const KParams P, const double *pd, const double
 }
 
 // Flat start: va = 0, vm = clamp(1), pg, qg at mid-bounds, p, q = flows at
-// those voltages (d = 0: cos d = 1, sin d = 0).
+// those voltages (d = 0: cos d = 1, sin d = 0). Rectangular: vr = clamp(1),
+// vi = 0, the same point and flows.
 __global__ void flat_kernel(const DevArrays d, int32_t ninst, int64_t nbr_items, int64_t nbus_items,
-                            int64_t ngen_items, double *x)
+                            int64_t ngen_items, int rect, double *x)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t total = nbr_items + nbus_items + ngen_items;
@@ -925,8 +1222,9 @@ __global__ void flat_kernel(const DevArrays d, int32_t ninst, int64_t nbr_items,
             split((int)(bi - d.bus_items[s]), I->nb, I->T, t, i);
             const double2 vb = d.vbnd[I->bus0 + i];
             const int64_t xva = I->x0 + (int64_t)I->nb * t;
-            x[xva + i] = 0.0;
-            x[xva + (int64_t)I->nb * I->T + i] = fmin(fmax(1.0, vb.x), vb.y);
+            const double v1 = fmin(fmax(1.0, vb.x), vb.y);
+            x[xva + i] = rect ? v1 : 0.0;
+            x[xva + (int64_t)I->nb * I->T + i] = rect ? 0.0 : v1;
         } else {
             const int64_t gi = it - nbr_items - nbus_items;
             const int s = ninst == 1 ? 0 : find_inst(d.gen_items, ninst, gi);
@@ -1009,10 +1307,19 @@ cudaError_t launch_pdl(K kernel, int grid, int block, cudaStream_t s, const KPar
 }
 
 template <bool C, bool J, bool H>
-cudaError_t dispatch(const KParams &P, bool one, bool occ, bool run_branch, bool run_bus, int gb, int bb,
-                     int gu, int bu, cudaStream_t s)
+cudaError_t dispatch(const KParams &P, bool one, bool occ, bool rect, bool run_branch, bool run_bus, int gb,
+                     int bb, int gu, int bu, cudaStream_t s)
 {
     cudaError_t e = cudaSuccess;
+    if (rect) {  // one register budget; the bus phase's rectangular variant
+        if (run_branch)
+            e = one ? launch_pdl(rect_branch_kernel<C, J, H, true>, gb, bb, s, P)
+                    : launch_pdl(rect_branch_kernel<C, J, H, false>, gb, bb, s, P);
+        if (e != cudaSuccess || !run_bus)
+            return e;
+        return one ? launch_pdl(bus_kernel<C, J, H, true, true>, gu, bu, s, P)
+                   : launch_pdl(bus_kernel<C, J, H, false, true>, gu, bu, s, P);
+    }
     if (run_branch) {
         if (occ)
             e = one ? launch_pdl(branch_kernel<C, J, H, true, true>, gb, bb, s, P)
@@ -1069,14 +1376,14 @@ int launch_all(Model &M, const EvalArgs &a, unsigned what, cudaStream_t s, int p
     P.order = L.bus_order ? M.d.bus_order : nullptr;
     cudaError_t e;
     switch ((C ? 1 : 0) | (J ? 2 : 0) | (H ? 4 : 0)) {
-    case 0: e = dispatch<false, false, false>(P, one, occ, run_branch, run_bus, gb, bb, gu, bu, s); break;
-    case 1: e = dispatch<true, false, false>(P, one, occ, run_branch, run_bus, gb, bb, gu, bu, s); break;
-    case 2: e = dispatch<false, true, false>(P, one, occ, run_branch, run_bus, gb, bb, gu, bu, s); break;
-    case 3: e = dispatch<true, true, false>(P, one, occ, run_branch, run_bus, gb, bb, gu, bu, s); break;
-    case 4: e = dispatch<false, false, true>(P, one, occ, run_branch, run_bus, gb, bb, gu, bu, s); break;
-    case 5: e = dispatch<true, false, true>(P, one, occ, run_branch, run_bus, gb, bb, gu, bu, s); break;
-    case 6: e = dispatch<false, true, true>(P, one, occ, run_branch, run_bus, gb, bb, gu, bu, s); break;
-    default: e = dispatch<true, true, true>(P, one, occ, run_branch, run_bus, gb, bb, gu, bu, s); break;
+    case 0: e = dispatch<false, false, false>(P, one, occ, M.rect, run_branch, run_bus, gb, bb, gu, bu, s); break;
+    case 1: e = dispatch<true, false, false>(P, one, occ, M.rect, run_branch, run_bus, gb, bb, gu, bu, s); break;
+    case 2: e = dispatch<false, true, false>(P, one, occ, M.rect, run_branch, run_bus, gb, bb, gu, bu, s); break;
+    case 3: e = dispatch<true, true, false>(P, one, occ, M.rect, run_branch, run_bus, gb, bb, gu, bu, s); break;
+    case 4: e = dispatch<false, false, true>(P, one, occ, M.rect, run_branch, run_bus, gb, bb, gu, bu, s); break;
+    case 5: e = dispatch<true, false, true>(P, one, occ, M.rect, run_branch, run_bus, gb, bb, gu, bu, s); break;
+    case 6: e = dispatch<false, true, true>(P, one, occ, M.rect, run_branch, run_bus, gb, bb, gu, bu, s); break;
+    default: e = dispatch<true, true, true>(P, one, occ, M.rect, run_branch, run_bus, gb, bb, gu, bu, s); break;
     }
     if (e == cudaSuccess && M.reserve && (C || J) && (phases & 2)) {
         const int64_t threads = 32 * M.nres;
@@ -1156,10 +1463,20 @@ int launch_jtprod(Model &M, const double *x, const double *v, double *out, cudaS
     const int gu = grid_for(M.nbus_items + M.ngen_items, 128, 0, M.num_sms, 0);
     const bool one = M.ninst == 1;
     cudaError_t e = cudaSuccess;
-    if (M.nbr_items > 0)
-        e = one ? launch_pdl(jt_branch_kernel<true>, gb, 128, s, P) : launch_pdl(jt_branch_kernel<false>, gb, 128, s, P);
-    if (e == cudaSuccess)
-        e = one ? launch_pdl(jt_bus_kernel<true>, gu, 128, s, P) : launch_pdl(jt_bus_kernel<false>, gu, 128, s, P);
+    if (M.rect) {
+        if (M.nbr_items > 0)
+            e = one ? launch_pdl(jt_branch_kernel<true, true>, gb, 128, s, P)
+                    : launch_pdl(jt_branch_kernel<false, true>, gb, 128, s, P);
+        if (e == cudaSuccess)
+            e = one ? launch_pdl(jt_bus_kernel<true, true>, gu, 128, s, P)
+                    : launch_pdl(jt_bus_kernel<false, true>, gu, 128, s, P);
+    } else {
+        if (M.nbr_items > 0)
+            e = one ? launch_pdl(jt_branch_kernel<true>, gb, 128, s, P)
+                    : launch_pdl(jt_branch_kernel<false>, gb, 128, s, P);
+        if (e == cudaSuccess)
+            e = one ? launch_pdl(jt_bus_kernel<true>, gu, 128, s, P) : launch_pdl(jt_bus_kernel<false>, gu, 128, s, P);
+    }
     if (e != cudaSuccess) {
         set_error("kernel launch failed: %s", cudaGetErrorString(e));
         return OPF_ECUDA;
@@ -1169,8 +1486,8 @@ int launch_jtprod(Model &M, const double *x, const double *v, double *out, cudaS
 
 int launch_cons_setflows(Model &M, double *x, double *obj, double *grad, double *c, cudaStream_t s)
 {
-    if (M.ninst != 1) {
-        set_error("launch_cons_setflows: single-instance models only");
+    if (M.ninst != 1 || M.rect) {
+        set_error("launch_cons_setflows: single-instance polar models only");
         return OPF_ESTATE;
     }
     KParams P = base_params(M);
@@ -1205,7 +1522,11 @@ int launch_flows(Model &M, double *x, cudaStream_t s)
         return OPF_OK;
     KParams P = base_params(M);
     const int grid = grid_for(M.nbr_items, 128, 0, M.num_sms, 0);
-    if (M.ninst == 1)
+    if (M.rect && M.ninst == 1)
+        flows_kernel<true, true><<<grid, 128, 0, s>>>(P, x);
+    else if (M.rect)
+        flows_kernel<false, true><<<grid, 128, 0, s>>>(P, x);
+    else if (M.ninst == 1)
         flows_kernel<true><<<grid, 128, 0, s>>>(P, x);
     else
         flows_kernel<false><<<grid, 128, 0, s>>>(P, x);
@@ -1228,7 +1549,7 @@ int launch_flat_start(Model &M, double *x, cudaStream_t s)
     const int64_t total = M.nbr_items + M.nbus_items + M.ngen_items;
     const int block = 256;
     const int grid = grid_for(total, block, 8, M.num_sms, 0);
-    flat_kernel<<<grid, block, 0, s>>>(M.d, M.ninst, M.nbr_items, M.nbus_items, M.ngen_items, x);
+    flat_kernel<<<grid, block, 0, s>>>(M.d, M.ninst, M.nbr_items, M.nbus_items, M.ngen_items, M.rect ? 1 : 0, x);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         set_error("kernel launch failed: %s", cudaGetErrorString(e));

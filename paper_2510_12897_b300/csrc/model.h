@@ -21,6 +21,11 @@ enum : unsigned { W_OBJ = 1u, W_GRAD = 2u, W_CONS = 4u, W_JAC = 8u, W_HESS = 16u
 //   d_ma    d2L/dvm_i dva_i    (d2L/dvm_i dva_j = -d_ma)
 //   d_mm    d2L/dvm_i^2
 //   x_mm    d2L/dvm_i dvm_j
+// In the rectangular form the last four fields hold instead
+//   d_aa    d2L/dvr_i^2 (= d2L/dvi_i^2)
+//   d_ma    d2L/dvr_i dvr_j (= d2L/dvi_i dvi_j)
+//   d_mm    d2L/dvi_i dvr_j (d2L/dvr_i dvi_j is its negation)
+//   x_mm    unused
 struct __align__(16) ArcScratch {
     double p, q, d_aa, d_ma, d_mm, x_mm;
 };
@@ -70,6 +75,7 @@ struct DevArrays {
                                   // rows, inside one period's balance-row group
     double2 *y_ff = nullptr, *y_ft = nullptr, *y_tf = nullptr, *y_tt = nullptr;  // (G, B)
     double *rate2 = nullptr;      // rate_a^2
+    double2 *tanb = nullptr;      // (tan angmax, tan angmin), rectangular form only
     // buses
     int4 *bus_a = nullptr;        // (first slot, end slot, first gen entry, end gen entry)
     int4 *bus_b = nullptr;        // (balance-row offset, va-row offset, vm-row offset,
@@ -117,6 +123,7 @@ struct HostInst {
 struct Model {
     int32_t ninst = 0;
     bool on_device = false;  // false: structure only (no device arrays)
+    bool rect = false;       // rectangular voltages (vr, vi) instead of polar (va, vm)
     bool link = false;
     double link_ratio = 0.0;
     std::vector<double> link_ratios;   // per instance (entry 0 unused)

@@ -41,8 +41,9 @@ int validate(const opf_network &n, int s)
     }
     int64_t nb = n.nbus, nl = n.nbranch, ng = n.ngen;
     // every in-instance offset (variables, rows, Jacobian and Hessian values,
-    // scratch slots) must fit in 32 bits; the Jacobian is the largest
-    if ((int64_t)n.nperiod * (1 + 30 * nl + 2 * nb + 4 * ng) > INT32_MAX / 2 ||
+    // scratch slots) must fit in 32 bits; the Jacobian is the largest (the
+    // rectangular form's bound covers both forms)
+    if ((int64_t)n.nperiod * (1 + 36 * nl + 6 * nb + 4 * ng) > INT32_MAX / 2 ||
         (int64_t)n.nperiod * (2 * nb + 2 * ng + 4 * nl + 10 * nl + 2 * nb) > INT32_MAX / 2) {
         set_error("instance %d: too large for 32-bit in-instance offsets", s);
         return OPF_EINVAL;
@@ -173,6 +174,19 @@ int build_model(const opf_network *nets, int32_t ninst, const opf_batch_opts *op
     }
     const double link_ratio = opts ? opts->link_ratio : 0.0;
     const double reserve = opts ? opts->reserve : 0.0;
+    const int32_t form = opts ? opts->form : OPF_FORM_POLAR;
+    if (form != OPF_FORM_POLAR && form != OPF_FORM_RECT) {
+        set_error("form must be OPF_FORM_POLAR or OPF_FORM_RECT");
+        return OPF_EINVAL;
+    }
+    const bool rect = form == OPF_FORM_RECT;
+    if (rect)  // the tangent form of the angle rows needs limits inside (-pi/2, pi/2)
+        for (int s = 0; s < ninst; s++)
+            for (int k = 0; k < nets[s].nbranch; k++)
+                if (!(std::fabs(nets[s].br_angmin[k]) < M_PI / 2) || !(std::fabs(nets[s].br_angmax[k]) < M_PI / 2)) {
+                    set_error("instance %d: branch %d angle limits outside (-pi/2, pi/2) (rectangular form)", s, k);
+                    return OPF_EINVAL;
+                }
     if (!(link_ratio >= 0.0) || !std::isfinite(link_ratio) || !(reserve >= 0.0) || !std::isfinite(reserve)) {
         set_error("link_ratio and reserve must be finite and >= 0");
         return OPF_EINVAL;
@@ -193,6 +207,7 @@ int build_model(const opf_network *nets, int32_t ninst, const opf_batch_opts *op
 
     Model *M = new Model();
     M->ninst = ninst;
+    M->rect = rect;
     M->link = link;
     M->link_ratio = link_ratio;
     M->link_ratios.assign(ninst, link_ratio);
@@ -221,6 +236,7 @@ int build_model(const opf_network *nets, int32_t ninst, const opf_batch_opts *op
     std::vector<int32_t> bus_order;
     std::vector<double2> y_ff, y_ft, y_tf, y_tt, gsbs, pbnd, qbnd, vbnd;
     std::vector<double> rate2, Pd, Qd, c2, c1, c0;
+    std::vector<double2> tanb;
     std::vector<int32_t> gen_list, load_ptr, load_list, gen_busid;
     std::vector<uint8_t> slot_code;
     std::vector<int64_t> br_items(1, 0), bus_items(1, 0), gen_items(1, 0);
@@ -278,6 +294,8 @@ int build_model(const opf_network *nets, int32_t ninst, const opf_batch_opts *op
             y_tf.push_back(tf);
             y_tt.push_back(tt);
             rate2.push_back(n.br_rate_a[k] * n.br_rate_a[k]);
+            if (rect)
+                tanb.push_back(make_double2(std::tan(n.br_angmax[k]), std::tan(n.br_angmin[k])));
         }
 
         // ---- arcs sorted per bus by (far bus, arc id)
@@ -352,8 +370,12 @@ int build_model(const opf_network *nets, int32_t ninst, const opf_batch_opts *op
             bus_a.push_back(make_int4(p0, p1, H.gen_ptr[i], H.gen_ptr[i + 1]));
             bus_b.push_back(make_int4((int32_t)jsum, (int32_t)hva, (int32_t)hvm, nd | (nlt << 16)));
             bus_c.push_back(make_int2((int32_t)lastmask, nlow));
-            jsum += 1 + (H.gen_ptr[i + 1] - H.gen_ptr[i]) + (p1 - p0);
-            if (p1 > p0) {
+            // balance rows: the voltage entries (vm; or vr, vi), generators, arcs
+            jsum += (rect ? 2 : 1) + (H.gen_ptr[i + 1] - H.gen_ptr[i]) + (p1 - p0);
+            if (rect) {  // rows vr_i: lower vr_j, diagonal; rows vi_i: every vr_j, lower vi_j, diagonal
+                hva += nlt + 1;
+                hvm += nd + nlt + 1;
+            } else if (p1 > p0) {
                 hva += nlt + 1;
                 hvm += (nd + 1) + nlt + 1;
             } else {
@@ -364,15 +386,15 @@ int build_model(const opf_network *nets, int32_t ninst, const opf_batch_opts *op
             vbnd.push_back(make_double2(n.bus_vmin[i], n.bus_vmax[i]));
         }
 
-        // ---- each arc's +1 entry in its bus's balance row: after the vm entry
-        // and the bus's generators, arcs in ascending id
+        // ---- each arc's +1 entry in its bus's balance row: after the voltage
+        // entries and the bus's generators, arcs in ascending id
         {
             std::vector<int32_t> jb(na);
             std::vector<int32_t> ids;
             for (int i = 0; i < nb; i++) {
                 ids.assign(H.slot_arc.begin() + H.arc_ptr[i], H.slot_arc.begin() + H.arc_ptr[i + 1]);
                 std::sort(ids.begin(), ids.end());
-                const int base = jp_local[i] + 1 + (H.gen_ptr[i + 1] - H.gen_ptr[i]);
+                const int base = jp_local[i] + (rect ? 2 : 1) + (H.gen_ptr[i + 1] - H.gen_ptr[i]);
                 for (size_t r = 0; r < ids.size(); r++)
                     jb[ids[r]] = base + (int32_t)r;
             }
@@ -432,7 +454,7 @@ int build_model(const opf_network *nets, int32_t ninst, const opf_batch_opts *op
         }
 
         // ---- offsets
-        I.jP = (int64_t)nb + ng + na;
+        I.jP = (int64_t)(rect ? 2 * nb : nb) + ng + na;
         I.hva = hva;
         I.hvm = hvm;
         I.x0 = xo;
@@ -445,8 +467,11 @@ int build_model(const opf_network *nets, int32_t ninst, const opf_batch_opts *op
         I.link_x0 = 0;
         I.res_c = I.res_j = -1;
         xo += (int64_t)T * (2 * nb + 2 * ng + 2 * na);
-        co += (int64_t)T * (1 + 7 * (int64_t)nl + 2 * nb) + (H.ramp ? (int64_t)ng * (T - 1) : 0);
-        jo += (int64_t)T * (1 + 30 * (int64_t)nl + 2 * nb + 2 * ng) + (H.ramp ? 2 * (int64_t)ng * (T - 1) : 0);
+        // rectangular: one more angle row per branch and a magnitude row per bus
+        co += (int64_t)T * (1 + (rect ? 8 : 7) * (int64_t)nl + (rect ? 3 : 2) * nb) +
+              (H.ramp ? (int64_t)ng * (T - 1) : 0);
+        jo += (int64_t)T * (1 + (rect ? 36 : 30) * (int64_t)nl + (rect ? 6 : 2) * nb + 2 * ng) +
+              (H.ramp ? 2 * (int64_t)ng * (T - 1) : 0);
         ho += (int64_t)T * (hva + hvm + ng + 2 * (int64_t)na);
         so += (int64_t)na * T;
         po += (int64_t)nb * T;
@@ -510,7 +535,7 @@ int build_model(const opf_network *nets, int32_t ninst, const opf_batch_opts *op
 #define UP(field, vec)                           \
     if (!rc)                                     \
         rc = upload(*M, &d.field, vec);
-    UP(br, br) UP(y_ff, y_ff) UP(y_ft, y_ft) UP(y_tf, y_tf) UP(y_tt, y_tt) UP(rate2, rate2)
+    UP(br, br) UP(y_ff, y_ff) UP(y_ft, y_ft) UP(y_tf, y_tf) UP(y_tt, y_tt) UP(rate2, rate2) UP(tanb, tanb)
     std::vector<double2> trig;
     for (int k = -kTrigK; k <= kTrigK; k++)
         trig.push_back(make_double2(std::sin((double)k / kTrigScale), std::cos((double)k / kTrigScale)));
@@ -581,8 +606,8 @@ void jac_pattern(const Model &M, int64_t *rows, int64_t *cols)
         const Offs X = xoffs(H, I);
         const int64_t nb = H.nb, nl = H.nl, ng = H.ng, T = H.T, na = 2 * nl;
         int64_t r = I.c0;
-        for (int64_t t = 0; t < T; t++)
-            put(r++, X.va + H.ref + nb * t);
+        for (int64_t t = 0; t < T; t++)  // va_ref, or vi_ref (rectangular)
+            put(r++, (M.rect ? X.vm : X.va) + H.ref + nb * t);
         for (int grp = 0; grp < 4; grp++)
             for (int64_t t = 0; t < T; t++)
                 for (int64_t k = 0; k < nl; k++) {
@@ -596,16 +621,26 @@ void jac_pattern(const Model &M, int64_t *rows, int64_t *cols)
                     put(r, own);
                     r++;
                 }
-        for (int64_t t = 0; t < T; t++)
-            for (int64_t k = 0; k < nl; k++) {
-                int64_t f = H.f[k], b = H.t[k];
-                put(r, X.va + std::min(f, b) + nb * t);
-                put(r, X.va + std::max(f, b) + nb * t);
-                r++;
-            }
+        // angle rows: (va_lo, va_hi); rectangular: (vr_lo, vr_hi, vi_lo, vi_hi)
+        auto angle_rows = [&]() {
+            for (int64_t t = 0; t < T; t++)
+                for (int64_t k = 0; k < nl; k++) {
+                    int64_t f = H.f[k], b = H.t[k];
+                    put(r, X.va + std::min(f, b) + nb * t);
+                    put(r, X.va + std::max(f, b) + nb * t);
+                    if (M.rect) {
+                        put(r, X.vm + std::min(f, b) + nb * t);
+                        put(r, X.vm + std::max(f, b) + nb * t);
+                    }
+                    r++;
+                }
+        };
+        angle_rows();
         for (int pq = 0; pq < 2; pq++)
             for (int64_t t = 0; t < T; t++)
                 for (int i = 0; i < H.nb; i++) {
+                    if (M.rect)
+                        put(r, X.va + i + nb * t);
                     put(r, X.vm + i + nb * t);
                     for (int p = H.gen_ptr[i]; p < H.gen_ptr[i + 1]; p++)
                         put(r, (pq ? X.qg : X.pg) + H.gen_list[p] + ng * t);
@@ -623,6 +658,15 @@ void jac_pattern(const Model &M, int64_t *rows, int64_t *cols)
                     put(r, X.q + a + na * t);
                     r++;
                 }
+        if (M.rect) {  // lower angle rows, then the magnitude rows (vr_i, vi_i)
+            angle_rows();
+            for (int64_t t = 0; t < T; t++)
+                for (int64_t i = 0; i < nb; i++) {
+                    put(r, X.va + i + nb * t);
+                    put(r, X.vm + i + nb * t);
+                    r++;
+                }
+        }
         if (H.ramp)
             for (int64_t t = 1; t < T; t++)
                 for (int64_t g = 0; g < ng; g++) {
@@ -669,7 +713,28 @@ void hess_pattern(const Model &M, int64_t *rows, int64_t *cols)
         const InstDev &I = M.inst[s];
         const Offs X = xoffs(H, I);
         const int64_t nb = H.nb, ng = H.ng, T = H.T, na = 2 * (int64_t)H.nl;
-        for (int64_t t = 0; t < T; t++)  // rows va_i
+        if (M.rect) {
+            for (int64_t t = 0; t < T; t++)  // rows vr_i: lower vr_j, diagonal
+                for (int i = 0; i < H.nb; i++) {
+                    neighbours(H, i, nbr);
+                    for (int j : nbr)
+                        if (j < i)
+                            put(X.va + i + nb * t, X.va + j + nb * t);
+                    put(X.va + i + nb * t, X.va + i + nb * t);
+                }
+            for (int64_t t = 0; t < T; t++)  // rows vi_i: every vr_j, lower vi_j, diagonal
+                for (int i = 0; i < H.nb; i++) {
+                    neighbours(H, i, nbr);
+                    const int64_t r = X.vm + i + nb * t;
+                    for (int j : nbr)
+                        put(r, X.va + j + nb * t);
+                    for (int j : nbr)
+                        if (j < i)
+                            put(r, X.vm + j + nb * t);
+                    put(r, r);
+                }
+        }
+        for (int64_t t = 0; t < T && !M.rect; t++)  // rows va_i
             for (int i = 0; i < H.nb; i++) {
                 neighbours(H, i, nbr);
                 if (nbr.empty())
@@ -679,7 +744,7 @@ void hess_pattern(const Model &M, int64_t *rows, int64_t *cols)
                         put(X.va + i + nb * t, X.va + j + nb * t);
                 put(X.va + i + nb * t, X.va + i + nb * t);
             }
-        for (int64_t t = 0; t < T; t++)  // rows vm_i
+        for (int64_t t = 0; t < T && !M.rect; t++)  // rows vm_i
             for (int i = 0; i < H.nb; i++) {
                 neighbours(H, i, nbr);
                 int64_t r = X.vm + i + nb * t;
@@ -722,7 +787,10 @@ void bounds(const Model &M, double *xl, double *xu, double *gl, double *gu)
         const int64_t nb = H.nb, nl = H.nl, ng = H.ng, T = H.T, na = 2 * nl;
         for (int64_t t = 0; t < T; t++) {
             for (int64_t i = 0; i < nb; i++) {
-                if (xl) {
+                if (xl && M.rect) {  // -vmax <= vr, vi <= vmax
+                    xl[X.va + i + nb * t] = xl[X.vm + i + nb * t] = -H.vmax[i];
+                    xu[X.va + i + nb * t] = xu[X.vm + i + nb * t] = H.vmax[i];
+                } else if (xl) {
                     xl[X.va + i + nb * t] = -inf;
                     xu[X.va + i + nb * t] = inf;
                     xl[X.vm + i + nb * t] = H.vmin[i];
@@ -755,14 +823,25 @@ void bounds(const Model &M, double *xl, double *xu, double *gl, double *gu)
             gl[c] = gu[c] = 0.0;
         for (int64_t t = 0; t < T; t++)
             for (int64_t k = 0; k < nl; k++, c++) {
-                gl[c] = H.angmin[k];
-                gu[c] = H.angmax[k];
+                gl[c] = M.rect ? -inf : H.angmin[k];
+                gu[c] = M.rect ? 0.0 : H.angmax[k];
             }
         for (int64_t r = 0; r < 2 * nb * T; r++, c++)
             gl[c] = gu[c] = 0.0;
         for (int64_t r = 0; r < 2 * nl * T; r++, c++) {
             gl[c] = -inf;
             gu[c] = 0.0;
+        }
+        if (M.rect) {  // lower angle rows [0, inf], magnitude rows [vmin^2, vmax^2]
+            for (int64_t r = 0; r < nl * T; r++, c++) {
+                gl[c] = 0.0;
+                gu[c] = inf;
+            }
+            for (int64_t t = 0; t < T; t++)
+                for (int64_t i = 0; i < nb; i++, c++) {
+                    gl[c] = H.vmin[i] * H.vmin[i];
+                    gu[c] = H.vmax[i] * H.vmax[i];
+                }
         }
         if (H.ramp)
             for (int64_t t = 1; t < T; t++)

@@ -41,7 +41,10 @@ class OpfNetwork(ctypes.Structure):
 
 class OpfBatchOpts(ctypes.Structure):
     _fields_ = [("link_ratio", ctypes.c_double), ("link_ratios", ctypes.POINTER(ctypes.c_double)),
-                ("reserve", ctypes.c_double)]
+                ("reserve", ctypes.c_double), ("form", ctypes.c_int32)]
+
+
+FORMS = {"polar": 0, "rect": 1}
 
 
 class OpfLaunch(ctypes.Structure):
@@ -198,12 +201,17 @@ class Model:
 
     ``grids`` is one ``synth.Grid``-like object (attributes as in opf.h) or a
     list of them (a batch). ``structure_only=True`` builds the host layout
-    only (dims, patterns, bounds) without touching a GPU.
+    only (dims, patterns, bounds) without touching a GPU. ``form`` is
+    "polar" (va, vm) or "rect" (vr, vi).
     """
 
     def __init__(self, grids, link_ratio: float = 0.0, structure_only: bool = False, link_ratios=None,
-                 reserve: float = 0.0):
-        batch = isinstance(grids, (list, tuple)) or link_ratios is not None or reserve > 0.0
+                 reserve: float = 0.0, form: str = "polar"):
+        if form not in FORMS:
+            raise ValueError("form must be 'polar' or 'rect'")
+        self.form = form
+        batch = (isinstance(grids, (list, tuple)) or link_ratios is not None or reserve > 0.0
+                 or form != "polar")
         gl = list(grids) if isinstance(grids, (list, tuple)) else [grids]
         self._keep = []
         arr = (OpfNetwork * len(gl))(*[_net_struct(g, self._keep) for g in gl])
@@ -213,7 +221,8 @@ class Model:
         if link_ratios is not None:
             lr = np.ascontiguousarray(link_ratios, dtype=np.float64)
             self._keep.append(lr)
-        opts = OpfBatchOpts(float(link_ratio), None if lr is None else lr.ctypes.data_as(_f64p), float(reserve))
+        opts = OpfBatchOpts(float(link_ratio), None if lr is None else lr.ctypes.data_as(_f64p), float(reserve),
+                            FORMS[form])
         if structure_only:
             _check(L.opf_structure_create(arr, len(gl), ctypes.byref(opts), ctypes.byref(h)))
         elif batch:

@@ -399,10 +399,12 @@ def n_vars(g: Grid) -> int:
     return T * (2 * g.nbus + 2 * g.ngen + 4 * g.nbranch)
 
 
-def random_point(g: Grid, rng: np.random.Generator) -> np.ndarray:
+def random_point(g: Grid, rng: np.random.Generator, form: str = "polar") -> np.ndarray:
     """x = [va, vm, pg, qg, p, q], each group ``elem + count * period``:
     va ~ U(-pi/6, pi/6), vm ~ U(vmin, vmax), pg and qg uniform in their
-    bounds, p, q ~ U(-rate_a, rate_a) of the arc's branch."""
+    bounds, p, q ~ U(-rate_a, rate_a) of the arc's branch. ``form="rect"``
+    gives the same draw in rectangular voltages, vr = vm cos va and
+    vi = vm sin va in the places of va and vm."""
     T, nb, ng, nl = g.nperiod, g.nbus, g.ngen, g.nbranch
     na = 2 * nl
     va = rng.uniform(-math.pi / 6, math.pi / 6, (T, nb))
@@ -412,6 +414,8 @@ def random_point(g: Grid, rng: np.random.Generator) -> np.ndarray:
     rate = np.concatenate([g.br_rate_a, g.br_rate_a])
     p = rng.uniform(-rate, rate, (T, na))
     q = rng.uniform(-rate, rate, (T, na))
+    if form == "rect":
+        va, vm = vm * np.cos(va), vm * np.sin(va)
     return np.concatenate([a.ravel() for a in (va, vm, pg, qg, p, q)])
 
 

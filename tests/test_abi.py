@@ -197,3 +197,33 @@ def test_warm_create_rejects_bad_options(L):
     h = ctypes.c_void_p()
     _expect(opf.OPF_EINVAL, opf._check, wl.opf_warm_create(ctypes.byref(net2), ctypes.byref(warm.WarmOpts(128, 128, 1e3, 1e-4, 1e-2, 1.0, 0)), ctypes.byref(h)))
     _expect(opf.OPF_EINVAL, opf._check, wl.opf_warm_create(None, None, ctypes.byref(h)))
+
+
+def test_rect_structure_matches_oracle(oracle_mod):
+    """Rectangular form (host-only model, no GPU): dims, both patterns and
+    all bounds equal the oracle's bit for bit, for a single grid, a
+    multi-period grid with ramps and reserve, and an N-1 batch with
+    per-instance ratios."""
+    from paper_2510_12897_b300 import opf, synth
+    cases = [(synth.case30(general=True), {}),
+             (synth.multi_period(synth.case30(), 3, seed=2, ramp_ratio=0.2), dict(reserve=0.1)),
+             (synth.contingencies(synth.case30(), 3, seed=1), dict(link_ratios=[0, .1, .2, .3], reserve=0.1))]
+    for g, opts in cases:
+        M = opf.Model(g, structure_only=True, form="rect", **opts)
+        O = oracle_mod.Oracle(g, form="rect", **opts)
+        assert (M.n, M.m, M.nnzj, M.nnzh) == (O.n, O.m, O.nnzj, O.nnzh)
+        for a, b in zip(M.jac_pattern() + M.hess_pattern(), O.jac_pattern() + O.hess_pattern()):
+            np.testing.assert_array_equal(a, b)
+        for a, b in zip(M.bounds(), O.bounds()):
+            np.testing.assert_array_equal(a, b)
+
+
+def test_rect_form_validation():
+    from paper_2510_12897_b300 import opf, synth
+    g = synth.case30()
+    wide = g.copy(br_angmax=np.where(np.arange(g.nbranch) == 2, np.pi / 2, g.br_angmax))
+    opf.Model(wide, structure_only=True)
+    with pytest.raises(opf.OpfError, match="angle limits"):
+        opf.Model(wide, structure_only=True, form="rect")
+    with pytest.raises(ValueError):
+        opf.Model(g, structure_only=True, form="cartesian")

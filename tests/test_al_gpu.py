@@ -19,7 +19,7 @@ def torch():
     return t
 
 
-@pytest.mark.parametrize("case", ["case30g", "mp30"])
+@pytest.mark.parametrize("case", ["case30g", "mp30", "rect30g"])
 def test_al_iterations_match_oracle(torch, oracle_mod, case):
     """Twenty Adam steps around one multiplier update from the flat start
     with random multipliers: iterates, multipliers and statistics equal the
@@ -28,10 +28,11 @@ def test_al_iterations_match_oracle(torch, oracle_mod, case):
     noise / 1e-8 per step: the bound on |x_gpu - x_oracle| is 1e-7 after 20
     steps (observed far below), 1e-9 relative on the statistics."""
     from paper_2510_12897_b300 import al
-    g = synth.case30(general=True) if case == "case30g" else \
-        synth.multi_period(synth.case30(general=True), 3, seed=5, ramp_ratio=0.2)
-    M = opf.Model(g)
-    O = oracle_mod.Oracle(g)
+    g = synth.multi_period(synth.case30(general=True), 3, seed=5, ramp_ratio=0.2) if case == "mp30" \
+        else synth.case30(general=True)
+    form = "rect" if case == "rect30g" else "polar"  # the loop on the rectangular form's callbacks
+    M = opf.Model(g, form=form)
+    O = oracle_mod.Oracle(g, form=form)
     dev = torch.device("cuda")
     x = torch.empty(M.n, dtype=torch.float64, device=dev)
     M.flat_start(x)
