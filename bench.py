@@ -122,6 +122,20 @@ def eval_bytes(g, nnzh):
     return reads + writes
 
 
+def eval_bytes_rect(g, nnzh):
+    """Algorithmic bytes of one fused evaluation in the rectangular form:
+    as the polar one with one more angle row per branch and a magnitude row
+    per bus, their Jacobian entries, and the two tangent bounds per branch."""
+    nb, nl, ng, nload = g.nbus, g.nbranch, g.ngen, g.nload
+    na = 2 * nl
+    n = 2 * nb + 2 * ng + 2 * na
+    m = 1 + 8 * nl + 3 * nb
+    nnzj = 1 + 36 * nl + 6 * nb + 2 * ng
+    reads = 8 * n + 8 * m + 64 * nl + 16 * nb + 16 * nload + 28 * ng
+    writes = 8 * (1 + n + m + nnzj + nnzh)
+    return reads + writes
+
+
 def jac_hess_bytes(g, nnzh):
     """Algorithmic bytes of one Jacobian + Hessian evaluation: x, lambda,
     branch parameters, gs/bs, generator bus + c2; the two value arrays."""
@@ -524,6 +538,10 @@ def main():
     if not args.no_batched and rank == 0:
         batched = batched_vs_plain(torch, opf, synth, stream, dev, cpu=not args.no_cpu)
 
+    rect = None
+    if rank == 0:
+        rect = rect_summary(torch, opf, synth, stream, dev, R, reps, ms_per_step * 1000.0)
+
     warm_start = None
     if not args.no_warm and rank == 0:
         warm_start = warm_start_summary(torch, opf, synth, dev, args.warm_epochs)
@@ -555,7 +573,7 @@ def main():
             "warm_cache": {"ms_per_step": warm_ms, "evals_per_s": 1000.0 / warm_ms,
                            "note": "one buffer set, data resident in L2 (the solver-loop case)"},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * K, "clocks": clocks,
-            "batched": batched, "warm_start": warm_start,
+            "batched": batched, "warm_start": warm_start, "rect": rect,
         }
         print(json.dumps(line), flush=True)
     if dist:
@@ -688,6 +706,66 @@ def batched_vs_plain(torch, opf, synth, stream, dev, cpu=False):
         out["sc1k_501"]["cpu_oracle_threads"] = {
             "value": rate, "unit": "instance evals/s", "cores": cores, "kind": "oracle",
             "sample": f"{k} full evaluations of 64 of the 501 instances in {el:.1f} s, one thread per core"}
+    return out
+
+
+def rect_summary(torch, opf, synth, stream, dev, R, reps, polar_us):
+    """The rectangular form on the 10k grid: all callbacks per evaluation
+    over R rotating buffer sets (as the headline), its two phases, and a
+    32-scenario batch, each autotuned."""
+    f64 = torch.float64
+    g = synth.case10k()
+    rng = np.random.default_rng(99)
+    models = [opf.Model(g, form="rect") for _ in range(R)]
+    xs = [torch.tensor(synth.random_point(g, rng, form="rect"), device=dev) for _ in range(R)]
+    ls = [torch.tensor(rng.standard_normal(models[0].m), device=dev) for _ in range(R)]
+    outs = [[torch.empty(k, dtype=f64, device=dev) for k in (1, Mk.n, Mk.m, Mk.nnzj, Mk.nnzh)] for Mk in models]
+    best, _ = models[0].autotune(xs[0], ls[0], reps=20, stream=stream)
+    for Mk in models:
+        Mk.set_launch(**best)
+
+    def graph_us(fn):
+        gr = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(stream):
+            for k in range(R):
+                fn(k)
+            torch.cuda.synchronize()
+            with torch.cuda.graph(gr, stream=stream):
+                for k in range(R):
+                    fn(k)
+        gr.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for _ in range(reps):
+                gr.replay()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        return 1000.0 * e0.elapsed_time(e1) / (reps * R)
+
+    us = graph_us(lambda k: models[k].eval_all(xs[k], ls[k], 1.0, *outs[k], stream=stream))
+    br = graph_us(lambda k: models[k].eval_phases(opf.OPF_PHASE_BRANCH, xs[k], ls[k], 1.0, *outs[k], stream=stream))
+    bu = graph_us(lambda k: models[k].eval_phases(opf.OPF_PHASE_BUS, xs[k], ls[k], 1.0, *outs[k], stream=stream))
+    jh = graph_us(lambda k: models[k].eval_jac_hess(xs[k], ls[k], 1.0, outs[k][3], outs[k][4], stream=stream))
+    hbm = load_peaks()[0]
+    eb = eval_bytes_rect(g, models[0].nnzh)
+    out = {"workload": "10,000-bus grid, rectangular form, all callbacks", "launch": best,
+           "us": us, "evals_per_s": 1e6 / us, "vs_polar_same_protocol": polar_us / us,
+           "phase_us": {"branch": br, "bus": bu}, "jac_hess_us": jh,
+           "algorithmic_bytes": eb, "achieved_gbs": eb / (us * 1e-6) / 1e9,
+           "hbm_frac": eb / (us * 1e-6) / 1e9 / hbm}
+    del models, outs
+    sc = synth.scenarios(g, 32, seed=5)
+    B = opf.Model(sc, form="rect")
+    xb = torch.tensor(synth.random_point(sc, rng, form="rect"), device=dev)
+    lb = torch.tensor(rng.standard_normal(B.m), device=dev)
+    ob = [torch.empty(k, dtype=f64, device=dev) for k in (1, B.n, B.m, B.nnzj, B.nnzh)]
+    B.autotune(xb, lb, reps=5, stream=stream)
+    tb = graph_us(lambda k: B.eval_all(xb, lb, 1.0, *ob, stream=stream))
+    out["case10k_32_scenarios"] = {"batched_us": tb, "evals_per_s": 32e6 / tb,
+                                   "achieved_gbs": 32 * eb / (tb * 1e-6) / 1e9,
+                                   "hbm_frac": 32 * eb / (tb * 1e-6) / 1e9 / hbm}
     return out
 
 

@@ -375,19 +375,10 @@ __global__ void __launch_bounds__(OCC ? 256 : 512, OCC ? 3 : 1) branch_kernel(co
     }
 }
 
-// gradient of c wR + d wI in the order (vr_f, vr_t, vi_f, vi_t)
+// gradient of a rectangular row in the order (vr_f, vr_t, vi_f, vi_t)
 struct Grad4 {
     double rf, rt, jf, jt;
 };
-__device__ __forceinline__ Grad4 wgrad(double c, double d, double vrf, double vrt, double vif, double vit)
-{
-    Grad4 g;
-    g.rf = fma(c, vrt, neg(d * vit));
-    g.rt = fma(c, vrf, d * vif);
-    g.jf = fma(c, vit, d * vrt);
-    g.jt = fma(c, vif, neg(d * vrf));
-    return g;
-}
 
 // the Jacobian entries of a rectangular row, columns ascending:
 // (vr_lo, vr_hi, vi_lo, vi_hi), then the own flow variable if `own`
@@ -496,34 +487,33 @@ __global__ void __launch_bounds__(512, 1) rect_branch_kernel(const KParams P)
             const bool f_lo = f < b;
             double *J = P.jac + I.j0;
             double *Jf = J + (T + 5 * rk);
-            // row p_fr - P_fr: a = -Gff (from end), c = -Gft, d = -Bft
-            Grad4 g = wgrad(neg(Yft.x), neg(Yft.y), vrf, vrt, vif, vit);
-            const double pa = neg(twice(Yff.x));
-            g.rf = fma(pa, vrf, g.rf);
-            g.jf = fma(pa, vif, g.jf);
-            put_rect(Jf, f_lo, g, true);
-            // row q_fr - Q_fr: a = Bff, c = Bft, d = -Gft
-            g = wgrad(Yft.y, neg(Yft.x), vrf, vrt, vif, vit);
-            const double qa = twice(Yff.y);
-            g.rf = fma(qa, vrf, g.rf);
-            g.jf = fma(qa, vif, g.jf);
-            put_rect(Jf + 5 * nlT, f_lo, g, true);
-            // row p_to - P_to: a = -Gtt (to end), c = -Gtf, d = Btf
-            g = wgrad(neg(Ytf.x), Ytf.y, vrf, vrt, vif, vit);
-            const double pb = neg(twice(Ytt.x));
-            g.rt = fma(pb, vrt, g.rt);
-            g.jt = fma(pb, vit, g.jt);
-            put_rect(Jf + 10 * nlT, f_lo, g, true);
-            // row q_to - Q_to: a = Btt, c = Btf, d = Gtf
-            g = wgrad(Ytf.y, Ytf.x, vrf, vrt, vif, vit);
-            const double qb = twice(Ytt.y);
-            g.rt = fma(qb, vrt, g.rt);
-            g.jt = fma(qb, vit, g.jt);
-            put_rect(Jf + 15 * nlT, f_lo, g, true);
-            // angle rows: c = -tan(limit), d = 1
-            put_rect(J + (T + 20 * nlT + 4 * rk), f_lo, wgrad(neg(tan_.x), 1.0, vrf, vrt, vif, vit), false);
-            put_rect(J + (T + 28 * nlT + 2 * jP * T + 4 * rk), f_lo, wgrad(neg(tan_.y), 1.0, vrf, vrt, vif, vit),
-                     false);
+            // With z = c + j d the (c, d) part of a row's gradient is
+            // (vr_f, vi_f) <- z V_t and (vr_t, -vi_t) <- z conj(V_f). The
+            // rows p_fr - P_fr and q_fr - Q_fr have z = -Yft and -j Yft, the
+            // rows p_to - P_to and q_to - Q_to z = -conj(Ytf) and j conj(Ytf):
+            // two complex products per end serve both of its rows.
+            const double y1r = fma(Yft.x, vrt, neg(Yft.y * vit)), y1i = fma(Yft.x, vit, Yft.y * vrt);  // Yft V_t
+            const double y2r = fma(Yft.x, vrf, Yft.y * vif), y2i = fma(Yft.y, vrf, neg(Yft.x * vif));  // Yft conj(V_f)
+            const double z1r = fma(Ytf.x, vrt, Ytf.y * vit), z1i = fma(Ytf.x, vit, neg(Ytf.y * vrt));  // conj(Ytf) V_t
+            const double z2r = fma(Ytf.x, vrf, neg(Ytf.y * vif));                                     // conj(Ytf V_f)
+            const double z2i = neg(fma(Ytf.x, vif, Ytf.y * vrf));
+            const double pa = neg(twice(Yff.x)), qa = twice(Yff.y);  // the from-end's own |V_f|^2 terms
+            const double pb = neg(twice(Ytt.x)), qb = twice(Ytt.y);
+            Grad4 g;
+            g.rf = fma(pa, vrf, neg(y1r)); g.jf = fma(pa, vif, neg(y1i)); g.rt = neg(y2r); g.jt = y2i;
+            put_rect(Jf, f_lo, g, true);                        // p_fr - P_fr
+            g.rf = fma(qa, vrf, y1i); g.jf = fma(qa, vif, neg(y1r)); g.rt = y2i; g.jt = y2r;
+            put_rect(Jf + 5 * nlT, f_lo, g, true);              // q_fr - Q_fr
+            g.rf = neg(z1r); g.jf = neg(z1i); g.rt = fma(pb, vrt, neg(z2r)); g.jt = fma(pb, vit, z2i);
+            put_rect(Jf + 10 * nlT, f_lo, g, true);             // p_to - P_to
+            g.rf = neg(z1i); g.jf = z1r; g.rt = fma(qb, vrt, neg(z2i)); g.jt = fma(qb, vit, neg(z2r));
+            put_rect(Jf + 15 * nlT, f_lo, g, true);             // q_to - Q_to
+            // angle rows, z = -tan(limit) + j: one FMA per entry
+            const double tu = neg(tan_.x), tl = neg(tan_.y);
+            g.rf = fma(tu, vrt, neg(vit)); g.jf = fma(tu, vit, vrt); g.rt = fma(tu, vrf, vif); g.jt = fma(tu, vif, neg(vrf));
+            put_rect(J + (T + 20 * nlT + 4 * rk), f_lo, g, false);
+            g.rf = fma(tl, vrt, neg(vit)); g.jf = fma(tl, vit, vrt); g.rt = fma(tl, vrf, vif); g.jt = fma(tl, vif, neg(vrf));
+            put_rect(J + (T + 28 * nlT + 2 * jP * T + 4 * rk), f_lo, g, false);
             double *Jb = J + (T + 24 * nlT + jP * ct);  // +1 of each arc in its bus's P and Q rows
             Jb[cur.jb.x] = 1.0;
             Jb[cur.jb.y] = 1.0;
