@@ -66,6 +66,11 @@ def parse():
     p.add_argument("--profile-batched", type=int, default=0, metavar="REPS",
                    help="profiling aid: only run REPS plain evaluations of the 10k-bus grid "
                         "with 32 load scenarios in one model, then exit")
+    p.add_argument("--profile-single", type=int, default=0, metavar="REPS",
+                   help="profiling aid: only run REPS plain evaluations of the 10k-bus grid "
+                        "(default launch shape), then exit")
+    p.add_argument("--form", choices=["polar", "rect"], default="polar",
+                   help="voltage form of the profiling aids' models")
     return p.parse_args()
 
 
@@ -348,17 +353,19 @@ def main():
         dist.barrier()
     dev = torch.device("cuda", local)
     f64 = torch.float64
-    if args.profile_batched:
-        sc = synth.scenarios(synth.case10k(), 32, seed=5)
-        Mb = opf.Model(sc)
+    if args.profile_batched or args.profile_single:
+        g = synth.case10k()
+        sc = synth.scenarios(g, 32, seed=5) if args.profile_batched else g
+        Mb = opf.Model(sc, form=args.form)
         rng = np.random.default_rng(7)
-        xb = torch.tensor(synth.random_point(sc, rng), device=dev)
+        xb = torch.tensor(synth.random_point(sc, rng, form=args.form), device=dev)
         lb = torch.tensor(rng.standard_normal(Mb.m), device=dev)
         ob = [torch.empty(k, dtype=f64, device=dev) for k in (1, Mb.n, Mb.m, Mb.nnzj, Mb.nnzh)]
-        for _ in range(args.profile_batched):
+        for _ in range(args.profile_batched or args.profile_single):
             Mb.eval_all(xb, lb, 1.0, *ob)
         torch.cuda.synchronize()
-        print(json.dumps({"profile_batched": args.profile_batched, "n": Mb.n, "m": Mb.m}))
+        print(json.dumps({"profile": args.profile_batched or args.profile_single, "form": args.form,
+                          "n": Mb.n, "m": Mb.m}))
         return
 
     g = synth.case10k(args.seed)

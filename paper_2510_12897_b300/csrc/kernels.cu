@@ -396,8 +396,8 @@ __device__ __forceinline__ void put_rect(double *J, bool f_lo, const Grad4 &g, b
 // slots as the polar branch kernel, without trigonometry. Row groups per
 // instance: ref, four flow groups, upper angle rows, P and Q balance, two
 // thermal groups, lower angle rows, magnitude rows, ramp rows.
-template <bool CONS, bool JAC, bool HESS, bool ONE>
-__global__ void __launch_bounds__(512, 1) rect_branch_kernel(const KParams P)
+template <bool CONS, bool JAC, bool HESS, bool ONE, bool OCC>
+__global__ void __launch_bounds__(OCC ? 256 : 512, OCC ? 3 : 1) rect_branch_kernel(const KParams P)
 {
     cudaTriggerProgrammaticLaunchCompletion();
     const DevArrays &d = P.d;
@@ -1301,10 +1301,13 @@ cudaError_t dispatch(const KParams &P, bool one, bool occ, bool rect, bool run_b
                      int bb, int gu, int bu, cudaStream_t s)
 {
     cudaError_t e = cudaSuccess;
-    if (rect) {  // one register budget; the bus phase's rectangular variant
-        if (run_branch)
-            e = one ? launch_pdl(rect_branch_kernel<C, J, H, true>, gb, bb, s, P)
-                    : launch_pdl(rect_branch_kernel<C, J, H, false>, gb, bb, s, P);
+    if (rect) {  // the rectangular branch kernel (two register budgets) and bus variant
+        if (run_branch && occ)
+            e = one ? launch_pdl(rect_branch_kernel<C, J, H, true, true>, gb, bb, s, P)
+                    : launch_pdl(rect_branch_kernel<C, J, H, false, true>, gb, bb, s, P);
+        else if (run_branch)
+            e = one ? launch_pdl(rect_branch_kernel<C, J, H, true, false>, gb, bb, s, P)
+                    : launch_pdl(rect_branch_kernel<C, J, H, false, false>, gb, bb, s, P);
         if (e != cudaSuccess || !run_bus)
             return e;
         return one ? launch_pdl(bus_kernel<C, J, H, true, true>, gu, bu, s, P)
