@@ -20,6 +20,11 @@ Parity status of each function (what pins it lives in tests/test_oracle_*.py):
                  Jacobian; trigonometric closed form of the angle rows; the
                  exact second-order expansion of the (quadratic) Lagrangian;
                  differences of cons and of grad + J^T lambda
+  storage        state-of-charge rows zero along a recurrence-integrated
+                 schedule; loss row zero at numpy's root of the loss balance
+                 and its loss term r |I|^2 in complex arithmetic; balance rows
+                 grow by ps, qs only; complementarity product; bounds; sizes;
+                 differences of cons and of grad + J^T lambda
 """
 from __future__ import annotations
 
@@ -67,6 +72,16 @@ class OraNet(ctypes.Structure):
     ]
 
 
+class OraStorage(ctypes.Structure):
+    _fields_ = [
+        ("nstor", ctypes.c_int32), ("bus", _i32p),
+        ("energy_rating", _f64p), ("charge_rating", _f64p), ("discharge_rating", _f64p),
+        ("thermal_rating", _f64p), ("eta_c", _f64p), ("eta_d", _f64p), ("r", _f64p),
+        ("p_loss", _f64p), ("qmin", _f64p), ("qmax", _f64p), ("e_init", _f64p),
+        ("dt", ctypes.c_double),
+    ]
+
+
 _lib = None
 
 
@@ -82,6 +97,9 @@ def lib():
         L.ora_create3.restype = ctypes.c_void_p
         L.ora_create3.argtypes = [ctypes.POINTER(OraNet), ctypes.c_int32, ctypes.c_double, _f64p, ctypes.c_double,
                                   ctypes.c_int32]
+        L.ora_create4.restype = ctypes.c_void_p
+        L.ora_create4.argtypes = [ctypes.POINTER(OraNet), ctypes.c_int32, ctypes.c_double, _f64p, ctypes.c_double,
+                                  ctypes.c_int32, ctypes.POINTER(OraStorage), ctypes.c_int32]
         L.ora_destroy.argtypes = [ctypes.c_void_p]
         L.ora_error.restype = ctypes.c_char_p
         L.ora_dims.argtypes = [ctypes.c_void_p, _i64p, _i64p, _i64p, _i64p]
@@ -123,11 +141,12 @@ class Oracle:
     per instance instead); ``reserve > 0`` adds per instance and period the
     row sum_g pg_g <= sum_g pmax_g - reserve * (total Pd). ``form``: "polar"
     (va, vm) or "rect" (vr, vi, with the angle and magnitude rows of the
-    rectangular model).
+    rectangular model). Grids carrying ``storage`` get the storage variables
+    and rows; ``compl`` adds the complementarity rows sc sd <= 0.
     """
 
     def __init__(self, grids, link_ratio: float = 0.0, link_ratios=None, reserve: float = 0.0,
-                 form: str = "polar"):
+                 form: str = "polar", compl: bool = False):
         if form not in ("polar", "rect"):
             raise ValueError("form must be 'polar' or 'rect'")
         self.form = form
@@ -143,9 +162,15 @@ class Oracle:
         if link_ratios is not None:
             lr = np.ascontiguousarray(link_ratios, dtype=np.float64)
             self._keep.append(lr)
-        self.ctx = lib().ora_create3(nets, len(grids), float(link_ratio),
+        stor = None
+        if any(getattr(g, "storage", None) is not None for g in grids):
+            stor = (OraStorage * len(grids))()
+            for k, g in enumerate(grids):
+                self._fill_storage(stor[k], getattr(g, "storage", None))
+        self._stor = stor
+        self.ctx = lib().ora_create4(nets, len(grids), float(link_ratio),
                                      None if lr is None else lr.ctypes.data_as(_f64p), float(reserve),
-                                     1 if form == "rect" else 0)
+                                     1 if form == "rect" else 0, stor, 1 if compl else 0)
         if not self.ctx:
             raise ValueError("oracle: " + lib().ora_error().decode())
         n, m, nj, nh = (ctypes.c_int64() for _ in range(4))
@@ -178,6 +203,24 @@ class Oracle:
         d.load_bus = i(g.load_bus)
         d.pd, d.qd = f(g.load_pd), f(g.load_qd)
         d.ramp_ratio = float(g.ramp_ratio)
+
+    def _fill_storage(self, d, st):
+        if st is None:
+            d.nstor, d.dt = 0, 1.0
+            return
+        keep = self._keep
+
+        def f(a):
+            a = _f64(a)
+            keep.append(a)
+            return _p(a, _f64p)
+
+        b = _i32(st.bus)
+        keep.append(b)
+        d.nstor, d.bus, d.dt = st.nstor, _p(b, _i32p), float(st.dt)
+        for name in ("energy_rating", "charge_rating", "discharge_rating", "thermal_rating", "eta_c", "eta_d",
+                     "r", "p_loss", "qmin", "qmax", "e_init"):
+            setattr(d, name, f(getattr(st, name)))
 
     def __del__(self):
         if getattr(self, "ctx", None) and _lib is not None:

@@ -31,6 +31,16 @@
  *     the thermal rows), w = V_f conj(V_t), valid for limits inside
  *     (-pi/2, pi/2); a voltage-magnitude row vmin^2 <= vr^2 + vi^2 <= vmax^2
  *     per bus (after those); demand terms gs |V|^2 and -bs |V|^2.
+ *   - multi-period with storage (Sec. III-C-2, the storage model of Geth,
+ *     Coffrin and Fobes the paper builds on, in polar voltages): per unit and
+ *     period ps, qs (power drawn from the bus, added to its balance rows),
+ *     sc, sd in [0, rating], se in [0, energy rating]; rows: state of charge
+ *     se_t - se_{t-1} - dt (eta_c sc_t - sd_t / eta_d) = 0 (the initial
+ *     energy in place of se_{-1}), converter losses
+ *     ps + sd - sc - r (ps^2 + qs^2) / vm^2 = p_loss (the loss through a
+ *     series resistance r carrying the current |S| / vm), thermal
+ *     ps^2 + qs^2 <= rating^2, and, when requested, the complementarity
+ *     sc sd <= 0 (with sc, sd >= 0 the inequality form of sc sd = 0).
  *
  * Where the paper is silent this oracle takes these readings: a flow row is
  * the arc variable minus the flow function; the thermal row is
@@ -73,12 +83,15 @@ enum { G_REF, G_FPF, G_FQF, G_FPT, G_FQT, G_ANG, G_PB, G_QB, G_THF, G_THT, G_ANL
 
 typedef struct {
     ora_net net;     /* pointers into the owned copies below */
-    void *own[32];
+    void *own[64];
     int nown;
     int64_t xoff, coff;  /* first variable / first row of this instance */
     int64_t n, m;
     int ramp;
     int rect;            /* rectangular voltages: vr, vi in the places of va, vm */
+    int ns, compl;       /* storage units; complementarity rows present */
+    ora_storage st;      /* pointers into the owned copies */
+    int64_t st_row;      /* first storage row, relative to coff */
     double *Pd, *Qd;     /* per bus and period: [nperiod][nbus] */
 } inst_t;
 
@@ -127,6 +140,21 @@ static int64_t v_q(const inst_t *s, int64_t a, int64_t t)
     int64_t T = s->net.nperiod, nbT = (int64_t)s->net.nbus * T, ngT = (int64_t)s->net.ngen * T;
     int64_t naT = 2 * (int64_t)s->net.nbranch * T;
     return s->xoff + 2 * nbT + 2 * ngT + naT + a + 2 * (int64_t)s->net.nbranch * t;
+}
+
+/* storage variables of unit k in period t: ps, qs, sc, sd, se after q */
+static int64_t v_st(const inst_t *s, int which, int64_t k, int64_t t)
+{
+    int64_t T = s->net.nperiod;
+    int64_t base = T * (2 * (int64_t)s->net.nbus + 2 * (int64_t)s->net.ngen + 4 * (int64_t)s->net.nbranch);
+    return s->xoff + base + (int64_t)which * s->ns * T + k + (int64_t)s->ns * t;
+}
+enum { V_PS, V_QS, V_SC, V_SD, V_SE };
+/* storage rows of unit k in period t: state of charge, losses, thermal, complementarity */
+enum { R_SOC, R_LOSS, R_STH, R_CMP };
+static int64_t row_st(const inst_t *s, int which, int64_t k, int64_t t)
+{
+    return s->coff + s->st_row + (int64_t)which * s->ns * s->net.nperiod + k + (int64_t)s->ns * t;
 }
 
 /* row of element e of group grp in period t (ramp: t = 1..T-1) */
@@ -440,6 +468,41 @@ ora_ctx *ora_create2(const ora_net *nets, int32_t ninst, double link_ratio, cons
 ora_ctx *ora_create3(const ora_net *nets, int32_t ninst, double link_ratio, const double *link_ratios,
                      double reserve, int32_t form)
 {
+    return ora_create4(nets, ninst, link_ratio, link_ratios, reserve, form, NULL, 0);
+}
+
+static int validate_storage(const ora_storage *st, int nbus)
+{
+    for (int k = 0; k < st->nstor; k++) {
+        if (st->bus[k] < 0 || st->bus[k] >= nbus) {
+            set_err("storage %d bus out of range", k);
+            return -1;
+        }
+        if (!(st->eta_c[k] > 0.0) || !(st->eta_d[k] > 0.0) || !(st->energy_rating[k] >= 0.0) ||
+            !(st->charge_rating[k] >= 0.0) || !(st->discharge_rating[k] >= 0.0) ||
+            !(st->thermal_rating[k] >= 0.0) || !(st->r[k] >= 0.0)) {
+            set_err("storage %d: efficiencies must be > 0 and ratings, r >= 0", k);
+            return -1;
+        }
+    }
+    if (!(st->dt > 0.0)) {
+        set_err("storage dt must be > 0");
+        return -1;
+    }
+    return 0;
+}
+
+ora_ctx *ora_create4(const ora_net *nets, int32_t ninst, double link_ratio, const double *link_ratios,
+                     double reserve, int32_t form, const ora_storage *stor, int32_t compl)
+{
+    if (stor && form != 0) {
+        set_err("storage needs the polar form");
+        return NULL;
+    }
+    if (stor)
+        for (int s = 0; s < ninst; s++)
+            if (validate_storage(&stor[s], nets[s].nbus))
+                return NULL;
     if (form != 0 && form != 1) {
         set_err("form must be 0 (polar) or 1 (rectangular)");
         return NULL;
@@ -525,6 +588,29 @@ ora_ctx *ora_create3(const ora_net *nets, int32_t ninst, double link_ratio, cons
         S->m = T * (1 + 7 * nl + 2 * nb) + (S->ramp ? ng * (T - 1) : 0);
         if (S->rect) /* the lower angle rows and the voltage-magnitude rows */
             S->m += T * (nl + nb);
+        S->ns = stor ? stor[s].nstor : 0;
+        S->compl = compl != 0 && S->ns > 0;
+        if (S->ns) {
+            const ora_storage *a = &stor[s];
+            ora_storage *b = &S->st;
+            int64_t k = S->ns;
+            *b = *a;
+            b->bus = own_copy(S, a->bus, sizeof(int32_t) * k);
+            b->energy_rating = own_copy(S, a->energy_rating, sizeof(double) * k);
+            b->charge_rating = own_copy(S, a->charge_rating, sizeof(double) * k);
+            b->discharge_rating = own_copy(S, a->discharge_rating, sizeof(double) * k);
+            b->thermal_rating = own_copy(S, a->thermal_rating, sizeof(double) * k);
+            b->eta_c = own_copy(S, a->eta_c, sizeof(double) * k);
+            b->eta_d = own_copy(S, a->eta_d, sizeof(double) * k);
+            b->r = own_copy(S, a->r, sizeof(double) * k);
+            b->p_loss = own_copy(S, a->p_loss, sizeof(double) * k);
+            b->qmin = own_copy(S, a->qmin, sizeof(double) * k);
+            b->qmax = own_copy(S, a->qmax, sizeof(double) * k);
+            b->e_init = own_copy(S, a->e_init, sizeof(double) * k);
+            S->st_row = S->m;
+            S->n += 5 * k * T;
+            S->m += (3 + S->compl) * k * T;
+        }
         S->xoff = xo;
         S->coff = co;
         xo += S->n;
@@ -544,7 +630,7 @@ ora_ctx *ora_create3(const ora_net *nets, int32_t ninst, double link_ratio, cons
         const ora_net *n = &C->in[s].net;
         int64_t T = n->nperiod;
         cap += T * (1 + 40 * (int64_t)n->nbranch + 6 * (int64_t)n->nbus + 2 * (int64_t)n->ngen) +
-               2 * (int64_t)n->ngen * T;
+               2 * (int64_t)n->ngen * T + 16 * (int64_t)C->in[s].ns * T;
     }
     cap += C->link ? 2 * (int64_t)nets[0].ngen * ninst : 0;
     if (C->reserve > 0.0)
@@ -610,6 +696,27 @@ ora_ctx *ora_create3(const ora_net *nets, int32_t ninst, double link_ratio, cons
                     push(keys, &cnt, N, row_of(S, G_RAMP, g, t), v_pg(S, g, t));
                     push(keys, &cnt, N, row_of(S, G_RAMP, g, t), v_pg(S, g, t - 1));
                 }
+            for (int k = 0; k < S->ns; k++) { /* storage: balance terms and rows */
+                int b = S->st.bus[k];
+                push(keys, &cnt, N, row_of(S, G_PB, b, t), v_st(S, V_PS, k, t));
+                push(keys, &cnt, N, row_of(S, G_QB, b, t), v_st(S, V_QS, k, t));
+                int64_t r = row_st(S, R_SOC, k, t);
+                push(keys, &cnt, N, r, v_st(S, V_SC, k, t));
+                push(keys, &cnt, N, r, v_st(S, V_SD, k, t));
+                push(keys, &cnt, N, r, v_st(S, V_SE, k, t));
+                if (t >= 1)
+                    push(keys, &cnt, N, r, v_st(S, V_SE, k, t - 1));
+                r = row_st(S, R_LOSS, k, t);
+                push(keys, &cnt, N, r, v_vm(S, b, t));
+                for (int w = V_PS; w <= V_SD; w++)
+                    push(keys, &cnt, N, r, v_st(S, w, k, t));
+                push(keys, &cnt, N, row_st(S, R_STH, k, t), v_st(S, V_PS, k, t));
+                push(keys, &cnt, N, row_st(S, R_STH, k, t), v_st(S, V_QS, k, t));
+                if (S->compl) {
+                    push(keys, &cnt, N, row_st(S, R_CMP, k, t), v_st(S, V_SC, k, t));
+                    push(keys, &cnt, N, row_st(S, R_CMP, k, t), v_st(S, V_SD, k, t));
+                }
+            }
         }
     }
     if (C->link)
@@ -643,7 +750,7 @@ ora_ctx *ora_create3(const ora_net *nets, int32_t ninst, double link_ratio, cons
         /* per branch: 10 (polar) or 12 (rectangular, 6 per end) voltage pairs
          * and 4 thermal diagonals; 2 per bus; 1 per generator */
         cap += (int64_t)n->nperiod * (12 * (int64_t)n->nbranch + 2 * (int64_t)n->nbus + n->ngen +
-                                      4 * (int64_t)n->nbranch);
+                                      4 * (int64_t)n->nbranch + 6 * (int64_t)C->in[s].ns);
     }
     keys = malloc(sizeof(int64_t) * (cap + 1));
     cnt = 0;
@@ -683,6 +790,17 @@ ora_ctx *ora_create3(const ora_net *nets, int32_t ninst, double link_ratio, cons
             for (int64_t a = 0; a < 2 * nl; a++) { /* thermal terms */
                 push(keys, &cnt, N, v_p(S, a, t), v_p(S, a, t));
                 push(keys, &cnt, N, v_q(S, a, t), v_q(S, a, t));
+            }
+            for (int k = 0; k < S->ns; k++) { /* storage losses (ps, qs, vm), thermal, complementarity */
+                int64_t vm = v_vm(S, S->st.bus[k], t);
+                int64_t ps = v_st(S, V_PS, k, t), qs = v_st(S, V_QS, k, t);
+                push(keys, &cnt, N, ps, vm);
+                push(keys, &cnt, N, ps, ps);
+                push(keys, &cnt, N, qs, vm);
+                push(keys, &cnt, N, qs, qs);
+                push(keys, &cnt, N, vm, vm);
+                if (S->compl)
+                    push(keys, &cnt, N, v_st(S, V_SD, k, t), v_st(S, V_SC, k, t));
             }
         }
     }
@@ -779,6 +897,28 @@ void ora_bounds(const ora_ctx *C, double *xl, double *xu, double *gl, double *gu
                     gl[row_of(S, G_RAMP, g, t)] = -d;
                     gu[row_of(S, G_RAMP, g, t)] = d;
                 }
+            for (int k = 0; k < S->ns; k++) {
+                const ora_storage *st = &S->st;
+                double S2 = st->thermal_rating[k];
+                xl[v_st(S, V_PS, k, t)] = -S2;
+                xu[v_st(S, V_PS, k, t)] = S2;
+                xl[v_st(S, V_QS, k, t)] = st->qmin[k];
+                xu[v_st(S, V_QS, k, t)] = st->qmax[k];
+                xl[v_st(S, V_SC, k, t)] = 0.0;
+                xu[v_st(S, V_SC, k, t)] = st->charge_rating[k];
+                xl[v_st(S, V_SD, k, t)] = 0.0;
+                xu[v_st(S, V_SD, k, t)] = st->discharge_rating[k];
+                xl[v_st(S, V_SE, k, t)] = 0.0;
+                xu[v_st(S, V_SE, k, t)] = st->energy_rating[k];
+                gl[row_st(S, R_SOC, k, t)] = gu[row_st(S, R_SOC, k, t)] = t == 0 ? st->e_init[k] : 0.0;
+                gl[row_st(S, R_LOSS, k, t)] = gu[row_st(S, R_LOSS, k, t)] = st->p_loss[k];
+                gl[row_st(S, R_STH, k, t)] = -INFINITY;
+                gu[row_st(S, R_STH, k, t)] = S2 * S2;
+                if (S->compl) {
+                    gl[row_st(S, R_CMP, k, t)] = -INFINITY;
+                    gu[row_st(S, R_CMP, k, t)] = 0.0;
+                }
+            }
         }
     }
     if (C->link) {
@@ -906,6 +1046,24 @@ void ora_cons(const ora_ctx *C, const double *x, double *c, double *scale)
                     double a = x[v_pg(S, g, t)], b = x[v_pg(S, g, t - 1)];
                     ADD(row_of(S, G_RAMP, g, t), a - b, fabs(a) + fabs(b));
                 }
+            for (int k = 0; k < S->ns; k++) {
+                const ora_storage *st = &S->st;
+                int bus = st->bus[k];
+                double ps = x[v_st(S, V_PS, k, t)], qs = x[v_st(S, V_QS, k, t)];
+                double sc = x[v_st(S, V_SC, k, t)], sd = x[v_st(S, V_SD, k, t)];
+                double se = x[v_st(S, V_SE, k, t)], sp = t ? x[v_st(S, V_SE, k, t - 1)] : 0.0;
+                double vm = x[v_vm(S, bus, t)];
+                ADD(row_of(S, G_PB, bus, t), ps, fabs(ps)); /* drawn from the bus */
+                ADD(row_of(S, G_QB, bus, t), qs, fabs(qs));
+                double chg = st->dt * (st->eta_c[k] * sc - sd / st->eta_d[k]);
+                ADD(row_st(S, R_SOC, k, t), se - sp - chg,
+                    fabs(se) + fabs(sp) + st->dt * (st->eta_c[k] * fabs(sc) + fabs(sd) / st->eta_d[k]));
+                double loss = st->r[k] * (ps * ps + qs * qs) / (vm * vm);
+                ADD(row_st(S, R_LOSS, k, t), ps + sd - sc - loss, fabs(ps) + fabs(sd) + fabs(sc) + loss);
+                ADD(row_st(S, R_STH, k, t), ps * ps + qs * qs, ps * ps + qs * qs);
+                if (S->compl)
+                    ADD(row_st(S, R_CMP, k, t), sc * sd, fabs(sc * sd));
+            }
         }
     }
     if (C->link) {
@@ -1035,6 +1193,35 @@ int ora_jac(const ora_ctx *C, const double *x, double *vals, double *scale)
                     acc(&A, row_of(S, G_RAMP, g, t), v_pg(S, g, t), 1.0, 1.0);
                     acc(&A, row_of(S, G_RAMP, g, t), v_pg(S, g, t - 1), -1.0, 1.0);
                 }
+            for (int k = 0; k < S->ns; k++) {
+                const ora_storage *st = &S->st;
+                int bus = st->bus[k];
+                int64_t ips = v_st(S, V_PS, k, t), iqs = v_st(S, V_QS, k, t);
+                int64_t isc = v_st(S, V_SC, k, t), isd = v_st(S, V_SD, k, t), ise = v_st(S, V_SE, k, t);
+                double ps = x[ips], qs = x[iqs], sc = x[isc], sd = x[isd];
+                double vm = x[v_vm(S, bus, t)], r = st->r[k], s2 = ps * ps + qs * qs;
+                acc(&A, row_of(S, G_PB, bus, t), ips, 1.0, 1.0);
+                acc(&A, row_of(S, G_QB, bus, t), iqs, 1.0, 1.0);
+                int64_t row = row_st(S, R_SOC, k, t);
+                acc(&A, row, isc, -st->dt * st->eta_c[k], st->dt * st->eta_c[k]);
+                acc(&A, row, isd, st->dt / st->eta_d[k], st->dt / st->eta_d[k]);
+                acc(&A, row, ise, 1.0, 1.0);
+                if (t >= 1)
+                    acc(&A, row, v_st(S, V_SE, k, t - 1), -1.0, 1.0);
+                /* d/dx of -r s2 vm^-2: -2 r ps vm^-2, -2 r qs vm^-2, 2 r s2 vm^-3 */
+                row = row_st(S, R_LOSS, k, t);
+                acc(&A, row, v_vm(S, bus, t), 2.0 * r * s2 / (vm * vm * vm), 2.0 * r * s2 / fabs(vm * vm * vm));
+                acc(&A, row, ips, 1.0 - 2.0 * r * ps / (vm * vm), 1.0 + 2.0 * r * fabs(ps) / (vm * vm));
+                acc(&A, row, iqs, -2.0 * r * qs / (vm * vm), 2.0 * r * fabs(qs) / (vm * vm));
+                acc(&A, row, isc, -1.0, 1.0);
+                acc(&A, row, isd, 1.0, 1.0);
+                acc(&A, row_st(S, R_STH, k, t), ips, 2.0 * ps, 2.0 * fabs(ps));
+                acc(&A, row_st(S, R_STH, k, t), iqs, 2.0 * qs, 2.0 * fabs(qs));
+                if (S->compl) {
+                    acc(&A, row_st(S, R_CMP, k, t), isc, sd, fabs(sd));
+                    acc(&A, row_st(S, R_CMP, k, t), isd, sc, fabs(sc));
+                }
+            }
         }
     }
     if (C->link) {
@@ -1131,6 +1318,25 @@ int ora_hess(const ora_ctx *C, const double *x, const double *lambda, double sig
                 acc_sym(&A, v_vm(S, i, t), v_vm(S, i, t), v, bnd);
                 if (S->rect)
                     acc_sym(&A, v_va(S, i, t), v_va(S, i, t), v, bnd);
+            }
+            /* storage: mu (loss row) times the Hessian of -r (ps^2 + qs^2) vm^-2,
+             * lambda (thermal) times 2 on (ps, ps), (qs, qs), and the
+             * complementarity row's 1 on (sd, sc) */
+            for (int k = 0; k < S->ns; k++) {
+                const ora_storage *st = &S->st;
+                int64_t ivm = v_vm(S, st->bus[k], t);
+                int64_t ips = v_st(S, V_PS, k, t), iqs = v_st(S, V_QS, k, t);
+                double ps = x[ips], qs = x[iqs], vm = x[ivm], r = st->r[k];
+                double mu = lambda[row_st(S, R_LOSS, k, t)], lt = lambda[row_st(S, R_STH, k, t)];
+                double v2 = vm * vm, v3 = v2 * vm, v4 = v2 * v2, s2 = ps * ps + qs * qs;
+                acc_sym(&A, ips, ips, -2.0 * r * mu / v2 + 2.0 * lt, 2.0 * fabs(r * mu) / v2 + 2.0 * fabs(lt));
+                acc_sym(&A, iqs, iqs, -2.0 * r * mu / v2 + 2.0 * lt, 2.0 * fabs(r * mu) / v2 + 2.0 * fabs(lt));
+                acc_sym(&A, ips, ivm, 4.0 * r * mu * ps / v3, 4.0 * fabs(r * mu * ps / v3));
+                acc_sym(&A, iqs, ivm, 4.0 * r * mu * qs / v3, 4.0 * fabs(r * mu * qs / v3));
+                acc_sym(&A, ivm, ivm, -6.0 * r * mu * s2 / v4, 6.0 * fabs(r * mu) * s2 / v4);
+                if (S->compl)
+                    acc_sym(&A, v_st(S, V_SD, k, t), v_st(S, V_SC, k, t), lambda[row_st(S, R_CMP, k, t)],
+                            fabs(lambda[row_st(S, R_CMP, k, t)]));
             }
         }
     }

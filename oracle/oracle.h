@@ -24,6 +24,16 @@
  * row is vi_ref; the angle group holds Im(w) - tan(angmax) Re(w) <= 0 and two
  * groups follow the thermal rows: Im(w) - tan(angmin) Re(w) >= 0 per branch
  * and vmin^2 <= vr^2 + vi^2 <= vmax^2 per bus (w = V_f conj(V_t)).
+ *
+ * Storage (polar form): variables ps, qs, sc, sd, se of every unit follow q,
+ * each group unit + nstor * period; rows, each group unit + nstor * period,
+ * follow the ramp rows:
+ *   state of charge  se_t - se_{t-1} - dt (eta_c sc_t - sd_t / eta_d) = 0
+ *                    (t = 0: se_0 - dt (...) = e_init)
+ *   converter losses ps + sd - sc - r (ps^2 + qs^2) / vm_bus^2 = p_loss
+ *   thermal          ps^2 + qs^2 <= thermal_rating^2
+ *   complementarity  sc sd <= 0 (only when requested)
+ * and ps, qs are drawn from the bus (added to its P and Q balance rows).
  */
 #ifndef OPF_ORACLE_H
 #define OPF_ORACLE_H
@@ -45,6 +55,17 @@ typedef struct {
     double ramp_ratio;                                   /* ramp rows if > 0 and nperiod > 1 */
 } ora_net;
 
+/* Storage units of one instance (multi-period model with storage): unit k
+ * at bus[k]; per period the variables ps, qs (power drawn from the bus),
+ * sc, sd (charging, discharging) and se (stored energy); dt hours per period. */
+typedef struct {
+    int32_t nstor;
+    const int32_t *bus;
+    const double *energy_rating, *charge_rating, *discharge_rating, *thermal_rating;
+    const double *eta_c, *eta_d, *r, *p_loss, *qmin, *qmax, *e_init;
+    double dt;
+} ora_storage;
+
 typedef struct ora_ctx ora_ctx;
 
 /* Builds layout and sparsity patterns. Copies every array. NULL on bad input. */
@@ -57,6 +78,12 @@ ora_ctx *ora_create2(const ora_net *nets, int32_t ninst, double link_ratio, cons
 /* As ora_create2 in the polar (form 0) or rectangular (form 1) voltages. */
 ora_ctx *ora_create3(const ora_net *nets, int32_t ninst, double link_ratio, const double *link_ratios,
                      double reserve, int32_t form);
+/* As ora_create3 (polar form only) with storage: stor[s] describes instance
+ * s's units (stor NULL: none). Per instance, after its ramp rows: state of
+ * charge, converter losses and thermal rows, and the complementarity rows
+ * sc sd <= 0 when compl != 0. */
+ora_ctx *ora_create4(const ora_net *nets, int32_t ninst, double link_ratio, const double *link_ratios,
+                     double reserve, int32_t form, const ora_storage *stor, int32_t compl);
 void ora_destroy(ora_ctx *);
 const char *ora_error(void);
 

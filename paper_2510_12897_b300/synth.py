@@ -37,6 +37,14 @@ side of the evaluation computes.
 Multi-period loads follow the paper's demand-curve interface (Sec. III-C-2,
 ``mpopf_model`` with a curve): every load is scaled per period by one daily
 curve, here a seeded sinusoid, times lognormal(0, 0.05) noise per load.
+
+Storage follows the paper's multi-period-with-storage cases (Sec. IV-B):
+units at the buses with the largest 10% of active load, energy rating 1.5
+times the bus's (base) demand; the paper takes the ratio of energy to
+charge and discharge rating from its storage reference without printing it,
+here 2 hours; thermal rating 1.1 times the larger rating, reactive limits
+half of it either way, efficiencies 0.95, series resistance 0.02 p.u., no
+standby loss, initial energy half the rating, periods spanning one day.
 """
 from __future__ import annotations
 
@@ -47,6 +55,29 @@ import numpy as np
 from scipy.spatial import cKDTree
 
 DEG = math.pi / 180.0
+
+
+@dataclass
+class Storage:
+    """Storage units of one network (multi-period model with storage)."""
+
+    bus: np.ndarray
+    energy_rating: np.ndarray
+    charge_rating: np.ndarray
+    discharge_rating: np.ndarray
+    thermal_rating: np.ndarray
+    eta_c: np.ndarray
+    eta_d: np.ndarray
+    r: np.ndarray
+    p_loss: np.ndarray
+    qmin: np.ndarray
+    qmax: np.ndarray
+    e_init: np.ndarray
+    dt: float
+
+    @property
+    def nstor(self) -> int:
+        return int(self.bus.shape[0])
 
 
 @dataclass
@@ -82,6 +113,7 @@ class Grid:
     ref_bus: int
     ramp_ratio: float = 0.0
     xy: np.ndarray | None = field(default=None, repr=False)
+    storage: Storage | None = field(default=None, repr=False)
 
     @property
     def nbranch(self) -> int:
@@ -396,7 +428,25 @@ def contingencies(g: Grid, count: int, seed: int) -> list[Grid]:
 
 def n_vars(g: Grid) -> int:
     T = g.nperiod
-    return T * (2 * g.nbus + 2 * g.ngen + 4 * g.nbranch)
+    ns = g.storage.nstor if g.storage is not None else 0
+    return T * (2 * g.nbus + 2 * g.ngen + 4 * g.nbranch + 5 * ns)
+
+
+def with_storage(g: Grid, share: float = 0.1, energy_factor: float = 1.5, hours: float = 2.0) -> Grid:
+    """Copy of multi-period ``g`` with storage units at the buses carrying the
+    largest ``share`` of base active load (recipe in the module docstring)."""
+    pd = np.zeros(g.nbus)
+    np.add.at(pd, g.load_bus, g.load_pd[0])
+    count = max(1, int(round(share * np.count_nonzero(pd))))
+    bus = np.sort(np.argsort(-pd, kind="stable")[:count]).astype(np.int32)
+    E = energy_factor * pd[bus]
+    rate = E / hours
+    S = 1.1 * rate
+    k = bus.shape[0]
+    st = Storage(bus=bus, energy_rating=E, charge_rating=rate.copy(), discharge_rating=rate.copy(),
+                 thermal_rating=S, eta_c=np.full(k, 0.95), eta_d=np.full(k, 0.95), r=np.full(k, 0.02),
+                 p_loss=np.zeros(k), qmin=-0.5 * S, qmax=0.5 * S, e_init=0.5 * E, dt=24.0 / g.nperiod)
+    return g.copy(storage=st)
 
 
 def random_point(g: Grid, rng: np.random.Generator, form: str = "polar") -> np.ndarray:
@@ -416,7 +466,15 @@ def random_point(g: Grid, rng: np.random.Generator, form: str = "polar") -> np.n
     q = rng.uniform(-rate, rate, (T, na))
     if form == "rect":
         va, vm = vm * np.cos(va), vm * np.sin(va)
-    return np.concatenate([a.ravel() for a in (va, vm, pg, qg, p, q)])
+    parts = [va, vm, pg, qg, p, q]
+    st = g.storage
+    if st is not None:  # ps, qs, sc, sd, se uniform in their bounds
+        parts += [rng.uniform(-st.thermal_rating, st.thermal_rating, (T, st.nstor)),
+                  rng.uniform(st.qmin, st.qmax, (T, st.nstor)),
+                  rng.uniform(0.0, st.charge_rating, (T, st.nstor)),
+                  rng.uniform(0.0, st.discharge_rating, (T, st.nstor)),
+                  rng.uniform(0.0, st.energy_rating, (T, st.nstor))]
+    return np.concatenate([a.ravel() for a in parts])
 
 
 def random_multipliers(m: int, rng: np.random.Generator) -> np.ndarray:
@@ -456,6 +514,11 @@ def case2k_secure(seed: int = 2000) -> Grid:
 def mp2k(nperiod: int = 96, seed: int = 2000) -> Grid:
     """The 2,000-bus grid over ``nperiod`` periods, ramp 0.2 Pmax."""
     return multi_period(case2k(seed), nperiod, seed, ramp_ratio=0.2)
+
+
+def mp2k_storage(nperiod: int = 96, seed: int = 2000) -> Grid:
+    """The 2,000-bus grid over ``nperiod`` periods with storage units."""
+    return with_storage(mp2k(nperiod, seed))
 
 
 def sc1k(ncont: int = 500, seed: int = 1000) -> list[Grid]:
