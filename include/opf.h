@@ -97,6 +97,31 @@ typedef struct {
 
 enum { OPF_FORM_POLAR = 0, OPF_FORM_RECT = 1 };
 
+/* Storage units of one network: the multi-period model with storage of
+ * Sec. III-C-2 (the storage model of Geth, Coffrin and Fobes the paper
+ * builds on), polar form only. Per unit k and period t the variables
+ * ps, qs (power drawn from bus[k], added to its P and Q balance rows),
+ * sc in [0, charge_rating], sd in [0, discharge_rating] and
+ * se in [0, energy_rating] follow q in x (each group k + nstor * t, in
+ * that order; ps in [-thermal_rating, thermal_rating], qs in [qmin, qmax]);
+ * the instance's rows gain, after its ramp rows (each group k + nstor * t):
+ *   state of charge  se_t - se_{t-1} - dt (eta_c sc_t - sd_t / eta_d) = 0,
+ *                    and = e_init in the first period (no se_{t-1} term)
+ *   converter losses ps + sd - sc - r (ps^2 + qs^2) / vm_bus^2 = p_loss
+ *   thermal          ps^2 + qs^2 <= thermal_rating^2
+ *   complementarity  sc sd <= 0, when opf_batch_opts.storage_complementarity
+ * Jacobian rows list their columns ascending; the Hessian gains (ps, vm),
+ * (ps, ps), (qs, vm), (qs, qs) per unit and period, (sd, sc) with the
+ * complementarity rows, and the loss term's part of (vm, vm). */
+typedef struct {
+    int32_t nstor;
+    const int32_t *bus;                                 /* [nstor] */
+    const double *energy_rating, *charge_rating, *discharge_rating, *thermal_rating;
+    const double *eta_c, *eta_d;                        /* > 0 */
+    const double *r, *p_loss, *qmin, *qmax, *e_init;    /* [nstor] */
+    double dt;                                          /* hours per period, > 0 */
+} opf_storage;
+
 typedef struct {
     double link_ratio; /* > 0: rows pg_s - pg_0 in [-ratio pmax, ratio pmax] for every
                           instance s >= 1 (all instances need equal ngen, nperiod 1) */
@@ -108,6 +133,9 @@ typedef struct {
                           i.e. the spare capacity covers that share of the demand */
     int32_t form;      /* OPF_FORM_POLAR (va, vm) or OPF_FORM_RECT (vr, vi), for every
                           instance; models from opf_model_create are polar */
+    const opf_storage *storage;      /* NULL, or [ninst] storage units per instance
+                                        (nstor 0 for none); polar form only */
+    int32_t storage_complementarity; /* nonzero: the rows sc sd <= 0 */
 } opf_batch_opts;
 
 typedef struct opf_model opf_model;

@@ -193,6 +193,14 @@ __device__ __forceinline__ void put5(double *J, bool f_lo, double vaf, double va
     J[4] = 1.0;
 }
 
+// a double4_16a of read-only data as two 16-byte loads
+__device__ __forceinline__ double4_16a ldg4(const double4_16a *p)
+{
+    const double2 a = __ldg(reinterpret_cast<const double2 *>(p));
+    const double2 b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+    return make_double4_16a(a.x, a.y, b.x, b.y);
+}
+
 // static (never written) data of one branch item
 struct BrStatic {
     int4 br;  // f, t, slot of the from-arc, slot of the to-arc
@@ -563,7 +571,7 @@ __global__ void __launch_bounds__(OCC ? 256 : 512, OCC ? 3 : 1) rect_branch_kern
 
 constexpr int kBusBlockMax = 256;
 
-template <bool CONS, bool JAC, bool HESS, bool ONE, bool RECT = false>
+template <bool CONS, bool JAC, bool HESS, bool ONE, bool RECT = false, bool STOR = false>
 __global__ void __launch_bounds__(kBusBlockMax) bus_kernel(const KParams P)
 {
     cudaTriggerProgrammaticLaunchCompletion();
@@ -579,6 +587,7 @@ __global__ void __launch_bounds__(kBusBlockMax) bus_kernel(const KParams P)
         int s, t, e;    // instance, period, bus or generator
         int4 a, b;      // bus: slots, generator entries, row offsets
         int2 m;         // bus: group-closing mask of its slots, number of lower slots
+        int2 st;        // bus: (first, end) entry of its storage units (STOR)
         double2 gsbs;
         int gfirst;     // first generator id at the bus, or -1
     };
@@ -606,6 +615,8 @@ __global__ void __launch_bounds__(kBusBlockMax) bus_kernel(const KParams P)
             q.b = __ldg(d.bus_b + ib);
             q.m = __ldg(d.bus_c + ib);
             q.gsbs = __ldg(d.gsbs + ib);
+            if (STOR)
+                q.st = __ldg(d.bus_st + ib);
             if (CONS && q.a.z < q.a.w)
                 q.gfirst = __ldg(d.gen_list + (ONE ? P.inst0.gl0 : __ldg(&d.inst[q.s].gl0)) + q.a.z);
         } else if (item < P.ngen_items) {
@@ -695,6 +706,87 @@ __global__ void __launch_bounds__(kBusBlockMax) bus_kernel(const KParams P)
                 for (int e = RECT ? 2 : 1; e <= ng_here + (RECT ? 1 : 0); e++) {
                     JP[e] = -1.0;
                     JQ[e] = -1.0;
+                }
+            }
+            double sP = 0.0, sQ = 0.0, sH = 0.0;  // storage: drawn P, Q; (vm, vm) part
+            if constexpr (STOR) {
+                // storage units at the bus (ascending id): ps and qs are
+                // drawn from the bus; each unit's state-of-charge, loss,
+                // thermal and complementarity rows, their Jacobian
+                // entries, and its Hessian entries (the loss term
+                // -r (ps^2 + qs^2) / vm^2 adds to the bus's (vm, vm))
+                const int ns = I.ns, nsT = ns * T, rt = ns * q.t;
+                const int ist = 2 * nbT + 2 * ngT + 2 * na * T;  // first ps
+                const double iv2 = 1.0 / (vm * vm), iv3 = iv2 / vm;
+                for (int e = q.st.x; e < q.st.y; e++) {
+                    const int k = __ldg(d.st_list + e);
+                    const double4_16a par = ldg4(d.st_par + I.st0 + k);  // (dt eta_c, dt / eta_d, r, e_init)
+                    const int v = ist + k + rt;
+                    const double ps = __ldg(xs + v), qs = __ldg(xs + v + nsT);
+                    const double s2 = fma(ps, ps, qs * qs);
+                    const int r = k + rt;  // row inside each storage group
+                    if (CONS) {
+                        const double sc = __ldg(xs + v + 2 * nsT), sd = __ldg(xs + v + 3 * nsT);
+                        const double se = __ldg(xs + v + 4 * nsT);
+                        const double sp = q.t ? __ldg(xs + v + 4 * nsT - ns) : 0.0;
+                        sP += ps;
+                        sQ += qs;
+                        double *c = P.c + I.c0 + I.st_c + r;
+                        c[0] = se - sp - fma(par.x, sc, neg(par.y * sd));
+                        c[nsT] = ps + sd - sc - par.z * s2 * iv2;
+                        c[2 * nsT] = s2;
+                        if (I.st_compl)
+                            c[3 * nsT] = sc * sd;
+                    }
+                    if (JAC) {
+                        const int u = 1 + ng_here + nsl + (e - q.st.x);  // after vm, generators, arcs
+                        double *JP = P.jac + I.j0 + (T + 22 * nlT + (int)I.jP * q.t + q.b.x);
+                        JP[u] = 1.0;
+                        JP[(int)I.jP * T + u] = 1.0;
+                        double *J = P.jac + I.j0 + I.st_j;
+                        double *Js = J + (q.t ? 3 * ns + 4 * (r - ns) : 3 * k);
+                        Js[0] = neg(par.x);
+                        Js[1] = par.y;
+                        if (q.t) {
+                            Js[2] = -1.0;
+                            Js[3] = 1.0;
+                        } else {
+                            Js[2] = 1.0;
+                        }
+                        double *Jl = J + ns * (4 * T - 1) + 5 * r;
+                        const double rr = twice(par.z) * iv2;  // 2 r / vm^2
+                        Jl[0] = rr * s2 / vm;
+                        Jl[1] = fma(neg(rr), ps, 1.0);
+                        Jl[2] = neg(rr * qs);
+                        Jl[3] = -1.0;
+                        Jl[4] = 1.0;
+                        double *Jt = J + ns * (4 * T - 1) + 5 * nsT + 2 * r;
+                        Jt[0] = twice(ps);
+                        Jt[1] = twice(qs);
+                        if (I.st_compl) {
+                            Jt[2 * nsT] = __ldg(xs + v + 3 * nsT);  // d(sc sd)/dsc = sd
+                            Jt[2 * nsT + 1] = __ldg(xs + v + 2 * nsT);
+                        }
+                    }
+                    if (HESS) {
+                        const double *L = P.lam + I.c0 + I.st_c + r;
+                        const double mu = __ldg(L + nsT), lt = __ldg(L + 2 * nsT);
+                        const double rm = par.z * mu;
+                        sH = fma(-6.0 * rm * s2, iv2 * iv2, sH);
+                        double *Hs = P.hess + I.h0 + I.st_h + 2 * r;
+                        const double dg = fma(-2.0 * rm, iv2, twice(lt));
+                        Hs[0] = 4.0 * rm * ps * iv3;  // (ps, vm)
+                        Hs[1] = dg;                   // (ps, ps)
+                        Hs[2 * nsT] = 4.0 * rm * qs * iv3;
+                        Hs[2 * nsT + 1] = dg;
+                        if (I.st_compl)
+                            P.hess[I.h0 + I.st_h + 4 * nsT + r] = __ldg(L + 3 * nsT);  // (sd, sc)
+                    }
+                    if (P.want_grad) {
+                        double *g = P.grad + I.x0 + v;
+                        for (int w = 0; w < 5; w++)
+                            g[w * nsT] = 0.0;
+                    }
                 }
             }
             if (CONS || HESS) {
@@ -794,6 +886,10 @@ __global__ void __launch_bounds__(kBusBlockMax) bus_kernel(const KParams P)
                 }
                 if (CONS) {
                     double *c = P.c + I.c0 + (T + 5 * nlT + nb * q.t + i);
+                    if (STOR) {
+                        Pb += sP;
+                        Qb += sQ;
+                    }
                     c[0] = Pb;
                     c[nbT] = Qb;
                     if (RECT)
@@ -803,6 +899,8 @@ __global__ void __launch_bounds__(kBusBlockMax) bus_kernel(const KParams P)
                     Hva[nlt] = dmm;
                     Hvm[nd + nlt] = dmm;
                 } else if (HESS) {
+                    if (STOR)
+                        dmm += sH;
                     if (nsl > 0) {
                         Hva[nlt] = daa;
                         Hvm[nlt] = dma;
@@ -1013,7 +1111,7 @@ __global__ void __launch_bounds__(512) jt_branch_kernel(const KParams P)
     }
 }
 
-template <bool ONE, bool RECT = false>
+template <bool ONE, bool RECT = false, bool STOR = false>
 __global__ void __launch_bounds__(256) jt_bus_kernel(const KParams P)
 {
     cudaTriggerProgrammaticLaunchCompletion();
@@ -1069,6 +1167,30 @@ __global__ void __launch_bounds__(256) jt_bus_kernel(const KParams P)
                 const double2 w = __ldcg(Sg + 3 * q);
                 dva += w.x;
                 dvm += w.y;
+            }
+            if constexpr (STOR) {  // the bus's storage units: their five entries, the loss rows' vm part
+                const int2 stb = __ldg(d.bus_st + ib);
+                const int ns = I.ns, nsT = ns * T;
+                const int ist = 2 * nbT + 2 * ngT + 2 * na * T;
+                const double iv2 = 1.0 / (vm * vm);
+                const double *Vs = V + I.st_c;
+                for (int e = stb.x; e < stb.y; e++) {
+                    const int k = __ldg(d.st_list + e);
+                    const double4_16a par = ldg4(d.st_par + I.st0 + k);
+                    const int r = k + ns * t, v = ist + r;
+                    const double ps = __ldg(xs + v), qs = __ldg(xs + v + nsT);
+                    const double sc = __ldg(xs + v + 2 * nsT), sd = __ldg(xs + v + 3 * nsT);
+                    const double vs = __ldg(Vs + r), vl = __ldg(Vs + nsT + r), vt = __ldg(Vs + 2 * nsT + r);
+                    const double vc = I.st_compl ? __ldg(Vs + 3 * nsT + r) : 0.0;
+                    const double vn = t + 1 < T ? __ldg(Vs + r + ns) : 0.0;  // next period's state of charge
+                    const double rr = twice(par.z) * iv2;  // 2 r / vm^2
+                    dvm = fma(vl * rr, fma(ps, ps, qs * qs) / vm, dvm);
+                    o[v] = fma(twice(ps), vt, fma(vl, fma(neg(rr), ps, 1.0), vP));
+                    o[v + nsT] = fma(twice(qs), vt, fma(vl, neg(rr * qs), vQ));
+                    o[v + 2 * nsT] = fma(vc, sd, fma(neg(par.x), vs, neg(vl)));
+                    o[v + 3 * nsT] = fma(vc, sc, fma(par.y, vs, vl));
+                    o[v + 4 * nsT] = vs - vn;
+                }
             }
             o[nb * t + i] = dva;
             o[nbT + nb * t + i] = dvm;
@@ -1215,6 +1337,17 @@ __global__ void flat_kernel(const DevArrays d, int32_t ninst, int64_t nbr_items,
             const double v1 = fmin(fmax(1.0, vb.x), vb.y);
             x[xva + i] = rect ? v1 : 0.0;
             x[xva + (int64_t)I->nb * I->T + i] = rect ? 0.0 : v1;
+            if (d.bus_st) {  // storage at the bus: idle (ps = qs = sc = sd = 0), se at its initial energy
+                const int2 stb = d.bus_st[I->bus0 + i];
+                const int64_t ns = I->ns, nsT = ns * I->T;
+                const int64_t ist = I->x0 + 2 * ((int64_t)I->nb + I->ng + 2 * (int64_t)I->nl) * I->T;
+                for (int e = stb.x; e < stb.y; e++) {
+                    const int k = d.st_list[e];
+                    const int64_t v = ist + k + ns * t;
+                    x[v] = x[v + nsT] = x[v + 2 * nsT] = x[v + 3 * nsT] = 0.0;
+                    x[v + 4 * nsT] = d.st_par[I->st0 + k].w;
+                }
+            }
         } else {
             const int64_t gi = it - nbr_items - nbus_items;
             const int s = ninst == 1 ? 0 : find_inst(d.gen_items, ninst, gi);
@@ -1297,8 +1430,8 @@ cudaError_t launch_pdl(K kernel, int grid, int block, cudaStream_t s, const KPar
 }
 
 template <bool C, bool J, bool H>
-cudaError_t dispatch(const KParams &P, bool one, bool occ, bool rect, bool run_branch, bool run_bus, int gb,
-                     int bb, int gu, int bu, cudaStream_t s)
+cudaError_t dispatch(const KParams &P, bool one, bool occ, bool rect, bool stor, bool run_branch, bool run_bus,
+                     int gb, int bb, int gu, int bu, cudaStream_t s)
 {
     cudaError_t e = cudaSuccess;
     if (rect) {  // the rectangular branch kernel (two register budgets) and bus variant
@@ -1323,6 +1456,9 @@ cudaError_t dispatch(const KParams &P, bool one, bool occ, bool rect, bool run_b
     }
     if (e != cudaSuccess || !run_bus)
         return e;
+    if (stor)  // storage units (polar only)
+        return one ? launch_pdl(bus_kernel<C, J, H, true, false, true>, gu, bu, s, P)
+                   : launch_pdl(bus_kernel<C, J, H, false, false, true>, gu, bu, s, P);
     return one ? launch_pdl(bus_kernel<C, J, H, true>, gu, bu, s, P)
                : launch_pdl(bus_kernel<C, J, H, false>, gu, bu, s, P);
 }
@@ -1369,14 +1505,14 @@ int launch_all(Model &M, const EvalArgs &a, unsigned what, cudaStream_t s, int p
     P.order = L.bus_order ? M.d.bus_order : nullptr;
     cudaError_t e;
     switch ((C ? 1 : 0) | (J ? 2 : 0) | (H ? 4 : 0)) {
-    case 0: e = dispatch<false, false, false>(P, one, occ, M.rect, run_branch, run_bus, gb, bb, gu, bu, s); break;
-    case 1: e = dispatch<true, false, false>(P, one, occ, M.rect, run_branch, run_bus, gb, bb, gu, bu, s); break;
-    case 2: e = dispatch<false, true, false>(P, one, occ, M.rect, run_branch, run_bus, gb, bb, gu, bu, s); break;
-    case 3: e = dispatch<true, true, false>(P, one, occ, M.rect, run_branch, run_bus, gb, bb, gu, bu, s); break;
-    case 4: e = dispatch<false, false, true>(P, one, occ, M.rect, run_branch, run_bus, gb, bb, gu, bu, s); break;
-    case 5: e = dispatch<true, false, true>(P, one, occ, M.rect, run_branch, run_bus, gb, bb, gu, bu, s); break;
-    case 6: e = dispatch<false, true, true>(P, one, occ, M.rect, run_branch, run_bus, gb, bb, gu, bu, s); break;
-    default: e = dispatch<true, true, true>(P, one, occ, M.rect, run_branch, run_bus, gb, bb, gu, bu, s); break;
+    case 0: e = dispatch<false, false, false>(P, one, occ, M.rect, M.storage, run_branch, run_bus, gb, bb, gu, bu, s); break;
+    case 1: e = dispatch<true, false, false>(P, one, occ, M.rect, M.storage, run_branch, run_bus, gb, bb, gu, bu, s); break;
+    case 2: e = dispatch<false, true, false>(P, one, occ, M.rect, M.storage, run_branch, run_bus, gb, bb, gu, bu, s); break;
+    case 3: e = dispatch<true, true, false>(P, one, occ, M.rect, M.storage, run_branch, run_bus, gb, bb, gu, bu, s); break;
+    case 4: e = dispatch<false, false, true>(P, one, occ, M.rect, M.storage, run_branch, run_bus, gb, bb, gu, bu, s); break;
+    case 5: e = dispatch<true, false, true>(P, one, occ, M.rect, M.storage, run_branch, run_bus, gb, bb, gu, bu, s); break;
+    case 6: e = dispatch<false, true, true>(P, one, occ, M.rect, M.storage, run_branch, run_bus, gb, bb, gu, bu, s); break;
+    default: e = dispatch<true, true, true>(P, one, occ, M.rect, M.storage, run_branch, run_bus, gb, bb, gu, bu, s); break;
     }
     if (e == cudaSuccess && M.reserve && (C || J) && (phases & 2)) {
         const int64_t threads = 32 * M.nres;
@@ -1467,7 +1603,10 @@ int launch_jtprod(Model &M, const double *x, const double *v, double *out, cudaS
         if (M.nbr_items > 0)
             e = one ? launch_pdl(jt_branch_kernel<true>, gb, 128, s, P)
                     : launch_pdl(jt_branch_kernel<false>, gb, 128, s, P);
-        if (e == cudaSuccess)
+        if (e == cudaSuccess && M.storage)
+            e = one ? launch_pdl(jt_bus_kernel<true, false, true>, gu, 128, s, P)
+                    : launch_pdl(jt_bus_kernel<false, false, true>, gu, 128, s, P);
+        else if (e == cudaSuccess)
             e = one ? launch_pdl(jt_bus_kernel<true>, gu, 128, s, P) : launch_pdl(jt_bus_kernel<false>, gu, 128, s, P);
     }
     if (e != cudaSuccess) {

@@ -53,7 +53,8 @@ struct __align__(16) InstDev {
     int32_t nload;      // loads of this instance
     int32_t lp0;        // first entry of this instance's bus->load pointers (nb + 1)
     int32_t ll0;        // first entry of this instance's bus->load list
-    int32_t pad1, pad2;
+    int32_t st_compl;   // storage complementarity rows present
+    int32_t pad2;
     int64_t x0, c0, j0, h0;
     int64_t ld0;        // first entry of this instance's loads in opf_set_loads arrays [T][nload]
     int64_t scr0;       // first arc-scratch slot (2 nl T slots per instance)
@@ -63,6 +64,9 @@ struct __align__(16) InstDev {
     int64_t link_c, link_j;  // this instance's linking rows and their Jacobian offset; -1 if none
     int64_t link_x0;    // first pg of instance 0 (linking partner)
     int64_t res_c, res_j;  // this instance's reserve rows (one per period) and their Jacobian offset; -1 if none
+    int64_t st_c, st_j, st_h;  // storage: first row, Jacobian value, Hessian value, inside the instance
+    int32_t ns;         // storage units
+    int32_t st0;        // first unit in the concatenated storage arrays
 };
 static_assert(sizeof(InstDev) % 16 == 0, "InstDev is loaded as int4 words");
 
@@ -94,6 +98,10 @@ struct DevArrays {
     double *c2 = nullptr, *c1 = nullptr, *c0 = nullptr;
     double2 *pbnd = nullptr, *qbnd = nullptr;  // (min, max), flat start only
     double2 *vbnd = nullptr;                   // (vmin, vmax) per bus, flat start only
+    // storage (multi-period model with storage)
+    int2 *bus_st = nullptr;       // per bus: (first, end) entry of its units in st_list
+    int32_t *st_list = nullptr;   // local unit ids, ascending per bus
+    double4_16a *st_par = nullptr;    // per unit: (dt eta_c, dt / eta_d, r, e_init)
     // instances and work lists
     InstDev *inst = nullptr;
     int64_t *br_items = nullptr;   // prefix of branch items (nl T) over instances, ninst + 1
@@ -118,12 +126,18 @@ struct HostInst {
     std::vector<int32_t> gen_ptr;   // nb + 1
     std::vector<int32_t> gen_list;  // ascending per bus
     std::vector<double> vmin, vmax, rate, angmin, angmax, pmin, pmax, qmin, qmax;
+    // storage units
+    int32_t ns = 0;
+    std::vector<int32_t> st_bus, st_ptr, st_list;  // st_ptr: nb + 1, st_list ascending per bus
+    std::vector<double> st_E, st_Pc, st_Pd, st_S, st_qmin, st_qmax, st_einit, st_ploss;
 };
 
 struct Model {
     int32_t ninst = 0;
     bool on_device = false;  // false: structure only (no device arrays)
     bool rect = false;       // rectangular voltages (vr, vi) instead of polar (va, vm)
+    bool storage = false;    // some instance has storage units
+    bool st_compl = false;   // storage complementarity rows
     bool link = false;
     double link_ratio = 0.0;
     std::vector<double> link_ratios;   // per instance (entry 0 unused)

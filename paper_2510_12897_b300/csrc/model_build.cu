@@ -197,6 +197,48 @@ int build_model(const opf_network *nets, int32_t ninst, const opf_batch_opts *op
                 set_error("link_ratios[%d] must be finite and >= 0", s);
                 return OPF_EINVAL;
             }
+    const opf_storage *stor = opts ? opts->storage : nullptr;
+    if (stor) {
+        if (rect) {
+            set_error("storage needs the polar form");
+            return OPF_EINVAL;
+        }
+        for (int s = 0; s < ninst; s++) {
+            const opf_storage &u = stor[s];
+            if (u.nstor < 0 || (u.nstor > 0 && (!u.bus || !u.energy_rating || !u.charge_rating ||
+                !u.discharge_rating || !u.thermal_rating || !u.eta_c || !u.eta_d || !u.r || !u.p_loss ||
+                !u.qmin || !u.qmax || !u.e_init))) {
+                set_error("instance %d: bad storage description (negative count or NULL array)", s);
+                return OPF_EINVAL;
+            }
+            if (u.nstor > 0 && !(u.dt > 0.0 && std::isfinite(u.dt))) {
+                set_error("instance %d: storage dt must be finite and > 0", s);
+                return OPF_EINVAL;
+            }
+            for (int k = 0; k < u.nstor; k++) {
+                if (u.bus[k] < 0 || u.bus[k] >= nets[s].nbus) {
+                    set_error("instance %d: storage %d bus out of range", s, k);
+                    return OPF_EINVAL;
+                }
+                const double v[] = {u.energy_rating[k], u.charge_rating[k], u.discharge_rating[k],
+                                    u.thermal_rating[k], u.r[k]};
+                bool ok = u.eta_c[k] > 0.0 && u.eta_d[k] > 0.0 && std::isfinite(u.eta_c[k]) &&
+                          std::isfinite(u.eta_d[k]) && std::isfinite(u.p_loss[k]) && std::isfinite(u.qmin[k]) &&
+                          std::isfinite(u.qmax[k]) && std::isfinite(u.e_init[k]);
+                for (double w : v)
+                    ok = ok && w >= 0.0 && std::isfinite(w);
+                if (!ok) {
+                    set_error("instance %d: storage %d: efficiencies must be > 0, ratings and r >= 0, "
+                              "all finite", s, k);
+                    return OPF_EINVAL;
+                }
+            }
+            if ((int64_t)nets[s].nperiod * u.nstor * 22 > INT32_MAX / 2) {
+                set_error("instance %d: storage too large for 32-bit in-instance offsets", s);
+                return OPF_EINVAL;
+            }
+        }
+    }
     bool link = (link_ratio > 0.0 || (opts && opts->link_ratios)) && ninst > 1;
     if (link)
         for (int s = 0; s < ninst; s++)
@@ -208,6 +250,9 @@ int build_model(const opf_network *nets, int32_t ninst, const opf_batch_opts *op
     Model *M = new Model();
     M->ninst = ninst;
     M->rect = rect;
+    for (int s = 0; stor && s < ninst; s++)
+        M->storage = M->storage || stor[s].nstor > 0;
+    M->st_compl = M->storage && opts->storage_complementarity != 0;
     M->link = link;
     M->link_ratio = link_ratio;
     M->link_ratios.assign(ninst, link_ratio);
@@ -237,6 +282,9 @@ int build_model(const opf_network *nets, int32_t ninst, const opf_batch_opts *op
     std::vector<double2> y_ff, y_ft, y_tf, y_tt, gsbs, pbnd, qbnd, vbnd;
     std::vector<double> rate2, Pd, Qd, c2, c1, c0;
     std::vector<double2> tanb;
+    std::vector<int2> bus_st;
+    std::vector<int32_t> st_list;
+    std::vector<double4_16a> st_par;
     std::vector<int32_t> gen_list, load_ptr, load_list, gen_busid;
     std::vector<uint8_t> slot_code;
     std::vector<int64_t> br_items(1, 0), bus_items(1, 0), gen_items(1, 0);
@@ -340,6 +388,38 @@ int build_model(const opf_network *nets, int32_t ninst, const opf_batch_opts *op
         for (int g = 0; g < ng; g++)
             gen_list.push_back(H.gen_list[g]);
 
+        // ---- storage units per bus (ascending id)
+        const int ns = stor ? stor[s].nstor : 0;
+        H.ns = ns;
+        H.st_ptr.assign(nb + 1, 0);
+        H.st_list.assign(ns, 0);
+        if (ns) {
+            const opf_storage &u = stor[s];
+            H.st_bus.assign(u.bus, u.bus + ns);
+            H.st_E.assign(u.energy_rating, u.energy_rating + ns);
+            H.st_Pc.assign(u.charge_rating, u.charge_rating + ns);
+            H.st_Pd.assign(u.discharge_rating, u.discharge_rating + ns);
+            H.st_S.assign(u.thermal_rating, u.thermal_rating + ns);
+            H.st_qmin.assign(u.qmin, u.qmin + ns);
+            H.st_qmax.assign(u.qmax, u.qmax + ns);
+            H.st_einit.assign(u.e_init, u.e_init + ns);
+            H.st_ploss.assign(u.p_loss, u.p_loss + ns);
+            for (int k = 0; k < ns; k++)
+                H.st_ptr[u.bus[k] + 1]++;
+            for (int i = 0; i < nb; i++)
+                H.st_ptr[i + 1] += H.st_ptr[i];
+            std::vector<int32_t> fill(H.st_ptr.begin(), H.st_ptr.end() - 1);
+            for (int k = 0; k < ns; k++)
+                H.st_list[fill[u.bus[k]]++] = k;
+        }
+        I.ns = ns;
+        I.st0 = (int32_t)st_par.size();
+        I.st_compl = M->st_compl && ns > 0;
+        for (int k = 0; k < ns; k++) {
+            const opf_storage &u = stor[s];
+            st_par.push_back(make_double4_16a(u.dt * u.eta_c[k], u.dt / u.eta_d[k], u.r[k], u.e_init[k]));
+        }
+
         // ---- per-bus row offsets inside one period, slot codes
         int64_t jsum = 0, hva = 0, hvm = 0;
         std::vector<int32_t> jp_local(nb);
@@ -371,7 +451,8 @@ int build_model(const opf_network *nets, int32_t ninst, const opf_batch_opts *op
             bus_b.push_back(make_int4((int32_t)jsum, (int32_t)hva, (int32_t)hvm, nd | (nlt << 16)));
             bus_c.push_back(make_int2((int32_t)lastmask, nlow));
             // balance rows: the voltage entries (vm; or vr, vi), generators, arcs
-            jsum += (rect ? 2 : 1) + (H.gen_ptr[i + 1] - H.gen_ptr[i]) + (p1 - p0);
+            jsum += (rect ? 2 : 1) + (H.gen_ptr[i + 1] - H.gen_ptr[i]) + (p1 - p0) +
+                    (H.st_ptr[i + 1] - H.st_ptr[i]);  // storage units after the arcs
             if (rect) {  // rows vr_i: lower vr_j, diagonal; rows vi_i: every vr_j, lower vi_j, diagonal
                 hva += nlt + 1;
                 hvm += nd + nlt + 1;
@@ -384,6 +465,7 @@ int build_model(const opf_network *nets, int32_t ninst, const opf_batch_opts *op
             double gsv = n.bus_gs ? n.bus_gs[i] : 0.0, bsv = n.bus_bs ? n.bus_bs[i] : 0.0;
             gsbs.push_back(make_double2(gsv, bsv));
             vbnd.push_back(make_double2(n.bus_vmin[i], n.bus_vmax[i]));
+            bus_st.push_back(make_int2((int32_t)st_list.size() + H.st_ptr[i], (int32_t)st_list.size() + H.st_ptr[i + 1]));
         }
 
         // ---- each arc's +1 entry in its bus's balance row: after the voltage
@@ -444,6 +526,7 @@ int build_model(const opf_network *nets, int32_t ninst, const opf_batch_opts *op
                 Qd[pd_base + (size_t)t * nb + n.load_bus[l]] += n.load_qd[(size_t)t * n.nload + l];
             }
 
+        st_list.insert(st_list.end(), H.st_list.begin(), H.st_list.end());
         for (int g = 0; g < ng; g++) {
             gen_busid.push_back(n.gen_bus[g]);
             c2.push_back(n.gen_c2[g]);
@@ -454,7 +537,7 @@ int build_model(const opf_network *nets, int32_t ninst, const opf_batch_opts *op
         }
 
         // ---- offsets
-        I.jP = (int64_t)(rect ? 2 * nb : nb) + ng + na;
+        I.jP = (int64_t)(rect ? 2 * nb : nb) + ng + na + ns;
         I.hva = hva;
         I.hvm = hvm;
         I.x0 = xo;
@@ -466,13 +549,22 @@ int build_model(const opf_network *nets, int32_t ninst, const opf_batch_opts *op
         I.link_c = I.link_j = -1;
         I.link_x0 = 0;
         I.res_c = I.res_j = -1;
-        xo += (int64_t)T * (2 * nb + 2 * ng + 2 * na);
+        xo += (int64_t)T * (2 * nb + 2 * ng + 2 * na + 5 * (int64_t)ns);
         // rectangular: one more angle row per branch and a magnitude row per bus
-        co += (int64_t)T * (1 + (rect ? 8 : 7) * (int64_t)nl + (rect ? 3 : 2) * nb) +
-              (H.ramp ? (int64_t)ng * (T - 1) : 0);
-        jo += (int64_t)T * (1 + (rect ? 36 : 30) * (int64_t)nl + (rect ? 6 : 2) * nb + 2 * ng) +
-              (H.ramp ? 2 * (int64_t)ng * (T - 1) : 0);
-        ho += (int64_t)T * (hva + hvm + ng + 2 * (int64_t)na);
+        const int64_t rows0 = (int64_t)T * (1 + (rect ? 8 : 7) * (int64_t)nl + (rect ? 3 : 2) * nb) +
+                              (H.ramp ? (int64_t)ng * (T - 1) : 0);
+        const int64_t jac0 = (int64_t)T * (1 + (rect ? 36 : 30) * (int64_t)nl + (rect ? 6 : 2) * nb + 2 * ng) +
+                             (H.ramp ? 2 * (int64_t)ng * (T - 1) : 0) + 2 * (int64_t)T * ns;  // + balance entries
+        const int64_t hes0 = (int64_t)T * (hva + hvm + ng + 2 * (int64_t)na);
+        // storage rows: state of charge (3 entries in the first period, 4
+        // after), losses (5), thermal (2), complementarity (2); Hessian
+        // (ps, vm), (ps, ps), (qs, vm), (qs, qs), complementarity (sd, sc)
+        I.st_c = rows0;
+        I.st_j = jac0;
+        I.st_h = hes0;
+        co += rows0 + (int64_t)(3 + I.st_compl) * ns * T;
+        jo += jac0 + (int64_t)ns * (4 * T - 1) + 7 * (int64_t)ns * T + (I.st_compl ? 2 * (int64_t)ns * T : 0);
+        ho += hes0 + (int64_t)(4 + I.st_compl) * ns * T;
         so += (int64_t)na * T;
         po += (int64_t)nb * T;
         br_items.push_back(br_items.back() + (int64_t)nl * T);
@@ -544,6 +636,9 @@ int build_model(const opf_network *nets, int32_t ninst, const opf_batch_opts *op
     UP(gen_busid, gen_busid)
     UP(bus_a, bus_a) UP(bus_b, bus_b) UP(bus_c, bus_c) UP(gsbs, gsbs) UP(slot_code, slot_code) UP(gen_list, gen_list)
     UP(Pd, Pd) UP(Qd, Qd) UP(c2, c2) UP(c1, c1) UP(c0, c0) UP(pbnd, pbnd) UP(qbnd, qbnd)
+    if (M->storage) {
+        UP(bus_st, bus_st) UP(st_list, st_list) UP(st_par, st_par)
+    }
     UP(vbnd, vbnd) UP(inst, M->inst) UP(br_items, br_items) UP(bus_items, bus_items)
     UP(gen_items, gen_items)
 #undef UP
@@ -648,6 +743,8 @@ void jac_pattern(const Model &M, int64_t *rows, int64_t *cols)
                     std::sort(arcs.begin(), arcs.end());
                     for (int a : arcs)
                         put(r, (pq ? X.q : X.p) + a + na * t);
+                    for (int u = H.st_ptr[i]; u < H.st_ptr[i + 1]; u++)  // storage: ps or qs
+                        put(r, X.q + na * T + (pq ? (int64_t)H.ns * T : 0) + H.st_list[u] + (int64_t)H.ns * t);
                     r++;
                 }
         for (int side = 0; side < 2; side++)
@@ -674,6 +771,34 @@ void jac_pattern(const Model &M, int64_t *rows, int64_t *cols)
                     put(r, X.pg + g + ng * t);
                     r++;
                 }
+        if (H.ns) {  // storage rows: state of charge, losses, thermal, complementarity
+            const int64_t ns = H.ns, st = X.q + na * T;
+            auto v = [&](int w, int64_t k, int64_t t) { return st + w * ns * T + k + ns * t; };
+            for (int64_t t = 0; t < T; t++)
+                for (int64_t k = 0; k < ns; k++, r++) {
+                    put(r, v(2, k, t));
+                    put(r, v(3, k, t));
+                    if (t >= 1)
+                        put(r, v(4, k, t - 1));
+                    put(r, v(4, k, t));
+                }
+            for (int64_t t = 0; t < T; t++)
+                for (int64_t k = 0; k < ns; k++, r++) {
+                    put(r, X.vm + H.st_bus[k] + nb * t);
+                    for (int w = 0; w < 4; w++)
+                        put(r, v(w, k, t));
+                }
+            for (int64_t t = 0; t < T; t++)
+                for (int64_t k = 0; k < ns; k++, r++) {
+                    put(r, v(0, k, t));
+                    put(r, v(1, k, t));
+                }
+            for (int64_t t = 0; t < T && I.st_compl; t++)
+                for (int64_t k = 0; k < ns; k++, r++) {
+                    put(r, v(2, k, t));
+                    put(r, v(3, k, t));
+                }
+        }
     }
     if (M.link) {
         int64_t r = M.link_c0, ng = M.host[0].ng;
@@ -774,6 +899,19 @@ void hess_pattern(const Model &M, int64_t *rows, int64_t *cols)
         for (int64_t t = 0; t < T; t++)
             for (int64_t a = 0; a < na; a++)
                 put(X.q + a + na * t, X.q + a + na * t);
+        if (H.ns) {  // rows ps, qs: (vm of the unit's bus, own diagonal); rows sd: (sd, sc)
+            const int64_t ns = H.ns, st = X.q + na * T;
+            for (int w = 0; w < 2; w++)
+                for (int64_t t = 0; t < T; t++)
+                    for (int64_t k = 0; k < ns; k++) {
+                        const int64_t r = st + w * ns * T + k + ns * t;
+                        put(r, X.vm + H.st_bus[k] + nb * t);
+                        put(r, r);
+                    }
+            for (int64_t t = 0; t < T && I.st_compl; t++)
+                for (int64_t k = 0; k < ns; k++)
+                    put(st + 3 * ns * T + k + ns * t, st + 2 * ns * T + k + ns * t);
+        }
     }
 }
 
@@ -812,6 +950,19 @@ void bounds(const Model &M, double *xl, double *xu, double *gl, double *gu)
                     xl[X.q + a + na * t] = -rate;
                     xu[X.q + a + na * t] = rate;
                 }
+            for (int64_t k = 0; xl && k < H.ns; k++) {  // ps, qs, sc, sd, se
+                const int64_t ns = H.ns, v = X.q + na * T + k + ns * t;
+                xl[v] = -H.st_S[k];
+                xu[v] = H.st_S[k];
+                xl[v + ns * T] = H.st_qmin[k];
+                xu[v + ns * T] = H.st_qmax[k];
+                xl[v + 2 * ns * T] = 0.0;
+                xu[v + 2 * ns * T] = H.st_Pc[k];
+                xl[v + 3 * ns * T] = 0.0;
+                xu[v + 3 * ns * T] = H.st_Pd[k];
+                xl[v + 4 * ns * T] = 0.0;
+                xu[v + 4 * ns * T] = H.st_E[k];
+            }
         }
         if (!gl)
             continue;
@@ -849,6 +1000,23 @@ void bounds(const Model &M, double *xl, double *xu, double *gl, double *gu)
                     gl[c] = -H.ramp_ratio * H.pmax[g];
                     gu[c] = H.ramp_ratio * H.pmax[g];
                 }
+        const int64_t ns = H.ns;
+        for (int64_t t = 0; t < T; t++)  // state of charge
+            for (int64_t k = 0; k < ns; k++, c++)
+                gl[c] = gu[c] = t == 0 ? H.st_einit[k] : 0.0;
+        for (int64_t t = 0; t < T; t++)  // losses
+            for (int64_t k = 0; k < ns; k++, c++)
+                gl[c] = gu[c] = H.st_ploss[k];
+        for (int64_t t = 0; t < T; t++)  // thermal
+            for (int64_t k = 0; k < ns; k++, c++) {
+                gl[c] = -inf;
+                gu[c] = H.st_S[k] * H.st_S[k];
+            }
+        for (int64_t t = 0; t < T && I.st_compl; t++)  // complementarity
+            for (int64_t k = 0; k < ns; k++, c++) {
+                gl[c] = -inf;
+                gu[c] = 0.0;
+            }
     }
     if (M.link && gl) {
         int64_t c = M.link_c0, ng = M.host[0].ng;

@@ -39,9 +39,18 @@ class OpfNetwork(ctypes.Structure):
     ]
 
 
+class OpfStorage(ctypes.Structure):
+    _fields_ = [("nstor", ctypes.c_int32), ("bus", _i32p),
+                ("energy_rating", _f64p), ("charge_rating", _f64p), ("discharge_rating", _f64p),
+                ("thermal_rating", _f64p), ("eta_c", _f64p), ("eta_d", _f64p), ("r", _f64p),
+                ("p_loss", _f64p), ("qmin", _f64p), ("qmax", _f64p), ("e_init", _f64p),
+                ("dt", ctypes.c_double)]
+
+
 class OpfBatchOpts(ctypes.Structure):
     _fields_ = [("link_ratio", ctypes.c_double), ("link_ratios", ctypes.POINTER(ctypes.c_double)),
-                ("reserve", ctypes.c_double), ("form", ctypes.c_int32)]
+                ("reserve", ctypes.c_double), ("form", ctypes.c_int32),
+                ("storage", ctypes.POINTER(OpfStorage)), ("storage_complementarity", ctypes.c_int32)]
 
 
 FORMS = {"polar": 0, "rect": 1}
@@ -177,6 +186,26 @@ def _net_struct(g, keep):
     return d
 
 
+def _storage_struct(st, keep):
+    d = OpfStorage()
+    if st is None:
+        d.nstor, d.dt = 0, 1.0
+        return d
+
+    def f(a):
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        keep.append(a)
+        return a.ctypes.data_as(_f64p)
+
+    b = np.ascontiguousarray(st.bus, dtype=np.int32)
+    keep.append(b)
+    d.nstor, d.bus, d.dt = st.nstor, b.ctypes.data_as(_i32p), float(st.dt)
+    for name in ("energy_rating", "charge_rating", "discharge_rating", "thermal_rating", "eta_c", "eta_d", "r",
+                 "p_loss", "qmin", "qmax", "e_init"):
+        setattr(d, name, f(getattr(st, name)))
+    return d
+
+
 def _ptr(t, n=None, name="buffer"):
     """Device pointer of a contiguous float64 CUDA tensor (or None)."""
     if t is None:
@@ -202,16 +231,20 @@ class Model:
     ``grids`` is one ``synth.Grid``-like object (attributes as in opf.h) or a
     list of them (a batch). ``structure_only=True`` builds the host layout
     only (dims, patterns, bounds) without touching a GPU. ``form`` is
-    "polar" (va, vm) or "rect" (vr, vi).
+    "polar" (va, vm) or "rect" (vr, vi). Grids carrying ``storage`` (a
+    ``synth.Storage``) get the storage variables and rows; ``compl`` adds
+    the complementarity rows.
     """
 
     def __init__(self, grids, link_ratio: float = 0.0, structure_only: bool = False, link_ratios=None,
-                 reserve: float = 0.0, form: str = "polar"):
+                 reserve: float = 0.0, form: str = "polar", compl: bool = False):
         if form not in FORMS:
             raise ValueError("form must be 'polar' or 'rect'")
         self.form = form
         batch = (isinstance(grids, (list, tuple)) or link_ratios is not None or reserve > 0.0
-                 or form != "polar")
+                 or form != "polar" or compl
+                 or any(getattr(g, "storage", None) is not None
+                        for g in (grids if isinstance(grids, (list, tuple)) else [grids])))
         gl = list(grids) if isinstance(grids, (list, tuple)) else [grids]
         self._keep = []
         arr = (OpfNetwork * len(gl))(*[_net_struct(g, self._keep) for g in gl])
@@ -221,8 +254,11 @@ class Model:
         if link_ratios is not None:
             lr = np.ascontiguousarray(link_ratios, dtype=np.float64)
             self._keep.append(lr)
+        stor = None
+        if any(getattr(g, "storage", None) is not None for g in gl):
+            stor = (OpfStorage * len(gl))(*[_storage_struct(getattr(g, "storage", None), self._keep) for g in gl])
         opts = OpfBatchOpts(float(link_ratio), None if lr is None else lr.ctypes.data_as(_f64p), float(reserve),
-                            FORMS[form])
+                            FORMS[form], stor, 1 if compl else 0)
         if structure_only:
             _check(L.opf_structure_create(arr, len(gl), ctypes.byref(opts), ctypes.byref(h)))
         elif batch:

@@ -227,3 +227,29 @@ def test_rect_form_validation():
         opf.Model(wide, structure_only=True, form="rect")
     with pytest.raises(ValueError):
         opf.Model(g, structure_only=True, form="cartesian")
+
+
+def test_storage_structure_matches_oracle(oracle_mod):
+    """Multi-period model with storage (host-only model): dims, patterns and
+    bounds equal the oracle's bit for bit, with and without complementarity
+    rows, alone and in a batch with reserve rows; invalid descriptions are
+    rejected before any device work."""
+    from paper_2510_12897_b300 import opf, synth
+    g = synth.with_storage(synth.multi_period(synth.case30(general=True), 4, seed=3, ramp_ratio=0.2))
+    batch = [synth.with_storage(synth.multi_period(synth.case30(), 2, seed=1)),
+             synth.multi_period(synth.case30(seed=31), 2, seed=2)]
+    for grids, opts in ((g, {}), (g, dict(compl=True)), (batch, dict(compl=True, reserve=0.1))):
+        M = opf.Model(grids, structure_only=True, **opts)
+        O = oracle_mod.Oracle(grids, **opts)
+        assert (M.n, M.m, M.nnzj, M.nnzh) == (O.n, O.m, O.nnzj, O.nnzh)
+        for a, b in zip(M.jac_pattern() + M.hess_pattern(), O.jac_pattern() + O.hess_pattern()):
+            np.testing.assert_array_equal(a, b)
+        for a, b in zip(M.bounds(), O.bounds()):
+            np.testing.assert_array_equal(a, b)
+    for change, msg in ((dict(bus=np.array([0, g.nbus], np.int32)), "bus"),
+                        (dict(eta_d=np.zeros(g.storage.nstor)), "efficienc"), (dict(dt=-1.0), "dt")):
+        bad = g.copy(storage=synth.replace(g.storage, **change))
+        with pytest.raises(opf.OpfError, match=msg):
+            opf.Model(bad, structure_only=True)
+    with pytest.raises(opf.OpfError, match="polar"):
+        opf.Model(g, structure_only=True, form="rect")

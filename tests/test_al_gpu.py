@@ -19,7 +19,7 @@ def torch():
     return t
 
 
-@pytest.mark.parametrize("case", ["case30g", "mp30", "rect30g"])
+@pytest.mark.parametrize("case", ["case30g", "mp30", "rect30g", "stor30"])
 def test_al_iterations_match_oracle(torch, oracle_mod, case):
     """Twenty Adam steps around one multiplier update from the flat start
     with random multipliers: iterates, multipliers and statistics equal the
@@ -28,8 +28,10 @@ def test_al_iterations_match_oracle(torch, oracle_mod, case):
     noise / 1e-8 per step: the bound on |x_gpu - x_oracle| is 1e-7 after 20
     steps (observed far below), 1e-9 relative on the statistics."""
     from paper_2510_12897_b300 import al
-    g = synth.multi_period(synth.case30(general=True), 3, seed=5, ramp_ratio=0.2) if case == "mp30" \
+    g = synth.multi_period(synth.case30(general=True), 3, seed=5, ramp_ratio=0.2) if case in ("mp30", "stor30") \
         else synth.case30(general=True)
+    if case == "stor30":  # the loop on the multi-period model with storage
+        g = synth.with_storage(g)
     form = "rect" if case == "rect30g" else "polar"  # the loop on the rectangular form's callbacks
     M = opf.Model(g, form=form)
     O = oracle_mod.Oracle(g, form=form)
