@@ -675,7 +675,22 @@ def batched_vs_plain(torch, opf, synth, stream, dev, cpu=False):
     tp = graph_us(plain_mp)
     out["mp2k_96"] = {"batched_us": tb, "plain_loop_us": tp, "speedup": tp / tb, "launch": tuned,
                       "batched_evals_per_s": 1e6 / tb, "period_evals_per_s": 96e6 / tb}
+    n_mp, m_mp = B.n, B.m
     del B, singles, os_
+    # the same multi-period model with storage units (Sec. III-C-2) and
+    # complementarity rows, autotuned
+    mps = synth.mp2k_storage()
+    Bs = opf.Model(mps, compl=True)
+    xs_b = torch.tensor(synth.random_point(mps, rng), device=dev)
+    ls_b = torch.tensor(rng.standard_normal(Bs.m), device=dev)
+    os_b = bufs(Bs)
+    cfg = Bs.autotune(xs_b, ls_b, reps=5, stream=stream)[0]
+    ts = graph_us(lambda: Bs.eval_all(xs_b, ls_b, 1.0, *os_b, stream=stream))
+    out["mp2k_96"]["with_storage"] = {
+        "batched_us": ts, "units": mps.storage.nstor, "extra_vars": Bs.n - n_mp,
+        "extra_rows": Bs.m - m_mp, "launch": cfg,
+        "vs_without_storage": ts / tb, "complementarity_rows": True}
+    del Bs, os_b
     # N-1: 1,000 buses, base + 500 contingencies
     insts = synth.sc1k()
     B = opf.Model(insts, link_ratio=0.2)

@@ -70,6 +70,7 @@ struct KParams {
     int64_t link_c0;    // first linking row
     int32_t want_grad, want_obj;
     int64_t nbr_items, nbus_items, ngen_items;
+    int64_t nst_items;  // storage unit items (bus kernel with storage)
     const int32_t *order = nullptr;  // bus-phase order within an instance, or null for id order
     double *xw = nullptr;            // x, writable (branch phase that sets the flows)
     const double *__restrict__ x;
@@ -579,7 +580,8 @@ __global__ void __launch_bounds__(kBusBlockMax) bus_kernel(const KParams P)
     __shared__ bool last;
     const DevArrays &d = P.d;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t total = P.nbus_items + P.ngen_items;
+    const int64_t nbg = P.nbus_items + P.ngen_items;
+    const int64_t total = nbg + (STOR ? P.nst_items : 0);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
 
@@ -592,11 +594,18 @@ __global__ void __launch_bounds__(kBusBlockMax) bus_kernel(const KParams P)
         int gfirst;     // first generator id at the bus, or -1
     };
     // items: generators first (the few blocks holding them do the objective
-    // reduction and finish early), then buses
+    // reduction and finish early), then buses, then storage units (unit
+    // index in e, its bus in a.x)
     auto load = [&](int64_t item) {
         Item q{};
         q.gfirst = -1;
-        if (item >= P.ngen_items && item < total) {
+        if (STOR && item >= nbg && item < total) {
+            item -= nbg;
+            q.s = ONE ? 0 : find_inst(d.st_items, P.ninst, item);
+            const InstDev *I = d.inst + q.s;
+            split((int)(item - (ONE ? 0 : __ldg(d.st_items + q.s))), __ldg(&I->ns), __ldg(&I->T), q.t, q.e);
+            q.a.x = __ldg(d.st_busid + __ldg(&I->st0) + q.e);
+        } else if (item >= P.ngen_items && item < nbg) {
             item -= P.ngen_items;
             int r, bus0;
             if (ONE) {
@@ -647,7 +656,73 @@ __global__ void __launch_bounds__(kBusBlockMax) bus_kernel(const KParams P)
         const int nl = I.nl, nb = I.nb, ng = I.ng, T = I.T;
         const int nbT = nb * T, ngT = ng * T, nlT = nl * T, na = 2 * nl;
         const double *__restrict__ xs = P.x + I.x0;
-        if (it >= P.ngen_items) {
+        if (STOR && it >= nbg) {
+            // one storage unit in one period: its state-of-charge, loss,
+            // thermal and complementarity rows, their Jacobian entries, its
+            // Hessian entries except the bus's (vm, vm), zero gradient
+            const int k = q.e, ns = I.ns, nsT = ns * T, r = k + ns * q.t;
+            const int v = 2 * nbT + 2 * ngT + 2 * na * T + r;  // ps of the unit
+            const double4_16a par = ldg4(d.st_par + I.st0 + k);  // (dt eta_c, dt / eta_d, r, e_init)
+            const double vm = __ldg(xs + nbT + nb * q.t + q.a.x);
+            const double ps = __ldg(xs + v), qs = __ldg(xs + v + nsT);
+            const double sc = __ldg(xs + v + 2 * nsT), sd = __ldg(xs + v + 3 * nsT);
+            const double s2 = fma(ps, ps, qs * qs);
+            const double iv2 = 1.0 / (vm * vm);
+            if (CONS) {
+                const double se = __ldg(xs + v + 4 * nsT);
+                const double sp = q.t ? __ldg(xs + v + 4 * nsT - ns) : 0.0;
+                double *c = P.c + I.c0 + I.st_c + r;
+                c[0] = se - sp - fma(par.x, sc, neg(par.y * sd));
+                c[nsT] = ps + sd - sc - par.z * s2 * iv2;
+                c[2 * nsT] = s2;
+                if (I.st_compl)
+                    c[3 * nsT] = sc * sd;
+            }
+            if (JAC) {
+                double *J = P.jac + I.j0 + I.st_j;
+                double *Js = J + (q.t ? 3 * ns + 4 * (r - ns) : 3 * k);
+                Js[0] = neg(par.x);
+                Js[1] = par.y;
+                if (q.t) {
+                    Js[2] = -1.0;
+                    Js[3] = 1.0;
+                } else {
+                    Js[2] = 1.0;
+                }
+                double *Jl = J + ns * (4 * T - 1) + 5 * r;
+                const double rr = twice(par.z) * iv2;  // 2 r / vm^2
+                Jl[0] = rr * s2 / vm;
+                Jl[1] = fma(neg(rr), ps, 1.0);
+                Jl[2] = neg(rr * qs);
+                Jl[3] = -1.0;
+                Jl[4] = 1.0;
+                double *Jt = J + ns * (4 * T - 1) + 5 * nsT + 2 * r;
+                Jt[0] = twice(ps);
+                Jt[1] = twice(qs);
+                if (I.st_compl) {
+                    Jt[2 * nsT] = sd;  // d(sc sd)/dsc
+                    Jt[2 * nsT + 1] = sc;
+                }
+            }
+            if (HESS) {
+                const double *L = P.lam + I.c0 + I.st_c + r;
+                const double rm = par.z * __ldg(L + nsT), lt = __ldg(L + 2 * nsT);
+                const double iv3 = iv2 / vm;
+                double *Hs = P.hess + I.h0 + I.st_h + 2 * r;
+                const double dg = fma(-2.0 * rm, iv2, twice(lt));
+                Hs[0] = 4.0 * rm * ps * iv3;  // (ps, vm)
+                Hs[1] = dg;                   // (ps, ps)
+                Hs[2 * nsT] = 4.0 * rm * qs * iv3;
+                Hs[2 * nsT + 1] = dg;
+                if (I.st_compl)
+                    P.hess[I.h0 + I.st_h + 4 * nsT + r] = __ldg(L + 3 * nsT);  // (sd, sc)
+            }
+            if (P.want_grad) {
+                double *g = P.grad + I.x0 + v;
+                for (int w = 0; w < 5; w++)
+                    g[w * nsT] = 0.0;
+            }
+        } else if (it >= P.ngen_items) {
             const int i = q.e;
             const int iva = nb * q.t, ivm = nbT + nb * q.t;
             // every dynamic scalar of the bus, issued together (rectangular:
@@ -710,82 +785,33 @@ __global__ void __launch_bounds__(kBusBlockMax) bus_kernel(const KParams P)
             }
             double sP = 0.0, sQ = 0.0, sH = 0.0;  // storage: drawn P, Q; (vm, vm) part
             if constexpr (STOR) {
-                // storage units at the bus (ascending id): ps and qs are
-                // drawn from the bus; each unit's state-of-charge, loss,
-                // thermal and complementarity rows, their Jacobian
-                // entries, and its Hessian entries (the loss term
-                // -r (ps^2 + qs^2) / vm^2 adds to the bus's (vm, vm))
+                // storage units at the bus (ascending id): ps and qs are drawn
+                // from the bus (balance sums and +1 entries), and each unit's
+                // loss term -r (ps^2 + qs^2) / vm^2 adds -6 r mu (ps^2 + qs^2)
+                // / vm^4 to the bus's (vm, vm); the rest of a unit's terms is
+                // its own item's
                 const int ns = I.ns, nsT = ns * T, rt = ns * q.t;
                 const int ist = 2 * nbT + 2 * ngT + 2 * na * T;  // first ps
-                const double iv2 = 1.0 / (vm * vm), iv3 = iv2 / vm;
                 for (int e = q.st.x; e < q.st.y; e++) {
                     const int k = __ldg(d.st_list + e);
-                    const double4_16a par = ldg4(d.st_par + I.st0 + k);  // (dt eta_c, dt / eta_d, r, e_init)
-                    const int v = ist + k + rt;
-                    const double ps = __ldg(xs + v), qs = __ldg(xs + v + nsT);
-                    const double s2 = fma(ps, ps, qs * qs);
-                    const int r = k + rt;  // row inside each storage group
-                    if (CONS) {
-                        const double sc = __ldg(xs + v + 2 * nsT), sd = __ldg(xs + v + 3 * nsT);
-                        const double se = __ldg(xs + v + 4 * nsT);
-                        const double sp = q.t ? __ldg(xs + v + 4 * nsT - ns) : 0.0;
-                        sP += ps;
-                        sQ += qs;
-                        double *c = P.c + I.c0 + I.st_c + r;
-                        c[0] = se - sp - fma(par.x, sc, neg(par.y * sd));
-                        c[nsT] = ps + sd - sc - par.z * s2 * iv2;
-                        c[2 * nsT] = s2;
-                        if (I.st_compl)
-                            c[3 * nsT] = sc * sd;
+                    if (CONS || HESS) {
+                        const double ps = __ldg(xs + ist + k + rt), qs = __ldg(xs + ist + nsT + k + rt);
+                        if (CONS) {
+                            sP += ps;
+                            sQ += qs;
+                        }
+                        if (HESS) {
+                            const double r = __ldg(&d.st_par[I.st0 + k].z);
+                            const double mu = __ldg(P.lam + I.c0 + I.st_c + nsT + k + rt);
+                            const double iv2 = 1.0 / (vm * vm);
+                            sH = fma(-6.0 * r * mu * fma(ps, ps, qs * qs), iv2 * iv2, sH);
+                        }
                     }
                     if (JAC) {
                         const int u = 1 + ng_here + nsl + (e - q.st.x);  // after vm, generators, arcs
                         double *JP = P.jac + I.j0 + (T + 22 * nlT + (int)I.jP * q.t + q.b.x);
                         JP[u] = 1.0;
                         JP[(int)I.jP * T + u] = 1.0;
-                        double *J = P.jac + I.j0 + I.st_j;
-                        double *Js = J + (q.t ? 3 * ns + 4 * (r - ns) : 3 * k);
-                        Js[0] = neg(par.x);
-                        Js[1] = par.y;
-                        if (q.t) {
-                            Js[2] = -1.0;
-                            Js[3] = 1.0;
-                        } else {
-                            Js[2] = 1.0;
-                        }
-                        double *Jl = J + ns * (4 * T - 1) + 5 * r;
-                        const double rr = twice(par.z) * iv2;  // 2 r / vm^2
-                        Jl[0] = rr * s2 / vm;
-                        Jl[1] = fma(neg(rr), ps, 1.0);
-                        Jl[2] = neg(rr * qs);
-                        Jl[3] = -1.0;
-                        Jl[4] = 1.0;
-                        double *Jt = J + ns * (4 * T - 1) + 5 * nsT + 2 * r;
-                        Jt[0] = twice(ps);
-                        Jt[1] = twice(qs);
-                        if (I.st_compl) {
-                            Jt[2 * nsT] = __ldg(xs + v + 3 * nsT);  // d(sc sd)/dsc = sd
-                            Jt[2 * nsT + 1] = __ldg(xs + v + 2 * nsT);
-                        }
-                    }
-                    if (HESS) {
-                        const double *L = P.lam + I.c0 + I.st_c + r;
-                        const double mu = __ldg(L + nsT), lt = __ldg(L + 2 * nsT);
-                        const double rm = par.z * mu;
-                        sH = fma(-6.0 * rm * s2, iv2 * iv2, sH);
-                        double *Hs = P.hess + I.h0 + I.st_h + 2 * r;
-                        const double dg = fma(-2.0 * rm, iv2, twice(lt));
-                        Hs[0] = 4.0 * rm * ps * iv3;  // (ps, vm)
-                        Hs[1] = dg;                   // (ps, ps)
-                        Hs[2 * nsT] = 4.0 * rm * qs * iv3;
-                        Hs[2 * nsT + 1] = dg;
-                        if (I.st_compl)
-                            P.hess[I.h0 + I.st_h + 4 * nsT + r] = __ldg(L + 3 * nsT);  // (sd, sc)
-                    }
-                    if (P.want_grad) {
-                        double *g = P.grad + I.x0 + v;
-                        for (int w = 0; w < 5; w++)
-                            g[w * nsT] = 0.0;
                     }
                 }
             }
@@ -1479,6 +1505,7 @@ int launch_all(Model &M, const EvalArgs &a, unsigned what, cudaStream_t s, int p
     P.nbr_items = M.nbr_items;
     P.nbus_items = M.nbus_items;
     P.ngen_items = M.ngen_items;
+    P.nst_items = M.nst_items;
     P.x = a.x;
     P.lam = a.lam;
     P.sigma = a.sigma;
@@ -1494,7 +1521,7 @@ int launch_all(Model &M, const EvalArgs &a, unsigned what, cudaStream_t s, int p
     const int bu = L.bus_block > kBusBlockMax ? kBusBlockMax : L.bus_block;
     const int gb = grid_for(M.nbr_items, L.branch_block, L.branch_ctas_per_sm, M.num_sms, 0);
     const int cap = max_part < M.max_part ? max_part : M.max_part;
-    const int gu = grid_for(M.nbus_items + M.ngen_items, bu, L.bus_ctas_per_sm, M.num_sms, cap);
+    const int gu = grid_for(M.nbus_items + M.ngen_items + M.nst_items, bu, L.bus_ctas_per_sm, M.num_sms, cap);
     // the branch phase is needed for its rows and for the scratch the bus
     // phase reads (balance sums, Hessian), and to zero the p, q gradient
     const bool run_branch = (phases & 1) && (C || J || H || P.want_grad) && M.nbr_items > 0;
@@ -1568,6 +1595,7 @@ KParams base_params(Model &M)
     P.nbr_items = M.nbr_items;
     P.nbus_items = M.nbus_items;
     P.ngen_items = M.ngen_items;
+    P.nst_items = M.nst_items;
     return P;
 }
 

@@ -102,6 +102,8 @@ struct DevArrays {
     int2 *bus_st = nullptr;       // per bus: (first, end) entry of its units in st_list
     int32_t *st_list = nullptr;   // local unit ids, ascending per bus
     double4_16a *st_par = nullptr;    // per unit: (dt eta_c, dt / eta_d, r, e_init)
+    int32_t *st_busid = nullptr;  // per unit: its local bus
+    int64_t *st_items = nullptr;  // prefix of storage items (ns T) over instances, ninst + 1
     // instances and work lists
     InstDev *inst = nullptr;
     int64_t *br_items = nullptr;   // prefix of branch items (nl T) over instances, ninst + 1
@@ -149,6 +151,7 @@ struct Model {
     int64_t link_c0 = 0, link_j0 = 0;  // first linking row / its first Jacobian value
     int64_t res_c0 = 0, res_j0 = 0;    // first reserve row / its first Jacobian value
     int64_t nbr_items = 0, nbus_items = 0, ngen_items = 0, narc_slots = 0;
+    int64_t nst_items = 0;        // storage items (units x periods, all instances)
     int64_t nload_total = 0;      // sum over instances of nload * nperiod
     int32_t max_part = 0;         // capacity of obj_part
     int device = 0, num_sms = 148;

@@ -287,7 +287,8 @@ int build_model(const opf_network *nets, int32_t ninst, const opf_batch_opts *op
     std::vector<double4_16a> st_par;
     std::vector<int32_t> gen_list, load_ptr, load_list, gen_busid;
     std::vector<uint8_t> slot_code;
-    std::vector<int64_t> br_items(1, 0), bus_items(1, 0), gen_items(1, 0);
+    std::vector<int64_t> br_items(1, 0), bus_items(1, 0), gen_items(1, 0), st_items(1, 0);
+    std::vector<int32_t> st_busid;
 
     int64_t xo = 0, co = 0, jo = 0, ho = 0, so = 0, po = 0;
     M->inst.resize(ninst);
@@ -570,6 +571,9 @@ int build_model(const opf_network *nets, int32_t ninst, const opf_batch_opts *op
         br_items.push_back(br_items.back() + (int64_t)nl * T);
         bus_items.push_back(bus_items.back() + (int64_t)nb * T);
         gen_items.push_back(gen_items.back() + (int64_t)ng * T);
+        st_items.push_back(st_items.back() + (int64_t)ns * T);
+        for (int k = 0; k < ns; k++)
+            st_busid.push_back(stor[s].bus[k]);
     }
     M->link_c0 = co;
     M->link_j0 = jo;
@@ -614,6 +618,7 @@ int build_model(const opf_network *nets, int32_t ninst, const opf_batch_opts *op
     M->nbr_items = br_items.back();
     M->nbus_items = bus_items.back();
     M->ngen_items = gen_items.back();
+    M->nst_items = st_items.back();
     M->narc_slots = so;
     M->max_part = 16 * M->num_sms;
     M->launch = opf_launch{128, 128, 0, 0, 0, 0};
@@ -637,7 +642,7 @@ int build_model(const opf_network *nets, int32_t ninst, const opf_batch_opts *op
     UP(bus_a, bus_a) UP(bus_b, bus_b) UP(bus_c, bus_c) UP(gsbs, gsbs) UP(slot_code, slot_code) UP(gen_list, gen_list)
     UP(Pd, Pd) UP(Qd, Qd) UP(c2, c2) UP(c1, c1) UP(c0, c0) UP(pbnd, pbnd) UP(qbnd, qbnd)
     if (M->storage) {
-        UP(bus_st, bus_st) UP(st_list, st_list) UP(st_par, st_par)
+        UP(bus_st, bus_st) UP(st_list, st_list) UP(st_par, st_par) UP(st_busid, st_busid) UP(st_items, st_items)
     }
     UP(vbnd, vbnd) UP(inst, M->inst) UP(br_items, br_items) UP(bus_items, bus_items)
     UP(gen_items, gen_items)
