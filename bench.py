@@ -62,6 +62,7 @@ def parse():
                    help="fixed launch shape instead of the autotuner's (profiling runs)")
     p.add_argument("--e2e-steps", type=int, default=256)
     p.add_argument("--no-warm", action="store_true", help="skip the learned warm-start section")
+    p.add_argument("--no-rect", action="store_true", help="skip the rectangular-form section")
     p.add_argument("--warm-epochs", type=int, default=600)
     p.add_argument("--profile-batched", type=int, default=0, metavar="REPS",
                    help="profiling aid: only run REPS plain evaluations of the 10k-bus grid "
@@ -546,7 +547,7 @@ def main():
         batched = batched_vs_plain(torch, opf, synth, stream, dev, cpu=not args.no_cpu)
 
     rect = None
-    if rank == 0:
+    if rank == 0 and not args.no_rect:
         rect = rect_summary(torch, opf, synth, stream, dev, R, reps, ms_per_step * 1000.0)
 
     warm_start = None

@@ -25,7 +25,7 @@ struct opf_al {
     double *obj = nullptr, *part = nullptr;  // part: [3][nparts] block partials
     double *bpow = nullptr;  // device: beta1^k, beta2^k, 1 - beta1^k, 1 - beta2^k
     // one inner iteration captured as a CUDA graph per (x, lambda) pair: the
-    // loop replays it instead of launching its seven kernels one by one
+    // loop replays it instead of launching its six kernels one by one
     cudaStream_t cap = nullptr;
     struct Graph {
         const double *x, *lam;
@@ -110,17 +110,25 @@ __device__ __forceinline__ double block_max(double v, double *red)
     return s;
 }
 
-// mu = rho (s - clip(s, gl, gu)), s = c + lambda / rho; per-block partials
-// of the row violation (max), sum mu^2 and sum lambda^2
+// mu = rho (s - clip(s, gl, gu)), s = c + lambda / rho (lambda times the
+// host's 1 / rho); per-block partials of the row violation (max), sum mu^2
+// and sum lambda^2. With `advance`, block 0 also advances the step count's
+// bias corrections for the Adam kernel that follows in the stream.
 __global__ void al_mu_kernel(const double *c, const double *lam, const double *gl, const double *gu, int64_t m,
-                             double rho, double *mu, double *part, int nparts)
+                             double rho, double inv_rho, double *mu, double *part, int nparts, double *bp)
 {
     __shared__ double red[32];
+    if (bp && blockIdx.x == 0 && threadIdx.x == 0) {
+        bp[0] *= 0.9;
+        bp[1] *= 0.999;
+        bp[2] = 1.0 - bp[0];
+        bp[3] = 1.0 - bp[1];
+    }
     double viol = 0.0, smu = 0.0, slam = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
          i += (int64_t)gridDim.x * blockDim.x) {
         const double ci = c[i], li = lam ? lam[i] : 0.0;
-        const double s = ci + li / rho;
+        const double s = fma(li, inv_rho, ci);
         const double d = s - fmin(fmax(s, gl[i]), gu[i]);
         const double mi = rho * d;
         mu[i] = mi;
@@ -159,29 +167,22 @@ __global__ void al_stats_kernel(const double *obj, const double *part, int npart
     }
 }
 
-// the step count's bias corrections, kept on the device (one thread)
-__global__ void al_step_kernel(double *bp)
-{
-    bp[0] *= 0.9;
-    bp[1] *= 0.999;
-    bp[2] = 1.0 - bp[0];
-    bp[3] = 1.0 - bp[1];
-}
-
-// Adam step on G = grad + u, then projection onto [xl, xu]
+// Adam step on G = grad + u, then projection onto [xl, xu]; the bias
+// corrections enter as two per-thread scalars, lr / (1 - b1^k) and
+// 1 / (1 - b2^k), leaving one square root and one division per entry
 __global__ void al_adam_kernel(double *x, const double *grad, const double *u, const double *xl, const double *xu,
                                double *m1, double *m2, int64_t n, double lr, const double *bp)
 {
     const double b1 = 0.9, b2 = 0.999, eps = 1e-8;
-    const double bc1 = bp[2], bc2 = bp[3];
+    const double k1 = lr / bp[2], k2 = 1.0 / bp[3];
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
          j += (int64_t)gridDim.x * blockDim.x) {
         const double G = grad[j] + u[j];
-        const double a = b1 * m1[j] + (1.0 - b1) * G;
-        const double b = b2 * m2[j] + (1.0 - b2) * G * G;
+        const double a = fma(b1, m1[j], (1.0 - b1) * G);
+        const double b = fma(b2, m2[j], (1.0 - b2) * G * G);
         m1[j] = a;
         m2[j] = b;
-        const double xn = x[j] - lr * (a / bc1) / (sqrt(b / bc2) + eps);
+        const double xn = x[j] - k1 * a / (sqrt(b * k2) + eps);
         x[j] = fmin(fmax(xn, xl[j]), xu[j]);
     }
 }
@@ -194,14 +195,17 @@ int grid_of(int64_t n)
     return (int)(g < 1 ? 1 : g);
 }
 
-// f, grad f, g at x; mu; optional statistics
-int al_point(opf_al *a, const double *x, const double *lam, bool want_grad, double *d_stats, cudaStream_t s)
+// f, grad f, g at x; mu; optional statistics; `advance`: also advance the
+// Adam step count (an inner iteration)
+int al_point(opf_al *a, const double *x, const double *lam, bool want_grad, double *d_stats, cudaStream_t s,
+             bool advance = false)
 {
     EvalArgs e{x, nullptr, 1.0, a->obj, want_grad ? a->grad : nullptr, a->c, nullptr, nullptr};
     int rc = launch_eval(*a->M, e, W_OBJ | (want_grad ? W_GRAD : 0u) | W_CONS, s);
     if (rc)
         return rc;
-    al_mu_kernel<<<a->nparts, 256, 0, s>>>(a->c, lam, a->gl, a->gu, a->m, a->rho, a->mu, a->part, a->nparts);
+    al_mu_kernel<<<a->nparts, 256, 0, s>>>(a->c, lam, a->gl, a->gu, a->m, a->rho, 1.0 / a->rho, a->mu, a->part,
+                                           a->nparts, advance ? a->bpow : nullptr);
     if (d_stats)
         al_stats_kernel<<<1, 32, 0, s>>>(a->obj, a->part, a->nparts, a->rho, d_stats);
     return al_check(cudaGetLastError(), "multiplier kernels");
@@ -304,15 +308,15 @@ int opf_al_reset(opf_al *al, double rho, double lr)
 
 namespace {
 
-// one inner iteration on stream s: f, grad f, g, mu; J^T mu; step; Adam
+// one inner iteration on stream s: f, grad f, g, mu (and the step count);
+// J^T mu; Adam
 int al_inner(opf_al *al, double *d_x, const double *d_lambda, cudaStream_t s)
 {
-    int rc = al_point(al, d_x, d_lambda, true, nullptr, s);
+    int rc = al_point(al, d_x, d_lambda, true, nullptr, s, true);
     if (!rc)
         rc = launch_jtprod(*al->M, d_x, al->mu, al->u, s);
     if (rc)
         return rc;
-    al_step_kernel<<<1, 1, 0, s>>>(al->bpow);
     al_adam_kernel<<<grid_of(al->n), 256, 0, s>>>(d_x, al->grad, al->u, al->xl, al->xu, al->m1, al->m2, al->n,
                                                   al->lr, al->bpow);
     return al_check(cudaGetLastError(), "Adam step");
