@@ -25,7 +25,7 @@ struct opf_al {
     double *obj = nullptr, *part = nullptr;  // part: [3][nparts] block partials
     double *bpow = nullptr;  // device: beta1^k, beta2^k, 1 - beta1^k, 1 - beta2^k
     // one inner iteration captured as a CUDA graph per (x, lambda) pair: the
-    // loop replays it instead of launching its six kernels one by one
+    // loop replays it instead of launching its five kernels one by one
     cudaStream_t cap = nullptr;
     struct Graph {
         const double *x, *lam;
@@ -111,19 +111,12 @@ __device__ __forceinline__ double block_max(double v, double *red)
 }
 
 // mu = rho (s - clip(s, gl, gu)), s = c + lambda / rho (lambda times the
-// host's 1 / rho); per-block partials of the row violation (max), sum mu^2
-// and sum lambda^2. With `advance`, block 0 also advances the step count's
-// bias corrections for the Adam kernel that follows in the stream.
+// host's 1 / rho, as the J^T mu kernels form it); per-block partials of the
+// row violation (max), sum mu^2 and sum lambda^2
 __global__ void al_mu_kernel(const double *c, const double *lam, const double *gl, const double *gu, int64_t m,
-                             double rho, double inv_rho, double *mu, double *part, int nparts, double *bp)
+                             double rho, double inv_rho, double *mu, double *part, int nparts)
 {
     __shared__ double red[32];
-    if (bp && blockIdx.x == 0 && threadIdx.x == 0) {
-        bp[0] *= 0.9;
-        bp[1] *= 0.999;
-        bp[2] = 1.0 - bp[0];
-        bp[3] = 1.0 - bp[1];
-    }
     double viol = 0.0, smu = 0.0, slam = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -195,17 +188,15 @@ int grid_of(int64_t n)
     return (int)(g < 1 ? 1 : g);
 }
 
-// f, grad f, g at x; mu; optional statistics; `advance`: also advance the
-// Adam step count (an inner iteration)
-int al_point(opf_al *a, const double *x, const double *lam, bool want_grad, double *d_stats, cudaStream_t s,
-             bool advance = false)
+// f, grad f, g at x; mu; optional statistics
+int al_point(opf_al *a, const double *x, const double *lam, bool want_grad, double *d_stats, cudaStream_t s)
 {
     EvalArgs e{x, nullptr, 1.0, a->obj, want_grad ? a->grad : nullptr, a->c, nullptr, nullptr};
     int rc = launch_eval(*a->M, e, W_OBJ | (want_grad ? W_GRAD : 0u) | W_CONS, s);
     if (rc)
         return rc;
     al_mu_kernel<<<a->nparts, 256, 0, s>>>(a->c, lam, a->gl, a->gu, a->m, a->rho, 1.0 / a->rho, a->mu, a->part,
-                                           a->nparts, advance ? a->bpow : nullptr);
+                                           a->nparts);
     if (d_stats)
         al_stats_kernel<<<1, 32, 0, s>>>(a->obj, a->part, a->nparts, a->rho, d_stats);
     return al_check(cudaGetLastError(), "multiplier kernels");
@@ -308,13 +299,14 @@ int opf_al_reset(opf_al *al, double rho, double lr)
 
 namespace {
 
-// one inner iteration on stream s: f, grad f, g, mu (and the step count);
-// J^T mu; Adam
+// one inner iteration on stream s: grad f and g at x; J^T mu with mu formed
+// from g where the product reads it (and the step count advanced); Adam
 int al_inner(opf_al *al, double *d_x, const double *d_lambda, cudaStream_t s)
 {
-    int rc = al_point(al, d_x, d_lambda, true, nullptr, s, true);
+    EvalArgs e{d_x, nullptr, 1.0, nullptr, al->grad, al->c, nullptr, nullptr};
+    int rc = launch_eval(*al->M, e, W_GRAD | W_CONS, s);
     if (!rc)
-        rc = launch_jtprod(*al->M, d_x, al->mu, al->u, s);
+        rc = launch_jtprod_al(*al->M, d_x, al->c, d_lambda, al->gl, al->gu, al->rho, al->u, al->bpow, s);
     if (rc)
         return rc;
     al_adam_kernel<<<grid_of(al->n), 256, 0, s>>>(d_x, al->grad, al->u, al->xl, al->xu, al->m1, al->m2, al->n,

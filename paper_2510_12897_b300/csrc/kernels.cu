@@ -73,6 +73,11 @@ struct KParams {
     int64_t nst_items;  // storage unit items (bus kernel with storage)
     const int32_t *order = nullptr;  // bus-phase order within an instance, or null for id order
     double *xw = nullptr;            // x, writable (branch phase that sets the flows)
+    // J^T mu of the augmented Lagrangian: v_i = mu_i = rho (s_i - clip(s_i, gl_i, gu_i)),
+    // s_i = c_i + lambda_i / rho, from the rows c (in P.c) and lambda (in P.lam)
+    const double *gl = nullptr, *gu = nullptr;
+    double rho = 1.0, inv_rho = 1.0;
+    double *bp = nullptr;            // the AL step count's bias corrections, advanced once
     const double *__restrict__ x;
     const double *__restrict__ lam;
     double sigma;
@@ -1018,6 +1023,17 @@ __global__ void __launch_bounds__(kBusBlockMax) bus_kernel(const KParams P)
 }
 
 // ---------------------------------------------------------------- J^T v --
+
+// entry i of the vector v of J^T v: the given v, or (AL) the augmented
+// Lagrangian's multiplier estimate mu_i computed from the row's value
+template <bool AL>
+__device__ __forceinline__ double vrow(const KParams &P, int64_t i)
+{
+    if (!AL)
+        return __ldg(P.lam + i);
+    const double s = fma(__ldg(P.lam + i), P.inv_rho, __ldg(P.c + i));
+    return P.rho * (s - fmin(fmax(s, __ldg(P.gl + i)), __ldg(P.gu + i)));
+}
 //
 // out = J^T v, term by term (no Jacobian stored). Branch phase: the flow,
 // angle and thermal rows of a branch give the p, q entries of its two arcs
@@ -1027,7 +1043,7 @@ __global__ void __launch_bounds__(kBusBlockMax) bus_kernel(const KParams P)
 // reference and balance-row terms; generator items take their balance,
 // ramp and linking rows.
 
-template <bool ONE, bool RECT = false>
+template <bool ONE, bool RECT = false, bool AL = false>
 __global__ void __launch_bounds__(512) jt_branch_kernel(const KParams P)
 {
     cudaTriggerProgrammaticLaunchCompletion();
@@ -1072,13 +1088,14 @@ __global__ void __launch_bounds__(512) jt_branch_kernel(const KParams P)
         const double vmf = __ldg(xs + ivm + f), vmt = __ldg(xs + ivm + b);
         const double pf = __ldg(xs + ip + ck), pt = __ldg(xs + ip + nl + ck);
         const double qf = __ldg(xs + iq + ck), qt = __ldg(xs + iq + nl + ck);
-        const double *V = P.lam + I.c0 + (T + rk);  // the vector v, indexed like the rows
-        const double m1 = __ldg(V), m2 = __ldg(V + nlT), m3 = __ldg(V + 2 * nlT), m4 = __ldg(V + 3 * nlT);
-        const double va_ = __ldg(V + 4 * nlT);
-        const double tf = __ldg(V + (5 * nlT + 2 * nbT)), tt = __ldg(V + (6 * nlT + 2 * nbT));
-        const double *VB = P.lam + I.c0 + (T + 5 * nlT + nb * ct);  // balance rows, period ct
-        const double bPf = __ldg(VB + f), bPt = __ldg(VB + b);
-        const double bQf = __ldg(VB + nbT + f), bQt = __ldg(VB + nbT + b);
+        const int64_t V = I.c0 + (T + rk);  // the vector v, indexed like the rows
+        const double m1 = vrow<AL>(P, V), m2 = vrow<AL>(P, V + nlT), m3 = vrow<AL>(P, V + 2 * nlT),
+                     m4 = vrow<AL>(P, V + 3 * nlT);
+        const double va_ = vrow<AL>(P, V + 4 * nlT);
+        const double tf = vrow<AL>(P, V + (5 * nlT + 2 * nbT)), tt = vrow<AL>(P, V + (6 * nlT + 2 * nbT));
+        const int64_t VB = I.c0 + (T + 5 * nlT + nb * ct);  // balance rows, period ct
+        const double bPf = vrow<AL>(P, VB + f), bPt = vrow<AL>(P, VB + b);
+        const double bQf = vrow<AL>(P, VB + nbT + f), bQt = vrow<AL>(P, VB + nbT + b);
         const double2 Yff = cur.yff, Yft = cur.yft, Ytf = cur.ytf, Ytt = cur.ytt;
         double *o = P.grad + I.x0;  // P.grad carries `out`
         if constexpr (RECT) {
@@ -1087,7 +1104,7 @@ __global__ void __launch_bounds__(512) jt_branch_kernel(const KParams P)
             // (Df/2)|V_f|^2 + (Dt/2)|V_t|^2 + aR wR + aI wI (angle rows: v at
             // the upper row's and the lower row's places)
             const double a1 = va_;
-            const double a2 = __ldg(V + (7 * nlT + 2 * nbT));
+            const double a2 = vrow<AL>(P, V + (7 * nlT + 2 * nbT));
             const double2 tn = __ldg(d.tanb + (I.br0 + ck));
             const double aR = neg(fma(m1, Yft.x, fma(neg(m2), Yft.y, fma(m3, Ytf.x,
                               fma(neg(m4), Ytf.y, fma(a1, tn.x, a2 * tn.y))))));
@@ -1137,11 +1154,17 @@ __global__ void __launch_bounds__(512) jt_branch_kernel(const KParams P)
     }
 }
 
-template <bool ONE, bool RECT = false, bool STOR = false>
+template <bool ONE, bool RECT = false, bool STOR = false, bool AL = false>
 __global__ void __launch_bounds__(256) jt_bus_kernel(const KParams P)
 {
     cudaTriggerProgrammaticLaunchCompletion();
     cudaGridDependencySynchronize();
+    if (AL && P.bp && blockIdx.x == 0 && threadIdx.x == 0) {  // the next Adam step's bias corrections
+        P.bp[0] *= 0.9;
+        P.bp[1] *= 0.999;
+        P.bp[2] = 1.0 - P.bp[0];
+        P.bp[3] = 1.0 - P.bp[1];
+    }
     const DevArrays &d = P.d;
     const int64_t total = P.nbus_items + P.ngen_items;
     for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < total;
@@ -1169,24 +1192,24 @@ __global__ void __launch_bounds__(256) jt_bus_kernel(const KParams P)
         const int nl = I.nl, nb = I.nb, ng = I.ng, T = I.T;
         const int nbT = nb * T, ngT = ng * T, nlT = nl * T, na = 2 * nl;
         const double *__restrict__ xs = P.x + I.x0;
-        const double *V = P.lam + I.c0;
+        const int64_t V = I.c0;  // the vector v, indexed like the rows
         double *o = P.grad + I.x0;
         if (it < P.nbus_items) {
             const int i = e, ib = I.bus0 + i;
             const int4 a = __ldg(d.bus_a + ib);
             const double2 gb = __ldg(d.gsbs + ib);
             const double vm = __ldg(xs + nbT + nb * t + i);
-            const double vP = __ldg(V + (T + 5 * nlT + nb * t + i)), vQ = __ldg(V + (T + 5 * nlT + nbT + nb * t + i));
+            const double vP = vrow<AL>(P, V + (T + 5 * nlT + nb * t + i)), vQ = vrow<AL>(P, V + (T + 5 * nlT + nbT + nb * t + i));
             const double2 *Sg = reinterpret_cast<const double2 *>(d.arcs + I.scr0 + (int64_t)na * t + a.x);
             double dva, dvm;
             if constexpr (RECT) {  // vr, vi: 2 V (gs vP - bs vQ + vV); the reference row is vi_ref
                 const double vr = __ldg(xs + nb * t + i);
-                const double vV = __ldg(V + (T + 8 * nlT + 2 * nbT + nb * t + i));
+                const double vV = vrow<AL>(P, V + (T + 8 * nlT + 2 * nbT + nb * t + i));
                 const double k = twice(fma(gb.x, vP, fma(neg(gb.y), vQ, vV)));
                 dva = vr * k;
-                dvm = fma(vm, k, i == I.ref ? __ldg(V + t) : 0.0);
+                dvm = fma(vm, k, i == I.ref ? vrow<AL>(P, V + t) : 0.0);
             } else {
-                dva = i == I.ref ? __ldg(V + t) : 0.0;
+                dva = i == I.ref ? vrow<AL>(P, V + t) : 0.0;
                 dvm = twice(vm * fma(gb.x, vP, neg(gb.y * vQ)));  // 2 vm (gs vP - bs vQ)
             }
             for (int q = 0; q < a.y - a.x; q++) {
@@ -1199,16 +1222,16 @@ __global__ void __launch_bounds__(256) jt_bus_kernel(const KParams P)
                 const int ns = I.ns, nsT = ns * T;
                 const int ist = 2 * nbT + 2 * ngT + 2 * na * T;
                 const double iv2 = 1.0 / (vm * vm);
-                const double *Vs = V + I.st_c;
+                const int64_t Vs = V + I.st_c;
                 for (int e = stb.x; e < stb.y; e++) {
                     const int k = __ldg(d.st_list + e);
                     const double4_16a par = ldg4(d.st_par + I.st0 + k);
                     const int r = k + ns * t, v = ist + r;
                     const double ps = __ldg(xs + v), qs = __ldg(xs + v + nsT);
                     const double sc = __ldg(xs + v + 2 * nsT), sd = __ldg(xs + v + 3 * nsT);
-                    const double vs = __ldg(Vs + r), vl = __ldg(Vs + nsT + r), vt = __ldg(Vs + 2 * nsT + r);
-                    const double vc = I.st_compl ? __ldg(Vs + 3 * nsT + r) : 0.0;
-                    const double vn = t + 1 < T ? __ldg(Vs + r + ns) : 0.0;  // next period's state of charge
+                    const double vs = vrow<AL>(P, Vs + r), vl = vrow<AL>(P, Vs + nsT + r), vt = vrow<AL>(P, Vs + 2 * nsT + r);
+                    const double vc = I.st_compl ? vrow<AL>(P, Vs + 3 * nsT + r) : 0.0;
+                    const double vn = t + 1 < T ? vrow<AL>(P, Vs + r + ns) : 0.0;  // next period's state of charge
                     const double rr = twice(par.z) * iv2;  // 2 r / vm^2
                     dvm = fma(vl * rr, fma(ps, ps, qs * qs) / vm, dvm);
                     o[v] = fma(twice(ps), vt, fma(vl, fma(neg(rr), ps, 1.0), vP));
@@ -1223,22 +1246,22 @@ __global__ void __launch_bounds__(256) jt_bus_kernel(const KParams P)
         } else {
             const int g = e;
             const int bus = __ldg(d.gen_busid + I.gen0 + g);
-            double vpg = neg(__ldg(V + (T + 5 * nlT + nb * t + bus)));
-            const double vqg = neg(__ldg(V + (T + 5 * nlT + nbT + nb * t + bus)));
+            double vpg = neg(vrow<AL>(P, V + (T + 5 * nlT + nb * t + bus)));
+            const double vqg = neg(vrow<AL>(P, V + (T + 5 * nlT + nbT + nb * t + bus)));
             if (I.ramp) {  // rows pg_t - pg_{t-1}, t = 1..T-1
                 const int rb = T + (RECT ? 8 * nlT + 3 * nbT : 7 * nlT + 2 * nbT);
                 if (t >= 1)
-                    vpg += __ldg(V + (rb + g + ng * (t - 1)));
+                    vpg += vrow<AL>(P, V + (rb + g + ng * (t - 1)));
                 if (t + 1 <= T - 1)
-                    vpg -= __ldg(V + (rb + g + ng * t));
+                    vpg -= vrow<AL>(P, V + (rb + g + ng * t));
             }
             if (I.link_c >= 0)  // rows pg_s - pg_0 of instance s >= 1
-                vpg += __ldg(P.lam + I.link_c + g);
+                vpg += vrow<AL>(P, I.link_c + g);
             if (I.res_c >= 0)  // the instance's reserve row of this period
-                vpg += __ldg(P.lam + I.res_c + t);
+                vpg += vrow<AL>(P, I.res_c + t);
             if (P.link && s == 0)  // instance 0 appears in every linking row
                 for (int q = 1; q < P.ninst; q++)
-                    vpg -= __ldg(P.lam + P.link_c0 + g + (int64_t)ng * (q - 1));
+                    vpg -= vrow<AL>(P, P.link_c0 + g + (int64_t)ng * (q - 1));
             o[2 * nbT + ng * t + g] = vpg;
             o[2 * nbT + ngT + ng * t + g] = vqg;
         }
@@ -1610,38 +1633,66 @@ int launch_status()
 }
 }  // namespace
 
-int launch_jtprod(Model &M, const double *x, const double *v, double *out, cudaStream_t s)
+namespace {
+template <bool AL>
+int jtprod_launch(Model &M, const KParams &P, cudaStream_t s)
 {
-    KParams P = base_params(M);
-    P.x = x;
-    P.lam = v;
-    P.grad = out;
     const int gb = grid_for(M.nbr_items, 128, 0, M.num_sms, 0);
     const int gu = grid_for(M.nbus_items + M.ngen_items, 128, 0, M.num_sms, 0);
     const bool one = M.ninst == 1;
     cudaError_t e = cudaSuccess;
     if (M.rect) {
         if (M.nbr_items > 0)
-            e = one ? launch_pdl(jt_branch_kernel<true, true>, gb, 128, s, P)
-                    : launch_pdl(jt_branch_kernel<false, true>, gb, 128, s, P);
+            e = one ? launch_pdl(jt_branch_kernel<true, true, AL>, gb, 128, s, P)
+                    : launch_pdl(jt_branch_kernel<false, true, AL>, gb, 128, s, P);
         if (e == cudaSuccess)
-            e = one ? launch_pdl(jt_bus_kernel<true, true>, gu, 128, s, P)
-                    : launch_pdl(jt_bus_kernel<false, true>, gu, 128, s, P);
+            e = one ? launch_pdl(jt_bus_kernel<true, true, false, AL>, gu, 128, s, P)
+                    : launch_pdl(jt_bus_kernel<false, true, false, AL>, gu, 128, s, P);
     } else {
         if (M.nbr_items > 0)
-            e = one ? launch_pdl(jt_branch_kernel<true>, gb, 128, s, P)
-                    : launch_pdl(jt_branch_kernel<false>, gb, 128, s, P);
+            e = one ? launch_pdl(jt_branch_kernel<true, false, AL>, gb, 128, s, P)
+                    : launch_pdl(jt_branch_kernel<false, false, AL>, gb, 128, s, P);
         if (e == cudaSuccess && M.storage)
-            e = one ? launch_pdl(jt_bus_kernel<true, false, true>, gu, 128, s, P)
-                    : launch_pdl(jt_bus_kernel<false, false, true>, gu, 128, s, P);
+            e = one ? launch_pdl(jt_bus_kernel<true, false, true, AL>, gu, 128, s, P)
+                    : launch_pdl(jt_bus_kernel<false, false, true, AL>, gu, 128, s, P);
         else if (e == cudaSuccess)
-            e = one ? launch_pdl(jt_bus_kernel<true>, gu, 128, s, P) : launch_pdl(jt_bus_kernel<false>, gu, 128, s, P);
+            e = one ? launch_pdl(jt_bus_kernel<true, false, false, AL>, gu, 128, s, P)
+                    : launch_pdl(jt_bus_kernel<false, false, false, AL>, gu, 128, s, P);
     }
     if (e != cudaSuccess) {
         set_error("kernel launch failed: %s", cudaGetErrorString(e));
         return OPF_ECUDA;
     }
     return launch_status();
+}
+}  // namespace
+
+int launch_jtprod(Model &M, const double *x, const double *v, double *out, cudaStream_t s)
+{
+    KParams P = base_params(M);
+    P.x = x;
+    P.lam = v;
+    P.grad = out;
+    return jtprod_launch<false>(M, P, s);
+}
+
+// out = J^T mu with the augmented Lagrangian's mu_i = rho (s_i - clip(s_i,
+// gl_i, gu_i)), s_i = c_i + lambda_i / rho, computed where each entry is
+// read from the rows c at x (no mu vector); advances the step state bp
+int launch_jtprod_al(Model &M, const double *x, const double *c, const double *lam, const double *gl,
+                     const double *gu, double rho, double *out, double *bp, cudaStream_t s)
+{
+    KParams P = base_params(M);
+    P.x = x;
+    P.lam = lam;
+    P.c = const_cast<double *>(c);  // read only in this mode
+    P.gl = gl;
+    P.gu = gu;
+    P.rho = rho;
+    P.inv_rho = 1.0 / rho;
+    P.bp = bp;
+    P.grad = out;
+    return jtprod_launch<true>(M, P, s);
 }
 
 int launch_cons_setflows(Model &M, double *x, double *obj, double *grad, double *c, cudaStream_t s)

@@ -184,6 +184,10 @@ int launch_eval(Model &M, const EvalArgs &a, unsigned what, cudaStream_t s, int 
 int launch_flat_start(Model &M, double *x, cudaStream_t s);
 int launch_sincos(Model &M, const double *d, int64_t n, double *sn, double *cs, cudaStream_t s);
 int launch_jtprod(Model &M, const double *x, const double *v, double *out, cudaStream_t s);
+// J^T mu of the augmented Lagrangian, mu from the rows c, lambda and the row
+// bounds where it is read; advances the step state bp (4 doubles) if not null
+int launch_jtprod_al(Model &M, const double *x, const double *c, const double *lam, const double *gl,
+                     const double *gu, double rho, double *out, double *bp, cudaStream_t s);
 int launch_flows(Model &M, double *x, cudaStream_t s);
 // single instance: p, q := flows at x's voltages (written into x), then the
 // objective, gradient and constraints at that point (flow rows zero)
