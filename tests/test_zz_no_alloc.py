@@ -35,16 +35,20 @@ def _close(name, got, ref, scale):
     assert not bad.any(), f"{name}: {int(bad.sum())} entries differ beyond the tolerance"
 
 
-@pytest.mark.parametrize("which", ["case30_general", "case10k", "mp30x6"])
+@pytest.mark.parametrize("which", ["case30_general", "case10k", "mp30x6", "rect30", "storage30x4"])
 def test_noalloc_matches_eval_all_twice(torch, oracle_mod, which):
     g = {"case30_general": lambda: synth.case30(general=True),
          "case10k": lambda: synth.case10k(),
          "mp30x6": lambda: synth.multi_period(synth.case30(general=True), 6, seed=4, ramp_ratio=0.2),
+         "rect30": lambda: synth.case30(general=True),
+         "storage30x4": lambda: synth.with_storage(synth.multi_period(synth.case30(general=True), 4, seed=4,
+                                                                      ramp_ratio=0.2)),
          }[which]()
-    M = opf.Model(g)
-    O = oracle_mod.Oracle(g)
+    opts = dict(form="rect") if which == "rect30" else dict(compl=True) if which == "storage30x4" else {}
+    M = opf.Model(g, **opts)
+    O = oracle_mod.Oracle(g, **opts)
     rng = np.random.default_rng(21)
-    x = synth.random_point(g, rng)
+    x = synth.random_point(g, rng, form=opts.get("form", "polar"))
     lam = rng.standard_normal(M.m)
     dev = torch.device("cuda")
     dx = torch.tensor(x, device=dev)
