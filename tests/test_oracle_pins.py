@@ -73,7 +73,7 @@ def test_sizes_closed_form(oracle_mod, gen):
     assert O.m == 1 + 7 * nl + 2 * nb
     assert O.nnzj == 1 + 30 * nl + 2 * nb + 2 * ng
     assert O.nnzh == 2 * with_branch + nb + 4 * len(pairs) + ng + 4 * nl
-    if not gen:  # the survey's 30-bus figures
+    if not gen:  # the 30-bus workload's closed-form figures
         assert (O.n, O.m, O.nnzj, O.nnzh) == (236, 348, 1303, 424)
 
 
