@@ -297,9 +297,13 @@ int opf_get_launch(const opf_model *model, opf_launch *cfg);
 int opf_set_launch(opf_model *model, const opf_launch *cfg);
 
 /* Autotuner: times each candidate launch shape (block sizes, persistence,
- * bus order, branch occupancy) of the fused opf_eval_all on this model (CUDA events, `reps` repetitions each, on `stream`), keeps the
- * fastest and returns it in *best with its time per eval in *best_us.
- * Allocates temporary output buffers for the duration of the call. */
+ * bus order, branch occupancy) of the fused opf_eval_all on this model as a
+ * CUDA graph of `reps` back-to-back evaluations (the way a solver loop
+ * replays them), on a private stream that first waits for `stream`; the six
+ * fastest are timed again over more launches. Keeps the fastest and returns
+ * it in *best with its time per eval in *best_us (CUDA events). Allocates
+ * temporary output buffers and a stream for the duration of the call, which
+ * synchronises with its own work before returning. */
 int opf_autotune(opf_model *model, const double *d_x, const double *d_lambda, int32_t reps,
                  void *stream, opf_launch *best, double *best_us);
 
