@@ -446,11 +446,17 @@ __global__ void __launch_bounds__(OCC ? 256 : 512, OCC ? 3 : 1) rect_branch_kern
     }
     cudaGridDependencySynchronize();
 
+    const int64_t first = it;
     for (; it < P.nbr_items; it += stride) {
+        if (OCC && it != first) {  // the low-register build loads each item's static data here
+            locate(it, s, t, k, kb);
+            st = load_br(d, kb, CONS, JAC);
+            tb = __ldg(d.tanb + kb);
+        }
         const BrStatic cur = st;
         const double2 tan_ = tb;
         const int cs = s, ct = t, ck = k;
-        if (it + stride < P.nbr_items) {  // prefetch the next item's static data
+        if (!OCC && it + stride < P.nbr_items) {  // prefetch the next item's static data
             locate(it + stride, s, t, k, kb);
             st = load_br(d, kb, CONS, JAC);
             tb = __ldg(d.tanb + kb);
