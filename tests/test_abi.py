@@ -253,3 +253,18 @@ def test_storage_structure_matches_oracle(oracle_mod):
             opf.Model(bad, structure_only=True)
     with pytest.raises(opf.OpfError, match="polar"):
         opf.Model(g, structure_only=True, form="rect")
+
+
+def test_hub_bus_structure_matches_oracle(oracle_mod):
+    """A bus with 45 arc slots (more than the 32 the per-bus bitmask covers):
+    patterns equal the oracle's bit for bit in every form."""
+    from paper_2510_12897_b300 import opf, synth
+    from tests.test_hub_gpu import hub_grid
+    g = hub_grid()
+    for opts, gg in (({}, g), (dict(form="rect"), g),
+                     (dict(compl=True), synth.with_storage(synth.multi_period(g, 3, seed=5, ramp_ratio=0.2)))):
+        M = opf.Model(gg, structure_only=True, **opts)
+        O = oracle_mod.Oracle(gg, **opts)
+        assert (M.n, M.m, M.nnzj, M.nnzh) == (O.n, O.m, O.nnzj, O.nnzh)
+        for a, b in zip(M.jac_pattern() + M.hess_pattern(), O.jac_pattern() + O.hess_pattern()):
+            np.testing.assert_array_equal(a, b)
