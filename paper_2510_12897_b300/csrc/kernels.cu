@@ -8,14 +8,22 @@
 //                diagonals, and the branch's second-order contributions to
 //                its two end buses' Hessian rows, which it stores in the
 //                per-arc scratch at the arc's slot in its bus's arc list.
-//  bus phase     one thread per (instance, period, bus) item, then one per
-//                (instance, period, generator) item. Sums the balance rows
-//                (the constraint! augmentations of Listing 3), writes their
-//                Jacobian rows, assembles the bus's Hessian rows va_i and vm_i
-//                from its slots in a fixed order (no atomics), and evaluates
-//                the cost, its gradient and Hessian, ramp rows (Listing 6) and
-//                linking rows. The objective is reduced in a fixed order by the
-//                last block to finish.
+//  bus phase     one thread per (instance, period, generator) item, then
+//                one per (instance, period, bus) item, then (storage models)
+//                one per (instance, period, storage unit). Sums the balance
+//                rows (the constraint! augmentations of Listing 3), writes
+//                their Jacobian rows, assembles the bus's Hessian rows va_i
+//                and vm_i from its slots in a fixed order (no atomics), and
+//                evaluates the cost, its gradient and Hessian, ramp rows
+//                (Listing 6) and linking rows; storage items write their
+//                unit's rows and derivatives. The objective is reduced in a
+//                fixed order by the last block to finish. A reserve kernel
+//                adds the reserve rows of batches that have them.
+//
+// The rectangular form (vr, vi in the places of va, vm) has its own branch
+// kernel and a template variant of the bus kernel; J^T v runs the same two
+// phases term by term (and, for the augmented-Lagrangian loop, forms each
+// multiplier from its row's value where it reads it).
 //
 // Both kernels are launched with programmatic dependent launch: each block
 // first loads the static network data of its first item (which no kernel

@@ -74,3 +74,13 @@ def test_storage_rejections(torch):
     bad = g.copy(storage=synth.replace(g.storage, dt=0.0))
     with pytest.raises(opf.OpfError, match="dt"):
         opf.Model(bad)
+
+
+def test_storage_single_period(torch, oracle_mod):
+    """One period: every state-of-charge row has its first-period form
+    (no previous energy)."""
+    g = synth.with_storage(synth.case30(general=True))
+    M, O = both(torch, oracle_mod, g, compl=True)
+    for x, lam in points(g, M.m, 3, seed=24):
+        check_against_oracle(O, run_all(torch, M, x, lam, 1.0), x, lam, 1.0)
+        jtprod_check(torch, M, O, x, lam)
