@@ -480,6 +480,14 @@ def main():
                 "frac": achieved / hbm, "traffic": profile_traffic(dominant),
                 "kernel": f"{dominant} phase", "kernel_us": dom_us,
                 "algorithmic_bytes_per_launch": dom_bytes, "peak_kind": peak_kind}
+    # the other phase, same arithmetic (both phases take about the same time)
+    oth, oth_us = ("bus", bus_us) if dominant == "branch" else ("branch", br_us)
+    oth_bytes = ev_bytes - br_bytes if oth == "bus" else br_bytes
+    roofline["other_phase"] = {"kernel": f"{oth} phase", "kernel_us": oth_us,
+                               "algorithmic_bytes_per_launch": oth_bytes,
+                               "achieved": oth_bytes / (oth_us * 1e-6) / 1e9,
+                               "frac": oth_bytes / (oth_us * 1e-6) / 1e9 / hbm,
+                               "traffic": profile_traffic(oth)}
 
     # one augmented-Lagrangian inner iteration (f, grad f, g, J^T mu, Adam
     # step) on the 10k grid: the callbacks inside a solver loop
