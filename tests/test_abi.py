@@ -19,8 +19,10 @@ def L():
 
 
 def test_exports_every_declared_symbol(L):
-    names = opf.declared_symbols() + opf.declared_symbols(os.path.join(os.path.dirname(opf.HEADER), "opf_warm.h"))
-    assert "opf_warm_train_step" in names and "opf_eval_all" in names
+    inc = os.path.dirname(opf.HEADER)
+    names = (opf.declared_symbols() + opf.declared_symbols(os.path.join(inc, "opf_warm.h"))
+             + opf.declared_symbols(os.path.join(inc, "opf_al.h")))
+    assert "opf_warm_train_step" in names and "opf_eval_all" in names and "opf_al_iterate" in names
     assert "opf_eval_jac_hess" in names and "opf_model_create" in names
     for name in names:
         assert hasattr(L, name), name
