@@ -150,7 +150,11 @@ typedef struct {
     int32_t bus_ctas_per_sm;
     int32_t bus_order;    /* 0: buses in id order; 1: buses sorted by arc count into warps
                              of 32, warps dealt heaviest and lightest alternately (fewer
-                             idle lanes in the slot loops: better for large batches) */
+                             idle lanes in the slot loops: better for large batches);
+                             2: buses with more than 6 arc slots (and at most 32) a warp
+                             each, one lane per slot, the others a thread each in id order
+                             (shorter longest thread: better for single instances; the
+                             rectangular form and storage models run 2 as 0) */
     int32_t branch_occupancy; /* 0: branch kernel compiled for up to 128 registers per
                                  thread (shortest chains); 1: for 80 (three blocks of 256
                                  per SM: more warps to hide latency in large batches) */

@@ -513,8 +513,8 @@ int opf_set_launch(opf_model *m, const opf_launch *cfg)
             set_error("block size %d not a multiple of 32 in [32, 1024]", b);
             return OPF_EINVAL;
         }
-    if (cfg->bus_order < 0 || cfg->bus_order > 1 || cfg->branch_occupancy < 0 || cfg->branch_occupancy > 1) {
-        set_error("bus_order and branch_occupancy must be 0 or 1");
+    if (cfg->bus_order < 0 || cfg->bus_order > 2 || cfg->branch_occupancy < 0 || cfg->branch_occupancy > 1) {
+        set_error("bus_order must be 0, 1 or 2 and branch_occupancy 0 or 1");
         return OPF_EINVAL;
     }
     if (cfg->branch_block > (cfg->branch_occupancy ? 256 : 512)) {
@@ -608,7 +608,7 @@ int opf_autotune(opf_model *m, const double *d_x, const double *d_lambda, int32_
     const int ublocks[] = {32, 64, 128, 256};  // the bus kernel stages at most 8 warps
     const int ctas[] = {0, 2, 4, 8, 16};
     for (int occ = 0; occ < 2 && !rc; occ++)
-    for (int order = 0; order < 2 && !rc; order++)
+    for (int order = 0; order < 3 && !rc; order++)
     for (int bb : bblocks)
         for (int bu : ublocks)
             for (int cb : ctas)

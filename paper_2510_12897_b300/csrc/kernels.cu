@@ -84,6 +84,8 @@ struct KParams {
     int32_t want_grad, want_obj;
     int64_t nbr_items, nbus_items, ngen_items;
     int64_t nst_items;  // storage unit items (bus kernel with storage)
+    int64_t nlight_items, nheavy_items;  // split bus phase: light-bus items, heavy-bus items
+    int32_t split_tblocks = 0;  // split bus phase: blocks of generator and light-bus items
     const int32_t *order = nullptr;  // bus-phase order within an instance, or null for id order
     double *xw = nullptr;            // x, writable (branch phase that sets the flows)
     // J^T mu of the augmented Lagrangian: v_i = mu_i = rho (s_i - clip(s_i, gl_i, gu_i)),
@@ -601,16 +603,175 @@ __global__ void __launch_bounds__(OCC ? 256 : 512, OCC ? 3 : 1) rect_branch_kern
 
 constexpr int kBusBlockMax = 256;
 
-template <bool CONS, bool JAC, bool HESS, bool ONE, bool RECT = false, bool STOR = false>
+// Split bus phase, heavy buses: one warp per (instance, period, bus) with
+// kLightSlots < slots <= 32, one lane per slot. A segmented inclusive scan
+// (shuffles, fixed order) sums each group of parallel arcs, whose last lane
+// writes the group's off-diagonal Hessian entries; butterfly sums (fixed
+// order) give the bus totals, and lane 0 finishes the bus exactly as a
+// light bus's thread does (polar form, no storage).
+__device__ __forceinline__ double seg_scan(double v, int lane, int head)
+{
+#pragma unroll
+    for (int dd = 1; dd < 32; dd <<= 1) {
+        const double y = __shfl_up_sync(0xffffffffu, v, dd);
+        if (lane - dd >= head)
+            v += y;
+    }
+    return v;
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int dd = 16; dd; dd >>= 1)
+        v += __shfl_xor_sync(0xffffffffu, v, dd);
+    return v;
+}
+
+template <bool CONS, bool JAC, bool HESS, bool ONE>
+__device__ void heavy_bus_warp(const KParams &P)
+{
+    const DevArrays &d = P.d;
+    const int lane = threadIdx.x & 31;
+    const int64_t hw = (int64_t)(blockIdx.x - P.split_tblocks) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (hw >= P.nheavy_items) {
+        cudaGridDependencySynchronize();
+        cudaTriggerProgrammaticLaunchCompletion();
+        return;
+    }
+    int s = 0, t = 0, h = 0;
+    if (ONE) {
+        split((int)hw, P.inst0.nheavy, P.inst0.T, t, h);
+    } else {
+        s = find_inst(d.heavy_items, P.ninst, hw);
+        const InstDev *Ip = d.inst + s;
+        split((int)(hw - __ldg(d.heavy_items + s)), __ldg(&Ip->nheavy), __ldg(&Ip->T), t, h);
+    }
+    const InstDev I = inst_of<ONE>(P, s);
+    const int i = __ldg(d.heavy_list + I.heavy0 + h);
+    const int ib = I.bus0 + i;
+    const int4 a = __ldg(d.bus_a + ib), b = __ldg(d.bus_b + ib);
+    const int2 m = __ldg(d.bus_c + ib);
+    const double2 gb = __ldg(d.gsbs + ib);
+    const int nsl = a.y - a.x;  // kLightSlots < nsl <= 32
+    const bool has = lane < nsl;
+    const unsigned code = has ? ((((unsigned)m.x >> lane) & 1u) | (lane < m.y ? 2u : 0u)) : 0u;
+    int gfirst = -1;
+    if (CONS && a.z < a.w)
+        gfirst = __ldg(d.gen_list + I.gl0 + a.z);
+    cudaGridDependencySynchronize();
+    cudaTriggerProgrammaticLaunchCompletion();
+
+    const int nl = I.nl, nb = I.nb, ng = I.ng, T = I.T;
+    const int nbT = nb * T, ngT = ng * T, nlT = nl * T, na = 2 * nl;
+    const double *__restrict__ xs = P.x + I.x0;
+    double2 v0 = make_double2(0.0, 0.0), v1 = make_double2(0.0, 0.0), v2 = make_double2(0.0, 0.0);
+    if (has) {
+        const double2 *S = reinterpret_cast<const double2 *>(d.arcs + I.scr0 + (int64_t)na * t + a.x + lane);
+        if (CONS)
+            v0 = __ldcg(S);
+        if (HESS) {
+            v1 = __ldcg(S + 1);
+            v2 = __ldcg(S + 2);
+        }
+    }
+    const int iva = nb * t, ivm = nbT + nb * t;
+    const double vm = __ldg(xs + ivm + i);
+    const int hva = (int)I.hva, hvm = (int)I.hvm;
+    double *Hvm = P.hess + I.h0 + (hva * T + hvm * t + b.z);
+    double *Hva = P.hess + I.h0 + (hva * t + b.y);
+    const int nd = b.w & 0xffff, nlt = b.w >> 16;
+    double taa = 0.0, tma = 0.0, tmm = 0.0, tp = 0.0, tq = 0.0;
+    if (HESS) {  // groups of parallel arcs end at SLOT_LAST slots
+        const unsigned below = (1u << lane) - 1u;
+        const unsigned tails = __ballot_sync(0xffffffffu, has && (code & SLOT_LAST));
+        const unsigned tb = tails & below;
+        const int ghead = tb ? 32 - __clz(tb) : 0;
+        const double gaa = seg_scan(v1.x, lane, ghead);
+        const double gma = seg_scan(v1.y, lane, ghead);
+        const double gmm = seg_scan(v2.y, lane, ghead);
+        if (has && (code & SLOT_LAST)) {
+            const int grp = __popc(tb);
+            Hvm[grp < nlt ? grp : grp + 1] = neg(gma);  // (vm_i, va_j)
+            if (code & SLOT_LOWER) {
+                Hva[grp] = neg(gaa);         // (va_i, va_j), j < i
+                Hvm[nd + 1 + grp] = gmm;     // (vm_i, vm_j), j < i
+            }
+        }
+        taa = warp_sum(v1.x);
+        tma = warp_sum(v1.y);
+        tmm = warp_sum(v2.x);
+    }
+    if (CONS) {
+        tp = warp_sum(v0.x);
+        tq = warp_sum(v0.y);
+    }
+    if (lane != 0)
+        return;
+    // lane 0: the bus's own terms, as for a light bus
+    const int ng_here = a.w - a.z;
+    if (P.want_grad) {
+        P.grad[I.x0 + iva + i] = 0.0;
+        P.grad[I.x0 + ivm + i] = 0.0;
+    }
+    if (i == I.ref) {
+        if (CONS)
+            P.c[I.c0 + t] = __ldg(xs + iva + i);
+        if (JAC)
+            P.jac[I.j0 + t] = 1.0;
+    }
+    if (JAC) {
+        const int jP = (int)I.jP;
+        double *JP = P.jac + I.j0 + (T + 22 * nlT + jP * t + b.x);
+        double *JQ = JP + jP * T;
+        const double v2m = twice(vm);
+        JP[0] = gb.x * v2m;
+        JQ[0] = neg(gb.y * v2m);
+        for (int e = 1; e <= ng_here; e++) {
+            JP[e] = -1.0;
+            JQ[e] = -1.0;
+        }
+    }
+    if (CONS) {
+        const double vm2 = vm * vm;
+        double Pb = fma(gb.x, vm2, __ldg(d.Pd + I.pd0 + (nb * t + i)));
+        double Qb = fma(neg(gb.y), vm2, __ldg(d.Qd + I.pd0 + (nb * t + i)));
+        for (int gp = a.z; gp < a.w; gp++) {
+            const int g = gp == a.z ? gfirst : __ldg(d.gen_list + I.gl0 + gp);
+            Pb -= __ldg(xs + 2 * nbT + ng * t + g);
+            Qb -= __ldg(xs + 2 * nbT + ngT + ng * t + g);
+        }
+        double *c = P.c + I.c0 + (T + 5 * nlT + nb * t + i);
+        c[0] = Pb + tp;
+        c[nbT] = Qb + tq;
+    }
+    if (HESS) {
+        const double *L = P.lam + I.c0 + (T + 5 * nlT + nb * t + i);
+        const double dmm = twice(fma(gb.x, __ldg(L), neg(gb.y * __ldg(L + nbT)))) + tmm;
+        Hva[nlt] = taa;
+        Hvm[nlt] = tma;
+        Hvm[nd + 1 + nlt] = dmm;
+    }
+}
+
+
+template <bool CONS, bool JAC, bool HESS, bool ONE, bool RECT = false, bool STOR = false, bool SPLIT = false>
 __global__ void __launch_bounds__(kBusBlockMax) bus_kernel(const KParams P)
 {
     __shared__ double wsum[32];
     __shared__ bool last;
+    if constexpr (SPLIT) {  // the blocks after the thread items take the heavy buses, a warp each
+        if ((int)blockIdx.x >= P.split_tblocks) {
+            heavy_bus_warp<CONS, JAC, HESS, ONE>(P);
+            return;
+        }
+    }
     const DevArrays &d = P.d;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t nbg = P.nbus_items + P.ngen_items;
+    const int64_t nbg = (SPLIT ? P.nlight_items : P.nbus_items) + P.ngen_items;
     const int64_t total = nbg + (STOR ? P.nst_items : 0);
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const unsigned tblocks = SPLIT ? (unsigned)P.split_tblocks : gridDim.x;
+    const int64_t stride = (int64_t)tblocks * blockDim.x;
     int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
 
     struct Item {
@@ -636,7 +797,13 @@ __global__ void __launch_bounds__(kBusBlockMax) bus_kernel(const KParams P)
         } else if (item >= P.ngen_items && item < nbg) {
             item -= P.ngen_items;
             int r, bus0;
-            if (ONE) {
+            if (SPLIT) {  // the light buses, in id order
+                q.s = ONE ? 0 : find_inst(d.light_items, P.ninst, item);
+                const InstDev *I = d.inst + q.s;
+                split((int)(item - (ONE ? 0 : __ldg(d.light_items + q.s))), __ldg(&I->nlight), __ldg(&I->T), q.t, r);
+                bus0 = ONE ? 0 : __ldg(&I->bus0);
+                q.e = __ldg(d.light_list + __ldg(&I->light0) + r);
+            } else if (ONE) {
                 q.s = 0;
                 split((int)item, P.inst0.nb, P.inst0.T, q.t, r);
                 bus0 = 0;
@@ -646,7 +813,8 @@ __global__ void __launch_bounds__(kBusBlockMax) bus_kernel(const KParams P)
                 split((int)(item - __ldg(d.bus_items + q.s)), __ldg(&I->nb), __ldg(&I->T), q.t, r);
                 bus0 = __ldg(&I->bus0);
             }
-            q.e = P.order ? __ldg(P.order + bus0 + r) : r;
+            if (!SPLIT)
+                q.e = P.order ? __ldg(P.order + bus0 + r) : r;
             const int ib = bus0 + q.e;
             q.a = __ldg(d.bus_a + ib);
             q.b = __ldg(d.bus_b + ib);
@@ -1003,9 +1171,9 @@ __global__ void __launch_bounds__(kBusBlockMax) bus_kernel(const KParams P)
     // Objective: fixed-order reduction (warp, block, then the last of the
     // blocks that can hold generator items sums their partials). Only those
     // blocks take part; they come first in the grid.
-    const int64_t per_pass = (int64_t)gridDim.x * blockDim.x;
+    const int64_t per_pass = stride;
     unsigned gblocks = P.ngen_items >= per_pass
-        ? gridDim.x : (unsigned)((P.ngen_items + blockDim.x - 1) / blockDim.x);
+        ? tblocks : (unsigned)((P.ngen_items + blockDim.x - 1) / blockDim.x);
     if (gblocks == 0)
         gblocks = 1;  // no generators: block 0 still writes the (zero) objective
     if (P.want_obj && blockIdx.x < gblocks) {
@@ -1504,7 +1672,7 @@ cudaError_t launch_pdl(K kernel, int grid, int block, cudaStream_t s, const KPar
 
 template <bool C, bool J, bool H>
 cudaError_t dispatch(const KParams &P, bool one, bool occ, bool rect, bool stor, bool run_branch, bool run_bus,
-                     int gb, int bb, int gu, int bu, cudaStream_t s)
+                     int gb, int bb, int gu, int bu, cudaStream_t s, bool splitb)
 {
     cudaError_t e = cudaSuccess;
     if (rect) {  // the rectangular branch kernel (two register budgets) and bus variant
@@ -1532,6 +1700,9 @@ cudaError_t dispatch(const KParams &P, bool one, bool occ, bool rect, bool stor,
     if (stor)  // storage units (polar only)
         return one ? launch_pdl(bus_kernel<C, J, H, true, false, true>, gu, bu, s, P)
                    : launch_pdl(bus_kernel<C, J, H, false, false, true>, gu, bu, s, P);
+    if (splitb)  // light buses a thread each, then heavy buses a warp each (gu counts both)
+        return one ? launch_pdl(bus_kernel<C, J, H, true, false, false, true>, gu, bu, s, P)
+                   : launch_pdl(bus_kernel<C, J, H, false, false, false, true>, gu, bu, s, P);
     return one ? launch_pdl(bus_kernel<C, J, H, true>, gu, bu, s, P)
                : launch_pdl(bus_kernel<C, J, H, false>, gu, bu, s, P);
 }
@@ -1553,6 +1724,8 @@ int launch_all(Model &M, const EvalArgs &a, unsigned what, cudaStream_t s, int p
     P.nbus_items = M.nbus_items;
     P.ngen_items = M.ngen_items;
     P.nst_items = M.nst_items;
+    P.nlight_items = M.nlight_items;
+    P.nheavy_items = M.nheavy_items;
     P.x = a.x;
     P.lam = a.lam;
     P.sigma = a.sigma;
@@ -1576,17 +1749,27 @@ int launch_all(Model &M, const EvalArgs &a, unsigned what, cudaStream_t s, int p
     const bool one = M.ninst == 1;
     const bool occ = L.branch_occupancy != 0;
     const int bb = L.branch_block;
-    P.order = L.bus_order ? M.d.bus_order : nullptr;
+    P.order = L.bus_order == 1 ? M.d.bus_order : nullptr;
+    // bus_order 2: the split bus phase where it applies (polar, no storage):
+    // light buses a thread each in the first blocks, heavy buses a warp each
+    // in the blocks after them; elsewhere buses in id order
+    const bool splitb = L.bus_order == 2 && M.split_ok && (phases & 2);
+    int gu_all = gu;
+    if (splitb) {
+        const int tb = grid_for(M.nlight_items + M.ngen_items, bu, L.bus_ctas_per_sm, M.num_sms, cap);
+        P.split_tblocks = tb;
+        gu_all = tb + (int)((M.nheavy_items + bu / 32 - 1) / (bu / 32));
+    }
     cudaError_t e;
     switch ((C ? 1 : 0) | (J ? 2 : 0) | (H ? 4 : 0)) {
-    case 0: e = dispatch<false, false, false>(P, one, occ, M.rect, M.storage, run_branch, run_bus, gb, bb, gu, bu, s); break;
-    case 1: e = dispatch<true, false, false>(P, one, occ, M.rect, M.storage, run_branch, run_bus, gb, bb, gu, bu, s); break;
-    case 2: e = dispatch<false, true, false>(P, one, occ, M.rect, M.storage, run_branch, run_bus, gb, bb, gu, bu, s); break;
-    case 3: e = dispatch<true, true, false>(P, one, occ, M.rect, M.storage, run_branch, run_bus, gb, bb, gu, bu, s); break;
-    case 4: e = dispatch<false, false, true>(P, one, occ, M.rect, M.storage, run_branch, run_bus, gb, bb, gu, bu, s); break;
-    case 5: e = dispatch<true, false, true>(P, one, occ, M.rect, M.storage, run_branch, run_bus, gb, bb, gu, bu, s); break;
-    case 6: e = dispatch<false, true, true>(P, one, occ, M.rect, M.storage, run_branch, run_bus, gb, bb, gu, bu, s); break;
-    default: e = dispatch<true, true, true>(P, one, occ, M.rect, M.storage, run_branch, run_bus, gb, bb, gu, bu, s); break;
+    case 0: e = dispatch<false, false, false>(P, one, occ, M.rect, M.storage, run_branch, run_bus, gb, bb, gu_all, bu, s, splitb); break;
+    case 1: e = dispatch<true, false, false>(P, one, occ, M.rect, M.storage, run_branch, run_bus, gb, bb, gu_all, bu, s, splitb); break;
+    case 2: e = dispatch<false, true, false>(P, one, occ, M.rect, M.storage, run_branch, run_bus, gb, bb, gu_all, bu, s, splitb); break;
+    case 3: e = dispatch<true, true, false>(P, one, occ, M.rect, M.storage, run_branch, run_bus, gb, bb, gu_all, bu, s, splitb); break;
+    case 4: e = dispatch<false, false, true>(P, one, occ, M.rect, M.storage, run_branch, run_bus, gb, bb, gu_all, bu, s, splitb); break;
+    case 5: e = dispatch<true, false, true>(P, one, occ, M.rect, M.storage, run_branch, run_bus, gb, bb, gu_all, bu, s, splitb); break;
+    case 6: e = dispatch<false, true, true>(P, one, occ, M.rect, M.storage, run_branch, run_bus, gb, bb, gu_all, bu, s, splitb); break;
+    default: e = dispatch<true, true, true>(P, one, occ, M.rect, M.storage, run_branch, run_bus, gb, bb, gu_all, bu, s, splitb); break;
     }
     if (e == cudaSuccess && M.reserve && (C || J) && (phases & 2)) {
         const int64_t threads = 32 * M.nres;
@@ -1643,6 +1826,8 @@ KParams base_params(Model &M)
     P.nbus_items = M.nbus_items;
     P.ngen_items = M.ngen_items;
     P.nst_items = M.nst_items;
+    P.nlight_items = M.nlight_items;
+    P.nheavy_items = M.nheavy_items;
     return P;
 }
 

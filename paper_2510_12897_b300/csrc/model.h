@@ -35,6 +35,11 @@ struct __align__(16) ArcScratch {
 constexpr int kTrigScale = 128;
 constexpr int kTrigK = 402;
 
+// split bus phase: buses with more arc slots than this (and at most 32) are
+// handled by a warp each, one lane per slot (6 measured best on the 10k
+// grid, among 4, 6, 8 and 10: a thread walks at most two chunks of slots)
+constexpr int kLightSlots = 6;
+
 // slot codes: the slot closes its far bus's group / the far bus is lower
 enum : uint8_t { SLOT_LAST = 1u, SLOT_LOWER = 2u };
 
@@ -67,6 +72,8 @@ struct __align__(16) InstDev {
     int64_t st_c, st_j, st_h;  // storage: first row, Jacobian value, Hessian value, inside the instance
     int32_t ns;         // storage units
     int32_t st0;        // first unit in the concatenated storage arrays
+    int32_t nlight, light0;  // split bus phase: buses one per thread (count, first list entry)
+    int32_t nheavy, heavy0;  // split bus phase: buses one per warp (more than kLightSlots slots)
 };
 static_assert(sizeof(InstDev) % 16 == 0, "InstDev is loaded as int4 words");
 
@@ -103,6 +110,10 @@ struct DevArrays {
     int32_t *st_list = nullptr;   // local unit ids, ascending per bus
     double4_16a *st_par = nullptr;    // per unit: (dt eta_c, dt / eta_d, r, e_init)
     int32_t *st_busid = nullptr;  // per unit: its local bus
+    // split bus phase: light buses (one thread each) and heavy buses (one
+    // warp each), local ids ascending per instance, and their item prefixes
+    int32_t *light_list = nullptr, *heavy_list = nullptr;
+    int64_t *light_items = nullptr, *heavy_items = nullptr;
     int64_t *st_items = nullptr;  // prefix of storage items (ns T) over instances, ninst + 1
     // instances and work lists
     InstDev *inst = nullptr;
@@ -152,6 +163,8 @@ struct Model {
     int64_t res_c0 = 0, res_j0 = 0;    // first reserve row / its first Jacobian value
     int64_t nbr_items = 0, nbus_items = 0, ngen_items = 0, narc_slots = 0;
     int64_t nst_items = 0;        // storage items (units x periods, all instances)
+    int64_t nlight_items = 0, nheavy_items = 0;  // split bus phase items
+    bool split_ok = false;        // the split bus phase applies (polar, no storage)
     int64_t nload_total = 0;      // sum over instances of nload * nperiod
     int32_t max_part = 0;         // capacity of obj_part
     int device = 0, num_sms = 148;

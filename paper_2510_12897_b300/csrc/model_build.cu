@@ -278,7 +278,8 @@ int build_model(const opf_network *nets, int32_t ninst, const opf_batch_opts *op
     // concatenated host arrays
     std::vector<int4> br, bus_a, bus_b;
     std::vector<int2> bus_c, br_jb;
-    std::vector<int32_t> bus_order;
+    std::vector<int32_t> bus_order, light_list, heavy_list;
+    std::vector<int64_t> light_items(1, 0), heavy_items(1, 0);
     std::vector<double2> y_ff, y_ft, y_tf, y_tt, gsbs, pbnd, qbnd, vbnd;
     std::vector<double> rate2, Pd, Qd, c2, c1, c0;
     std::vector<double2> tanb;
@@ -469,6 +470,20 @@ int build_model(const opf_network *nets, int32_t ninst, const opf_batch_opts *op
             bus_st.push_back(make_int2((int32_t)st_list.size() + H.st_ptr[i], (int32_t)st_list.size() + H.st_ptr[i + 1]));
         }
 
+        // ---- split bus phase lists: heavy buses (kLightSlots < slots <= 32)
+        // get a warp each, the others a thread each; both in id order
+        I.light0 = (int32_t)light_list.size();
+        I.heavy0 = (int32_t)heavy_list.size();
+        for (int i = 0; i < nb; i++) {
+            const int ns_i = H.arc_ptr[i + 1] - H.arc_ptr[i];
+            if (ns_i > kLightSlots && ns_i <= 32)
+                heavy_list.push_back(i);
+            else
+                light_list.push_back(i);
+        }
+        I.nlight = (int32_t)light_list.size() - I.light0;
+        I.nheavy = (int32_t)heavy_list.size() - I.heavy0;
+
         // ---- each arc's +1 entry in its bus's balance row: after the voltage
         // entries and the bus's generators, arcs in ascending id
         {
@@ -572,6 +587,8 @@ int build_model(const opf_network *nets, int32_t ninst, const opf_batch_opts *op
         bus_items.push_back(bus_items.back() + (int64_t)nb * T);
         gen_items.push_back(gen_items.back() + (int64_t)ng * T);
         st_items.push_back(st_items.back() + (int64_t)ns * T);
+        light_items.push_back(light_items.back() + (int64_t)I.nlight * T);
+        heavy_items.push_back(heavy_items.back() + (int64_t)I.nheavy * T);
         for (int k = 0; k < ns; k++)
             st_busid.push_back(stor[s].bus[k]);
     }
@@ -619,6 +636,9 @@ int build_model(const opf_network *nets, int32_t ninst, const opf_batch_opts *op
     M->nbus_items = bus_items.back();
     M->ngen_items = gen_items.back();
     M->nst_items = st_items.back();
+    M->nlight_items = light_items.back();
+    M->nheavy_items = heavy_items.back();
+    M->split_ok = !rect && !stor;
     M->narc_slots = so;
     M->max_part = 16 * M->num_sms;
     M->launch = opf_launch{128, 128, 0, 0, 0, 0};
@@ -641,6 +661,10 @@ int build_model(const opf_network *nets, int32_t ninst, const opf_batch_opts *op
     UP(gen_busid, gen_busid)
     UP(bus_a, bus_a) UP(bus_b, bus_b) UP(bus_c, bus_c) UP(gsbs, gsbs) UP(slot_code, slot_code) UP(gen_list, gen_list)
     UP(Pd, Pd) UP(Qd, Qd) UP(c2, c2) UP(c1, c1) UP(c0, c0) UP(pbnd, pbnd) UP(qbnd, qbnd)
+    if (M->split_ok) {
+        UP(light_list, light_list) UP(heavy_list, heavy_list) UP(light_items, light_items)
+        UP(heavy_items, heavy_items)
+    }
     if (M->storage) {
         UP(bus_st, bus_st) UP(st_list, st_list) UP(st_par, st_par) UP(st_busid, st_busid) UP(st_items, st_items)
     }

@@ -188,6 +188,9 @@ def test_host_buffers_variant(torch, oracle_mod):
          branch_occupancy=0),
     dict(branch_block=128, bus_block=64, branch_ctas_per_sm=2, bus_ctas_per_sm=0, bus_order=0,
          branch_occupancy=1),
+    dict(branch_block=32, bus_block=32, branch_ctas_per_sm=4, bus_ctas_per_sm=4, bus_order=2),
+    dict(branch_block=128, bus_block=256, branch_ctas_per_sm=0, bus_ctas_per_sm=0, bus_order=2,
+         branch_occupancy=1),
 ])
 def test_launch_shapes(torch, oracle_mod, launch):
     """Every launch shape the autotuner may pick gives parity (grid-stride
@@ -449,3 +452,24 @@ def test_pipelined_host_calls(torch, oracle_mod):
         ref = run_all(torch, M, x, lam, 1.0)
         for k, v in o.items():
             np.testing.assert_array_equal(v, ref[k])
+
+
+
+@pytest.mark.parametrize("which", ["case30g", "batch_links", "case10k", "hub"])
+def test_split_bus_phase(torch, oracle_mod, which):
+    """The split bus phase (bus_order 2: buses with more than eight arc slots
+    a warp each, one lane per slot, the others a thread each) against the
+    oracle: single instance, an N-1 batch with linking rows, the 10k grid
+    (buses up to 16 slots), and a hub bus beyond 32 slots (kept per thread)."""
+    from tests.test_hub_gpu import hub_grid
+    g = {"case30g": lambda: synth.case30(general=True),
+         "batch_links": lambda: synth.contingencies(synth.case30(general=True), 6, seed=3),
+         "case10k": lambda: synth.case10k(),
+         "hub": hub_grid}[which]()
+    link = 0.2 if which == "batch_links" else 0.0
+    M, O = both(torch, oracle_mod, g, link=link)
+    for k, (x, lam) in enumerate(points(g, M.m, 2, seed=34)):
+        for bu, cu in ((32, 0), (128, 2)):
+            launch = dict(branch_block=64, bus_block=bu, branch_ctas_per_sm=0, bus_ctas_per_sm=cu, bus_order=2)
+            sigma = 0.0 if k else 1.0
+            check_against_oracle(O, run_all(torch, M, x, lam, sigma, launch), x, lam, sigma, f"pt{k} bu{bu} ")
