@@ -768,10 +768,15 @@ __global__ void __launch_bounds__(kBusBlockMax) bus_kernel(const KParams P)
     }
     const DevArrays &d = P.d;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t nbg = (SPLIT ? P.nlight_items : P.nbus_items) + P.ngen_items;
-    const int64_t total = nbg + (STOR ? P.nst_items : 0);
     const unsigned tblocks = SPLIT ? (unsigned)P.split_tblocks : gridDim.x;
     const int64_t stride = (int64_t)tblocks * blockDim.x;
+    // generator items fill whole blocks when they fit in one pass, so that
+    // the blocks holding them (which reduce the objective) hold no bus and
+    // finish early: padding items after them do nothing
+    const int64_t gpad = P.ngen_items < stride ? (P.ngen_items + blockDim.x - 1) / blockDim.x * blockDim.x
+                                               : P.ngen_items;
+    const int64_t nbg = (SPLIT ? P.nlight_items : P.nbus_items) + gpad;
+    const int64_t total = nbg + (STOR ? P.nst_items : 0);
     int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
 
     struct Item {
@@ -794,8 +799,8 @@ __global__ void __launch_bounds__(kBusBlockMax) bus_kernel(const KParams P)
             const InstDev *I = d.inst + q.s;
             split((int)(item - (ONE ? 0 : __ldg(d.st_items + q.s))), __ldg(&I->ns), __ldg(&I->T), q.t, q.e);
             q.a.x = __ldg(d.st_busid + __ldg(&I->st0) + q.e);
-        } else if (item >= P.ngen_items && item < nbg) {
-            item -= P.ngen_items;
+        } else if (item >= gpad && item < nbg) {
+            item -= gpad;
             int r, bus0;
             if (SPLIT) {  // the light buses, in id order
                 q.s = ONE ? 0 : find_inst(d.light_items, P.ninst, item);
@@ -919,7 +924,7 @@ __global__ void __launch_bounds__(kBusBlockMax) bus_kernel(const KParams P)
                 for (int w = 0; w < 5; w++)
                     g[w * nsT] = 0.0;
             }
-        } else if (it >= P.ngen_items) {
+        } else if (it >= gpad) {
             const int i = q.e;
             const int iva = nb * q.t, ivm = nbT + nb * q.t;
             // every dynamic scalar of the bus, issued together (rectangular:
@@ -1133,7 +1138,7 @@ __global__ void __launch_bounds__(kBusBlockMax) bus_kernel(const KParams P)
                     }
                 }
             }
-        } else {
+        } else if (it < P.ngen_items) {  // (padding items after the generators do nothing)
             const int g = q.e;
             const int ipg = 2 * nbT + ng * q.t + g;
             const int gg = I.gen0 + g;
@@ -1741,7 +1746,10 @@ int launch_all(Model &M, const EvalArgs &a, unsigned what, cudaStream_t s, int p
     const int bu = L.bus_block > kBusBlockMax ? kBusBlockMax : L.bus_block;
     const int gb = grid_for(M.nbr_items, L.branch_block, L.branch_ctas_per_sm, M.num_sms, 0);
     const int cap = max_part < M.max_part ? max_part : M.max_part;
-    const int gu = grid_for(M.nbus_items + M.ngen_items + M.nst_items, bu, L.bus_ctas_per_sm, M.num_sms, cap);
+    // the bus kernel pads the generator items to whole blocks (when they fit
+    // in one pass of the grid): size the grid for the padded count
+    const int64_t gpad = (M.ngen_items + bu - 1) / bu * bu;
+    const int gu = grid_for(M.nbus_items + gpad + M.nst_items, bu, L.bus_ctas_per_sm, M.num_sms, cap);
     // the branch phase is needed for its rows and for the scratch the bus
     // phase reads (balance sums, Hessian), and to zero the p, q gradient
     const bool run_branch = (phases & 1) && (C || J || H || P.want_grad) && M.nbr_items > 0;
@@ -1756,7 +1764,7 @@ int launch_all(Model &M, const EvalArgs &a, unsigned what, cudaStream_t s, int p
     const bool splitb = L.bus_order == 2 && M.split_ok && (phases & 2);
     int gu_all = gu;
     if (splitb) {
-        const int tb = grid_for(M.nlight_items + M.ngen_items, bu, L.bus_ctas_per_sm, M.num_sms, cap);
+        const int tb = grid_for(M.nlight_items + gpad, bu, L.bus_ctas_per_sm, M.num_sms, cap);
         P.split_tblocks = tb;
         gu_all = tb + (int)((M.nheavy_items + bu / 32 - 1) / (bu / 32));
     }
@@ -1928,7 +1936,8 @@ int launch_cons_setflows(Model &M, double *x, double *obj, double *grad, double 
                        grid_for(M.nbr_items, 128, 0, M.num_sms, 0), 128, s, P);
     if (e == cudaSuccess)
         e = launch_pdl(bus_kernel<true, false, false, true>,
-                       grid_for(M.nbus_items + M.ngen_items, 128, 0, M.num_sms, M.max_part), 128, s, P);
+                       grid_for(M.nbus_items + (M.ngen_items + 127) / 128 * 128, 128, 0, M.num_sms, M.max_part), 128,
+                       s, P);
     if (e != cudaSuccess) {
         set_error("kernel launch failed: %s", cudaGetErrorString(e));
         return OPF_ECUDA;
