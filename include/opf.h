@@ -157,7 +157,10 @@ typedef struct {
                              rectangular form and storage models run 2 as 0) */
     int32_t branch_occupancy; /* 0: branch kernel compiled for up to 128 registers per
                                  thread (shortest chains); 1: for 80 (three blocks of 256
-                                 per SM: more warps to hide latency in large batches) */
+                                 per SM: more warps to hide latency in large batches);
+                                 2: two threads per branch, one per end (shorter chains:
+                                 better for single instances; polar form, the rectangular
+                                 form runs 2 as 0) */
 } opf_launch;
 
 /* Create a model for one network (Listing 3; multi-period if nperiod > 1).

@@ -513,13 +513,13 @@ int opf_set_launch(opf_model *m, const opf_launch *cfg)
             set_error("block size %d not a multiple of 32 in [32, 1024]", b);
             return OPF_EINVAL;
         }
-    if (cfg->bus_order < 0 || cfg->bus_order > 2 || cfg->branch_occupancy < 0 || cfg->branch_occupancy > 1) {
-        set_error("bus_order must be 0, 1 or 2 and branch_occupancy 0 or 1");
+    if (cfg->bus_order < 0 || cfg->bus_order > 2 || cfg->branch_occupancy < 0 || cfg->branch_occupancy > 2) {
+        set_error("bus_order and branch_occupancy must be 0, 1 or 2");
         return OPF_EINVAL;
     }
-    if (cfg->branch_block > (cfg->branch_occupancy ? 256 : 512)) {
+    if (cfg->branch_block > (cfg->branch_occupancy == 1 ? 256 : 512)) {
         set_error("branch_block %d above the branch kernel's limit (%d)", cfg->branch_block,
-                  cfg->branch_occupancy ? 256 : 512);
+                  cfg->branch_occupancy == 1 ? 256 : 512);
         return OPF_EINVAL;
     }
     if (cfg->branch_ctas_per_sm < 0 || cfg->bus_ctas_per_sm < 0 || cfg->branch_ctas_per_sm > 64 ||
@@ -607,7 +607,7 @@ int opf_autotune(opf_model *m, const double *d_x, const double *d_lambda, int32_
     const int bblocks[] = {32, 64, 128, 256, 512};
     const int ublocks[] = {32, 64, 128, 256};  // the bus kernel stages at most 8 warps
     const int ctas[] = {0, 2, 4, 8, 16};
-    for (int occ = 0; occ < 2 && !rc; occ++)
+    for (int occ = 0; occ < 3 && !rc; occ++)
     for (int order = 0; order < 3 && !rc; order++)
     for (int bb : bblocks)
         for (int bu : ublocks)
@@ -615,7 +615,7 @@ int opf_autotune(opf_model *m, const double *d_x, const double *d_lambda, int32_
                 for (int cu : ctas) {
                     if (rc || (cu != 0 && cu != cb))  // keep the search small: equal persistence
                         continue;
-                    if (occ && bb > 256)
+                    if (occ == 1 && bb > 256)
                         continue;
                     M.launch = opf_launch{bb, bu, cb, cu, order, occ};
                     const float ms = time_graph(M, a, reps, 2, cs, e0, e1);

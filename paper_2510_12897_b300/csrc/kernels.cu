@@ -409,6 +409,155 @@ __global__ void __launch_bounds__(OCC ? 256 : 512, OCC ? 3 : 1) branch_kernel(co
     }
 }
 
+// Branch phase with two threads per branch item (branch_occupancy 2, polar
+// form): the lanes 2q and 2q + 1 of a warp take the from-end and the to-end
+// of item q. Each computes the shared trigonometry and, for its own end,
+// the two flow rows with their Jacobian rows, the thermal row and its
+// Jacobian and Hessian entries, the balance +1 entries, the arc's scratch
+// record and its gradient zeros; the from-end lane also writes the angle
+// row. The Hessian's U and V (section above) are sums of one part per end,
+// exchanged between the two lanes with one shuffle each and added in the
+// same order in both. Every per-end formula is the from-end one with the
+// ends swapped: at the to-end the angle is va_t - va_f.
+template <bool CONS, bool JAC, bool HESS, bool ONE>
+__global__ void __launch_bounds__(512, 1) branch2_kernel(const KParams P)
+{
+    const DevArrays &d = P.d;
+    const int lane = threadIdx.x & 31;
+    const int e = lane & 1;                                      // 0: from-end, 1: to-end
+    const unsigned pair = 3u << (lane & ~1);                     // this pair's lanes
+    const int64_t stride = ((int64_t)gridDim.x * blockDim.x) >> 1;
+    int64_t it = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 1;
+
+    auto locate = [&](int64_t item, int &s, int &t, int &k, int &kb) {
+        if (ONE) {
+            s = 0;
+            split((int)item, P.inst0.nl, P.inst0.T, t, k);
+            kb = k;
+        } else {
+            s = find_inst(d.br_items, P.ninst, item);
+            const InstDev *I = d.inst + s;
+            split((int)(item - __ldg(d.br_items + s)), __ldg(&I->nl), __ldg(&I->T), t, k);
+            kb = __ldg(&I->br0) + k;
+        }
+    };
+    int s = 0, t = 0, k = 0, kb = 0;
+    int4 br = make_int4(0, 0, 0, 0);
+    int jb = 0;
+    double2 Yo = make_double2(0.0, 0.0), Yx = make_double2(0.0, 0.0);
+    double r2 = 0.0;
+    auto load = [&]() {  // this end's static data
+        br = __ldg(d.br + kb);
+        if (JAC) {
+            const int2 j2 = __ldg(d.br_jb + kb);
+            jb = e ? j2.y : j2.x;
+        }
+        Yo = __ldg((e ? d.y_tt : d.y_ff) + kb);
+        Yx = __ldg((e ? d.y_tf : d.y_ft) + kb);
+        if (CONS)
+            r2 = __ldg(d.rate2 + kb);
+    };
+    if (it < P.nbr_items) {  // static prologue, overlaps the previous kernel
+        locate(it, s, t, k, kb);
+        load();
+    }
+    cudaGridDependencySynchronize();
+    cudaTriggerProgrammaticLaunchCompletion();  // the next kernel may launch now
+
+    const int64_t first = it;
+    for (; it < P.nbr_items; it += stride) {
+        if (it != first) {
+            locate(it, s, t, k, kb);
+            load();
+        }
+        const InstDev I = inst_of<ONE>(P, s);
+        const int nl = I.nl, nb = I.nb, ng = I.ng, T = I.T;
+        const int nbT = nb * T, ngT = ng * T, nlT = nl * T, na = 2 * nl;
+        const int rk = k + nl * t;
+        const int f = br.x, b = br.y;
+        const int own = e ? b : f, far = e ? f : b;
+        const double *__restrict__ xs = P.x + I.x0;
+        const int iva = nb * t, ivm = nbT + nb * t;
+        const int ip = 2 * nbT + 2 * ngT + na * t, iq = ip + na * T;
+        const int arc = e ? nl + k : k;  // this end's arc
+        const double vao = __ldg(xs + iva + own), vax = __ldg(xs + iva + far);
+        const double vo = __ldg(xs + ivm + own), vx = __ldg(xs + ivm + far);
+        double po = 0, qo = 0;
+        if (CONS || JAC || HESS) {
+            po = __ldg(xs + ip + arc);
+            qo = __ldg(xs + iq + arc);
+        }
+        double mP = 0, mQ = 0, lth = 0;
+        if (HESS) {
+            const double *L = P.lam + I.c0 + (T + rk);
+            mP = __ldg(L + (e ? 2 * nlT : 0));
+            mQ = __ldg(L + (e ? 3 * nlT : nlT));
+            lth = __ldg(L + ((e ? 6 : 5) * nlT + 2 * nbT));
+        }
+        const double dlt = vao - vax;  // this end's angle
+        double sn, cs_;
+        sincos_tab(dlt, d.trig, &sn, &cs_);
+        const double vft = vo * vx;
+        const double A = fma(Yx.x, cs_, Yx.y * sn);
+        const double B = fma(Yx.x, sn, neg(Yx.y * cs_));
+        if (CONS) {
+            const double vo2 = vo * vo;
+            double *c = P.c + I.c0 + (T + rk);
+            c[e ? 2 * nlT : 0] = po - fma(Yo.x, vo2, vft * A);
+            c[e ? 3 * nlT : nlT] = qo - fma(neg(Yo.y), vo2, vft * B);
+            if (!e)
+                c[4 * nlT] = dlt;
+            c[(e ? 6 : 5) * nlT + 2 * nbT] = fma(po, po, qo * qo) - r2;
+        }
+        if (JAC) {
+            const int jP = (int)I.jP;
+            const bool o_lo = own < far;
+            const double v2o = twice(vo);
+            const double uB = vft * B, uA = vft * A;
+            double *J = P.jac + I.j0;
+            double *Jf = J + (T + 5 * rk + (e ? 10 * nlT : 0));
+            // (va_own, va_far, vm_own, vm_far) of p - P and q - Q at this end
+            put5(Jf, o_lo, uB, neg(uB), neg(fma(Yo.x, v2o, vx * A)), neg(vo * A));
+            put5(Jf + 5 * nlT, o_lo, neg(uA), uA, fma(Yo.y, v2o, neg(vx * B)), neg(vo * B));
+            if (!e) {  // angle row va_f - va_t
+                double *Ja = J + (T + 20 * nlT + 2 * rk);
+                Ja[0] = flip(1.0, !o_lo);
+                Ja[1] = flip(1.0, o_lo);
+            }
+            double *Jb = J + (T + 22 * nlT + jP * t);  // +1 of the arc in its bus's P and Q rows
+            Jb[jb] = 1.0;
+            Jb[jP * T + jb] = 1.0;
+            double *Jt = J + (T + 22 * nlT + 2 * jP * T + 2 * rk + (e ? 2 * nlT : 0));  // thermal row
+            Jt[0] = twice(po);
+            Jt[1] = twice(qo);
+        }
+        if (HESS || CONS) {
+            ArcScratch *S = d.arcs + I.scr0 + na * t;
+            double2 *so = reinterpret_cast<double2 *>(S + (e ? br.w : br.z));
+            so[0] = make_double2(po, qo);
+            if (HESS) {
+                // U = (m1 Aft + m2 Bft) + (m3 Atf + m4 Btf), V = (m2 Aft - m1 Bft) + (m3 Btf - m4 Atf)
+                const double Ue = fma(mP, A, mQ * B);
+                const double Ve = flip(fma(mQ, A, neg(mP * B)), e);
+                const double Uo = __shfl_xor_sync(pair, Ue, 1), Vo = __shfl_xor_sync(pair, Ve, 1);
+                const double U = e ? Uo + Ue : Ue + Uo;  // from-end part first in both lanes
+                const double V = e ? Vo + Ve : Ve + Vo;
+                const double We = fma(mP, Yo.x, neg(mQ * Yo.y));
+                so[1] = make_double2(vft * U, flip(vx * V, !e));
+                so[2] = make_double2(neg(twice(We)), neg(U));
+                double *Hp = P.hess + I.h0 + ((int)(I.hva + I.hvm) * T + ngT + arc + na * t);
+                const double l2 = twice(lth);
+                Hp[0] = l2;       // (p_arc, p_arc)
+                Hp[na * T] = l2;  // (q_arc, q_arc)
+            }
+        }
+        if (P.want_grad) {
+            P.grad[I.x0 + ip + arc] = 0.0;
+            P.grad[I.x0 + iq + arc] = 0.0;
+        }
+    }
+}
+
 // gradient of a rectangular row in the order (vr_f, vr_t, vi_f, vi_t)
 struct Grad4 {
     double rf, rt, jf, jt;
@@ -1676,8 +1825,8 @@ cudaError_t launch_pdl(K kernel, int grid, int block, cudaStream_t s, const KPar
 }
 
 template <bool C, bool J, bool H>
-cudaError_t dispatch(const KParams &P, bool one, bool occ, bool rect, bool stor, bool run_branch, bool run_bus,
-                     int gb, int bb, int gu, int bu, cudaStream_t s, bool splitb)
+cudaError_t dispatch(const KParams &P, bool one, bool occ, bool occ2, bool rect, bool stor, bool run_branch,
+                     bool run_bus, int gb, int bb, int gu, int bu, cudaStream_t s, bool splitb)
 {
     cudaError_t e = cudaSuccess;
     if (rect) {  // the rectangular branch kernel (two register budgets) and bus variant
@@ -1692,7 +1841,10 @@ cudaError_t dispatch(const KParams &P, bool one, bool occ, bool rect, bool stor,
         return one ? launch_pdl(bus_kernel<C, J, H, true, true>, gu, bu, s, P)
                    : launch_pdl(bus_kernel<C, J, H, false, true>, gu, bu, s, P);
     }
-    if (run_branch) {
+    if (run_branch && occ2) {  // two threads per branch item (gb counts both)
+        e = one ? launch_pdl(branch2_kernel<C, J, H, true>, gb, bb, s, P)
+                : launch_pdl(branch2_kernel<C, J, H, false>, gb, bb, s, P);
+    } else if (run_branch) {
         if (occ)
             e = one ? launch_pdl(branch_kernel<C, J, H, true, true>, gb, bb, s, P)
                     : launch_pdl(branch_kernel<C, J, H, false, true>, gb, bb, s, P);
@@ -1755,7 +1907,10 @@ int launch_all(Model &M, const EvalArgs &a, unsigned what, cudaStream_t s, int p
     const bool run_branch = (phases & 1) && (C || J || H || P.want_grad) && M.nbr_items > 0;
     const bool run_bus = phases & 2;
     const bool one = M.ninst == 1;
-    const bool occ = L.branch_occupancy != 0;
+    const bool occ = L.branch_occupancy == 1;
+    // branch_occupancy 2: two threads per branch item (polar form)
+    const bool occ2 = L.branch_occupancy == 2 && !M.rect;
+    const int gb2 = occ2 ? grid_for(2 * M.nbr_items, L.branch_block, L.branch_ctas_per_sm, M.num_sms, 0) : gb;
     const int bb = L.branch_block;
     P.order = L.bus_order == 1 ? M.d.bus_order : nullptr;
     // bus_order 2: the split bus phase where it applies (polar, no storage):
@@ -1770,14 +1925,14 @@ int launch_all(Model &M, const EvalArgs &a, unsigned what, cudaStream_t s, int p
     }
     cudaError_t e;
     switch ((C ? 1 : 0) | (J ? 2 : 0) | (H ? 4 : 0)) {
-    case 0: e = dispatch<false, false, false>(P, one, occ, M.rect, M.storage, run_branch, run_bus, gb, bb, gu_all, bu, s, splitb); break;
-    case 1: e = dispatch<true, false, false>(P, one, occ, M.rect, M.storage, run_branch, run_bus, gb, bb, gu_all, bu, s, splitb); break;
-    case 2: e = dispatch<false, true, false>(P, one, occ, M.rect, M.storage, run_branch, run_bus, gb, bb, gu_all, bu, s, splitb); break;
-    case 3: e = dispatch<true, true, false>(P, one, occ, M.rect, M.storage, run_branch, run_bus, gb, bb, gu_all, bu, s, splitb); break;
-    case 4: e = dispatch<false, false, true>(P, one, occ, M.rect, M.storage, run_branch, run_bus, gb, bb, gu_all, bu, s, splitb); break;
-    case 5: e = dispatch<true, false, true>(P, one, occ, M.rect, M.storage, run_branch, run_bus, gb, bb, gu_all, bu, s, splitb); break;
-    case 6: e = dispatch<false, true, true>(P, one, occ, M.rect, M.storage, run_branch, run_bus, gb, bb, gu_all, bu, s, splitb); break;
-    default: e = dispatch<true, true, true>(P, one, occ, M.rect, M.storage, run_branch, run_bus, gb, bb, gu_all, bu, s, splitb); break;
+    case 0: e = dispatch<false, false, false>(P, one, occ, occ2, M.rect, M.storage, run_branch, run_bus, gb2, bb, gu_all, bu, s, splitb); break;
+    case 1: e = dispatch<true, false, false>(P, one, occ, occ2, M.rect, M.storage, run_branch, run_bus, gb2, bb, gu_all, bu, s, splitb); break;
+    case 2: e = dispatch<false, true, false>(P, one, occ, occ2, M.rect, M.storage, run_branch, run_bus, gb2, bb, gu_all, bu, s, splitb); break;
+    case 3: e = dispatch<true, true, false>(P, one, occ, occ2, M.rect, M.storage, run_branch, run_bus, gb2, bb, gu_all, bu, s, splitb); break;
+    case 4: e = dispatch<false, false, true>(P, one, occ, occ2, M.rect, M.storage, run_branch, run_bus, gb2, bb, gu_all, bu, s, splitb); break;
+    case 5: e = dispatch<true, false, true>(P, one, occ, occ2, M.rect, M.storage, run_branch, run_bus, gb2, bb, gu_all, bu, s, splitb); break;
+    case 6: e = dispatch<false, true, true>(P, one, occ, occ2, M.rect, M.storage, run_branch, run_bus, gb2, bb, gu_all, bu, s, splitb); break;
+    default: e = dispatch<true, true, true>(P, one, occ, occ2, M.rect, M.storage, run_branch, run_bus, gb2, bb, gu_all, bu, s, splitb); break;
     }
     if (e == cudaSuccess && M.reserve && (C || J) && (phases & 2)) {
         const int64_t threads = 32 * M.nres;

@@ -189,6 +189,10 @@ def test_host_buffers_variant(torch, oracle_mod):
     dict(branch_block=128, bus_block=64, branch_ctas_per_sm=2, bus_ctas_per_sm=0, bus_order=0,
          branch_occupancy=1),
     dict(branch_block=32, bus_block=32, branch_ctas_per_sm=4, bus_ctas_per_sm=4, bus_order=2),
+    dict(branch_block=64, bus_block=64, branch_ctas_per_sm=0, bus_ctas_per_sm=0, bus_order=2,
+         branch_occupancy=2),
+    dict(branch_block=512, bus_block=128, branch_ctas_per_sm=1, bus_ctas_per_sm=0, bus_order=1,
+         branch_occupancy=2),
     dict(branch_block=128, bus_block=256, branch_ctas_per_sm=0, bus_ctas_per_sm=0, bus_order=2,
          branch_occupancy=1),
 ])
@@ -473,3 +477,29 @@ def test_split_bus_phase(torch, oracle_mod, which):
             launch = dict(branch_block=64, bus_block=bu, branch_ctas_per_sm=0, bus_ctas_per_sm=cu, bus_order=2)
             sigma = 0.0 if k else 1.0
             check_against_oracle(O, run_all(torch, M, x, lam, sigma, launch), x, lam, sigma, f"pt{k} bu{bu} ")
+
+
+
+@pytest.mark.parametrize("which", ["case30g", "batch_links", "case10k", "mp30"])
+def test_two_threads_per_branch(torch, oracle_mod, which):
+    """branch_occupancy 2: each branch item by two lanes (from-end, to-end)
+    exchanging the Hessian's U and V by shuffles; every output against the
+    oracle, in one-thread-per-item and persistent grids; and the rectangular
+    form, which runs it as its own branch kernel."""
+    g = {"case30g": lambda: synth.case30(general=True),
+         "batch_links": lambda: synth.contingencies(synth.case30(general=True), 6, seed=3),
+         "case10k": lambda: synth.case10k(),
+         "mp30": lambda: synth.multi_period(synth.case30(general=True), 4, seed=8, ramp_ratio=0.2)}[which]()
+    link = 0.2 if which == "batch_links" else 0.0
+    M, O = both(torch, oracle_mod, g, link=link)
+    for k, (x, lam) in enumerate(points(g, M.m, 2, seed=35)):
+        for bb, cb in ((32, 0), (256, 1)):
+            launch = dict(branch_block=bb, bus_block=64, branch_ctas_per_sm=cb, bus_ctas_per_sm=0, bus_order=0,
+                          branch_occupancy=2)
+            sigma = 0.0 if k else 1.0
+            check_against_oracle(O, run_all(torch, M, x, lam, sigma, launch), x, lam, sigma, f"pt{k} bb{bb} ")
+    if which == "case30g":
+        Mr, Or = both(torch, oracle_mod, g, form="rect")
+        x, lam = next(points(g, Mr.m, 1, seed=36))
+        check_against_oracle(Or, run_all(torch, Mr, x, lam, 1.0, dict(branch_block=64, bus_block=64,
+                             branch_ctas_per_sm=0, bus_ctas_per_sm=0, bus_order=0, branch_occupancy=2)), x, lam, 1.0)
