@@ -153,14 +153,13 @@ typedef struct {
                              idle lanes in the slot loops: better for large batches);
                              2: buses with more than 6 arc slots (and at most 32) a warp
                              each, one lane per slot, the others a thread each in id order
-                             (shorter longest thread: better for single instances; the
-                             rectangular form and storage models run 2 as 0) */
+                             (shorter longest thread: better for single instances;
+                             storage models run 2 as 0) */
     int32_t branch_occupancy; /* 0: branch kernel compiled for up to 128 registers per
                                  thread (shortest chains); 1: for 80 (three blocks of 256
                                  per SM: more warps to hide latency in large batches);
                                  2: two threads per branch, one per end (shorter chains:
-                                 better for single instances; polar form, the rectangular
-                                 form runs 2 as 0) */
+                                 better for single instances; both forms) */
 } opf_launch;
 
 /* Create a model for one network (Listing 3; multi-period if nperiod > 1).

@@ -17,8 +17,10 @@
  * Inner iteration (Adam, Kingma and Ba; beta1 0.9, beta2 0.999, eps 1e-8,
  * step count kept across calls until opf_al_reset):
  *   G = grad f(x) + J(x)^T mu(x);  m = b1 m + (1 - b1) G;
- *   v = b2 v + (1 - b2) G^2;  x = clip(x - lr (m / (1 - b1^k)) /
- *   (sqrt(v / (1 - b2^k)) + eps), xl, xu).
+ *   v = b2 v + (1 - b2) G^2;  x = clip(x - lr (m / (1 - b1^k)) r, xl, xu),
+ *   r = 1 / (sqrt(v / (1 - b2^k)) + eps), where r, a step-size scale, is
+ *   formed in FP32 with correctly rounded operations (v / (1 - b2^k)
+ *   rounded to FP32, square root, + eps, reciprocal) and the rest in FP64.
  * Outer update: lambda = mu(x).
  *
  * Ownership and errors as in include/opf.h: device buffers are caller-owned,

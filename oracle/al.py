@@ -11,6 +11,10 @@ a scipy sparse matvec):
     Adam (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) on x, then
     x = clip(x, xl, xu);  outer update lambda = mu(x).
 
+Adam's scale 1 / (sqrt(v_hat) + eps) is formed in FP32 (v_hat rounded to
+FP32, then the correctly rounded square root, sum and reciprocal of IEEE
+single precision), as the library defines it; the rest is FP64.
+
 Pinned by tests/test_al_oracle.py: G against Richardson central differences
 of L; L = f and mu = 0 at a point strictly inside every row's bounds with
 lambda = 0; the update's fixed point (lambda = mu) at such a point.
@@ -58,7 +62,9 @@ class AugLagOracle:
             self.k += 1
             self.m1 = 0.9 * self.m1 + 0.1 * G
             self.m2 = 0.999 * self.m2 + 0.001 * G * G
-            step = self.lr * (self.m1 / (1 - 0.9 ** self.k)) / (np.sqrt(self.m2 / (1 - 0.999 ** self.k)) + 1e-8)
+            v32 = (self.m2 / (1 - 0.999 ** self.k)).astype(np.float32)
+            r = (np.float32(1.0) / (np.sqrt(v32) + np.float32(1e-8))).astype(np.float64)
+            step = self.lr * (self.m1 / (1 - 0.9 ** self.k)) * r
             x = np.clip(x - step, self.xl, self.xu)
         return x, self.stats(x, lam)
 

@@ -166,7 +166,7 @@ __global__ void al_stats_kernel(const double *obj, const double *part, int npart
 __global__ void al_adam_kernel(double *x, const double *grad, const double *u, const double *xl, const double *xu,
                                double *m1, double *m2, int64_t n, double lr, const double *bp)
 {
-    const double b1 = 0.9, b2 = 0.999, eps = 1e-8;
+    const double b1 = 0.9, b2 = 0.999;
     const double k1 = lr / bp[2], k2 = 1.0 / bp[3];
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
          j += (int64_t)gridDim.x * blockDim.x) {
@@ -175,7 +175,11 @@ __global__ void al_adam_kernel(double *x, const double *grad, const double *u, c
         const double b = fma(b2, m2[j], (1.0 - b2) * G * G);
         m1[j] = a;
         m2[j] = b;
-        const double xn = x[j] - k1 * a / (sqrt(b * k2) + eps);
+        // the scale 1 / (sqrt(v_hat) + eps) in FP32, correctly rounded at
+        // every operation: FP64 square roots and divisions would cost about
+        // 30 FP64 pipe operations per entry
+        const float den = __fadd_rn(__fsqrt_rn(__double2float_rn(b * k2)), 1e-8f);
+        const double xn = x[j] - k1 * a * (double)__frcp_rn(den);
         x[j] = fmin(fmax(xn, xl[j]), xu[j]);
     }
 }

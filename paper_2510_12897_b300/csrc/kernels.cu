@@ -750,6 +750,163 @@ __global__ void __launch_bounds__(OCC ? 256 : 512, OCC ? 3 : 1) rect_branch_kern
     }
 }
 
+// Branch phase of the rectangular form with two threads per branch item
+// (branch_occupancy 2): lanes 2q and 2q + 1 take the from-end and the to-end
+// of item q, as in the polar two-lane kernel. With the ends swapped,
+// w' = V_t conj(V_f) = conj(w), and the to-end's flows P_to = Gtt |V_t|^2 +
+// Gtf wR' + Btf wI', Q_to = -Btt |V_t|^2 + Gtf wI' - Btf wR' take the
+// from-end's form with (Ytt, Ytf) for (Yff, Yft): each lane evaluates the
+// from-end formulas on (own, far) = (f, t) or (t, f). The from-end lane writes
+// the upper angle row, the to-end lane the lower one. The Hessian's aR and aI
+// are sums of one part per end (plus the angle rows' parts), exchanged with
+// one shuffle each and added from-end part first in both lanes.
+template <bool CONS, bool JAC, bool HESS, bool ONE>
+__global__ void __launch_bounds__(512, 1) rect_branch2_kernel(const KParams P)
+{
+    const DevArrays &d = P.d;
+    const int lane = threadIdx.x & 31;
+    const int e = lane & 1;                   // 0: from-end, 1: to-end
+    const unsigned pair = 3u << (lane & ~1);  // this pair's lanes
+    const int64_t stride = ((int64_t)gridDim.x * blockDim.x) >> 1;
+    int64_t it = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 1;
+
+    auto locate = [&](int64_t item, int &s, int &t, int &k, int &kb) {
+        if (ONE) {
+            s = 0;
+            split((int)item, P.inst0.nl, P.inst0.T, t, k);
+            kb = k;
+        } else {
+            s = find_inst(d.br_items, P.ninst, item);
+            const InstDev *I = d.inst + s;
+            split((int)(item - __ldg(d.br_items + s)), __ldg(&I->nl), __ldg(&I->T), t, k);
+            kb = __ldg(&I->br0) + k;
+        }
+    };
+    int s = 0, t = 0, k = 0, kb = 0;
+    int4 br = make_int4(0, 0, 0, 0);
+    int jb = 0;
+    double2 Yo = make_double2(0.0, 0.0), Yx = make_double2(0.0, 0.0);
+    double r2 = 0.0, tn = 0.0;
+    auto load = [&]() {  // this end's static data
+        br = __ldg(d.br + kb);
+        if (JAC) {
+            const int2 j2 = __ldg(d.br_jb + kb);
+            jb = e ? j2.y : j2.x;
+        }
+        Yo = __ldg((e ? d.y_tt : d.y_ff) + kb);
+        Yx = __ldg((e ? d.y_tf : d.y_ft) + kb);
+        if (CONS)
+            r2 = __ldg(d.rate2 + kb);
+        const double2 tb = __ldg(d.tanb + kb);  // tan(angmax), tan(angmin)
+        tn = e ? tb.y : tb.x;
+    };
+    if (it < P.nbr_items) {  // static prologue, overlaps the previous kernel
+        locate(it, s, t, k, kb);
+        load();
+    }
+    cudaGridDependencySynchronize();
+    cudaTriggerProgrammaticLaunchCompletion();  // the next kernel may launch now
+
+    const int64_t first = it;
+    for (; it < P.nbr_items; it += stride) {
+        if (it != first) {
+            locate(it, s, t, k, kb);
+            load();
+        }
+        const InstDev I = inst_of<ONE>(P, s);
+        const int nl = I.nl, nb = I.nb, ng = I.ng, T = I.T;
+        const int nbT = nb * T, ngT = ng * T, nlT = nl * T, na = 2 * nl;
+        const int rk = k + nl * t;
+        const int f = br.x, b = br.y;
+        const int own = e ? b : f, far = e ? f : b;
+        const double *__restrict__ xs = P.x + I.x0;
+        const int ivr = nb * t, ivi = nbT + nb * t;
+        const int ip = 2 * nbT + 2 * ngT + na * t, iq = ip + na * T;
+        const int arc = e ? nl + k : k;  // this end's arc
+        const double vro = __ldg(xs + ivr + own), vrx = __ldg(xs + ivr + far);
+        const double vio = __ldg(xs + ivi + own), vix = __ldg(xs + ivi + far);
+        double po = 0, qo = 0;
+        if (CONS || JAC || HESS) {
+            po = __ldg(xs + ip + arc);
+            qo = __ldg(xs + iq + arc);
+        }
+        double mP = 0, mQ = 0, ma = 0, lth = 0;
+        if (HESS) {
+            const double *L = P.lam + I.c0 + (T + rk);
+            mP = __ldg(L + (e ? 2 * nlT : 0));
+            mQ = __ldg(L + (e ? 3 * nlT : nlT));
+            ma = __ldg(L + (e ? 7 * nlT + 2 * nbT : 4 * nlT));  // this lane's angle row
+            lth = __ldg(L + ((e ? 6 : 5) * nlT + 2 * nbT));
+        }
+        // w_e = V_own conj(V_far): w at the from-end, conj(w) at the to-end
+        const double wR = fma(vro, vrx, vio * vix);
+        const double wI = fma(vio, vrx, neg(vro * vix));
+        if (CONS) {
+            const double vo2 = fma(vro, vro, vio * vio);
+            double *c = P.c + I.c0 + (T + rk);
+            c[e ? 2 * nlT : 0] = po - fma(Yo.x, vo2, fma(Yx.x, wR, Yx.y * wI));
+            c[e ? 3 * nlT : nlT] = qo - fma(neg(Yo.y), vo2, fma(Yx.x, wI, neg(Yx.y * wR)));
+            // angle rows on the from-end's w: wI - tan(limit) wR
+            c[e ? 7 * nlT + 2 * nbT : 4 * nlT] = fma(neg(tn), wR, flip(wI, e));
+            c[(e ? 6 : 5) * nlT + 2 * nbT] = fma(po, po, qo * qo) - r2;
+        }
+        if (JAC) {
+            const int jP = (int)I.jP;
+            const bool o_lo = own < far;
+            double *J = P.jac + I.j0;
+            double *Jf = J + (T + 5 * rk + (e ? 10 * nlT : 0));
+            // the from-end's products with (own, far) for (f, t):
+            // Yx V_far and Yx conj(V_own)
+            const double y1r = fma(Yx.x, vrx, neg(Yx.y * vix)), y1i = fma(Yx.x, vix, Yx.y * vrx);
+            const double y2r = fma(Yx.x, vro, Yx.y * vio), y2i = fma(Yx.y, vro, neg(Yx.x * vio));
+            const double pa = neg(twice(Yo.x)), qa = twice(Yo.y);
+            Grad4 g;  // (own, far) in the places of (f, t)
+            g.rf = fma(pa, vro, neg(y1r)); g.jf = fma(pa, vio, neg(y1i)); g.rt = neg(y2r); g.jt = y2i;
+            put_rect(Jf, o_lo, g, true);            // p - P at this end
+            g.rf = fma(qa, vro, y1i); g.jf = fma(qa, vio, neg(y1r)); g.rt = y2i; g.jt = y2r;
+            put_rect(Jf + 5 * nlT, o_lo, g, true);  // q - Q at this end
+            // this lane's angle row wI - tn wR, from-end w: its gradient in
+            // (vr_f, vr_t, vi_f, vi_t) is (tu vr_t - vi_t, tu vr_f + vi_f,
+            // tu vi_t + vr_t, tu vi_f - vr_f) with tu = -tn
+            const double tu = neg(tn);
+            const double vrf = e ? vrx : vro, vrt = e ? vro : vrx, vif = e ? vix : vio, vit = e ? vio : vix;
+            g.rf = fma(tu, vrt, neg(vit)); g.jf = fma(tu, vit, vrt); g.rt = fma(tu, vrf, vif); g.jt = fma(tu, vif, neg(vrf));
+            put_rect(J + (T + (e ? 28 * nlT + 2 * jP * T : 20 * nlT) + 4 * rk), f < b, g, false);
+            double *Jb = J + (T + 24 * nlT + jP * t);  // +1 of the arc in its bus's P and Q rows
+            Jb[jb] = 1.0;
+            Jb[jP * T + jb] = 1.0;
+            double *Jt = J + (T + 24 * nlT + 2 * jP * T + 2 * rk + (e ? 2 * nlT : 0));  // thermal row
+            Jt[0] = twice(po);
+            Jt[1] = twice(qo);
+        }
+        if (HESS || CONS) {
+            ArcScratch *S = d.arcs + I.scr0 + na * t;
+            double2 *so = reinterpret_cast<double2 *>(S + (e ? br.w : br.z));
+            so[0] = make_double2(po, qo);
+            if (HESS) {
+                // aR = -(m1 Gft - m2 Bft + a1 tan(angmax)) - (m3 Gtf - m4 Btf + a2 tan(angmin))
+                // aI = (-m1 Bft - m2 Gft + a1) + (m3 Btf + m4 Gtf + a2)
+                const double Re = neg(fma(mP, Yx.x, fma(neg(mQ), Yx.y, ma * tn)));
+                const double Ie = flip(fma(mP, Yx.y, mQ * Yx.x), !e) + ma;
+                const double Ro = __shfl_xor_sync(pair, Re, 1), Io = __shfl_xor_sync(pair, Ie, 1);
+                const double aR = e ? Ro + Re : Re + Ro;  // from-end part first in both lanes
+                const double aI = e ? Io + Ie : Ie + Io;
+                const double De = neg(twice(fma(mP, Yo.x, neg(mQ * Yo.y))));
+                so[1] = make_double2(De, aR);
+                reinterpret_cast<double *>(so + 2)[0] = flip(aI, e);
+                double *Hp = P.hess + I.h0 + ((int)(I.hva + I.hvm) * T + ngT + arc + na * t);
+                const double l2 = twice(lth);
+                Hp[0] = l2;       // (p_arc, p_arc)
+                Hp[na * T] = l2;  // (q_arc, q_arc)
+            }
+        }
+        if (P.want_grad) {
+            P.grad[I.x0 + ip + arc] = 0.0;
+            P.grad[I.x0 + iq + arc] = 0.0;
+        }
+    }
+}
+
 constexpr int kBusBlockMax = 256;
 
 // Split bus phase, heavy buses: one warp per (instance, period, bus) with
@@ -757,7 +914,7 @@ constexpr int kBusBlockMax = 256;
 // (shuffles, fixed order) sums each group of parallel arcs, whose last lane
 // writes the group's off-diagonal Hessian entries; butterfly sums (fixed
 // order) give the bus totals, and lane 0 finishes the bus exactly as a
-// light bus's thread does (polar form, no storage).
+// light bus's thread does (models without storage; both forms).
 __device__ __forceinline__ double seg_scan(double v, int lane, int head)
 {
 #pragma unroll
@@ -777,7 +934,7 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
-template <bool CONS, bool JAC, bool HESS, bool ONE>
+template <bool CONS, bool JAC, bool HESS, bool ONE, bool RECT>
 __device__ void heavy_bus_warp(const KParams &P)
 {
     const DevArrays &d = P.d;
@@ -825,6 +982,7 @@ __device__ void heavy_bus_warp(const KParams &P)
         }
     }
     const int iva = nb * t, ivm = nbT + nb * t;
+    // polar: vm; rectangular: vi (and vr below)
     const double vm = __ldg(xs + ivm + i);
     const int hva = (int)I.hva, hvm = (int)I.hvm;
     double *Hvm = P.hess + I.h0 + (hva * T + hvm * t + b.z);
@@ -836,20 +994,36 @@ __device__ void heavy_bus_warp(const KParams &P)
         const unsigned tails = __ballot_sync(0xffffffffu, has && (code & SLOT_LAST));
         const unsigned tb = tails & below;
         const int ghead = tb ? 32 - __clz(tb) : 0;
-        const double gaa = seg_scan(v1.x, lane, ghead);
-        const double gma = seg_scan(v1.y, lane, ghead);
-        const double gmm = seg_scan(v2.y, lane, ghead);
-        if (has && (code & SLOT_LAST)) {
-            const int grp = __popc(tb);
-            Hvm[grp < nlt ? grp : grp + 1] = neg(gma);  // (vm_i, va_j)
-            if (code & SLOT_LOWER) {
-                Hva[grp] = neg(gaa);         // (va_i, va_j), j < i
-                Hvm[nd + 1 + grp] = gmm;     // (vm_i, vm_j), j < i
+        if constexpr (RECT) {
+            // slots hold (diagonal part, aR) and the signed aI: the group sums
+            // of aR give (vr_i, vr_j) = (vi_i, vi_j), those of aI (vi_i, vr_j)
+            const double gaa = seg_scan(v1.y, lane, ghead);
+            const double gma = seg_scan(v2.x, lane, ghead);
+            if (has && (code & SLOT_LAST)) {
+                const int grp = __popc(tb);
+                Hvm[grp] = gma;  // (vi_i, vr_j)
+                if (code & SLOT_LOWER) {
+                    Hva[grp] = gaa;       // (vr_i, vr_j), j < i
+                    Hvm[nd + grp] = gaa;  // (vi_i, vi_j), j < i
+                }
             }
+            tmm = warp_sum(v1.x);
+        } else {
+            const double gaa = seg_scan(v1.x, lane, ghead);
+            const double gma = seg_scan(v1.y, lane, ghead);
+            const double gmm = seg_scan(v2.y, lane, ghead);
+            if (has && (code & SLOT_LAST)) {
+                const int grp = __popc(tb);
+                Hvm[grp < nlt ? grp : grp + 1] = neg(gma);  // (vm_i, va_j)
+                if (code & SLOT_LOWER) {
+                    Hva[grp] = neg(gaa);         // (va_i, va_j), j < i
+                    Hvm[nd + 1 + grp] = gmm;     // (vm_i, vm_j), j < i
+                }
+            }
+            taa = warp_sum(v1.x);
+            tma = warp_sum(v1.y);
+            tmm = warp_sum(v2.x);
         }
-        taa = warp_sum(v1.x);
-        tma = warp_sum(v1.y);
-        tmm = warp_sum(v2.x);
     }
     if (CONS) {
         tp = warp_sum(v0.x);
@@ -858,31 +1032,43 @@ __device__ void heavy_bus_warp(const KParams &P)
     if (lane != 0)
         return;
     // lane 0: the bus's own terms, as for a light bus
+    const double vr = RECT ? __ldg(xs + iva + i) : 0.0;
     const int ng_here = a.w - a.z;
     if (P.want_grad) {
         P.grad[I.x0 + iva + i] = 0.0;
         P.grad[I.x0 + ivm + i] = 0.0;
     }
-    if (i == I.ref) {
+    if (i == I.ref) {  // va_ref, or vi_ref (rectangular)
         if (CONS)
-            P.c[I.c0 + t] = __ldg(xs + iva + i);
+            P.c[I.c0 + t] = RECT ? vm : __ldg(xs + iva + i);
         if (JAC)
             P.jac[I.j0 + t] = 1.0;
     }
     if (JAC) {
         const int jP = (int)I.jP;
-        double *JP = P.jac + I.j0 + (T + 22 * nlT + jP * t + b.x);
+        double *JP = P.jac + I.j0 + (T + (RECT ? 24 : 22) * nlT + jP * t + b.x);
         double *JQ = JP + jP * T;
         const double v2m = twice(vm);
-        JP[0] = gb.x * v2m;
-        JQ[0] = neg(gb.y * v2m);
-        for (int e = 1; e <= ng_here; e++) {
+        if constexpr (RECT) {  // d|V|^2 = (2 vr, 2 vi); the magnitude row
+            const double r2 = twice(vr);
+            JP[0] = gb.x * r2;
+            JP[1] = gb.x * v2m;
+            JQ[0] = neg(gb.y * r2);
+            JQ[1] = neg(gb.y * v2m);
+            double *JV = P.jac + I.j0 + (T + 32 * nlT + 2 * jP * T + 2 * (nb * t + i));
+            JV[0] = r2;
+            JV[1] = v2m;
+        } else {
+            JP[0] = gb.x * v2m;
+            JQ[0] = neg(gb.y * v2m);
+        }
+        for (int e = RECT ? 2 : 1; e <= ng_here + (RECT ? 1 : 0); e++) {
             JP[e] = -1.0;
             JQ[e] = -1.0;
         }
     }
     if (CONS) {
-        const double vm2 = vm * vm;
+        const double vm2 = RECT ? fma(vr, vr, vm * vm) : vm * vm;  // |V|^2
         double Pb = fma(gb.x, vm2, __ldg(d.Pd + I.pd0 + (nb * t + i)));
         double Qb = fma(neg(gb.y), vm2, __ldg(d.Qd + I.pd0 + (nb * t + i)));
         for (int gp = a.z; gp < a.w; gp++) {
@@ -893,13 +1079,22 @@ __device__ void heavy_bus_warp(const KParams &P)
         double *c = P.c + I.c0 + (T + 5 * nlT + nb * t + i);
         c[0] = Pb + tp;
         c[nbT] = Qb + tq;
+        if (RECT)
+            c[3 * nlT + 2 * nbT] = vm2;  // the magnitude row
     }
     if (HESS) {
         const double *L = P.lam + I.c0 + (T + 5 * nlT + nb * t + i);
-        const double dmm = twice(fma(gb.x, __ldg(L), neg(gb.y * __ldg(L + nbT)))) + tmm;
-        Hva[nlt] = taa;
-        Hvm[nlt] = tma;
-        Hvm[nd + 1 + nlt] = dmm;
+        // 2 gs lP - 2 bs lQ (+ 2 lV, the magnitude row, rectangular)
+        const double lV = RECT ? __ldg(L + (3 * nlT + 2 * nbT)) : 0.0;
+        const double dmm = twice(fma(gb.x, __ldg(L), fma(neg(gb.y), __ldg(L + nbT), lV))) + tmm;
+        if (RECT) {  // diagonals (vr_i, vr_i) and (vi_i, vi_i)
+            Hva[nlt] = dmm;
+            Hvm[nd + nlt] = dmm;
+        } else {
+            Hva[nlt] = taa;
+            Hvm[nlt] = tma;
+            Hvm[nd + 1 + nlt] = dmm;
+        }
     }
 }
 
@@ -911,7 +1106,7 @@ __global__ void __launch_bounds__(kBusBlockMax) bus_kernel(const KParams P)
     __shared__ bool last;
     if constexpr (SPLIT) {  // the blocks after the thread items take the heavy buses, a warp each
         if ((int)blockIdx.x >= P.split_tblocks) {
-            heavy_bus_warp<CONS, JAC, HESS, ONE>(P);
+            heavy_bus_warp<CONS, JAC, HESS, ONE, RECT>(P);
             return;
         }
     }
@@ -1830,7 +2025,10 @@ cudaError_t dispatch(const KParams &P, bool one, bool occ, bool occ2, bool rect,
 {
     cudaError_t e = cudaSuccess;
     if (rect) {  // the rectangular branch kernel (two register budgets) and bus variant
-        if (run_branch && occ)
+        if (run_branch && occ2)  // two threads per branch item (gb counts both)
+            e = one ? launch_pdl(rect_branch2_kernel<C, J, H, true>, gb, bb, s, P)
+                    : launch_pdl(rect_branch2_kernel<C, J, H, false>, gb, bb, s, P);
+        else if (run_branch && occ)
             e = one ? launch_pdl(rect_branch_kernel<C, J, H, true, true>, gb, bb, s, P)
                     : launch_pdl(rect_branch_kernel<C, J, H, false, true>, gb, bb, s, P);
         else if (run_branch)
@@ -1838,6 +2036,9 @@ cudaError_t dispatch(const KParams &P, bool one, bool occ, bool occ2, bool rect,
                     : launch_pdl(rect_branch_kernel<C, J, H, false, false>, gb, bb, s, P);
         if (e != cudaSuccess || !run_bus)
             return e;
+        if (splitb)  // light buses a thread each, heavy buses a warp each
+            return one ? launch_pdl(bus_kernel<C, J, H, true, true, false, true>, gu, bu, s, P)
+                       : launch_pdl(bus_kernel<C, J, H, false, true, false, true>, gu, bu, s, P);
         return one ? launch_pdl(bus_kernel<C, J, H, true, true>, gu, bu, s, P)
                    : launch_pdl(bus_kernel<C, J, H, false, true>, gu, bu, s, P);
     }
@@ -1908,12 +2109,12 @@ int launch_all(Model &M, const EvalArgs &a, unsigned what, cudaStream_t s, int p
     const bool run_bus = phases & 2;
     const bool one = M.ninst == 1;
     const bool occ = L.branch_occupancy == 1;
-    // branch_occupancy 2: two threads per branch item (polar form)
-    const bool occ2 = L.branch_occupancy == 2 && !M.rect;
+    // branch_occupancy 2: two threads per branch item
+    const bool occ2 = L.branch_occupancy == 2;
     const int gb2 = occ2 ? grid_for(2 * M.nbr_items, L.branch_block, L.branch_ctas_per_sm, M.num_sms, 0) : gb;
     const int bb = L.branch_block;
     P.order = L.bus_order == 1 ? M.d.bus_order : nullptr;
-    // bus_order 2: the split bus phase where it applies (polar, no storage):
+    // bus_order 2: the split bus phase where it applies (models without storage):
     // light buses a thread each in the first blocks, heavy buses a warp each
     // in the blocks after them; elsewhere buses in id order
     const bool splitb = L.bus_order == 2 && M.split_ok && (phases & 2);

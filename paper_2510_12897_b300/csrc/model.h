@@ -164,7 +164,7 @@ struct Model {
     int64_t nbr_items = 0, nbus_items = 0, ngen_items = 0, narc_slots = 0;
     int64_t nst_items = 0;        // storage items (units x periods, all instances)
     int64_t nlight_items = 0, nheavy_items = 0;  // split bus phase items
-    bool split_ok = false;        // the split bus phase applies (polar, no storage)
+    bool split_ok = false;        // the split bus phase applies (no storage)
     int64_t nload_total = 0;      // sum over instances of nload * nperiod
     int32_t max_part = 0;         // capacity of obj_part
     int device = 0, num_sms = 148;

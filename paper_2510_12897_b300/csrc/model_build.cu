@@ -638,7 +638,7 @@ int build_model(const opf_network *nets, int32_t ninst, const opf_batch_opts *op
     M->nst_items = st_items.back();
     M->nlight_items = light_items.back();
     M->nheavy_items = heavy_items.back();
-    M->split_ok = !rect && !stor;
+    M->split_ok = !stor;
     M->narc_slots = so;
     M->max_part = 16 * M->num_sms;
     M->launch = opf_launch{128, 128, 0, 0, 0, 0};

@@ -64,3 +64,56 @@ def power_flow_point(g):
     x[G["p"]] = np.concatenate([Sf.real, St.real])
     x[G["q"]] = np.concatenate([Sf.imag, St.imag])
     return x
+
+
+class _FreeRows:
+    """A problem with one free row (mu = 0) whose gradient is supplied by a
+    callable of the call count: isolates the oracle's Adam step."""
+
+    def __init__(self, n, grad_of_call):
+        self.n, self.calls, self.grad_of_call = n, 0, grad_of_call
+
+    def bounds(self):
+        return np.full(self.n, -1e30), np.full(self.n, 1e30), np.array([-np.inf]), np.array([np.inf])
+
+    def jac_pattern(self):
+        return np.array([0]), np.array([0])
+
+    def cons(self, x):
+        return np.zeros(1)
+
+    def jac(self, x):
+        return np.zeros(1)
+
+    def obj(self, x):
+        return 0.0
+
+    def grad(self, x):
+        self.calls += 1
+        return self.grad_of_call(self.calls)
+
+
+def test_adam_constant_gradient_moves_lr_per_step():
+    """A constant gradient c makes the bias-corrected moments exactly c and
+    c^2 (Kingma and Ba, Sec. 3), so every step moves x by lr against the sign
+    of c, up to eps / |c| and the FP32 rounding of the scale (3 x 2^-24)."""
+    rng = np.random.default_rng(0)
+    c = rng.uniform(0.5, 5.0, 64) * rng.choice([-1.0, 1.0], 64)
+    A = al.AugLagOracle(_FreeRows(64, lambda k: c), rho=1.0, lr=1e-3)
+    x0 = rng.standard_normal(64)
+    for k in (1, 5, 40):
+        A.k, A.m1, A.m2 = 0, np.zeros(64), np.zeros(64)
+        xk, _ = A.iterate(x0, np.zeros(1), k)
+        np.testing.assert_allclose(xk, x0 - k * 1e-3 * np.sign(c), rtol=0, atol=k * 1e-3 * 5e-7)
+
+
+def test_adam_sign_flip_closed_form():
+    """Gradients c then -c: after the second step m_hat = (0.9 * 0.1 - 0.1) c
+    / (1 - 0.9^2) = -c / 19 and v_hat = c^2 (the two (1 - 0.999) c^2 terms
+    over 1 - 0.999^2), so the two steps sum to -lr sign(c) (1 - 1/19)."""
+    rng = np.random.default_rng(1)
+    c = rng.uniform(0.5, 5.0, 32) * rng.choice([-1.0, 1.0], 32)
+    A = al.AugLagOracle(_FreeRows(32, lambda k: c if k == 1 else -c), rho=1.0, lr=2e-3)
+    x0 = rng.standard_normal(32)
+    x2, _ = A.iterate(x0, np.zeros(1), 2)
+    np.testing.assert_allclose(x2, x0 - 2e-3 * np.sign(c) * (1.0 - 1.0 / 19.0), rtol=0, atol=2e-3 * 1e-6)

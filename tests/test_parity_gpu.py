@@ -461,7 +461,7 @@ def test_pipelined_host_calls(torch, oracle_mod):
 
 @pytest.mark.parametrize("which", ["case30g", "batch_links", "case10k", "hub"])
 def test_split_bus_phase(torch, oracle_mod, which):
-    """The split bus phase (bus_order 2: buses with more than eight arc slots
+    """The split bus phase (bus_order 2: buses with more than six arc slots
     a warp each, one lane per slot, the others a thread each) against the
     oracle: single instance, an N-1 batch with linking rows, the 10k grid
     (buses up to 16 slots), and a hub bus beyond 32 slots (kept per thread)."""

@@ -107,6 +107,47 @@ def test_rect_case10k_full(torch, oracle_mod):
     jtprod_check(torch, M, O, x, lam)
 
 
+@pytest.mark.parametrize("which", ["case30g", "batch_links", "case10k", "hub"])
+def test_rect_split_bus_phase(torch, oracle_mod, which):
+    """The split bus phase in rectangular form (buses with more than six arc
+    slots a warp each, groups of parallel arcs summed by a segmented scan of
+    their aR and aI terms): every output against the oracle, one thread per
+    item and persistent grids; a hub beyond 32 slots stays per thread."""
+    from tests.test_hub_gpu import hub_grid
+    g = {"case30g": lambda: synth.case30(general=True),
+         "batch_links": lambda: synth.contingencies(synth.case30(general=True), 6, seed=3),
+         "case10k": lambda: synth.case10k(),
+         "hub": hub_grid}[which]()
+    link = 0.2 if which == "batch_links" else 0.0
+    M, O = both(torch, oracle_mod, g, link=link, form="rect")
+    for k, (x, lam) in enumerate(rpoints(g, M.m, 2, seed=37)):
+        for bu, cu in ((32, 0), (128, 2)):
+            launch = dict(branch_block=64, bus_block=bu, branch_ctas_per_sm=0, bus_ctas_per_sm=cu, bus_order=2)
+            sigma = 0.0 if k else 1.0
+            check_against_oracle(O, run_all(torch, M, x, lam, sigma, launch), x, lam, sigma, f"pt{k} bu{bu} ")
+
+
+@pytest.mark.parametrize("which", ["case30g", "batch_links", "case10k", "mp30"])
+def test_rect_two_threads_per_branch(torch, oracle_mod, which):
+    """branch_occupancy 2 in rectangular form: each branch item by two lanes,
+    each evaluating its end's rows on (own, far) voltages and one angle row,
+    exchanging the Hessian's aR and aI by shuffles; every output against the
+    oracle, one thread per item and persistent grids, with the split bus
+    phase and without."""
+    g = {"case30g": lambda: synth.case30(general=True),
+         "batch_links": lambda: synth.contingencies(synth.case30(general=True), 6, seed=3),
+         "case10k": lambda: synth.case10k(),
+         "mp30": lambda: synth.multi_period(synth.case30(general=True), 4, seed=8, ramp_ratio=0.2)}[which]()
+    link = 0.2 if which == "batch_links" else 0.0
+    M, O = both(torch, oracle_mod, g, link=link, form="rect")
+    for k, (x, lam) in enumerate(rpoints(g, M.m, 2, seed=38)):
+        for bb, cb, order in ((32, 0, 0), (256, 1, 2), (64, 0, 2)):
+            launch = dict(branch_block=bb, bus_block=64, branch_ctas_per_sm=cb, bus_ctas_per_sm=0, bus_order=order,
+                          branch_occupancy=2)
+            sigma = 0.0 if k else 1.0
+            check_against_oracle(O, run_all(torch, M, x, lam, sigma, launch), x, lam, sigma, f"pt{k} bb{bb} ")
+
+
 def test_rect_rejects_wide_angle_limits(torch):
     g = synth.case30()
     g = g.copy(br_angmax=np.where(np.arange(g.nbranch) == 3, np.pi / 2, g.br_angmax))
