@@ -93,6 +93,9 @@ def load_bf16_peak():
         return 1800.0
 
 
+LAUNCH_KEYS = ("branch_block", "bus_block", "branch_ctas_per_sm", "bus_ctas_per_sm", "bus_order", "branch_occupancy")
+
+
 def profile_value(kernel, key):
     """A number 'key: N' from the committed ncu summary of the branch or bus
     kernel on the 10k grid (dram_bytes_per_launch, fp64_flops_per_launch),
@@ -357,6 +360,8 @@ def main():
         g = synth.case10k()
         sc = synth.scenarios(g, 32, seed=5) if args.profile_batched else g
         Mb = opf.Model(sc, form=args.form)
+        if args.launch:  # a fixed launch shape (else the model's default)
+            Mb.set_launch(**dict(zip(LAUNCH_KEYS, (int(v) for v in args.launch.split(",")))))
         rng = np.random.default_rng(7)
         xb = torch.tensor(synth.random_point(sc, rng, form=args.form), device=dev)
         lb = torch.tensor(rng.standard_normal(Mb.m), device=dev)
@@ -382,9 +387,7 @@ def main():
 
     # launch shape: the autotuner's pick on this workload, shared by all sets
     if args.launch:
-        keys = ("branch_block", "bus_block", "branch_ctas_per_sm", "bus_ctas_per_sm", "bus_order",
-                "branch_occupancy")
-        best, tuned_us = dict(zip(keys, (int(v) for v in args.launch.split(",")))), None
+        best, tuned_us = dict(zip(LAUNCH_KEYS, (int(v) for v in args.launch.split(",")))), None
     elif args.no_autotune:
         best, tuned_us = M0.get_launch(), None
     else:
