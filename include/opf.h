@@ -154,7 +154,13 @@ typedef struct {
                              2: buses with more than 6 arc slots (and at most 32) a warp
                              each, one lane per slot, the others a thread each in id order
                              (shorter longest thread: better for single instances;
-                             storage models run 2 as 0) */
+                             storage models run 2 as 0); 3: the fused evaluation, one
+                             kernel per evaluation and no arc scratch: whole buses
+                             packed into warps, one lane per arc slot, each lane
+                             evaluating its arc end's rows and second-order parts,
+                             summed per bus by segmented warp scans (polar form
+                             without storage, buses of at most 32 arc slots; other
+                             models run 3 as 2; the branch fields are unused) */
     int32_t branch_occupancy; /* 0: branch kernel compiled for up to 128 registers per
                                  thread (shortest chains); 1: for 80 (three blocks of 256
                                  per SM: more warps to hide latency in large batches);

@@ -513,8 +513,8 @@ int opf_set_launch(opf_model *m, const opf_launch *cfg)
             set_error("block size %d not a multiple of 32 in [32, 1024]", b);
             return OPF_EINVAL;
         }
-    if (cfg->bus_order < 0 || cfg->bus_order > 2 || cfg->branch_occupancy < 0 || cfg->branch_occupancy > 2) {
-        set_error("bus_order and branch_occupancy must be 0, 1 or 2");
+    if (cfg->bus_order < 0 || cfg->bus_order > 3 || cfg->branch_occupancy < 0 || cfg->branch_occupancy > 2) {
+        set_error("bus_order must be 0, 1, 2 or 3 and branch_occupancy 0, 1 or 2");
         return OPF_EINVAL;
     }
     if (cfg->branch_block > (cfg->branch_occupancy == 1 ? 256 : 512)) {
@@ -607,8 +607,10 @@ int opf_autotune(opf_model *m, const double *d_x, const double *d_lambda, int32_
     const int bblocks[] = {32, 64, 128, 256, 512};
     const int ublocks[] = {32, 64, 128, 256};  // the bus kernel stages at most 8 warps
     const int ctas[] = {0, 2, 4, 8, 16};
+    // bus_order 3 (the fused evaluation, where the model allows it) has no
+    // branch kernel: its candidates vary the bus block and persistence only
     for (int occ = 0; occ < 3 && !rc; occ++)
-    for (int order = 0; order < 3 && !rc; order++)
+    for (int order = 0; order < (M.fuse_ok ? 4 : 3) && !rc; order++)
     for (int bb : bblocks)
         for (int bu : ublocks)
             for (int cb : ctas)
@@ -616,6 +618,8 @@ int opf_autotune(opf_model *m, const double *d_x, const double *d_lambda, int32_
                     if (rc || (cu != 0 && cu != cb))  // keep the search small: equal persistence
                         continue;
                     if (occ == 1 && bb > 256)
+                        continue;
+                    if (order == 3 && (occ != 0 || bb != 128))
                         continue;
                     M.launch = opf_launch{bb, bu, cb, cu, order, occ};
                     const float ms = time_graph(M, a, reps, 2, cs, e0, e1);

@@ -85,6 +85,7 @@ struct KParams {
     int64_t nbr_items, nbus_items, ngen_items;
     int64_t nst_items;  // storage unit items (bus kernel with storage)
     int64_t nlight_items, nheavy_items;  // split bus phase: light-bus items, heavy-bus items
+    int64_t npack_items = 0;             // fused evaluation: packed-warp items
     int32_t split_tblocks = 0;  // split bus phase: blocks of generator and light-bus items
     const int32_t *order = nullptr;  // bus-phase order within an instance, or null for id order
     double *xw = nullptr;            // x, writable (branch phase that sets the flows)
@@ -1099,14 +1100,322 @@ __device__ void heavy_bus_warp(const KParams &P)
 }
 
 
-template <bool CONS, bool JAC, bool HESS, bool ONE, bool RECT = false, bool STOR = false, bool SPLIT = false>
+// Fused evaluation (bus_order 3, polar form, no storage): the whole
+// evaluation in one kernel, without the arc scratch. Buses are packed whole
+// into warps, one lane per arc slot (a bus without arcs takes one lane), so
+// a bus's arcs sit in consecutive lanes of one warp. Each slot lane does the
+// work of one lane of the two-lane branch kernel for its arc's end at its
+// bus (the end's flow rows, Jacobian rows, thermal row, balance +1 entries,
+// flow Hessian diagonals and gradient zeros; the from-end lane also the
+// angle row), and forms the far end's part of U and V itself (the far
+// multipliers and admittance; the far angle is -d, so sin changes sign)
+// instead of receiving it. The slot's second-order parts are then summed
+// per bus and per group of parallel arcs by segmented inclusive scans over
+// the lanes (fixed order; only as many steps as the warp's longest bus or
+// group needs, and no group scan in warps whose groups are single arcs),
+// and the last lane of each bus writes the bus's own rows, as the bus phase
+// does. Generator items run in the blocks before the packed warps.
+template <bool CONS, bool JAC, bool HESS, bool ONE>
+__device__ void fused_bus_warp(const KParams &P)
+{
+    const DevArrays &d = P.d;
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int64_t w = (int64_t)(blockIdx.x - P.split_tblocks) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (w >= P.npack_items) {
+        cudaGridDependencySynchronize();
+        cudaTriggerProgrammaticLaunchCompletion();
+        return;
+    }
+    int s = 0, t = 0, wl = 0;
+    if (ONE) {
+        split((int)w, P.inst0.npack, P.inst0.T, t, wl);
+    } else {
+        s = find_inst(d.pack_items, P.ninst, w);
+        const InstDev *Ip = d.inst + s;
+        split((int)(w - __ldg(d.pack_items + s)), __ldg(&Ip->npack), __ldg(&Ip->T), t, wl);
+    }
+    const InstDev I = inst_of<ONE>(P, s);
+    const int4 ld = __ldg(d.pack + (((int64_t)I.pack0 + wl) << 5) + lane);  // (arc, bus, flags, group)
+    const int fl = ld.z;
+    const bool valid = (fl & PK_VALID) != 0, tail = (fl & PK_TAIL) != 0;
+    const bool has = ld.x >= 0;  // an arc end (else a bus without arcs, or padding)
+    const int nl = I.nl;
+    const int e = has && ld.x >= nl ? 1 : 0;  // 0: from-end, 1: to-end
+    const int k = has ? ld.x - e * nl : 0;
+    const int kb = I.br0 + k;
+    // static data: this end's branch, the bus's offsets (and, at the bus's
+    // last lane, its slots, generators and shunt)
+    int4 br = make_int4(0, 0, 0, 0), a = make_int4(0, 0, 0, 0), b = make_int4(0, 0, 0, 0);
+    int jb = 0, gfirst = -1;
+    double2 Yo = make_double2(0.0, 0.0), Yx = make_double2(0.0, 0.0), Yf = make_double2(0.0, 0.0);
+    double2 gb = make_double2(0.0, 0.0);
+    double r2 = 0.0;
+    if (has) {
+        br = __ldg(d.br + kb);
+        if (JAC) {
+            const int2 j2 = __ldg(d.br_jb + kb);
+            jb = e ? j2.y : j2.x;
+        }
+        Yo = __ldg((e ? d.y_tt : d.y_ff) + kb);
+        Yx = __ldg((e ? d.y_tf : d.y_ft) + kb);
+        if (HESS)
+            Yf = __ldg((e ? d.y_ft : d.y_tf) + kb);  // the far end's
+        if (CONS)
+            r2 = __ldg(d.rate2 + kb);
+    }
+    const int i = ld.y;
+    if (valid) {
+        const int ib = I.bus0 + i;
+        b = __ldg(d.bus_b + ib);
+        if (tail) {
+            a = __ldg(d.bus_a + ib);
+            gb = __ldg(d.gsbs + ib);
+            if (CONS && a.z < a.w)
+                gfirst = __ldg(d.gen_list + I.gl0 + a.z);
+        }
+    }
+    cudaGridDependencySynchronize();
+    cudaTriggerProgrammaticLaunchCompletion();  // the next kernel may launch now
+
+    const int nb = I.nb, ng = I.ng, T = I.T;
+    const int nbT = nb * T, ngT = ng * T, nlT = nl * T, na = 2 * nl;
+    const int rk = k + nl * t;
+    const int f = br.x, bt = br.y;
+    const int own = has ? (e ? bt : f) : i, far = e ? f : bt;
+    const double *__restrict__ xs = P.x + I.x0;
+    const int iva = nb * t, ivm = nbT + nb * t;
+    const int ip = 2 * nbT + 2 * ngT + na * t, iq = ip + na * T;
+    const int arc = e ? nl + k : k;  // this end's arc
+    double vao = 0.0, vax = 0.0, vo = 0.0, vx = 0.0, po = 0.0, qo = 0.0;
+    if (valid) {
+        vao = __ldg(xs + iva + own);
+        vo = __ldg(xs + ivm + own);
+    }
+    if (has) {
+        vax = __ldg(xs + iva + far);
+        vx = __ldg(xs + ivm + far);
+        if (CONS || JAC || HESS) {
+            po = __ldg(xs + ip + arc);
+            qo = __ldg(xs + iq + arc);
+        }
+    }
+    double mP = 0, mQ = 0, lth = 0, fP = 0, fQ = 0;
+    if (HESS && has) {
+        const double *L = P.lam + I.c0 + (T + rk);
+        mP = __ldg(L + (e ? 2 * nlT : 0));
+        mQ = __ldg(L + (e ? 3 * nlT : nlT));
+        lth = __ldg(L + ((e ? 6 : 5) * nlT + 2 * nbT));
+        fP = __ldg(L + (e ? 0 : 2 * nlT));  // the far end's flow rows
+        fQ = __ldg(L + (e ? nlT : 3 * nlT));
+    }
+    double lP = 0.0, lQ = 0.0, Pd = 0.0, Qd = 0.0, pg1 = 0.0, qg1 = 0.0;
+    if (valid && tail) {  // the bus's own dynamic scalars
+        if (HESS) {
+            const double *L = P.lam + I.c0 + (T + 5 * nlT + nb * t + i);
+            lP = __ldg(L);
+            lQ = __ldg(L + nbT);
+        }
+        if (CONS) {
+            Pd = __ldg(d.Pd + I.pd0 + (nb * t + i));
+            Qd = __ldg(d.Qd + I.pd0 + (nb * t + i));
+            if (gfirst >= 0) {
+                pg1 = __ldg(xs + 2 * nbT + ng * t + gfirst);
+                qg1 = __ldg(xs + 2 * nbT + ngT + ng * t + gfirst);
+            }
+        }
+    }
+
+    // the arc end: as one lane of the two-lane branch kernel
+    double h1 = 0.0, h2 = 0.0, h3 = 0.0, h4 = 0.0;  // the slot's Hessian parts (the scratch record's)
+    if (has) {
+        const double dlt = vao - vax;  // this end's angle
+        double sn, cs_;
+        sincos_tab(dlt, d.trig, &sn, &cs_);
+        const double vft = vo * vx;
+        const double A = fma(Yx.x, cs_, Yx.y * sn);
+        const double B = fma(Yx.x, sn, neg(Yx.y * cs_));
+        if (CONS) {
+            const double vo2 = vo * vo;
+            double *c = P.c + I.c0 + (T + rk);
+            c[e ? 2 * nlT : 0] = po - fma(Yo.x, vo2, vft * A);
+            c[e ? 3 * nlT : nlT] = qo - fma(neg(Yo.y), vo2, vft * B);
+            if (!e)
+                c[4 * nlT] = dlt;
+            c[(e ? 6 : 5) * nlT + 2 * nbT] = fma(po, po, qo * qo) - r2;
+        }
+        if (JAC) {
+            const int jP = (int)I.jP;
+            const bool o_lo = own < far;
+            const double v2o = twice(vo);
+            const double uB = vft * B, uA = vft * A;
+            double *J = P.jac + I.j0;
+            double *Jf = J + (T + 5 * rk + (e ? 10 * nlT : 0));
+            put5(Jf, o_lo, uB, neg(uB), neg(fma(Yo.x, v2o, vx * A)), neg(vo * A));
+            put5(Jf + 5 * nlT, o_lo, neg(uA), uA, fma(Yo.y, v2o, neg(vx * B)), neg(vo * B));
+            if (!e) {  // angle row va_f - va_t
+                double *Ja = J + (T + 20 * nlT + 2 * rk);
+                Ja[0] = flip(1.0, !o_lo);
+                Ja[1] = flip(1.0, o_lo);
+            }
+            double *Jb = J + (T + 22 * nlT + jP * t);  // +1 of the arc in its bus's P and Q rows
+            Jb[jb] = 1.0;
+            Jb[jP * T + jb] = 1.0;
+            double *Jt = J + (T + 22 * nlT + 2 * jP * T + 2 * rk + (e ? 2 * nlT : 0));  // thermal row
+            Jt[0] = twice(po);
+            Jt[1] = twice(qo);
+        }
+        if (HESS) {
+            const double Ue = fma(mP, A, mQ * B);
+            const double Ve = flip(fma(mQ, A, neg(mP * B)), e);
+            // the far end's part: angle -d, admittance Yf, its multipliers
+            const double Af = fma(Yf.x, cs_, neg(Yf.y * sn));
+            const double Bf = neg(fma(Yf.x, sn, Yf.y * cs_));
+            const double Uf = fma(fP, Af, fQ * Bf);
+            const double Vf = flip(fma(fQ, Af, neg(fP * Bf)), !e);
+            const double U = e ? Uf + Ue : Ue + Uf;  // from-end part first
+            const double V = e ? Vf + Ve : Ve + Vf;
+            const double We = fma(mP, Yo.x, neg(mQ * Yo.y));
+            h1 = vft * U;
+            h2 = flip(vx * V, !e);
+            h3 = neg(twice(We));
+            h4 = neg(U);
+            double *Hp = P.hess + I.h0 + ((int)(I.hva + I.hvm) * T + ngT + arc + na * t);
+            const double l2 = twice(lth);
+            Hp[0] = l2;       // (p_arc, p_arc)
+            Hp[na * T] = l2;  // (q_arc, q_arc)
+        }
+        if (P.want_grad) {
+            P.grad[I.x0 + ip + arc] = 0.0;
+            P.grad[I.x0 + iq + arc] = 0.0;
+        }
+    }
+
+    // segmented sums over the lanes: buses (a bus starts at its head lane;
+    // padding lanes are single segments) and groups of parallel arcs (a
+    // group starts after a group's last slot; a bus's last slot closes its
+    // last group)
+    const unsigned upto = (2u << lane) - 1u;  // this lane and the ones below
+    const unsigned bheads = __ballot_sync(full, (fl & PK_HEAD) || !valid);
+    const int bhead = 31 - __clz(bheads & upto);
+    const int bmax = __reduce_max_sync(full, (unsigned)(lane - bhead + 1));
+    double tp = po, tq = qo, taa = h1, tma = h2, tmm = h3;
+    for (int dd = 1; dd < bmax; dd <<= 1) {
+        const bool in = lane - dd >= bhead;
+        if (CONS) {
+            const double yp = __shfl_up_sync(full, tp, dd), yq = __shfl_up_sync(full, tq, dd);
+            if (in) {
+                tp += yp;
+                tq += yq;
+            }
+        }
+        if (HESS) {
+            const double ya = __shfl_up_sync(full, taa, dd), ym = __shfl_up_sync(full, tma, dd);
+            const double yv = __shfl_up_sync(full, tmm, dd);
+            if (in) {
+                taa += ya;
+                tma += ym;
+                tmm += yv;
+            }
+        }
+    }
+    const int nd = b.w & 0xffff, nlt = b.w >> 16;
+    const int hva = (int)I.hva, hvm = (int)I.hvm;
+    double *Hvm = P.hess + I.h0 + (hva * T + hvm * t + b.z);
+    double *Hva = P.hess + I.h0 + (hva * t + b.y);
+    if (HESS) {
+        double gaa = h1, gma = h2, gmm = h4;
+        const unsigned multi = __ballot_sync(full, has && !(fl & PK_GTAIL));
+        if (multi) {  // some group of parallel arcs has more than one slot
+            const unsigned gtails = __ballot_sync(full, (fl & PK_GTAIL) || !valid);
+            const int ghead = 31 - __clz(((gtails << 1) | 1u) & upto);
+            const int gmax = __reduce_max_sync(full, (unsigned)(lane - ghead + 1));
+            for (int dd = 1; dd < gmax; dd <<= 1) {
+                const double ya = __shfl_up_sync(full, gaa, dd), ym = __shfl_up_sync(full, gma, dd);
+                const double yv = __shfl_up_sync(full, gmm, dd);
+                if (lane - dd >= ghead) {
+                    gaa += ya;
+                    gma += ym;
+                    gmm += yv;
+                }
+            }
+        }
+        if (has && (fl & PK_GTAIL)) {  // the group's off-diagonal entries
+            const int grp = ld.w;
+            Hvm[grp < nlt ? grp : grp + 1] = neg(gma);  // (vm_i, va_j)
+            if (fl & PK_LOWER) {
+                Hva[grp] = neg(gaa);      // (va_i, va_j), j < i
+                Hvm[nd + 1 + grp] = gmm;  // (vm_i, vm_j), j < i
+            }
+        }
+    }
+    if (!(valid && tail))
+        return;
+    // the bus's last lane: its own terms, as in the bus phase
+    const int nsl = a.y - a.x, ng_here = a.w - a.z;
+    if (P.want_grad) {
+        P.grad[I.x0 + iva + i] = 0.0;
+        P.grad[I.x0 + ivm + i] = 0.0;
+    }
+    if (i == I.ref) {
+        if (CONS)
+            P.c[I.c0 + t] = vao;
+        if (JAC)
+            P.jac[I.j0 + t] = 1.0;
+    }
+    if (JAC) {
+        const int jP = (int)I.jP;
+        double *JP = P.jac + I.j0 + (T + 22 * nlT + jP * t + b.x);
+        double *JQ = JP + jP * T;
+        const double v2m = twice(vo);
+        JP[0] = gb.x * v2m;
+        JQ[0] = neg(gb.y * v2m);
+        for (int g = 1; g <= ng_here; g++) {
+            JP[g] = -1.0;
+            JQ[g] = -1.0;
+        }
+    }
+    if (CONS) {
+        const double vm2 = vo * vo;
+        double Pb = fma(gb.x, vm2, Pd), Qb = fma(neg(gb.y), vm2, Qd);
+        if (gfirst >= 0) {
+            Pb -= pg1;
+            Qb -= qg1;
+            for (int gp = a.z + 1; gp < a.w; gp++) {
+                const int g = __ldg(d.gen_list + I.gl0 + gp);
+                Pb -= __ldg(xs + 2 * nbT + ng * t + g);
+                Qb -= __ldg(xs + 2 * nbT + ngT + ng * t + g);
+            }
+        }
+        double *c = P.c + I.c0 + (T + 5 * nlT + nb * t + i);
+        c[0] = Pb + tp;
+        c[nbT] = Qb + tq;
+    }
+    if (HESS) {
+        const double dmm = twice(fma(gb.x, lP, neg(gb.y * lQ))) + tmm;
+        if (nsl > 0) {
+            Hva[nlt] = taa;
+            Hvm[nlt] = tma;
+            Hvm[nd + 1 + nlt] = dmm;
+        } else {
+            Hvm[0] = dmm;
+        }
+    }
+}
+
+
+template <bool CONS, bool JAC, bool HESS, bool ONE, bool RECT = false, bool STOR = false, bool SPLIT = false,
+          bool FUSED = false>
 __global__ void __launch_bounds__(kBusBlockMax) bus_kernel(const KParams P)
 {
     __shared__ double wsum[32];
     __shared__ bool last;
     if constexpr (SPLIT) {  // the blocks after the thread items take the heavy buses, a warp each
         if ((int)blockIdx.x >= P.split_tblocks) {
-            heavy_bus_warp<CONS, JAC, HESS, ONE, RECT>(P);
+            if constexpr (FUSED)  // or, fused, the packed warps of whole buses
+                fused_bus_warp<CONS, JAC, HESS, ONE>(P);
+            else
+                heavy_bus_warp<CONS, JAC, HESS, ONE, RECT>(P);
             return;
         }
     }
@@ -1119,7 +1428,7 @@ __global__ void __launch_bounds__(kBusBlockMax) bus_kernel(const KParams P)
     // finish early: padding items after them do nothing
     const int64_t gpad = P.ngen_items < stride ? (P.ngen_items + blockDim.x - 1) / blockDim.x * blockDim.x
                                                : P.ngen_items;
-    const int64_t nbg = (SPLIT ? P.nlight_items : P.nbus_items) + gpad;
+    const int64_t nbg = (FUSED ? 0 : SPLIT ? P.nlight_items : P.nbus_items) + gpad;
     const int64_t total = nbg + (STOR ? P.nst_items : 0);
     int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
 
@@ -2021,9 +2330,15 @@ cudaError_t launch_pdl(K kernel, int grid, int block, cudaStream_t s, const KPar
 
 template <bool C, bool J, bool H>
 cudaError_t dispatch(const KParams &P, bool one, bool occ, bool occ2, bool rect, bool stor, bool run_branch,
-                     bool run_bus, int gb, int bb, int gu, int bu, cudaStream_t s, bool splitb)
+                     bool run_bus, int gb, int bb, int gu, int bu, cudaStream_t s, bool splitb, bool fused)
 {
     cudaError_t e = cudaSuccess;
+    if (fused) {  // one kernel: generator items, then the packed warps (gu counts both)
+        if (!run_bus)
+            return e;
+        return one ? launch_pdl(bus_kernel<C, J, H, true, false, false, true, true>, gu, bu, s, P)
+                   : launch_pdl(bus_kernel<C, J, H, false, false, false, true, true>, gu, bu, s, P);
+    }
     if (rect) {  // the rectangular branch kernel (two register budgets) and bus variant
         if (run_branch && occ2)  // two threads per branch item (gb counts both)
             e = one ? launch_pdl(rect_branch2_kernel<C, J, H, true>, gb, bb, s, P)
@@ -2117,23 +2432,32 @@ int launch_all(Model &M, const EvalArgs &a, unsigned what, cudaStream_t s, int p
     // bus_order 2: the split bus phase where it applies (models without storage):
     // light buses a thread each in the first blocks, heavy buses a warp each
     // in the blocks after them; elsewhere buses in id order
-    const bool splitb = L.bus_order == 2 && M.split_ok && (phases & 2);
+    const bool splitb = L.bus_order >= 2 && M.split_ok && (phases & 2);
+    // bus_order 3: the fused evaluation where it applies (polar, no storage,
+    // at most 32 arc slots per bus), one kernel per evaluation (launched
+    // with the bus phase; the branch phase alone launches nothing)
+    const bool fused = L.bus_order == 3 && M.fuse_ok;
     int gu_all = gu;
-    if (splitb) {
+    if (fused) {
+        const int tb = grid_for(gpad, bu, L.bus_ctas_per_sm, M.num_sms, cap);
+        P.split_tblocks = tb;
+        P.npack_items = M.npack_items;
+        gu_all = tb + (int)((M.npack_items + bu / 32 - 1) / (bu / 32));
+    } else if (splitb) {
         const int tb = grid_for(M.nlight_items + gpad, bu, L.bus_ctas_per_sm, M.num_sms, cap);
         P.split_tblocks = tb;
         gu_all = tb + (int)((M.nheavy_items + bu / 32 - 1) / (bu / 32));
     }
     cudaError_t e;
     switch ((C ? 1 : 0) | (J ? 2 : 0) | (H ? 4 : 0)) {
-    case 0: e = dispatch<false, false, false>(P, one, occ, occ2, M.rect, M.storage, run_branch, run_bus, gb2, bb, gu_all, bu, s, splitb); break;
-    case 1: e = dispatch<true, false, false>(P, one, occ, occ2, M.rect, M.storage, run_branch, run_bus, gb2, bb, gu_all, bu, s, splitb); break;
-    case 2: e = dispatch<false, true, false>(P, one, occ, occ2, M.rect, M.storage, run_branch, run_bus, gb2, bb, gu_all, bu, s, splitb); break;
-    case 3: e = dispatch<true, true, false>(P, one, occ, occ2, M.rect, M.storage, run_branch, run_bus, gb2, bb, gu_all, bu, s, splitb); break;
-    case 4: e = dispatch<false, false, true>(P, one, occ, occ2, M.rect, M.storage, run_branch, run_bus, gb2, bb, gu_all, bu, s, splitb); break;
-    case 5: e = dispatch<true, false, true>(P, one, occ, occ2, M.rect, M.storage, run_branch, run_bus, gb2, bb, gu_all, bu, s, splitb); break;
-    case 6: e = dispatch<false, true, true>(P, one, occ, occ2, M.rect, M.storage, run_branch, run_bus, gb2, bb, gu_all, bu, s, splitb); break;
-    default: e = dispatch<true, true, true>(P, one, occ, occ2, M.rect, M.storage, run_branch, run_bus, gb2, bb, gu_all, bu, s, splitb); break;
+    case 0: e = dispatch<false, false, false>(P, one, occ, occ2, M.rect, M.storage, run_branch, run_bus, gb2, bb, gu_all, bu, s, splitb, fused); break;
+    case 1: e = dispatch<true, false, false>(P, one, occ, occ2, M.rect, M.storage, run_branch, run_bus, gb2, bb, gu_all, bu, s, splitb, fused); break;
+    case 2: e = dispatch<false, true, false>(P, one, occ, occ2, M.rect, M.storage, run_branch, run_bus, gb2, bb, gu_all, bu, s, splitb, fused); break;
+    case 3: e = dispatch<true, true, false>(P, one, occ, occ2, M.rect, M.storage, run_branch, run_bus, gb2, bb, gu_all, bu, s, splitb, fused); break;
+    case 4: e = dispatch<false, false, true>(P, one, occ, occ2, M.rect, M.storage, run_branch, run_bus, gb2, bb, gu_all, bu, s, splitb, fused); break;
+    case 5: e = dispatch<true, false, true>(P, one, occ, occ2, M.rect, M.storage, run_branch, run_bus, gb2, bb, gu_all, bu, s, splitb, fused); break;
+    case 6: e = dispatch<false, true, true>(P, one, occ, occ2, M.rect, M.storage, run_branch, run_bus, gb2, bb, gu_all, bu, s, splitb, fused); break;
+    default: e = dispatch<true, true, true>(P, one, occ, occ2, M.rect, M.storage, run_branch, run_bus, gb2, bb, gu_all, bu, s, splitb, fused); break;
     }
     if (e == cudaSuccess && M.reserve && (C || J) && (phases & 2)) {
         const int64_t threads = 32 * M.nres;

@@ -43,6 +43,11 @@ constexpr int kLightSlots = 6;
 // slot codes: the slot closes its far bus's group / the far bus is lower
 enum : uint8_t { SLOT_LAST = 1u, SLOT_LOWER = 2u };
 
+// fused evaluation (bus_order 3): whole buses packed into warps, one lane per
+// arc slot (a bus without arcs takes one lane). Per lane an int4 (arc id or
+// -1, local bus, flags, group index of the slot within its bus); flags:
+enum : int32_t { PK_VALID = 1, PK_HEAD = 2, PK_TAIL = 4, PK_GTAIL = 8, PK_LOWER = 16 };
+
 // One instance of a batch, as seen by the kernels. Offsets are absolute
 // positions in the caller's x / g / Jacobian / Hessian arrays and in the
 // model's concatenated network arrays.
@@ -74,6 +79,7 @@ struct __align__(16) InstDev {
     int32_t st0;        // first unit in the concatenated storage arrays
     int32_t nlight, light0;  // split bus phase: buses one per thread (count, first list entry)
     int32_t nheavy, heavy0;  // split bus phase: buses one per warp (more than kLightSlots slots)
+    int32_t npack, pack0;    // fused evaluation: packed warps of one period (count, first warp)
 };
 static_assert(sizeof(InstDev) % 16 == 0, "InstDev is loaded as int4 words");
 
@@ -114,6 +120,10 @@ struct DevArrays {
     // warp each), local ids ascending per instance, and their item prefixes
     int32_t *light_list = nullptr, *heavy_list = nullptr;
     int64_t *light_items = nullptr, *heavy_items = nullptr;
+    // fused evaluation: 32 lane words per packed warp, and the prefix of
+    // packed-warp items (npack T) over instances
+    int4 *pack = nullptr;
+    int64_t *pack_items = nullptr;
     int64_t *st_items = nullptr;  // prefix of storage items (ns T) over instances, ninst + 1
     // instances and work lists
     InstDev *inst = nullptr;
@@ -165,6 +175,8 @@ struct Model {
     int64_t nst_items = 0;        // storage items (units x periods, all instances)
     int64_t nlight_items = 0, nheavy_items = 0;  // split bus phase items
     bool split_ok = false;        // the split bus phase applies (no storage)
+    int64_t npack_items = 0;      // fused evaluation: packed warps x periods, all instances
+    bool fuse_ok = false;         // the fused evaluation applies (polar, no storage, <= 32 slots per bus)
     int64_t nload_total = 0;      // sum over instances of nload * nperiod
     int32_t max_part = 0;         // capacity of obj_part
     int device = 0, num_sms = 148;

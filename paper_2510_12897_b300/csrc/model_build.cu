@@ -279,7 +279,9 @@ int build_model(const opf_network *nets, int32_t ninst, const opf_batch_opts *op
     std::vector<int4> br, bus_a, bus_b;
     std::vector<int2> bus_c, br_jb;
     std::vector<int32_t> bus_order, light_list, heavy_list;
-    std::vector<int64_t> light_items(1, 0), heavy_items(1, 0);
+    std::vector<int64_t> light_items(1, 0), heavy_items(1, 0), pack_items(1, 0);
+    std::vector<int4> pack;
+    bool fits32 = true;  // every bus has at most 32 arc slots
     std::vector<double2> y_ff, y_ft, y_tf, y_tt, gsbs, pbnd, qbnd, vbnd;
     std::vector<double> rate2, Pd, Qd, c2, c1, c0;
     std::vector<double2> tanb;
@@ -484,6 +486,43 @@ int build_model(const opf_network *nets, int32_t ninst, const opf_batch_opts *op
         I.nlight = (int32_t)light_list.size() - I.light0;
         I.nheavy = (int32_t)heavy_list.size() - I.heavy0;
 
+        // ---- fused evaluation: buses in id order packed whole into warps of
+        // 32 lanes, one lane per arc slot (one for a bus without arcs); the
+        // rest of a warp that cannot take the next bus is padding
+        I.pack0 = (int32_t)(pack.size() / 32);
+        {
+            const size_t lo = (size_t)I.slot0;
+            auto close_warp = [&]() {
+                while (pack.size() % 32)
+                    pack.push_back(make_int4(-1, -1, 0, 0));
+            };
+            for (int i = 0; i < nb; i++) {
+                const int p0 = H.arc_ptr[i], p1 = H.arc_ptr[i + 1];
+                const int lanes = p1 > p0 ? p1 - p0 : 1;
+                if (lanes > 32) {
+                    fits32 = false;
+                    continue;
+                }
+                if (pack.size() % 32 + lanes > 32)
+                    close_warp();
+                if (p1 == p0) {
+                    pack.push_back(make_int4(-1, i, PK_VALID | PK_HEAD | PK_TAIL | PK_GTAIL, 0));
+                    continue;
+                }
+                int grp = 0;
+                for (int p = p0; p < p1; p++) {
+                    const uint8_t code = slot_code[lo + p];
+                    int fl = PK_VALID | (p == p0 ? PK_HEAD : 0) | (p + 1 == p1 ? PK_TAIL : 0) |
+                             ((code & SLOT_LAST) ? PK_GTAIL : 0) | ((code & SLOT_LOWER) ? PK_LOWER : 0);
+                    pack.push_back(make_int4(H.slot_arc[p], i, fl, grp));
+                    if (code & SLOT_LAST)
+                        grp++;
+                }
+            }
+            close_warp();
+        }
+        I.npack = (int32_t)(pack.size() / 32) - I.pack0;
+
         // ---- each arc's +1 entry in its bus's balance row: after the voltage
         // entries and the bus's generators, arcs in ascending id
         {
@@ -589,6 +628,7 @@ int build_model(const opf_network *nets, int32_t ninst, const opf_batch_opts *op
         st_items.push_back(st_items.back() + (int64_t)ns * T);
         light_items.push_back(light_items.back() + (int64_t)I.nlight * T);
         heavy_items.push_back(heavy_items.back() + (int64_t)I.nheavy * T);
+        pack_items.push_back(pack_items.back() + (int64_t)I.npack * T);
         for (int k = 0; k < ns; k++)
             st_busid.push_back(stor[s].bus[k]);
     }
@@ -639,6 +679,8 @@ int build_model(const opf_network *nets, int32_t ninst, const opf_batch_opts *op
     M->nlight_items = light_items.back();
     M->nheavy_items = heavy_items.back();
     M->split_ok = !stor;
+    M->npack_items = pack_items.back();
+    M->fuse_ok = !rect && !stor && fits32;
     M->narc_slots = so;
     M->max_part = 16 * M->num_sms;
     M->launch = opf_launch{128, 128, 0, 0, 0, 0};
@@ -664,6 +706,9 @@ int build_model(const opf_network *nets, int32_t ninst, const opf_batch_opts *op
     if (M->split_ok) {
         UP(light_list, light_list) UP(heavy_list, heavy_list) UP(light_items, light_items)
         UP(heavy_items, heavy_items)
+    }
+    if (M->fuse_ok) {
+        UP(pack, pack) UP(pack_items, pack_items)
     }
     if (M->storage) {
         UP(bus_st, bus_st) UP(st_list, st_list) UP(st_par, st_par) UP(st_busid, st_busid) UP(st_items, st_items)

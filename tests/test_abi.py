@@ -171,7 +171,7 @@ def test_null_and_state_errors(L):
     _expect(opf.OPF_EINVAL, opf._check, L.opf_set_launch(M.h, ctypes.byref(cfg)))
     assert b"multiple of 32" in L.opf_last_error()
     for bad in (opf.OpfLaunch(512, 128, 0, 0, 0, 1), opf.OpfLaunch(1024, 128, 0, 0, 0, 0),
-                opf.OpfLaunch(128, 128, 0, 0, 3, 0), opf.OpfLaunch(128, 128, 0, 0, 0, -1),
+                opf.OpfLaunch(128, 128, 0, 0, 4, 0), opf.OpfLaunch(128, 128, 0, 0, 0, -1),
                 opf.OpfLaunch(128, 128, 0, 0, 0, 3)):
         _expect(opf.OPF_EINVAL, opf._check, L.opf_set_launch(M.h, ctypes.byref(bad)))
     ok = opf.OpfLaunch(256, 64, 0, 0, 1, 1)

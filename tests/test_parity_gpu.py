@@ -503,3 +503,74 @@ def test_two_threads_per_branch(torch, oracle_mod, which):
         x, lam = next(points(g, Mr.m, 1, seed=36))
         check_against_oracle(Or, run_all(torch, Mr, x, lam, 1.0, dict(branch_block=64, bus_block=64,
                              branch_ctas_per_sm=0, bus_ctas_per_sm=0, bus_order=0, branch_occupancy=2)), x, lam, 1.0)
+
+
+FUSED = dict(branch_block=128, bus_block=64, branch_ctas_per_sm=0, bus_ctas_per_sm=0, bus_order=3)
+
+
+def isolated_bus_grid():
+    g = synth.case30(general=True)
+    return g.copy(nbus=g.nbus + 1, bus_vmin=np.append(g.bus_vmin, 0.95), bus_vmax=np.append(g.bus_vmax, 1.05),
+                  bus_gs=np.append(g.bus_gs, 0.01), bus_bs=np.append(g.bus_bs, 0.02))
+
+
+@pytest.mark.parametrize("which", ["case30g", "isolated", "batch_links", "reserve", "case10k", "mp30", "hub"])
+def test_fused_evaluation(torch, oracle_mod, which):
+    """bus_order 3, the one-kernel evaluation (whole buses packed into warps,
+    one lane per arc slot, per-bus and per-group segmented scans): every
+    output against the oracle with bus blocks of 32 and 128 and a persistent
+    generator grid; single instances, a bus without arcs, an N-1 batch with
+    linking rows, one with reserve rows and corrective ratios, the 10k grid,
+    multiple periods with ramp rows, and a hub beyond 32 slots (which runs
+    the split bus phase instead)."""
+    from tests.test_hub_gpu import hub_grid
+    g = {"case30g": lambda: synth.case30(general=True),
+         "isolated": isolated_bus_grid,
+         "batch_links": lambda: synth.contingencies(synth.case30(general=True), 6, seed=3),
+         "reserve": lambda: synth.contingencies(synth.case30(general=True), 9, seed=7),
+         "case10k": lambda: synth.case10k(),
+         "mp30": lambda: synth.multi_period(synth.case30(general=True), 4, seed=8, ramp_ratio=0.2),
+         "hub": hub_grid}[which]()
+    link = 0.2 if which == "batch_links" else 0.0
+    opts = dict(link_ratios=[0.0] + [0.05 * k for k in range(1, 10)], reserve=0.1) if which == "reserve" else {}
+    M, O = both(torch, oracle_mod, g, link=link, **opts)
+    for k, (x, lam) in enumerate(points(g, M.m, 2, seed=39)):
+        for bu, cu in ((32, 0), (128, 2)):
+            launch = dict(FUSED, bus_block=bu, bus_ctas_per_sm=cu)
+            sigma = 0.0 if k else 0.8
+            check_against_oracle(O, run_all(torch, M, x, lam, sigma, launch), x, lam, sigma, f"pt{k} bu{bu} ")
+
+
+def test_fused_separate_callbacks(torch, oracle_mod):
+    """The fused kernel's template variants (constraints only, Jacobian only,
+    Hessian only, objective and gradient only, Jacobian + Hessian) write the
+    same values as its all-callback variant, and the branch phase alone
+    launches nothing."""
+    g = synth.multi_period(synth.case30(general=True), 3, seed=9, ramp_ratio=0.2)
+    M, O = both(torch, oracle_mod, g)
+    x, lam = next(points(g, M.m, 1, seed=40))
+    fused = run_all(torch, M, x, lam, 1.0, FUSED)
+    check_against_oracle(O, fused, x, lam, 1.0)
+    dx, dl = dev(torch, x), dev(torch, lam)
+    c = torch.empty(M.m, dtype=torch.float64, device="cuda")
+    jv = torch.empty(M.nnzj, dtype=torch.float64, device="cuda")
+    hv = torch.empty(M.nnzh, dtype=torch.float64, device="cuda")
+    jv2, hv2 = torch.empty_like(jv), torch.empty_like(hv)
+    ob = torch.empty(1, dtype=torch.float64, device="cuda")
+    gr = torch.empty(M.n, dtype=torch.float64, device="cuda")
+    M.eval_cons(dx, c)
+    M.eval_jac(dx, jv)
+    M.eval_hess(dx, dl, 1.0, hv)
+    M.eval_jac_hess(dx, dl, 1.0, jv2, hv2)
+    M.eval_obj_grad(dx, ob, gr)
+    torch.cuda.synchronize()
+    for name, a, b in (("c", c, "c"), ("jv", jv, "jv"), ("jv2", jv2, "jv"), ("hv", hv, "hv"), ("hv2", hv2, "hv"),
+                       ("grad", gr, "grad"), ("obj", ob, "obj")):
+        np.testing.assert_array_equal(host(a), fused[b], err_msg=name)
+    c2 = torch.full((M.m,), np.nan, dtype=torch.float64, device="cuda")
+    M.eval_phases(1, dx, c=c2)  # the branch phase alone: no kernel in the fused evaluation
+    torch.cuda.synchronize()
+    assert np.all(np.isnan(host(c2)))
+    M.eval_phases(2, dx, c=c2)  # the bus phase: the whole evaluation
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(host(c2), fused["c"])
