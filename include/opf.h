@@ -160,7 +160,9 @@ typedef struct {
                              evaluating its arc end's rows and second-order parts,
                              summed per bus by segmented warp scans (polar form
                              without storage, buses of at most 32 arc slots; other
-                             models run 3 as 2; the branch fields are unused) */
+                             models run 3 as 2; the branch fields are unused, except
+                             branch_occupancy 2: two warps per packed warp, one for
+                             the rows and Jacobian, one for the Hessian) */
     int32_t branch_occupancy; /* 0: branch kernel compiled for up to 128 registers per
                                  thread (shortest chains); 1: for 80 (three blocks of 256
                                  per SM: more warps to hide latency in large batches);

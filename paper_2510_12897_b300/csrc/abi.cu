@@ -619,7 +619,7 @@ int opf_autotune(opf_model *m, const double *d_x, const double *d_lambda, int32_
                         continue;
                     if (occ == 1 && bb > 256)
                         continue;
-                    if (order == 3 && (occ != 0 || bb != 128))
+                    if (order == 3 && (occ == 1 || bb != 128))  // occupancy 2: two roles per packed warp
                         continue;
                     M.launch = opf_launch{bb, bu, cb, cu, order, occ};
                     const float ms = time_graph(M, a, reps, 2, cs, e0, e1);

@@ -86,6 +86,7 @@ struct KParams {
     int64_t nst_items;  // storage unit items (bus kernel with storage)
     int64_t nlight_items, nheavy_items;  // split bus phase: light-bus items, heavy-bus items
     int64_t npack_items = 0;             // fused evaluation: packed-warp items
+    int32_t fuse_roles = 0;              // fused evaluation: two warps (rows, Hessian) per packed warp
     int32_t split_tblocks = 0;  // split bus phase: blocks of generator and light-bus items
     const int32_t *order = nullptr;  // bus-phase order within an instance, or null for id order
     double *xw = nullptr;            // x, writable (branch phase that sets the flows)
@@ -1115,13 +1116,18 @@ __device__ void heavy_bus_warp(const KParams &P)
 // group needs, and no group scan in warps whose groups are single arcs),
 // and the last lane of each bus writes the bus's own rows, as the bus phase
 // does. Generator items run in the blocks before the packed warps.
+//
+// With two roles (branch_occupancy 2 in this mode) each packed warp of buses
+// is taken by two warps, one writing the rows and the Jacobian (and the
+// gradient zeros), the other the Hessian; both evaluate the shared
+// trigonometry, so the dependent chain of each is shorter at the cost of
+// that duplicated work.
 template <bool CONS, bool JAC, bool HESS, bool ONE>
-__device__ void fused_bus_warp(const KParams &P)
+__device__ void fused_bus_warp(const KParams &P, const int64_t w, const bool grad_here)
 {
     const DevArrays &d = P.d;
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const int64_t w = (int64_t)(blockIdx.x - P.split_tblocks) * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (w >= P.npack_items) {
         cudaGridDependencySynchronize();
         cudaTriggerProgrammaticLaunchCompletion();
@@ -1285,7 +1291,7 @@ __device__ void fused_bus_warp(const KParams &P)
             Hp[0] = l2;       // (p_arc, p_arc)
             Hp[na * T] = l2;  // (q_arc, q_arc)
         }
-        if (P.want_grad) {
+        if (P.want_grad && grad_here) {
             P.grad[I.x0 + ip + arc] = 0.0;
             P.grad[I.x0 + iq + arc] = 0.0;
         }
@@ -1353,7 +1359,7 @@ __device__ void fused_bus_warp(const KParams &P)
         return;
     // the bus's last lane: its own terms, as in the bus phase
     const int nsl = a.y - a.x, ng_here = a.w - a.z;
-    if (P.want_grad) {
+    if (P.want_grad && grad_here) {
         P.grad[I.x0 + iva + i] = 0.0;
         P.grad[I.x0 + ivm + i] = 0.0;
     }
@@ -1412,9 +1418,19 @@ __global__ void __launch_bounds__(kBusBlockMax) bus_kernel(const KParams P)
     __shared__ bool last;
     if constexpr (SPLIT) {  // the blocks after the thread items take the heavy buses, a warp each
         if ((int)blockIdx.x >= P.split_tblocks) {
-            if constexpr (FUSED)  // or, fused, the packed warps of whole buses
-                fused_bus_warp<CONS, JAC, HESS, ONE>(P);
-            else
+            if constexpr (FUSED) {  // or, fused, the packed warps of whole buses
+                const int64_t wr = (int64_t)(blockIdx.x - P.split_tblocks) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+                if constexpr (HESS && (CONS || JAC)) {
+                    if (P.fuse_roles) {  // even warps: rows and Jacobian; odd warps: Hessian
+                        if (wr & 1)
+                            fused_bus_warp<false, false, true, ONE>(P, wr >> 1, false);
+                        else
+                            fused_bus_warp<CONS, JAC, false, ONE>(P, wr >> 1, true);
+                        return;
+                    }
+                }
+                fused_bus_warp<CONS, JAC, HESS, ONE>(P, wr, true);
+            } else
                 heavy_bus_warp<CONS, JAC, HESS, ONE, RECT>(P);
             return;
         }
@@ -2442,7 +2458,10 @@ int launch_all(Model &M, const EvalArgs &a, unsigned what, cudaStream_t s, int p
         const int tb = grid_for(gpad, bu, L.bus_ctas_per_sm, M.num_sms, cap);
         P.split_tblocks = tb;
         P.npack_items = M.npack_items;
-        gu_all = tb + (int)((M.npack_items + bu / 32 - 1) / (bu / 32));
+        // two roles only where there is both a Hessian and rows or Jacobian to write
+        P.fuse_roles = L.branch_occupancy == 2 && H && (C || J) ? 1 : 0;
+        const int64_t warps = M.npack_items * (P.fuse_roles ? 2 : 1);
+        gu_all = tb + (int)((warps + bu / 32 - 1) / (bu / 32));
     } else if (splitb) {
         const int tb = grid_for(M.nlight_items + gpad, bu, L.bus_ctas_per_sm, M.num_sms, cap);
         P.split_tblocks = tb;

@@ -518,8 +518,9 @@ def isolated_bus_grid():
 def test_fused_evaluation(torch, oracle_mod, which):
     """bus_order 3, the one-kernel evaluation (whole buses packed into warps,
     one lane per arc slot, per-bus and per-group segmented scans): every
-    output against the oracle with bus blocks of 32 and 128 and a persistent
-    generator grid; single instances, a bus without arcs, an N-1 batch with
+    output against the oracle with bus blocks of 32 to 128, a persistent
+    generator grid, and one or two warps (rows and Jacobian; Hessian) per
+    packed warp; single instances, a bus without arcs, an N-1 batch with
     linking rows, one with reserve rows and corrective ratios, the 10k grid,
     multiple periods with ramp rows, and a hub beyond 32 slots (which runs
     the split bus phase instead)."""
@@ -535,13 +536,15 @@ def test_fused_evaluation(torch, oracle_mod, which):
     opts = dict(link_ratios=[0.0] + [0.05 * k for k in range(1, 10)], reserve=0.1) if which == "reserve" else {}
     M, O = both(torch, oracle_mod, g, link=link, **opts)
     for k, (x, lam) in enumerate(points(g, M.m, 2, seed=39)):
-        for bu, cu in ((32, 0), (128, 2)):
-            launch = dict(FUSED, bus_block=bu, bus_ctas_per_sm=cu)
+        for bu, cu, occ in ((32, 0, 0), (128, 2, 0), (64, 0, 2), (128, 4, 2)):
+            launch = dict(FUSED, bus_block=bu, bus_ctas_per_sm=cu, branch_occupancy=occ)
             sigma = 0.0 if k else 0.8
-            check_against_oracle(O, run_all(torch, M, x, lam, sigma, launch), x, lam, sigma, f"pt{k} bu{bu} ")
+            check_against_oracle(O, run_all(torch, M, x, lam, sigma, launch), x, lam, sigma,
+                                 f"pt{k} bu{bu} occ{occ} ")
 
 
-def test_fused_separate_callbacks(torch, oracle_mod):
+@pytest.mark.parametrize("occ", [0, 2])
+def test_fused_separate_callbacks(torch, oracle_mod, occ):
     """The fused kernel's template variants (constraints only, Jacobian only,
     Hessian only, objective and gradient only, Jacobian + Hessian) write the
     same values as its all-callback variant, and the branch phase alone
@@ -549,7 +552,7 @@ def test_fused_separate_callbacks(torch, oracle_mod):
     g = synth.multi_period(synth.case30(general=True), 3, seed=9, ramp_ratio=0.2)
     M, O = both(torch, oracle_mod, g)
     x, lam = next(points(g, M.m, 1, seed=40))
-    fused = run_all(torch, M, x, lam, 1.0, FUSED)
+    fused = run_all(torch, M, x, lam, 1.0, dict(FUSED, branch_occupancy=occ))
     check_against_oracle(O, fused, x, lam, 1.0)
     dx, dl = dev(torch, x), dev(torch, lam)
     c = torch.empty(M.m, dtype=torch.float64, device="cuda")
