@@ -158,9 +158,9 @@ typedef struct {
                              kernel per evaluation and no arc scratch: whole buses
                              packed into warps, one lane per arc slot, each lane
                              evaluating its arc end's rows and second-order parts,
-                             summed per bus by segmented warp scans (polar form
-                             without storage, buses of at most 32 arc slots; other
-                             models run 3 as 2; the branch fields are unused, except
+                             summed per bus by segmented warp scans (models
+                             without storage whose buses have at most 32 arc
+                             slots, either form; other models run 3 as 2; the branch fields are unused, except
                              branch_occupancy 2: two warps per packed warp, one for
                              the rows and Jacobian, one for the Hessian) */
     int32_t branch_occupancy; /* 0: branch kernel compiled for up to 128 registers per

@@ -1101,7 +1101,85 @@ __device__ void heavy_bus_warp(const KParams &P)
 }
 
 
-// Fused evaluation (bus_order 3, polar form, no storage): the whole
+// One arc end of the fused evaluation in rectangular form: the rows, the
+// Jacobian, the flow Hessian diagonals and the gradient zeros of one lane of
+// the rectangular two-lane branch kernel, with the far end's parts of aR and
+// aI formed here from the far multipliers, admittance and angle limit.
+// Returns the slot's Hessian parts: h1 the diagonal part, h2 aR, h3 the
+// signed aI.
+template <bool CONS, bool JAC, bool HESS>
+__device__ __forceinline__ void fused_rect_arc(const KParams &P, const InstDev &I, int e, int k, int t, int own,
+                                               int far, int4 br, int jb, double2 Yo, double2 Yx, double2 Yf,
+                                               double r2, double tno, double tnf, double vro, double vrx,
+                                               double vio, double vix, double po, double qo, double mP, double mQ,
+                                               double ma, double lth, double fP, double fQ, double fa,
+                                               bool grad_here, double &h1, double &h2, double &h3)
+{
+    const int nl = I.nl, nb = I.nb, ng = I.ng, T = I.T;
+    const int nbT = nb * T, ngT = ng * T, nlT = nl * T, na = 2 * nl;
+    const int rk = k + nl * t;
+    const int f = br.x, b = br.y;
+    const int ip = 2 * nbT + 2 * ngT + na * t, iq = ip + na * T;
+    const int arc = e ? nl + k : k;
+    // w_e = V_own conj(V_far): w at the from-end, conj(w) at the to-end
+    const double wR = fma(vro, vrx, vio * vix);
+    const double wI = fma(vio, vrx, neg(vro * vix));
+    if (CONS) {
+        const double vo2 = fma(vro, vro, vio * vio);
+        double *c = P.c + I.c0 + (T + rk);
+        c[e ? 2 * nlT : 0] = po - fma(Yo.x, vo2, fma(Yx.x, wR, Yx.y * wI));
+        c[e ? 3 * nlT : nlT] = qo - fma(neg(Yo.y), vo2, fma(Yx.x, wI, neg(Yx.y * wR)));
+        c[e ? 7 * nlT + 2 * nbT : 4 * nlT] = fma(neg(tno), wR, flip(wI, e));  // this lane's angle row
+        c[(e ? 6 : 5) * nlT + 2 * nbT] = fma(po, po, qo * qo) - r2;
+    }
+    if (JAC) {
+        const int jP = (int)I.jP;
+        const bool o_lo = own < far;
+        double *J = P.jac + I.j0;
+        double *Jf = J + (T + 5 * rk + (e ? 10 * nlT : 0));
+        const double y1r = fma(Yx.x, vrx, neg(Yx.y * vix)), y1i = fma(Yx.x, vix, Yx.y * vrx);
+        const double y2r = fma(Yx.x, vro, Yx.y * vio), y2i = fma(Yx.y, vro, neg(Yx.x * vio));
+        const double pa = neg(twice(Yo.x)), qa = twice(Yo.y);
+        Grad4 g;  // (own, far) in the places of (f, t)
+        g.rf = fma(pa, vro, neg(y1r)); g.jf = fma(pa, vio, neg(y1i)); g.rt = neg(y2r); g.jt = y2i;
+        put_rect(Jf, o_lo, g, true);
+        g.rf = fma(qa, vro, y1i); g.jf = fma(qa, vio, neg(y1r)); g.rt = y2i; g.jt = y2r;
+        put_rect(Jf + 5 * nlT, o_lo, g, true);
+        const double tu = neg(tno);
+        const double vrf = e ? vrx : vro, vrt = e ? vro : vrx, vif = e ? vix : vio, vit = e ? vio : vix;
+        g.rf = fma(tu, vrt, neg(vit)); g.jf = fma(tu, vit, vrt); g.rt = fma(tu, vrf, vif); g.jt = fma(tu, vif, neg(vrf));
+        put_rect(J + (T + (e ? 28 * nlT + 2 * jP * T : 20 * nlT) + 4 * rk), f < b, g, false);
+        double *Jb = J + (T + 24 * nlT + jP * t);  // +1 of the arc in its bus's P and Q rows
+        Jb[jb] = 1.0;
+        Jb[jP * T + jb] = 1.0;
+        double *Jt = J + (T + 24 * nlT + 2 * jP * T + 2 * rk + (e ? 2 * nlT : 0));  // thermal row
+        Jt[0] = twice(po);
+        Jt[1] = twice(qo);
+    }
+    if (HESS) {
+        // aR = -(m1 Gft - m2 Bft + a1 tan(angmax)) - (m3 Gtf - m4 Btf + a2 tan(angmin))
+        // aI = (-m1 Bft - m2 Gft + a1) + (m3 Btf + m4 Gtf + a2): one part per end
+        const double Re = neg(fma(mP, Yx.x, fma(neg(mQ), Yx.y, ma * tno)));
+        const double Ie = flip(fma(mP, Yx.y, mQ * Yx.x), !e) + ma;
+        const double Rf = neg(fma(fP, Yf.x, fma(neg(fQ), Yf.y, fa * tnf)));
+        const double If = flip(fma(fP, Yf.y, fQ * Yf.x), e) + fa;
+        const double aR = e ? Rf + Re : Re + Rf;  // from-end part first
+        const double aI = e ? If + Ie : Ie + If;
+        h1 = neg(twice(fma(mP, Yo.x, neg(mQ * Yo.y))));
+        h2 = aR;
+        h3 = flip(aI, e);
+        double *Hp = P.hess + I.h0 + ((int)(I.hva + I.hvm) * T + ngT + arc + na * t);
+        const double l2 = twice(lth);
+        Hp[0] = l2;       // (p_arc, p_arc)
+        Hp[na * T] = l2;  // (q_arc, q_arc)
+    }
+    if (P.want_grad && grad_here) {
+        P.grad[I.x0 + ip + arc] = 0.0;
+        P.grad[I.x0 + iq + arc] = 0.0;
+    }
+}
+
+// Fused evaluation (bus_order 3, models without storage): the whole
 // evaluation in one kernel, without the arc scratch. Buses are packed whole
 // into warps, one lane per arc slot (a bus without arcs takes one lane), so
 // a bus's arcs sit in consecutive lanes of one warp. Each slot lane does the
@@ -1115,14 +1193,17 @@ __device__ void heavy_bus_warp(const KParams &P)
 // the lanes (fixed order; only as many steps as the warp's longest bus or
 // group needs, and no group scan in warps whose groups are single arcs),
 // and the last lane of each bus writes the bus's own rows, as the bus phase
-// does. Generator items run in the blocks before the packed warps.
+// does. Generator items run in the blocks before the packed warps. In
+// rectangular form the slot lane does one lane of the rectangular two-lane
+// kernel (fused_rect_arc), and the scans sum the diagonal parts per bus and
+// aR and the signed aI per group.
 //
 // With two roles (branch_occupancy 2 in this mode) each packed warp of buses
 // is taken by two warps, one writing the rows and the Jacobian (and the
 // gradient zeros), the other the Hessian; both evaluate the shared
 // trigonometry, so the dependent chain of each is shorter at the cost of
 // that duplicated work.
-template <bool CONS, bool JAC, bool HESS, bool ONE>
+template <bool CONS, bool JAC, bool HESS, bool ONE, bool RECT = false>
 __device__ void fused_bus_warp(const KParams &P, const int64_t w, const bool grad_here)
 {
     const DevArrays &d = P.d;
@@ -1156,7 +1237,7 @@ __device__ void fused_bus_warp(const KParams &P, const int64_t w, const bool gra
     int jb = 0, gfirst = -1;
     double2 Yo = make_double2(0.0, 0.0), Yx = make_double2(0.0, 0.0), Yf = make_double2(0.0, 0.0);
     double2 gb = make_double2(0.0, 0.0);
-    double r2 = 0.0;
+    double r2 = 0.0, tno = 0.0, tnf = 0.0;
     if (has) {
         br = __ldg(d.br + kb);
         if (JAC) {
@@ -1169,6 +1250,11 @@ __device__ void fused_bus_warp(const KParams &P, const int64_t w, const bool gra
             Yf = __ldg((e ? d.y_ft : d.y_tf) + kb);  // the far end's
         if (CONS)
             r2 = __ldg(d.rate2 + kb);
+        if (RECT) {  // this lane's angle row limit and the far lane's
+            const double2 tb = __ldg(d.tanb + kb);  // tan(angmax), tan(angmin)
+            tno = e ? tb.y : tb.x;
+            tnf = e ? tb.x : tb.y;
+        }
     }
     const int i = ld.y;
     if (valid) {
@@ -1206,7 +1292,7 @@ __device__ void fused_bus_warp(const KParams &P, const int64_t w, const bool gra
             qo = __ldg(xs + iq + arc);
         }
     }
-    double mP = 0, mQ = 0, lth = 0, fP = 0, fQ = 0;
+    double mP = 0, mQ = 0, lth = 0, fP = 0, fQ = 0, ma = 0, fa = 0;
     if (HESS && has) {
         const double *L = P.lam + I.c0 + (T + rk);
         mP = __ldg(L + (e ? 2 * nlT : 0));
@@ -1214,13 +1300,19 @@ __device__ void fused_bus_warp(const KParams &P, const int64_t w, const bool gra
         lth = __ldg(L + ((e ? 6 : 5) * nlT + 2 * nbT));
         fP = __ldg(L + (e ? 0 : 2 * nlT));  // the far end's flow rows
         fQ = __ldg(L + (e ? nlT : 3 * nlT));
+        if (RECT) {  // the angle rows: upper (from-end lane's), lower (to-end lane's)
+            ma = __ldg(L + (e ? 7 * nlT + 2 * nbT : 4 * nlT));
+            fa = __ldg(L + (e ? 4 * nlT : 7 * nlT + 2 * nbT));
+        }
     }
-    double lP = 0.0, lQ = 0.0, Pd = 0.0, Qd = 0.0, pg1 = 0.0, qg1 = 0.0;
+    double lP = 0.0, lQ = 0.0, lV = 0.0, Pd = 0.0, Qd = 0.0, pg1 = 0.0, qg1 = 0.0;
     if (valid && tail) {  // the bus's own dynamic scalars
         if (HESS) {
             const double *L = P.lam + I.c0 + (T + 5 * nlT + nb * t + i);
             lP = __ldg(L);
             lQ = __ldg(L + nbT);
+            if (RECT)  // the magnitude row
+                lV = __ldg(L + (3 * nlT + 2 * nbT));
         }
         if (CONS) {
             Pd = __ldg(d.Pd + I.pd0 + (nb * t + i));
@@ -1234,7 +1326,11 @@ __device__ void fused_bus_warp(const KParams &P, const int64_t w, const bool gra
 
     // the arc end: as one lane of the two-lane branch kernel
     double h1 = 0.0, h2 = 0.0, h3 = 0.0, h4 = 0.0;  // the slot's Hessian parts (the scratch record's)
-    if (has) {
+    if constexpr (RECT) {
+        if (has)
+            fused_rect_arc<CONS, JAC, HESS>(P, I, e, k, t, own, far, br, jb, Yo, Yx, Yf, r2, tno, tnf, vao, vax, vo,
+                                            vx, po, qo, mP, mQ, ma, lth, fP, fQ, fa, grad_here, h1, h2, h3);
+    } else if (has) {
         const double dlt = vao - vax;  // this end's angle
         double sn, cs_;
         sincos_tab(dlt, d.trig, &sn, &cs_);
@@ -1305,7 +1401,9 @@ __device__ void fused_bus_warp(const KParams &P, const int64_t w, const bool gra
     const unsigned bheads = __ballot_sync(full, (fl & PK_HEAD) || !valid);
     const int bhead = 31 - __clz(bheads & upto);
     const int bmax = __reduce_max_sync(full, (unsigned)(lane - bhead + 1));
-    double tp = po, tq = qo, taa = h1, tma = h2, tmm = h3;
+    // bus sums: p, q; polar: the (va, va), (vm, va), (vm, vm) parts;
+    // rectangular: the diagonal part
+    double tp = po, tq = qo, taa = h1, tma = h2, tmm = RECT ? h1 : h3;
     for (int dd = 1; dd < bmax; dd <<= 1) {
         const bool in = lane - dd >= bhead;
         if (CONS) {
@@ -1315,14 +1413,17 @@ __device__ void fused_bus_warp(const KParams &P, const int64_t w, const bool gra
                 tq += yq;
             }
         }
-        if (HESS) {
+        if (HESS && !RECT) {
             const double ya = __shfl_up_sync(full, taa, dd), ym = __shfl_up_sync(full, tma, dd);
-            const double yv = __shfl_up_sync(full, tmm, dd);
             if (in) {
                 taa += ya;
                 tma += ym;
-                tmm += yv;
             }
+        }
+        if (HESS) {
+            const double yv = __shfl_up_sync(full, tmm, dd);
+            if (in)
+                tmm += yv;
         }
     }
     const int nd = b.w & 0xffff, nlt = b.w >> 16;
@@ -1330,7 +1431,8 @@ __device__ void fused_bus_warp(const KParams &P, const int64_t w, const bool gra
     double *Hvm = P.hess + I.h0 + (hva * T + hvm * t + b.z);
     double *Hva = P.hess + I.h0 + (hva * t + b.y);
     if (HESS) {
-        double gaa = h1, gma = h2, gmm = h4;
+        // group sums: polar (va, va), (vm, va), (vm, vm) parts; rectangular aR, signed aI
+        double gaa = RECT ? h2 : h1, gma = RECT ? h3 : h2, gmm = h4;
         const unsigned multi = __ballot_sync(full, has && !(fl & PK_GTAIL));
         if (multi) {  // some group of parallel arcs has more than one slot
             const unsigned gtails = __ballot_sync(full, (fl & PK_GTAIL) || !valid);
@@ -1338,51 +1440,72 @@ __device__ void fused_bus_warp(const KParams &P, const int64_t w, const bool gra
             const int gmax = __reduce_max_sync(full, (unsigned)(lane - ghead + 1));
             for (int dd = 1; dd < gmax; dd <<= 1) {
                 const double ya = __shfl_up_sync(full, gaa, dd), ym = __shfl_up_sync(full, gma, dd);
-                const double yv = __shfl_up_sync(full, gmm, dd);
+                const double yv = RECT ? 0.0 : __shfl_up_sync(full, gmm, dd);
                 if (lane - dd >= ghead) {
                     gaa += ya;
                     gma += ym;
-                    gmm += yv;
+                    if (!RECT)
+                        gmm += yv;
                 }
             }
         }
         if (has && (fl & PK_GTAIL)) {  // the group's off-diagonal entries
             const int grp = ld.w;
-            Hvm[grp < nlt ? grp : grp + 1] = neg(gma);  // (vm_i, va_j)
-            if (fl & PK_LOWER) {
-                Hva[grp] = neg(gaa);      // (va_i, va_j), j < i
-                Hvm[nd + 1 + grp] = gmm;  // (vm_i, vm_j), j < i
+            if (RECT) {
+                Hvm[grp] = gma;  // (vi_i, vr_j)
+                if (fl & PK_LOWER) {
+                    Hva[grp] = gaa;       // (vr_i, vr_j), j < i
+                    Hvm[nd + grp] = gaa;  // (vi_i, vi_j), j < i
+                }
+            } else {
+                Hvm[grp < nlt ? grp : grp + 1] = neg(gma);  // (vm_i, va_j)
+                if (fl & PK_LOWER) {
+                    Hva[grp] = neg(gaa);      // (va_i, va_j), j < i
+                    Hvm[nd + 1 + grp] = gmm;  // (vm_i, vm_j), j < i
+                }
             }
         }
     }
     if (!(valid && tail))
         return;
-    // the bus's last lane: its own terms, as in the bus phase
+    // the bus's last lane: its own terms, as in the bus phase (rectangular:
+    // vr, vi in the places of va, vm, and the magnitude row)
     const int nsl = a.y - a.x, ng_here = a.w - a.z;
     if (P.want_grad && grad_here) {
         P.grad[I.x0 + iva + i] = 0.0;
         P.grad[I.x0 + ivm + i] = 0.0;
     }
-    if (i == I.ref) {
+    if (i == I.ref) {  // va_ref, or vi_ref
         if (CONS)
-            P.c[I.c0 + t] = vao;
+            P.c[I.c0 + t] = RECT ? vo : vao;
         if (JAC)
             P.jac[I.j0 + t] = 1.0;
     }
     if (JAC) {
         const int jP = (int)I.jP;
-        double *JP = P.jac + I.j0 + (T + 22 * nlT + jP * t + b.x);
+        double *JP = P.jac + I.j0 + (T + (RECT ? 24 : 22) * nlT + jP * t + b.x);
         double *JQ = JP + jP * T;
         const double v2m = twice(vo);
-        JP[0] = gb.x * v2m;
-        JQ[0] = neg(gb.y * v2m);
-        for (int g = 1; g <= ng_here; g++) {
+        if constexpr (RECT) {  // d|V|^2 = (2 vr, 2 vi); the magnitude row
+            const double r2m = twice(vao);
+            JP[0] = gb.x * r2m;
+            JP[1] = gb.x * v2m;
+            JQ[0] = neg(gb.y * r2m);
+            JQ[1] = neg(gb.y * v2m);
+            double *JV = P.jac + I.j0 + (T + 32 * nlT + 2 * jP * T + 2 * (nb * t + i));
+            JV[0] = r2m;
+            JV[1] = v2m;
+        } else {
+            JP[0] = gb.x * v2m;
+            JQ[0] = neg(gb.y * v2m);
+        }
+        for (int g = RECT ? 2 : 1; g <= ng_here + (RECT ? 1 : 0); g++) {
             JP[g] = -1.0;
             JQ[g] = -1.0;
         }
     }
     if (CONS) {
-        const double vm2 = vo * vo;
+        const double vm2 = RECT ? fma(vao, vao, vo * vo) : vo * vo;  // |V|^2
         double Pb = fma(gb.x, vm2, Pd), Qb = fma(neg(gb.y), vm2, Qd);
         if (gfirst >= 0) {
             Pb -= pg1;
@@ -1396,8 +1519,14 @@ __device__ void fused_bus_warp(const KParams &P, const int64_t w, const bool gra
         double *c = P.c + I.c0 + (T + 5 * nlT + nb * t + i);
         c[0] = Pb + tp;
         c[nbT] = Qb + tq;
+        if (RECT)
+            c[3 * nlT + 2 * nbT] = vm2;  // the magnitude row
     }
-    if (HESS) {
+    if (HESS && RECT) {  // diagonals (vr_i, vr_i) and (vi_i, vi_i)
+        const double dmm = twice(fma(gb.x, lP, fma(neg(gb.y), lQ, lV))) + tmm;
+        Hva[nlt] = dmm;
+        Hvm[nd + nlt] = dmm;
+    } else if (HESS) {
         const double dmm = twice(fma(gb.x, lP, neg(gb.y * lQ))) + tmm;
         if (nsl > 0) {
             Hva[nlt] = taa;
@@ -1423,13 +1552,13 @@ __global__ void __launch_bounds__(kBusBlockMax) bus_kernel(const KParams P)
                 if constexpr (HESS && (CONS || JAC)) {
                     if (P.fuse_roles) {  // even warps: rows and Jacobian; odd warps: Hessian
                         if (wr & 1)
-                            fused_bus_warp<false, false, true, ONE>(P, wr >> 1, false);
+                            fused_bus_warp<false, false, true, ONE, RECT>(P, wr >> 1, false);
                         else
-                            fused_bus_warp<CONS, JAC, false, ONE>(P, wr >> 1, true);
+                            fused_bus_warp<CONS, JAC, false, ONE, RECT>(P, wr >> 1, true);
                         return;
                     }
                 }
-                fused_bus_warp<CONS, JAC, HESS, ONE>(P, wr, true);
+                fused_bus_warp<CONS, JAC, HESS, ONE, RECT>(P, wr, true);
             } else
                 heavy_bus_warp<CONS, JAC, HESS, ONE, RECT>(P);
             return;
@@ -2352,6 +2481,9 @@ cudaError_t dispatch(const KParams &P, bool one, bool occ, bool occ2, bool rect,
     if (fused) {  // one kernel: generator items, then the packed warps (gu counts both)
         if (!run_bus)
             return e;
+        if (rect)
+            return one ? launch_pdl(bus_kernel<C, J, H, true, true, false, true, true>, gu, bu, s, P)
+                       : launch_pdl(bus_kernel<C, J, H, false, true, false, true, true>, gu, bu, s, P);
         return one ? launch_pdl(bus_kernel<C, J, H, true, false, false, true, true>, gu, bu, s, P)
                    : launch_pdl(bus_kernel<C, J, H, false, false, false, true, true>, gu, bu, s, P);
     }
@@ -2449,7 +2581,7 @@ int launch_all(Model &M, const EvalArgs &a, unsigned what, cudaStream_t s, int p
     // light buses a thread each in the first blocks, heavy buses a warp each
     // in the blocks after them; elsewhere buses in id order
     const bool splitb = L.bus_order >= 2 && M.split_ok && (phases & 2);
-    // bus_order 3: the fused evaluation where it applies (polar, no storage,
+    // bus_order 3: the fused evaluation where it applies (no storage,
     // at most 32 arc slots per bus), one kernel per evaluation (launched
     // with the bus phase; the branch phase alone launches nothing)
     const bool fused = L.bus_order == 3 && M.fuse_ok;

@@ -176,7 +176,7 @@ struct Model {
     int64_t nlight_items = 0, nheavy_items = 0;  // split bus phase items
     bool split_ok = false;        // the split bus phase applies (no storage)
     int64_t npack_items = 0;      // fused evaluation: packed warps x periods, all instances
-    bool fuse_ok = false;         // the fused evaluation applies (polar, no storage, <= 32 slots per bus)
+    bool fuse_ok = false;         // the fused evaluation applies (no storage, <= 32 slots per bus)
     int64_t nload_total = 0;      // sum over instances of nload * nperiod
     int32_t max_part = 0;         // capacity of obj_part
     int device = 0, num_sms = 148;

@@ -680,7 +680,7 @@ int build_model(const opf_network *nets, int32_t ninst, const opf_batch_opts *op
     M->nheavy_items = heavy_items.back();
     M->split_ok = !stor;
     M->npack_items = pack_items.back();
-    M->fuse_ok = !rect && !stor && fits32;
+    M->fuse_ok = !stor && fits32;
     M->narc_slots = so;
     M->max_part = 16 * M->num_sms;
     M->launch = opf_launch{128, 128, 0, 0, 0, 0};

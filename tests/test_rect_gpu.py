@@ -148,6 +148,33 @@ def test_rect_two_threads_per_branch(torch, oracle_mod, which):
             check_against_oracle(O, run_all(torch, M, x, lam, sigma, launch), x, lam, sigma, f"pt{k} bb{bb} ")
 
 
+@pytest.mark.parametrize("which", ["case30g", "isolated", "batch_links", "case10k", "mp30", "hub"])
+def test_rect_fused_evaluation(torch, oracle_mod, which):
+    """bus_order 3 in rectangular form: the one-kernel evaluation (whole buses
+    packed into warps, each slot lane one lane of the rectangular two-lane
+    kernel with the far end's aR and aI parts formed in place, per-bus sums
+    of the diagonal parts and per-group sums of aR and aI by segmented
+    scans); every output against the oracle, one or two warps per packed
+    warp; a hub beyond 32 slots runs the split bus phase instead."""
+    from tests.test_hub_gpu import hub_grid
+    from tests.test_parity_gpu import isolated_bus_grid
+    g = {"case30g": lambda: synth.case30(general=True),
+         "isolated": isolated_bus_grid,
+         "batch_links": lambda: synth.contingencies(synth.case30(general=True), 6, seed=3),
+         "case10k": lambda: synth.case10k(),
+         "mp30": lambda: synth.multi_period(synth.case30(general=True), 4, seed=8, ramp_ratio=0.2),
+         "hub": hub_grid}[which]()
+    link = 0.2 if which == "batch_links" else 0.0
+    M, O = both(torch, oracle_mod, g, link=link, form="rect")
+    for k, (x, lam) in enumerate(rpoints(g, M.m, 2, seed=41)):
+        for bu, cu, occ in ((32, 0, 0), (128, 2, 0), (64, 0, 2)):
+            launch = dict(branch_block=128, bus_block=bu, branch_ctas_per_sm=0, bus_ctas_per_sm=cu, bus_order=3,
+                          branch_occupancy=occ)
+            sigma = 0.0 if k else 0.9
+            check_against_oracle(O, run_all(torch, M, x, lam, sigma, launch), x, lam, sigma,
+                                 f"pt{k} bu{bu} occ{occ} ")
+
+
 def test_rect_rejects_wide_angle_limits(torch):
     g = synth.case30()
     g = g.copy(br_angmax=np.where(np.arange(g.nbranch) == 3, np.pi / 2, g.br_angmax))
