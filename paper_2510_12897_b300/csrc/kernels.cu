@@ -2149,6 +2149,37 @@ __global__ void __launch_bounds__(512) jt_branch_kernel(const KParams P)
     }
 }
 
+// J^T v at one (instance, period, generator): its balance, ramp, linking
+// and reserve rows
+template <bool RECT, bool AL>
+__device__ __forceinline__ void jt_gen_item(const KParams &P, const InstDev &I, int s, int t, int g)
+{
+    const DevArrays &d = P.d;
+    const int nl = I.nl, nb = I.nb, ng = I.ng, T = I.T;
+    const int nbT = nb * T, ngT = ng * T, nlT = nl * T;
+    const int64_t V = I.c0;  // the vector v, indexed like the rows
+    double *o = P.grad + I.x0;
+    const int bus = __ldg(d.gen_busid + I.gen0 + g);
+    double vpg = neg(vrow<AL>(P, V + (T + 5 * nlT + nb * t + bus)));
+    const double vqg = neg(vrow<AL>(P, V + (T + 5 * nlT + nbT + nb * t + bus)));
+    if (I.ramp) {  // rows pg_t - pg_{t-1}, t = 1..T-1
+        const int rb = T + (RECT ? 8 * nlT + 3 * nbT : 7 * nlT + 2 * nbT);
+        if (t >= 1)
+            vpg += vrow<AL>(P, V + (rb + g + ng * (t - 1)));
+        if (t + 1 <= T - 1)
+            vpg -= vrow<AL>(P, V + (rb + g + ng * t));
+    }
+    if (I.link_c >= 0)  // rows pg_s - pg_0 of instance s >= 1
+        vpg += vrow<AL>(P, I.link_c + g);
+    if (I.res_c >= 0)  // the instance's reserve row of this period
+        vpg += vrow<AL>(P, I.res_c + t);
+    if (P.link && s == 0)  // instance 0 appears in every linking row
+        for (int q = 1; q < P.ninst; q++)
+            vpg -= vrow<AL>(P, P.link_c0 + g + (int64_t)ng * (q - 1));
+    o[2 * nbT + ng * t + g] = vpg;
+    o[2 * nbT + ngT + ng * t + g] = vqg;
+}
+
 template <bool ONE, bool RECT = false, bool STOR = false, bool AL = false>
 __global__ void __launch_bounds__(256) jt_bus_kernel(const KParams P)
 {
@@ -2239,27 +2270,176 @@ __global__ void __launch_bounds__(256) jt_bus_kernel(const KParams P)
             o[nb * t + i] = dva;
             o[nbT + nb * t + i] = dvm;
         } else {
-            const int g = e;
-            const int bus = __ldg(d.gen_busid + I.gen0 + g);
-            double vpg = neg(vrow<AL>(P, V + (T + 5 * nlT + nb * t + bus)));
-            const double vqg = neg(vrow<AL>(P, V + (T + 5 * nlT + nbT + nb * t + bus)));
-            if (I.ramp) {  // rows pg_t - pg_{t-1}, t = 1..T-1
-                const int rb = T + (RECT ? 8 * nlT + 3 * nbT : 7 * nlT + 2 * nbT);
-                if (t >= 1)
-                    vpg += vrow<AL>(P, V + (rb + g + ng * (t - 1)));
-                if (t + 1 <= T - 1)
-                    vpg -= vrow<AL>(P, V + (rb + g + ng * t));
-            }
-            if (I.link_c >= 0)  // rows pg_s - pg_0 of instance s >= 1
-                vpg += vrow<AL>(P, I.link_c + g);
-            if (I.res_c >= 0)  // the instance's reserve row of this period
-                vpg += vrow<AL>(P, I.res_c + t);
-            if (P.link && s == 0)  // instance 0 appears in every linking row
-                for (int q = 1; q < P.ninst; q++)
-                    vpg -= vrow<AL>(P, P.link_c0 + g + (int64_t)ng * (q - 1));
-            o[2 * nbT + ng * t + g] = vpg;
-            o[2 * nbT + ngT + ng * t + g] = vqg;
+            jt_gen_item<RECT, AL>(P, I, s, t, e);
         }
+    }
+}
+
+// Fused J^T v (bus_order 3, models without storage): one kernel, the
+// packed warps of the fused evaluation. Each slot lane takes its arc end: the
+// p and q entries of its arc completely (flow row, thermal row, the balance
+// rows of its bus, whose v it reads) and the va, vm (vr, vi) parts of its
+// bus's entries from every row of its branch (its own end's flow rows, the
+// far end's, the angle rows). The parts are summed per bus by a segmented
+// scan and the bus's last lane adds the reference and balance-row terms.
+// Generator items run in the blocks before the packed warps.
+template <bool ONE, bool RECT, bool AL>
+__device__ void fused_jt_warp(const KParams &P, const int64_t w)
+{
+    const DevArrays &d = P.d;
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    if (w >= P.npack_items) {
+        cudaGridDependencySynchronize();
+        cudaTriggerProgrammaticLaunchCompletion();
+        return;
+    }
+    int s = 0, t = 0, wl = 0;
+    if (ONE) {
+        split((int)w, P.inst0.npack, P.inst0.T, t, wl);
+    } else {
+        s = find_inst(d.pack_items, P.ninst, w);
+        const InstDev *Ip = d.inst + s;
+        split((int)(w - __ldg(d.pack_items + s)), __ldg(&Ip->npack), __ldg(&Ip->T), t, wl);
+    }
+    const InstDev I = inst_of<ONE>(P, s);
+    const int4 ld = __ldg(d.pack + (((int64_t)I.pack0 + wl) << 5) + lane);  // (arc, bus, flags, group)
+    const int fl = ld.z;
+    const bool valid = (fl & PK_VALID) != 0, tail = (fl & PK_TAIL) != 0;
+    const bool has = ld.x >= 0;
+    const int nl = I.nl;
+    const int e = has && ld.x >= nl ? 1 : 0;  // 0: from-end, 1: to-end
+    const int k = has ? ld.x - e * nl : 0;
+    const int kb = I.br0 + k;
+    int4 br = make_int4(0, 0, 0, 0);
+    double2 Yo = make_double2(0.0, 0.0), Yx = make_double2(0.0, 0.0), Yf = make_double2(0.0, 0.0);
+    double2 gb = make_double2(0.0, 0.0);
+    double tno = 0.0, tnf = 0.0;
+    if (has) {
+        br = __ldg(d.br + kb);
+        Yo = __ldg((e ? d.y_tt : d.y_ff) + kb);
+        Yx = __ldg((e ? d.y_tf : d.y_ft) + kb);
+        Yf = __ldg((e ? d.y_ft : d.y_tf) + kb);
+        if (RECT) {
+            const double2 tb = __ldg(d.tanb + kb);
+            tno = e ? tb.y : tb.x;
+            tnf = e ? tb.x : tb.y;
+        }
+    }
+    const int i = ld.y;
+    if (valid && tail)
+        gb = __ldg(d.gsbs + I.bus0 + i);
+    cudaGridDependencySynchronize();
+    cudaTriggerProgrammaticLaunchCompletion();  // the next kernel may launch now
+
+    const int nb = I.nb, ng = I.ng, T = I.T;
+    const int nbT = nb * T, ngT = ng * T, nlT = nl * T, na = 2 * nl;
+    const int rk = k + nl * t;
+    const int own = has ? (e ? br.y : br.x) : i, far = e ? br.x : br.y;
+    const double *__restrict__ xs = P.x + I.x0;
+    const int iva = nb * t, ivm = nbT + nb * t;
+    const int ip = 2 * nbT + 2 * ngT + na * t, iq = ip + na * T;
+    const int arc = e ? nl + k : k;
+    double *o = P.grad + I.x0;  // P.grad carries `out`
+    double vao = 0.0, vo = 0.0, bP = 0.0, bQ = 0.0;
+    const int64_t VB = I.c0 + (T + 5 * nlT + nb * t);  // balance rows, period t
+    if (valid) {
+        vao = __ldg(xs + iva + own);
+        vo = __ldg(xs + ivm + own);
+        bP = vrow<AL>(P, VB + i);
+        bQ = vrow<AL>(P, VB + nbT + i);
+    }
+    double dA = 0.0, dM = 0.0;  // this slot's va and vm (vr and vi) parts
+    if (has) {
+        const double vax = __ldg(xs + iva + far), vx = __ldg(xs + ivm + far);
+        const double po = __ldg(xs + ip + arc), qo = __ldg(xs + iq + arc);
+        const int64_t V = I.c0 + (T + rk);  // the vector v, indexed like the rows
+        const double mP = vrow<AL>(P, V + (e ? 2 * nlT : 0)), mQ = vrow<AL>(P, V + (e ? 3 * nlT : nlT));
+        const double fP = vrow<AL>(P, V + (e ? 0 : 2 * nlT)), fQ = vrow<AL>(P, V + (e ? nlT : 3 * nlT));
+        const double th = vrow<AL>(P, V + ((e ? 6 : 5) * nlT + 2 * nbT));
+        // own variables: flow row, thermal row, balance row of the arc's bus
+        o[ip + arc] = fma(twice(po), th, mP + bP);
+        o[iq + arc] = fma(twice(qo), th, mQ + bQ);
+        if constexpr (RECT) {
+            // v^T g over the branch's rows: (De/2)|V_own|^2 + ... + aR wR + aI wI
+            const double ma = vrow<AL>(P, V + (e ? 7 * nlT + 2 * nbT : 4 * nlT));
+            const double fa = vrow<AL>(P, V + (e ? 4 * nlT : 7 * nlT + 2 * nbT));
+            const double Re = neg(fma(mP, Yx.x, fma(neg(mQ), Yx.y, ma * tno)));
+            const double Ie = flip(fma(mP, Yx.y, mQ * Yx.x), !e) + ma;
+            const double Rf = neg(fma(fP, Yf.x, fma(neg(fQ), Yf.y, fa * tnf)));
+            const double If = flip(fma(fP, Yf.y, fQ * Yf.x), e) + fa;
+            const double aR = e ? Rf + Re : Re + Rf;  // from-end part first
+            const double sI = flip(e ? If + Ie : Ie + If, e);
+            const double De = neg(twice(fma(mP, Yo.x, neg(mQ * Yo.y))));
+            dA = fma(De, vao, fma(aR, vax, neg(sI * vx)));
+            dM = fma(De, vo, fma(aR, vx, sI * vax));
+        } else {
+            const double va_ = vrow<AL>(P, V + 4 * nlT);  // the angle row
+            double sn, cs_;
+            sincos_tab(vao - vax, d.trig, &sn, &cs_);
+            const double vft = vo * vx;
+            const double A = fma(Yx.x, cs_, Yx.y * sn), B = fma(Yx.x, sn, neg(Yx.y * cs_));
+            const double Af = fma(Yf.x, cs_, neg(Yf.y * sn)), Bf = neg(fma(Yf.x, sn, Yf.y * cs_));
+            const double dva = fma(mP, B, fma(neg(mQ), A, fma(neg(fP), Bf, fQ * Af)));
+            dA = fma(vft, dva, flip(va_, e));
+            dM = fma(neg(mP), fma(Yo.x, twice(vo), vx * A), fma(mQ, fma(Yo.y, twice(vo), neg(vx * B)),
+                                                                  neg(vx * fma(fP, Af, fQ * Bf))));
+        }
+    }
+    // per-bus sums of the slots' parts
+    const unsigned upto = (2u << lane) - 1u;
+    const unsigned bheads = __ballot_sync(full, (fl & PK_HEAD) || !valid);
+    const int bhead = 31 - __clz(bheads & upto);
+    const int bmax = __reduce_max_sync(full, (unsigned)(lane - bhead + 1));
+    for (int dd = 1; dd < bmax; dd <<= 1) {
+        const double ya = __shfl_up_sync(full, dA, dd), ym = __shfl_up_sync(full, dM, dd);
+        if (lane - dd >= bhead) {
+            dA += ya;
+            dM += ym;
+        }
+    }
+    if (!(valid && tail))
+        return;
+    const double vref = i == I.ref ? vrow<AL>(P, I.c0 + t) : 0.0;
+    if constexpr (RECT) {  // vr, vi: 2 V (gs vP - bs vQ + vV); the reference row is vi_ref
+        const double vV = vrow<AL>(P, I.c0 + (T + 8 * nlT + 2 * nbT + nb * t + i));
+        const double kk = twice(fma(gb.x, bP, fma(neg(gb.y), bQ, vV)));
+        o[iva + i] = fma(vao, kk, dA);
+        o[ivm + i] = fma(vo, kk, dM) + vref;
+    } else {
+        o[iva + i] = dA + vref;
+        o[ivm + i] = fma(twice(vo), fma(gb.x, bP, neg(gb.y * bQ)), dM);  // 2 vm (gs vP - bs vQ)
+    }
+}
+
+template <bool ONE, bool RECT, bool AL>
+__global__ void __launch_bounds__(256) jt_fused_kernel(const KParams P)
+{
+    if ((int)blockIdx.x >= P.split_tblocks) {  // the packed warps
+        fused_jt_warp<ONE, RECT, AL>(P, (int64_t)(blockIdx.x - P.split_tblocks) * (blockDim.x >> 5) +
+                                            (threadIdx.x >> 5));
+        return;
+    }
+    cudaGridDependencySynchronize();
+    cudaTriggerProgrammaticLaunchCompletion();  // the next kernel may launch now
+    if (AL && P.bp && blockIdx.x == 0 && threadIdx.x == 0) {  // the next Adam step's bias corrections
+        P.bp[0] *= 0.9;
+        P.bp[1] *= 0.999;
+        P.bp[2] = 1.0 - P.bp[0];
+        P.bp[3] = 1.0 - P.bp[1];
+    }
+    const DevArrays &d = P.d;
+    for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < P.ngen_items;
+         it += (int64_t)P.split_tblocks * blockDim.x) {
+        int s, t, g;
+        if (ONE) {
+            s = 0;
+            split((int)it, P.inst0.ng, P.inst0.T, t, g);
+        } else {
+            s = find_inst(d.gen_items, P.ninst, it);
+            split((int)(it - __ldg(d.gen_items + s)), __ldg(&d.inst[s].ng), __ldg(&d.inst[s].T), t, g);
+        }
+        jt_gen_item<RECT, AL>(P, inst_of<ONE>(P, s), s, t, g);
     }
 }
 
@@ -2689,7 +2869,19 @@ int jtprod_launch(Model &M, const KParams &P, cudaStream_t s)
     const int gu = grid_for(M.nbus_items + M.ngen_items, 128, 0, M.num_sms, 0);
     const bool one = M.ninst == 1;
     cudaError_t e = cudaSuccess;
-    if (M.rect) {
+    if (M.launch.bus_order == 3 && M.fuse_ok) {  // the fused evaluation's layout: one kernel
+        const int bu = M.launch.bus_block > kBusBlockMax ? kBusBlockMax : M.launch.bus_block;
+        KParams Q = P;
+        Q.split_tblocks = grid_for(M.ngen_items, bu, M.launch.bus_ctas_per_sm, M.num_sms, 0);
+        Q.npack_items = M.npack_items;
+        const int grid = Q.split_tblocks + (int)((M.npack_items + bu / 32 - 1) / (bu / 32));
+        if (M.rect)
+            e = one ? launch_pdl(jt_fused_kernel<true, true, AL>, grid, bu, s, Q)
+                    : launch_pdl(jt_fused_kernel<false, true, AL>, grid, bu, s, Q);
+        else
+            e = one ? launch_pdl(jt_fused_kernel<true, false, AL>, grid, bu, s, Q)
+                    : launch_pdl(jt_fused_kernel<false, false, AL>, grid, bu, s, Q);
+    } else if (M.rect) {
         if (M.nbr_items > 0)
             e = one ? launch_pdl(jt_branch_kernel<true, true, AL>, gb, 128, s, P)
                     : launch_pdl(jt_branch_kernel<false, true, AL>, gb, 128, s, P);

@@ -19,10 +19,12 @@ def torch():
     return t
 
 
+@pytest.mark.parametrize("fused", [False, True])
 @pytest.mark.parametrize("case", ["case30g", "mp30", "rect30g", "stor30"])
-def test_al_iterations_match_oracle(torch, oracle_mod, case):
+def test_al_iterations_match_oracle(torch, oracle_mod, case, fused):
     """Twenty Adam steps around one multiplier update from the flat start
-    with random multipliers: iterates, multipliers and statistics equal the
+    with random multipliers, with the two-phase kernels and with the fused
+    evaluation and J^T mu: iterates, multipliers and statistics equal the
     oracle's. Adam divides by sqrt(v) + 1e-8, so a gradient entry that is
     rounding noise in both implementations can move x by up to lr x
     noise / 1e-8 per step: the bound on |x_gpu - x_oracle| is 1e-7 after 20
@@ -34,6 +36,8 @@ def test_al_iterations_match_oracle(torch, oracle_mod, case):
         g = synth.with_storage(g)
     form = "rect" if case == "rect30g" else "polar"  # the loop on the rectangular form's callbacks
     M = opf.Model(g, form=form)
+    if fused:  # the one-kernel evaluation and J^T mu (storage models keep two phases)
+        M.set_launch(branch_block=128, bus_block=64, branch_ctas_per_sm=0, bus_ctas_per_sm=0, bus_order=3)
     O = oracle_mod.Oracle(g, form=form)
     dev = torch.device("cuda")
     x = torch.empty(M.n, dtype=torch.float64, device=dev)

@@ -577,3 +577,40 @@ def test_fused_separate_callbacks(torch, oracle_mod, occ):
     M.eval_phases(2, dx, c=c2)  # the bus phase: the whole evaluation
     torch.cuda.synchronize()
     np.testing.assert_array_equal(host(c2), fused["c"])
+
+
+@pytest.mark.parametrize("which", ["case30g", "isolated", "batch_links", "reserve", "mp30", "case10k", "rect30g",
+                                   "rect_mp30"])
+def test_fused_jtprod(torch, oracle_mod, which):
+    """J^T v with the fused layout (bus_order 3): one kernel whose slot lanes
+    give their arc's p, q entries and their bus's va, vm (vr, vi) parts from
+    every row of the branch, summed by a segmented scan; against the
+    oracle's sparse Jacobian transposed, both forms, single, batch with
+    linking or reserve rows, multiple periods."""
+    import scipy.sparse as sp
+    g = {"case30g": lambda: synth.case30(general=True),
+         "isolated": isolated_bus_grid,
+         "batch_links": lambda: synth.contingencies(synth.case30(general=True), 6, seed=3),
+         "reserve": lambda: synth.contingencies(synth.case30(general=True), 9, seed=7),
+         "mp30": lambda: synth.multi_period(synth.case30(general=True), 4, seed=8, ramp_ratio=0.2),
+         "case10k": lambda: synth.case10k(),
+         "rect30g": lambda: synth.case30(general=True),
+         "rect_mp30": lambda: synth.multi_period(synth.case30(general=True), 3, seed=8, ramp_ratio=0.2)}[which]()
+    form = "rect" if which.startswith("rect") else "polar"
+    link = 0.2 if which == "batch_links" else 0.0
+    opts = dict(link_ratios=[0.0] + [0.05 * k for k in range(1, 10)], reserve=0.1) if which == "reserve" else {}
+    M, O = both(torch, oracle_mod, g, link=link, form=form, **opts)
+    rng = np.random.default_rng(42)
+    gl = g if isinstance(g, list) else [g]
+    x = np.concatenate([synth.random_point(h, rng, form=form) for h in gl])
+    v = rng.standard_normal(M.m)
+    r, c = O.jac_pattern()
+    jv, js = O.jac(x, with_scale=True)
+    ref = sp.coo_matrix((jv, (r, c)), shape=(O.m, O.n)).T @ v
+    scale = sp.coo_matrix((js, (r, c)), shape=(O.m, O.n)).T @ np.abs(v)
+    for bu in (32, 128):
+        M.set_launch(**dict(FUSED, bus_block=bu))
+        out = torch.full((M.n,), np.nan, dtype=torch.float64, device="cuda")
+        M.eval_jtprod(dev(torch, x), dev(torch, v), out)
+        torch.cuda.synchronize()
+        close(f"jtprod bu{bu}", host(out), ref, scale)
