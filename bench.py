@@ -604,7 +604,7 @@ def main():
             "al_inner_iteration_us": al_us,
             "warm_cache": {"ms_per_step": warm_ms, "evals_per_s": 1000.0 / warm_ms,
                            "note": "one buffer set, data resident in L2 (the solver-loop case)"},
-            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 2 * K, "clocks": clocks,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": (1 if fused else 2) * K, "clocks": clocks,
             "batched": batched, "warm_start": warm_start, "rect": rect,
         }
         print(json.dumps(line), flush=True)

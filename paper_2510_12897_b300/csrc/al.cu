@@ -170,7 +170,7 @@ __global__ void al_adam_kernel(double *x, const double *grad, const double *u, c
     const double k1 = lr / bp[2], k2 = 1.0 / bp[3];
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
          j += (int64_t)gridDim.x * blockDim.x) {
-        const double G = grad[j] + u[j];
+        const double G = grad ? grad[j] + u[j] : u[j];  // u alone: the whole gradient
         const double a = fma(b1, m1[j], (1.0 - b1) * G);
         const double b = fma(b2, m2[j], (1.0 - b2) * G * G);
         m1[j] = a;
@@ -307,14 +307,22 @@ namespace {
 // from g where the product reads it (and the step count advanced); Adam
 int al_inner(opf_al *al, double *d_x, const double *d_lambda, cudaStream_t s)
 {
-    EvalArgs e{d_x, nullptr, 1.0, nullptr, al->grad, al->c, nullptr, nullptr};
-    int rc = launch_eval(*al->M, e, W_GRAD | W_CONS, s);
-    if (!rc)
-        rc = launch_jtprod_al(*al->M, d_x, al->c, d_lambda, al->gl, al->gu, al->rho, al->u, al->bpow, s);
+    // the whole gradient in one kernel where the model allows it; else the
+    // constraints and grad f, then J^T mu formed from them
+    const bool one = al_grad_fused_ok(*al->M);
+    int rc = OPF_OK;
+    if (one) {
+        rc = launch_al_grad(*al->M, d_x, d_lambda, al->gl, al->gu, al->rho, al->u, al->bpow, s);
+    } else {
+        EvalArgs e{d_x, nullptr, 1.0, nullptr, al->grad, al->c, nullptr, nullptr};
+        rc = launch_eval(*al->M, e, W_GRAD | W_CONS, s);
+        if (!rc)
+            rc = launch_jtprod_al(*al->M, d_x, al->c, d_lambda, al->gl, al->gu, al->rho, al->u, al->bpow, s);
+    }
     if (rc)
         return rc;
-    al_adam_kernel<<<grid_of(al->n), 256, 0, s>>>(d_x, al->grad, al->u, al->xl, al->xu, al->m1, al->m2, al->n,
-                                                  al->lr, al->bpow);
+    al_adam_kernel<<<grid_of(al->n), 256, 0, s>>>(d_x, one ? nullptr : al->grad, al->u, al->xl, al->xu, al->m1,
+                                                  al->m2, al->n, al->lr, al->bpow);
     return al_check(cudaGetLastError(), "Adam step");
 }
 

@@ -2443,6 +2443,179 @@ __global__ void __launch_bounds__(256) jt_fused_kernel(const KParams P)
     }
 }
 
+// The augmented Lagrangian's gradient in one kernel (fused layout, polar,
+// without linking or reserve rows): out = grad f + J^T mu with mu_r =
+// rho (s_r - clip(s_r, gl_r, gu_r)), s_r = c_r + lambda_r / rho, where every
+// row value c_r is formed where it is needed instead of being read: each
+// slot lane forms its own end's flow and thermal rows, the far end's flow
+// rows and the angle row, and their multipliers; the bus's last lane forms
+// the balance rows from the scanned p and q sums, and hands their
+// multipliers back to the bus's slot lanes by shuffles for the p and q
+// entries; it also writes its generators' entries (cost gradient, balance
+// and ramp rows). Advances the Adam step state bp like the J^T kernels.
+__device__ __forceinline__ double al_mu(const KParams &P, int64_t row, double c)
+{
+    const double s = fma(__ldg(P.lam + row), P.inv_rho, c);
+    return P.rho * (s - fmin(fmax(s, __ldg(P.gl + row)), __ldg(P.gu + row)));
+}
+
+template <bool ONE>
+__global__ void __launch_bounds__(256) al_grad_kernel(const KParams P)
+{
+    const DevArrays &d = P.d;
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (w >= P.npack_items) {
+        cudaGridDependencySynchronize();
+        cudaTriggerProgrammaticLaunchCompletion();
+        return;
+    }
+    int s = 0, t = 0, wl = 0;
+    if (ONE) {
+        split((int)w, P.inst0.npack, P.inst0.T, t, wl);
+    } else {
+        s = find_inst(d.pack_items, P.ninst, w);
+        const InstDev *Ip = d.inst + s;
+        split((int)(w - __ldg(d.pack_items + s)), __ldg(&Ip->npack), __ldg(&Ip->T), t, wl);
+    }
+    const InstDev I = inst_of<ONE>(P, s);
+    const int4 ld = __ldg(d.pack + (((int64_t)I.pack0 + wl) << 5) + lane);  // (arc, bus, flags, group)
+    const int fl = ld.z;
+    const bool valid = (fl & PK_VALID) != 0, tail = (fl & PK_TAIL) != 0;
+    const bool has = ld.x >= 0;
+    const int nl = I.nl;
+    const int e = has && ld.x >= nl ? 1 : 0;  // 0: from-end, 1: to-end
+    const int k = has ? ld.x - e * nl : 0;
+    const int kb = I.br0 + k;
+    int4 br = make_int4(0, 0, 0, 0), a = make_int4(0, 0, 0, 0);
+    double2 Yo = make_double2(0.0, 0.0), Yx = make_double2(0.0, 0.0);
+    double2 Yfo = make_double2(0.0, 0.0), Yf = make_double2(0.0, 0.0), gb = make_double2(0.0, 0.0);
+    double r2 = 0.0;
+    if (has) {
+        br = __ldg(d.br + kb);
+        Yo = __ldg((e ? d.y_tt : d.y_ff) + kb);
+        Yx = __ldg((e ? d.y_tf : d.y_ft) + kb);
+        Yfo = __ldg((e ? d.y_ff : d.y_tt) + kb);  // the far end's own and transfer admittances
+        Yf = __ldg((e ? d.y_ft : d.y_tf) + kb);
+        r2 = __ldg(d.rate2 + kb);
+    }
+    const int i = ld.y;
+    if (valid && tail) {
+        a = __ldg(d.bus_a + I.bus0 + i);
+        gb = __ldg(d.gsbs + I.bus0 + i);
+    }
+    cudaGridDependencySynchronize();
+    cudaTriggerProgrammaticLaunchCompletion();  // the next kernel may launch now
+    if (P.bp && w == 0 && lane == 0) {  // the next Adam step's bias corrections
+        P.bp[0] *= 0.9;
+        P.bp[1] *= 0.999;
+        P.bp[2] = 1.0 - P.bp[0];
+        P.bp[3] = 1.0 - P.bp[1];
+    }
+
+    const int nb = I.nb, ng = I.ng, T = I.T;
+    const int nbT = nb * T, ngT = ng * T, nlT = nl * T, na = 2 * nl;
+    const int rk = k + nl * t;
+    const int own = has ? (e ? br.y : br.x) : i, far = e ? br.x : br.y;
+    const double *__restrict__ xs = P.x + I.x0;
+    const int iva = nb * t, ivm = nbT + nb * t;
+    const int ip = 2 * nbT + 2 * ngT + na * t, iq = ip + na * T;
+    const int arc = e ? nl + k : k, farc = e ? k : nl + k;
+    double *o = P.grad + I.x0;  // P.grad carries `out`
+    const int64_t R = I.c0 + T + rk;  // this branch's first flow row
+    double vao = 0.0, vo = 0.0, po = 0.0, qo = 0.0;
+    if (valid) {
+        vao = __ldg(xs + iva + own);
+        vo = __ldg(xs + ivm + own);
+    }
+    double dA = 0.0, dM = 0.0, mP = 0.0, mQ = 0.0, mth = 0.0;
+    if (has) {
+        const double vax = __ldg(xs + iva + far), vx = __ldg(xs + ivm + far);
+        po = __ldg(xs + ip + arc);
+        qo = __ldg(xs + iq + arc);
+        const double pf = __ldg(xs + ip + farc), qf = __ldg(xs + iq + farc);
+        const double dlt = vao - vax;
+        double sn, cs_;
+        sincos_tab(dlt, d.trig, &sn, &cs_);
+        const double vft = vo * vx;
+        const double A = fma(Yx.x, cs_, Yx.y * sn), B = fma(Yx.x, sn, neg(Yx.y * cs_));
+        const double Af = fma(Yf.x, cs_, neg(Yf.y * sn)), Bf = neg(fma(Yf.x, sn, Yf.y * cs_));
+        // the branch's rows at this lane: own and far flow rows, the angle row, own thermal row
+        mP = al_mu(P, R + (e ? 2 * nlT : 0), po - fma(Yo.x, vo * vo, vft * A));
+        mQ = al_mu(P, R + (e ? 3 * nlT : nlT), qo - fma(neg(Yo.y), vo * vo, vft * B));
+        const double fP = al_mu(P, R + (e ? 0 : 2 * nlT), pf - fma(Yfo.x, vx * vx, vft * Af));
+        const double fQ = al_mu(P, R + (e ? nlT : 3 * nlT), qf - fma(neg(Yfo.y), vx * vx, vft * Bf));
+        const double mang = al_mu(P, R + 4 * nlT, flip(dlt, e));  // va_f - va_t
+        mth = al_mu(P, R + ((e ? 6 : 5) * nlT + 2 * nbT), fma(po, po, qo * qo) - r2);
+        const double dva = fma(mP, B, fma(neg(mQ), A, fma(neg(fP), Bf, fQ * Af)));
+        dA = fma(vft, dva, flip(mang, e));
+        dM = fma(neg(mP), fma(Yo.x, twice(vo), vx * A), fma(mQ, fma(Yo.y, twice(vo), neg(vx * B)),
+                                                              neg(vx * fma(fP, Af, fQ * Bf))));
+    }
+    // per-bus sums: p, q (for the balance rows) and the voltage parts
+    const unsigned upto = (2u << lane) - 1u;
+    const unsigned bheads = __ballot_sync(full, (fl & PK_HEAD) || !valid);
+    const int bhead = 31 - __clz(bheads & upto);
+    const int bmax = __reduce_max_sync(full, (unsigned)(lane - bhead + 1));
+    double tp = po, tq = qo;
+    for (int dd = 1; dd < bmax; dd <<= 1) {
+        const double yp = __shfl_up_sync(full, tp, dd), yq = __shfl_up_sync(full, tq, dd);
+        const double ya = __shfl_up_sync(full, dA, dd), ym = __shfl_up_sync(full, dM, dd);
+        if (lane - dd >= bhead) {
+            tp += yp;
+            tq += yq;
+            dA += ya;
+            dM += ym;
+        }
+    }
+    // the bus's last lane: its balance rows and their multipliers
+    double mbP = 0.0, mbQ = 0.0;
+    const int64_t RB = I.c0 + (T + 5 * nlT + nb * t + i);  // balance P row of the bus
+    if (valid && tail) {
+        const double vm2 = vo * vo;
+        double Pb = fma(gb.x, vm2, __ldg(d.Pd + I.pd0 + (nb * t + i)));
+        double Qb = fma(neg(gb.y), vm2, __ldg(d.Qd + I.pd0 + (nb * t + i)));
+        for (int gp = a.z; gp < a.w; gp++) {
+            const int g = __ldg(d.gen_list + I.gl0 + gp);
+            Pb -= __ldg(xs + 2 * nbT + ng * t + g);
+            Qb -= __ldg(xs + 2 * nbT + ngT + ng * t + g);
+        }
+        mbP = al_mu(P, RB, Pb + tp);
+        mbQ = al_mu(P, RB + nbT, Qb + tq);
+    }
+    // hand them to the bus's slot lanes (the first tail lane at or above this one)
+    const unsigned tails = __ballot_sync(full, tail || !valid);
+    const int mytail = __ffs(tails & ~(upto >> 1)) - 1;
+    mbP = __shfl_sync(full, mbP, mytail);
+    mbQ = __shfl_sync(full, mbQ, mytail);
+    if (has) {  // own variables: flow row, thermal row, balance row of the arc's bus
+        o[ip + arc] = fma(twice(po), mth, mP + mbP);
+        o[iq + arc] = fma(twice(qo), mth, mQ + mbQ);
+    }
+    if (!(valid && tail))
+        return;
+    const double mref = i == I.ref ? al_mu(P, I.c0 + t, vao) : 0.0;
+    o[iva + i] = dA + mref;
+    o[ivm + i] = fma(twice(vo), fma(gb.x, mbP, neg(gb.y * mbQ)), dM);  // 2 vm (gs muP - bs muQ)
+    const int rb = T + 7 * nlT + 2 * nbT;  // ramp rows
+    for (int gp = a.z; gp < a.w; gp++) {  // the bus's generators: cost, balance and ramp rows
+        const int g = __ldg(d.gen_list + I.gl0 + gp);
+        const int ipg = 2 * nbT + ng * t + g;
+        const double pg = __ldg(xs + ipg);
+        const int gg = I.gen0 + g;
+        double upg = fma(twice(__ldg(d.c2 + gg)), pg, __ldg(d.c1 + gg)) - mbP;
+        if (I.ramp) {  // rows pg_t - pg_{t-1}, t = 1..T-1
+            if (t >= 1)
+                upg += al_mu(P, I.c0 + (rb + g + ng * (t - 1)), pg - __ldg(xs + ipg - ng));
+            if (t + 1 <= T - 1)
+                upg -= al_mu(P, I.c0 + (rb + g + ng * t), __ldg(xs + ipg + ng) - pg);
+        }
+        o[ipg] = upg;
+        o[ipg + ngT] = neg(mbQ);
+    }
+}
+
 // p, q of every arc := the flows at the point's voltages (flow rows exactly
 // zero), one thread per branch item.
 template <bool ONE, bool RECT = false>
@@ -2933,6 +3106,37 @@ int launch_jtprod_al(Model &M, const double *x, const double *c, const double *l
     P.bp = bp;
     P.grad = out;
     return jtprod_launch<true>(M, P, s);
+}
+
+bool al_grad_fused_ok(const Model &M)
+{
+    return M.launch.bus_order == 3 && M.fuse_ok && !M.rect && !M.link && !M.reserve;
+}
+
+// out = grad f + J^T mu of the augmented Lagrangian in one kernel (see
+// al_grad_kernel); only where al_grad_fused_ok
+int launch_al_grad(Model &M, const double *x, const double *lam, const double *gl, const double *gu, double rho,
+                   double *out, double *bp, cudaStream_t s)
+{
+    KParams P = base_params(M);
+    P.x = x;
+    P.lam = lam;
+    P.gl = gl;
+    P.gu = gu;
+    P.rho = rho;
+    P.inv_rho = 1.0 / rho;
+    P.bp = bp;
+    P.grad = out;
+    P.npack_items = M.npack_items;
+    const int bu = M.launch.bus_block > kBusBlockMax ? kBusBlockMax : M.launch.bus_block;
+    const int grid = (int)((M.npack_items + bu / 32 - 1) / (bu / 32));
+    cudaError_t e = M.ninst == 1 ? launch_pdl(al_grad_kernel<true>, grid < 1 ? 1 : grid, bu, s, P)
+                                 : launch_pdl(al_grad_kernel<false>, grid < 1 ? 1 : grid, bu, s, P);
+    if (e != cudaSuccess) {
+        set_error("kernel launch failed: %s", cudaGetErrorString(e));
+        return OPF_ECUDA;
+    }
+    return launch_status();
 }
 
 int launch_cons_setflows(Model &M, double *x, double *obj, double *grad, double *c, cudaStream_t s)

@@ -213,6 +213,11 @@ int launch_jtprod(Model &M, const double *x, const double *v, double *out, cudaS
 // bounds where it is read; advances the step state bp (4 doubles) if not null
 int launch_jtprod_al(Model &M, const double *x, const double *c, const double *lam, const double *gl,
                      const double *gu, double rho, double *out, double *bp, cudaStream_t s);
+// the augmented Lagrangian's gradient grad f + J^T mu in one kernel (fused
+// layout, polar, no linking or reserve rows: al_grad_fused_ok)
+bool al_grad_fused_ok(const Model &M);
+int launch_al_grad(Model &M, const double *x, const double *lam, const double *gl, const double *gu, double rho,
+                   double *out, double *bp, cudaStream_t s);
 int launch_flows(Model &M, double *x, cudaStream_t s);
 // single instance: p, q := flows at x's voltages (written into x), then the
 // objective, gradient and constraints at that point (flow rows zero)

@@ -20,11 +20,13 @@ def torch():
 
 
 @pytest.mark.parametrize("fused", [False, True])
-@pytest.mark.parametrize("case", ["case30g", "mp30", "rect30g", "stor30"])
+@pytest.mark.parametrize("case", ["case30g", "mp30", "rect30g", "stor30", "n1_30"])
 def test_al_iterations_match_oracle(torch, oracle_mod, case, fused):
     """Twenty Adam steps around one multiplier update from the flat start
     with random multipliers, with the two-phase kernels and with the fused
-    evaluation and J^T mu: iterates, multipliers and statistics equal the
+    layout (one-kernel gradient on polar models without linking or reserve
+    rows, the fused evaluation and J^T mu on the rectangular form; storage
+    models keep two phases): iterates, multipliers and statistics equal the
     oracle's. Adam divides by sqrt(v) + 1e-8, so a gradient entry that is
     rounding noise in both implementations can move x by up to lr x
     noise / 1e-8 per step: the bound on |x_gpu - x_oracle| is 1e-7 after 20
@@ -34,9 +36,11 @@ def test_al_iterations_match_oracle(torch, oracle_mod, case, fused):
         else synth.case30(general=True)
     if case == "stor30":  # the loop on the multi-period model with storage
         g = synth.with_storage(g)
+    if case == "n1_30":  # a batch of N-1 instances (several instances, no linking rows)
+        g = synth.contingencies(synth.case30(general=True), 3, seed=4)
     form = "rect" if case == "rect30g" else "polar"  # the loop on the rectangular form's callbacks
     M = opf.Model(g, form=form)
-    if fused:  # the one-kernel evaluation and J^T mu (storage models keep two phases)
+    if fused:
         M.set_launch(branch_block=128, bus_block=64, branch_ctas_per_sm=0, bus_ctas_per_sm=0, bus_order=3)
     O = oracle_mod.Oracle(g, form=form)
     dev = torch.device("cuda")
