@@ -656,7 +656,7 @@ def batched_vs_plain(torch, opf, synth, stream, dev, cpu=False):
     xb = torch.tensor(synth.random_point(sc, rng), device=dev)
     lb = torch.tensor(rng.standard_normal(B.m), device=dev)
     ob = bufs(B)
-    tuned = {"batched": B.autotune(xb, lb, reps=5, stream=stream)[0]}
+    tuned = {"batched": B.autotune(xb, lb, reps=10, stream=stream)[0]}
     tb = graph_us(lambda: B.eval_all(xb, lb, 1.0, *ob, stream=stream))
     grids = [g10.copy(load_pd=sc.load_pd[t:t + 1], load_qd=sc.load_qd[t:t + 1]) for t in range(S)]
     singles = [opf.Model(gt) for gt in grids]
@@ -683,7 +683,7 @@ def batched_vs_plain(torch, opf, synth, stream, dev, cpu=False):
     xb = torch.tensor(synth.random_point(mp, rng), device=dev)
     lb = torch.tensor(rng.standard_normal(B.m), device=dev)
     ob = bufs(B)
-    tuned = {"batched": B.autotune(xb, lb, reps=5, stream=stream)[0]}
+    tuned = {"batched": B.autotune(xb, lb, reps=10, stream=stream)[0]}
     tb = graph_us(lambda: B.eval_all(xb, lb, 1.0, *ob, stream=stream))
     grids = [mp.copy(load_pd=mp.load_pd[t:t + 1], load_qd=mp.load_qd[t:t + 1], ramp_ratio=0.0)
              for t in range(mp.nperiod)]
@@ -722,7 +722,7 @@ def batched_vs_plain(torch, opf, synth, stream, dev, cpu=False):
     xb = torch.tensor(np.concatenate([synth.random_point(s, rng) for s in insts]), device=dev)
     lb = torch.tensor(rng.standard_normal(B.m), device=dev)
     ob = bufs(B)
-    tuned = {"batched": B.autotune(xb, lb, reps=5, stream=stream)[0]}
+    tuned = {"batched": B.autotune(xb, lb, reps=10, stream=stream)[0]}
     tb = graph_us(lambda: B.eval_all(xb, lb, 1.0, *ob, stream=stream))
     singles = [opf.Model(s) for s in insts]
     xs_ = [torch.tensor(synth.random_point(s, rng), device=dev) for s in insts]
@@ -810,7 +810,7 @@ def rect_summary(torch, opf, synth, stream, dev, R, reps, polar_us):
     xb = torch.tensor(synth.random_point(sc, rng, form="rect"), device=dev)
     lb = torch.tensor(rng.standard_normal(B.m), device=dev)
     ob = [torch.empty(k, dtype=f64, device=dev) for k in (1, B.n, B.m, B.nnzj, B.nnzh)]
-    B.autotune(xb, lb, reps=5, stream=stream)
+    B.autotune(xb, lb, reps=10, stream=stream)
     tb = graph_us(lambda k: B.eval_all(xb, lb, 1.0, *ob, stream=stream))
     out["case10k_32_scenarios"] = {"batched_us": tb, "evals_per_s": 32e6 / tb,
                                    "achieved_gbs": 32 * eb / (tb * 1e-6) / 1e9,
