@@ -35,7 +35,8 @@ def _close(name, got, ref, scale):
     assert not bad.any(), f"{name}: {int(bad.sum())} entries differ beyond the tolerance"
 
 
-@pytest.mark.parametrize("which", ["case30_general", "case10k", "mp30x6", "rect30", "storage30x4"])
+@pytest.mark.parametrize("which", ["case30_general", "case10k", "mp30x6", "rect30", "storage30x4",
+                                   "case10k_fused", "rect30_fused"])
 def test_noalloc_matches_eval_all_twice(torch, oracle_mod, which):
     g = {"case30_general": lambda: synth.case30(general=True),
          "case10k": lambda: synth.case10k(),
@@ -43,9 +44,13 @@ def test_noalloc_matches_eval_all_twice(torch, oracle_mod, which):
          "rect30": lambda: synth.case30(general=True),
          "storage30x4": lambda: synth.with_storage(synth.multi_period(synth.case30(general=True), 4, seed=4,
                                                                       ramp_ratio=0.2)),
+         "case10k_fused": lambda: synth.case10k(),
+         "rect30_fused": lambda: synth.case30(general=True),
          }[which]()
-    opts = dict(form="rect") if which == "rect30" else dict(compl=True) if which == "storage30x4" else {}
+    opts = dict(form="rect") if which.startswith("rect30") else dict(compl=True) if which == "storage30x4" else {}
     M = opf.Model(g, **opts)
+    if which.endswith("_fused"):  # the one-kernel evaluation needs no arc scratch
+        M.set_launch(branch_block=128, bus_block=32, branch_ctas_per_sm=0, bus_ctas_per_sm=0, bus_order=3)
     O = oracle_mod.Oracle(g, **opts)
     rng = np.random.default_rng(21)
     x = synth.random_point(g, rng, form=opts.get("form", "polar"))
