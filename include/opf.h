@@ -235,7 +235,10 @@ int opf_eval_all(opf_model *model, const double *d_x, const double *d_lambda, do
  * generator terms, objective), or both (= opf_eval_all). A bus phase alone
  * reads the scratch of the last branch phase run on this model, which must
  * have had the same outputs selected and the same d_x / d_lambda. For timing
- * and for overlapping the phases of independent models. */
+ * and for overlapping the phases of independent models. With the fused
+ * evaluation (bus_order 3, where the model allows it) there is one kernel:
+ * OPF_PHASE_BUS runs the whole evaluation and OPF_PHASE_BRANCH alone runs
+ * nothing. */
 enum { OPF_PHASE_BRANCH = 1, OPF_PHASE_BUS = 2 };
 int opf_eval_phases(opf_model *model, int32_t phases, const double *d_x, const double *d_lambda,
                     double obj_weight, double *d_obj, double *d_grad, double *d_c,
