@@ -20,7 +20,7 @@ def torch():
 
 
 @pytest.mark.parametrize("fused", [False, True])
-@pytest.mark.parametrize("case", ["case30g", "mp30", "rect30g", "stor30", "n1_30"])
+@pytest.mark.parametrize("case", ["case30g", "mp30", "rect30g", "stor30", "n1_30", "mgen_mp30"])
 def test_al_iterations_match_oracle(torch, oracle_mod, case, fused):
     """Twenty Adam steps around one multiplier update from the flat start
     with random multipliers, with the two-phase kernels and with the fused
@@ -38,6 +38,9 @@ def test_al_iterations_match_oracle(torch, oracle_mod, case, fused):
         g = synth.with_storage(g)
     if case == "n1_30":  # a batch of N-1 instances (several instances, no linking rows)
         g = synth.contingencies(synth.case30(general=True), 3, seed=4)
+    if case == "mgen_mp30":  # buses with several generators, multi-period with ramp rows
+        from tests.test_parity_gpu import multi_gen_grid
+        g = multi_gen_grid(3)
     form = "rect" if case == "rect30g" else "polar"  # the loop on the rectangular form's callbacks
     M = opf.Model(g, form=form)
     if fused:

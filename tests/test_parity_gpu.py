@@ -614,3 +614,46 @@ def test_fused_jtprod(torch, oracle_mod, which):
         M.eval_jtprod(dev(torch, x), dev(torch, v), out)
         torch.cuda.synchronize()
         close(f"jtprod bu{bu}", host(out), ref, scale)
+
+
+def multi_gen_grid(T=1):
+    """The general 30-bus grid with extra generators at buses that already
+    have one (two buses with two, one with three), so that the bus loops over
+    several generators run; optionally multi-period with ramp rows."""
+    g = synth.case30(general=True)
+    rng = np.random.default_rng(77)
+    extra = np.array([g.gen_bus[1], g.gen_bus[2], g.gen_bus[2], g.gen_bus[0]], dtype=g.gen_bus.dtype)
+    k = len(extra)
+    cat = lambda a, b: np.concatenate([a, b]).astype(a.dtype)  # noqa: E731
+    g = g.copy(gen_bus=cat(g.gen_bus, extra), gen_pmin=cat(g.gen_pmin, np.zeros(k)),
+               gen_pmax=cat(g.gen_pmax, rng.uniform(0.5, 2.0, k)), gen_qmin=cat(g.gen_qmin, -np.ones(k)),
+               gen_qmax=cat(g.gen_qmax, np.ones(k)), gen_c2=cat(g.gen_c2, rng.uniform(0.01, 0.1, k)),
+               gen_c1=cat(g.gen_c1, rng.uniform(10, 40, k)), gen_c0=cat(g.gen_c0, rng.uniform(0, 5, k)))
+    return synth.multi_period(g, T, seed=6, ramp_ratio=0.2) if T > 1 else g
+
+
+@pytest.mark.parametrize("T", [1, 3])
+def test_multi_generator_buses(torch, oracle_mod, T):
+    """Buses with two and three generators: every output and J^T v against
+    the oracle with the two-phase kernels, the split bus phase and the fused
+    evaluation (one and two warps per packed warp)."""
+    import scipy.sparse as sp
+    g = multi_gen_grid(T)
+    counts = np.bincount(g.gen_bus, minlength=g.nbus)
+    assert counts.max() == 3 and (counts >= 2).sum() == 3
+    M, O = both(torch, oracle_mod, g)
+    x, lam = next(points(g, M.m, 1, seed=43))
+    v = np.random.default_rng(44).standard_normal(M.m)
+    r, c = O.jac_pattern()
+    jv, js = O.jac(x, with_scale=True)
+    ref = sp.coo_matrix((jv, (r, c)), shape=(O.m, O.n)).T @ v
+    scale = sp.coo_matrix((js, (r, c)), shape=(O.m, O.n)).T @ np.abs(v)
+    for launch in (dict(branch_block=128, bus_block=128, branch_ctas_per_sm=0, bus_ctas_per_sm=0, bus_order=0),
+                   dict(branch_block=64, bus_block=64, branch_ctas_per_sm=0, bus_ctas_per_sm=0, bus_order=2,
+                        branch_occupancy=2),
+                   FUSED, dict(FUSED, branch_occupancy=2)):
+        check_against_oracle(O, run_all(torch, M, x, lam, 0.9, launch), x, lam, 0.9, f"{launch} ")
+        out = torch.full((M.n,), np.nan, dtype=torch.float64, device="cuda")
+        M.eval_jtprod(dev(torch, x), dev(torch, v), out)
+        torch.cuda.synchronize()
+        close(f"jtprod {launch}", host(out), ref, scale)
