@@ -23,7 +23,7 @@ struct opf_al {
     double *xl = nullptr, *xu = nullptr, *gl = nullptr, *gu = nullptr;
     double *grad = nullptr, *c = nullptr, *mu = nullptr, *u = nullptr, *m1 = nullptr, *m2 = nullptr;
     double *obj = nullptr, *part = nullptr;  // part: [3][nparts] block partials
-    double *bpow = nullptr;  // device: beta1^k, beta2^k, 1 - beta1^k, 1 - beta2^k
+    double *bpow = nullptr;  // device: beta1^k, beta2^k, 1 - beta1^k, 1 - beta2^k and their reciprocals
     // one inner iteration captured as a CUDA graph per (x, lambda) pair: the
     // loop replays it instead of launching its five kernels one by one
     cudaStream_t cap = nullptr;
@@ -167,7 +167,7 @@ __global__ void al_adam_kernel(double *x, const double *grad, const double *u, c
                                double *m1, double *m2, int64_t n, double lr, const double *bp)
 {
     const double b1 = 0.9, b2 = 0.999;
-    const double k1 = lr / bp[2], k2 = 1.0 / bp[3];
+    const double k1 = lr * bp[4], k2 = bp[5];  // the reciprocals of 1 - b1^k, 1 - b2^k, formed once per step
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
          j += (int64_t)gridDim.x * blockDim.x) {
         const double G = grad ? grad[j] + u[j] : u[j];  // u alone: the whole gradient
@@ -248,9 +248,9 @@ int opf_al_create(opf_model *model, const opf_al_opts *opts, opf_al **out)
     if (!rc) rc = al_alloc(a, &a->m2, a->n);
     if (!rc) rc = al_alloc(a, &a->obj, 1);
     if (!rc) rc = al_alloc(a, &a->part, 3 * (size_t)a->nparts);
-    if (!rc) rc = al_alloc(a, &a->bpow, 4);
+    if (!rc) rc = al_alloc(a, &a->bpow, 6);
     if (!rc) {
-        const double init[4] = {1.0, 1.0, 0.0, 0.0};
+        const double init[6] = {1.0, 1.0, 0.0, 0.0, 0.0, 0.0};
         rc = al_check(cudaMemcpy(a->bpow, init, sizeof(init), cudaMemcpyHostToDevice), "step state");
     }
     if (!rc)
@@ -292,7 +292,7 @@ int opf_al_reset(opf_al *al, double rho, double lr)
     al->rho = rho;
     al->lr = lr;
     al->step = 0;
-    const double init[4] = {1.0, 1.0, 0.0, 0.0};
+    const double init[6] = {1.0, 1.0, 0.0, 0.0, 0.0, 0.0};
     int rc = al_check(cudaMemset(al->m1, 0, sizeof(double) * al->n), "clear moments");
     if (!rc)
         rc = al_check(cudaMemset(al->m2, 0, sizeof(double) * al->n), "clear moments");

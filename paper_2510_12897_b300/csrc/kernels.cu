@@ -2190,6 +2190,8 @@ __global__ void __launch_bounds__(256) jt_bus_kernel(const KParams P)
         P.bp[1] *= 0.999;
         P.bp[2] = 1.0 - P.bp[0];
         P.bp[3] = 1.0 - P.bp[1];
+        P.bp[4] = 1.0 / P.bp[2];  // once here, not per Adam entry
+        P.bp[5] = 1.0 / P.bp[3];
     }
     const DevArrays &d = P.d;
     const int64_t total = P.nbus_items + P.ngen_items;
@@ -2427,6 +2429,8 @@ __global__ void __launch_bounds__(256) jt_fused_kernel(const KParams P)
         P.bp[1] *= 0.999;
         P.bp[2] = 1.0 - P.bp[0];
         P.bp[3] = 1.0 - P.bp[1];
+        P.bp[4] = 1.0 / P.bp[2];  // once here, not per Adam entry
+        P.bp[5] = 1.0 / P.bp[3];
     }
     const DevArrays &d = P.d;
     for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < P.ngen_items;
@@ -2512,6 +2516,8 @@ __global__ void __launch_bounds__(256) al_grad_kernel(const KParams P)
         P.bp[1] *= 0.999;
         P.bp[2] = 1.0 - P.bp[0];
         P.bp[3] = 1.0 - P.bp[1];
+        P.bp[4] = 1.0 / P.bp[2];  // once here, not per Adam entry
+        P.bp[5] = 1.0 / P.bp[3];
     }
 
     const int nb = I.nb, ng = I.ng, T = I.T;
