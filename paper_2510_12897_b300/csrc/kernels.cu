@@ -216,6 +216,25 @@ __device__ __forceinline__ void put5(double *J, bool f_lo, double vaf, double va
     J[4] = 1.0;
 }
 
+// put5 for a whole warp whose lanes hold 32 consecutive rows of one group
+// (J0 = the first row's entries): the 160 values pass through this warp's
+// shared-memory stage and leave as five coalesced 256-byte stores
+__device__ __forceinline__ void put5_warp(double *stg, double *J0, int lane, bool f_lo, double vaf, double vat,
+                                          double vmf, double vmt)
+{
+    double *r = stg + 5 * lane;
+    r[0] = f_lo ? vaf : vat;
+    r[1] = f_lo ? vat : vaf;
+    r[2] = f_lo ? vmf : vmt;
+    r[3] = f_lo ? vmt : vmf;
+    r[4] = 1.0;
+    __syncwarp();
+#pragma unroll
+    for (int m = 0; m < 5; m++)
+        J0[lane + 32 * m] = stg[lane + 32 * m];
+    __syncwarp();
+}
+
 // a double4_16a of read-only data as two 16-byte loads
 __device__ __forceinline__ double4_16a ldg4(const double4_16a *p)
 {
@@ -251,6 +270,7 @@ __global__ void __launch_bounds__(OCC ? 256 : 512, OCC ? 3 : 1) branch_kernel(co
     const DevArrays &d = P.d;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ double stage[JAC ? 16 : 1][JAC ? 160 : 1];  // per warp: one flow-row group's Jacobian values
 
     auto locate = [&](int64_t item, int &s, int &t, int &k, int &kb) {
         if (ONE) {
@@ -355,14 +375,39 @@ __global__ void __launch_bounds__(OCC ? 256 : 512, OCC ? 3 : 1) branch_kernel(co
             const double uB = vft * Bft, uA = vft * Aft, wB = vft * Btf, wA = vft * Atf;
             double *J = P.jac + I.j0;
             double *Jf = J + (T + 5 * rk);
-            // row p_fr - P_fr
-            put5(Jf, f_lo, uB, neg(uB), neg(fma(Yff.x, v2f, vmt * Aft)), neg(vmf * Aft));
-            // row q_fr - Q_fr
-            put5(Jf + 5 * nlT, f_lo, neg(uA), uA, fma(Yff.y, v2f, neg(vmt * Bft)), neg(vmf * Bft));
-            // row p_to - P_to
-            put5(Jf + 10 * nlT, f_lo, neg(wB), wB, neg(vmt * Atf), neg(fma(Ytt.x, v2t, vmf * Atf)));
-            // row q_to - Q_to
-            put5(Jf + 15 * nlT, f_lo, wA, neg(wA), neg(vmt * Btf), fma(Ytt.y, v2t, neg(vmf * Btf)));
+            // When the warp's 32 items are consecutive elements of one
+            // instance, each flow-row group's 32 x 5 values are contiguous:
+            // staged through shared memory and written coalesced (the
+            // scattered 8-byte stores took a third of the batched phase)
+            const unsigned am = __activemask();
+            bool coal = false;
+            if (am == 0xffffffffu) {  // every lane takes every shuffle (no short-circuit around them)
+                const int lane = threadIdx.x & 31;
+                const int rk0 = __shfl_sync(am, rk, 0), s0 = __shfl_sync(am, cs, 0);
+                const bool mine = (rk == rk0 + lane) & (cs == s0);
+                coal = __all_sync(am, mine);
+            }
+            if (coal) {
+                const int lane = threadIdx.x & 31;
+                double *stg = stage[threadIdx.x >> 5];
+                double *J0 = Jf - 5 * lane;  // the warp's first row
+                put5_warp(stg, J0, lane, f_lo, uB, neg(uB), neg(fma(Yff.x, v2f, vmt * Aft)), neg(vmf * Aft));
+                put5_warp(stg, J0 + 5 * nlT, lane, f_lo, neg(uA), uA, fma(Yff.y, v2f, neg(vmt * Bft)),
+                          neg(vmf * Bft));
+                put5_warp(stg, J0 + 10 * nlT, lane, f_lo, neg(wB), wB, neg(vmt * Atf),
+                          neg(fma(Ytt.x, v2t, vmf * Atf)));
+                put5_warp(stg, J0 + 15 * nlT, lane, f_lo, wA, neg(wA), neg(vmt * Btf),
+                          fma(Ytt.y, v2t, neg(vmf * Btf)));
+            } else {
+                // row p_fr - P_fr
+                put5(Jf, f_lo, uB, neg(uB), neg(fma(Yff.x, v2f, vmt * Aft)), neg(vmf * Aft));
+                // row q_fr - Q_fr
+                put5(Jf + 5 * nlT, f_lo, neg(uA), uA, fma(Yff.y, v2f, neg(vmt * Bft)), neg(vmf * Bft));
+                // row p_to - P_to
+                put5(Jf + 10 * nlT, f_lo, neg(wB), wB, neg(vmt * Atf), neg(fma(Ytt.x, v2t, vmf * Atf)));
+                // row q_to - Q_to
+                put5(Jf + 15 * nlT, f_lo, wA, neg(wA), neg(vmt * Btf), fma(Ytt.y, v2t, neg(vmf * Btf)));
+            }
             double *Ja = J + (T + 20 * nlT + 2 * rk);  // angle row va_f - va_t
             Ja[0] = flip(1.0, !f_lo);
             Ja[1] = flip(1.0, f_lo);
