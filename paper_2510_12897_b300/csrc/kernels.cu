@@ -25,6 +25,12 @@
 // phases term by term (and, for the augmented-Lagrangian loop, forms each
 // multiplier from its row's value where it reads it).
 //
+// The fused evaluation (bus_order 3) is one kernel instead of two: whole
+// buses packed into warps, one lane per arc end, per-bus sums by segmented
+// warp scans (fused_bus_warp); J^T v (fused_jt_warp) and the augmented
+// Lagrangian's gradient (al_grad_kernel) have one-kernel forms on the same
+// packed warps.
+//
 // Both kernels are launched with programmatic dependent launch: each block
 // first loads the static network data of its first item (which no kernel
 // writes), then waits for the previous kernel in the stream to complete
