@@ -214,15 +214,18 @@ def test_isolated_bus_single_bus_no_generators(torch, oracle_mod):
                 bus_bs=np.append(g.bus_bs, 0.02))
     M, O = both(torch, oracle_mod, g2)
     x, lam = next(points(g2, M.m, 1, seed=4))
-    check_against_oracle(O, run_all(torch, M, x, lam, 1.0), x, lam, 1.0)
+    launches = (None, dict(FUSED, bus_block=32), dict(FUSED, branch_occupancy=2))  # two-phase, fused
+    for launch in launches:
+        check_against_oracle(O, run_all(torch, M, x, lam, 1.0, launch), x, lam, 1.0, f"{launch} ")
     nogen = g.copy(gen_bus=g.gen_bus[:0], gen_pmin=g.gen_pmin[:0], gen_pmax=g.gen_pmax[:0],
                    gen_qmin=g.gen_qmin[:0], gen_qmax=g.gen_qmax[:0], gen_c2=g.gen_c2[:0],
                    gen_c1=g.gen_c1[:0], gen_c0=g.gen_c0[:0])
     M, O = both(torch, oracle_mod, nogen)
     x, lam = next(points(nogen, M.m, 1, seed=5))
-    got = run_all(torch, M, x, lam, 1.0)
-    check_against_oracle(O, got, x, lam, 1.0)
-    assert got["obj"][0] == 0.0
+    for launch in launches:
+        got = run_all(torch, M, x, lam, 1.0, launch)
+        check_against_oracle(O, got, x, lam, 1.0, f"{launch} ")
+        assert got["obj"][0] == 0.0
 
 
 # ------------------------------------------------ multi-period, batch --
