@@ -638,6 +638,7 @@ __global__ void __launch_bounds__(OCC ? 256 : 512, OCC ? 3 : 1) rect_branch_kern
     const DevArrays &d = P.d;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ double stage[JAC ? 16 : 1][JAC ? 160 : 1];  // per warp: one flow-row group's Jacobian values
 
     auto locate = [&](int64_t item, int &s, int &t, int &k, int &kb) {
         if (ONE) {
@@ -741,15 +742,41 @@ __global__ void __launch_bounds__(OCC ? 256 : 512, OCC ? 3 : 1) rect_branch_kern
             const double z2i = neg(fma(Ytf.x, vif, Ytf.y * vrf));
             const double pa = neg(twice(Yff.x)), qa = twice(Yff.y);  // the from-end's own |V_f|^2 terms
             const double pb = neg(twice(Ytt.x)), qb = twice(Ytt.y);
+            // the four flow rows, staged per warp and written coalesced when
+            // the warp's items are consecutive rows of one instance (as in
+            // the polar branch kernel; every lane takes every shuffle)
+            const unsigned am = __activemask();
+            bool coal = false;
+            if (am == 0xffffffffu) {
+                const int lane = threadIdx.x & 31;
+                const int rk0 = __shfl_sync(am, rk, 0), s0 = __shfl_sync(am, cs, 0);
+                const bool mine = (rk == rk0 + lane) & (cs == s0);
+                coal = __all_sync(am, mine);
+            }
+            const int lane = threadIdx.x & 31;
+            double *J0 = Jf - 5 * lane;
+            double *stg = stage[threadIdx.x >> 5];
             Grad4 g;
             g.rf = fma(pa, vrf, neg(y1r)); g.jf = fma(pa, vif, neg(y1i)); g.rt = neg(y2r); g.jt = y2i;
-            put_rect(Jf, f_lo, g, true);                        // p_fr - P_fr
+            if (coal)  // p_fr - P_fr
+                put5_warp(stg, J0, lane, f_lo, g.rf, g.rt, g.jf, g.jt);
+            else
+                put_rect(Jf, f_lo, g, true);
             g.rf = fma(qa, vrf, y1i); g.jf = fma(qa, vif, neg(y1r)); g.rt = y2i; g.jt = y2r;
-            put_rect(Jf + 5 * nlT, f_lo, g, true);              // q_fr - Q_fr
+            if (coal)  // q_fr - Q_fr
+                put5_warp(stg, J0 + 5 * nlT, lane, f_lo, g.rf, g.rt, g.jf, g.jt);
+            else
+                put_rect(Jf + 5 * nlT, f_lo, g, true);
             g.rf = neg(z1r); g.jf = neg(z1i); g.rt = fma(pb, vrt, neg(z2r)); g.jt = fma(pb, vit, z2i);
-            put_rect(Jf + 10 * nlT, f_lo, g, true);             // p_to - P_to
+            if (coal)  // p_to - P_to
+                put5_warp(stg, J0 + 10 * nlT, lane, f_lo, g.rf, g.rt, g.jf, g.jt);
+            else
+                put_rect(Jf + 10 * nlT, f_lo, g, true);
             g.rf = neg(z1i); g.jf = z1r; g.rt = fma(qb, vrt, neg(z2i)); g.jt = fma(qb, vit, neg(z2r));
-            put_rect(Jf + 15 * nlT, f_lo, g, true);             // q_to - Q_to
+            if (coal)  // q_to - Q_to
+                put5_warp(stg, J0 + 15 * nlT, lane, f_lo, g.rf, g.rt, g.jf, g.jt);
+            else
+                put_rect(Jf + 15 * nlT, f_lo, g, true);
             // angle rows, z = -tan(limit) + j: one FMA per entry
             const double tu = neg(tan_.x), tl = neg(tan_.y);
             g.rf = fma(tu, vrt, neg(vit)); g.jf = fma(tu, vit, vrt); g.rt = fma(tu, vrf, vif); g.jt = fma(tu, vif, neg(vrf));
