@@ -177,6 +177,11 @@ def test_null_and_state_errors(L):
     ok = opf.OpfLaunch(256, 64, 0, 0, 1, 1)
     opf._check(L.opf_set_launch(M.h, ctypes.byref(ok)))
     assert M.get_launch() == ok.as_dict()
+    # the fused evaluation (bus_order 3), with one or two warps per packed warp
+    for occ in (0, 2):
+        fused = opf.OpfLaunch(128, 32, 0, 4, 3, occ)
+        opf._check(L.opf_set_launch(M.h, ctypes.byref(fused)))
+        assert M.get_launch() == fused.as_dict()
 
 
 def test_warm_create_rejects_bad_options(L):
