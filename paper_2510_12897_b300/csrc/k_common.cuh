@@ -1,0 +1,193 @@
+// k_common.cuh: kernel parameters and the helpers every evaluation kernel uses
+//
+// Part of the translation unit of kernels.cu, which includes it inside
+// namespace opf::(anonymous) after model.h; not a standalone header.
+
+struct KParams {
+    DevArrays d;
+    InstDev inst0;  // instance 0: the only one when ninst == 1
+    int32_t ninst;
+    int32_t link;       // linking rows present (J^T v of instance 0's generators)
+    int64_t link_c0;    // first linking row
+    int32_t want_grad, want_obj;
+    int64_t nbr_items, nbus_items, ngen_items;
+    int64_t nst_items;  // storage unit items (bus kernel with storage)
+    int64_t nlight_items, nheavy_items;  // split bus phase: light-bus items, heavy-bus items
+    int64_t npack_items = 0;             // fused evaluation: packed-warp items
+    int32_t fuse_roles = 0;              // fused evaluation: two warps (rows, Hessian) per packed warp
+    int32_t split_tblocks = 0;  // split bus phase: blocks of generator and light-bus items
+    const int32_t *order = nullptr;  // bus-phase order within an instance, or null for id order
+    double *xw = nullptr;            // x, writable (branch phase that sets the flows)
+    // J^T mu of the augmented Lagrangian: v_i = mu_i = rho (s_i - clip(s_i, gl_i, gu_i)),
+    // s_i = c_i + lambda_i / rho, from the rows c (in P.c) and lambda (in P.lam)
+    const double *gl = nullptr, *gu = nullptr;
+    double rho = 1.0, inv_rho = 1.0;
+    double *bp = nullptr;            // the AL step count's bias corrections, advanced once
+    const double *__restrict__ x;
+    const double *__restrict__ lam;
+    double sigma;
+    double *obj, *grad, *c, *jac, *hess;
+};
+
+// largest s with prefix[s] <= item (instances with no items are skipped)
+__device__ __forceinline__ int find_inst(const int64_t *__restrict__ prefix, int ninst, int64_t item)
+{
+    int lo = 0, hi = ninst - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(prefix + mid) <= item)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void split(int loc, int count, int T, int &t, int &e)
+{
+    if (T == 1) {
+        t = 0;
+        e = loc;
+    } else {
+        t = loc / count;
+        e = loc - t * count;
+    }
+}
+
+// the descriptor of instance s (kernel parameter for a single instance)
+template <bool ONE>
+__device__ __forceinline__ InstDev inst_of(const KParams &P, int s)
+{
+    if (ONE)
+        return P.inst0;
+    InstDev I;
+    const int4 *src = reinterpret_cast<const int4 *>(P.d.inst + s);
+    int4 *dst = reinterpret_cast<int4 *>(&I);
+#pragma unroll
+    for (int w = 0; w < (int)(sizeof(InstDev) / 16); w++)
+        dst[w] = __ldg(src + w);
+    return I;
+}
+
+// -v on the integer pipe (an opaque XOR of the sign bit: a plain negation
+// could be rematerialised as an FP64 instruction, the scarce unit here)
+__device__ __forceinline__ double neg(double v)
+{
+    long long r;
+    asm("xor.b64 %0, %1, 0x8000000000000000;" : "=l"(r) : "l"(__double_as_longlong(v)));
+    return __longlong_as_double(r);
+}
+
+// v or -v on the integer pipe
+__device__ __forceinline__ double flip(double v, bool f)
+{
+    long long r;
+    asm("xor.b64 %0, %1, %2;"
+        : "=l"(r)
+        : "l"(__double_as_longlong(v)), "l"(f ? (long long)0x8000000000000000ULL : 0LL));
+    return __longlong_as_double(r);
+}
+
+// 2 v exactly, on the integer pipe: a normal v gets one more in its exponent
+// field; zero and subnormals shift their magnitude left by one (carrying into
+// the exponent field where the result becomes normal); the largest binade
+// overflows to infinity; infinities and NaNs are returned unchanged.
+__device__ __forceinline__ double twice(double v)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const unsigned long long sign = b & 0x8000000000000000ULL;
+    const unsigned long long mag = b & 0x7fffffffffffffffULL;
+    const unsigned ex = (unsigned)(mag >> 52);
+    unsigned long long r = b + (1ULL << 52);
+    r = ex == 0u ? (sign | (mag << 1)) : r;
+    r = ex == 0x7feu ? (sign | 0x7ff0000000000000ULL) : r;
+    r = ex == 0x7ffu ? b : r;
+    return __longlong_as_double((long long)r);
+}
+
+// Table-driven sine and cosine (the table-lookup method of Gal and Bachelis,
+// 1991, and of Tang, 1989): d = k h + e with h = 1/kTrigScale, k = rint(d/h)
+// (by adding 1.5 * 2^52), e = d - k h (exact, Sterbenz); sin(k h), cos(k h)
+// from the table; sin e = e - e^3/6 + e^5/120 and cos e = 1 - e^2/2 + e^4/24,
+// whose truncation errors are below 1e-20 for |e| <= 1/256; then
+// sin d = sin(kh) cos e + cos(kh) sin e, cos d = cos(kh) cos e - sin(kh) sin e.
+// Thirteen FP64 operations. |d| beyond the table falls back to sincos().
+__device__ __forceinline__ void sincos_tab(double d, const double2 *__restrict__ tab, double *sn,
+                                           double *cs)
+{
+    const double shift = 6755399441055744.0;  // 1.5 * 2^52
+    const double t = fma(d, (double)kTrigScale, shift);
+    const int k = __double2loint(t);
+    if (k < -kTrigK || k > kTrigK) {
+        sincos(d, sn, cs);
+        return;
+    }
+    const double kd = t - shift;
+    const double e = fma(kd, -1.0 / kTrigScale, d);
+    const double e2 = e * e;
+    const double se = fma(e * e2, fma(e2, 1.0 / 120.0, -1.0 / 6.0), e);
+    const double ce = fma(e2, fma(e2, 1.0 / 24.0, -0.5), 1.0);
+    const double2 tk = __ldg(tab + (k + kTrigK));
+    *sn = fma(tk.x, ce, tk.y * se);
+    *cs = fma(tk.y, ce, neg(tk.x * se));
+}
+
+// five Jacobian entries of a flow row, columns ascending:
+// (va_lo, va_hi, vm_lo, vm_hi, own) where lo/hi order the two end buses
+__device__ __forceinline__ void put5(double *J, bool f_lo, double vaf, double vat, double vmf,
+                                     double vmt)
+{
+    J[0] = f_lo ? vaf : vat;
+    J[1] = f_lo ? vat : vaf;
+    J[2] = f_lo ? vmf : vmt;
+    J[3] = f_lo ? vmt : vmf;
+    J[4] = 1.0;
+}
+
+// put5 for a whole warp whose lanes hold 32 consecutive rows of one group
+// (J0 = the first row's entries): the 160 values pass through this warp's
+// shared-memory stage and leave as five coalesced 256-byte stores
+__device__ __forceinline__ void put5_warp(double *stg, double *J0, int lane, bool f_lo, double vaf, double vat,
+                                          double vmf, double vmt)
+{
+    double *r = stg + 5 * lane;
+    r[0] = f_lo ? vaf : vat;
+    r[1] = f_lo ? vat : vaf;
+    r[2] = f_lo ? vmf : vmt;
+    r[3] = f_lo ? vmt : vmf;
+    r[4] = 1.0;
+    __syncwarp();
+#pragma unroll
+    for (int m = 0; m < 5; m++)
+        J0[lane + 32 * m] = stg[lane + 32 * m];
+    __syncwarp();
+}
+
+// a double4_16a of read-only data as two 16-byte loads
+__device__ __forceinline__ double4_16a ldg4(const double4_16a *p)
+{
+    const double2 a = __ldg(reinterpret_cast<const double2 *>(p));
+    const double2 b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+    return make_double4_16a(a.x, a.y, b.x, b.y);
+}
+
+// static (never written) data of one branch item
+struct BrStatic {
+    int4 br;  // f, t, slot of the from-arc, slot of the to-arc
+    int2 jb;  // the arcs' entries in their buses' balance rows (one period)
+    double2 yff, yft, ytf, ytt;
+    double r2;
+};
+
+__device__ __forceinline__ BrStatic load_br(const DevArrays &d, int kb, bool need_r2, bool need_jb)
+{
+    BrStatic s;
+    s.br = __ldg(d.br + kb);
+    s.jb = need_jb ? __ldg(d.br_jb + kb) : make_int2(0, 0);
+    s.yff = __ldg(d.y_ff + kb);
+    s.yft = __ldg(d.y_ft + kb);
+    s.ytf = __ldg(d.y_tf + kb);
+    s.ytt = __ldg(d.y_tt + kb);
+    s.r2 = need_r2 ? __ldg(d.rate2 + kb) : 0.0;
+    return s;
+}
