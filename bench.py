@@ -93,6 +93,9 @@ def load_bf16_peak():
         return 1800.0
 
 
+# seconds of untimed replays before the timed region (half as long after it)
+LOAD_S = 0.8
+
 LAUNCH_KEYS = ("branch_block", "bus_block", "branch_ctas_per_sm", "bus_ctas_per_sm", "bus_order", "branch_occupancy")
 
 
@@ -110,6 +113,22 @@ def profile_value(kernel, key):
 
 def profile_traffic(kernel):
     return profile_value(kernel, "dram_bytes_per_launch")
+
+
+def profile_source(kernel):
+    """Where a stored per-launch counter comes from: the committed ncu
+    summary (its first indented line is the ncu command that produced it)."""
+    path = os.path.join("profiles", f"{kernel}_kernel_case10k.md")
+    cmd = None
+    try:
+        for line in open(os.path.join(ROOT, path)):
+            if line.startswith("    ncu"):
+                cmd = line.strip()
+                break
+    except OSError:
+        return None
+    return {"from_profile": path, "ncu_command": cmd,
+            "note": "stored counter from an ncu capture of this kernel, not measured in this run"}
 
 
 # FP64 peak from the unit counts: 148 SMs x 2 FP64 FMA per clock (ncu:
@@ -177,18 +196,25 @@ class Clocks:
         self.index = index
         self.proc = None
         self.path = None
+        self.marks = []
 
     def __enter__(self):
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
         try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu=timestamp,{self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
         time.sleep(0.3)
         return self
+
+    def mark(self):
+        """Host time of a boundary of the loaded window (first and last
+        marks bound the samples the summary keeps)."""
+        self.marks.append(time.time())
 
     def __exit__(self, *exc):
         if self.proc:
@@ -200,12 +226,18 @@ class Clocks:
                 self.proc.kill()
 
     def summary(self):
-        rows = []
+        import datetime
+        rows, stamps = [], []
         try:
             for line in open(self.path):
                 f = [x.strip() for x in line.split(",")]
-                if len(f) >= 9 and f[1].replace(".", "").isdigit():
-                    rows.append(f)
+                if len(f) >= 10 and f[2].replace(".", "").isdigit():
+                    try:
+                        ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                    except ValueError:
+                        ts = None
+                    rows.append(f[1:])
+                    stamps.append(ts)
         except OSError:
             pass
         finally:
@@ -215,6 +247,11 @@ class Clocks:
                 pass
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        if len(self.marks) >= 2:  # keep the samples inside the loaded window
+            inside = [r for r, ts in zip(rows, stamps)
+                      if ts is not None and self.marks[0] <= ts <= self.marks[-1]]
+            if len(inside) >= 3:
+                rows = inside
         sm = [float(r[1]) for r in rows]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
@@ -301,12 +338,13 @@ def reference_arm(args):
     warmup = max(3, min(args.warmup, 64))
     rate, k, el = cpu_oracle_rate(g, seconds=60.0, max_steps=args.steps, warmup=warmup)
     cores = 1
+    host_cores = len(os.sched_getaffinity(0))
     line = {
         "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
         "steps": k, "warmup": warmup, "ms_per_step": 1000.0 * el / k,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": WORKLOAD},
-        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "host_cores": host_cores, "kind": "oracle",
                          "sample": f"{k} of the requested {args.steps} steps (bounded to ~60 s), "
                                    "single-threaded C oracle, full 10k-bus evaluation per step"},
         "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -315,6 +353,18 @@ def reference_arm(args):
 
 
 # ------------------------------------------------------- multi-rank glue --
+
+def timing_plan(steps, sets):
+    """How K timed steps map onto graph replays over R rotating buffer sets:
+    (full, tail, secondary). The timed region is 'full' replays of the
+    R-step graph plus one replay of a 'tail'-step graph (none if 0), which
+    is exactly K steps for any K >= 1 and R >= 1, K < R included; the
+    secondary timings replay the R-step graph 'secondary' >= 1 times."""
+    if steps < 1 or sets < 1:
+        raise ValueError("steps and sets must be >= 1")
+    full, tail = divmod(steps, sets)
+    return full, tail, max(1, full)
+
 
 def max_over_ranks(value, dist, device):
     """The largest of every rank's value (identity on one process)."""
@@ -425,6 +475,16 @@ def main():
         torch.cuda.synchronize()
         return max_over_ranks(e0.elapsed_time(e1), dist, dev)
 
+    def load_for(graph, seconds):
+        """Untimed replays of a graph for about 'seconds' (the loaded window
+        around the timed region)."""
+        t_end = time.time() + seconds
+        with torch.cuda.stream(stream):
+            while time.time() < t_end:
+                for _ in range(16):
+                    graph.replay()
+                torch.cuda.synchronize()
+
     # warm-up (untimed)
     with torch.cuda.stream(stream):
         for k in range(args.warmup):
@@ -432,21 +492,34 @@ def main():
     torch.cuda.synchronize()
 
     K = args.steps
+    # the timed region: K steps, step k on buffer set k mod R, as K // R
+    # replays of an R-step graph and one replay of a (K mod R)-step graph
+    # (K < R: only the latter). The load window replays the R-step graph
+    # before and after it, so the clock sampler sees the GPU under load and
+    # the first timed steps meet the sets used longest ago (out of L2).
+    full_reps, tail_steps, reps = timing_plan(K, R)
     g_full = capture(step, R)
-    g_tail = capture(step, K % R) if K % R else None
+    g_tail = capture(step, tail_steps) if tail_steps else None
     g_full.replay()
     torch.cuda.synchronize()
     with Clocks(local) as clk:
-        ms = timed(g_full, K // R, g_tail)
+        clk.mark()
+        load_for(g_full, LOAD_S)
+        ms = timed(g_full, full_reps, g_tail)
+        load_for(g_full, LOAD_S / 2)
+        clk.mark()
     clocks = clk.summary()
     ms_per_step = ms / K
     value = job_rate(world, K, ms / 1000.0)
+
+    # secondary timings (warm cache, the phases alone, Jacobian + Hessian):
+    # whole R-step graphs, max(1, K // R) replays each, whatever K is
 
     # warm cache: the same step on one buffer set (the solver-loop case,
     # data resident in L2)
     g_warm = capture(lambda k, st: step(0, st), R)
     g_warm.replay()
-    warm_ms = timed(g_warm, K // R) / (R * (K // R))
+    warm_ms = timed(g_warm, reps) / (R * reps)
 
     # dominant kernel alone: branch phase, same rotation
     def branch_only(k, s):
@@ -461,7 +534,6 @@ def main():
         o = outs[k % R]
         models[k % R].eval_jac_hess(xs[k % R], ls[k % R], 1.0, o[3], o[4], stream=s)
 
-    reps = max(1, K // R)
     # bus_order 3: the fused evaluation, one kernel per step (the synthetic
     # 10k grid's buses have at most 32 arc slots, so it applies): no branch
     # phase to time, and the one kernel is the dominant one
@@ -491,7 +563,8 @@ def main():
     achieved = dom_bytes / (dom_us * 1e-6) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": profile_traffic(dominant),
-                "kernel": label, "kernel_us": dom_us,
+                "traffic_source": profile_source(dominant),
+                "kernel": label, "kernel_us": dom_us, "kernel_us_source": "CUDA events in this run",
                 "algorithmic_bytes_per_launch": dom_bytes, "peak_kind": peak_kind}
     if not fused:  # the other phase, same arithmetic (both phases take about the same time)
         oth, oth_us = ("bus", bus_us) if dominant == "branch" else ("branch", br_us)
@@ -500,7 +573,8 @@ def main():
                                    "algorithmic_bytes_per_launch": oth_bytes,
                                    "achieved": oth_bytes / (oth_us * 1e-6) / 1e9,
                                    "frac": oth_bytes / (oth_us * 1e-6) / 1e9 / hbm,
-                                   "traffic": profile_traffic(oth)}
+                                   "traffic": profile_traffic(oth),
+                                   "traffic_source": profile_source(oth)}
 
     # one augmented-Lagrangian inner iteration (f, grad f, g, J^T mu, Adam
     # step) on the 10k grid: the callbacks inside a solver loop
@@ -527,7 +601,7 @@ def main():
     fp64 = None
     if fl_ev and dom_fl:
         fp64 = {"bound": "alu", "unit": "TFLOP/s", "peak": FP64_PEAK_TFLOPS, "peak_kind": "unit counts x clock",
-                "eval_flops": fl_ev,
+                "eval_flops": fl_ev, "flops_source": profile_source("fused" if fused else "branch"),
                 "eval_achieved": fl_ev / (ms_per_step * 1e-3) / 1e12,
                 "eval_frac": fl_ev / (ms_per_step * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
                 "kernel": label, "kernel_achieved": dom_fl / (dom_us * 1e-6) / 1e12,
@@ -582,8 +656,10 @@ def main():
     if not args.no_cpu and rank == 0:
         rate, k, el = cpu_oracle_rate(g, seconds=10.0)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "host_cores": len(os.sched_getaffinity(0)),
                "sample": f"{k} full 10k-bus evaluations (obj, grad, cons, jac, hess) in {el:.1f} s, "
-                         "single-threaded C oracle"}
+                         "single-threaded C oracle (one of the host's cores; the thread-per-core "
+                         "rate over independent instances is batched.sc1k_501.cpu_oracle_threads)"}
 
     if rank == 0:
         line = {

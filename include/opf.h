@@ -265,7 +265,10 @@ int opf_eval_all_host(opf_model *model, const double *h_x, const double *h_lambd
  * library holds until the process exits; the call itself calls no
  * allocator. Limits: models needing more than 174,074 arc slots (2 x
  * branches x periods, summed over instances) are rejected with OPF_EINVAL
- * and a message naming the sizes. The first call on a device looks up the
+ * and a message naming the sizes, unless the model's launch shape is the
+ * one-kernel fused evaluation (bus_order 3 where the model allows it),
+ * which writes no arc slots and so has no such limit. The current device
+ * must be the model's (else OPF_EINVAL). The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress, with that device current)
  * and caches it: make that first call before any stream capture. Every
  * call, on every model, shares the one array and leaves its last contents

@@ -108,6 +108,8 @@ def lib():
         L.ora_bounds.argtypes = [ctypes.c_void_p, _f64p, _f64p, _f64p, _f64p]
         L.ora_obj.restype = ctypes.c_double
         L.ora_obj.argtypes = [ctypes.c_void_p, _f64p]
+        L.ora_obj_scale.restype = ctypes.c_double
+        L.ora_obj_scale.argtypes = [ctypes.c_void_p, _f64p]
         L.ora_grad.argtypes = [ctypes.c_void_p, _f64p, _f64p]
         L.ora_cons.argtypes = [ctypes.c_void_p, _f64p, _f64p, _f64p]
         L.ora_jac.restype = ctypes.c_int
@@ -245,9 +247,11 @@ class Oracle:
         lib().ora_bounds(self.ctx, _p(xl, _f64p), _p(xu, _f64p), _p(gl, _f64p), _p(gu, _f64p))
         return xl, xu, gl, gu
 
-    def obj(self, x):
+    def obj(self, x, with_scale: bool = False):
+        """f(x); with_scale: (f, the sum of the magnitudes of its terms)."""
         x = _f64(x)
-        return lib().ora_obj(self.ctx, _p(x, _f64p))
+        f = lib().ora_obj(self.ctx, _p(x, _f64p))
+        return (f, lib().ora_obj_scale(self.ctx, _p(x, _f64p))) if with_scale else f
 
     def grad(self, x):
         x = _f64(x)

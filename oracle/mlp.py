@@ -15,8 +15,12 @@ Loss of one profile (with the C oracle for f, g and the bounds):
     L = f(x) + w (sum_i (g_i - clip(g_i, gl_i, gu_i))^2
                   + sum_j (x_j - clip(x_j, xl_j, xu_j))^2)
 Parity status: forward/backward pinned by central differences and by the
-erf form of GELU (the tanh form is within 1e-3 of it); the loss is the C
-oracle's f and g, pinned in test_oracle_pins.
+erf form of GELU (the tanh form is within 1e-3 of it). point() pinned on a
+two-bus lossless line: bounds mid-points and half ranges, the reference
+angle, the padded block offsets, and p, q equal to the textbook lossless
+flows. loss() pinned on the same line with every row, bound violation and
+the quadratic cost written out by hand (tests/test_mlp_oracle.py); f and g
+are the C oracle's, pinned in test_oracle_pins.
 """
 from __future__ import annotations
 

@@ -965,6 +965,24 @@ double ora_obj(const ora_ctx *C, const double *x)
     return f;
 }
 
+/* Contribution scale of the objective: the sum of the magnitudes of its
+ * terms, |c2 pg^2| + |c1 pg| + |c0| over generators and periods (the scale
+ * against which a differently ordered sum of the same terms is judged). */
+double ora_obj_scale(const ora_ctx *C, const double *x)
+{
+    double s_f = 0.0;
+    for (int s = 0; s < C->ninst; s++) {
+        const inst_t *S = &C->in[s];
+        const ora_net *n = &S->net;
+        for (int t = 0; t < n->nperiod; t++)
+            for (int g = 0; g < n->ngen; g++) {
+                double pg = x[v_pg(S, g, t)];
+                s_f += fabs(n->c2[g] * pg * pg) + fabs(n->c1[g] * pg) + fabs(n->c0[g]);
+            }
+    }
+    return s_f;
+}
+
 void ora_grad(const ora_ctx *C, const double *x, double *grad)
 {
     memset(grad, 0, sizeof(double) * C->n);

@@ -96,6 +96,7 @@ void ora_bounds(const ora_ctx *, double *xl, double *xu, double *gl, double *gu)
  * over all contributions to the entry, of a bound on each contribution's
  * absolute value. Tolerances are stated relative to it. Pass NULL to skip. */
 double ora_obj(const ora_ctx *, const double *x);
+double ora_obj_scale(const ora_ctx *, const double *x);  /* sum of |terms| of f */
 void ora_grad(const ora_ctx *, const double *x, double *g);
 void ora_cons(const ora_ctx *, const double *x, double *c, double *scale);
 int ora_jac(const ora_ctx *, const double *x, double *vals, double *scale);

@@ -40,14 +40,20 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 unsigned char *g_addr[kMaxDevices] = {};
 
-// device address of g_noalloc_scratch on the current device (set up once)
-int scratch_address(unsigned char **out)
+// device address of g_noalloc_scratch on the current device (set up once);
+// the current device must be the model's (its arrays live there)
+int scratch_address(int model_device, unsigned char **out)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) {
         opf::set_error("noalloc: cudaGetDevice failed: %s", cudaGetErrorString(e));
         return OPF_ECUDA;
+    }
+    if (dev != model_device) {
+        opf::set_error("noalloc: the current device is %d but the model lives on device %d; "
+                       "make the model's device current before the call", dev, model_device);
+        return OPF_EINVAL;
     }
     if (dev < 0 || dev >= kMaxDevices) {
         opf::set_error("noalloc: device %d beyond the %d supported", dev, kMaxDevices);
@@ -87,7 +93,10 @@ extern "C" int opf_eval_all_noalloc(opf_model *m, const double *d_x, const doubl
         set_error("d_x is NULL, or d_lambda is NULL with d_hvals requested");
         return OPF_EINVAL;
     }
-    if (M.narc_slots > kMaxSlots) {
+    // the fused one-kernel evaluation (bus_order 3 where the model allows
+    // it) keeps its per-arc parts in registers and writes no arc scratch
+    const bool fused = M.launch.bus_order == 3 && M.fuse_ok;
+    if (!fused && M.narc_slots > kMaxSlots) {
         set_error("noalloc: model needs %lld arc scratch slots (%lld bytes); the static scratch "
                   "holds %lld slots (OPF_NOALLOC_SCRATCH_BYTES = %zu)",
                   (long long)M.narc_slots, (long long)(M.narc_slots * (int64_t)sizeof(ArcScratch)),
@@ -95,7 +104,7 @@ extern "C" int opf_eval_all_noalloc(opf_model *m, const double *d_x, const doubl
         return OPF_EINVAL;
     }
     unsigned char *base = nullptr;
-    int rc = scratch_address(&base);
+    int rc = scratch_address(M.device, &base);
     if (rc)
         return rc;
     unsigned int *ticket = reinterpret_cast<unsigned int *>(base);
