@@ -304,9 +304,10 @@ int opf_set_loads(opf_model *model, const double *d_load_pd, const double *d_loa
  * flows at those voltages. Into d_x (n). */
 int opf_flat_start(opf_model *model, double *d_x, void *stream);
 
-/* The sine and cosine the branch kernel evaluates (table-driven: a table of
- * sin and cos at multiples of 1/128 plus short Taylor series and the
- * angle-addition formulas; CUDA's sincos beyond |d| > 3.14), applied to n
+/* The sine and cosine the evaluation kernels use (table-driven: a table of
+ * sin and cos at multiples of 1/256, short Taylor series of the remainder
+ * whose small terms are formed in FP32, and the angle-addition formulas;
+ * CUDA's sincos for |d| >= 3.140625), applied to n
  * angles d_angle into d_sin, d_cos (device buffers). For checking its
  * accuracy against other implementations. */
 int opf_sincos(opf_model *model, const double *d_angle, int64_t n, double *d_sin, double *d_cos,

@@ -462,18 +462,18 @@ __device__ void fused_bus_warp(const KParams &P, const int64_t w, const bool gra
             Jt[1] = twice(qo);
         }
         if (HESS) {
-            const double Ue = fma(mP, A, mQ * B);
-            const double Ve = flip(fma(mQ, A, neg(mP * B)), e);
-            // the far end's part: angle -d, admittance Yf, its multipliers
-            const double Af = fma(Yf.x, cs_, neg(Yf.y * sn));
-            const double Bf = neg(fma(Yf.x, sn, Yf.y * cs_));
-            const double Uf = fma(fP, Af, fQ * Bf);
-            const double Vf = flip(fma(fQ, Af, neg(fP * Bf)), !e);
-            const double U = e ? Uf + Ue : Ue + Uf;  // from-end part first
-            const double V = e ? Vf + Ve : Ve + Vf;
+            // U = mP A + mQ B + fP A' + fQ B' (A', B' the far end's, at angle
+            // -d) = alpha cos d + beta sin d in this end's angle d, with
+            // alpha, beta from the multipliers and admittances only (formed
+            // while the sine and cosine are computed); dU/dd = beta cos d -
+            // alpha sin d, and d2L/dvm_own dva_own = -vm_far dU/dd
+            const double alpha = fma(mP, Yx.x, fma(neg(mQ), Yx.y, fma(fP, Yf.x, neg(fQ * Yf.y))));
+            const double beta = fma(mP, Yx.y, fma(mQ, Yx.x, fma(neg(fP), Yf.y, neg(fQ * Yf.x))));
+            const double U = fma(alpha, cs_, beta * sn);
+            const double Vn = fma(alpha, sn, neg(beta * cs_));  // -dU/dd
             const double We = fma(mP, Yo.x, neg(mQ * Yo.y));
             h1 = vft * U;
-            h2 = flip(vx * V, !e);
+            h2 = vx * Vn;
             h3 = neg(twice(We));
             h4 = neg(U);
             double *Hp = P.hess + I.h0 + ((int)(I.hva + I.hvm) * T + ngT + arc + na * t);

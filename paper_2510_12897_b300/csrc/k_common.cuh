@@ -105,31 +105,77 @@ __device__ __forceinline__ double twice(double v)
     return __longlong_as_double((long long)r);
 }
 
-// Table-driven sine and cosine (the table-lookup method of Gal and Bachelis,
-// 1991, and of Tang, 1989): d = k h + e with h = 1/kTrigScale, k = rint(d/h)
-// (by adding 1.5 * 2^52), e = d - k h (exact, Sterbenz); sin(k h), cos(k h)
-// from the table; sin e = e - e^3/6 + e^5/120 and cos e = 1 - e^2/2 + e^4/24,
-// whose truncation errors are below 1e-20 for |e| <= 1/256; then
-// sin d = sin(kh) cos e + cos(kh) sin e, cos d = cos(kh) cos e - sin(kh) sin e.
-// Thirteen FP64 operations. |d| beyond the table falls back to sincos().
+// ---- FP32 <-> FP64 on the integer pipe (the conversion instructions run at
+// the FP64 rate, the scarce unit here)
+
+// v > 0 (or 0) truncated to FP32 (relative error below 2^-23); values below
+// the FP32 normal range give 0
+__device__ __forceinline__ float f32_of_pos(double v)
+{
+    const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
+    if (hi < (897u << 20))
+        return 0.0f;
+    return __uint_as_float(((hi - (896u << 20)) << 3) | (lo >> 29));
+}
+
+// exact widening of a normal FP32 value (zero and subnormals give 0)
+__device__ __forceinline__ double f64_of(float f)
+{
+    const unsigned b = __float_as_uint(f);
+    const unsigned ex = (b >> 23) & 0xffu;
+    const unsigned hi = (b & 0x80000000u) | ((ex + 896u) << 20) | ((b & 0x7fffffu) >> 3);
+    const unsigned lo = b << 29;
+    return ex == 0u ? 0.0 : __hiloint2double((int)hi, (int)lo);
+}
+
+// k / kTrigScale exactly, for |k| < 2048
+__device__ __forceinline__ double k_over_scale(int k)
+{
+    const unsigned a = (unsigned)(k < 0 ? -k : k);
+    const int nbit = 31 - __clz((int)(a | 1u));  // position of the leading bit
+    const unsigned mant = (a << (20 - nbit)) & 0xfffffu;
+    const unsigned hi = (k < 0 ? 0x80000000u : 0u) | ((unsigned)(1023 + nbit - 8) << 20) | mant;
+    return a == 0u ? 0.0 : __hiloint2double((int)hi, 0);
+}
+static_assert(kTrigScale == 256, "k_over_scale divides by 2^8");
+
+// CUDA's sincos, kept out of line: the rare path of sincos_tab (its argument
+// reduction is long and would otherwise be inlined at every call site)
+__device__ __noinline__ void sincos_far(double d, double *sn, double *cs)
+{
+    sincos(d, sn, cs);
+}
+
+// Table-driven sine and cosine (the table-lookup method of Tang, 1989, and
+// of Gal and Bachelis, 1991): d = k h + e with h = 1/256, k = rint(d / h)
+// (by adding 1.5 * 2^52 to 256 d), e = d - k h (exact, Sterbenz), |e| <= 1/512;
+//   sin e = e + e^3 c,  c = -1/6 + e^2/120,
+//   cos e = 1 + q,      q = -e^2/2 + e^4/24,
+// with c and e^4/24 in FP32 (absolute errors below 1e-8 in c, so below 4e-17
+// in e^3 c, and below 1e-19 in e^4/24), e^2, e^3 and the rest in FP64; the
+// series' truncation is below 1e-21; then
+//   sin d = S + S q + C sin e,  cos d = C + C q - S sin e
+// with (S, C) = (sin kh, cos kh) from the table. Ten FP64 operations.
+// |d| >= 3.140625 (or NaN) falls back to CUDA's sincos.
 __device__ __forceinline__ void sincos_tab(double d, const double2 *__restrict__ tab, double *sn,
                                            double *cs)
 {
-    const double shift = 6755399441055744.0;  // 1.5 * 2^52
-    const double t = fma(d, (double)kTrigScale, shift);
-    const int k = __double2loint(t);
-    if (k < -kTrigK || k > kTrigK) {
-        sincos(d, sn, cs);
+    if (((unsigned)__double2hiint(d) & 0x7fffffffu) >= 0x40092000u) {  // |d| >= 3.140625
+        sincos_far(d, sn, cs);
         return;
     }
-    const double kd = t - shift;
-    const double e = fma(kd, -1.0 / kTrigScale, d);
-    const double e2 = e * e;
-    const double se = fma(e * e2, fma(e2, 1.0 / 120.0, -1.0 / 6.0), e);
-    const double ce = fma(e2, fma(e2, 1.0 / 24.0, -0.5), 1.0);
+    const double t = fma(d, (double)kTrigScale, 6755399441055744.0);  // + 1.5 * 2^52
+    const int k = __double2loint(t);
     const double2 tk = __ldg(tab + (k + kTrigK));
-    *sn = fma(tk.x, ce, tk.y * se);
-    *cs = fma(tk.y, ce, neg(tk.x * se));
+    const double e = d - k_over_scale(k);
+    const double e2 = e * e;
+    const float z = f32_of_pos(e2);
+    const float cf = fmaf(z, 1.0f / 120.0f, -1.0f / 6.0f);
+    const float rf = (z * z) * (1.0f / 24.0f);
+    const double se = fma(e * e2, f64_of(cf), e);
+    const double q = fma(e2, -0.5, f64_of(rf));
+    *sn = fma(tk.y, se, fma(tk.x, q, tk.x));
+    *cs = fma(neg(tk.x), se, fma(tk.y, q, tk.y));
 }
 
 // five Jacobian entries of a flow row, columns ascending:

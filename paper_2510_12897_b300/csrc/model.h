@@ -32,8 +32,8 @@ struct __align__(16) ArcScratch {
 
 // Table of the table-driven sine/cosine of the branch kernel: (sin, cos) at
 // k / kTrigScale for |k| <= kTrigK, which covers |d| <= pi.
-constexpr int kTrigScale = 128;
-constexpr int kTrigK = 402;
+constexpr int kTrigScale = 256;
+constexpr int kTrigK = 804;
 
 // split bus phase: buses with more arc slots than this (and at most 32) are
 // handled by a warp each, one lane per slot (6 measured best on the 10k

@@ -486,9 +486,12 @@ int build_model(const opf_network *nets, int32_t ninst, const opf_batch_opts *op
         I.nlight = (int32_t)light_list.size() - I.light0;
         I.nheavy = (int32_t)heavy_list.size() - I.heavy0;
 
-        // ---- fused evaluation: buses in id order packed whole into warps of
-        // 32 lanes, one lane per arc slot (one for a bus without arcs); the
-        // rest of a warp that cannot take the next bus is padding
+        // ---- fused evaluation: buses packed whole into warps of 32 lanes,
+        // one lane per arc slot (one for a bus without arcs), in order of
+        // arc count (descending, then id): the buses of a warp have similar
+        // slot counts, so most warps' segmented scans take fewer steps (a
+        // warp scans as many steps as its largest bus needs); the rest of a
+        // warp that cannot take the next bus is padding
         I.pack0 = (int32_t)(pack.size() / 32);
         {
             const size_t lo = (size_t)I.slot0;
@@ -496,7 +499,12 @@ int build_model(const opf_network *nets, int32_t ninst, const opf_batch_opts *op
                 while (pack.size() % 32)
                     pack.push_back(make_int4(-1, -1, 0, 0));
             };
-            for (int i = 0; i < nb; i++) {
+            std::vector<int32_t> by_deg(nb);
+            std::iota(by_deg.begin(), by_deg.end(), 0);
+            std::stable_sort(by_deg.begin(), by_deg.end(), [&](int x, int y) {
+                return H.arc_ptr[x + 1] - H.arc_ptr[x] > H.arc_ptr[y + 1] - H.arc_ptr[y];
+            });
+            for (int i : by_deg) {
                 const int p0 = H.arc_ptr[i], p1 = H.arc_ptr[i + 1];
                 const int lanes = p1 > p0 ? p1 - p0 : 1;
                 if (lanes > 32) {

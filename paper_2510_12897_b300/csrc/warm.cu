@@ -166,8 +166,12 @@ __global__ void __launch_bounds__(128) umma_gemm_kernel(const __grid_constant__ 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int bm = blockIdx.y * UBM, bn = blockIdx.x * UBN;
     const int nk = g.K / UBK;
+    // set by the producer or the MMA issuer when one of its bounded waits
+    // gives up: both stop issuing, and the epilogue writes nothing
+    __shared__ int s_abort;
 
     if (threadIdx.x == 0) {
+        s_abort = 0;
         for (int st = 0; st < USTAGES; st++) {
             mbar_init(full(st), 1);
             mbar_init(empty(st), 1);
@@ -183,16 +187,23 @@ __global__ void __launch_bounds__(128) umma_gemm_kernel(const __grid_constant__ 
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *slot_ptr;
+    volatile int *abort_flag = &s_abort;
 
+    int issued = 0;  // producer: k tiles whose loads were issued
     if (warp == 0) {
         if (lane == 0) {  // producer
             for (int kt = 0; kt < nk; kt++) {
                 const int st = kt % USTAGES, round = kt / USTAGES;
-                if (round > 0)
-                    mbar_wait(empty(st), (round - 1) & 1);
+                if (*abort_flag)
+                    break;
+                if (round > 0 && !mbar_wait(empty(st), (round - 1) & 1)) {
+                    *abort_flag = 1;
+                    break;
+                }
                 mbar_expect_tx(full(st), 2 * UTILE);
                 tma_load_2d(sA + st * UTILE, &tmA, kt * UBK, bm, full(st));
                 tma_load_2d(sB + st * UTILE, &tmB, kt * UBK, bn, full(st));
+                issued = kt + 1;
             }
         }
         __syncwarp();
@@ -200,7 +211,12 @@ __global__ void __launch_bounds__(128) umma_gemm_kernel(const __grid_constant__ 
         if (lane == 0) {  // MMA issuer
             for (int kt = 0; kt < nk; kt++) {
                 const int st = kt % USTAGES, round = kt / USTAGES;
-                mbar_wait(full(st), round & 1);
+                if (*abort_flag)
+                    break;
+                if (!mbar_wait(full(st), round & 1)) {
+                    *abort_flag = 1;
+                    break;
+                }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
                 for (int k = 0; k < UBK / 16; k++)  // 16 elements = 32 bytes along K per MMA
@@ -208,58 +224,73 @@ __global__ void __launch_bounds__(128) umma_gemm_kernel(const __grid_constant__ 
                          (kt | k) != 0);
                 umma_commit(empty(st));
             }
+            // also after a stop: done then arrives once every MMA issued
+            // above has completed, so the accumulator is quiet before dealloc
             umma_commit(done);
         }
         __syncwarp();
     }
 
-    // epilogue: thread (warp, lane) holds row bm + 32 warp + lane
-    mbar_wait(done, 0);
+    // every thread waits (bounded) for the MMAs; the epilogue runs only if
+    // they all completed and no role gave up
+    const bool mma_done = mbar_wait(done, 0);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const int m = bm + 32 * warp + lane;
-    const size_t row = (size_t)m * g.ldc;
+    const bool skip = __syncthreads_or(!mma_done || s_abort) != 0;
+    if (!skip) {
+        // epilogue: thread (warp, lane) holds row bm + 32 warp + lane
+        const int m = bm + 32 * warp + lane;
+        const size_t row = (size_t)m * g.ldc;
 #pragma unroll 1
-    for (int c = 0; c < UBN / 16; c++) {
-        uint32_t r[16];
-        tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + 16 * c, r);
-        const int n0 = bn + 16 * c;
-        float v[16];
-#pragma unroll
-        for (int j = 0; j < 16; j++)
-            v[j] = __uint_as_float(r[j]);
-        if (g.epi == EPI_BIAS_GELU || g.epi == EPI_BIAS) {
+        for (int c = 0; c < UBN / 16; c++) {
+            uint32_t r[16];
+            tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + 16 * c, r);
+            const int n0 = bn + 16 * c;
+            float v[16];
 #pragma unroll
             for (int j = 0; j < 16; j++)
-                v[j] += g.bias[n0 + j];
-        } else if (g.epi == EPI_DGELU) {
-            const float4 *z4 = reinterpret_cast<const float4 *>(g.zsaved + row + n0);
+                v[j] = __uint_as_float(r[j]);
+            if (g.epi == EPI_BIAS_GELU || g.epi == EPI_BIAS) {
 #pragma unroll
-            for (int q = 0; q < 4; q++) {
-                const float4 z = z4[q];
-                v[4 * q] *= gelu_grad(z.x);
-                v[4 * q + 1] *= gelu_grad(z.y);
-                v[4 * q + 2] *= gelu_grad(z.z);
-                v[4 * q + 3] *= gelu_grad(z.w);
+                for (int j = 0; j < 16; j++)
+                    v[j] += g.bias[n0 + j];
+            } else if (g.epi == EPI_DGELU) {
+                const float4 *z4 = reinterpret_cast<const float4 *>(g.zsaved + row + n0);
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const float4 z = z4[q];
+                    v[4 * q] *= gelu_grad(z.x);
+                    v[4 * q + 1] *= gelu_grad(z.y);
+                    v[4 * q + 2] *= gelu_grad(z.z);
+                    v[4 * q + 3] *= gelu_grad(z.w);
+                }
+            }
+            float4 *o4 = reinterpret_cast<float4 *>(g.outf + row + n0);
+#pragma unroll
+            for (int q = 0; q < 4; q++)
+                o4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            if (g.outh) {
+                __nv_bfloat162 h[8];
+#pragma unroll
+                for (int q = 0; q < 8; q++)
+                    h[q] = g.epi == EPI_BIAS_GELU ? __floats2bfloat162_rn(gelu(v[2 * q]), gelu(v[2 * q + 1]))
+                                                  : __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+                uint4 *oh = reinterpret_cast<uint4 *>(g.outh + row + n0);
+                oh[0] = *reinterpret_cast<const uint4 *>(&h[0]);
+                oh[1] = *reinterpret_cast<const uint4 *>(&h[4]);
             }
         }
-        float4 *o4 = reinterpret_cast<float4 *>(g.outf + row + n0);
-#pragma unroll
-        for (int q = 0; q < 4; q++)
-            o4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-        if (g.outh) {
-            __nv_bfloat162 h[8];
-#pragma unroll
-            for (int q = 0; q < 8; q++)
-                h[q] = g.epi == EPI_BIAS_GELU ? __floats2bfloat162_rn(gelu(v[2 * q]), gelu(v[2 * q + 1]))
-                                              : __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
-            uint4 *oh = reinterpret_cast<uint4 *>(g.outh + row + n0);
-            oh[0] = *reinterpret_cast<const uint4 *>(&h[0]);
-            oh[1] = *reinterpret_cast<const uint4 *>(&h[4]);
-        }
+    }  // !skip
+    if (skip && warp == 0 && lane == 0) {
+        // the producer's own copies in flight: wait (bounded) for the last
+        // load phase of each stage it used, so that no TMA write lands in
+        // shared memory after the block exits (phases of one barrier
+        // complete in order, so the last one implies the earlier ones)
+        for (int kt = issued > USTAGES ? issued - USTAGES : 0; kt < issued; kt++)
+            mbar_wait(full(kt % USTAGES), (kt / USTAGES) & 1);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0)
+    if (warp == 0)  // always freed, also after a stop
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(UBN));
 }
 

@@ -326,14 +326,16 @@ def test_sc1k_501_full(torch, oracle_mod):
 # ------------------------------------------------ trig and large angles --
 
 def test_table_sincos_against_cuda(torch):
-    """The branch kernel's table-driven sine and cosine against CUDA's
+    """The kernels' table-driven sine and cosine against CUDA's
     double-precision sin and cos (through torch) and the host libm, on
-    angles across and beyond the table: absolute error below 4e-16."""
+    angles across the table, at its nodes and midpoints, at its edges and
+    beyond it: absolute error below 4e-16; tiny angles give sin d = d."""
     M = opf.Model(synth.case30())
     rng = np.random.default_rng(3)
     ang = np.concatenate([rng.uniform(-3.2, 3.2, 200_000), rng.uniform(-50, 50, 20_000),
-                          np.arange(-402, 403) / 128.0, (np.arange(-402, 402) + 0.5) / 128.0,
-                          [0.0, -0.0, 1e-300, -1e-300, np.pi, -np.pi]])
+                          np.arange(-804, 805) / 256.0, (np.arange(-804, 804) + 0.5) / 256.0,
+                          [0.0, -0.0, 1e-300, -1e-300, 1e-10, np.pi, -np.pi, 3.140625, -3.140625,
+                           np.nextafter(3.140625, 0.0), np.nextafter(-3.140625, 0.0)]])
     d = dev(torch, ang)
     sn = torch.empty_like(d)
     cs = torch.empty_like(d)
@@ -345,6 +347,7 @@ def test_table_sincos_against_cuda(torch):
     assert np.max(np.abs(host(cs) - c_ref)) < 4e-16
     assert np.max(np.abs(host(sn) - np.sin(ang))) < 4e-16
     assert np.max(np.abs(host(cs) - np.cos(ang))) < 4e-16
+    assert host(sn)[np.flatnonzero(ang == 1e-300)[0]] == 1e-300
 
 
 def test_large_angle_differences(torch, oracle_mod):
