@@ -460,12 +460,18 @@ def main():
         return gr
 
     def timed(graph_full, reps, tail=None):
+        """Milliseconds of `reps` replays of graph_full and one of tail (the
+        timed steps), between a synchronize + barrier on each side. An
+        untimed replay of graph_full is queued ahead of the start event, so
+        the timed replays are already queued when it fires: the graph
+        launch latency stays outside, as in a long run of steps."""
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
         with torch.cuda.stream(stream):
+            graph_full.replay()  # untimed pre-roll
             e0.record(stream)
             for _ in range(reps):
                 graph_full.replay()

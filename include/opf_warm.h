@@ -92,6 +92,16 @@ int opf_warm_forward(opf_warm *w, const double *d_load_pd, const double *d_load_
                      void *stream);
 int opf_warm_backward(opf_warm *w, const float *d_dy, float *d_grad, void *stream);
 
+/* The network's intermediate tensors after the last forward (and backward)
+ * pass, for checking each layer against the oracle on its own inputs: into
+ * HOST buffers (any may be NULL) the BF16 input u ([batch][n_in], raw 16-bit
+ * words), the FP32 pre-activations z1, z2 ([batch][hidden]), their BF16
+ * GELU outputs h1, h2 (raw 16-bit), and the FP32 pre-activation gradients
+ * dz2, dz1 of the last backward pass ([batch][hidden]; the next GEMM takes
+ * them rounded to BF16). Synchronises the device. */
+int opf_warm_get_activations(const opf_warm *w, uint16_t *h_u, float *h_z1, uint16_t *h_h1, float *h_z2,
+                             uint16_t *h_h2, float *h_dz2, float *h_dz1);
+
 /* The physics half of a training step, for checking: from given network
  * outputs d_y ([batch][n_out] floats), the batch loss statistics (as in
  * opf_warm_train_step) and its gradient with respect to y into d_dy. */

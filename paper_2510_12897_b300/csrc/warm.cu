@@ -1227,6 +1227,29 @@ int opf_warm_set_lr(opf_warm *w, double lr, double lr_out)
     return OPF_OK;
 }
 
+int opf_warm_get_activations(const opf_warm *w, uint16_t *h_u, float *h_z1, uint16_t *h_h1, float *h_z2,
+                             uint16_t *h_h2, float *h_dz2, float *h_dz1)
+{
+    if (!w) {
+        set_error("opf_warm_get_activations: NULL handle");
+        return OPF_EINVAL;
+    }
+    const size_t bh = (size_t)w->B * w->H, bk = (size_t)w->B * w->Kin;
+    struct Part {
+        void *dst;
+        const void *src;
+        size_t bytes;
+    } parts[] = {{h_u, w->U, 2 * bk},      {h_z1, w->Z1, 4 * bh},   {h_h1, w->H1, 2 * bh}, {h_z2, w->Z2, 4 * bh},
+                 {h_h2, w->H2, 2 * bh},    {h_dz2, w->dZ2f, 4 * bh}, {h_dz1, w->dZ1f, 4 * bh}};
+    int rc = OPF_OK;
+    for (const Part &q : parts)
+        if (!rc && q.dst)
+            rc = check_cuda(cudaMemcpy(q.dst, q.src, q.bytes, cudaMemcpyDeviceToHost), "get activations");
+    if (!rc)
+        rc = check_timeout();
+    return rc;
+}
+
 int opf_warm_get_params(const opf_warm *w, float *h)
 {
     if (!w || !h) {

@@ -38,6 +38,7 @@ def _lib():
             "opf_warm_loss_grad": [_vp, _vp, _vp, _vp, _vp, _vp, _vp],
             "opf_warm_set_lr": [_vp, ctypes.c_double, ctypes.c_double],
             "opf_warm_get_params": [_vp, _vp],
+            "opf_warm_get_activations": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
             "opf_warm_set_params": [_vp, _vp],
         }
         for name, args in sig.items():
@@ -132,6 +133,22 @@ class WarmStart:
         out = np.empty(self.n_params, np.float32)
         opf._check(_lib().opf_warm_get_params(self.h, out.ctypes.data))
         return out
+
+    def activations(self):
+        """(u, z1, h1, z2, h2, dz2, dz1) of the last forward/backward pass as
+        float64 arrays (BF16 ones widened exactly); see
+        opf_warm_get_activations."""
+        hid = _hidden_of(self.n_params, self.n_in, self.n_out)
+        B = self.batch
+        u = np.empty((B, self.n_in), np.uint16)
+        h1, h2 = np.empty((B, hid), np.uint16), np.empty((B, hid), np.uint16)
+        z1, z2, dz2, dz1 = (np.empty((B, hid), np.float32) for _ in range(4))
+        opf._check(_lib().opf_warm_get_activations(self.h, *(a.ctypes.data for a in (u, z1, h1, z2, h2, dz2, dz1))))
+
+        def widen(a):  # BF16 words are the top halves of FP32 words
+            return (a.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+        return (widen(u), z1.astype(np.float64), widen(h1), z2.astype(np.float64), widen(h2),
+                dz2.astype(np.float64), dz1.astype(np.float64))
 
     def set_params(self, p):
         p = np.ascontiguousarray(p, np.float32)

@@ -73,6 +73,116 @@ def test_network_forward_backward_against_oracle(torch):
     ws.close()
 
 
+U8, U24 = 2.0 ** -8, 2.0 ** -24  # BF16 and FP32 unit roundoffs
+
+
+def _check_entries(name, got, ref, bound):
+    """|got - ref| <= 2 bound entry by entry (2: slack on a worst-case bound)."""
+    err = np.abs(got - ref)
+    bad = err > 2 * bound
+    assert not bad.any(), (name, int(bad.sum()), float(np.max(err / np.maximum(bound, 1e-300))))
+
+
+@pytest.mark.slow
+def test_network_elementwise_full_shapes(torch):
+    """Every GEMM and epilogue of the BF16 network (tcgen05, FP32
+    accumulation) at the 2,000-bus workload's shapes (input 2,816 = 2 x 1,400
+    loads padded to 128, width 1,024, output 5,120, batch 4,096), forward and
+    backward, entry by entry against the FP64 oracle evaluated on that
+    layer's own inputs as the kernels stored them (BF16 activations, FP32
+    pre-activations and gradients, read back with opf_warm_get_activations)
+    and the same BF16 weights. Each entry's bound is the arithmetic's own:
+    K u24 sum_k |a_ik||b_kj| for an FP32-accumulated GEMM of exact BF16
+    products, u24 for the FP32 bias and GELU epilogues, u8 |h| where the
+    epilogue rounds to BF16. The input map is checked against the oracle's
+    (one BF16 ulp at rounding boundaries). Shapes that are not multiples of
+    the tiles are rejected by opf_warm_create (test_abi)."""
+    from paper_2510_12897_b300 import warm
+    g = synth.case2k_secure()
+    B, hid = 4096, 1024
+    ws = warm.WarmStart(g, batch=B, hidden=hid, seed=3)
+    n_in, n_out = ws.n_in, ws.n_out
+    assert (n_in, n_out) == (2816, 5120)
+    p0 = ws.get_params()
+    k = hid * n_in + hid + hid * hid + hid
+    rng = np.random.default_rng(4)
+    p0[k:] = (rng.standard_normal(p0.size - k) / np.sqrt(hid)).astype(np.float32)
+    ws.set_params(p0)
+    pd, qd = synth.load_samples(g, B, seed=11)
+    dev = torch.device("cuda")
+    y = torch.empty(B * n_out, dtype=torch.float32, device=dev)
+    ws.forward(torch.tensor(pd, device=dev), torch.tensor(qd, device=dev), y)
+    dY = np.zeros((B, n_out))
+    nbp, ngp = mlp.pad(g.nbus), mlp.pad(g.ngen)
+    for o, c in ((0, g.nbus), (nbp, g.nbus), (2 * nbp, g.ngen), (2 * nbp + ngp, g.ngen)):
+        dY[:, o:o + c] = rng.standard_normal((B, c)) / B
+    dY = bf16(dY)
+    grad = torch.empty(ws.n_params, dtype=torch.float32, device=dev)
+    ws.backward(torch.tensor(dY, dtype=torch.float32, device=dev), grad)
+    torch.cuda.synchronize()
+    Yg = y.cpu().numpy().astype(np.float64).reshape(B, n_out)
+    gg = grad.cpu().numpy().astype(np.float64)
+    Ug, Z1g, H1g, Z2g, H2g, dZ2g, dZ1g = ws.activations()
+    ws.close()
+
+    W1, b1, W2, b2, W3, b3 = mlp.unpack(p0.astype(np.float64), n_in, hid, n_out)
+    W1, W2, W3 = bf16(W1), bf16(W2), bf16(W3)
+    aW1, aW2, aW3 = np.abs(W1), np.abs(W2), np.abs(W3)
+    # the input map: the kernel forms u = 5 pd / pd0 - 5 in FP32 (absolute
+    # error below 4e-6 for |5 pd / pd0| < 8), then rounds to BF16; the oracle's
+    # FP64 u rounded to BF16 agrees but where the two straddle a BF16
+    # boundary (one ulp) or u is within the FP32 error of zero
+    Uo = bf16(mlp.inputs(pd, qd, g.load_pd[0], g.load_qd[0], n_in))
+    du = np.abs(Ug - Uo)
+    assert np.all(du <= 2.0 ** -7 * np.abs(Uo) + 8e-6) and np.mean(du > 0) < 1e-3
+    aU = np.abs(Ug)
+
+    def layer(A, W, b, aW):
+        ref = A @ W.T + b
+        return ref, A.shape[1] * U24 * (np.abs(A) @ aW.T) + U24 * (np.abs(ref) + np.abs(b))
+
+    # forward, layer by layer on the kernels' own inputs
+    Z1o, e = layer(Ug, W1, b1, aW1)
+    _check_entries("z1", Z1g, Z1o, e)
+    H1o = mlp.gelu(Z1g)
+    _check_entries("h1", H1g, H1o, U8 * np.abs(H1o) + 1e-6 * (1.0 + np.abs(Z1g)))
+    Z2o, e = layer(H1g, W2, b2, aW2)
+    _check_entries("z2", Z2g, Z2o, e)
+    H2o = mlp.gelu(Z2g)
+    _check_entries("h2", H2g, H2o, U8 * np.abs(H2o) + 1e-6 * (1.0 + np.abs(Z2g)))
+    Yo, e = layer(H2g, W3, b3, aW3)
+    _check_entries("y", Yg, Yo, e)
+    assert np.median(np.abs(Yo)) > 1e-2  # a non-trivial output
+    # backward, layer by layer (dY is exact in BF16; the kernels round dz to BF16 for the next GEMM)
+    adY = np.abs(dY)
+    G = {}
+    G["W3"] = (dY.T @ H2g, B * U24 * (adY.T @ np.abs(H2g)))
+    G["b3"] = (dY.sum(0), B * U24 * adY.sum(0))
+    dH2 = dY @ W3
+    gp2 = mlp.gelu_grad(Z2g)
+    dZ2o = dH2 * gp2
+    _check_entries("dz2", dZ2g, dZ2o,
+                   np.abs(gp2) * n_out * U24 * (adY @ aW3) + U24 * np.abs(dZ2o) + 1e-6 * np.abs(dH2))
+    dZ2b = bf16(dZ2g)
+    G["W2"] = (dZ2b.T @ H1g, B * U24 * (np.abs(dZ2b).T @ np.abs(H1g)))
+    G["b2"] = (dZ2g.sum(0), B * U24 * np.abs(dZ2g).sum(0))
+    dH1 = dZ2b @ W2
+    gp1 = mlp.gelu_grad(Z1g)
+    dZ1o = dH1 * gp1
+    _check_entries("dz1", dZ1g, dZ1o,
+                   np.abs(gp1) * hid * U24 * (np.abs(dZ2b) @ aW2) + U24 * np.abs(dZ1o) + 1e-6 * np.abs(dH1))
+    dZ1b = bf16(dZ1g)
+    G["W1"] = (dZ1b.T @ Ug, B * U24 * (np.abs(dZ1b).T @ aU))
+    G["b1"] = (dZ1g.sum(0), B * U24 * np.abs(dZ1g).sum(0))
+    for name, got in zip(("W1", "b1", "W2", "b2", "W3", "b3"), mlp.unpack(gg, n_in, hid, n_out)):
+        ref, e = G[name]
+        _check_entries("grad " + name, got, ref, e + 1e-30)
+    # end to end from the oracle's own input, as a whole: BF16-size relative error
+    pq = np.concatenate([W1.ravel(), b1, W2.ravel(), b2, W3.ravel(), b3])
+    Yf, _ = mlp.forward(pq, Uo, n_in, hid, n_out)
+    assert rel_err(Yg, Yf) < 1e-2
+
+
 def test_physics_gradient_against_oracle_differences(torch, oracle_mod):
     """dL/dy of the penalised loss, from the library's callbacks (cons,
     grad, J^T twice through the flows), against central differences of the
@@ -172,18 +282,19 @@ def test_trained_network_beats_flat_start(torch, oracle_mod):
 
 @pytest.mark.slow
 def test_full_size_gain_judged_by_oracle(torch, oracle_mod):
-    """The 2,000-bus workload: 100k training profiles, 200 epochs, batches
-    of 4,096; on 32 held-out profiles the FP64 oracle's max violation
-    (constraints and bounds) of the predicted point is at least 9x below
-    the flat start's at the median and 4x below it on every profile (the
-    penalised loss's own minimiser, solved per profile on the CPU, sits near 10x)."""
+    """The 2,000-bus workload: 100k training profiles, 600 epochs, batches
+    of 4,096 (the benchmark's schedule); on 64 held-out profiles the FP64
+    oracle's max violation (constraints and bounds) of the predicted point is
+    at least 10x below the flat start's at the median and 5x below it on
+    every profile (the penalised loss's own minimiser, solved per profile on
+    the CPU, sits near 10x)."""
     from paper_2510_12897_b300 import warm
     g = synth.case2k_secure()
     N, B = 100_000, 4096
     pd, qd = synth.load_samples(g, N + B, seed=2024)
     dev = torch.device("cuda")
     ws = warm.WarmStart(g, batch=B, hidden=1024, seed=0)
-    warm.train(ws, torch.tensor(pd[:N], device=dev), torch.tensor(qd[:N], device=dev), epochs=200,
+    warm.train(ws, torch.tensor(pd[:N], device=dev), torch.tensor(qd[:N], device=dev), epochs=600,
                lr=1e-4, lr_out=1e-2, decay=1000.0)
     x = torch.empty(ws.n_x * B, dtype=torch.float64, device=dev)
     ws.predict(torch.tensor(pd[N:], device=dev), torch.tensor(qd[N:], device=dev), x)
@@ -195,7 +306,7 @@ def test_full_size_gain_judged_by_oracle(torch, oracle_mod):
     xf = xf.cpu().numpy()
     counts = [g.nbus, g.nbus, g.ngen, g.ngen, 2 * g.nbranch, 2 * g.nbranch]
     gains = []
-    for t in range(0, B, B // 32):
+    for t in range(0, B, B // 64):
         parts, off = [], 0
         for c in counts:
             parts.append(xw[off + c * t: off + c * (t + 1)])
@@ -204,5 +315,5 @@ def test_full_size_gain_judged_by_oracle(torch, oracle_mod):
         O = oracle_mod.Oracle(gt)
         gains.append(max(O.cvio(xf)) / max(O.cvio(np.concatenate(parts))))
     ws.close()
-    assert np.median(gains) >= 9.0, gains
-    assert min(gains) >= 4.0, gains
+    assert np.median(gains) >= 10.0, gains
+    assert min(gains) >= 5.0, gains
