@@ -62,6 +62,34 @@ int opf_al_iterate(opf_al *al, double *d_x, const double *d_lambda, int32_t iter
 /* Multiplier update at d_x: d_lambda = mu(x). d_stats as above, at d_x. */
 int opf_al_update(opf_al *al, const double *d_x, double *d_lambda, double *d_stats, void *stream);
 
+/* One projected Newton-CG step of L(.; lambda) on d_x (a second-order inner
+ * step that uses the Jacobian and Lagrangian-Hessian values of
+ * include/opf.h): at x, with c = g(x), s = c + lambda / rho, mu = rho (s -
+ * clip(s, gl, gu)) and D_i = 1 where s_i lies outside [gl_i, gu_i] (else 0),
+ *   G = grad f(x) + J^T mu,  K = H(x; mu, sigma = 1) + rho J^T diag(D) J
+ * (H from opf_eval_hess with the multipliers mu, J from opf_eval_jac; K is
+ * L's generalised Hessian). Free entries: all but x_j at xl_j with G_j > 0
+ * and x_j at xu_j with G_j < 0. With the Jacobi diagonal M_j = K_jj (1
+ * where K_jj <= 1e-12) and a Levenberg-Marquardt weight delta: conjugate
+ * gradients with the preconditioner M (1 + delta) on (K + delta diag(M)) p =
+ * -G over the free entries, from p = 0, at most cg_iters iterations,
+ * stopping at non-positive curvature (taking the first direction itself if
+ * that happens at once) or when r^T z falls below 1e-24 of its first value.
+ * Then x_t = clip(x + 2^-t p, xl, xu), t = 0..7, and x becomes the x_t of
+ * the smallest t with L(x_t) <= L(x) + 1e-4 2^-t G^T p; else the x_t of
+ * least L if below L(x); else x is left unchanged. delta starts at 1e-2
+ * (again after opf_al_reset) and is kept on the device between steps:
+ * divided by 4 after a full step, multiplied by 10 after a step of 1/8 or
+ * less (or none), within [1e-8, 1e4]. Every sum is a fixed-
+ * order reduction and every scalar stays on the device (no host round
+ * trip). d_stats (3 doubles, may be NULL) as in opf_al_iterate, at the new
+ * x; d_step (n, may be NULL) receives p. cg_iters >= 1. The Adam state is
+ * not touched. The paper's interior-point solvers (Sec. IV-A) take Newton
+ * steps on the KKT system with a sparse direct solver; this is the matrix-
+ * free counterpart on the augmented Lagrangian. */
+int opf_al_newton(opf_al *al, double *d_x, const double *d_lambda, int32_t cg_iters, double *d_stats,
+                  double *d_step, void *stream);
+
 /* Clear the Adam moments and step count; set the penalty and step size. */
 int opf_al_reset(opf_al *al, double rho, double lr);
 

@@ -26,6 +26,7 @@ def _lib():
             "opf_al_iterate": [_vp, _vp, _vp, ctypes.c_int32, _vp, _vp],
             "opf_al_update": [_vp, _vp, _vp, _vp, _vp],
             "opf_al_reset": [_vp, ctypes.c_double, ctypes.c_double],
+            "opf_al_newton": [_vp, _vp, _vp, ctypes.c_int32, _vp, _vp, _vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -63,6 +64,13 @@ class AugLag:
         M = self.model
         opf._check(_lib().opf_al_update(self.h, opf._ptr(x, M.n, "x"), opf._ptr(lam, M.m, "lambda"),
                                         opf._ptr(stats, 3, "stats"), opf._stream(stream)))
+
+    def newton(self, x, lam, cg_iters: int = 50, stats=None, step=None, stream=None):
+        """One projected Newton-CG step on x (see opf_al_newton)."""
+        M = self.model
+        opf._check(_lib().opf_al_newton(self.h, opf._ptr(x, M.n, "x"), opf._ptr(lam, M.m, "lambda"), int(cg_iters),
+                                        opf._ptr(stats, 3, "stats"), opf._ptr(step, M.n, "step"),
+                                        opf._stream(stream)))
 
     def reset(self, rho: float, lr: float):
         opf._check(_lib().opf_al_reset(self.h, float(rho), float(lr)))

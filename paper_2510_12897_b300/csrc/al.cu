@@ -1,6 +1,7 @@
 // Augmented-Lagrangian loop (include/opf_al.h): Adam inner iterations on
 // L(x; lambda) with the library's callback kernels, multiplier updates, and
 // the statistics of a point, all on the device.
+#include <climits>
 #include <cmath>
 #include <vector>
 
@@ -9,6 +10,8 @@
 
 namespace opf {
 void bounds(const Model &M, double *xl, double *xu, double *gl, double *gu);
+void jac_pattern(const Model &M, int64_t *rows, int64_t *cols);
+void hess_pattern(const Model &M, int64_t *rows, int64_t *cols);
 }  // namespace opf
 
 using namespace opf;
@@ -32,7 +35,23 @@ struct opf_al {
         cudaGraphExec_t exec;
     };
     std::vector<Graph> graphs;
+    // projected Newton-CG step (opf_al_newton), set up on first use: the
+    // Jacobian as CSR (its pattern order) and CSC (a permutation of its
+    // values), the Hessian's lower triangle as CSR and its strict upper part
+    // (the transpose) as CSR with a permutation, the diagonal's position
+    bool nt_ready = false;
+    int32_t *jptr = nullptr, *jcol = nullptr, *tptr = nullptr, *trow = nullptr, *tperm = nullptr;
+    int32_t *hptr = nullptr, *hcol = nullptr, *uptr = nullptr, *ucol = nullptr, *uperm = nullptr, *hdiag = nullptr;
+    double *jv = nullptr, *hv = nullptr, *G = nullptr, *r = nullptr, *z = nullptr, *dv = nullptr, *q = nullptr;
+    double *p = nullptr, *minv = nullptr, *t = nullptr, *Dm = nullptr, *xt = nullptr, *tstats = nullptr;
+    double *cgs = nullptr;  // device scalars of the step (see nt_scalar_kernel), delta kept across steps
+    double *mdiag = nullptr;  // Jacobi diagonal of K
+    unsigned char *F = nullptr;  // free entries
 };
+
+// the Newton step's device scalars (opf_al_newton)
+enum { CG_RZ = 0, CG_RZ0, CG_ALPHA, CG_BETA, CG_DONE, CG_GP, CG_COPY, CG_MOVE, CG_ASTAR, CG_DELTA, CG_N };
+constexpr double kDelta0 = 1e-2;  // first Levenberg-Marquardt weight
 
 namespace {
 
@@ -298,6 +317,8 @@ int opf_al_reset(opf_al *al, double rho, double lr)
         rc = al_check(cudaMemset(al->m2, 0, sizeof(double) * al->n), "clear moments");
     if (!rc)
         rc = al_check(cudaMemcpy(al->bpow, init, sizeof(init), cudaMemcpyHostToDevice), "step state");
+    if (!rc && al->nt_ready)  // the Newton step's first weight again
+        rc = al_check(cudaMemcpy(al->cgs + CG_DELTA, &kDelta0, sizeof(double), cudaMemcpyHostToDevice), "delta");
     return rc;
 }
 
@@ -356,7 +377,415 @@ int al_graph(opf_al *al, double *d_x, const double *d_lambda, cudaGraphExec_t *o
     return OPF_OK;
 }
 
+// ---- projected Newton-CG step (opf_al_newton) -------------------------
+//
+// K = H(x; mu, 1) + rho J^T diag(D) J (H the Lagrangian Hessian, D_i = 1
+// where s_i = c_i + lambda_i / rho lies outside [gl_i, gu_i]); Jacobi-
+// preconditioned CG on K p = -G over the free entries; a backtracking search
+// over eight step lengths. Every reduction is a fixed-order two-level sum
+// (block partials, then one warp), and every scalar of the iteration lives
+// on the device, so the whole step runs without a host round trip.
+
+constexpr int kNls = 8;  // trial step lengths 1, 1/2, ..., 1/128
+
+
+// per-column setup: G = grad f + J^T mu; the free set; the Jacobi diagonal
+// M_j = H_jj + rho sum_i D_i J_ij^2 (1 where <= 1e-12) and the inverse of
+// the preconditioner M_j (1 + delta); r = -G on the free set, z, d = z,
+// p = 0; block partials of r^T z
+__global__ void nt_setup_kernel(int64_t n, const double *grad, const double *jv, const int32_t *tptr,
+                                const int32_t *trow, const int32_t *tperm, const double *mu, const double *Dm,
+                                const double *hv, const int32_t *hdiag, double rho, const double *x, const double *xl,
+                                const double *xu, double *G, unsigned char *F, double *mdiag, double *minv, double *r,
+                                double *z, double *dv, double *p, double *part, int nparts, const double *cgs)
+{
+    const double delta = cgs[CG_DELTA];
+    __shared__ double red[32];
+    double acc = 0.0;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        double g = 0.0, dsum = 0.0;
+        for (int32_t k = tptr[j]; k < tptr[j + 1]; k++) {
+            const double a = jv[tperm[k]];
+            const int32_t i = trow[k];
+            g = fma(a, mu[i], g);
+            dsum = fma(Dm[i] * a, a, dsum);
+        }
+        g += grad[j];
+        const bool free_j = !((x[j] <= xl[j] && g > 0.0) || (x[j] >= xu[j] && g < 0.0));
+        double mj = fma(rho, dsum, hdiag[j] >= 0 ? hv[hdiag[j]] : 0.0);
+        if (mj <= 1e-12)
+            mj = 1.0;
+        const double mi = 1.0 / (mj * (1.0 + delta));
+        const double rj = free_j ? -g : 0.0;
+        const double zj = rj * mi;
+        G[j] = g;
+        F[j] = free_j;
+        mdiag[j] = mj;
+        minv[j] = mi;
+        r[j] = rj;
+        z[j] = zj;
+        dv[j] = zj;
+        p[j] = 0.0;
+        acc = fma(rj, zj, acc);
+    }
+    const double b = block_sum(acc, red);
+    if (threadIdx.x == 0)
+        part[blockIdx.x] = b;
+}
+
+// D_i from s_i = c_i + lambda_i / rho (as the multiplier kernel forms it)
+__global__ void nt_active_kernel(int64_t m, const double *c, const double *lam, const double *gl, const double *gu,
+                                 double inv_rho, double *Dm)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        const double s = fma(lam ? lam[i] : 0.0, inv_rho, c[i]);
+        Dm[i] = (s < gl[i] || s > gu[i]) ? 1.0 : 0.0;
+    }
+}
+
+// t_i = D_i (J d)_i
+__global__ void nt_jd_kernel(int64_t m, const int32_t *jptr, const int32_t *jcol, const double *jv, const double *Dm,
+                             const double *dv, double *t, const double *cgs)
+{
+    if (cgs[CG_DONE] != 0.0)
+        return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        if (Dm[i] != 0.0)
+            for (int32_t k = jptr[i]; k < jptr[i + 1]; k++)
+                acc = fma(jv[k], dv[jcol[k]], acc);
+        t[i] = acc;
+    }
+}
+
+// q = ((K + delta diag(M)) d) on the free set: the lower triangle, its
+// transpose, rho J^T t, delta M_j d_j; block partials of d^T q
+__global__ void nt_kd_kernel(int64_t n, const int32_t *hptr, const int32_t *hcol, const double *hv,
+                             const int32_t *uptr, const int32_t *ucol, const int32_t *uperm, const int32_t *tptr,
+                             const int32_t *trow, const int32_t *tperm, const double *jv, const double *t, double rho,
+                             const unsigned char *F, const double *mdiag, const double *dv, double *q, double *part,
+                             int nparts, const double *cgs)
+{
+    __shared__ double red[32];
+    if (cgs[CG_DONE] != 0.0)
+        return;
+    const double delta = cgs[CG_DELTA];
+    double acc = 0.0;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        double h = 0.0, a = 0.0;
+        for (int32_t k = hptr[j]; k < hptr[j + 1]; k++)
+            h = fma(hv[k], dv[hcol[k]], h);
+        for (int32_t k = uptr[j]; k < uptr[j + 1]; k++)
+            h = fma(hv[uperm[k]], dv[ucol[k]], h);
+        for (int32_t k = tptr[j]; k < tptr[j + 1]; k++)
+            a = fma(jv[tperm[k]], t[trow[k]], a);
+        const double qj = F[j] ? fma(delta * mdiag[j], dv[j], fma(rho, a, h)) : 0.0;
+        q[j] = qj;
+        acc = fma(dv[j], qj, acc);
+    }
+    const double b = block_sum(acc, red);
+    if (threadIdx.x == 0)
+        part[blockIdx.x] = b;
+}
+
+// p += alpha d, r -= alpha q, z = r / M; block partials of r^T z (or, where
+// the first curvature test failed, p = d)
+__global__ void nt_update_kernel(int64_t n, const double *dv, const double *q, const double *minv, double *p, double *r,
+                                 double *z, double *part, int nparts, const double *cgs)
+{
+    __shared__ double red[32];
+    if (cgs[CG_DONE] != 0.0) {
+        if (cgs[CG_COPY] != 0.0)
+            for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+                 j += (int64_t)gridDim.x * blockDim.x)
+                p[j] = dv[j];
+        return;
+    }
+    const double a = cgs[CG_ALPHA];
+    double acc = 0.0;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        p[j] = fma(a, dv[j], p[j]);
+        const double rj = fma(-a, q[j], r[j]);
+        const double zj = rj * minv[j];
+        r[j] = rj;
+        z[j] = zj;
+        acc = fma(rj, zj, acc);
+    }
+    const double b = block_sum(acc, red);
+    if (threadIdx.x == 0)
+        part[blockIdx.x] = b;
+}
+
+// d = z + beta d
+__global__ void nt_dir_kernel(int64_t n, const double *z, double *dv, const double *cgs)
+{
+    if (cgs[CG_DONE] != 0.0)
+        return;
+    const double b = cgs[CG_BETA];
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+        dv[j] = fma(b, dv[j], z[j]);
+}
+
+// block partials of a^T b
+__global__ void nt_dot_kernel(int64_t n, const double *a, const double *b, double *part, int nparts)
+{
+    __shared__ double red[32];
+    double acc = 0.0;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+        acc = fma(a[j], b[j], acc);
+    const double s = block_sum(acc, red);
+    if (threadIdx.x == 0)
+        part[blockIdx.x] = s;
+}
+
+enum { NT_INIT, NT_DQ, NT_RZ, NT_GP };
+
+// the sum of the partials (one warp, fixed order) and the step's scalar logic
+__global__ void nt_scalar_kernel(const double *part, int nparts, double *cgs, int mode, int k)
+{
+    double v = 0.0;
+    for (int q = threadIdx.x; q < nparts; q += 32)
+        v += part[q];
+    for (int off = 16; off; off >>= 1)
+        v += __shfl_down_sync(0xffffffffu, v, off);
+    if (threadIdx.x != 0)
+        return;
+    if (mode == NT_INIT) {
+        cgs[CG_RZ] = cgs[CG_RZ0] = v;
+        cgs[CG_DONE] = v == 0.0 ? 1.0 : 0.0;
+        cgs[CG_COPY] = 0.0;
+    } else if (mode == NT_DQ) {
+        if (cgs[CG_DONE] != 0.0)
+            return;
+        if (v <= 0.0) {  // non-positive curvature: stop (the first direction itself if k == 0)
+            cgs[CG_DONE] = 1.0;
+            cgs[CG_COPY] = k == 0 ? 1.0 : 0.0;
+        } else {
+            cgs[CG_ALPHA] = cgs[CG_RZ] / v;
+        }
+    } else if (mode == NT_RZ) {
+        if (cgs[CG_DONE] != 0.0)
+            return;
+        if (v <= 1e-24 * cgs[CG_RZ0]) {
+            cgs[CG_DONE] = 1.0;
+        } else {
+            cgs[CG_BETA] = v / cgs[CG_RZ];
+            cgs[CG_RZ] = v;
+        }
+    } else {
+        cgs[CG_GP] = v;
+    }
+}
+
+// trial point x_t = clip(x + a p, xl, xu)
+__global__ void nt_trial_kernel(int64_t n, const double *x, const double *p, double a, const double *xl,
+                                const double *xu, double *xt)
+{
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+        xt[j] = fmin(fmax(fma(a, p[j], x[j]), xl[j]), xu[j]);
+}
+
+// the step length: the largest 2^-t with L_t <= L_0 + 1e-4 2^-t G^T p, else
+// the one of least L_t if below L_0, else none (tstats: [3] per trial, then
+// the base point's); the next Levenberg-Marquardt weight: delta / 4 after a
+// full step, delta 10 after a step of 1/8 or less (or none), within
+// [1e-8, 1e4]
+__global__ void nt_select_kernel(const double *tstats, double *cgs)
+{
+    const double L0 = tstats[3 * kNls + 2], gp = cgs[CG_GP];
+    int pick = -1;
+    for (int t = 0; t < kNls && pick < 0; t++)
+        if (tstats[3 * t + 2] <= fma(1e-4 * ldexp(1.0, -t), gp, L0))
+            pick = t;
+    if (pick < 0) {
+        int best = 0;
+        for (int t = 1; t < kNls; t++)
+            if (tstats[3 * t + 2] < tstats[3 * best + 2])
+                best = t;
+        if (tstats[3 * best + 2] < L0)
+            pick = best;
+    }
+    cgs[CG_MOVE] = pick >= 0 ? 1.0 : 0.0;
+    cgs[CG_ASTAR] = pick >= 0 ? ldexp(1.0, -pick) : 0.0;
+    double dl = cgs[CG_DELTA];
+    if (pick == 0)
+        dl = dl / 4.0;
+    else if (pick < 0 || pick > 2)
+        dl = dl * 10.0;
+    cgs[CG_DELTA] = fmin(fmax(dl, 1e-8), 1e4);
+}
+
+__global__ void nt_apply_kernel(int64_t n, double *x, const double *p, const double *xl, const double *xu,
+                                const double *cgs)
+{
+    if (cgs[CG_MOVE] == 0.0)
+        return;
+    const double a = cgs[CG_ASTAR];
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+        x[j] = fmin(fmax(fma(a, p[j], x[j]), xl[j]), xu[j]);
+}
+
+// host: the sparse structures of the step, from the model's patterns
+int nt_setup(opf_al *a)
+{
+    if (a->nt_ready)
+        return OPF_OK;
+    const Model &M = *a->M;
+    const int64_t n = a->n, m = a->m, nj = M.nnzj, nh = M.nnzh;
+    if (nj >= INT32_MAX || nh >= INT32_MAX || n >= INT32_MAX || m >= INT32_MAX) {
+        set_error("opf_al_newton: model too large for 32-bit sparse indices");
+        return OPF_EINVAL;
+    }
+    std::vector<int64_t> jr(nj), jc(nj), hr(nh), hc(nh);
+    jac_pattern(M, jr.data(), jc.data());
+    hess_pattern(M, hr.data(), hc.data());
+    std::vector<int32_t> jptr(m + 1, 0), jcol(nj), tptr(n + 1, 0), trow(nj), tperm(nj);
+    for (int64_t k = 0; k < nj; k++) {
+        jptr[jr[k] + 1]++;
+        tptr[jc[k] + 1]++;
+        jcol[k] = (int32_t)jc[k];
+    }
+    for (int64_t i = 0; i < m; i++)
+        jptr[i + 1] += jptr[i];
+    for (int64_t j = 0; j < n; j++)
+        tptr[j + 1] += tptr[j];
+    {  // CSC: entries of each column in ascending row (the pattern is row-major)
+        std::vector<int32_t> fill(tptr.begin(), tptr.end() - 1);
+        for (int64_t k = 0; k < nj; k++) {
+            const int32_t at = fill[jc[k]]++;
+            trow[at] = (int32_t)jr[k];
+            tperm[at] = (int32_t)k;
+        }
+    }
+    std::vector<int32_t> hptr(n + 1, 0), hcol(nh), uptr(n + 1, 0), hdiag(n, -1);
+    for (int64_t k = 0; k < nh; k++) {
+        hptr[hr[k] + 1]++;
+        hcol[k] = (int32_t)hc[k];
+        if (hr[k] == hc[k])
+            hdiag[hr[k]] = (int32_t)k;
+        else
+            uptr[hc[k] + 1]++;
+    }
+    for (int64_t j = 0; j < n; j++) {
+        hptr[j + 1] += hptr[j];
+        uptr[j + 1] += uptr[j];
+    }
+    std::vector<int32_t> ucol(uptr[n]), uperm(uptr[n]);
+    {
+        std::vector<int32_t> fill(uptr.begin(), uptr.end() - 1);
+        for (int64_t k = 0; k < nh; k++)
+            if (hr[k] != hc[k]) {
+                const int32_t at = fill[hc[k]]++;
+                ucol[at] = (int32_t)hr[k];
+                uperm[at] = (int32_t)k;
+            }
+    }
+    auto up = [&](int32_t **dst, const std::vector<int32_t> &v) {
+        int rc = al_alloc(a, dst, v.size());
+        if (!rc && !v.empty())
+            rc = al_check(cudaMemcpy(*dst, v.data(), sizeof(int32_t) * v.size(), cudaMemcpyHostToDevice),
+                          "upload Newton structures");
+        return rc;
+    };
+    int rc = OPF_OK;
+    if (!rc) rc = up(&a->jptr, jptr);
+    if (!rc) rc = up(&a->jcol, jcol);
+    if (!rc) rc = up(&a->tptr, tptr);
+    if (!rc) rc = up(&a->trow, trow);
+    if (!rc) rc = up(&a->tperm, tperm);
+    if (!rc) rc = up(&a->hptr, hptr);
+    if (!rc) rc = up(&a->hcol, hcol);
+    if (!rc) rc = up(&a->uptr, uptr);
+    if (!rc) rc = up(&a->ucol, ucol);
+    if (!rc) rc = up(&a->uperm, uperm);
+    if (!rc) rc = up(&a->hdiag, hdiag);
+    if (!rc) rc = al_alloc(a, &a->jv, nj);
+    if (!rc) rc = al_alloc(a, &a->hv, nh);
+    for (double **v : {&a->G, &a->r, &a->z, &a->dv, &a->q, &a->p, &a->minv, &a->xt})
+        if (!rc)
+            rc = al_alloc(a, v, n);
+    if (!rc) rc = al_alloc(a, &a->t, m);
+    if (!rc) rc = al_alloc(a, &a->Dm, m);
+    if (!rc) rc = al_alloc(a, &a->tstats, 3 * (kNls + 1));
+    if (!rc) rc = al_alloc(a, &a->cgs, CG_N);
+    if (!rc) rc = al_alloc(a, &a->F, n);
+    if (!rc) rc = al_alloc(a, &a->mdiag, n);
+    if (!rc)
+        rc = al_check(cudaMemcpy(a->cgs + CG_DELTA, &kDelta0, sizeof(double), cudaMemcpyHostToDevice), "delta");
+    if (!rc)
+        a->nt_ready = true;
+    return rc;
+}
+
+// one projected Newton-CG step on stream s (see opf_al_newton)
+int nt_step(opf_al *a, double *d_x, const double *d_lambda, int cg_iters, double *d_stats, cudaStream_t s)
+{
+    const int64_t n = a->n, m = a->m;
+    const int gn = grid_of(n), gm = grid_of(m), np = a->nparts;
+    // base point: f, grad f, g, J; the multipliers mu and the statistics (L_0)
+    EvalArgs e{d_x, nullptr, 1.0, a->obj, a->grad, a->c, a->jv, nullptr};
+    int rc = launch_eval(*a->M, e, W_OBJ | W_GRAD | W_CONS | W_JAC, s);
+    if (rc)
+        return rc;
+    al_mu_kernel<<<np, 256, 0, s>>>(a->c, d_lambda, a->gl, a->gu, m, a->rho, 1.0 / a->rho, a->mu, a->part, np);
+    al_stats_kernel<<<1, 32, 0, s>>>(a->obj, a->part, np, a->rho, a->tstats + 3 * kNls);
+    nt_active_kernel<<<gm, 256, 0, s>>>(m, a->c, d_lambda, a->gl, a->gu, 1.0 / a->rho, a->Dm);
+    // the Lagrangian Hessian with the AL multipliers mu, sigma = 1
+    EvalArgs eh{d_x, a->mu, 1.0, nullptr, nullptr, nullptr, nullptr, a->hv};
+    rc = launch_eval(*a->M, eh, W_HESS, s);
+    if (rc)
+        return rc;
+    nt_setup_kernel<<<np, 256, 0, s>>>(n, a->grad, a->jv, a->tptr, a->trow, a->tperm, a->mu, a->Dm, a->hv, a->hdiag,
+                                       a->rho, d_x, a->xl, a->xu, a->G, a->F, a->mdiag, a->minv, a->r, a->z, a->dv,
+                                       a->p, a->part, np, a->cgs);
+    nt_scalar_kernel<<<1, 32, 0, s>>>(a->part, np, a->cgs, NT_INIT, 0);
+    for (int k = 0; k < cg_iters; k++) {
+        nt_jd_kernel<<<gm, 256, 0, s>>>(m, a->jptr, a->jcol, a->jv, a->Dm, a->dv, a->t, a->cgs);
+        nt_kd_kernel<<<np, 256, 0, s>>>(n, a->hptr, a->hcol, a->hv, a->uptr, a->ucol, a->uperm, a->tptr, a->trow,
+                                        a->tperm, a->jv, a->t, a->rho, a->F, a->mdiag, a->dv, a->q, a->part, np,
+                                        a->cgs);
+        nt_scalar_kernel<<<1, 32, 0, s>>>(a->part, np, a->cgs, NT_DQ, k);
+        nt_update_kernel<<<np, 256, 0, s>>>(n, a->dv, a->q, a->minv, a->p, a->r, a->z, a->part, np, a->cgs);
+        nt_scalar_kernel<<<1, 32, 0, s>>>(a->part, np, a->cgs, NT_RZ, k);
+        nt_dir_kernel<<<gn, 256, 0, s>>>(n, a->z, a->dv, a->cgs);
+    }
+    rc = al_check(cudaGetLastError(), "CG kernels");
+    if (rc)
+        return rc;
+    nt_dot_kernel<<<np, 256, 0, s>>>(n, a->G, a->p, a->part, np);
+    nt_scalar_kernel<<<1, 32, 0, s>>>(a->part, np, a->cgs, NT_GP, 0);
+    for (int t = 0; t < kNls && !rc; t++) {
+        nt_trial_kernel<<<gn, 256, 0, s>>>(n, d_x, a->p, ldexp(1.0, -t), a->xl, a->xu, a->xt);
+        rc = al_point(a, a->xt, d_lambda, false, a->tstats + 3 * t, s);
+    }
+    if (rc)
+        return rc;
+    nt_select_kernel<<<1, 1, 0, s>>>(a->tstats, a->cgs);
+    nt_apply_kernel<<<gn, 256, 0, s>>>(n, d_x, a->p, a->xl, a->xu, a->cgs);
+    rc = al_check(cudaGetLastError(), "line search kernels");
+    if (!rc && d_stats)
+        rc = al_point(a, d_x, d_lambda, false, d_stats, s);
+    return rc;
+}
+
 }  // namespace
+
+int opf_al_newton(opf_al *al, double *d_x, const double *d_lambda, int32_t cg_iters, double *d_stats,
+                  double *d_step, void *stream)
+{
+    if (!al || !d_x || !d_lambda || cg_iters < 1) {
+        set_error("opf_al_newton: need a loop, d_x, d_lambda and cg_iters >= 1");
+        return OPF_EINVAL;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int rc = nt_setup(al);
+    if (!rc)
+        rc = nt_step(al, d_x, d_lambda, cg_iters, d_stats, s);
+    if (!rc && d_step)
+        rc = al_check(cudaMemcpyAsync(d_step, al->p, sizeof(double) * al->n, cudaMemcpyDeviceToDevice, s),
+                      "copy the CG direction");
+    return rc;
+}
 
 int opf_al_iterate(opf_al *al, double *d_x, const double *d_lambda, int32_t iters, double *d_stats, void *stream)
 {

@@ -117,3 +117,81 @@ def test_adam_sign_flip_closed_form():
     x0 = rng.standard_normal(32)
     x2, _ = A.iterate(x0, np.zeros(1), 2)
     np.testing.assert_allclose(x2, x0 - 2e-3 * np.sign(c) * (1.0 - 1.0 / 19.0), rtol=0, atol=2e-3 * 1e-6)
+
+
+# ---- the projected Newton-CG step (NewtonOracle, pcg)
+
+def test_newton_system_is_the_gradients_derivative(oracle_mod):
+    """K v (K = H(x; mu, 1) + rho J^T D J, H assembled symmetric from its
+    lower triangle) equals Richardson central differences of the AL gradient
+    G along v, at a point where every row's s stays on its side of its bounds
+    over the differencing interval (so D is constant there); several
+    directions, multi-period general grid."""
+    g = synth.multi_period(synth.case30(general=True), 2, seed=4, ramp_ratio=0.2)
+    O = oracle_mod.Oracle(g)
+    A = al.NewtonOracle(O, rho=7.0, lr=1e-3)
+    rng = np.random.default_rng(5)
+    x = synth.random_point(g, rng)
+    lam = rng.standard_normal(O.m)
+    G, K, D, _, _ = A.system(x, lam)
+    assert 0 < D.sum() < O.m  # active and inactive rows
+    xl, xu, gl, gu = O.bounds()
+    for k in range(4):
+        v = rng.standard_normal(O.n)
+        h = 1e-6
+        s_lo = O.cons(x - h * v) + lam / A.rho
+        s_hi = O.cons(x + h * v) + lam / A.rho
+        Dl = ((s_lo < gl) | (s_lo > gu)).astype(float)
+        Dh = ((s_hi < gl) | (s_hi > gu)).astype(float)
+        assert np.array_equal(Dl, D) and np.array_equal(Dh, D)
+        d1 = (A.gradient(x + h * v, lam) - A.gradient(x - h * v, lam)) / (2 * h)
+        d2 = (A.gradient(x + h / 2 * v, lam) - A.gradient(x - h / 2 * v, lam)) / h
+        fd = (4 * d2 - d1) / 3
+        Kv = K @ v
+        np.testing.assert_allclose(Kv, fd, rtol=1e-5, atol=1e-5 * max(1.0, float(np.max(np.abs(Kv)))))
+
+
+def test_pcg_solves_spd_systems():
+    """On a symmetric positive definite system the preconditioned CG reaches
+    numpy's dense solution over the free entries (the others stay zero); on
+    an indefinite one whose first direction has negative curvature it
+    returns that direction."""
+    rng = np.random.default_rng(7)
+    n = 40
+    A0 = rng.standard_normal((n, n))
+    K = A0 @ A0.T + n * np.eye(n)
+    G = rng.standard_normal(n)
+    F = rng.uniform(size=n) > 0.2
+    Mj = np.diag(K).copy()
+    p = al.pcg(lambda v: K @ v, G, F, Mj, 200)
+    ff = np.flatnonzero(F)
+    want = np.linalg.solve(K[np.ix_(ff, ff)], -G[ff])
+    np.testing.assert_allclose(p[ff], want, rtol=1e-10, atol=1e-12)
+    assert np.all(p[~F] == 0.0)
+    Kneg = -np.eye(n)
+    Fall = np.ones(n, bool)
+    p1 = al.pcg(lambda v: Kneg @ v, G, Fall, np.ones(n), 10)
+    np.testing.assert_array_equal(p1, -G)
+
+
+def test_newton_steps_never_raise_L_and_reach_feasibility(oracle_mod):
+    """The step never increases L(x; lambda); an outer loop of ten Newton
+    steps per multiplier update (rho 1000) takes the 30-bus grid from the
+    flat start to a max row violation below 1e-4 in twelve updates (a
+    first-order loop stalls near 0.06 on the 2,000-bus grid)."""
+    g = synth.secure_ratings(synth.case30())
+    O = oracle_mod.Oracle(g)
+    A = al.NewtonOracle(O, rho=1000.0, lr=1e-3)
+    xl, xu, _, _ = O.bounds()
+    nb, ng, nl = g.nbus, g.ngen, g.nbranch
+    x = np.concatenate([np.zeros(nb), np.clip(np.ones(nb), xl[nb:2 * nb], xu[nb:2 * nb]),
+                        0.5 * (xl[2 * nb:2 * nb + 2 * ng] + xu[2 * nb:2 * nb + 2 * ng]), np.zeros(4 * nl)])
+    lam = np.zeros(O.m)
+    viol0 = A.stats(x, lam)[1]
+    for outer in range(12):
+        for _ in range(10):
+            L0 = A.value(x, lam)
+            x, st, _ = A.newton_step(x, lam, 100)
+            assert st[2] <= L0 + 1e-12 * max(1.0, abs(L0))
+        lam, st = A.update(x, lam)
+    assert A.stats(x, lam)[1] < 1e-4 < 0.5 < viol0
