@@ -96,6 +96,10 @@ def load_bf16_peak():
 # seconds of untimed replays before the timed region (half as long after it)
 LOAD_S = 0.8
 
+# the batches as one persistent kernel per evaluation (fused layout)
+ONE_KERNEL = dict(branch_block=128, bus_block=64, branch_ctas_per_sm=0, bus_ctas_per_sm=16, bus_order=3,
+                  branch_occupancy=0)
+
 LAUNCH_KEYS = ("branch_block", "bus_block", "branch_ctas_per_sm", "bus_ctas_per_sm", "bus_order", "branch_occupancy")
 
 
@@ -596,6 +600,16 @@ def main():
         e1.record(stream)
     torch.cuda.synchronize()
     al_us = 1000.0 * e0.elapsed_time(e1) / 200
+    # one projected Newton-CG step (50 CG iterations) on the 10k grid
+    A10.newton(xa, la, 50, stream=stream)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(5):
+            A10.newton(xa, la, 50, stream=stream)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    newton_us = 1000.0 * e0.elapsed_time(e1) / 5
     A10.close()
 
     if fused:
@@ -684,6 +698,9 @@ def main():
             "phase_us": ({"fused": bus_us} if fused else {"branch": br_us, "bus": bus_us}) | {"autotune_eval": tuned_us},
             "fp64_roofline": fp64,
             "al_inner_iteration_us": al_us,
+            "al_newton_step_us": {"value": newton_us, "cg_iterations": 50,
+                                  "note": "one opf_al_newton step on the 10k grid: f, g, J, H evaluations, "
+                                          "50 CG iterations of 6 kernels, 8 trial evaluations"},
             "warm_cache": {"ms_per_step": warm_ms, "evals_per_s": 1000.0 / warm_ms,
                            "note": "one buffer set, data resident in L2 (the solver-loop case)"},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": (1 if fused else 2) * K, "clocks": clocks,
@@ -722,6 +739,15 @@ def batched_vs_plain(torch, opf, synth, stream, dev, cpu=False):
     def bufs(M):
         return [torch.empty(k, dtype=f64, device=dev) for k in (1, M.n, M.m, M.nnzj, M.nnzh)]
 
+    def one_kernel_us(Bm, xb, lb, ob, cfg):
+        """The batch as one persistent kernel per evaluation (the fused layout,
+        bus_order 3, persistent generator blocks and packed warps), timed like
+        the tuned shape, which is then restored."""
+        Bm.set_launch(**ONE_KERNEL)
+        t = graph_us(lambda: Bm.eval_all(xb, lb, 1.0, *ob, stream=stream))
+        Bm.set_launch(**cfg)
+        return t
+
     def tune_all(models, x, lam):
         """The autotuner's shape for the first per-instance model, used by all."""
         cfg = models[0].autotune(x, lam, reps=20, stream=stream)[0]
@@ -740,6 +766,7 @@ def batched_vs_plain(torch, opf, synth, stream, dev, cpu=False):
     ob = bufs(B)
     tuned = {"batched": B.autotune(xb, lb, reps=10, stream=stream)[0]}
     tb = graph_us(lambda: B.eval_all(xb, lb, 1.0, *ob, stream=stream))
+    t1 = one_kernel_us(B, xb, lb, ob, tuned["batched"])
     grids = [g10.copy(load_pd=sc.load_pd[t:t + 1], load_qd=sc.load_qd[t:t + 1]) for t in range(S)]
     singles = [opf.Model(gt) for gt in grids]
     xs_ = [torch.tensor(synth.random_point(gt, rng), device=dev) for gt in grids]
@@ -755,6 +782,7 @@ def batched_vs_plain(torch, opf, synth, stream, dev, cpu=False):
     ev = eval_bytes(g10, singles[0].nnzh)
     out["case10k_32_scenarios"] = {
         "batched_us": tb, "plain_loop_us": tp, "speedup": tp / tb, "launch": tuned,
+        "one_kernel_us": t1, "one_kernel_speedup": tp / t1,
         "evals_per_s": S * 1e6 / tb,
         "achieved_gbs": S * ev / (tb * 1e-6) / 1e9,
         "hbm_frac": S * ev / (tb * 1e-6) / 1e9 / load_peaks()[0]}
@@ -767,6 +795,7 @@ def batched_vs_plain(torch, opf, synth, stream, dev, cpu=False):
     ob = bufs(B)
     tuned = {"batched": B.autotune(xb, lb, reps=10, stream=stream)[0]}
     tb = graph_us(lambda: B.eval_all(xb, lb, 1.0, *ob, stream=stream))
+    t1 = one_kernel_us(B, xb, lb, ob, tuned["batched"])
     grids = [mp.copy(load_pd=mp.load_pd[t:t + 1], load_qd=mp.load_qd[t:t + 1], ramp_ratio=0.0)
              for t in range(mp.nperiod)]
     singles = [opf.Model(gt) for gt in grids]
@@ -781,6 +810,7 @@ def batched_vs_plain(torch, opf, synth, stream, dev, cpu=False):
 
     tp = graph_us(plain_mp)
     out["mp2k_96"] = {"batched_us": tb, "plain_loop_us": tp, "speedup": tp / tb, "launch": tuned,
+                      "one_kernel_us": t1, "one_kernel_speedup": tp / t1,
                       "batched_evals_per_s": 1e6 / tb, "period_evals_per_s": 96e6 / tb}
     n_mp, m_mp = B.n, B.m
     del B, singles, os_
@@ -806,6 +836,7 @@ def batched_vs_plain(torch, opf, synth, stream, dev, cpu=False):
     ob = bufs(B)
     tuned = {"batched": B.autotune(xb, lb, reps=10, stream=stream)[0]}
     tb = graph_us(lambda: B.eval_all(xb, lb, 1.0, *ob, stream=stream))
+    t1 = one_kernel_us(B, xb, lb, ob, tuned["batched"])
     singles = [opf.Model(s) for s in insts]
     xs_ = [torch.tensor(synth.random_point(s, rng), device=dev) for s in insts]
     ls_ = [torch.tensor(rng.standard_normal(s.m), device=dev) for s in singles]
@@ -818,6 +849,7 @@ def batched_vs_plain(torch, opf, synth, stream, dev, cpu=False):
 
     tp = graph_us(plain_sc, reps=5)
     out["sc1k_501"] = {"batched_us": tb, "plain_loop_us": tp, "speedup": tp / tb, "launch": tuned,
+                       "one_kernel_us": t1, "one_kernel_speedup": tp / t1,
                        "instance_evals_per_s": 501e6 / tb}
     # the same batch with per-contingency corrective ratios and reserve rows
     ratios = np.concatenate([[0.0], np.random.default_rng(3).uniform(0.1, 0.3, len(insts) - 1)])
@@ -1003,6 +1035,32 @@ def warm_start_summary(torch, opf, synth, dev, epochs):
             traj.append(float(st[1]))
         al_runs[start] = traj
         A.close()
+    # the second-order step (opf_al_newton: Jacobian and Hessian values, CG
+    # on the AL's generalised Hessian) on the same profile: 10 multiplier
+    # updates of 10 Newton steps, rho 1000, from both starts
+    newton_runs, newton_ms = {}, None
+    for start in ("flat", "warm"):
+        x1 = torch.empty(M1.n, dtype=f64, device=dev)
+        if start == "flat":
+            M1.flat_start(x1)
+        else:
+            x1.copy_(xw)
+        lam = torch.zeros(M1.m, dtype=f64, device=dev)
+        A = al.AugLag(M1, rho=1000.0, lr=1e-3)
+        A.update(x1, lam, st)
+        traj = [float(st[1])]
+        lam.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(10):
+            for _ in range(10):
+                A.newton(x1, lam, 100)
+            A.update(x1, lam, st)
+            traj.append(float(st[1]))
+        torch.cuda.synchronize()
+        newton_ms = 1000.0 * (time.perf_counter() - t0) / 100
+        newton_runs[start] = traj
+        A.close()
     return {
         "grid": "2,000 buses, 2,600 branches, 500 generators, 1,400 loads (ratings secured by a DC dispatch)",
         "network": "3 layers, width 1024, GELU, BF16 with FP32 accumulation",
@@ -1020,6 +1078,11 @@ def warm_start_summary(torch, opf, synth, dev, epochs):
         "al_loop": {"problem": "held-out profile 0, single period", "rho": 100.0, "lr": 3e-3,
                     "inner_per_outer": 100, "max_row_violation_flat": al_runs["flat"],
                     "max_row_violation_warm": al_runs["warm"]},
+        "al_newton_loop": {"problem": "held-out profile 0, single period", "rho": 1000.0,
+                           "newton_steps_per_outer": 10, "cg_iterations": 100,
+                           "ms_per_newton_step": newton_ms,
+                           "max_row_violation_flat": newton_runs["flat"],
+                           "max_row_violation_warm": newton_runs["warm"]},
     }
 
 

@@ -64,7 +64,7 @@ int opf_al_update(opf_al *al, const double *d_x, double *d_lambda, double *d_sta
 
 /* One projected Newton-CG step of L(.; lambda) on d_x (a second-order inner
  * step that uses the Jacobian and Lagrangian-Hessian values of
- * include/opf.h): at x, with c = g(x), s = c + lambda / rho, mu = rho (s -
+ * include/opf.h): x is first projected onto [xl, xu] (in place); at x, with c = g(x), s = c + lambda / rho, mu = rho (s -
  * clip(s, gl, gu)) and D_i = 1 where s_i lies outside [gl_i, gu_i] (else 0),
  *   G = grad f(x) + J^T mu,  K = H(x; mu, sigma = 1) + rho J^T diag(D) J
  * (H from opf_eval_hess with the multipliers mu, J from opf_eval_jac; K is
@@ -75,7 +75,9 @@ int opf_al_update(opf_al *al, const double *d_x, double *d_lambda, double *d_sta
  * -G over the free entries, from p = 0, at most cg_iters iterations,
  * stopping at non-positive curvature (taking the first direction itself if
  * that happens at once) or when r^T z falls below 1e-24 of its first value.
- * Then x_t = clip(x + 2^-t p, xl, xu), t = 0..7, and x becomes the x_t of
+ * p is scaled by 1 / max_j |p_j| where that is above 1 (no entry moves by
+ * more than 1 in one step). Then x_t = clip(x + 2^-t p, xl, xu), t = 0..7,
+ * and x becomes the x_t of
  * the smallest t with L(x_t) <= L(x) + 1e-4 2^-t G^T p; else the x_t of
  * least L if below L(x); else x is left unchanged. delta starts at 1e-2
  * (again after opf_al_reset) and is kept on the device between steps:

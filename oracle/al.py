@@ -78,6 +78,7 @@ class NewtonOracle(AugLagOracle):
     the steps' order, with the C oracle's callbacks and scipy's sparse
     products (TEST INFRASTRUCTURE ONLY, as above):
 
+        x = clip(x, xl, xu),
         c = g(x), s = c + lambda / rho, d = s - clip(s, gl, gu), mu = rho d,
         D_i = 1 where s_i lies outside [gl_i, gu_i] (else 0),
         G = grad f(x) + J^T mu,
@@ -88,7 +89,9 @@ class NewtonOracle(AugLagOracle):
     (K + delta diag(M)) p = -G over the free entries, at most `cg_iters`
     iterations, stopping at non-positive curvature (the first direction
     itself is taken if that happens at once) or when r^T z falls below 1e-24
-    of its first value; then x_t = clip(x + a_t p) for a_t = 1, 1/2, ...,
+    of its first value; p scaled by 1 / max|p_j| where that is above 1 (no
+    entry moves by more than 1 in one step); then x_t = clip(x + a_t p) for
+    a_t = 1, 1/2, ...,
     1/128 and the largest a_t with L(x_t) <= L(x) + 1e-4 a_t G^T p is taken,
     else the a_t of least L(x_t) if it is below L(x), else no move. The
     Levenberg-Marquardt weight delta (1e-2 at first) is divided by 4 after a
@@ -122,11 +125,14 @@ class NewtonOracle(AugLagOracle):
         return G, K, D, F, Mj
 
     def newton_step(self, x, lam, cg_iters):
-        x = np.array(x, dtype=np.float64, copy=True)
+        x = np.clip(np.array(x, dtype=np.float64), self.xl, self.xu)
         G, K, _, F, Mj = self.system(x, lam)
         dl = self.delta
         Kd = K + sp.diags(dl * Mj)
         p = pcg(lambda v: Kd @ v, G, F, Mj * (1.0 + dl), cg_iters)
+        pm = float(np.max(np.abs(p))) if len(p) else 0.0
+        if pm > 1.0:  # no entry moves by more than 1 (per-unit) in one step
+            p = p * (1.0 / pm)
         L0 = self.value(x, lam)
         gp = float(G @ p)
         trials = [self.value(np.clip(x + 0.5 ** t * p, self.xl, self.xu), lam) for t in range(self.NLS)]

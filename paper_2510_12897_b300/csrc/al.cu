@@ -50,7 +50,7 @@ struct opf_al {
 };
 
 // the Newton step's device scalars (opf_al_newton)
-enum { CG_RZ = 0, CG_RZ0, CG_ALPHA, CG_BETA, CG_DONE, CG_GP, CG_COPY, CG_MOVE, CG_ASTAR, CG_DELTA, CG_N };
+enum { CG_RZ = 0, CG_RZ0, CG_ALPHA, CG_BETA, CG_DONE, CG_GP, CG_COPY, CG_MOVE, CG_ASTAR, CG_DELTA, CG_SCALE, CG_N };
 constexpr double kDelta0 = 1e-2;  // first Levenberg-Marquardt weight
 
 namespace {
@@ -538,7 +538,7 @@ __global__ void nt_dot_kernel(int64_t n, const double *a, const double *b, doubl
         part[blockIdx.x] = s;
 }
 
-enum { NT_INIT, NT_DQ, NT_RZ, NT_GP };
+enum { NT_INIT, NT_DQ, NT_RZ, NT_GP, NT_PMAX };
 
 // the sum of the partials (one warp, fixed order) and the step's scalar logic
 __global__ void nt_scalar_kernel(const double *part, int nparts, double *cgs, int mode, int k)
@@ -575,6 +575,46 @@ __global__ void nt_scalar_kernel(const double *part, int nparts, double *cgs, in
     } else {
         cgs[CG_GP] = v;
     }
+}
+
+// max |p_j| (block partials, then one warp): the step's cap, scale =
+// 1 / max|p_j| where that is above 1
+__global__ void nt_pmax_kernel(int64_t n, const double *p, double *part)
+{
+    __shared__ double red[32];
+    double v = 0.0;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+        v = fmax(v, fabs(p[j]));
+    const double b = block_max(v, red);
+    if (threadIdx.x == 0)
+        part[blockIdx.x] = b;
+}
+
+__global__ void nt_pscale_kernel(const double *part, int nparts, double *cgs)
+{
+    double v = 0.0;
+    for (int q = threadIdx.x; q < nparts; q += 32)
+        v = fmax(v, part[q]);
+    for (int off = 16; off; off >>= 1)
+        v = fmax(v, __shfl_down_sync(0xffffffffu, v, off));
+    if (threadIdx.x == 0)
+        cgs[CG_SCALE] = v > 1.0 ? 1.0 / v : 1.0;
+}
+
+__global__ void nt_scale_kernel(int64_t n, double *p, const double *cgs)
+{
+    const double c = cgs[CG_SCALE];
+    if (c == 1.0)
+        return;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+        p[j] = p[j] * c;
+}
+
+// x = clip(x, xl, xu)
+__global__ void nt_clip_kernel(int64_t n, double *x, const double *xl, const double *xu)
+{
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+        x[j] = fmin(fmax(x[j], xl[j]), xu[j]);
 }
 
 // trial point x_t = clip(x + a p, xl, xu)
@@ -722,6 +762,7 @@ int nt_step(opf_al *a, double *d_x, const double *d_lambda, int cg_iters, double
 {
     const int64_t n = a->n, m = a->m;
     const int gn = grid_of(n), gm = grid_of(m), np = a->nparts;
+    nt_clip_kernel<<<gn, 256, 0, s>>>(n, d_x, a->xl, a->xu);  // the step starts inside the bounds
     // base point: f, grad f, g, J; the multipliers mu and the statistics (L_0)
     EvalArgs e{d_x, nullptr, 1.0, a->obj, a->grad, a->c, a->jv, nullptr};
     int rc = launch_eval(*a->M, e, W_OBJ | W_GRAD | W_CONS | W_JAC, s);
@@ -752,6 +793,10 @@ int nt_step(opf_al *a, double *d_x, const double *d_lambda, int cg_iters, double
     rc = al_check(cudaGetLastError(), "CG kernels");
     if (rc)
         return rc;
+    // no entry moves by more than 1 (per-unit) in one step
+    nt_pmax_kernel<<<np, 256, 0, s>>>(n, a->p, a->part);
+    nt_pscale_kernel<<<1, 32, 0, s>>>(a->part, np, a->cgs);
+    nt_scale_kernel<<<gn, 256, 0, s>>>(n, a->p, a->cgs);
     nt_dot_kernel<<<np, 256, 0, s>>>(n, a->G, a->p, a->part, np);
     nt_scalar_kernel<<<1, 32, 0, s>>>(a->part, np, a->cgs, NT_GP, 0);
     for (int t = 0; t < kNls && !rc; t++) {

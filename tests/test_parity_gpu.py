@@ -304,23 +304,32 @@ def test_case10k_full(torch, oracle_mod):
     check_against_oracle(O, run_all(torch, M, x, lam, 1.0, best), x, lam, 1.0, "tuned ")
 
 
+# one persistent kernel per evaluation of a whole batch: the fused layout
+# with generator blocks and packed warps looping over the grid
+FUSED_PERSISTENT = dict(branch_block=128, bus_block=64, branch_ctas_per_sm=0, bus_ctas_per_sm=16, bus_order=3)
+
+
 @pytest.mark.slow
 def test_mp2k_96_full(torch, oracle_mod):
-    """2,000-bus grid over 96 periods with ramp rows, every entry."""
+    """2,000-bus grid over 96 periods with ramp rows, every entry, with the
+    default two-kernel shape and as one persistent kernel per evaluation."""
     g = synth.mp2k()
     M, O = both(torch, oracle_mod, g)
     x, lam = next(points(g, M.m, 1, seed=11))
     check_against_oracle(O, run_all(torch, M, x, lam, 1.0), x, lam, 1.0)
+    check_against_oracle(O, run_all(torch, M, x, lam, 1.0, FUSED_PERSISTENT), x, lam, 1.0, "one kernel ")
 
 
 @pytest.mark.slow
 def test_sc1k_501_full(torch, oracle_mod):
     """1,000-bus base case plus 500 N-1 contingencies (uneven sizes) with
-    linking rows, every entry."""
+    linking rows, every entry, with the default two-kernel shape and as one
+    persistent kernel per evaluation."""
     insts = synth.sc1k()
     M, O = both(torch, oracle_mod, insts, link=0.2)
     x, lam = next(points(insts, M.m, 1, seed=12))
     check_against_oracle(O, run_all(torch, M, x, lam, 1.0), x, lam, 1.0)
+    check_against_oracle(O, run_all(torch, M, x, lam, 1.0, FUSED_PERSISTENT), x, lam, 1.0, "one kernel ")
 
 
 # ------------------------------------------------ trig and large angles --
