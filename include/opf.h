@@ -193,38 +193,55 @@ int opf_structure_create(const opf_network *nets, int32_t ninst, const opf_batch
 
 int opf_model_destroy(opf_model *model);
 
-/* n variables, m constraints, Jacobian and Hessian (lower) nonzeros. */
+/* n variables, m constraints, Jacobian and Hessian (lower) nonzeros of the
+ * model of Listing 3 (Sec. III-B): the sizes of the arrays the callbacks of
+ * Listing 1 (Sec. II-B) fill. */
 int opf_dims(const opf_model *model, int64_t *n, int64_t *m, int64_t *nnz_jac,
              int64_t *nnz_hess);
 
-/* Pattern of kind OPF_JAC or OPF_HESS into HOST arrays of nnz entries each. */
+/* Pattern of kind OPF_JAC or OPF_HESS into HOST arrays of nnz entries each
+ * (the structure behind jac! and hess! of Listing 1; the automatic
+ * sparsity detection of Sec. II-B, done once here from the model's layout): (row,
+ * col) pairs, 0-based, sorted row-major, the Hessian as its lower triangle.
+ * The indices are int64 so that batches beyond 2^31 entries need no second
+ * call; every value array of the eval calls is in this order. */
 int opf_sparsity(const opf_model *model, int32_t kind, int64_t *rows, int64_t *cols);
 
 /* Variable and constraint bounds into HOST arrays (n and m entries);
  * infinite bounds are +-INFINITY. */
 int opf_bounds(const opf_model *model, double *xl, double *xu, double *gl, double *gu);
 
-/* Objective (one double, d_obj) and gradient (n) at d_x (n). Either output
- * may be NULL. The objective is a fixed-order (deterministic) reduction. */
+/* Objective (one double, d_obj) and gradient (n) at d_x (n): obj and grad!
+ * of Listing 1, the generator cost of Listing 3 summed over generators,
+ * periods and instances. Either output may be NULL. The objective is a
+ * fixed-order (deterministic) reduction. */
 int opf_eval_obj_grad(opf_model *model, const double *d_x, double *d_obj, double *d_grad,
                       void *stream);
 
-/* Constraint values g(x) into d_c (m). */
+/* Constraint values g(x) into d_c (m): cons! of Listing 1, the rows of
+ * Listing 3 (reference angle, flow rows, angle difference, P and Q balance
+ * with their constraint! augmentations, thermal) and the ramp rows of
+ * Listings 6-7 (Sec. III-C-2), in the order and index rule of Listing 10. */
 int opf_eval_cons(opf_model *model, const double *d_x, double *d_c, void *stream);
 
-/* Jacobian values (nnz_jac) in pattern order. */
+/* Jacobian values (nnz_jac) in pattern order: jac! of Listing 1. */
 int opf_eval_jac(opf_model *model, const double *d_x, double *d_jvals, void *stream);
 
-/* Lagrangian Hessian values (nnz_hess) at d_x (n), d_lambda (m), obj_weight. */
+/* Values (nnz_hess, lower triangle, pattern order) of obj_weight * Hessian
+ * of f plus sum_i lambda_i * Hessian of g_i at d_x (n), d_lambda (m):
+ * hess!(x, l, H; obj_weight) of Listing 1. */
 int opf_eval_hess(opf_model *model, const double *d_x, const double *d_lambda,
                   double obj_weight, double *d_hvals, void *stream);
 
-/* Fused Jacobian and Hessian: one pass over the network. */
+/* Fused Jacobian and Hessian (opf_eval_jac and opf_eval_hess in one pass
+ * over the network): the pair a Newton-type solver requests each iteration
+ * (Sec. IV, the callbacks inside the paper's solvers). */
 int opf_eval_jac_hess(opf_model *model, const double *d_x, const double *d_lambda,
                       double obj_weight, double *d_jvals, double *d_hvals, void *stream);
 
-/* Every callback in one pass; any output may be NULL (skipped). d_lambda may
- * be NULL only if d_hvals is NULL. */
+/* Every callback of Listing 1 (obj, grad!, cons!, jac!, hess!)
+ * in one pass; any output may be NULL (skipped). d_lambda may be NULL only
+ * if d_hvals is NULL. */
 int opf_eval_all(opf_model *model, const double *d_x, const double *d_lambda, double obj_weight,
                  double *d_obj, double *d_grad, double *d_c, double *d_jvals, double *d_hvals,
                  void *stream);
