@@ -118,12 +118,13 @@ def test_al_loop_reduces_violation(torch):
     A.close()
 
 
-@pytest.mark.parametrize("case", ["case30g", "mp30", "n1_30"])
+@pytest.mark.parametrize("case", ["case30g", "mp30", "n1_30", "rect30g", "stor30"])
 def test_newton_steps_match_oracle(torch, oracle_mod, case):
     """Four projected Newton-CG steps (opf_al_newton: Jacobian and
     Lagrangian-Hessian values, Jacobi-preconditioned CG with a Levenberg-
     Marquardt weight kept on the device, eight-length backtracking) from the
-    flat start with random multipliers, against the oracle taking the same
+    flat start with random multipliers (polar and rectangular forms, a
+    multi-period model, an N-1 batch, storage units), against the oracle taking the same
     steps with scipy's sparse products: the CG direction of each step, the
     iterates and the statistics, at 8 CG iterations per step. The two sides
     sum in different orders, and CG's loss of orthogonality amplifies that
@@ -135,9 +136,13 @@ def test_newton_steps_match_oracle(torch, oracle_mod, case):
     from paper_2510_12897_b300 import al
     g = {"case30g": lambda: synth.case30(general=True),
          "mp30": lambda: synth.multi_period(synth.case30(general=True), 3, seed=5, ramp_ratio=0.2),
-         "n1_30": lambda: synth.contingencies(synth.case30(general=True), 3, seed=4)}[case]()
-    M = opf.Model(g)
-    O = oracle_mod.Oracle(g)
+         "n1_30": lambda: synth.contingencies(synth.case30(general=True), 3, seed=4),
+         "rect30g": lambda: synth.case30(general=True),
+         "stor30": lambda: synth.with_storage(synth.multi_period(synth.case30(general=True), 3, seed=5,
+                                                                ramp_ratio=0.2))}[case]()
+    opts = dict(form="rect") if case == "rect30g" else {}
+    M = opf.Model(g, **opts)
+    O = oracle_mod.Oracle(g, **opts)
     dev = torch.device("cuda")
     x = torch.empty(M.n, dtype=torch.float64, device=dev)
     M.flat_start(x)
