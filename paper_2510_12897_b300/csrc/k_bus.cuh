@@ -294,10 +294,20 @@ __device__ __forceinline__ void fused_rect_arc(const KParams &P, const InstDev &
 //
 // With two roles (branch_occupancy 2 in this mode) each packed warp of buses
 // is taken by two warps, one writing the rows and the Jacobian (and the
-// gradient zeros), the other the Hessian; both evaluate the shared
-// trigonometry, so the dependent chain of each is shorter at the cost of
-// that duplicated work.
-template <bool CONS, bool JAC, bool HESS, bool ONE, bool RECT = false>
+// gradient zeros), the other the Hessian, so the dependent chain of each is
+// shorter. In blocks of one warp both evaluate the shared trigonometry.
+// Two-role exchange (polar, blocks of two warps or more, where both warps of
+// a pair are in one block): the rows warp of a pair publishes each lane's
+// sine and cosine in shared memory and raises the pair's flag; the Hessian
+// warp waits for the flag (bounded: on a timeout it computes them itself,
+// with the same result) instead of recomputing them. One slot per pair of a
+// block (at most kBusBlockMax / 64 pairs); the flags are cleared at the
+// block's start.
+__shared__ double2 g_role_sc[kBusBlockMax / 64][32];
+__shared__ int g_role_flag[kBusBlockMax / 64];
+constexpr int kRoleWaitPolls = 1 << 20;
+
+template <bool CONS, bool JAC, bool HESS, bool ONE, bool RECT = false, int ROLE = 0>
 __device__ void fused_bus_warp(const KParams &P, const int64_t w, const bool grad_here)
 {
     const DevArrays &d = P.d;
@@ -424,10 +434,38 @@ __device__ void fused_bus_warp(const KParams &P, const int64_t w, const bool gra
         if (has)
             fused_rect_arc<CONS, JAC, HESS>(P, I, e, k, t, own, far, br, jb, Yo, Yx, Yf, r2, tno, tnf, vao, vax, vo,
                                             vx, po, qo, mP, mQ, ma, lth, fP, fQ, fa, grad_here, h1, h2, h3);
-    } else if (has) {
+    } else {
         const double dlt = vao - vax;  // this end's angle
-        double sn, cs_;
-        sincos_tab(dlt, d.trig, &sn, &cs_);
+        double sn = 0.0, cs_ = 1.0;
+        if (ROLE == 1) {  // rows warp of a pair: compute and publish
+            if (has)
+                sincos_tab(dlt, d.trig, &sn, &cs_);
+            const int pair = (int)(threadIdx.x >> 6);
+            g_role_sc[pair][lane] = make_double2(sn, cs_);
+            __syncwarp();
+            if (lane == 0)
+                cuda::atomic_ref<int, cuda::thread_scope_block>(g_role_flag[pair]).store(1, cuda::memory_order_release);
+        } else if (ROLE == 2) {  // Hessian warp of a pair: wait for the rows warp's
+            const int pair = (int)(threadIdx.x >> 6);
+            int ok = 0;
+            if (lane == 0) {
+                cuda::atomic_ref<int, cuda::thread_scope_block> f(g_role_flag[pair]);
+                for (int i = 0; i < kRoleWaitPolls && !ok; i++)
+                    ok = f.load(cuda::memory_order_acquire);
+            }
+            ok = __shfl_sync(full, ok, 0);
+            __syncwarp();  // orders the lanes' reads after lane 0's acquire
+            if (ok) {
+                const double2 v = g_role_sc[pair][lane];
+                sn = v.x;
+                cs_ = v.y;
+            } else if (has) {
+                sincos_tab(dlt, d.trig, &sn, &cs_);
+            }
+        } else if (has) {
+            sincos_tab(dlt, d.trig, &sn, &cs_);
+        }
+        if (has) {
         const double vft = vo * vx;
         const double A = fma(Yx.x, cs_, Yx.y * sn);
         const double B = fma(Yx.x, sn, neg(Yx.y * cs_));
@@ -485,6 +523,7 @@ __device__ void fused_bus_warp(const KParams &P, const int64_t w, const bool gra
             P.grad[I.x0 + ip + arc] = 0.0;
             P.grad[I.x0 + iq + arc] = 0.0;
         }
+        }  // has
     }
 
     // segmented sums over the lanes: buses (a bus starts at its head lane;
@@ -645,10 +684,21 @@ __global__ void __launch_bounds__(kBusBlockMax) bus_kernel(const KParams P)
                 const int64_t wr = (int64_t)(blockIdx.x - P.split_tblocks) * (blockDim.x >> 5) + (threadIdx.x >> 5);
                 if constexpr (HESS && (CONS || JAC)) {
                     if (P.fuse_roles) {  // even warps: rows and Jacobian; odd warps: Hessian
-                        if (wr & 1)
+                        // blocks of at least two warps hold both warps of a pair: the
+                        // Hessian warp takes the rows warp's sine and cosine (polar)
+                        if (!RECT && blockDim.x >= 64) {
+                            if (threadIdx.x < kBusBlockMax / 64)
+                                g_role_flag[threadIdx.x] = 0;
+                            __syncthreads();
+                            if (wr & 1)
+                                fused_bus_warp<false, false, true, ONE, RECT, 2>(P, wr >> 1, false);
+                            else
+                                fused_bus_warp<CONS, JAC, false, ONE, RECT, 1>(P, wr >> 1, true);
+                        } else if (wr & 1) {
                             fused_bus_warp<false, false, true, ONE, RECT>(P, wr >> 1, false);
-                        else
+                        } else {
                             fused_bus_warp<CONS, JAC, false, ONE, RECT>(P, wr >> 1, true);
+                        }
                         return;
                     }
                 }

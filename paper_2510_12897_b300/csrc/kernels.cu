@@ -78,6 +78,8 @@
 // Hessian is constant: Df on (vr_f, vr_f) and (vi_f, vi_f), Dt likewise at
 // the to-end, aR on (vr_f, vr_t) and (vi_f, vi_t), aI on (vi_f, vr_t) and
 // -aI on (vr_f, vi_t).
+#include <cuda/atomic>
+
 #include "model.h"
 
 namespace opf {
@@ -205,7 +207,24 @@ int launch_all(Model &M, const EvalArgs &a, unsigned what, cudaStream_t s, int p
     P.want_grad = (what & W_GRAD) ? 1 : 0;
     P.want_obj = (what & W_OBJ) ? 1 : 0;
     const opf_launch &L = M.launch;
-    const int bu = L.bus_block > kBusBlockMax ? kBusBlockMax : L.bus_block;
+    // bus_order 3: the fused evaluation where it applies (no storage,
+    // at most 32 arc slots per bus), one kernel per evaluation (launched
+    // with the bus phase; the branch phase alone launches nothing)
+    const bool fused = L.bus_order == 3 && M.fuse_ok;
+    // fused, branch_occupancy 2: two roles (a rows warp and a Hessian warp
+    // per packed warp) where there is both a Hessian and rows or Jacobian to
+    // write; for the Jacobian and Hessian alone only while the packed warps
+    // fit one per SM sub-partition (beyond that the operands both warps form
+    // cost more FP64 issue than the shorter chains save)
+    const bool fill = M.npack_items <= 4 * (int64_t)M.num_sms;
+    const bool roles = fused && L.branch_occupancy == 2 && H && (C || (J && fill));
+    int bu = L.bus_block > kBusBlockMax ? kBusBlockMax : L.bus_block;
+    // the other calls of a two-role shape with arc work (rows, Jacobian or
+    // Hessian) run one warp per packed warp in blocks of half the size: as
+    // many packed warps per block (the objective and gradient alone keep
+    // the block: its packed warps only write gradient zeros)
+    if (fused && L.branch_occupancy == 2 && !roles && (C || J || H) && bu >= 64)
+        bu /= 2;
     const int gb = grid_for(M.nbr_items, L.branch_block, L.branch_ctas_per_sm, M.num_sms, 0);
     const int cap = max_part < M.max_part ? max_part : M.max_part;
     // the bus kernel pads the generator items to whole blocks (when they fit
@@ -227,17 +246,12 @@ int launch_all(Model &M, const EvalArgs &a, unsigned what, cudaStream_t s, int p
     // light buses a thread each in the first blocks, heavy buses a warp each
     // in the blocks after them; elsewhere buses in id order
     const bool splitb = L.bus_order >= 2 && M.split_ok && (phases & 2);
-    // bus_order 3: the fused evaluation where it applies (no storage,
-    // at most 32 arc slots per bus), one kernel per evaluation (launched
-    // with the bus phase; the branch phase alone launches nothing)
-    const bool fused = L.bus_order == 3 && M.fuse_ok;
     int gu_all = gu;
     if (fused) {
         const int tb = grid_for(gpad, bu, L.bus_ctas_per_sm, M.num_sms, cap);
         P.split_tblocks = tb;
         P.npack_items = M.npack_items;
-        // two roles only where there is both a Hessian and rows or Jacobian to write
-        P.fuse_roles = L.branch_occupancy == 2 && H && (C || J) ? 1 : 0;
+        P.fuse_roles = roles ? 1 : 0;
         const int64_t warps = M.npack_items * (P.fuse_roles ? 2 : 1);
         gu_all = tb + (int)((warps + bu / 32 - 1) / (bu / 32));
     } else if (splitb) {

@@ -536,7 +536,8 @@ def test_fused_evaluation(torch, oracle_mod, which):
     one lane per arc slot, per-bus and per-group segmented scans): every
     output against the oracle with bus blocks of 32 to 128, a persistent
     generator grid, and one or two warps (rows and Jacobian; Hessian) per
-    packed warp; single instances, a bus without arcs, an N-1 batch with
+    packed warp (in blocks of one warp each computes the sine and cosine; in
+    larger blocks the Hessian warp takes the rows warp's); single instances, a bus without arcs, an N-1 batch with
     linking rows, one with reserve rows and corrective ratios, the 10k grid,
     multiple periods with ramp rows, and a hub beyond 32 slots (which runs
     the split bus phase instead)."""
@@ -552,7 +553,7 @@ def test_fused_evaluation(torch, oracle_mod, which):
     opts = dict(link_ratios=[0.0] + [0.05 * k for k in range(1, 10)], reserve=0.1) if which == "reserve" else {}
     M, O = both(torch, oracle_mod, g, link=link, **opts)
     for k, (x, lam) in enumerate(points(g, M.m, 2, seed=39)):
-        for bu, cu, occ in ((32, 0, 0), (128, 2, 0), (64, 0, 2), (128, 4, 2)):
+        for bu, cu, occ in ((32, 0, 0), (128, 2, 0), (32, 0, 2), (64, 0, 2), (128, 4, 2)):
             launch = dict(FUSED, bus_block=bu, bus_ctas_per_sm=cu, branch_occupancy=occ)
             sigma = 0.0 if k else 0.8
             check_against_oracle(O, run_all(torch, M, x, lam, sigma, launch), x, lam, sigma,
@@ -593,6 +594,26 @@ def test_fused_separate_callbacks(torch, oracle_mod, occ):
     M.eval_phases(2, dx, c=c2)  # the bus phase: the whole evaluation
     torch.cuda.synchronize()
     np.testing.assert_array_equal(host(c2), fused["c"])
+
+
+def test_fused_roles_rule_10k(torch):
+    """With two roles on the 10k grid (more packed warps than SM sub-
+    partitions) the all-callback evaluation runs two warps per packed warp
+    and the Jacobian + Hessian call one: both write the same values, bit for
+    bit (the all-callback values are checked against the oracle in
+    test_fused_evaluation)."""
+    g = synth.case10k()
+    M = opf.Model(g)
+    x, lam = next(points(g, M.m, 1, seed=41))
+    for occ in (0, 2):
+        fused = run_all(torch, M, x, lam, 0.7, dict(FUSED, bus_block=128, branch_occupancy=occ))
+        dx, dl = dev(torch, x), dev(torch, lam)
+        jv = torch.empty(M.nnzj, dtype=torch.float64, device="cuda")
+        hv = torch.empty(M.nnzh, dtype=torch.float64, device="cuda")
+        M.eval_jac_hess(dx, dl, 0.7, jv, hv)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(host(jv), fused["jv"], err_msg=f"occ{occ} jv")
+        np.testing.assert_array_equal(host(hv), fused["hv"], err_msg=f"occ{occ} hv")
 
 
 @pytest.mark.parametrize("which", ["case30g", "isolated", "batch_links", "reserve", "mp30", "case10k", "rect30g",
