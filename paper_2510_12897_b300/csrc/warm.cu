@@ -26,26 +26,59 @@ namespace {
 //
 // C[M x N] = A[M x K] B[N x K]^T with BF16 operands and FP32 accumulation on
 // the 5th-generation tensor cores. Both operands are row-major with K
-// contiguous (the backward pass feeds transposed copies). One CTA of 128
-// threads per 128 x 128 tile of C:
-//   warp 0, one lane   TMA producer: 128 x 64 tiles of A and B (128-byte
-//                      swizzle) into a 3-stage ring, completion counted in
-//                      bytes on the stage's "full" mbarrier;
-//   warp 1, one lane   MMA issuer: per stage four tcgen05.mma (M 128, N 128,
-//                      K 16) from shared-memory descriptors into a 128-column
-//                      FP32 accumulator in tensor memory; tcgen05.commit
-//                      frees the stage ("empty") and finally signals "done";
-//   warps 0-3          epilogue: tcgen05.ld of their 32 accumulator lanes,
-//                      16 columns at a time, bias / GELU / GELU' in FP32,
-//                      stores.
-// Every wait on an mbarrier gives up after a bounded number of polls and
-// records the timeout in a device flag the host reads (no unbounded spin).
-// M and N must be multiples of 128, K of 64.
+// contiguous (the backward pass feeds transposed copies). Persistent: one
+// CTA of 192 threads per SM walks the 128 x BN tiles of C (BN 256, or 128
+// where N is not a multiple of 256), M-blocks fastest:
+//   warp 0, one lane   TMA producer: 128 x 64 tiles of A and BN x 64 tiles
+//                      of B (128-byte swizzle) into a ring of stages across
+//                      the tiles, completion counted in bytes on the
+//                      stage's "full" mbarrier;
+//   warp 1, one lane   MMA issuer: per stage four tcgen05.mma (M 128, N BN,
+//                      K 16) from shared-memory descriptors into one of two
+//                      BN-column FP32 accumulators in tensor memory, tile
+//                      after tile alternating; tcgen05.commit frees the
+//                      stage ("empty") and, after a tile's last stage,
+//                      hands the accumulator to the epilogue ("tfull");
+//   warps 2-5          epilogue: tcgen05.ld of their 32 accumulator lanes
+//                      (warp w reads lanes 32 (w mod 4) and up), 32 columns
+//                      at a time, bias / GELU / GELU' in FP32, stores; then
+//                      the accumulator is free again ("tempty"), so one
+//                      tile's epilogue runs under the next tile's MMAs.
+// Every wait on an mbarrier gives up after a bounded number of polls, or
+// once another role gave up, and a timeout is recorded in a device flag the
+// host reads (no unbounded spin). M must be a multiple of 128, N of 128, K
+// of 64.
 
-constexpr int UBM = 128, UBN = 128, UBK = 64, USTAGES = 3;
-constexpr int UTILE = UBM * UBK * 2;                   // bytes of one A or B stage tile
-constexpr int USMEM = 2 * USTAGES * UTILE + 1024 + 256;  // tiles, alignment slack, barriers
+constexpr int UBM = 128, UBK = 64;
 constexpr uint32_t kWaitPolls = 1u << 22;
+
+// the shared-memory plan of a tile width BN: the stage ring (A then B tile
+// per stage), then the mbarriers full[S], empty[S], tfull[2], tempty[2],
+// quiet, the tensor-memory address slot, and the epilogue warps' staging
+// blocks
+template <int BN>
+struct GemmCfg {
+    static constexpr int ATILE = UBM * UBK * 2;  // bytes of an A stage tile
+    static constexpr int BTILE = BN * UBK * 2;   // bytes of a B stage tile
+    static constexpr int STAGE = ATILE + BTILE;
+    static constexpr int STAGES = BN == 256 ? 4 : 6;  // 192 KB of stages
+    static constexpr int NBAR = 2 * STAGES + 5;
+    static constexpr int STG_LD = 36;  // staging row stride in floats (16-byte rows, no bank conflicts)
+    static constexpr int STG = 4 * 32 * STG_LD * 4;  // one 32 x 32 FP32 block per epilogue warp
+    static constexpr int SMEM = STAGES * STAGE + 1024 + 8 * NBAR + 32 + STG;  // + alignment slack
+    static constexpr uint32_t TCOLS = 2 * BN;  // two accumulators
+    // instruction descriptor of kind::f16: D FP32, A and B BF16, both
+    // K-major, N >> 3 at bit 17, M >> 4 at bit 24
+    static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                                      ((uint32_t)(UBM >> 4) << 24);
+};
+
+// a tensor map with the height of its box (128 rows for A operands; 128 or
+// 256 for B operands: the tile width BN of the GEMM that reads it)
+struct GMap {
+    CUtensorMap map;
+    int box_rows;
+};
 
 __device__ int g_umma_timeout;  // set when a bounded wait gave up
 
@@ -92,6 +125,31 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
     return false;
 }
 
+// mbar_wait that also gives up (without recording a timeout) once another
+// role of the CTA has raised the abort flag
+__device__ __forceinline__ bool mbar_wait_live(uint32_t bar, uint32_t parity, volatile int *abort_flag)
+{
+    for (uint32_t i = 0; i < kWaitPolls; i++) {
+        uint32_t ok;
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok)
+            return true;
+        if (*abort_flag)
+            return false;
+    }
+    atomicExch(&g_umma_timeout, 1);
+    return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar)
 {
     asm volatile(
@@ -109,15 +167,10 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr)
            ((uint64_t)1u << 46) | ((uint64_t)2u << 61);
 }
 
-// instruction descriptor of kind::f16: D FP32, A and B BF16, both K-major,
-// N = 128 (N >> 3 at bit 17), M = 128 (M >> 4 at bit 24)
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(UBN >> 3) << 17) |
-                            ((uint32_t)(UBM >> 4) << 24);
-
-__device__ __forceinline__ void umma(uint32_t tmem, uint64_t da, uint64_t db, uint32_t acc)
+__device__ __forceinline__ void umma(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc)
 {
     asm volatile("{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(tmem),
-                 "l"(da), "l"(db), "r"(kIdesc), "r"(acc));
+                 "l"(da), "l"(db), "r"(idesc), "r"(acc));
 }
 
 __device__ __forceinline__ void umma_commit(uint32_t bar)
@@ -125,23 +178,34 @@ __device__ __forceinline__ void umma_commit(uint32_t bar)
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t r[16])
+// 32 consecutive accumulator columns of the warp's 32 lanes, one per thread
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t r[32])
 {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// GELU, tanh form, and its derivative
+// GELU, tanh form: 0.5 z (1 + tanh u) = z / (1 + exp(-2u)), u = k0 (z + k1
+// z^3), the logistic form (no cancellation for negative z); the fast
+// exponential and division keep its relative error near 1e-6, far below the
+// BF16 rounding of the activation it feeds (the argument is clamped at 80 so
+// that the denominator stays finite; there the result is below 1e-34 |z|)
 __device__ __forceinline__ float gelu(float z)
 {
     const float k0 = 0.7978845608028654f, k1 = 0.044715f;
-    return 0.5f * z * (1.0f + tanhf(k0 * (z + k1 * z * z * z)));
+    const float m2u = -2.0f * k0 * fmaf(k1 * z, z * z, z);
+    return __fdividef(z, 1.0f + __expf(fminf(m2u, 80.0f)));
 }
 
+// its derivative, from the tanh form (FP32 library tanh: it feeds FP32
+// gradients)
 __device__ __forceinline__ float gelu_grad(float z)
 {
     const float k0 = 0.7978845608028654f, k1 = 0.044715f;
@@ -149,38 +213,46 @@ __device__ __forceinline__ float gelu_grad(float z)
     return 0.5f * (1.0f + t) + 0.5f * z * (1.0f - t * t) * k0 * (1.0f + 3.0f * k1 * z * z);
 }
 
-__global__ void __launch_bounds__(128) umma_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
-                                                        const __grid_constant__ CUtensorMap tmB, const GemmArgs g)
+template <int BN>
+__global__ void __launch_bounds__(192, 1) umma_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                           const __grid_constant__ CUtensorMap tmB, const GemmArgs g)
 {
+    using C = GemmCfg<BN>;
     extern __shared__ uint8_t smem_raw[];
+    // set by a role whose bounded wait gave up: every role stops issuing,
+    // and the epilogue writes nothing more
+    __shared__ int s_abort;
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;  // 1024-byte aligned tiles
-    const uint32_t sA = base, sB = base + USTAGES * UTILE;
-    const uint32_t bars = sB + USTAGES * UTILE;   // full[S], empty[S], done: 8 bytes each
-    const uint32_t slot = bars + 8 * (2 * USTAGES + 1);
+    const uint32_t bars = base + C::STAGES * C::STAGE;
+    const uint32_t slot = bars + 8u * C::NBAR;
     uint32_t *slot_ptr = reinterpret_cast<uint32_t *>(smem_raw + (slot - raw));
+    const uint32_t stg_at = (slot + 4u + 15u) & ~15u;  // after the slot, 16-byte aligned
+    float *stage_f = reinterpret_cast<float *>(smem_raw + (stg_at - raw));
     auto full = [&](int st) { return bars + 8u * st; };
-    auto empty = [&](int st) { return bars + 8u * (USTAGES + st); };
-    const uint32_t done = bars + 8u * (2 * USTAGES);
+    auto empty = [&](int st) { return bars + 8u * (C::STAGES + st); };
+    auto tfull = [&](int a) { return bars + 8u * (2 * C::STAGES + a); };
+    auto tempty = [&](int a) { return bars + 8u * (2 * C::STAGES + 2 + a); };
+    const uint32_t quiet = bars + 8u * (2 * C::STAGES + 4);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int bm = blockIdx.y * UBM, bn = blockIdx.x * UBN;
-    const int nk = g.K / UBK;
-    // set by the producer or the MMA issuer when one of its bounded waits
-    // gives up: both stop issuing, and the epilogue writes nothing
-    __shared__ int s_abort;
+    const int mt = g.M / UBM, tiles = mt * (g.N / BN), nk = g.K / UBK;
 
     if (threadIdx.x == 0) {
         s_abort = 0;
-        for (int st = 0; st < USTAGES; st++) {
+        for (int st = 0; st < C::STAGES; st++) {
             mbar_init(full(st), 1);
             mbar_init(empty(st), 1);
         }
-        mbar_init(done, 1);
+        for (int a = 0; a < 2; a++) {
+            mbar_init(tfull(a), 1);
+            mbar_init(tempty(a), 128);  // every epilogue thread arrives
+        }
+        mbar_init(quiet, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) {  // 128 accumulator columns
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(UBN));
+    if (warp == 1) {  // two accumulators of BN columns
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(C::TCOLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -189,109 +261,149 @@ __global__ void __launch_bounds__(128) umma_gemm_kernel(const __grid_constant__ 
     const uint32_t tmem = *slot_ptr;
     volatile int *abort_flag = &s_abort;
 
-    int issued = 0;  // producer: k tiles whose loads were issued
+    int issued = 0;  // producer: stage loads issued (k steps over all its tiles)
     if (warp == 0) {
         if (lane == 0) {  // producer
-            for (int kt = 0; kt < nk; kt++) {
-                const int st = kt % USTAGES, round = kt / USTAGES;
-                if (*abort_flag)
-                    break;
-                if (round > 0 && !mbar_wait(empty(st), (round - 1) & 1)) {
-                    *abort_flag = 1;
-                    break;
+            int it = 0;
+            bool stop = false;
+            for (int tile = blockIdx.x; tile < tiles && !stop; tile += gridDim.x) {
+                const int bm = (tile % mt) * UBM, bn = (tile / mt) * BN;
+                for (int kt = 0; kt < nk; kt++, it++) {
+                    const int st = it % C::STAGES, round = it / C::STAGES;
+                    if (*abort_flag ||
+                        (round > 0 && !mbar_wait_live(empty(st), (round - 1) & 1, abort_flag))) {
+                        stop = true;
+                        break;
+                    }
+                    const uint32_t sa = base + st * C::STAGE;
+                    mbar_expect_tx(full(st), C::STAGE);
+                    tma_load_2d(sa, &tmA, kt * UBK, bm, full(st));
+                    tma_load_2d(sa + C::ATILE, &tmB, kt * UBK, bn, full(st));
+                    issued = it + 1;
                 }
-                mbar_expect_tx(full(st), 2 * UTILE);
-                tma_load_2d(sA + st * UTILE, &tmA, kt * UBK, bm, full(st));
-                tma_load_2d(sB + st * UTILE, &tmB, kt * UBK, bn, full(st));
-                issued = kt + 1;
             }
+            if (stop)
+                *abort_flag = 1;
         }
         __syncwarp();
     } else if (warp == 1) {
         if (lane == 0) {  // MMA issuer
-            for (int kt = 0; kt < nk; kt++) {
-                const int st = kt % USTAGES, round = kt / USTAGES;
-                if (*abort_flag)
-                    break;
-                if (!mbar_wait(full(st), round & 1)) {
-                    *abort_flag = 1;
+            int it = 0, j = 0;
+            bool stop = false;
+            for (int tile = blockIdx.x; tile < tiles && !stop; tile += gridDim.x, j++) {
+                const int acc = j & 1, use = j >> 1;
+                // the accumulator's previous tile must have left tensor memory
+                if (use > 0 && !mbar_wait_live(tempty(acc), (use - 1) & 1, abort_flag)) {
+                    stop = true;
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t d = tmem + (uint32_t)(acc * BN);
+                for (int kt = 0; kt < nk; kt++, it++) {
+                    const int st = it % C::STAGES, round = it / C::STAGES;
+                    if (!mbar_wait_live(full(st), round & 1, abort_flag)) {
+                        stop = true;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t sa = base + st * C::STAGE, sb = sa + C::ATILE;
 #pragma unroll
-                for (int k = 0; k < UBK / 16; k++)  // 16 elements = 32 bytes along K per MMA
-                    umma(tmem, smem_desc(sA + st * UTILE + 32 * k), smem_desc(sB + st * UTILE + 32 * k),
-                         (kt | k) != 0);
-                umma_commit(empty(st));
+                    for (int k = 0; k < UBK / 16; k++)  // 16 elements = 32 bytes along K per MMA
+                        umma(d, smem_desc(sa + 32 * k), smem_desc(sb + 32 * k), C::IDESC, (kt | k) != 0);
+                    umma_commit(empty(st));
+                }
+                if (!stop)
+                    umma_commit(tfull(acc));
             }
-            // also after a stop: done then arrives once every MMA issued
-            // above has completed, so the accumulator is quiet before dealloc
-            umma_commit(done);
+            if (stop)
+                *abort_flag = 1;
+            // also after a stop: quiet then arrives once every MMA issued
+            // above has completed, so tensor memory is idle before dealloc
+            umma_commit(quiet);
         }
         __syncwarp();
+    } else {  // epilogue: warp w reads accumulator lanes 32 (w mod 4) .. + 31
+        const int q = warp & 3;
+        int j = 0;
+        for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, j++) {
+            const int acc = j & 1, use = j >> 1;
+            if (!mbar_wait_live(tfull(acc), use & 1, abort_flag)) {
+                *abort_flag = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int bm = (tile % mt) * UBM, bn = (tile / mt) * BN;
+            const uint32_t tb = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * BN);
+            // each 32 x 32 block: thread = row out of tensor memory, into
+            // this warp's staging block, back out as 8 threads per 128-byte
+            // row segment (4 rows per instruction) for the epilogue and
+            // coalesced stores
+            float *stg = stage_f + (warp - 2) * (32 * C::STG_LD);
+            const int cg = lane & 7, rs = lane >> 3;
+#pragma unroll 1
+            for (int c = 0; c < BN / 32; c++) {
+                uint32_t r[32];
+                tmem_ld32(tb + 32 * c, r);
+#pragma unroll
+                for (int qq = 0; qq < 8; qq++)
+                    *reinterpret_cast<float4 *>(stg + lane * C::STG_LD + 4 * qq) =
+                        make_float4(__uint_as_float(r[4 * qq]), __uint_as_float(r[4 * qq + 1]),
+                                    __uint_as_float(r[4 * qq + 2]), __uint_as_float(r[4 * qq + 3]));
+                __syncwarp();
+                const int n = bn + 32 * c + 4 * cg;  // this thread's 4 columns
+                float4 bb = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (g.epi == EPI_BIAS_GELU || g.epi == EPI_BIAS)
+                    bb = __ldg(reinterpret_cast<const float4 *>(g.bias + n));
+#pragma unroll 2
+                for (int rr = 0; rr < 8; rr++) {
+                    const int rl = 4 * rr + rs;  // row within the warp's 32
+                    float4 v = *reinterpret_cast<const float4 *>(stg + rl * C::STG_LD + 4 * cg);
+                    const size_t at = (size_t)(bm + 32 * q + rl) * g.ldc + n;
+                    if (g.epi == EPI_BIAS_GELU || g.epi == EPI_BIAS) {
+                        v.x += bb.x;
+                        v.y += bb.y;
+                        v.z += bb.z;
+                        v.w += bb.w;
+                    } else if (g.epi == EPI_DGELU) {
+                        const float4 z = *reinterpret_cast<const float4 *>(g.zsaved + at);
+                        v.x *= gelu_grad(z.x);
+                        v.y *= gelu_grad(z.y);
+                        v.z *= gelu_grad(z.z);
+                        v.w *= gelu_grad(z.w);
+                    }
+                    *reinterpret_cast<float4 *>(g.outf + at) = v;
+                    if (g.outh) {
+                        const bool act = g.epi == EPI_BIAS_GELU;
+                        __nv_bfloat162 h[2];
+                        h[0] = act ? __floats2bfloat162_rn(gelu(v.x), gelu(v.y)) : __floats2bfloat162_rn(v.x, v.y);
+                        h[1] = act ? __floats2bfloat162_rn(gelu(v.z), gelu(v.w)) : __floats2bfloat162_rn(v.z, v.w);
+                        *reinterpret_cast<uint2 *>(g.outh + at) = *reinterpret_cast<const uint2 *>(h);
+                    }
+                }
+                __syncwarp();  // the block is read before the next one is staged
+            }
+            // this thread's reads of the accumulator are complete (the
+            // loads waited): the MMA issuer may overwrite it
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive(tempty(acc));
+        }
     }
 
-    // every thread waits (bounded) for the MMAs; the epilogue runs only if
-    // they all completed and no role gave up
-    const bool mma_done = mbar_wait(done, 0);
+    // every MMA issued has completed once quiet's first phase has
+    mbar_wait(quiet, 0);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const bool skip = __syncthreads_or(!mma_done || s_abort) != 0;
-    if (!skip) {
-        // epilogue: thread (warp, lane) holds row bm + 32 warp + lane
-        const int m = bm + 32 * warp + lane;
-        const size_t row = (size_t)m * g.ldc;
-#pragma unroll 1
-        for (int c = 0; c < UBN / 16; c++) {
-            uint32_t r[16];
-            tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + 16 * c, r);
-            const int n0 = bn + 16 * c;
-            float v[16];
-#pragma unroll
-            for (int j = 0; j < 16; j++)
-                v[j] = __uint_as_float(r[j]);
-            if (g.epi == EPI_BIAS_GELU || g.epi == EPI_BIAS) {
-#pragma unroll
-                for (int j = 0; j < 16; j++)
-                    v[j] += g.bias[n0 + j];
-            } else if (g.epi == EPI_DGELU) {
-                const float4 *z4 = reinterpret_cast<const float4 *>(g.zsaved + row + n0);
-#pragma unroll
-                for (int q = 0; q < 4; q++) {
-                    const float4 z = z4[q];
-                    v[4 * q] *= gelu_grad(z.x);
-                    v[4 * q + 1] *= gelu_grad(z.y);
-                    v[4 * q + 2] *= gelu_grad(z.z);
-                    v[4 * q + 3] *= gelu_grad(z.w);
-                }
-            }
-            float4 *o4 = reinterpret_cast<float4 *>(g.outf + row + n0);
-#pragma unroll
-            for (int q = 0; q < 4; q++)
-                o4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-            if (g.outh) {
-                __nv_bfloat162 h[8];
-#pragma unroll
-                for (int q = 0; q < 8; q++)
-                    h[q] = g.epi == EPI_BIAS_GELU ? __floats2bfloat162_rn(gelu(v[2 * q]), gelu(v[2 * q + 1]))
-                                                  : __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
-                uint4 *oh = reinterpret_cast<uint4 *>(g.outh + row + n0);
-                oh[0] = *reinterpret_cast<const uint4 *>(&h[0]);
-                oh[1] = *reinterpret_cast<const uint4 *>(&h[4]);
-            }
-        }
-    }  // !skip
-    if (skip && warp == 0 && lane == 0) {
+    if (warp == 0 && lane == 0 && *abort_flag) {
         // the producer's own copies in flight: wait (bounded) for the last
         // load phase of each stage it used, so that no TMA write lands in
         // shared memory after the block exits (phases of one barrier
         // complete in order, so the last one implies the earlier ones)
-        for (int kt = issued > USTAGES ? issued - USTAGES : 0; kt < issued; kt++)
-            mbar_wait(full(kt % USTAGES), (kt / USTAGES) & 1);
+        for (int kt = issued > C::STAGES ? issued - C::STAGES : 0; kt < issued; kt++)
+            mbar_wait(full(kt % C::STAGES), (kt / C::STAGES) & 1);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0)  // always freed, also after a stop
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(UBN));
+    if (warp == 1)  // always freed, also after a stop
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TCOLS));
 }
 
 // out [C][R] = in [R][C]^T (BF16; R and C multiples of 32), 32 x 32 tiles
@@ -314,18 +426,45 @@ cudaError_t transpose(const bf16 *in, int R, int C, bf16 *out, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t gemm(const CUtensorMap &A, const CUtensorMap &B, const GemmArgs &g, cudaStream_t s)
+// the tile width of a GEMM whose C has N columns
+int tile_n(int N)
 {
-    umma_gemm_kernel<<<dim3(g.N / UBN, g.M / UBM), 128, USMEM, s>>>(A, B, g);
+    return N % 256 == 0 ? 256 : 128;
+}
+
+// one persistent launch: min(tiles, SMs) CTAs; the shapes, the maps' box
+// heights and the alignment of the epilogue's vector accesses are checked
+// here, before anything runs
+cudaError_t gemm(const GMap &A, const GMap &B, const GemmArgs &g, cudaStream_t s)
+{
+    const int bn = B.box_rows;
+    auto misaligned = [](const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) != 0; };
+    if (A.box_rows != UBM || bn != tile_n(g.N) || g.M <= 0 || g.N <= 0 || g.K <= 0 || g.M % UBM ||
+        g.N % bn || g.K % UBK || g.ldc % 8 || misaligned(g.bias) || misaligned(g.zsaved) ||
+        misaligned(g.outf) || misaligned(g.outh))
+        return cudaErrorInvalidValue;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess)
+        return e;
+    const int tiles = (g.M / UBM) * (g.N / bn);
+    const int grid = tiles < sms ? tiles : sms;
+    if (bn == 256)
+        umma_gemm_kernel<256><<<grid, 192, GemmCfg<256>::SMEM, s>>>(A.map, B.map, g);
+    else
+        umma_gemm_kernel<128><<<grid, 192, GemmCfg<128>::SMEM, s>>>(A.map, B.map, g);
     return cudaGetLastError();
 }
 
-// tensor map of a row-major [rows][k] BF16 matrix, boxes of 128 rows x 64
+// tensor map of a row-major [rows][k] BF16 matrix, boxes of box_rows rows x
+// 64 (128 bytes, the swizzle span)
 using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-bool make_map(CUtensorMap *map, const bf16 *ptr, int rows, int k)
+bool make_map(GMap *m, const bf16 *ptr, int rows, int k, int box_rows)
 {
     static EncodeTiled encode = nullptr;
     if (!encode) {
@@ -337,13 +476,28 @@ bool make_map(CUtensorMap *map, const bf16 *ptr, int rows, int k)
             return false;
         encode = reinterpret_cast<EncodeTiled>(fn);
     }
+    if (rows % box_rows)
+        return false;
+    m->box_rows = box_rows;
     const cuuint64_t dims[2] = {(cuuint64_t)k, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)k * 2};
-    const cuuint32_t box[2] = {UBK, UBM};
+    const cuuint32_t box[2] = {UBK, (cuuint32_t)box_rows};
     const cuuint32_t estr[2] = {1, 1};
-    return encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16 *>(ptr), dims, strides, box, estr,
+    return encode(&m->map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16 *>(ptr), dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// A operand [M][K]: boxes of 128 rows; B operand [N][K]: boxes of the
+// GEMM's tile width
+bool map_a(GMap *m, const bf16 *ptr, int rows, int k)
+{
+    return make_map(m, ptr, rows, k, UBM);
+}
+
+bool map_b(GMap *m, const bf16 *ptr, int rows, int k)
+{
+    return make_map(m, ptr, rows, k, tile_n(rows));
 }
 
 // ------------------------------------------------------------- elementwise --
@@ -360,21 +514,66 @@ struct WarmDev {
 // u = normalised loads (BF16, zero padding): (load / base - 1) / 0.2 as one
 // FP32 FMA with the precomputed 5 / base (0 where the base load is 0); the
 // result is rounded to BF16 anyway
+// x rounded to the nearest FP32 (ties to even) on the integer pipe: the
+// conversion instruction issues at the FP64 rate on this GPU, so it is kept
+// for the values outside FP32's normal range only (zero and double
+// subnormals round to a signed zero exactly)
+__device__ __forceinline__ float f32_rn(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned int sign = (unsigned int)(b >> 63) << 31;
+    const int e = (int)((b >> 52) & 0x7FF);
+    if (e == 0)
+        return __uint_as_float(sign);
+    const int ef = e - 1023 + 127;  // FP32 biased exponent
+    if (ef <= 0 || ef >= 255)
+        return (float)x;
+    const unsigned long long m = b & 0xFFFFFFFFFFFFFull;  // 52 fraction bits
+    const unsigned int mf = (unsigned int)(m >> 29);        // the 23 kept
+    const unsigned long long rem = m & 0x1FFFFFFFull, half = 1ull << 28;
+    unsigned int bits = ((unsigned int)ef << 23) | mf;
+    if (rem > half || (rem == half && (mf & 1u)))
+        bits += 1u;  // a carry moves into the exponent (to infinity past the largest float)
+    return __uint_as_float(bits | sign);
+}
+
+// one load's input entry j of a profile whose loads start at ps, qs
+__device__ __forceinline__ float input_of(const WarmDev &w, const double *ps, const double *qs, int j, double v)
+{
+    if (j < w.nload) {
+        const float k = w.pk[j];
+        return k != 0.f ? fmaf(f32_rn(v), k, -5.f) : 0.f;
+    }
+    if (j < 2 * w.nload) {
+        const float k = w.qk[j - w.nload];
+        return k != 0.f ? fmaf(f32_rn(v), k, -5.f) : 0.f;
+    }
+    return 0.f;
+}
+
+// grid (column blocks, profile blocks); each warp takes 256 consecutive
+// entries of a row as 8 rounds of 32 (coalesced loads, eight in flight per
+// thread; 64-byte stores); rows y, y + gridDim.y, ... per block row
 __global__ void prep_kernel(const WarmDev w, const double *pd, const double *qd, bf16 *U)
 {
-    const int64_t total = (int64_t)w.B * w.Kin;
-    for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < total;
-         it += (int64_t)gridDim.x * blockDim.x) {
-        const int s = (int)(it / w.Kin), j = (int)(it - (int64_t)s * w.Kin);
-        float u = 0.f;
-        if (j < w.nload) {
-            const float k = w.pk[j];
-            u = k != 0.f ? fmaf((float)pd[(int64_t)s * w.nload + j], k, -5.f) : 0.f;
-        } else if (j < 2 * w.nload) {
-            const float k = w.qk[j - w.nload];
-            u = k != 0.f ? fmaf((float)qd[(int64_t)s * w.nload + j - w.nload], k, -5.f) : 0.f;
+    const int jb = blockIdx.x * (blockDim.x * 8) + (threadIdx.x >> 5) * 256 + (threadIdx.x & 31);
+    if (jb >= w.Kin)
+        return;
+    for (int s = blockIdx.y; s < w.B; s += gridDim.y) {
+        const double *ps = pd + (int64_t)s * w.nload, *qs = qd + (int64_t)s * w.nload;
+        bf16 *us = U + (int64_t)s * w.Kin;
+        double v[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            const int j = jb + 32 * q;
+            v[q] = j < w.nload ? __ldg(ps + j) : j < 2 * w.nload ? __ldg(qs + j - w.nload) : 0.0;
         }
-        U[it] = __float2bfloat16_rn(u);
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            const int j = jb + 32 * q;
+            if (j < w.Kin)
+                us[j] = __float2bfloat16_rn(input_of(w, ps, qs, j, v[q]));
+        }
     }
 }
 
@@ -700,7 +899,7 @@ struct opf_warm {
     bf16 *UT = nullptr, *H1T = nullptr, *H2T = nullptr, *W2T = nullptr, *W3T = nullptr, *dYT = nullptr,
          *dZ2T = nullptr, *dZ1T = nullptr;
     // TMA tensor maps of every GEMM operand (buffers fixed for the model's life)
-    CUtensorMap mU, mW1, mH1, mW2, mH2, mW3, mdYT, mH2T, mdY, mW3T, mdZ2T, mH1T, mdZ2, mW2T, mdZ1T, mUT;
+    GMap mU, mW1, mH1, mW2, mH2, mW3, mdYT, mH2T, mdY, mW3T, mdZ2T, mH1T, mdZ2, mW2T, mdZ1T, mUT;
     float *Z1 = nullptr, *Z2 = nullptr, *Y = nullptr, *dYf = nullptr, *dZ2f = nullptr, *dZ1f = nullptr;
     double *x = nullptr, *c = nullptr, *gradf = nullptr, *obj = nullptr, *v1 = nullptr, *u2 = nullptr,
            *part = nullptr;
@@ -819,8 +1018,9 @@ GemmArgs gargs(int M, int N, int K, int ldc, int epi, const float *bias, const f
     return g;
 }
 
-// forward pass: U (already prepared) -> Z1, H1, Z2, H2, Y
-int forward(opf_warm *w, cudaStream_t s)
+// forward pass: U (already prepared) -> Z1, H1, Z2, H2, and Y into y
+// (w->Y unless given)
+int forward(opf_warm *w, cudaStream_t s, float *y = nullptr)
 {
     const int B = w->B, H = w->H;
     cudaError_t e =
@@ -828,7 +1028,7 @@ int forward(opf_warm *w, cudaStream_t s)
     if (e == cudaSuccess)
         e = gemm(w->mH1, w->mW2, gargs(B, H, H, H, EPI_BIAS_GELU, w->params + w->ob2, nullptr, w->Z2, w->H2), s);
     if (e == cudaSuccess)
-        e = gemm(w->mH2, w->mW3, gargs(B, w->Nout, H, w->Nout, EPI_BIAS, w->params + w->ob3, nullptr, w->Y, nullptr), s);
+        e = gemm(w->mH2, w->mW3, gargs(B, w->Nout, H, w->Nout, EPI_BIAS, w->params + w->ob3, nullptr, y ? y : w->Y, nullptr), s);
     return check_cuda(e, "forward GEMMs");
 }
 
@@ -1046,21 +1246,26 @@ int opf_warm_create(const opf_network *net, const opf_warm_opts *opts, opf_warm 
     if (!rc) rc = walloc(w, &w->part, 2 * (size_t)w->nparts);
     if (!rc) {  // tensor maps: A operands [M][K], B operands [N][K]
         const int B = w->B, H = w->H, Kin = w->Kin, No = w->Nout;
-        const bool ok = make_map(&w->mU, w->U, B, Kin) && make_map(&w->mW1, w->W1h, H, Kin) &&
-                        make_map(&w->mH1, w->H1, B, H) && make_map(&w->mW2, w->W2h, H, H) &&
-                        make_map(&w->mH2, w->H2, B, H) && make_map(&w->mW3, w->W3h, No, H) &&
-                        make_map(&w->mdYT, w->dYT, No, B) && make_map(&w->mH2T, w->H2T, H, B) &&
-                        make_map(&w->mdY, w->dYh, B, No) && make_map(&w->mW3T, w->W3T, H, No) &&
-                        make_map(&w->mdZ2T, w->dZ2T, H, B) && make_map(&w->mH1T, w->H1T, H, B) &&
-                        make_map(&w->mdZ2, w->dZ2h, B, H) && make_map(&w->mW2T, w->W2T, H, H) &&
-                        make_map(&w->mdZ1T, w->dZ1T, H, B) && make_map(&w->mUT, w->UT, Kin, B);
+        const bool ok = map_a(&w->mU, w->U, B, Kin) && map_b(&w->mW1, w->W1h, H, Kin) &&
+                        map_a(&w->mH1, w->H1, B, H) && map_b(&w->mW2, w->W2h, H, H) &&
+                        map_a(&w->mH2, w->H2, B, H) && map_b(&w->mW3, w->W3h, No, H) &&
+                        map_a(&w->mdYT, w->dYT, No, B) && map_b(&w->mH2T, w->H2T, H, B) &&
+                        map_a(&w->mdY, w->dYh, B, No) && map_b(&w->mW3T, w->W3T, H, No) &&
+                        map_a(&w->mdZ2T, w->dZ2T, H, B) && map_b(&w->mH1T, w->H1T, H, B) &&
+                        map_a(&w->mdZ2, w->dZ2h, B, H) && map_b(&w->mW2T, w->W2T, H, H) &&
+                        map_a(&w->mdZ1T, w->dZ1T, H, B) && map_b(&w->mUT, w->UT, Kin, B);
         if (!ok) {
             set_error("opf_warm_create: cuTensorMapEncodeTiled failed");
             rc = OPF_ECUDA;
         }
     }
     if (!rc)
-        rc = check_cuda(cudaFuncSetAttribute(umma_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, USMEM),
+        rc = check_cuda(cudaFuncSetAttribute(umma_gemm_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             GemmCfg<256>::SMEM),
+                        "GEMM shared memory");
+    if (!rc)
+        rc = check_cuda(cudaFuncSetAttribute(umma_gemm_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             GemmCfg<128>::SMEM),
                         "GEMM shared memory");
     if (!rc) {  // the structured bounds of the kernels against the model's own
         double *b = nullptr;
@@ -1130,9 +1335,12 @@ int opf_warm_forward(opf_warm *w, const double *d_pd, const double *d_qd, float 
         return OPF_EINVAL;
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    prep_kernel<<<grid1((int64_t)w->B * w->Kin), 256, 0, s>>>(dev_of(w), d_pd, d_qd, w->U);
-    int rc = forward(w, s);
-    if (!rc && d_y)
+    prep_kernel<<<dim3((w->Kin + 1023) / 1024, w->B < 65535 ? w->B : 65535), 128, 0, s>>>(dev_of(w), d_pd, d_qd, w->U);
+    // the output layer writes the caller's buffer directly where its
+    // vector stores may (16-byte aligned), else w->Y and a copy
+    const bool direct = d_y && (reinterpret_cast<uintptr_t>(d_y) & 15u) == 0;
+    int rc = forward(w, s, direct ? d_y : nullptr);
+    if (!rc && d_y && !direct)
         rc = check_cuda(cudaMemcpyAsync(d_y, w->Y, sizeof(float) * w->B * w->Nout, cudaMemcpyDeviceToDevice, s), "copy output");
     return rc;
 }
@@ -1177,7 +1385,7 @@ int opf_warm_train_step(opf_warm *w, const double *d_pd, const double *d_qd, dou
         return OPF_EINVAL;
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    prep_kernel<<<grid1((int64_t)w->B * w->Kin), 256, 0, s>>>(dev_of(w), d_pd, d_qd, w->U);
+    prep_kernel<<<dim3((w->Kin + 1023) / 1024, w->B < 65535 ? w->B : 65535), 128, 0, s>>>(dev_of(w), d_pd, d_qd, w->U);
     int rc = forward(w, s);
     if (!rc)
         rc = loss_grad(w, d_pd, d_qd, d_stats, s);
@@ -1205,7 +1413,7 @@ int opf_warm_predict(opf_warm *w, const double *d_pd, const double *d_qd, double
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const WarmDev d = dev_of(w);
-    prep_kernel<<<grid1((int64_t)w->B * w->Kin), 256, 0, s>>>(d, d_pd, d_qd, w->U);
+    prep_kernel<<<dim3((w->Kin + 1023) / 1024, w->B < 65535 ? w->B : 65535), 128, 0, s>>>(d, d_pd, d_qd, w->U);
     int rc = forward(w, s);
     if (!rc) {
         rc = check_cuda(cudaMemsetAsync(d_x, 0, sizeof(double) * w->n, s), "clear x");
