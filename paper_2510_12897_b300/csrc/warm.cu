@@ -27,7 +27,7 @@ namespace {
 // C[M x N] = A[M x K] B[N x K]^T with BF16 operands and FP32 accumulation on
 // the 5th-generation tensor cores. Both operands are row-major with K
 // contiguous (the backward pass feeds transposed copies). Persistent: one
-// CTA of 192 threads per SM walks the 128 x BN tiles of C (BN 256, or 128
+// CTA of 320 threads per SM walks the 128 x BN tiles of C (BN 256, or 128
 // where N is not a multiple of 256), M-blocks fastest:
 //   warp 0, one lane   TMA producer: 128 x 64 tiles of A and BN x 64 tiles
 //                      of B (128-byte swizzle) into a ring of stages across
@@ -39,9 +39,11 @@ namespace {
 //                      after tile alternating; tcgen05.commit frees the
 //                      stage ("empty") and, after a tile's last stage,
 //                      hands the accumulator to the epilogue ("tfull");
-//   warps 2-5          epilogue: tcgen05.ld of their 32 accumulator lanes
-//                      (warp w reads lanes 32 (w mod 4) and up), 32 columns
-//                      at a time, bias / GELU / GELU' in FP32, stores; then
+//   warps 2-9          epilogue: tcgen05.ld of their 32 accumulator lanes
+//                      (warp w reads lanes 32 (w mod 4) and up; two warps
+//                      per lane quarter, half the columns each), 32 columns
+//                      at a time, staged through shared memory into row
+//                      segments, bias / GELU / GELU' in FP32, stores; then
 //                      the accumulator is free again ("tempty"), so one
 //                      tile's epilogue runs under the next tile's MMAs.
 // Every wait on an mbarrier gives up after a bounded number of polls, or
@@ -50,6 +52,8 @@ namespace {
 // of 64.
 
 constexpr int UBM = 128, UBK = 64;
+constexpr int kEpiWarps = 8;                      // two per accumulator lane quarter
+constexpr int kGemmThreads = 64 + 32 * kEpiWarps;  // producer, MMA issuer, epilogue
 constexpr uint32_t kWaitPolls = 1u << 22;
 
 // the shared-memory plan of a tile width BN: the stage ring (A then B tile
@@ -63,8 +67,8 @@ struct GemmCfg {
     static constexpr int STAGE = ATILE + BTILE;
     static constexpr int STAGES = BN == 256 ? 4 : 6;  // 192 KB of stages
     static constexpr int NBAR = 2 * STAGES + 5;
-    static constexpr int STG_LD = 36;  // staging row stride in floats (16-byte rows, no bank conflicts)
-    static constexpr int STG = 4 * 32 * STG_LD * 4;  // one 32 x 32 FP32 block per epilogue warp
+    static constexpr int STG_LD = 20;  // staging row stride in floats (16-byte aligned rows)
+    static constexpr int STG = kEpiWarps * 32 * STG_LD * 4;  // one 32 x 16 FP32 block per epilogue warp
     static constexpr int SMEM = STAGES * STAGE + 1024 + 8 * NBAR + 32 + STG;  // + alignment slack
     static constexpr uint32_t TCOLS = 2 * BN;  // two accumulators
     // instruction descriptor of kind::f16: D FP32, A and B BF16, both
@@ -214,7 +218,7 @@ __device__ __forceinline__ float gelu_grad(float z)
 }
 
 template <int BN>
-__global__ void __launch_bounds__(192, 1) umma_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
+__global__ void __launch_bounds__(kGemmThreads, 1) umma_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                                                            const __grid_constant__ CUtensorMap tmB, const GemmArgs g)
 {
     using C = GemmCfg<BN>;
@@ -246,7 +250,7 @@ __global__ void __launch_bounds__(192, 1) umma_gemm_kernel(const __grid_constant
         }
         for (int a = 0; a < 2; a++) {
             mbar_init(tfull(a), 1);
-            mbar_init(tempty(a), 128);  // every epilogue thread arrives
+            mbar_init(tempty(a), 32 * kEpiWarps);  // every epilogue thread arrives
         }
         mbar_init(quiet, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -322,8 +326,12 @@ __global__ void __launch_bounds__(192, 1) umma_gemm_kernel(const __grid_constant
             umma_commit(quiet);
         }
         __syncwarp();
-    } else {  // epilogue: warp w reads accumulator lanes 32 (w mod 4) .. + 31
-        const int q = warp & 3;
+    } else {  // epilogue: warp w reads accumulator lanes 32 (w mod 4) .. + 31,
+              // warps 2-5 the first half of the columns, warps 6-9 the second
+        const int e = warp - 2, q = warp & 3;
+        const int c0 = (e >> 2) * (BN / 64), c1 = c0 + BN / 64;  // its 32-column chunks
+        float *stg = stage_f + e * (32 * C::STG_LD);
+        const int cg = lane & 3, rs = lane >> 2;
         int j = 0;
         for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, j++) {
             const int acc = j & 1, use = j >> 1;
@@ -334,53 +342,55 @@ __global__ void __launch_bounds__(192, 1) umma_gemm_kernel(const __grid_constant
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const int bm = (tile % mt) * UBM, bn = (tile / mt) * BN;
             const uint32_t tb = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * BN);
-            // each 32 x 32 block: thread = row out of tensor memory, into
-            // this warp's staging block, back out as 8 threads per 128-byte
-            // row segment (4 rows per instruction) for the epilogue and
-            // coalesced stores
-            float *stg = stage_f + (warp - 2) * (32 * C::STG_LD);
-            const int cg = lane & 7, rs = lane >> 3;
+            // each 32 x 16 half of a chunk: thread = row out of tensor
+            // memory, into the warp's staging block, back out as 4 threads
+            // per 64-byte row segment (8 rows per instruction) for the
+            // epilogue and coalesced stores
 #pragma unroll 1
-            for (int c = 0; c < BN / 32; c++) {
+            for (int c = c0; c < c1; c++) {
                 uint32_t r[32];
                 tmem_ld32(tb + 32 * c, r);
 #pragma unroll
-                for (int qq = 0; qq < 8; qq++)
-                    *reinterpret_cast<float4 *>(stg + lane * C::STG_LD + 4 * qq) =
-                        make_float4(__uint_as_float(r[4 * qq]), __uint_as_float(r[4 * qq + 1]),
-                                    __uint_as_float(r[4 * qq + 2]), __uint_as_float(r[4 * qq + 3]));
-                __syncwarp();
-                const int n = bn + 32 * c + 4 * cg;  // this thread's 4 columns
-                float4 bb = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (g.epi == EPI_BIAS_GELU || g.epi == EPI_BIAS)
-                    bb = __ldg(reinterpret_cast<const float4 *>(g.bias + n));
+                for (int hh = 0; hh < 2; hh++) {
+#pragma unroll
+                    for (int qq = 0; qq < 4; qq++)
+                        *reinterpret_cast<float4 *>(stg + lane * C::STG_LD + 4 * qq) =
+                            make_float4(__uint_as_float(r[16 * hh + 4 * qq]), __uint_as_float(r[16 * hh + 4 * qq + 1]),
+                                        __uint_as_float(r[16 * hh + 4 * qq + 2]),
+                                        __uint_as_float(r[16 * hh + 4 * qq + 3]));
+                    __syncwarp();
+                    const int n = bn + 32 * c + 16 * hh + 4 * cg;  // this thread's 4 columns
+                    float4 bb = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (g.epi == EPI_BIAS_GELU || g.epi == EPI_BIAS)
+                        bb = __ldg(reinterpret_cast<const float4 *>(g.bias + n));
 #pragma unroll 2
-                for (int rr = 0; rr < 8; rr++) {
-                    const int rl = 4 * rr + rs;  // row within the warp's 32
-                    float4 v = *reinterpret_cast<const float4 *>(stg + rl * C::STG_LD + 4 * cg);
-                    const size_t at = (size_t)(bm + 32 * q + rl) * g.ldc + n;
-                    if (g.epi == EPI_BIAS_GELU || g.epi == EPI_BIAS) {
-                        v.x += bb.x;
-                        v.y += bb.y;
-                        v.z += bb.z;
-                        v.w += bb.w;
-                    } else if (g.epi == EPI_DGELU) {
-                        const float4 z = *reinterpret_cast<const float4 *>(g.zsaved + at);
-                        v.x *= gelu_grad(z.x);
-                        v.y *= gelu_grad(z.y);
-                        v.z *= gelu_grad(z.z);
-                        v.w *= gelu_grad(z.w);
+                    for (int rr = 0; rr < 4; rr++) {
+                        const int rl = 8 * rr + rs;  // row within the warp's 32
+                        float4 v = *reinterpret_cast<const float4 *>(stg + rl * C::STG_LD + 4 * cg);
+                        const size_t at = (size_t)(bm + 32 * q + rl) * g.ldc + n;
+                        if (g.epi == EPI_BIAS_GELU || g.epi == EPI_BIAS) {
+                            v.x += bb.x;
+                            v.y += bb.y;
+                            v.z += bb.z;
+                            v.w += bb.w;
+                        } else if (g.epi == EPI_DGELU) {
+                            const float4 z = *reinterpret_cast<const float4 *>(g.zsaved + at);
+                            v.x *= gelu_grad(z.x);
+                            v.y *= gelu_grad(z.y);
+                            v.z *= gelu_grad(z.z);
+                            v.w *= gelu_grad(z.w);
+                        }
+                        *reinterpret_cast<float4 *>(g.outf + at) = v;
+                        if (g.outh) {
+                            const bool act = g.epi == EPI_BIAS_GELU;
+                            __nv_bfloat162 h[2];
+                            h[0] = act ? __floats2bfloat162_rn(gelu(v.x), gelu(v.y)) : __floats2bfloat162_rn(v.x, v.y);
+                            h[1] = act ? __floats2bfloat162_rn(gelu(v.z), gelu(v.w)) : __floats2bfloat162_rn(v.z, v.w);
+                            *reinterpret_cast<uint2 *>(g.outh + at) = *reinterpret_cast<const uint2 *>(h);
+                        }
                     }
-                    *reinterpret_cast<float4 *>(g.outf + at) = v;
-                    if (g.outh) {
-                        const bool act = g.epi == EPI_BIAS_GELU;
-                        __nv_bfloat162 h[2];
-                        h[0] = act ? __floats2bfloat162_rn(gelu(v.x), gelu(v.y)) : __floats2bfloat162_rn(v.x, v.y);
-                        h[1] = act ? __floats2bfloat162_rn(gelu(v.z), gelu(v.w)) : __floats2bfloat162_rn(v.z, v.w);
-                        *reinterpret_cast<uint2 *>(g.outh + at) = *reinterpret_cast<const uint2 *>(h);
-                    }
+                    __syncwarp();  // the block is read before the next one is staged
                 }
-                __syncwarp();  // the block is read before the next one is staged
             }
             // this thread's reads of the accumulator are complete (the
             // loads waited): the MMA issuer may overwrite it
@@ -452,9 +462,9 @@ cudaError_t gemm(const GMap &A, const GMap &B, const GemmArgs &g, cudaStream_t s
     const int tiles = (g.M / UBM) * (g.N / bn);
     const int grid = tiles < sms ? tiles : sms;
     if (bn == 256)
-        umma_gemm_kernel<256><<<grid, 192, GemmCfg<256>::SMEM, s>>>(A.map, B.map, g);
+        umma_gemm_kernel<256><<<grid, kGemmThreads, GemmCfg<256>::SMEM, s>>>(A.map, B.map, g);
     else
-        umma_gemm_kernel<128><<<grid, 192, GemmCfg<128>::SMEM, s>>>(A.map, B.map, g);
+        umma_gemm_kernel<128><<<grid, kGemmThreads, GemmCfg<128>::SMEM, s>>>(A.map, B.map, g);
     return cudaGetLastError();
 }
 
