@@ -670,7 +670,12 @@ def main():
 
     warm_start = None
     if not args.no_warm and rank == 0:
-        warm_start = warm_start_summary(torch, opf, synth, dev, args.warm_epochs)
+        # an NVTX range, so that a profiler can select this section's launches
+        torch.cuda.nvtx.range_push("warm_start")
+        try:
+            warm_start = warm_start_summary(torch, opf, synth, dev, args.warm_epochs)
+        finally:
+            torch.cuda.nvtx.range_pop()
 
     cpu = None
     if not args.no_cpu and rank == 0:
