@@ -88,22 +88,7 @@ __device__ __forceinline__ double flip(double v, bool f)
     return __longlong_as_double(r);
 }
 
-// 2 v exactly, on the integer pipe: a normal v gets one more in its exponent
-// field; zero and subnormals shift their magnitude left by one (carrying into
-// the exponent field where the result becomes normal); the largest binade
-// overflows to infinity; infinities and NaNs are returned unchanged.
-__device__ __forceinline__ double twice(double v)
-{
-    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-    const unsigned long long sign = b & 0x8000000000000000ULL;
-    const unsigned long long mag = b & 0x7fffffffffffffffULL;
-    const unsigned ex = (unsigned)(mag >> 52);
-    unsigned long long r = b + (1ULL << 52);
-    r = ex == 0u ? (sign | (mag << 1)) : r;
-    r = ex == 0x7feu ? (sign | 0x7ff0000000000000ULL) : r;
-    r = ex == 0x7ffu ? b : r;
-    return __longlong_as_double((long long)r);
-}
+#include "bits.cuh"  // twice (and the other integer-pipe helpers)
 
 // ---- FP32 <-> FP64 on the integer pipe (the conversion instructions run at
 // the FP64 rate, the scarce unit here)

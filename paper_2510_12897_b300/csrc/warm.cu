@@ -22,6 +22,8 @@ using namespace opf;
 
 namespace {
 
+#include "bits.cuh"
+
 // ------------------------------------------------------------------ GEMM --
 //
 // C[M x N] = A[M x K] B[N x K]^T with BF16 operands and FP32 accumulation on
@@ -512,6 +514,46 @@ bool map_b(GMap *m, const bf16 *ptr, int rows, int k)
 
 // ------------------------------------------------------------- elementwise --
 
+// The element-wise kernels below take kBatch elements per thread and loop
+// step, their loads issued before any of their arithmetic, so that each
+// thread keeps kBatch loads in flight (one at a time left these kernels at
+// a fraction of the memory bandwidth); every thread still visits its
+// elements in the same order.
+constexpr int kBatch = 4;
+
+// The FP64 work of these kernels is rare (a violated bound, a nonzero
+// residual), so it sits behind a warp vote: a warp in which no lane needs it
+// skips the instructions, which would otherwise issue for the whole warp
+// (predicated, or computed on every lane and selected). Each lane's result
+// does not depend on the vote.
+
+// x - clip(x, lo, hi), the subtraction only in warps with a lane outside
+__device__ __forceinline__ double excess_w(double x, double lo, double hi)
+{
+    const long long kx = order_key(x);
+    const bool below = kx < order_key(lo), above = kx > order_key(hi);
+    double r = 0.0;
+    if (__any_sync(__activemask(), below || above))
+        r = below ? x - lo : above ? x - hi : 0.0;
+    return r;
+}
+
+// x - clip(x, -h, h), h >= 0, likewise
+__device__ __forceinline__ double excess_sym_w(double x, double h)
+{
+    const bool out = (__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFll) > __double_as_longlong(h);
+    double r = 0.0;
+    if (__any_sync(__activemask(), out))
+        r = excess_sym(x, h);
+    return r;
+}
+
+// acc + r^2, the FMA only in warps with a nonzero r
+__device__ __forceinline__ double add_square_w(double acc, double r)
+{
+    return __any_sync(__activemask(), !is_zero(r)) ? fma(r, r, acc) : acc;
+}
+
 struct WarmDev {
     int B, nb, ng, nl, nload, Kin, Nout, nbp, ngp, ref;
     double va_scale, penalty;
@@ -519,34 +561,14 @@ struct WarmDev {
     const double *vmin, *vmax;               // per bus
     const double *pmin, *pmax, *qmin, *qmax; // per generator
     const double *angmin, *angmax, *rate;    // per branch
+    // (lo + hi) / 2 and (hi - lo) / 2 of vm, pg, qg (the output map's terms)
+    const double *vmid, *pmid, *phalf, *qmid, *qhalf;
+    double inv_b;  // 1 / B
 };
 
 // u = normalised loads (BF16, zero padding): (load / base - 1) / 0.2 as one
 // FP32 FMA with the precomputed 5 / base (0 where the base load is 0); the
 // result is rounded to BF16 anyway
-// x rounded to the nearest FP32 (ties to even) on the integer pipe: the
-// conversion instruction issues at the FP64 rate on this GPU, so it is kept
-// for the values outside FP32's normal range only (zero and double
-// subnormals round to a signed zero exactly)
-__device__ __forceinline__ float f32_rn(double x)
-{
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const unsigned int sign = (unsigned int)(b >> 63) << 31;
-    const int e = (int)((b >> 52) & 0x7FF);
-    if (e == 0)
-        return __uint_as_float(sign);
-    const int ef = e - 1023 + 127;  // FP32 biased exponent
-    if (ef <= 0 || ef >= 255)
-        return (float)x;
-    const unsigned long long m = b & 0xFFFFFFFFFFFFFull;  // 52 fraction bits
-    const unsigned int mf = (unsigned int)(m >> 29);        // the 23 kept
-    const unsigned long long rem = m & 0x1FFFFFFFull, half = 1ull << 28;
-    unsigned int bits = ((unsigned int)ef << 23) | mf;
-    if (rem > half || (rem == half && (mf & 1u)))
-        bits += 1u;  // a carry moves into the exponent (to infinity past the largest float)
-    return __uint_as_float(bits | sign);
-}
-
 // one load's input entry j of a profile whose loads start at ps, qs
 __device__ __forceinline__ float input_of(const WarmDev &w, const double *ps, const double *qs, int j, double v)
 {
@@ -591,28 +613,43 @@ __global__ void prep_kernel(const WarmDev w, const double *pd, const double *qd,
 // -> va, vm, pg, qg of the batch model (period t = profile t): va = va_scale
 // ya (0 at the reference bus), vm = mid + yv, pg = mid + half-range yp, qg
 // likewise; y = 0 is the flat start
-__global__ void map_kernel(const WarmDev w, const float *Y, double *x)
+// block b takes the periods b, b + gridDim.x, ...; its threads walk a
+// period's outputs (no division); the FP32 outputs are widened exactly on
+// the integer pipe
+__global__ void map_kernel(const WarmDev w, const float *__restrict__ Y, double *__restrict__ x)
 {
     const int per = 2 * w.nb + 2 * w.ng;
-    const int64_t total = (int64_t)w.B * per;
     const int64_t nbT = (int64_t)w.nb * w.B, ngT = (int64_t)w.ng * w.B;
-    for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < total;
-         it += (int64_t)gridDim.x * blockDim.x) {
-        const int t = (int)(it / per), j = (int)(it - (int64_t)t * per);
+    for (int t = blockIdx.x; t < w.B; t += gridDim.x) {
         const float *y = Y + (int64_t)t * w.Nout;
-        if (j < w.nb) {
-            x[(int64_t)w.nb * t + j] = j == w.ref ? 0.0 : w.va_scale * (double)y[j];
-        } else if (j < 2 * w.nb) {
-            const int i = j - w.nb;
-            x[nbT + (int64_t)w.nb * t + i] = 0.5 * (w.vmin[i] + w.vmax[i]) + (double)y[w.nbp + i];
-        } else if (j < 2 * w.nb + w.ng) {
-            const int g = j - 2 * w.nb;
-            x[2 * nbT + (int64_t)w.ng * t + g] =
-                0.5 * (w.pmin[g] + w.pmax[g]) + 0.5 * (w.pmax[g] - w.pmin[g]) * (double)y[2 * w.nbp + g];
-        } else {
-            const int g = j - 2 * w.nb - w.ng;
-            x[2 * nbT + ngT + (int64_t)w.ng * t + g] =
-                0.5 * (w.qmin[g] + w.qmax[g]) + 0.5 * (w.qmax[g] - w.qmin[g]) * (double)y[2 * w.nbp + w.ngp + g];
+        for (int j0 = threadIdx.x; j0 < per; j0 += kBatch * blockDim.x) {
+            float yv[kBatch];
+#pragma unroll
+            for (int u = 0; u < kBatch; u++) {  // output column of entry j
+                const int j = j0 + u * blockDim.x;
+                const int col = j < w.nb ? j : j < 2 * w.nb ? w.nbp + j - w.nb
+                                : j < 2 * w.nb + w.ng ? 2 * w.nbp + j - 2 * w.nb
+                                                      : 2 * w.nbp + w.ngp + j - 2 * w.nb - w.ng;
+                yv[u] = __ldg(y + (j < per ? col : 0));
+            }
+#pragma unroll
+            for (int u = 0; u < kBatch; u++) {
+                const int j = j0 + u * blockDim.x;
+                if (j >= per)
+                    break;
+                if (j < w.nb) {
+                    x[(int64_t)w.nb * t + j] = j == w.ref ? 0.0 : w.va_scale * widen(yv[u]);
+                } else if (j < 2 * w.nb) {
+                    const int i = j - w.nb;
+                    x[nbT + (int64_t)w.nb * t + i] = w.vmid[i] + widen(yv[u]);
+                } else if (j < 2 * w.nb + w.ng) {
+                    const int g = j - 2 * w.nb;
+                    x[2 * nbT + (int64_t)w.ng * t + g] = fma(w.phalf[g], widen(yv[u]), w.pmid[g]);
+                } else {
+                    const int g = j - 2 * w.nb - w.ng;
+                    x[2 * nbT + ngT + (int64_t)w.ng * t + g] = fma(w.qhalf[g], widen(yv[u]), w.qmid[g]);
+                }
+            }
         }
     }
 }
@@ -701,41 +738,121 @@ __global__ void bounds_check_kernel(const WarmDev w, const double *xl, const dou
 }
 
 // constraint rows: rho = c - clip(c, gl, gu); v1 = (2 penalty / B) rho;
-// per-block sums of rho^2 into part
-__global__ void resid_kernel(const WarmDev w, const double *c, int64_t m, double *v1, double *part)
+// per-block sums of rho^2 into part. The rows with bounds [0, 0] (flow,
+// balance and reference rows) have rho = c: only the angle and thermal rows
+// clip
+__global__ void resid_kernel(const WarmDev w, const double *__restrict__ c, int64_t m, double *__restrict__ v1,
+                             double *part)
 {
     __shared__ double red[32];
     double acc = 0.0;
     const double k = 2.0 * w.penalty / w.B;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const double ci = c[i];
-        double lo, hi;
-        row_bounds(w, i, lo, hi);
-        const double rho = ci - fmin(fmax(ci, lo), hi);
-        v1[i] = k * rho;
-        acc += rho * rho;
+    const int64_t T = w.B, nlT = (int64_t)w.nl * T, nbT = (int64_t)w.nb * T;
+    const int64_t a0 = T + 4 * nlT, a1 = T + 5 * nlT, th = T + 5 * nlT + 2 * nbT;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < m; i0 += kBatch * stride) {
+        double cv[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; u++) {
+            const int64_t i = i0 + u * stride;
+            cv[u] = i < m ? __ldg(c + i) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kBatch; u++) {
+            const int64_t i = i0 + u * stride;
+            if (i >= m)
+                break;
+            const double ci = cv[u];
+            double rho = ci;
+            if (i >= a0 && i < a1) {  // angle rows
+                const unsigned kk = (unsigned)(i - a0) % (unsigned)w.nl;  // 32-bit: the batch model has < 2^31 rows
+                rho = excess_w(ci, w.angmin[kk], w.angmax[kk]);
+            } else if (i >= th) {  // thermal rows: (-inf, 0]
+                rho = order_key(ci) > 0 ? ci : 0.0;
+            }
+            // two FP64 instructions per row: the floor of this kernel on this
+            // GPU (a vote to skip the zero rows measured slower: the balance
+            // rows are nonzero in every warp)
+            v1[i] = k * rho;
+            acc = fma(rho, rho, acc);
+        }
     }
     const double s = block_sum(acc, red);
     if (threadIdx.x == 0)
         part[blockIdx.x] = s;
 }
 
+// variable e of a period's bounded entries (vm, pg, qg, p, q; va has no
+// bounds): its index in period t and its bounds ([-hi, hi] where sym)
+struct BoundRef {
+    int64_t j;
+    double lo, hi;
+    bool sym;
+};
+
+__device__ __forceinline__ BoundRef bound_ref(const WarmDev &w, int t, int e)
+{
+    const int nb = w.nb, ng = w.ng, nl = w.nl, na = 2 * nl;
+    const int64_t T = w.B, nbT = (int64_t)nb * T, ngT = (int64_t)ng * T, naT = (int64_t)na * T;
+    BoundRef r;
+    r.sym = false;
+    if (e < nb) {
+        r.j = nbT + (int64_t)nb * t + e;
+        r.lo = w.vmin[e];
+        r.hi = w.vmax[e];
+    } else if (e < nb + ng) {
+        const int g = e - nb;
+        r.j = 2 * nbT + (int64_t)ng * t + g;
+        r.lo = w.pmin[g];
+        r.hi = w.pmax[g];
+    } else if (e < nb + 2 * ng) {
+        const int g = e - nb - ng;
+        r.j = 2 * nbT + ngT + (int64_t)ng * t + g;
+        r.lo = w.qmin[g];
+        r.hi = w.qmax[g];
+    } else {  // p block, then q block, each [period][arc]; arcs k and nl + k share branch k's rating
+        int a = e - nb - 2 * ng;
+        r.j = 2 * nbT + 2 * ngT + (int64_t)na * t;
+        if (a >= na) {
+            a -= na;
+            r.j += naT;
+        }
+        r.j += a;
+        r.hi = w.rate[a < nl ? a : a - nl];
+        r.lo = 0.0;
+        r.sym = true;
+    }
+    return r;
+}
+
 // variable bounds: per-block sums of r^2, r = x - clip(x, xl, xu) (their
 // gradient enters through the flow multipliers for p, q and through the
-// output map for vm, pg, qg)
-__global__ void bound_kernel(const WarmDev w, const double *x, int64_t n, double *part)
+// output map for vm, pg, qg); only violated bounds add. Block b takes the
+// periods b, b + gridDim.x, ...; its threads walk a period's bounded
+// entries, so every bound is indexed directly, with no division
+__global__ void bound_kernel(const WarmDev w, const double *__restrict__ x, double *part)
 {
     __shared__ double red[32];
     double acc = 0.0;
-    const int64_t j0 = (int64_t)w.nb * w.B;  // va has no bounds
-    for (int64_t j = j0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        double lo, hi;
-        var_bounds(w, j, lo, hi);
-        const double xj = x[j];
-        const double r = xj - fmin(fmax(xj, lo), hi);
-        acc += r * r;
+    const int per = w.nb + 2 * w.ng + 4 * w.nl;
+    for (int t = blockIdx.x; t < w.B; t += gridDim.x) {
+        for (int e0 = threadIdx.x; e0 < per; e0 += kBatch * blockDim.x) {
+            BoundRef br[kBatch];
+            double xv[kBatch];
+#pragma unroll
+            for (int u = 0; u < kBatch; u++) {
+                const int e = e0 + u * blockDim.x;
+                br[u] = bound_ref(w, t, e < per ? e : 0);
+                xv[u] = __ldg(x + br[u].j);
+            }
+#pragma unroll
+            for (int u = 0; u < kBatch; u++) {
+                if (e0 + u * (int)blockDim.x >= per)
+                    break;
+                const double r = br[u].sym ? excess_sym_w(xv[u], br[u].hi) : excess_w(xv[u], br[u].lo, br[u].hi);
+                acc = add_square_w(acc, r);
+            }
+        }
     }
     const double s = block_sum(acc, red);
     if (threadIdx.x == 0)
@@ -751,26 +868,58 @@ __global__ void bound_kernel(const WarmDev w, const double *x, int64_t n, double
 // rows, where v2 = -g_own = -(2 x_own v_thermal + v_balance + k r_own),
 // k = 2 penalty / B. This kernel overwrites the flow rows of v1 with v2 (one
 // thread per branch and period, its four arc variables).
-__global__ void flowmult_kernel(const WarmDev w, const int4 *br, const double *x, double *v)
+// Block b takes the periods b, b + gridDim.x, ...; its threads the
+// branches, two per loop step with every load issued first. The clip, the
+// doubling and the signs are exact integer work or free FMA operand
+// negations: one FMA per arc variable, a second where its bound is violated.
+__global__ void flowmult_kernel(const WarmDev w, const int4 *__restrict__ br, const double *__restrict__ x,
+                                double *v)
 {
+    constexpr int NB = 2;  // branches per thread and loop step
     const int64_t T = w.B, nl = w.nl, nb = w.nb, ng = w.ng, na = 2 * nl;
     const int64_t nlT = nl * T, nbT = nb * T, ngT = ng * T;
     const double kpen = 2.0 * w.penalty / w.B;
-    for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < nlT;
-         it += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t t = it / nl, k = it - t * nl;
-        const int4 b = __ldg(br + k);
+    for (int t = blockIdx.x; t < w.B; t += gridDim.x) {
         const int64_t ip = 2 * nbT + 2 * ngT + na * t, iq = ip + na * T;
-        const int64_t own[4] = {ip + k, iq + k, ip + nl + k, iq + nl + k};
-        const int64_t th = T + 5 * nlT + 2 * nbT + it;  // thermal row (from); + nlT: to
-        const int64_t bal = T + 5 * nlT + nb * t;       // P balance of bus 0 in period t; + nbT: Q
-        const int64_t vb[4] = {bal + b.x, bal + nbT + b.x, bal + b.y, bal + nbT + b.y};
+        const int64_t bal = T + 5 * nlT + nb * t;  // P balance of bus 0 in period t; + nbT: Q
+        for (int k0 = threadIdx.x; k0 < w.nl; k0 += NB * blockDim.x) {
+            int4 bb[NB];
+            double xo[NB][4], vt[NB][2], vbv[NB][4], rate[NB];
 #pragma unroll
-        for (int g = 0; g < 4; g++) {
-            const double xo = x[own[g]], rate = w.rate[k];
-            const double r = xo - fmin(fmax(xo, -rate), rate);
-            const double vt = v[th + (g < 2 ? 0 : nlT)];
-            v[T + it + g * nlT] = -(fma(2.0 * xo, vt, v[vb[g]]) + kpen * r);
+            for (int u = 0; u < NB; u++) {
+                const int k = min(k0 + u * (int)blockDim.x, w.nl - 1);  // past the end: a valid branch, not stored
+                bb[u] = __ldg(br + k);
+                rate[u] = w.rate[k];
+                xo[u][0] = __ldg(x + ip + k);
+                xo[u][1] = __ldg(x + iq + k);
+                xo[u][2] = __ldg(x + ip + nl + k);
+                xo[u][3] = __ldg(x + iq + nl + k);
+                const int64_t th = T + 5 * nlT + 2 * nbT + nl * t + k;  // thermal row (from); + nlT: to
+                vt[u][0] = v[th];
+                vt[u][1] = v[th + nlT];
+            }
+#pragma unroll
+            for (int u = 0; u < NB; u++) {
+                vbv[u][0] = v[bal + bb[u].x];
+                vbv[u][1] = v[bal + nbT + bb[u].x];
+                vbv[u][2] = v[bal + bb[u].y];
+                vbv[u][3] = v[bal + nbT + bb[u].y];
+            }
+#pragma unroll
+            for (int u = 0; u < NB; u++) {
+                const int k = k0 + u * blockDim.x;
+                if (k >= w.nl)
+                    break;
+                const int64_t it = nl * t + k;
+#pragma unroll
+                for (int g = 0; g < 4; g++) {
+                    const double r = excess_sym_w(xo[u][g], rate[u]);
+                    double out = fma(-twice(xo[u][g]), vt[u][g < 2 ? 0 : 1], -vbv[u][g]);
+                    if (__any_sync(__activemask(), !is_zero(r)))
+                        out = fma(-kpen, r, out);
+                    v[T + it + g * nlT] = out;
+                }
+            }
         }
     }
 }
@@ -796,42 +945,88 @@ __global__ void stats_kernel(const WarmDev w, const double *part, int nparts, co
 // dL/dy from dL/dx = u (J^T v2) + the bound term + grad f / B (on pg),
 // through the output map: FP32 for the checks and the bias gradient, BF16
 // copies for the GEMMs; padding entries and the reference angle get 0
-__global__ void dmap_kernel(const WarmDev w, const double *x, const double *u2, const double *gradf,
-                            float *dYf, bf16 *dYh)
+// block b takes the periods b, b + gridDim.x, ...; its threads walk a
+// period's outputs (no division); clips and conversions on the integer pipe
+__global__ void dmap_kernel(const WarmDev w, const double *__restrict__ x, const double *__restrict__ u2,
+                            const double *__restrict__ gradf, float *__restrict__ dYf, bf16 *__restrict__ dYh)
 {
-    const int64_t total = (int64_t)w.B * w.Nout;
     const int64_t nbT = (int64_t)w.nb * w.B, ngT = (int64_t)w.ng * w.B;
     const double k = 2.0 * w.penalty / w.B;
-    auto over = [](double v, double lo, double hi) { return v - fmin(fmax(v, lo), hi); };
-    for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < total;
-         it += (int64_t)gridDim.x * blockDim.x) {
-        const int t = (int)(it / w.Nout), j = (int)(it - (int64_t)t * w.Nout);
-        double d = 0.0;
-        if (j < w.nbp) {
-            if (j < w.nb && j != w.ref)
-                d = w.va_scale * u2[(int64_t)w.nb * t + j];
-        } else if (j < 2 * w.nbp) {
-            const int i = j - w.nbp;
-            if (i < w.nb) {
-                const int64_t ix = nbT + (int64_t)w.nb * t + i;
-                d = u2[ix] + k * over(x[ix], w.vmin[i], w.vmax[i]);
+    for (int t = blockIdx.x; t < w.B; t += gridDim.x) {
+        for (int j0 = threadIdx.x; j0 < w.Nout; j0 += kBatch * blockDim.x) {
+            // the entry's block (0 va, 1 vm, 2 pg, 3 qg; -1 padding or the
+            // reference angle), element, variable index, and its loads
+            int blk[kBatch], el[kBatch];
+            double uv[kBatch], xv[kBatch], gv[kBatch];
+#pragma unroll
+            for (int u = 0; u < kBatch; u++) {
+                const int j = j0 + u * blockDim.x;
+                int b = -1, e = 0;
+                int64_t i = 0;
+                if (j < w.nbp) {
+                    if (j < w.nb && j != w.ref) {
+                        b = 0;
+                        e = j;
+                        i = (int64_t)w.nb * t + j;
+                    }
+                } else if (j < 2 * w.nbp) {
+                    e = j - w.nbp;
+                    if (e < w.nb) {
+                        b = 1;
+                        i = nbT + (int64_t)w.nb * t + e;
+                    }
+                } else if (j < 2 * w.nbp + w.ngp) {
+                    e = j - 2 * w.nbp;
+                    if (e < w.ng) {
+                        b = 2;
+                        i = 2 * nbT + (int64_t)w.ng * t + e;
+                    }
+                } else if (j < w.Nout) {
+                    e = j - 2 * w.nbp - w.ngp;
+                    if (e < w.ng) {
+                        b = 3;
+                        i = 2 * nbT + ngT + (int64_t)w.ng * t + e;
+                    }
+                }
+                blk[u] = b;
+                el[u] = e;
+                uv[u] = b >= 0 ? __ldg(u2 + i) : 0.0;
+                xv[u] = b >= 1 ? __ldg(x + i) : 0.0;
+                gv[u] = b == 2 ? __ldg(gradf + i) : 0.0;
             }
-        } else if (j < 2 * w.nbp + w.ngp) {
-            const int g = j - 2 * w.nbp;
-            if (g < w.ng) {
-                const int64_t ix = 2 * nbT + (int64_t)w.ng * t + g;
-                d = 0.5 * (w.pmax[g] - w.pmin[g]) *
-                    (u2[ix] + gradf[ix] / w.B + k * over(x[ix], w.pmin[g], w.pmax[g]));
-            }
-        } else {
-            const int g = j - 2 * w.nbp - w.ngp;
-            if (g < w.ng) {
-                const int64_t ix = 2 * nbT + ngT + (int64_t)w.ng * t + g;
-                d = 0.5 * (w.qmax[g] - w.qmin[g]) * (u2[ix] + k * over(x[ix], w.qmin[g], w.qmax[g]));
+#pragma unroll
+            for (int u = 0; u < kBatch; u++) {
+                const int j = j0 + u * blockDim.x;
+                if (j >= w.Nout)
+                    break;
+                const int e = el[u];
+                double d = 0.0;
+                if (blk[u] == 0) {
+                    d = w.va_scale * uv[u];
+                } else if (blk[u] == 1) {
+                    d = uv[u];
+                    const double r = excess_w(xv[u], w.vmin[e], w.vmax[e]);
+                    if (__any_sync(__activemask(), !is_zero(r)))
+                        d = fma(k, r, d);
+                } else if (blk[u] == 2) {
+                    double a = fma(gv[u], w.inv_b, uv[u]);
+                    const double r = excess_w(xv[u], w.pmin[e], w.pmax[e]);
+                    if (__any_sync(__activemask(), !is_zero(r)))
+                        a = fma(k, r, a);
+                    d = w.phalf[e] * a;
+                } else if (blk[u] == 3) {
+                    double a = uv[u];
+                    const double r = excess_w(xv[u], w.qmin[e], w.qmax[e]);
+                    if (__any_sync(__activemask(), !is_zero(r)))
+                        a = fma(k, r, a);
+                    d = w.qhalf[e] * a;
+                }
+                const int64_t at = (int64_t)w.Nout * t + j;
+                const float df = f32_rn(d);
+                dYf[at] = df;
+                dYh[at] = __float2bfloat16_rn(df);
             }
         }
-        dYf[it] = (float)d;
-        dYh[it] = __float2bfloat16_rn((float)d);
     }
 }
 
@@ -901,6 +1096,7 @@ struct opf_warm {
     float *params = nullptr, *grads = nullptr, *am = nullptr, *av = nullptr;
     bf16 *W1h = nullptr, *W2h = nullptr, *W3h = nullptr;
     float *pk = nullptr, *qk = nullptr;
+    double *vmid = nullptr, *pmid = nullptr, *phalf = nullptr, *qmid = nullptr, *qhalf = nullptr;
     double *vmin = nullptr, *vmax = nullptr, *pmin = nullptr,
            *pmax = nullptr, *qmin = nullptr, *qmax = nullptr, *gl = nullptr, *gu = nullptr,
            *xl = nullptr, *xu = nullptr, *angmin = nullptr, *angmax = nullptr, *rate = nullptr;
@@ -980,6 +1176,12 @@ WarmDev dev_of(const opf_warm *w)
     d.angmin = w->angmin;
     d.angmax = w->angmax;
     d.rate = w->rate;
+    d.vmid = w->vmid;
+    d.pmid = w->pmid;
+    d.phalf = w->phalf;
+    d.qmid = w->qmid;
+    d.qhalf = w->qhalf;
+    d.inv_b = 1.0 / w->B;
     return d;
 }
 
@@ -1089,20 +1291,20 @@ int backward(opf_warm *w, cudaStream_t s)
 int loss_grad(opf_warm *w, const double *d_pd, const double *d_qd, double *d_stats, cudaStream_t s)
 {
     const WarmDev d = dev_of(w);
-    map_kernel<<<grid1((int64_t)w->B * (2 * w->nb + 2 * w->ng)), 256, 0, s>>>(d, w->Y, w->x);
+    map_kernel<<<w->B < w->nparts ? w->B : w->nparts, 256, 0, s>>>(d, w->Y, w->x);
     int rc = launch_set_loads(*w->M, d_pd, d_qd, s);
     if (!rc)  // p, q := flows at the voltages; objective, gradient, constraints there
         rc = launch_cons_setflows(*w->M, w->x, w->obj, w->gradf, w->c, s);
     if (!rc) {  // v1 = 2 penalty rho / B; residual sums; flow rows of v1 := v2
         resid_kernel<<<w->nparts, 256, 0, s>>>(d, w->c, w->m, w->v1, w->part);
-        bound_kernel<<<w->nparts, 256, 0, s>>>(d, w->x, w->n, w->part + w->nparts);
+        bound_kernel<<<w->nparts, 256, 0, s>>>(d, w->x, w->part + w->nparts);
         if (d_stats)
             stats_kernel<<<1, 32, 0, s>>>(d, w->part, 2 * w->nparts, w->obj, d_stats);
-        flowmult_kernel<<<grid1((int64_t)w->nl * w->B), 256, 0, s>>>(d, w->M->d.br, w->x, w->v1);
+        flowmult_kernel<<<w->B < w->nparts ? w->B : w->nparts, 256, 0, s>>>(d, w->M->d.br, w->x, w->v1);
         rc = launch_jtprod(*w->M, w->x, w->v1, w->u2, s);
     }
     if (!rc)
-        dmap_kernel<<<grid1((int64_t)w->B * w->Nout), 256, 0, s>>>(d, w->x, w->u2, w->gradf, w->dYf, w->dYh);
+        dmap_kernel<<<w->B < w->nparts ? w->B : w->nparts, 256, 0, s>>>(d, w->x, w->u2, w->gradf, w->dYf, w->dYh);
     if (!rc)
         rc = check_cuda(cudaGetLastError(), "loss gradient");
     return rc;
@@ -1227,6 +1429,22 @@ int opf_warm_create(const opf_network *net, const opf_warm_opts *opts, opf_warm 
     if (!rc) rc = wupload(w, &w->angmin, std::vector<double>(net->br_angmin, net->br_angmin + w->nl));
     if (!rc) rc = wupload(w, &w->angmax, std::vector<double>(net->br_angmax, net->br_angmax + w->nl));
     if (!rc) rc = wupload(w, &w->rate, std::vector<double>(net->br_rate_a, net->br_rate_a + w->nl));
+    {
+        std::vector<double> vmid(w->nb), pmid(w->ng), phalf(w->ng), qmid(w->ng), qhalf(w->ng);
+        for (int i = 0; i < w->nb; i++)
+            vmid[i] = 0.5 * (vmin[i] + vmax[i]);
+        for (int g = 0; g < w->ng; g++) {
+            pmid[g] = 0.5 * (pmin[g] + pmax[g]);
+            phalf[g] = 0.5 * (pmax[g] - pmin[g]);
+            qmid[g] = 0.5 * (qmin[g] + qmax[g]);
+            qhalf[g] = 0.5 * (qmax[g] - qmin[g]);
+        }
+        if (!rc) rc = wupload(w, &w->vmid, vmid);
+        if (!rc) rc = wupload(w, &w->pmid, pmid);
+        if (!rc) rc = wupload(w, &w->phalf, phalf);
+        if (!rc) rc = wupload(w, &w->qmid, qmid);
+        if (!rc) rc = wupload(w, &w->qhalf, qhalf);
+    }
     if (!rc) rc = walloc(w, &w->U, (size_t)w->B * w->Kin);
     if (!rc) rc = walloc(w, &w->H1, act);
     if (!rc) rc = walloc(w, &w->H2, act);
@@ -1427,7 +1645,7 @@ int opf_warm_predict(opf_warm *w, const double *d_pd, const double *d_qd, double
     int rc = forward(w, s);
     if (!rc) {
         rc = check_cuda(cudaMemsetAsync(d_x, 0, sizeof(double) * w->n, s), "clear x");
-        map_kernel<<<grid1((int64_t)w->B * (2 * w->nb + 2 * w->ng)), 256, 0, s>>>(d, w->Y, d_x);
+        map_kernel<<<w->B < w->nparts ? w->B : w->nparts, 256, 0, s>>>(d, w->Y, d_x);
         if (!rc)
             rc = launch_flows(*w->M, d_x, s);
     }

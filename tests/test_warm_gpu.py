@@ -83,6 +83,40 @@ def _check_entries(name, got, ref, bound):
     assert not bad.any(), (name, int(bad.sum()), float(np.max(err / np.maximum(bound, 1e-300))))
 
 
+def test_forward_output_alignment(torch):
+    """opf_warm_forward writes a 16-byte aligned output buffer directly from
+    the last GEMM's epilogue and any other buffer through the network's own
+    output and a copy; both give the same values, bit for bit, and leave the
+    entries around the output untouched."""
+    from paper_2510_12897_b300 import warm
+    g = synth.case30(general=True)
+    B, hid = 128, 256
+    ws = warm.WarmStart(g, batch=B, hidden=hid, seed=3)
+    p0 = ws.get_params()
+    k = hid * ws.n_in + hid + hid * hid + hid
+    p0[k:] = (np.random.default_rng(5).standard_normal(p0.size - k) / np.sqrt(hid)).astype(np.float32)
+    ws.set_params(p0)
+    pd, qd = synth.load_samples(g, B, seed=12)
+    dev = torch.device("cuda")
+    pd_t, qd_t = torch.tensor(pd, device=dev), torch.tensor(qd, device=dev)
+    n = B * ws.n_out
+    buf = torch.full((n + 8,), -7.0, dtype=torch.float32, device=dev)
+    aligned, shifted = buf[4:4 + n], buf[1:1 + n]  # 16 and 4 bytes past the allocation
+    assert aligned.data_ptr() % 16 == 0 and shifted.data_ptr() % 16 == 4
+    ws.forward(pd_t, qd_t, aligned)
+    torch.cuda.synchronize()
+    a = aligned.cpu().numpy().copy()
+    assert np.all(buf[:4].cpu().numpy() == -7.0) and np.all(buf[4 + n:].cpu().numpy() == -7.0)
+    buf.fill_(-7.0)
+    ws.forward(pd_t, qd_t, shifted)
+    torch.cuda.synchronize()
+    b = shifted.cpu().numpy()
+    ws.close()
+    assert np.all(buf[:1].cpu().numpy() == -7.0) and np.all(buf[1 + n:].cpu().numpy() == -7.0)
+    np.testing.assert_array_equal(a, b)
+    assert np.isfinite(a).all() and np.abs(a).max() > 0
+
+
 @pytest.mark.slow
 def test_network_elementwise_full_shapes(torch):
     """Every GEMM and epilogue of the BF16 network (tcgen05, FP32
