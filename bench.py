@@ -65,11 +65,15 @@ def parse():
     p.add_argument("--no-rect", action="store_true", help="skip the rectangular-form section")
     p.add_argument("--warm-epochs", type=int, default=600)
     p.add_argument("--profile-batched", type=int, default=0, metavar="REPS",
-                   help="profiling aid: only run REPS plain evaluations of the 10k-bus grid "
-                        "with 32 load scenarios in one model, then exit")
+                   help="profiling aid: only run REPS plain evaluations of one batched model "
+                        "(--profile-case), then exit")
     p.add_argument("--profile-single", type=int, default=0, metavar="REPS",
                    help="profiling aid: only run REPS plain evaluations of the 10k-bus grid "
                         "(default launch shape), then exit")
+    p.add_argument("--profile-case", choices=["case10k_x32", "mp2k_96", "sc1k_501"], default="case10k_x32",
+                   help="the batch --profile-batched evaluates: 32 load scenarios of the 10k-bus grid, "
+                        "96 periods of the 2k-bus grid, or the 1k-bus grid with 500 contingencies and "
+                        "linking rows")
     p.add_argument("--form", choices=["polar", "rect"], default="polar",
                    help="voltage form of the profiling aids' models")
     return p.parse_args()
@@ -411,13 +415,21 @@ def main():
     dev = torch.device("cuda", local)
     f64 = torch.float64
     if args.profile_batched or args.profile_single:
-        g = synth.case10k()
-        sc = synth.scenarios(g, 32, seed=5) if args.profile_batched else g
-        Mb = opf.Model(sc, form=args.form)
+        opts = {}
+        if not args.profile_batched:
+            sc = synth.case10k()
+        elif args.profile_case == "mp2k_96":
+            sc = synth.mp2k()
+        elif args.profile_case == "sc1k_501":
+            sc, opts = synth.sc1k(), dict(link_ratio=0.2)
+        else:
+            sc = synth.scenarios(synth.case10k(), 32, seed=5)
+        Mb = opf.Model(sc, form=args.form, **opts)
         if args.launch:  # a fixed launch shape (else the model's default)
             Mb.set_launch(**dict(zip(LAUNCH_KEYS, (int(v) for v in args.launch.split(",")))))
         rng = np.random.default_rng(7)
-        xb = torch.tensor(synth.random_point(sc, rng, form=args.form), device=dev)
+        gl = sc if isinstance(sc, list) else [sc]
+        xb = torch.tensor(np.concatenate([synth.random_point(h, rng, form=args.form) for h in gl]), device=dev)
         lb = torch.tensor(rng.standard_normal(Mb.m), device=dev)
         ob = [torch.empty(k, dtype=f64, device=dev) for k in (1, Mb.n, Mb.m, Mb.nnzj, Mb.nnzh)]
         for _ in range(args.profile_batched or args.profile_single):

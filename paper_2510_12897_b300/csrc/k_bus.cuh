@@ -998,8 +998,14 @@ __global__ void __launch_bounds__(kBusBlockMax) bus_kernel(const KParams P)
 #pragma unroll
                     for (int u = 0; u < 4; u++) {
                         const int a = a0 + u;
-                        if (a >= nsl)
+                        // a warp-uniform exit once no lane has slot a: the
+                        // FP64 work of absent slots is then not issued (an
+                        // FP64 warp instruction costs the same with any
+                        // number of active lanes)
+                        if (!__any_sync(__activemask(), a < nsl))
                             break;
+                        if (a >= nsl)
+                            continue;
                         if (CONS) {
                             Pb += v0[u].x;
                             Qb += v0[u].y;
@@ -1010,12 +1016,17 @@ __global__ void __launch_bounds__(kBusBlockMax) bus_kernel(const KParams P)
                                 ? (((unsigned)q.m.x >> a) & 1u) | (a < q.m.y ? 2u : 0u)
                                 : (unsigned)__ldg(code + a);
                             dmm += v1[u].x;
-                            if (first) {
+                            if (__any_sync(__activemask(), !first)) {
+                                if (first) {
+                                    acc_aa = v1[u].y;
+                                    acc_ma = v2[u].x;
+                                } else {
+                                    acc_aa += v1[u].y;
+                                    acc_ma += v2[u].x;
+                                }
+                            } else {
                                 acc_aa = v1[u].y;
                                 acc_ma = v2[u].x;
-                            } else {
-                                acc_aa += v1[u].y;
-                                acc_ma += v2[u].x;
                             }
                             first = (cd & SLOT_LAST) != 0;
                             if (first) {  // a group of parallel arcs ends
@@ -1033,14 +1044,23 @@ __global__ void __launch_bounds__(kBusBlockMax) bus_kernel(const KParams P)
                             daa += v1[u].x;
                             dma += v1[u].y;
                             dmm += v2[u].x;
-                            if (first) {
+                            // a slot that continues a group of parallel arcs
+                            // adds to its sums; the additions issue only in
+                            // warps that have such a slot
+                            if (__any_sync(__activemask(), !first)) {
+                                if (first) {
+                                    acc_ma = neg(v1[u].y);
+                                    acc_aa = neg(v1[u].x);
+                                    acc_mm = v2[u].y;
+                                } else {
+                                    acc_ma -= v1[u].y;
+                                    acc_aa -= v1[u].x;
+                                    acc_mm += v2[u].y;
+                                }
+                            } else {
                                 acc_ma = neg(v1[u].y);
                                 acc_aa = neg(v1[u].x);
                                 acc_mm = v2[u].y;
-                            } else {
-                                acc_ma -= v1[u].y;
-                                acc_aa -= v1[u].x;
-                                acc_mm += v2[u].y;
                             }
                             first = (cd & SLOT_LAST) != 0;
                             if (first) {  // a group of parallel arcs ends: write its entries
