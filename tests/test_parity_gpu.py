@@ -600,13 +600,15 @@ def test_fused_roles_rule_10k(torch):
     """With two roles on the 10k grid (more packed warps than SM sub-
     partitions) the all-callback evaluation runs two warps per packed warp
     and the Jacobian + Hessian call one: both write the same values, bit for
-    bit (the all-callback values are checked against the oracle in
+    bit, and so does the all-callback evaluation with one warp per packed
+    warp (the all-callback values are checked against the oracle in
     test_fused_evaluation)."""
     g = synth.case10k()
     M = opf.Model(g)
     x, lam = next(points(g, M.m, 1, seed=41))
+    outs = {}
     for occ in (0, 2):
-        fused = run_all(torch, M, x, lam, 0.7, dict(FUSED, bus_block=128, branch_occupancy=occ))
+        fused = outs[occ] = run_all(torch, M, x, lam, 0.7, dict(FUSED, bus_block=128, branch_occupancy=occ))
         dx, dl = dev(torch, x), dev(torch, lam)
         jv = torch.empty(M.nnzj, dtype=torch.float64, device="cuda")
         hv = torch.empty(M.nnzh, dtype=torch.float64, device="cuda")
@@ -614,6 +616,10 @@ def test_fused_roles_rule_10k(torch):
         torch.cuda.synchronize()
         np.testing.assert_array_equal(host(jv), fused["jv"], err_msg=f"occ{occ} jv")
         np.testing.assert_array_equal(host(hv), fused["hv"], err_msg=f"occ{occ} hv")
+    # two roles (the Hessian warp takes the rows warp's sine and cosine) and
+    # one warp per packed warp: the same arithmetic, the same values
+    for k in ("obj", "grad", "c", "jv", "hv"):
+        np.testing.assert_array_equal(outs[2][k], outs[0][k], err_msg=f"two roles vs one warp: {k}")
 
 
 @pytest.mark.parametrize("which", ["case30g", "isolated", "batch_links", "reserve", "mp30", "case10k", "rect30g",
