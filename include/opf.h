@@ -337,8 +337,10 @@ int opf_set_launch(opf_model *model, const opf_launch *cfg);
 /* Autotuner: times each candidate launch shape (block sizes, persistence,
  * bus order, branch occupancy) of the fused opf_eval_all on this model as a
  * CUDA graph of `reps` back-to-back evaluations (the way a solver loop
- * replays them), on a private stream that first waits for `stream`; the six
- * fastest are timed again over more launches. Keeps the fastest and returns
+ * replays them), on a private stream that first waits for `stream`; the
+ * eight fastest are then timed again in six interleaved rounds (each
+ * captured once, best launch each, so that drift between candidates falls
+ * on all of them alike). Keeps the fastest and returns
  * it in *best with its time per eval in *best_us (CUDA events). Allocates
  * temporary output buffers and a stream for the duration of the call, which
  * synchronises with its own work before returning. */
