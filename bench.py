@@ -457,7 +457,8 @@ def main():
     elif args.no_autotune:
         best, tuned_us = M0.get_launch(), None
     else:
-        best, tuned_us = M0.autotune(xs[0], ls[0], reps=20, stream=stream)
+        ranked = M0.autotune_list(xs[0], ls[0], reps=20, max_shapes=4, stream=stream)
+        best, tuned_us = ranked[0]
     for Mk in models:
         Mk.set_launch(**best)
     torch.cuda.synchronize()
@@ -496,6 +497,41 @@ def main():
             e1.record(stream)
         torch.cuda.synchronize()
         return max_over_ranks(e0.elapsed_time(e1), dist, dev)
+
+    # the tuner times one buffer set (resident in L2); this benchmark rotates
+    # R sets (data from HBM), where shapes within a few percent of each other
+    # in the tuner can swap places: its finalists are re-timed here, as R-step
+    # graphs, best of 3 interleaved rounds, and the fastest is kept (each
+    # rank on its own, without barriers: every rank tunes its own replica)
+    finalists = None
+    if not args.launch and not args.no_autotune and len(ranked) > 1:
+        graphs = []
+        for shape, _ in ranked:
+            for Mk in models:
+                Mk.set_launch(**shape)
+            graphs.append(capture(step, R))
+        bench_ms = [float("inf")] * len(ranked)
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            for gr in graphs:
+                gr.replay()  # warm-up
+        for rnd in range(3):
+            for q in range(len(ranked)):
+                k = (q + rnd) % len(ranked)
+                with torch.cuda.stream(stream):
+                    f0.record(stream)
+                    graphs[k].replay()
+                    f1.record(stream)
+                torch.cuda.synchronize()
+                bench_ms[k] = min(bench_ms[k], f0.elapsed_time(f1))
+        pick = min(range(len(ranked)), key=lambda k: bench_ms[k])
+        best, tuned_us = ranked[pick]
+        for Mk in models:
+            Mk.set_launch(**best)
+        finalists = [{"launch": shape, "tuner_us": us, "rotating_sets_us": 1000.0 * bench_ms[k] / R}
+                     for k, (shape, us) in enumerate(ranked)]
+        del graphs
+        torch.cuda.synchronize()
 
     def load_for(graph, seconds):
         """Untimed replays of a graph for about 'seconds' (the loaded window
@@ -713,6 +749,7 @@ def main():
             "jac_hess": {"us": jh_us, "evals_per_s": 1e6 / jh_us, "algorithmic_bytes": jac_hess_bytes(g, nnzh),
                          "frac": jac_hess_bytes(g, nnzh) / (jh_us * 1e-6) / 1e9 / hbm},
             "phase_us": ({"fused": bus_us} if fused else {"branch": br_us, "bus": bus_us}) | {"autotune_eval": tuned_us},
+            "launch_finalists": finalists,
             "fp64_roofline": fp64,
             "al_inner_iteration_us": al_us,
             "al_newton_step_us": {"value": newton_us, "cg_iterations": 50,

@@ -347,6 +347,17 @@ int opf_set_launch(opf_model *model, const opf_launch *cfg);
 int opf_autotune(opf_model *model, const double *d_x, const double *d_lambda, int32_t reps,
                  void *stream, opf_launch *best, double *best_us);
 
+/* opf_autotune that also returns its finalists: into the HOST arrays
+ * shapes[] and us[] (caller-owned, max_shapes >= 1 entries each) the shapes
+ * of its final stage, fastest first, with their times per evaluation in us,
+ * and their number in *n_shapes (at most max_shapes, at most eight). For a
+ * caller whose conditions differ from the tuner's (the tuner times one
+ * buffer set, resident in L2 for small models) and who re-times the few
+ * finalists under its own. Sets the model's shape to the fastest, as
+ * opf_autotune does. OPF_EINVAL for a null array or max_shapes < 1. */
+int opf_autotune_list(opf_model *model, const double *d_x, const double *d_lambda, int32_t reps,
+                      void *stream, opf_launch *shapes, double *us, int32_t max_shapes, int32_t *n_shapes);
+
 /* opf_eval_all_host without the final synchronisation, pipelined across
  * calls: inputs are copied in on an internal stream into one of two staging
  * slots, the evaluation runs on a second internal stream and the outputs

@@ -260,6 +260,30 @@ int opf_eval_phases(opf_model *m, int32_t phases, const double *d_x, const doubl
     return eval(m, mask_of(a), a, stream, phases);
 }
 
+namespace {
+// the device staging of the host-buffer calls: x, lambda, obj, grad, c, J,
+// H, each starting on a 512-byte boundary (like separately allocated
+// buffers; packed 8 bytes apart they slowed the kernels' stores)
+struct StageLayout {
+    size_t x, l, obj, g, c, j, h, words;
+};
+
+StageLayout stage_layout(const Model &M)
+{
+    auto up = [](int64_t k) { return (size_t)((k + 63) / 64 * 64); };  // doubles, 512-byte multiples
+    StageLayout L;
+    L.x = 0;
+    L.l = L.x + up(M.n);
+    L.obj = L.l + up(M.m);
+    L.g = L.obj + up(1);
+    L.c = L.g + up(M.n);
+    L.j = L.c + up(M.m);
+    L.h = L.j + up(M.nnzj);
+    L.words = L.h + up(M.nnzh);
+    return L;
+}
+}  // namespace
+
 int opf_eval_all_host(opf_model *m, const double *h_x, const double *h_lambda, double obj_weight,
                       double *h_obj, double *h_grad, double *h_c, double *h_jvals, double *h_hvals,
                       void *stream)
@@ -273,7 +297,8 @@ int opf_eval_all_host(opf_model *m, const double *h_x, const double *h_lambda, d
         return OPF_EINVAL;
     }
     // staging: x, lambda, obj, grad, c, J, H
-    const size_t need = sizeof(double) * (size_t)(M.n + M.m + 1 + M.n + M.m + M.nnzj + M.nnzh);
+    const StageLayout SL = stage_layout(M);
+    const size_t need = sizeof(double) * SL.words;
     if (M.stage_bytes < need) {
         if (M.stage)
             cudaFree(M.stage);
@@ -286,8 +311,8 @@ int opf_eval_all_host(opf_model *m, const double *h_x, const double *h_lambda, d
         }
         M.stage_bytes = need;
     }
-    double *dx = M.stage, *dl = dx + M.n, *dobj = dl + M.m, *dg = dobj + 1, *dc = dg + M.n;
-    double *dj = dc + M.m, *dh = dj + M.nnzj;
+    double *dx = M.stage + SL.x, *dl = M.stage + SL.l, *dobj = M.stage + SL.obj, *dg = M.stage + SL.g;
+    double *dc = M.stage + SL.c, *dj = M.stage + SL.j, *dh = M.stage + SL.h;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemcpyAsync(dx, h_x, sizeof(double) * M.n, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && h_hvals)
@@ -331,7 +356,8 @@ int opf_eval_all_host_async(opf_model *m, const double *h_x, const double *h_lam
         set_error("h_x is NULL, or h_lambda is NULL with h_hvals requested");
         return OPF_EINVAL;
     }
-    const size_t words = (size_t)(M.n + M.m + 1 + M.n + M.m + M.nnzj + M.nnzh);
+    const StageLayout SL = stage_layout(M);
+    const size_t words = SL.words;
     if (!M.s_cmp) {  // first use: two staging slots, three streams, events
         bool ok = true;
         for (int k = 0; k < 2 && ok; k++)
@@ -352,8 +378,9 @@ int opf_eval_all_host_async(opf_model *m, const double *h_x, const double *h_lam
     }
     const int k = M.aslot;
     M.aslot ^= 1;
-    double *dx = M.astage[k], *dl = dx + M.n, *dobj = dl + M.m, *dg = dobj + 1, *dc = dg + M.n;
-    double *dj = dc + M.m, *dh = dj + M.nnzj;
+    double *const base = M.astage[k];
+    double *dx = base + SL.x, *dl = base + SL.l, *dobj = base + SL.obj, *dg = base + SL.g;
+    double *dc = base + SL.c, *dj = base + SL.j, *dh = base + SL.h;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // copy-in after the compute that last read this slot (not after the
     // caller's stream: it waits for the previous call's outputs, and
@@ -568,8 +595,11 @@ float time_graph(Model &M, const EvalArgs &a, int reps, int launches, cudaStream
 }
 }  // namespace
 
-int opf_autotune(opf_model *m, const double *d_x, const double *d_lambda, int32_t reps, void *stream,
-                 opf_launch *best, double *best_us)
+namespace {
+// the autotuner; with `ranked`, also its finalists with their final-stage
+// times per evaluation (us), fastest first
+int autotune_impl(opf_model *m, const double *d_x, const double *d_lambda, int32_t reps, void *stream,
+                  opf_launch *best, double *best_us, std::vector<std::pair<double, opf_launch>> *ranked)
 {
     int rc = check_dev(m);
     if (rc)
@@ -682,6 +712,8 @@ int opf_autotune(opf_model *m, const double *d_x, const double *d_lambda, int32_
                 best_ms = fbest[k];
                 bestc = timed[k].second;
             }
+            if (!rc && ranked)
+                ranked->push_back({1000.0 * fbest[k] / reps, timed[k].second});
             if (execs[k])
                 cudaGraphExecDestroy(execs[k]);
             if (graphs[k])
@@ -706,6 +738,38 @@ int opf_autotune(opf_model *m, const double *d_x, const double *d_lambda, int32_
         *best = bestc;
     if (best_us)
         *best_us = 1000.0 * best_ms / reps;
+    if (ranked)
+        std::stable_sort(ranked->begin(), ranked->end(),
+                         [](const std::pair<double, opf_launch> &x, const std::pair<double, opf_launch> &y) {
+                             return x.first < y.first;
+                         });
+    return OPF_OK;
+}
+}  // namespace
+
+int opf_autotune(opf_model *m, const double *d_x, const double *d_lambda, int32_t reps, void *stream,
+                 opf_launch *best, double *best_us)
+{
+    return autotune_impl(m, d_x, d_lambda, reps, stream, best, best_us, nullptr);
+}
+
+int opf_autotune_list(opf_model *m, const double *d_x, const double *d_lambda, int32_t reps, void *stream,
+                      opf_launch *shapes, double *us, int32_t max_shapes, int32_t *n_shapes)
+{
+    if (!shapes || !us || !n_shapes || max_shapes < 1) {
+        set_error("opf_autotune_list needs shapes, us, n_shapes and max_shapes >= 1");
+        return OPF_EINVAL;
+    }
+    std::vector<std::pair<double, opf_launch>> ranked;
+    const int rc = autotune_impl(m, d_x, d_lambda, reps, stream, nullptr, nullptr, &ranked);
+    if (rc)
+        return rc;
+    const int32_t k = ranked.size() < (size_t)max_shapes ? (int32_t)ranked.size() : max_shapes;
+    for (int32_t q = 0; q < k; q++) {
+        shapes[q] = ranked[q].second;
+        us[q] = ranked[q].first;
+    }
+    *n_shapes = k;
     return OPF_OK;
 }
 

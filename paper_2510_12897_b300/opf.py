@@ -112,6 +112,8 @@ def lib():
         "opf_get_launch": [_vp, ctypes.POINTER(OpfLaunch)],
         "opf_set_launch": [_vp, ctypes.POINTER(OpfLaunch)],
         "opf_autotune": [_vp, _vp, _vp, ctypes.c_int32, _vp, ctypes.POINTER(OpfLaunch), _f64p],
+        "opf_autotune_list": [_vp, _vp, _vp, ctypes.c_int32, _vp, ctypes.POINTER(OpfLaunch), _f64p, ctypes.c_int32,
+                              ctypes.POINTER(ctypes.c_int32)],
         "opf_host_register": [_vp, ctypes.c_size_t],
         "opf_host_unregister": [_vp],
     }
@@ -406,3 +408,12 @@ class Model:
         _check(lib().opf_autotune(self.h, _ptr(x, self.n, "x"), _ptr(lam, self.m, "lambda"), int(reps),
                                   _stream(stream), ctypes.byref(cfg), ctypes.byref(us)))
         return cfg.as_dict(), us.value
+
+    def autotune_list(self, x, lam, reps: int = 20, max_shapes: int = 8, stream=None):
+        """The autotuner's finalists, fastest first: [(shape dict, us per eval)]."""
+        shapes = (OpfLaunch * int(max_shapes))()
+        us = (ctypes.c_double * int(max_shapes))()
+        k = ctypes.c_int32()
+        _check(lib().opf_autotune_list(self.h, _ptr(x, self.n, "x"), _ptr(lam, self.m, "lambda"), int(reps),
+                                       _stream(stream), shapes, us, int(max_shapes), ctypes.byref(k)))
+        return [(shapes[q].as_dict(), us[q]) for q in range(k.value)]

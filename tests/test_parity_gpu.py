@@ -302,6 +302,15 @@ def test_case10k_full(torch, oracle_mod):
     check_against_oracle(O, run_all(torch, M, x, lam, 1.0), x, lam, 1.0, "default ")
     best, _ = M.autotune(dev(torch, x), dev(torch, lam), reps=3)
     check_against_oracle(O, run_all(torch, M, x, lam, 1.0, best), x, lam, 1.0, "tuned ")
+    # the tuner's finalists (the benchmark re-times them under its own
+    # protocol): fastest first, the model left in the first, each correct
+    ranked = M.autotune_list(dev(torch, x), dev(torch, lam), reps=3, max_shapes=4)
+    assert 1 <= len(ranked) <= 4
+    assert all(ranked[k][1] <= ranked[k + 1][1] for k in range(len(ranked) - 1))
+    assert M.get_launch() == ranked[0][0]
+    for k, (shape, us) in enumerate(ranked):
+        assert us > 0
+        check_against_oracle(O, run_all(torch, M, x, lam, 1.0, shape), x, lam, 1.0, f"finalist {k} ")
 
 
 # one persistent kernel per evaluation of a whole batch: the fused layout
