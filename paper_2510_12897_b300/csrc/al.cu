@@ -47,6 +47,11 @@ struct opf_al {
     double *cgs = nullptr;  // device scalars of the step (see nt_scalar_kernel), delta kept across steps
     double *mdiag = nullptr;  // Jacobi diagonal of K
     unsigned char *F = nullptr;  // free entries
+    // the CG loop of a step as one CUDA graph (its kernels read only the
+    // loop's own buffers), captured for one iteration count at a time
+    cudaGraphExec_t cg_exec = nullptr;
+    int cg_iters = 0;
+    unsigned *ticket = nullptr;  // last-block counter of the CG reductions (0 between launches)
 };
 
 // the Newton step's device scalars (opf_al_newton)
@@ -83,6 +88,10 @@ void al_drop_graphs(opf_al *a)
     for (auto &g : a->graphs)
         cudaGraphExecDestroy(g.exec);
     a->graphs.clear();
+    if (a->cg_exec)
+        cudaGraphExecDestroy(a->cg_exec);
+    a->cg_exec = nullptr;
+    a->cg_iters = 0;
 }
 
 void al_free(opf_al *a)
@@ -458,98 +467,12 @@ __global__ void nt_jd_kernel(int64_t m, const int32_t *jptr, const int32_t *jcol
     }
 }
 
-// q = ((K + delta diag(M)) d) on the free set: the lower triangle, its
-// transpose, rho J^T t, delta M_j d_j; block partials of d^T q
-__global__ void nt_kd_kernel(int64_t n, const int32_t *hptr, const int32_t *hcol, const double *hv,
-                             const int32_t *uptr, const int32_t *ucol, const int32_t *uperm, const int32_t *tptr,
-                             const int32_t *trow, const int32_t *tperm, const double *jv, const double *t, double rho,
-                             const unsigned char *F, const double *mdiag, const double *dv, double *q, double *part,
-                             int nparts, const double *cgs)
-{
-    __shared__ double red[32];
-    if (cgs[CG_DONE] != 0.0)
-        return;
-    const double delta = cgs[CG_DELTA];
-    double acc = 0.0;
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
-        double h = 0.0, a = 0.0;
-        for (int32_t k = hptr[j]; k < hptr[j + 1]; k++)
-            h = fma(hv[k], dv[hcol[k]], h);
-        for (int32_t k = uptr[j]; k < uptr[j + 1]; k++)
-            h = fma(hv[uperm[k]], dv[ucol[k]], h);
-        for (int32_t k = tptr[j]; k < tptr[j + 1]; k++)
-            a = fma(jv[tperm[k]], t[trow[k]], a);
-        const double qj = F[j] ? fma(delta * mdiag[j], dv[j], fma(rho, a, h)) : 0.0;
-        q[j] = qj;
-        acc = fma(dv[j], qj, acc);
-    }
-    const double b = block_sum(acc, red);
-    if (threadIdx.x == 0)
-        part[blockIdx.x] = b;
-}
-
-// p += alpha d, r -= alpha q, z = r / M; block partials of r^T z (or, where
-// the first curvature test failed, p = d)
-__global__ void nt_update_kernel(int64_t n, const double *dv, const double *q, const double *minv, double *p, double *r,
-                                 double *z, double *part, int nparts, const double *cgs)
-{
-    __shared__ double red[32];
-    if (cgs[CG_DONE] != 0.0) {
-        if (cgs[CG_COPY] != 0.0)
-            for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
-                 j += (int64_t)gridDim.x * blockDim.x)
-                p[j] = dv[j];
-        return;
-    }
-    const double a = cgs[CG_ALPHA];
-    double acc = 0.0;
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
-        p[j] = fma(a, dv[j], p[j]);
-        const double rj = fma(-a, q[j], r[j]);
-        const double zj = rj * minv[j];
-        r[j] = rj;
-        z[j] = zj;
-        acc = fma(rj, zj, acc);
-    }
-    const double b = block_sum(acc, red);
-    if (threadIdx.x == 0)
-        part[blockIdx.x] = b;
-}
-
-// d = z + beta d
-__global__ void nt_dir_kernel(int64_t n, const double *z, double *dv, const double *cgs)
-{
-    if (cgs[CG_DONE] != 0.0)
-        return;
-    const double b = cgs[CG_BETA];
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
-        dv[j] = fma(b, dv[j], z[j]);
-}
-
-// block partials of a^T b
-__global__ void nt_dot_kernel(int64_t n, const double *a, const double *b, double *part, int nparts)
-{
-    __shared__ double red[32];
-    double acc = 0.0;
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
-        acc = fma(a[j], b[j], acc);
-    const double s = block_sum(acc, red);
-    if (threadIdx.x == 0)
-        part[blockIdx.x] = s;
-}
-
 enum { NT_INIT, NT_DQ, NT_RZ, NT_GP, NT_PMAX };
 
 // the sum of the partials (one warp, fixed order) and the step's scalar logic
-__global__ void nt_scalar_kernel(const double *part, int nparts, double *cgs, int mode, int k)
+// the scalar step of a mode from the sum v of the partials (one thread)
+__device__ void nt_scalar_apply(double v, double *cgs, int mode, int k)
 {
-    double v = 0.0;
-    for (int q = threadIdx.x; q < nparts; q += 32)
-        v += part[q];
-    for (int off = 16; off; off >>= 1)
-        v += __shfl_down_sync(0xffffffffu, v, off);
-    if (threadIdx.x != 0)
-        return;
     if (mode == NT_INIT) {
         cgs[CG_RZ] = cgs[CG_RZ0] = v;
         cgs[CG_DONE] = v == 0.0 ? 1.0 : 0.0;
@@ -575,6 +498,127 @@ __global__ void nt_scalar_kernel(const double *part, int nparts, double *cgs, in
     } else {
         cgs[CG_GP] = v;
     }
+}
+
+// one warp: the partials summed in a fixed order (lane-strided, then a
+// shuffle tree), then the mode's scalar step by lane 0
+__device__ void nt_scalar_warp(const double *part, int nparts, double *cgs, int mode, int k)
+{
+    double v = 0.0;
+    for (int q = threadIdx.x; q < nparts; q += 32)
+        v += __ldcg(part + q);  // through L2: other blocks' partials
+    for (int off = 16; off; off >>= 1)
+        v += __shfl_down_sync(0xffffffffu, v, off);
+    if (threadIdx.x == 0)
+        nt_scalar_apply(v, cgs, mode, k);
+}
+
+__global__ void nt_scalar_kernel(const double *part, int nparts, double *cgs, int mode, int k)
+{
+    nt_scalar_warp(part, nparts, cgs, mode, k);
+}
+
+// the end of a kernel whose nparts (= gridDim.x) blocks each wrote one
+// partial: every block takes a ticket after its partial is visible, and the
+// block with the last ticket runs the scalar step (nt_scalar_warp, the same
+// fixed-order sum) and returns the ticket to 0 for the next launch. Only
+// that block writes the scalars, after every block has read them.
+__device__ void nt_scalar_last(const double *part, int nparts, double *cgs, int mode, int k, unsigned *ticket)
+{
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        __threadfence();  // this block's partial before its ticket
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last || threadIdx.x >= 32)
+        return;
+    __threadfence();
+    nt_scalar_warp(part, nparts, cgs, mode, k);
+    if (threadIdx.x == 0)
+        *ticket = 0u;
+}
+
+// q = ((K + delta diag(M)) d) on the free set: the lower triangle, its
+// transpose, rho J^T t, delta M_j d_j; block partials of d^T q
+__global__ void nt_kd_kernel(int64_t n, const int32_t *hptr, const int32_t *hcol, const double *hv,
+                             const int32_t *uptr, const int32_t *ucol, const int32_t *uperm, const int32_t *tptr,
+                             const int32_t *trow, const int32_t *tperm, const double *jv, const double *t, double rho,
+                             const unsigned char *F, const double *mdiag, const double *dv, double *q, double *part,
+                             int nparts, double *cgs, int k_iter, unsigned *ticket)
+{
+    __shared__ double red[32];
+    if (cgs[CG_DONE] != 0.0)
+        return;
+    const double delta = cgs[CG_DELTA];
+    double acc = 0.0;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        double h = 0.0, a = 0.0;
+        for (int32_t k = hptr[j]; k < hptr[j + 1]; k++)
+            h = fma(hv[k], dv[hcol[k]], h);
+        for (int32_t k = uptr[j]; k < uptr[j + 1]; k++)
+            h = fma(hv[uperm[k]], dv[ucol[k]], h);
+        for (int32_t k = tptr[j]; k < tptr[j + 1]; k++)
+            a = fma(jv[tperm[k]], t[trow[k]], a);
+        const double qj = F[j] ? fma(delta * mdiag[j], dv[j], fma(rho, a, h)) : 0.0;
+        q[j] = qj;
+        acc = fma(dv[j], qj, acc);
+    }
+    const double b = block_sum(acc, red);
+    if (threadIdx.x == 0)
+        part[blockIdx.x] = b;
+    nt_scalar_last(part, nparts, cgs, NT_DQ, k_iter, ticket);  // d^T q: alpha or the stop
+}
+
+// p += alpha d, r -= alpha q, z = r / M; block partials of r^T z (or, where
+// the first curvature test failed, p = d)
+__global__ void nt_update_kernel(int64_t n, const double *dv, const double *q, const double *minv, double *p, double *r,
+                                 double *z, double *part, int nparts, double *cgs, int k_iter, unsigned *ticket)
+{
+    __shared__ double red[32];
+    if (cgs[CG_DONE] != 0.0) {
+        if (cgs[CG_COPY] != 0.0)
+            for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+                 j += (int64_t)gridDim.x * blockDim.x)
+                p[j] = dv[j];
+        return;
+    }
+    const double a = cgs[CG_ALPHA];
+    double acc = 0.0;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        p[j] = fma(a, dv[j], p[j]);
+        const double rj = fma(-a, q[j], r[j]);
+        const double zj = rj * minv[j];
+        r[j] = rj;
+        z[j] = zj;
+        acc = fma(rj, zj, acc);
+    }
+    const double b = block_sum(acc, red);
+    if (threadIdx.x == 0)
+        part[blockIdx.x] = b;
+    nt_scalar_last(part, nparts, cgs, NT_RZ, k_iter, ticket);  // r^T z: beta or the stop
+}
+
+// d = z + beta d
+__global__ void nt_dir_kernel(int64_t n, const double *z, double *dv, const double *cgs)
+{
+    if (cgs[CG_DONE] != 0.0)
+        return;
+    const double b = cgs[CG_BETA];
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+        dv[j] = fma(b, dv[j], z[j]);
+}
+
+// block partials of a^T b
+__global__ void nt_dot_kernel(int64_t n, const double *a, const double *b, double *part, int nparts)
+{
+    __shared__ double red[32];
+    double acc = 0.0;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+        acc = fma(a[j], b[j], acc);
+    const double s = block_sum(acc, red);
+    if (threadIdx.x == 0)
+        part[blockIdx.x] = s;
 }
 
 // max |p_j| (block partials, then one warp): the step's cap, scale =
@@ -748,6 +792,7 @@ int nt_setup(opf_al *a)
     if (!rc) rc = al_alloc(a, &a->Dm, m);
     if (!rc) rc = al_alloc(a, &a->tstats, 3 * (kNls + 1));
     if (!rc) rc = al_alloc(a, &a->cgs, CG_N);
+    if (!rc) rc = al_alloc(a, &a->ticket, 1);
     if (!rc) rc = al_alloc(a, &a->F, n);
     if (!rc) rc = al_alloc(a, &a->mdiag, n);
     if (!rc)
@@ -758,6 +803,62 @@ int nt_setup(opf_al *a)
 }
 
 // one projected Newton-CG step on stream s (see opf_al_newton)
+// the CG iterations of a step, four kernels each (the d^T q and r^T z
+// scalar steps run in the last block of the kernels that form the partials),
+// launched on stream s
+void nt_cg_kernels(opf_al *a, int cg_iters, cudaStream_t s)
+{
+    const int64_t n = a->n, m = a->m;
+    const int gn = grid_of(n), gm = grid_of(m), np = a->nparts;
+    for (int k = 0; k < cg_iters; k++) {
+        nt_jd_kernel<<<gm, 256, 0, s>>>(m, a->jptr, a->jcol, a->jv, a->Dm, a->dv, a->t, a->cgs);
+        nt_kd_kernel<<<np, 256, 0, s>>>(n, a->hptr, a->hcol, a->hv, a->uptr, a->ucol, a->uperm, a->tptr, a->trow,
+                                        a->tperm, a->jv, a->t, a->rho, a->F, a->mdiag, a->dv, a->q, a->part, np,
+                                        a->cgs, k, a->ticket);
+        nt_update_kernel<<<np, 256, 0, s>>>(n, a->dv, a->q, a->minv, a->p, a->r, a->z, a->part, np, a->cgs, k,
+                                            a->ticket);
+        nt_dir_kernel<<<gn, 256, 0, s>>>(n, a->z, a->dv, a->cgs);
+    }
+}
+
+// the CG iterations as one CUDA graph (captured on the loop's private
+// stream, replayed on the caller's): the kernels read only the loop's own
+// buffers and rho, so the graph serves every step with the same iteration
+// count until a reset changes rho
+int nt_cg_graph(opf_al *a, int cg_iters, cudaGraphExec_t *out)
+{
+    if (a->cg_exec && a->cg_iters == cg_iters) {
+        *out = a->cg_exec;
+        return OPF_OK;
+    }
+    if (a->cg_exec)
+        cudaGraphExecDestroy(a->cg_exec);
+    a->cg_exec = nullptr;
+    a->cg_iters = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int rc = al_check(cudaStreamBeginCapture(a->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+    if (rc)
+        return rc;
+    nt_cg_kernels(a, cg_iters, a->cap);
+    const cudaError_t le = cudaGetLastError();
+    const cudaError_t e = cudaStreamEndCapture(a->cap, &graph);
+    if (le != cudaSuccess)
+        rc = al_check(le, "CG kernels");
+    else if (e != cudaSuccess)
+        rc = al_check(e, "end capture");
+    else
+        rc = al_check(cudaGraphInstantiate(&exec, graph, 0), "graph instantiate");
+    if (graph)
+        cudaGraphDestroy(graph);
+    if (rc)
+        return rc;
+    a->cg_exec = exec;
+    a->cg_iters = cg_iters;
+    *out = exec;
+    return OPF_OK;
+}
+
 int nt_step(opf_al *a, double *d_x, const double *d_lambda, int cg_iters, double *d_stats, cudaStream_t s)
 {
     const int64_t n = a->n, m = a->m;
@@ -780,17 +881,12 @@ int nt_step(opf_al *a, double *d_x, const double *d_lambda, int cg_iters, double
                                        a->rho, d_x, a->xl, a->xu, a->G, a->F, a->mdiag, a->minv, a->r, a->z, a->dv,
                                        a->p, a->part, np, a->cgs);
     nt_scalar_kernel<<<1, 32, 0, s>>>(a->part, np, a->cgs, NT_INIT, 0);
-    for (int k = 0; k < cg_iters; k++) {
-        nt_jd_kernel<<<gm, 256, 0, s>>>(m, a->jptr, a->jcol, a->jv, a->Dm, a->dv, a->t, a->cgs);
-        nt_kd_kernel<<<np, 256, 0, s>>>(n, a->hptr, a->hcol, a->hv, a->uptr, a->ucol, a->uperm, a->tptr, a->trow,
-                                        a->tperm, a->jv, a->t, a->rho, a->F, a->mdiag, a->dv, a->q, a->part, np,
-                                        a->cgs);
-        nt_scalar_kernel<<<1, 32, 0, s>>>(a->part, np, a->cgs, NT_DQ, k);
-        nt_update_kernel<<<np, 256, 0, s>>>(n, a->dv, a->q, a->minv, a->p, a->r, a->z, a->part, np, a->cgs);
-        nt_scalar_kernel<<<1, 32, 0, s>>>(a->part, np, a->cgs, NT_RZ, k);
-        nt_dir_kernel<<<gn, 256, 0, s>>>(n, a->z, a->dv, a->cgs);
-    }
-    rc = al_check(cudaGetLastError(), "CG kernels");
+    cudaGraphExec_t cg = nullptr;
+    rc = nt_cg_graph(a, cg_iters, &cg);
+    if (!rc)  // the counter is 0 after every complete launch; set it so for this step in any case
+        rc = al_check(cudaMemsetAsync(a->ticket, 0, sizeof(unsigned), s), "CG ticket");
+    if (!rc)
+        rc = al_check(cudaGraphLaunch(cg, s), "CG graph launch");
     if (rc)
         return rc;
     // no entry moves by more than 1 (per-unit) in one step
