@@ -35,18 +35,6 @@ __device__ __forceinline__ long long order_key(double x)
     return b >= 0 ? b : b ^ 0x7FFFFFFFFFFFFFFFll;
 }
 
-// x - clip(x, lo, hi): 0 inside the bounds (no FP64 instruction), one
-// subtraction outside; a NaN x stays NaN
-__device__ __forceinline__ double excess(double x, double lo, double hi)
-{
-    const long long kx = order_key(x);
-    if (kx < order_key(lo))
-        return x - lo;
-    if (kx > order_key(hi))
-        return x - hi;
-    return 0.0;
-}
-
 // x - clip(x, -h, h) for h >= 0: 0 inside (no FP64 instruction), one
 // subtraction outside, its sign from the sign bit; a NaN x stays NaN
 __device__ __forceinline__ double excess_sym(double x, double h)
