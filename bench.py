@@ -866,6 +866,12 @@ def batched_vs_plain(torch, opf, synth, stream, dev, cpu=False):
     out["mp2k_96"] = {"batched_us": tb, "plain_loop_us": tp, "speedup": tp / tb, "launch": tuned,
                       "one_kernel_us": t1, "one_kernel_speedup": tp / t1,
                       "batched_evals_per_s": 1e6 / tb, "period_evals_per_s": 96e6 / tb}
+    if cpu:  # the oracle over the periods, one thread per host core
+        rate, k, el, cores = cpu_oracle_threads(grids[:32], 10.0)
+        out["mp2k_96"]["cpu_oracle_threads"] = {
+            "value": rate, "unit": "period evals/s", "cores": cores, "kind": "oracle",
+            "sample": f"{k} full evaluations of single-period models of 32 of the 96 periods in {el:.1f} s, "
+                      "one thread per core (the ramp rows, which couple the periods, left out)"}
     n_mp, m_mp = B.n, B.m
     del B, singles, os_
     # the same multi-period model with storage units (Sec. III-C-2) and
