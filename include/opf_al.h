@@ -86,7 +86,9 @@ int opf_al_update(opf_al *al, const double *d_x, double *d_lambda, double *d_sta
  * order reduction and every scalar stays on the device (no host round
  * trip). d_stats (3 doubles, may be NULL) as in opf_al_iterate, at the new
  * x; d_step (n, may be NULL) receives p. cg_iters >= 1. The Adam state is
- * not touched. The paper's interior-point solvers (Sec. IV-A) take Newton
+ * not touched. The first call builds the sparse structures; the CG
+ * iterations are captured once per cg_iters as a CUDA graph and replayed
+ * (opf_al_reset drops it, since it holds rho). The paper's interior-point solvers (Sec. IV-A) take Newton
  * steps on the KKT system with a sparse direct solver; this is the matrix-
  * free counterpart on the augmented Lagrangian. */
 int opf_al_newton(opf_al *al, double *d_x, const double *d_lambda, int32_t cg_iters, double *d_stats,
