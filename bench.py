@@ -457,7 +457,7 @@ def main():
     elif args.no_autotune:
         best, tuned_us = M0.get_launch(), None
     else:
-        ranked = M0.autotune_list(xs[0], ls[0], reps=20, max_shapes=4, stream=stream)
+        ranked = M0.autotune_list(xs[0], ls[0], reps=20, max_shapes=12, stream=stream)
         best, tuned_us = ranked[0]
     for Mk in models:
         Mk.set_launch(**best)
@@ -500,7 +500,8 @@ def main():
 
     # the tuner times one buffer set (resident in L2); this benchmark rotates
     # R sets (data from HBM), where shapes within a few percent of each other
-    # in the tuner can swap places: its finalists are re-timed here, as R-step
+    # in the tuner can swap places: its finalists (the fastest of each
+    # structural class among them) are re-timed here, as R-step
     # graphs, best of 3 interleaved rounds, and the fastest is kept (each
     # rank on its own, without barriers: every rank tunes its own replica)
     finalists = None

@@ -338,9 +338,11 @@ int opf_set_launch(opf_model *model, const opf_launch *cfg);
  * bus order, branch occupancy) of the fused opf_eval_all on this model as a
  * CUDA graph of `reps` back-to-back evaluations (the way a solver loop
  * replays them), on a private stream that first waits for `stream`; the
- * eight fastest are then timed again in six interleaved rounds (each
- * captured once, best launch each, so that drift between candidates falls
- * on all of them alike). Keeps the fastest and returns
+ * finalists (the fastest shape of each class of bus order and branch
+ * occupancy, then the fastest others, twelve at most) are then timed again
+ * in six interleaved rounds (each captured once, best launch each, so that
+ * drift between candidates falls on all of them alike). Keeps the fastest
+ * and returns
  * it in *best with its time per eval in *best_us (CUDA events). Allocates
  * temporary output buffers and a stream for the duration of the call, which
  * synchronises with its own work before returning. */
@@ -350,7 +352,7 @@ int opf_autotune(opf_model *model, const double *d_x, const double *d_lambda, in
 /* opf_autotune that also returns its finalists: into the HOST arrays
  * shapes[] and us[] (caller-owned, max_shapes >= 1 entries each) the shapes
  * of its final stage, fastest first, with their times per evaluation in us,
- * and their number in *n_shapes (at most max_shapes, at most eight). For a
+ * and their number in *n_shapes (at most max_shapes, at most twelve). For a
  * caller whose conditions differ from the tuner's (the tuner times one
  * buffer set, resident in L2 for small models) and who re-times the few
  * finalists under its own. Sets the model's shape to the fastest, as

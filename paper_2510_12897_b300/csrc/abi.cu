@@ -671,12 +671,44 @@ int autotune_impl(opf_model *m, const double *d_x, const double *d_lambda, int32
                   [](const std::pair<float, opf_launch> &x, const std::pair<float, opf_launch> &y) {
                       return x.first < y.first;
                   });
-        // stage 2: the 8 fastest, each captured once, then timed in 6
+        // stage 2: the finalists, each captured once, then timed in 6
         // interleaved rounds (the round's first candidate rotating), best
         // launch each: drift of clocks or power between candidates falls on
         // all of them alike, and the top shapes (often within a few percent
-        // of each other) are compared under the same conditions
-        const size_t nf = timed.size() < 8 ? timed.size() : 8;
+        // of each other) are compared under the same conditions. The
+        // finalists are the fastest candidate of each structural class (bus
+        // order and branch occupancy: different kernels, which a caller
+        // with other conditions may rank differently), then the fastest of
+        // the rest, 12 in all at most
+        {
+            auto same = [](const opf_launch &x, const opf_launch &y) {
+                return x.branch_block == y.branch_block && x.bus_block == y.bus_block &&
+                       x.branch_ctas_per_sm == y.branch_ctas_per_sm && x.bus_ctas_per_sm == y.bus_ctas_per_sm &&
+                       x.bus_order == y.bus_order && x.branch_occupancy == y.branch_occupancy;
+            };
+            std::vector<std::pair<float, opf_launch>> finals;
+            bool seen[16] = {};
+            for (const auto &c : timed) {
+                const int cls = (c.second.bus_order & 3) * 4 + (c.second.branch_occupancy & 3);
+                if (!seen[cls]) {
+                    seen[cls] = true;
+                    finals.push_back(c);
+                }
+            }
+            for (const auto &c : timed) {
+                if (finals.size() >= 12)
+                    break;
+                bool in = false;
+                for (const auto &f : finals)
+                    in = in || same(f.second, c.second);
+                if (!in)
+                    finals.push_back(c);
+            }
+            if (finals.size() > 12)
+                finals.resize(12);
+            timed.swap(finals);
+        }
+        const size_t nf = timed.size();
         std::vector<cudaGraph_t> graphs(nf, nullptr);
         std::vector<cudaGraphExec_t> execs(nf, nullptr);
         std::vector<float> fbest(nf, 1e30f);
