@@ -52,6 +52,11 @@ struct opf_al {
     cudaGraphExec_t cg_exec = nullptr;
     int cg_iters = 0;
     unsigned *ticket = nullptr;  // last-block counter of the CG reductions (0 between launches)
+    // the step's Jacobian values in CSC order (jv[tperm]) and the Hessian's
+    // strict upper part in its CSR order (hv[uperm]), gathered once per step
+    // so that the CG products read them without the permutation
+    double *jvt = nullptr, *hvu = nullptr;
+    int64_t nu = 0;  // strict upper entries of the Hessian
 };
 
 // the Newton step's device scalars (opf_al_newton)
@@ -402,6 +407,19 @@ constexpr int kNls = 8;  // trial step lengths 1, 1/2, ..., 1/128
 // M_j = H_jj + rho sum_i D_i J_ij^2 (1 where <= 1e-12) and the inverse of
 // the preconditioner M_j (1 + delta); r = -G on the free set, z, d = z,
 // p = 0; block partials of r^T z
+// out[k] = v[perm[k]] for k < count, two arrays in one pass
+__global__ void nt_gather_kernel(int64_t n1, const int32_t *perm1, const double *v1, double *out1, int64_t n2,
+                                 const int32_t *perm2, const double *v2, double *out2)
+{
+    const int64_t total = n1 > n2 ? n1 : n2;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
+        if (k < n1)
+            out1[k] = v1[perm1[k]];
+        if (k < n2)
+            out2[k] = v2[perm2[k]];
+    }
+}
+
 __global__ void nt_setup_kernel(int64_t n, const double *grad, const double *jv, const int32_t *tptr,
                                 const int32_t *trow, const int32_t *tperm, const double *mu, const double *Dm,
                                 const double *hv, const int32_t *hdiag, double rho, const double *x, const double *xl,
@@ -542,8 +560,8 @@ __device__ void nt_scalar_last(const double *part, int nparts, double *cgs, int 
 // q = ((K + delta diag(M)) d) on the free set: the lower triangle, its
 // transpose, rho J^T t, delta M_j d_j; block partials of d^T q
 __global__ void nt_kd_kernel(int64_t n, const int32_t *hptr, const int32_t *hcol, const double *hv,
-                             const int32_t *uptr, const int32_t *ucol, const int32_t *uperm, const int32_t *tptr,
-                             const int32_t *trow, const int32_t *tperm, const double *jv, const double *t, double rho,
+                             const int32_t *uptr, const int32_t *ucol, const double *hvu, const int32_t *tptr,
+                             const int32_t *trow, const double *jvt, const double *t, double rho,
                              const unsigned char *F, const double *mdiag, const double *dv, double *q, double *part,
                              int nparts, double *cgs, int k_iter, unsigned *ticket)
 {
@@ -557,9 +575,9 @@ __global__ void nt_kd_kernel(int64_t n, const int32_t *hptr, const int32_t *hcol
         for (int32_t k = hptr[j]; k < hptr[j + 1]; k++)
             h = fma(hv[k], dv[hcol[k]], h);
         for (int32_t k = uptr[j]; k < uptr[j + 1]; k++)
-            h = fma(hv[uperm[k]], dv[ucol[k]], h);
+            h = fma(hvu[k], dv[ucol[k]], h);
         for (int32_t k = tptr[j]; k < tptr[j + 1]; k++)
-            a = fma(jv[tperm[k]], t[trow[k]], a);
+            a = fma(jvt[k], t[trow[k]], a);
         const double qj = F[j] ? fma(delta * mdiag[j], dv[j], fma(rho, a, h)) : 0.0;
         q[j] = qj;
         acc = fma(dv[j], qj, acc);
@@ -785,6 +803,9 @@ int nt_setup(opf_al *a)
     if (!rc) rc = up(&a->hdiag, hdiag);
     if (!rc) rc = al_alloc(a, &a->jv, nj);
     if (!rc) rc = al_alloc(a, &a->hv, nh);
+    if (!rc) rc = al_alloc(a, &a->jvt, nj);
+    if (!rc) rc = al_alloc(a, &a->hvu, ucol.size());
+    a->nu = (int64_t)ucol.size();
     for (double **v : {&a->G, &a->r, &a->z, &a->dv, &a->q, &a->p, &a->minv, &a->xt})
         if (!rc)
             rc = al_alloc(a, v, n);
@@ -812,9 +833,9 @@ void nt_cg_kernels(opf_al *a, int cg_iters, cudaStream_t s)
     const int gn = grid_of(n), gm = grid_of(m), np = a->nparts;
     for (int k = 0; k < cg_iters; k++) {
         nt_jd_kernel<<<gm, 256, 0, s>>>(m, a->jptr, a->jcol, a->jv, a->Dm, a->dv, a->t, a->cgs);
-        nt_kd_kernel<<<np, 256, 0, s>>>(n, a->hptr, a->hcol, a->hv, a->uptr, a->ucol, a->uperm, a->tptr, a->trow,
-                                        a->tperm, a->jv, a->t, a->rho, a->F, a->mdiag, a->dv, a->q, a->part, np,
-                                        a->cgs, k, a->ticket);
+        nt_kd_kernel<<<np, 256, 0, s>>>(n, a->hptr, a->hcol, a->hv, a->uptr, a->ucol, a->hvu, a->tptr, a->trow,
+                                        a->jvt, a->t, a->rho, a->F, a->mdiag, a->dv, a->q, a->part, np, a->cgs, k,
+                                        a->ticket);
         nt_update_kernel<<<np, 256, 0, s>>>(n, a->dv, a->q, a->minv, a->p, a->r, a->z, a->part, np, a->cgs, k,
                                             a->ticket);
         nt_dir_kernel<<<gn, 256, 0, s>>>(n, a->z, a->dv, a->cgs);
@@ -877,6 +898,10 @@ int nt_step(opf_al *a, double *d_x, const double *d_lambda, int cg_iters, double
     rc = launch_eval(*a->M, eh, W_HESS, s);
     if (rc)
         return rc;
+    {
+        const int64_t nj = a->M->nnzj, big = nj > a->nu ? nj : a->nu;
+        nt_gather_kernel<<<grid_of(big), 256, 0, s>>>(nj, a->tperm, a->jv, a->jvt, a->nu, a->uperm, a->hv, a->hvu);
+    }
     nt_setup_kernel<<<np, 256, 0, s>>>(n, a->grad, a->jv, a->tptr, a->trow, a->tperm, a->mu, a->Dm, a->hv, a->hdiag,
                                        a->rho, d_x, a->xl, a->xu, a->G, a->F, a->mdiag, a->minv, a->r, a->z, a->dv,
                                        a->p, a->part, np, a->cgs);
