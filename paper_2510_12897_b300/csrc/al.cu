@@ -470,6 +470,34 @@ __global__ void nt_active_kernel(int64_t m, const double *c, const double *lam, 
     }
 }
 
+// acc + sum over e in [e0, e1) of val[e] x[idx[e]], added in order of e:
+// the first eight entries' indices and values are loaded together and then
+// their gathers (a row's loads in flight at once rather than one dependent
+// pair per entry), the rest one by one
+__device__ __forceinline__ double row_dot(const int32_t *idx, const double *val, const double *x, int32_t e0,
+                                          int32_t e1, double acc)
+{
+    int32_t c[8];
+    double v[8], g[8];
+#pragma unroll
+    for (int u = 0; u < 8; u++)
+        if (e0 + u < e1) {
+            c[u] = __ldg(idx + e0 + u);
+            v[u] = __ldg(val + e0 + u);
+        }
+#pragma unroll
+    for (int u = 0; u < 8; u++)
+        if (e0 + u < e1)
+            g[u] = x[c[u]];
+#pragma unroll
+    for (int u = 0; u < 8; u++)
+        if (e0 + u < e1)
+            acc = fma(v[u], g[u], acc);
+    for (int32_t e = e0 + 8; e < e1; e++)
+        acc = fma(val[e], x[idx[e]], acc);
+    return acc;
+}
+
 // t_i = D_i (J d)_i
 __global__ void nt_jd_kernel(int64_t m, const int32_t *jptr, const int32_t *jcol, const double *jv, const double *Dm,
                              const double *dv, double *t, const double *cgs)
@@ -479,8 +507,7 @@ __global__ void nt_jd_kernel(int64_t m, const int32_t *jptr, const int32_t *jcol
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
         double acc = 0.0;
         if (Dm[i] != 0.0)
-            for (int32_t k = jptr[i]; k < jptr[i + 1]; k++)
-                acc = fma(jv[k], dv[jcol[k]], acc);
+            acc = row_dot(jcol, jv, dv, jptr[i], jptr[i + 1], acc);
         t[i] = acc;
     }
 }
@@ -571,13 +598,9 @@ __global__ void nt_kd_kernel(int64_t n, const int32_t *hptr, const int32_t *hcol
     const double delta = cgs[CG_DELTA];
     double acc = 0.0;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
-        double h = 0.0, a = 0.0;
-        for (int32_t k = hptr[j]; k < hptr[j + 1]; k++)
-            h = fma(hv[k], dv[hcol[k]], h);
-        for (int32_t k = uptr[j]; k < uptr[j + 1]; k++)
-            h = fma(hvu[k], dv[ucol[k]], h);
-        for (int32_t k = tptr[j]; k < tptr[j + 1]; k++)
-            a = fma(jvt[k], t[trow[k]], a);
+        double h = row_dot(hcol, hv, dv, hptr[j], hptr[j + 1], 0.0);
+        h = row_dot(ucol, hvu, dv, uptr[j], uptr[j + 1], h);
+        const double a = row_dot(trow, jvt, t, tptr[j], tptr[j + 1], 0.0);
         const double qj = F[j] ? fma(delta * mdiag[j], dv[j], fma(rho, a, h)) : 0.0;
         q[j] = qj;
         acc = fma(dv[j], qj, acc);
