@@ -209,7 +209,9 @@ __global__ void __launch_bounds__(256) jt_bus_kernel(const KParams P)
         const int64_t V = I.c0;  // the vector v, indexed like the rows
         double *o = P.grad + I.x0;
         if (it < P.nbus_items) {
-            const int i = e, ib = I.bus0 + i;
+            // buses in the arc-count order (lanes of a warp walk similar
+            // slot counts); the bus's entries are its own wherever it lands
+            const int i = __ldg(d.bus_order + I.bus0 + e), ib = I.bus0 + i;
             const int4 a = __ldg(d.bus_a + ib);
             const double2 gb = __ldg(d.gsbs + ib);
             const double vm = __ldg(xs + nbT + nb * t + i);
@@ -226,10 +228,24 @@ __global__ void __launch_bounds__(256) jt_bus_kernel(const KParams P)
                 dva = i == I.ref ? vrow<AL>(P, V + t) : 0.0;
                 dvm = twice(vm * fma(gb.x, vP, neg(gb.y * vQ)));  // 2 vm (gs vP - bs vQ)
             }
-            for (int q = 0; q < a.y - a.x; q++) {
-                const double2 w = __ldcg(Sg + 3 * q);
-                dva += w.x;
-                dvm += w.y;
+            // the slots' records four at a time (their loads together), added
+            // in slot order; the warp leaves once no lane has another slot
+            const int nsl = a.y - a.x;
+            for (int q0 = 0; q0 < nsl; q0 += 4) {
+                double2 w[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++)
+                    if (q0 + u < nsl)
+                        w[u] = __ldcg(Sg + 3 * (q0 + u));
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    if (!__any_sync(__activemask(), q0 + u < nsl))
+                        break;
+                    if (q0 + u < nsl) {
+                        dva += w[u].x;
+                        dvm += w[u].y;
+                    }
+                }
             }
             if constexpr (STOR) {  // the bus's storage units: their five entries, the loss rows' vm part
                 const int2 stb = __ldg(d.bus_st + ib);
