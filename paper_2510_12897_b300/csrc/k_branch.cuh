@@ -99,10 +99,17 @@ __global__ void __launch_bounds__(OCC ? 256 : 512, OCC ? 3 : 1) branch_kernel(co
         if (CONS) {
             const double vf2 = vmf * vmf, vt2 = vmt * vmt;
             double *c = P.c + I.c0 + (T + rk);
-            c[0] = pf - fma(Yff.x, vf2, vft * Aft);
-            c[nlT] = qf - fma(neg(Yff.y), vf2, vft * Bft);
-            c[2 * nlT] = pt - fma(Ytt.x, vt2, vft * Atf);
-            c[3 * nlT] = qt - fma(neg(Ytt.y), vt2, vft * Btf);
+            if (SETF) {  // p, q were just set to these flows: the rows are exactly zero
+                c[0] = 0.0;
+                c[nlT] = 0.0;
+                c[2 * nlT] = 0.0;
+                c[3 * nlT] = 0.0;
+            } else {
+                c[0] = pf - fma(Yff.x, vf2, vft * Aft);
+                c[nlT] = qf - fma(neg(Yff.y), vf2, vft * Bft);
+                c[2 * nlT] = pt - fma(Ytt.x, vt2, vft * Atf);
+                c[3 * nlT] = qt - fma(neg(Ytt.y), vt2, vft * Btf);
+            }
             c[4 * nlT] = dlt;
             c[5 * nlT + 2 * nbT] = fma(pf, pf, qf * qf) - cur.r2;
             c[6 * nlT + 2 * nbT] = fma(pt, pt, qt * qt) - cur.r2;
