@@ -125,14 +125,20 @@ def profile_traffic(kernel):
 
 def profile_source(kernel):
     """Where a stored per-launch counter comes from: the committed ncu
-    summary (its first indented line is the ncu command that produced it)."""
+    summary (its first indented block is the ncu command that produced it,
+    continued over lines that end in a backslash)."""
     path = os.path.join("profiles", f"{kernel}_kernel_case10k.md")
     cmd = None
     try:
+        parts = []
         for line in open(os.path.join(ROOT, path)):
-            if line.startswith("    ncu"):
-                cmd = line.strip()
+            if not parts and not line.startswith("    ncu"):
+                continue
+            text = line.strip()
+            parts.append(text.rstrip("\\").strip())
+            if not text.endswith("\\"):
                 break
+        cmd = " ".join(parts) if parts else None
     except OSError:
         return None
     return {"from_profile": path, "ncu_command": cmd,

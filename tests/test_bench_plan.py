@@ -52,3 +52,17 @@ def test_bench_driver_command_prints_a_full_line():
     assert e2e["value"] > 0 and e2e["h2d_bytes_per_step"] > 0 and e2e["d2h_bytes_per_step"] > 0
     assert d["gpu_launches"] >= 20
     assert d["clocks"]["samples"] >= 1
+
+
+@pytest.mark.parametrize("kernel", ["fused", "branch", "bus"])
+def test_stored_counters_and_their_commands(kernel):
+    """The per-launch counters bench.py reads from the committed ncu
+    summaries parse, and each names the whole ncu command that took them
+    (clocks left alone, a bench.py run of committed files)."""
+    import bench
+    assert bench.profile_value(kernel, "dram_bytes_per_launch") > 0
+    assert bench.profile_value(kernel, "fp64_flops_per_launch") > 0
+    src = bench.profile_source(kernel)
+    cmd = src["ncu_command"]
+    assert cmd.startswith("ncu ") and "--clock-control none" in cmd
+    assert "python bench.py" in cmd and "\\" not in cmd
